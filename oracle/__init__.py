@@ -1,0 +1,252 @@
+"""ctypes wrapper of the CPU oracle -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
+arm of ``bench.py`` may import this package.  The CUDA library never loads it.
+
+The oracle is plain single-threaded C (``f2m_oracle.c``, ``certify.c``), built
+with ``gcc -O2`` and no fast-math by ``build()``.  Arrays cross as numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_SOURCES = ["f2m_oracle.c", "certify.c"]
+
+OR_OK = 0
+OR_INVALID = 1
+OR_NOT_CONVERGED = 4
+OR_OVERFLOW = 5
+OR_PRICING_OVERFLOW = 6
+OR_INFEASIBLE = 7
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/_build/liboracle.so (gcc -O2, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES + ["f2m_oracle.h"]]
+    if not force and os.path.exists(_LIB_PATH):
+        t = os.path.getmtime(_LIB_PATH)
+        if all(os.path.getmtime(s) <= t for s in srcs):
+            return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-Wextra",
+           "-fno-fast-math", "-o", tmp] + [os.path.join(_HERE, s) for s in _SOURCES] + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_lib = None
+
+_i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+_u8p = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+
+
+class _Params(C.Structure):
+    _fields_ = [("frac_bits", C.c_int32), ("damping_shift", C.c_int32),
+                ("max_iters", C.c_int64), ("max_pricing_rounds", C.c_int32),
+                ("pricing", C.c_int32), ("finisher", C.c_int32)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("iterations", C.c_int64), ("phases", C.c_int64),
+                ("pricing_rounds", C.c_int64), ("edges_added", C.c_int64),
+                ("finisher_calls", C.c_int64), ("augmentations", C.c_int64),
+                ("bound2", C.c_int64), ("frac_bits", C.c_int32),
+                ("certified", C.c_int32), ("status", C.c_int32)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        L.or_nint_sqrt.restype = C.c_int64
+        L.or_nint_sqrt.argtypes = [C.c_int64]
+        L.or_nint_sqrt_array.argtypes = [C.c_int64, _i64p, _i64p]
+        L.or_cost_table.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _i32p]
+        L.or_sweep.restype = C.c_int
+        L.or_sweep.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _i32p, C.c_int32, C.c_int32,
+                               _i32p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.or_bound2.restype = C.c_int64
+        L.or_bound2.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _i32p, C.c_int32]
+        L.or_gdp.restype = C.c_int
+        L.or_gdp.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_int32, C.c_int32, C.c_int64,
+                             _i32p, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p, C.c_int64]
+        L.or_extract.restype = C.c_int64
+        L.or_extract.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _i32p, C.c_int32, _u8p]
+        L.or_finisher.restype = C.c_int
+        L.or_finisher.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _i32p, C.c_int32, _u8p,
+                                  _i32p, C.POINTER(C.c_int64)]
+        L.or_pricing_rows.restype = C.c_int64
+        L.or_pricing_rows.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _i32p, C.c_int32,
+                                      C.c_int32, C.c_int32, C.c_void_p, C.c_int64]
+        L.or_merge.restype = C.c_int64
+        L.or_merge.argtypes = [C.c_int32, _i32p, _i32p, C.c_int64, _i32p, _i32p, _i32p]
+        L.or_solve.restype = C.c_void_p
+        L.or_solve.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_void_p,
+                               C.POINTER(_Params), C.POINTER(_Info), C.c_void_p, C.c_void_p,
+                               C.c_int64]
+        L.or_result_nnz.restype = C.c_int64
+        L.or_result_nnz.argtypes = [C.c_void_p]
+        L.or_result_copy.argtypes = [C.c_void_p, _i32p, _i32p, _u8p, _i32p]
+        L.or_result_free.argtypes = [C.c_void_p]
+        L.or_certify.restype = C.c_int
+        L.or_certify.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _u8p, _i32p, C.c_int32,
+                                 C.c_int64, C.c_int32]
+        _lib = L
+    return _lib
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def nint_sqrt(d2) -> np.ndarray:
+    d2 = np.ascontiguousarray(d2, dtype=np.int64)
+    out = np.empty_like(d2)
+    lib().or_nint_sqrt_array(d2.size, d2.reshape(-1), out.reshape(-1))
+    return out
+
+
+def cost_table(xy, row_ptr, col) -> np.ndarray:
+    xy, row_ptr, col = _i32(xy), _i32(row_ptr), _i32(col)
+    out = np.empty(col.size, dtype=np.int32)
+    lib().or_cost_table(row_ptr.size - 1, xy.reshape(-1), row_ptr, col, out)
+    return out
+
+
+def sweep(row_ptr, col, cost, lam, F=8, shift=2):
+    """One Jacobi GDP sweep: returns (status, lam_new, bound2, changed)."""
+    row_ptr, col, cost, lam = _i32(row_ptr), _i32(col), _i32(cost), _i32(lam)
+    out = np.empty_like(lam)
+    b2, ch = C.c_int64(), C.c_int64()
+    st = lib().or_sweep(lam.size, row_ptr, col, cost, lam, F, shift, out, C.byref(b2), C.byref(ch))
+    return st, out, b2.value, ch.value
+
+
+def bound2(row_ptr, col, cost, lam, fb=8) -> int:
+    return int(lib().or_bound2(row_ptr.size - 1, _i32(row_ptr), _i32(col), _i32(cost), _i32(lam), fb))
+
+
+def gdp(row_ptr, col, cost, lam0, F=8, shift=2, max_iters=100000, trace=False):
+    """GDP phase: returns (status, lam, iters, trace_bound2, trace_changed)."""
+    lam = _i32(lam0).copy()
+    it = C.c_int64()
+    tb = np.zeros(max_iters if trace else 1, dtype=np.int64)
+    tc = np.zeros_like(tb)
+    st = lib().or_gdp(lam.size, _i32(row_ptr), _i32(col), _i32(cost), F, shift, max_iters, lam,
+                      C.byref(it), tb.ctypes.data if trace else None,
+                      tc.ctypes.data if trace else None, max_iters if trace else 0)
+    k = it.value
+    return st, lam, k, (tb[:k] if trace else None), (tc[:k] if trace else None)
+
+
+def extract(row_ptr, col, cost, lam, fb=8):
+    x2 = np.zeros(np.asarray(col).size, dtype=np.uint8)
+    bad = lib().or_extract(row_ptr.size - 1, _i32(row_ptr), _i32(col), _i32(cost), _i32(lam), fb, x2)
+    return int(bad), x2
+
+
+def finisher(row_ptr, col, cost, lam, F=8):
+    """Exact min-cost-flow finisher: returns (status, x2, lam2 at F+1 bits, augmentations)."""
+    x2 = np.zeros(np.asarray(col).size, dtype=np.uint8)
+    lam = _i32(lam)
+    lam2 = np.zeros_like(lam)
+    aug = C.c_int64()
+    st = lib().or_finisher(lam.size, _i32(row_ptr), _i32(col), _i32(cost), lam, F, x2, lam2,
+                           C.byref(aug))
+    return st, x2, lam2, aug.value
+
+
+def pricing(xy, row_ptr, col, lam, fb=8, rows=None, cap=None):
+    """Pairs (u < v) outside the CSR with negative reduced cost, ascending; int32 [m, 2]."""
+    xy, row_ptr, col, lam = _i32(xy), _i32(row_ptr), _i32(col), _i32(lam)
+    n = lam.size
+    u0, u1 = (0, n) if rows is None else rows
+    cnt = lib().or_pricing_rows(n, xy.reshape(-1), row_ptr, col, lam, fb, u0, u1, None, 0)
+    if cap is not None and cnt > cap:
+        return cnt, None
+    out = np.zeros((max(cnt, 1), 2), dtype=np.int32)
+    lib().or_pricing_rows(n, xy.reshape(-1), row_ptr, col, lam, fb, u0, u1, out.ctypes.data, cnt)
+    return cnt, out[:cnt]
+
+
+def merge(row_ptr, col, pairs):
+    row_ptr, col = _i32(row_ptr), _i32(col)
+    pairs = _i32(np.asarray(pairs).reshape(-1, 2))
+    n = row_ptr.size - 1
+    nrp = np.zeros(n + 1, dtype=np.int32)
+    ncl = np.zeros(col.size + 2 * pairs.shape[0] + 1, dtype=np.int32)
+    nnz = lib().or_merge(n, row_ptr, col, pairs.shape[0], pairs.reshape(-1) if pairs.size else np.zeros(2, np.int32), nrp, ncl)
+    return nrp, ncl[:nnz].copy()
+
+
+@dataclass
+class OracleResult:
+    status: int
+    iterations: int
+    phases: int
+    pricing_rounds: int
+    edges_added: int
+    finisher_calls: int
+    augmentations: int
+    bound2: int
+    frac_bits: int
+    certified: int
+    row_ptr: np.ndarray
+    col: np.ndarray
+    x2: np.ndarray
+    lam: np.ndarray
+    trace_bound2: np.ndarray | None = None
+    trace_changed: np.ndarray | None = None
+
+    @property
+    def opt(self) -> float:
+        """The dual bound as a length: bound2 / (2 * 2^frac_bits)."""
+        return self.bound2 / (2.0 * (1 << self.frac_bits))
+
+
+def solve(xy, row_ptr, col, lam0=None, F=8, shift=2, max_iters=200000, max_pricing_rounds=64,
+          pricing=True, finisher=True, trace_cap=0) -> OracleResult:
+    xy, row_ptr, col = _i32(xy), _i32(row_ptr), _i32(col)
+    n = row_ptr.size - 1
+    p = _Params(F, shift, max_iters, max_pricing_rounds, int(pricing), int(finisher))
+    info = _Info()
+    lam0a = None if lam0 is None else _i32(lam0)
+    tb = np.zeros(max(trace_cap, 1), dtype=np.int64)
+    tc = np.zeros_like(tb)
+    h = lib().or_solve(n, xy.reshape(-1), row_ptr, col,
+                       None if lam0a is None else lam0a.ctypes.data, C.byref(p), C.byref(info),
+                       tb.ctypes.data if trace_cap else None,
+                       tc.ctypes.data if trace_cap else None, trace_cap)
+    try:
+        nnz = lib().or_result_nnz(h)
+        rp = np.zeros(n + 1, dtype=np.int32)
+        cl = np.zeros(max(nnz, 1), dtype=np.int32)
+        x2 = np.zeros(max(nnz, 1), dtype=np.uint8)
+        lam = np.zeros(n, dtype=np.int32)
+        lib().or_result_copy(h, rp, cl, x2, lam)
+    finally:
+        lib().or_result_free(h)
+    k = min(info.iterations, trace_cap)
+    return OracleResult(info.status, info.iterations, info.phases, info.pricing_rounds,
+                        info.edges_added, info.finisher_calls, info.augmentations, info.bound2,
+                        info.frac_bits, info.certified, rp, cl[:nnz], x2[:nnz], lam,
+                        tb[:k] if trace_cap else None, tc[:k] if trace_cap else None)
+
+
+def certify(xy, row_ptr, col, x2, lam, fb, bound2, full_scan=True) -> int:
+    """0 if (x2, lam) is certified optimal (see certify.c), else the failed check number."""
+    xy, row_ptr, col = _i32(xy), _i32(row_ptr), _i32(col)
+    return int(lib().or_certify(row_ptr.size - 1, xy.reshape(-1), row_ptr, col,
+                                np.ascontiguousarray(x2, dtype=np.uint8), _i32(lam), fb,
+                                int(bound2), int(full_scan)))
