@@ -1,0 +1,200 @@
+/* f2m.h -- C ABI of the GB300 (sm_103a) solver for the fractional 2-matching
+ * (F2M) LP relaxation of the TSP by the gradient descent procedure (GDP) of
+ * A. Antonov, "Gradient descent procedure for solving linear programming
+ * relaxations of combinatorial optimization problems in parallel mode on extra
+ * large scale" (arXiv 2011.08170).
+ *
+ * The problem (Section 4, "F2M"): given points p_v with integer coordinates and
+ * an undirected candidate edge set E, minimise sum_e c_e x_e subject to
+ * sum_{e in delta(v)} x_e = 2 for every node v and 0 <= x_e <= 1.  Costs are
+ * TSPLIB EUC_2D lengths c_uv = floor(sqrt(dx^2 + dy^2) + 1/2) (the input of the
+ * paper's program is TSPLIB 2-D coordinates, Section 5.1).  The optimum is
+ * {0, 1/2, 1} valued (Section 4).
+ *
+ * The method (Sections 2-4): lambda_v is adjusted until the modified objective
+ * z_e = c_e - lambda_u - lambda_v (Eq. 9) is "trivial": z_e < 0 on x_e = 1,
+ * z_e = 0 on x_e = 1/2, z_e > 0 on x_e = 0 (rule (7)).  The gradient at v is
+ * taken from the 2nd and 3rd shortest adjusted edges at v (Eq. 10), computed
+ * for every node in parallel (Section 5.1).
+ *
+ * Numbers.  lambda and z are exact fixed-point integers in units of
+ * 2^-frac_bits of a length unit.  One GDP sweep (Jacobi) sets, for every v,
+ *   delta_v = trunc((z(2) + z(3)) / 2^damping_shift),  lambda_v += delta_v,
+ * where z(2) <= z(3) are the 2nd and 3rd smallest z over the row of v.  The dual
+ * bound reported is bound2 = 2 * LB = 4 * sum_v lambda_v + sum over directed
+ * CSR entries of min(0, z_e), i.e. twice the Lagrangian bound
+ * LB = 2 sum lambda + sum_e min(0, z_e), in units of 2^-frac_bits.  Every result
+ * is bit-exact and independent of thread scheduling.
+ *
+ * A solve repeats: GDP to a fixed point; an all-pairs pricing scan that adds
+ * every non-candidate edge with z < 0 (the candidate graph may miss optimal
+ * edges, Section 5.3); primal x from the signs of z (rule 7); where that x is
+ * infeasible (the degenerate stops of Section 3, last paragraph) an exact
+ * min-cost-flow finisher on the host, after which lambda has frac_bits + 1
+ * bits.  It ends when a scan with the final lambda finds nothing: x and lambda
+ * are then certified optimal for the COMPLETE graph on the points.
+ *
+ * Conventions.
+ *  - Pointers marked "host or device" may point to either; the library asks
+ *    the driver which.  Work runs on the stream given at create time.
+ *  - The library copies every input; the caller owns every output buffer.
+ *  - No call exits or aborts.  Each returns a status; f2m_last_error(ctx)
+ *    gives a message for the last failure on that context.
+ *  - A context is not thread-safe: use one per host thread.
+ *  - Indices in and out are the caller's numbering.
+ */
+#ifndef F2M_H
+#define F2M_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  F2M_OK = 0,
+  F2M_ERR_INVALID_ARG = 1,      /* bad size, range, pointer or CSR */
+  F2M_ERR_CUDA = 2,             /* a CUDA call failed */
+  F2M_ERR_OOM = 3,              /* device or host allocation failed */
+  F2M_ERR_NOT_CONVERGED = 4,    /* iteration or pricing-round cap reached */
+  F2M_ERR_OVERFLOW = 5,         /* some |lambda| reached 2^29 (units 2^-F) */
+  F2M_ERR_PRICING_OVERFLOW = 6, /* pair buffer too small (handled inside f2m_solve) */
+  F2M_ERR_INFEASIBLE = 7,       /* no fractional 2-matching on the candidate graph */
+  F2M_ERR_TIMEOUT = 8           /* a device-wide barrier wait ran past its budget */
+} f2m_status;
+
+typedef struct f2m_ctx f2m_ctx;   /* opaque, library-owned */
+
+typedef struct {
+  int32_t frac_bits;            /* F, fractional bits of lambda; 1..8; default 8 */
+  int32_t damping_shift;        /* delta = trunc((z2+z3) / 2^shift); 1..8; default 2 */
+  int64_t max_iters;            /* sweeps per GDP phase; default 1,000,000 */
+  int32_t max_pricing_rounds;   /* pricing scans per solve; default 64 */
+  int32_t pricing;              /* 0 = solve on the candidate graph only, 1 = full scan (default) */
+  int64_t pricing_cap;          /* initial pair-buffer capacity; default 1 << 20 */
+  int64_t barrier_budget_cycles;/* spin budget of one device-wide barrier wait; default 4e9 */
+  int32_t finisher;             /* 1 = exact finisher when rule (7) gives an infeasible x (default) */
+  uint32_t flags;               /* reserved, 0 */
+} f2m_params;
+
+typedef struct {
+  int64_t iterations;           /* GDP sweeps, all phases */
+  int64_t phases;               /* GDP phases */
+  int64_t pricing_rounds;       /* pricing scans */
+  int64_t edges_added;          /* undirected edges added by pricing */
+  int64_t finisher_calls;
+  int64_t augmentations;        /* unit augmentations in the finisher */
+  int64_t bound2;               /* 2*LB in units 2^-frac_bits */
+  int64_t nnz;                  /* directed CSR entries after pricing */
+  int32_t frac_bits;            /* of bound2 and lambda: F, or F+1 after the finisher */
+  int32_t certified;            /* 0 none, 1 optimal on the candidate graph, 2 optimal on all pairs */
+  int32_t status;               /* f2m_status of the solve */
+  int32_t reserved;
+  double ms_gdp;                /* device time of the GDP phases */
+  double ms_pricing;            /* device time of the pricing scans */
+  double ms_merge;              /* device time of the CSR merges */
+  double ms_extract;            /* device time of the sign extraction */
+  double ms_finish;             /* host time of the finisher incl. copies */
+  double ms_total;              /* host wall time of f2m_solve */
+} f2m_info;
+
+/* Fills *p with the defaults above.  p must not be NULL. */
+void f2m_default_params(f2m_params* p);
+
+/* Creates a solver context for one instance (Section 4 F2M on a candidate graph;
+ * Section 5.1 input: 2-D integer coordinates).
+ *   xy       [n][2] int32, host or device; every coordinate in [0, 2^20).
+ *   n        number of nodes, 4 <= n < 2^24.
+ *   row_ptr  [n+1] int32, host or device; row_ptr[0] = 0, nondecreasing.
+ *   col      [row_ptr[n]] int32, host or device; the candidate graph with both
+ *            directions stored, each row sorted ascending, no self-loops, no
+ *            duplicates, and every node of degree >= 3 (Eq. 10 needs a 3rd edge).
+ *   params   NULL for defaults.
+ *   stream   cudaStream_t (as void*) on which all work of this context runs;
+ *            NULL = the legacy default stream.
+ *   out      receives the context; on failure *out is NULL.
+ * Computes the cost table (one exact integer cost per CSR entry) on the device.
+ * lambda starts at 0.  Errors: INVALID_ARG (with the first violated rule in
+ * f2m_last_error(NULL)), OOM, CUDA. */
+f2m_status f2m_create(const int32_t* xy, int32_t n, const int32_t* row_ptr, const int32_t* col,
+                      const f2m_params* params, void* stream, f2m_ctx** out);
+
+/* Releases all memory of ctx.  NULL is ignored. */
+void f2m_destroy(f2m_ctx* ctx);
+
+/* Sets lambda (warm start, resume from a checkpoint).
+ *   lambda  [n] int32, host or device, units 2^-frac_bits; |lambda| < 2^29.
+ * Errors: INVALID_ARG (range), CUDA. */
+f2m_status f2m_set_lambda(f2m_ctx* ctx, const int32_t* lambda, int32_t frac_bits);
+
+/* Full solve from the current lambda (see the header comment).  info may be
+ * NULL.  Returns F2M_OK when certified (info->certified = 2 with pricing on, 1
+ * with pricing off); NOT_CONVERGED when a cap ran out first (lambda and x
+ * then hold the last state); OVERFLOW, INFEASIBLE, TIMEOUT, CUDA, OOM. */
+f2m_status f2m_solve(f2m_ctx* ctx, f2m_info* info);
+
+/* ---- the hot-path steps, one call each (Sections 4 and 5.1) --------------- */
+
+/* One GDP phase (Eq. 9, Eq. 10, Jacobi): up to max_sweeps sweeps from the
+ * current lambda (units 2^-F), stopping after the first sweep that changes no
+ * lambda.  Runs as one persistent cooperative kernel with a device-wide
+ * barrier per sweep.
+ *   sweeps         out: sweeps run.
+ *   trace_bound2   NULL or [trace_cap] int64 (host or device): bound2 at the
+ *                  lambda each sweep started from.
+ *   trace_changed  NULL or [trace_cap] int64: #nodes whose lambda changed.
+ * Returns OK at a fixed point, NOT_CONVERGED at max_sweeps, OVERFLOW (lambda
+ * left at the input of the overflowing sweep), TIMEOUT, CUDA. */
+f2m_status f2m_gdp(f2m_ctx* ctx, int64_t max_sweeps, int64_t* sweeps, int64_t* trace_bound2,
+                   int64_t* trace_changed, int64_t trace_cap);
+
+/* Pricing scan: every pair u < v that is not a candidate edge and has
+ * c_uv * 2^fb < lambda_u + lambda_v (z < 0), fb = the current frac_bits.
+ *   count  out: number of such pairs (may exceed cap).
+ *   pairs  NULL or [cap][2] int32 (host or device): the pairs, ascending
+ *          (u, v) (caller numbering), when count <= cap.
+ * The pairs are not added; see f2m_add_edges.  Errors: CUDA, OOM. */
+f2m_status f2m_price(f2m_ctx* ctx, int64_t* count, int32_t* pairs, int64_t cap);
+
+/* Adds undirected edges to the candidate graph (both directions, rows kept
+ * sorted, pairs already present ignored) and their costs.
+ *   pairs  [npairs][2] int32, host or device, u != v, both in [0, n).
+ * Errors: INVALID_ARG, OOM, CUDA. */
+f2m_status f2m_add_edges(f2m_ctx* ctx, const int32_t* pairs, int64_t npairs);
+
+/* Primal from rule (7): x2_e = 2 if z_e < 0, 1 if z_e = 0, 0 if z_e > 0 (x in
+ * half units), at the current lambda.
+ *   x2   NULL or [nnz] uint8 (host or device), in the CSR order of f2m_get_x.
+ *   bad  out: number of nodes whose row of x2 does not sum to 4. */
+f2m_status f2m_extract(f2m_ctx* ctx, uint8_t* x2, int64_t* bad);
+
+/* ---- results ----------------------------------------------------------------- */
+
+/* lambda [n] int32 (host or device) in units 2^-(*frac_bits). */
+f2m_status f2m_get_lambda(f2m_ctx* ctx, int32_t* lambda, int32_t* frac_bits);
+
+/* bound2 = 2*LB at the current lambda, in units 2^-(*frac_bits). */
+f2m_status f2m_get_bound(f2m_ctx* ctx, int64_t* bound2, int32_t* frac_bits);
+
+/* The current candidate graph and x of the last solve (or extraction).
+ *   nnz_inout  in: capacity of col/x2; out: entries needed.  Call with NULL
+ *              arrays to query the size (it grows with pricing).
+ *   row_ptr    NULL or [n+1] int32;  col  NULL or [nnz] int32;
+ *   x2         NULL or [nnz] uint8 (0, 1, 2 = x of 0, 1/2, 1);
+ *   cost       NULL or [nnz] int32: c_e of each entry.
+ * All host or device.  INVALID_ARG if the capacity is too small. */
+f2m_status f2m_get_x(f2m_ctx* ctx, int64_t* nnz_inout, int32_t* row_ptr, int32_t* col,
+                     uint8_t* x2, int32_t* cost);
+
+/* Static text for a status code. */
+const char* f2m_status_string(f2m_status s);
+
+/* Message of the last failure on ctx (or of the last failed f2m_create when
+ * ctx is NULL); "" if none.  Valid until the next call on the same context. */
+const char* f2m_last_error(const f2m_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* F2M_H */

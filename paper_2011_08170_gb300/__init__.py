@@ -1,0 +1,322 @@
+"""Python binding of the f2m C ABI (include/f2m.h): argument marshalling only.
+
+Every step of the solve runs in the CUDA library ``_build/libf2m.so`` (built by
+``paper_2011_08170_gb300.build.build()``).  There is no fallback: if the library
+is missing or no GPU is present, ``load()`` raises.
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); outputs are
+numpy arrays unless ``device`` is given, in which case they are torch tensors
+allocated there.  Work runs on ``torch.cuda.current_stream()`` unless a stream
+is passed to ``f2m_create``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libf2m.so")
+
+F2M_OK = 0
+F2M_ERR_INVALID_ARG = 1
+F2M_ERR_CUDA = 2
+F2M_ERR_OOM = 3
+F2M_ERR_NOT_CONVERGED = 4
+F2M_ERR_OVERFLOW = 5
+F2M_ERR_PRICING_OVERFLOW = 6
+F2M_ERR_INFEASIBLE = 7
+F2M_ERR_TIMEOUT = 8
+
+# every symbol the header declares
+EXPORTS = ["f2m_default_params", "f2m_create", "f2m_destroy", "f2m_set_lambda", "f2m_solve",
+           "f2m_gdp", "f2m_price", "f2m_add_edges", "f2m_extract", "f2m_get_lambda",
+           "f2m_get_bound", "f2m_get_x", "f2m_status_string", "f2m_last_error"]
+
+
+class f2m_params(C.Structure):
+    _fields_ = [("frac_bits", C.c_int32), ("damping_shift", C.c_int32),
+                ("max_iters", C.c_int64), ("max_pricing_rounds", C.c_int32),
+                ("pricing", C.c_int32), ("pricing_cap", C.c_int64),
+                ("barrier_budget_cycles", C.c_int64), ("finisher", C.c_int32),
+                ("flags", C.c_uint32)]
+
+
+class f2m_info(C.Structure):
+    _fields_ = [("iterations", C.c_int64), ("phases", C.c_int64),
+                ("pricing_rounds", C.c_int64), ("edges_added", C.c_int64),
+                ("finisher_calls", C.c_int64), ("augmentations", C.c_int64),
+                ("bound2", C.c_int64), ("nnz", C.c_int64), ("frac_bits", C.c_int32),
+                ("certified", C.c_int32), ("status", C.c_int32), ("reserved", C.c_int32),
+                ("ms_gdp", C.c_double), ("ms_pricing", C.c_double), ("ms_merge", C.c_double),
+                ("ms_extract", C.c_double), ("ms_finish", C.c_double), ("ms_total", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class F2MError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libf2m.so and declare its signatures.  Raises if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"the f2m CUDA library is not built ({path}); run "
+                           "paper_2011_08170_gb300.build.build() first")
+    L = C.CDLL(path)
+    vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    L.f2m_default_params.argtypes = [C.POINTER(f2m_params)]
+    L.f2m_default_params.restype = None
+    L.f2m_create.argtypes = [vp, i32, vp, vp, C.POINTER(f2m_params), vp, C.POINTER(vp)]
+    L.f2m_destroy.argtypes = [vp]
+    L.f2m_destroy.restype = None
+    L.f2m_set_lambda.argtypes = [vp, vp, i32]
+    L.f2m_solve.argtypes = [vp, C.POINTER(f2m_info)]
+    L.f2m_gdp.argtypes = [vp, i64, C.POINTER(i64), vp, vp, i64]
+    L.f2m_price.argtypes = [vp, C.POINTER(i64), vp, i64]
+    L.f2m_add_edges.argtypes = [vp, vp, i64]
+    L.f2m_extract.argtypes = [vp, vp, C.POINTER(i64)]
+    L.f2m_get_lambda.argtypes = [vp, vp, C.POINTER(i32)]
+    L.f2m_get_bound.argtypes = [vp, C.POINTER(i64), C.POINTER(i32)]
+    L.f2m_get_x.argtypes = [vp, C.POINTER(i64), vp, vp, vp, vp]
+    L.f2m_status_string.argtypes = [i32]
+    L.f2m_status_string.restype = C.c_char_p
+    L.f2m_last_error.argtypes = [vp]
+    L.f2m_last_error.restype = C.c_char_p
+    for name in ("f2m_create", "f2m_set_lambda", "f2m_solve", "f2m_gdp", "f2m_price",
+                 "f2m_add_edges", "f2m_extract", "f2m_get_lambda", "f2m_get_bound", "f2m_get_x"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+# ---- marshalling helpers ------------------------------------------------------------
+
+def _ptr(a):
+    """(pointer, keepalive) for a numpy array or torch tensor; None passes NULL."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr"):  # torch tensor
+        if not a.is_contiguous():
+            a = a.contiguous()
+        return a.data_ptr(), a
+    a = np.ascontiguousarray(a)
+    return a.ctypes.data, a
+
+
+def _as(a, dtype):
+    if hasattr(a, "data_ptr"):
+        import torch
+        tmap = {np.int32: torch.int32, np.int64: torch.int64, np.uint8: torch.uint8}
+        return a.to(tmap[dtype]).contiguous()
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _out(shape, dtype, device):
+    if device is None:
+        return np.zeros(shape, dtype=dtype)
+    import torch
+    tmap = {np.int32: torch.int32, np.int64: torch.int64, np.uint8: torch.uint8}
+    return torch.zeros(shape, dtype=tmap[dtype], device=device)
+
+
+def _stream_handle(stream):
+    if stream is not None:
+        return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+class Ctx:
+    """Owns one f2m_ctx*; destroyed with the object."""
+
+    def __init__(self, handle, n):
+        self.handle = handle
+        self.n = n
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.f2m_destroy(self.handle)
+            self.handle = None
+
+
+def _check(ctx, st):
+    if st != F2M_OK:
+        L = load()
+        msg = L.f2m_last_error(ctx.handle if isinstance(ctx, Ctx) else None).decode()
+        name = L.f2m_status_string(st).decode()
+        raise F2MError(st, f"{name}: {msg}")
+
+
+# ---- the C ABI, one function each --------------------------------------------------
+
+def f2m_default_params(**overrides) -> f2m_params:
+    p = f2m_params()
+    load().f2m_default_params(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def f2m_create(xy, row_ptr, col, params: f2m_params | None = None, stream=None) -> Ctx:
+    L = load()
+    xy = _as(xy, np.int32)
+    row_ptr = _as(row_ptr, np.int32)
+    col = _as(col, np.int32)
+    n = int(row_ptr.shape[0]) - 1
+    pxy, k1 = _ptr(xy)
+    prp, k2 = _ptr(row_ptr)
+    pcol, k3 = _ptr(col)
+    h = C.c_void_p()
+    st = L.f2m_create(pxy, n, prp, pcol, C.byref(params) if params is not None else None,
+                      _stream_handle(stream), C.byref(h))
+    _check(None, st)
+    return Ctx(h.value, n)
+
+
+def f2m_destroy(ctx: Ctx) -> None:
+    if ctx.handle:
+        load().f2m_destroy(ctx.handle)
+        ctx.handle = None
+
+
+def f2m_set_lambda(ctx: Ctx, lam, frac_bits: int) -> None:
+    p, keep = _ptr(_as(lam, np.int32))
+    _check(ctx, load().f2m_set_lambda(ctx.handle, p, frac_bits))
+
+
+def f2m_solve(ctx: Ctx, raise_on_error: bool = True) -> f2m_info:
+    info = f2m_info()
+    st = load().f2m_solve(ctx.handle, C.byref(info))
+    if raise_on_error:
+        _check(ctx, st)
+    return info
+
+
+def f2m_gdp(ctx: Ctx, max_sweeps: int, trace_cap: int = 0):
+    """One GDP phase; returns (status, sweeps, trace_bound2, trace_changed)."""
+    sw = C.c_int64()
+    tb = np.zeros(max(trace_cap, 1), np.int64)
+    tc = np.zeros(max(trace_cap, 1), np.int64)
+    st = load().f2m_gdp(ctx.handle, max_sweeps, C.byref(sw), tb.ctypes.data if trace_cap else None,
+                        tc.ctypes.data if trace_cap else None, trace_cap)
+    if st not in (F2M_OK, F2M_ERR_NOT_CONVERGED, F2M_ERR_OVERFLOW, F2M_ERR_TIMEOUT):
+        _check(ctx, st)
+    k = min(sw.value, trace_cap)
+    return st, sw.value, (tb[:k] if trace_cap else None), (tc[:k] if trace_cap else None)
+
+
+def f2m_price(ctx: Ctx, cap: int | None = None):
+    """Pricing scan; returns (count, pairs int32 [count, 2] in unspecified order)."""
+    L = load()
+    cnt = C.c_int64()
+    _check(ctx, L.f2m_price(ctx.handle, C.byref(cnt), None, 0))
+    c = cnt.value
+    if cap is not None and c > cap:
+        return c, None
+    out = np.zeros((max(c, 1), 2), np.int32)
+    if c:
+        _check(ctx, L.f2m_price(ctx.handle, C.byref(cnt), out.ctypes.data, c))
+    return c, out[:c]
+
+
+def f2m_add_edges(ctx: Ctx, pairs) -> None:
+    pairs = _as(pairs, np.int32)
+    npairs = int(pairs.shape[0]) if pairs.ndim == 2 else int(pairs.shape[0]) // 2
+    p, keep = _ptr(pairs)
+    _check(ctx, load().f2m_add_edges(ctx.handle, p, npairs))
+
+
+def f2m_extract(ctx: Ctx, device=None):
+    """Rule (7) extraction at the current lambda; returns (bad_rows, x2)."""
+    nnz = C.c_int64(0)
+    _check(ctx, load().f2m_get_x(ctx.handle, C.byref(nnz), None, None, None, None))
+    x2 = _out((nnz.value,), np.uint8, device)
+    p, keep = _ptr(x2)
+    bad = C.c_int64()
+    _check(ctx, load().f2m_extract(ctx.handle, p, C.byref(bad)))
+    return bad.value, x2
+
+
+def f2m_get_lambda(ctx: Ctx, device=None):
+    """Returns (lambda int32 [n], frac_bits)."""
+    lam = _out((ctx.n,), np.int32, device)
+    p, keep = _ptr(lam)
+    fb = C.c_int32()
+    _check(ctx, load().f2m_get_lambda(ctx.handle, p, C.byref(fb)))
+    return lam, fb.value
+
+
+def f2m_get_bound(ctx: Ctx):
+    """Returns (bound2, frac_bits): 2*LB in units 2^-frac_bits."""
+    b = C.c_int64()
+    fb = C.c_int32()
+    _check(ctx, load().f2m_get_bound(ctx.handle, C.byref(b), C.byref(fb)))
+    return b.value, fb.value
+
+
+def f2m_get_x(ctx: Ctx, device=None):
+    """Returns (row_ptr, col, x2, cost) of the current candidate graph."""
+    L = load()
+    nnz = C.c_int64(0)
+    _check(ctx, L.f2m_get_x(ctx.handle, C.byref(nnz), None, None, None, None))
+    rp = _out((ctx.n + 1,), np.int32, device)
+    col = _out((nnz.value,), np.int32, device)
+    x2 = _out((nnz.value,), np.uint8, device)
+    cost = _out((nnz.value,), np.int32, device)
+    ptrs = [_ptr(a) for a in (rp, col, x2, cost)]
+    _check(ctx, L.f2m_get_x(ctx.handle, C.byref(nnz), *[p for p, _ in ptrs]))
+    return rp, col, x2, cost
+
+
+@dataclass
+class Solution:
+    info: dict
+    row_ptr: np.ndarray
+    col: np.ndarray
+    x2: np.ndarray
+    lam: np.ndarray
+    frac_bits: int
+
+    @property
+    def opt(self) -> float:
+        """The certified optimum as a length: bound2 / (2 * 2^frac_bits)."""
+        return self.info["bound2"] / (2.0 * (1 << self.info["frac_bits"]))
+
+
+def solve(xy, row_ptr, col, lam0=None, params: f2m_params | None = None, stream=None) -> Solution:
+    """Create, optionally warm-start, solve, and read back everything."""
+    ctx = f2m_create(xy, row_ptr, col, params, stream)
+    try:
+        if lam0 is not None:
+            f2m_set_lambda(ctx, lam0, (params.frac_bits if params is not None else 8))
+        info = f2m_solve(ctx)
+        rp, c, x2, _ = f2m_get_x(ctx)
+        lam, fb = f2m_get_lambda(ctx)
+        return Solution(info.as_dict(), rp, c, x2, lam, fb)
+    finally:
+        f2m_destroy(ctx)
+
+
+def f2m_status_string(status: int) -> str:
+    return load().f2m_status_string(status).decode()
+
+
+def f2m_last_error(ctx: Ctx | None = None) -> str:
+    return load().f2m_last_error(ctx.handle if ctx is not None else None).decode()

@@ -1,0 +1,621 @@
+// C ABI of the f2m library (declared in include/f2m.h): context, input
+// validation, the hot-path step calls and the solve driver.
+//
+// The driver runs on the host and only sequences device work: every GDP sweep,
+// pricing test, merge and extraction runs in this library's kernels on the
+// context's stream; the host reads back one small status block per step.  The
+// exception is the exact finisher (finisher.cpp), a min-cost flow that runs on
+// the host when the sign rule (7) leaves some node with a row sum other than 2.
+#include <chrono>
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/f2m.h"
+#include "f2m_internal.h"
+
+using namespace f2m;
+
+struct f2m_ctx {
+  int32_t n = 0;
+  int64_t nnz = 0;
+  int64_t ec_cap = 0;
+  cudaStream_t st = nullptr;
+  f2m_params p{};
+  int num_sms = 0;
+  int2* d_xy = nullptr;
+  int32_t* d_rp = nullptr;
+  int2* d_ec = nullptr;
+  uint8_t* d_x2 = nullptr;
+  int32_t* d_lam[2] = {nullptr, nullptr};
+  int32_t* d_lam2 = nullptr;
+  int cur = 0;          // d_lam[cur] holds lambda in units 2^-F
+  int32_t fb_cur = 8;   // F, or F+1 while d_lam2 holds the current lambda
+  GdpCtl* d_gdp = nullptr;
+  long long* d_trace_b2 = nullptr;
+  unsigned long long* d_trace_ch = nullptr;
+  int64_t trace_cap = 0;
+  float4* d_pts = nullptr;
+  int2* d_pairs = nullptr;
+  int64_t pairs_cap = 0;
+  int64_t npairs = 0;   // pairs held in d_pairs after the last scan
+  unsigned long long* d_count = nullptr;
+  unsigned int* d_tile = nullptr;
+  int32_t* d_deg = nullptr;
+  int32_t* d_tmp_rp = nullptr;
+  int32_t* d_new_rp = nullptr;
+  int32_t* d_block_sums = nullptr;
+  int32_t* d_tmp_col = nullptr;
+  int64_t tmp_col_cap = 0;
+  int32_t* d_out_a = nullptr;  // split scratch for f2m_get_x
+  int32_t* d_out_b = nullptr;
+  int64_t out_cap = 0;
+  CheckCtl* d_check = nullptr;
+  long long* d_scalar = nullptr;
+  unsigned long long* d_bad = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::string err;
+};
+
+static thread_local std::string g_create_error;
+
+static f2m_status fail(f2m_ctx* ctx, f2m_status s, const std::string& msg) {
+  if (ctx) ctx->err = msg; else g_create_error = msg;
+  return s;
+}
+
+static f2m_status cuda_fail(f2m_ctx* ctx, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return fail(ctx, F2M_ERR_OOM, m);
+  return fail(ctx, F2M_ERR_CUDA, m);
+}
+
+#define CK(ctx, call)                                          \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
+  } while (0)
+
+template <typename T>
+static cudaError_t dalloc(T** p, int64_t count) {
+  *p = nullptr;
+  size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
+  return cudaMalloc((void**)p, bytes);
+}
+
+template <typename T>
+static void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+static float elapsed_ms(f2m_ctx* c) {
+  float ms = 0.f;
+  cudaEventSynchronize(c->ev1);
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  return ms;
+}
+
+extern "C" void f2m_default_params(f2m_params* p) {
+  if (!p) return;
+  p->frac_bits = 8;
+  p->damping_shift = 2;
+  p->max_iters = 1000000;
+  p->max_pricing_rounds = 64;
+  p->pricing = 1;
+  p->pricing_cap = 1 << 20;
+  p->barrier_budget_cycles = 4000000000LL;
+  p->finisher = 1;
+  p->flags = 0;
+}
+
+extern "C" const char* f2m_status_string(f2m_status s) {
+  switch (s) {
+    case F2M_OK: return "ok";
+    case F2M_ERR_INVALID_ARG: return "invalid argument";
+    case F2M_ERR_CUDA: return "CUDA error";
+    case F2M_ERR_OOM: return "out of memory";
+    case F2M_ERR_NOT_CONVERGED: return "not converged";
+    case F2M_ERR_OVERFLOW: return "lambda overflow";
+    case F2M_ERR_PRICING_OVERFLOW: return "pricing buffer overflow";
+    case F2M_ERR_INFEASIBLE: return "infeasible";
+    case F2M_ERR_TIMEOUT: return "device barrier timeout";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* f2m_last_error(const f2m_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+extern "C" void f2m_destroy(f2m_ctx* c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  dfree(c->d_xy); dfree(c->d_rp); dfree(c->d_ec); dfree(c->d_x2);
+  dfree(c->d_lam[0]); dfree(c->d_lam[1]); dfree(c->d_lam2); dfree(c->d_gdp);
+  dfree(c->d_trace_b2); dfree(c->d_trace_ch); dfree(c->d_pts); dfree(c->d_pairs);
+  dfree(c->d_count); dfree(c->d_tile); dfree(c->d_deg); dfree(c->d_tmp_rp); dfree(c->d_new_rp);
+  dfree(c->d_block_sums); dfree(c->d_tmp_col); dfree(c->d_out_a); dfree(c->d_out_b);
+  dfree(c->d_check); dfree(c->d_scalar); dfree(c->d_bad);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  delete c;
+}
+
+static f2m_status check_params(const f2m_params& p) {
+  if (p.frac_bits < 1 || p.frac_bits > 8) return fail(nullptr, F2M_ERR_INVALID_ARG, "frac_bits must be in 1..8");
+  if (p.damping_shift < 1 || p.damping_shift > 8) return fail(nullptr, F2M_ERR_INVALID_ARG, "damping_shift must be in 1..8");
+  if (p.max_iters < 0 || p.max_pricing_rounds < 0 || p.pricing_cap < 1 || p.barrier_budget_cycles < 0)
+    return fail(nullptr, F2M_ERR_INVALID_ARG, "negative cap or budget");
+  return F2M_OK;
+}
+
+static std::string check_message(int flags, int first) {
+  static const char* names[] = {"row_ptr not monotone or not ending at nnz", "column index out of range",
+                                "row not sorted ascending or duplicate column", "self-loop",
+                                "CSR not symmetric", "node degree below 3",
+                                "coordinate outside [0, 2^20)", "pair out of range or u == v"};
+  std::string m;
+  for (int b = 0; b < 8; ++b)
+    if (flags & (1 << b)) {
+      if (!m.empty()) m += "; ";
+      m += names[b];
+    }
+  return m + " (first at index " + std::to_string(first) + ")";
+}
+
+static cudaError_t reset_check(f2m_ctx* c) {
+  CheckCtl h{0, INT_MAX};
+  return cudaMemcpyAsync(c->d_check, &h, sizeof(h), cudaMemcpyHostToDevice, c->st);
+}
+
+static cudaError_t read_check(f2m_ctx* c, CheckCtl* h) {
+  cudaError_t e = cudaMemcpyAsync(h, c->d_check, sizeof(*h), cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  return e;
+}
+
+extern "C" f2m_status f2m_create(const int32_t* xy, int32_t n, const int32_t* row_ptr,
+                                 const int32_t* col, const f2m_params* params, void* stream,
+                                 f2m_ctx** out) {
+  if (!out) return fail(nullptr, F2M_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  g_create_error.clear();
+  if (!xy || !row_ptr || !col) return fail(nullptr, F2M_ERR_INVALID_ARG, "NULL input array");
+  if (n < 4 || n >= (1 << 24)) return fail(nullptr, F2M_ERR_INVALID_ARG, "n must be in [4, 2^24)");
+  f2m_params p;
+  if (params) p = *params; else f2m_default_params(&p);
+  if (check_params(p) != F2M_OK) return F2M_ERR_INVALID_ARG;
+
+  f2m_ctx* c = new (std::nothrow) f2m_ctx();
+  if (!c) return fail(nullptr, F2M_ERR_OOM, "host allocation");
+  c->n = n;
+  c->p = p;
+  c->st = (cudaStream_t)stream;
+  c->fb_cur = p.frac_bits;
+  f2m_status s = F2M_OK;
+  int32_t* d_col = nullptr;
+  do {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    if (e == cudaSuccess) e = dalloc(&c->d_rp, n + 1);
+    if (e == cudaSuccess) e = dalloc(&c->d_xy, n);
+    if (e == cudaSuccess) e = dalloc(&c->d_check, 1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_rp, row_ptr, sizeof(int32_t) * (n + 1), cudaMemcpyDefault, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_xy, xy, sizeof(int2) * n, cudaMemcpyDefault, c->st);
+    int32_t nnz_h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nnz_h, c->d_rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) { s = cuda_fail(nullptr, e, "create: upload"); break; }
+    if (nnz_h < 3 * (int64_t)n) { s = fail(nullptr, F2M_ERR_INVALID_ARG, "row_ptr[n] < 3n: some node has degree below 3"); break; }
+    c->nnz = nnz_h;
+    e = reset_check(c);
+    if (e == cudaSuccess) e = launch_check(c->d_xy, c->d_rp, nullptr, n, c->nnz, c->d_check, c->st);
+    CheckCtl h{};
+    if (e == cudaSuccess) e = read_check(c, &h);
+    if (e != cudaSuccess) { s = cuda_fail(nullptr, e, "create: check row_ptr"); break; }
+    if (h.flags) { s = fail(nullptr, F2M_ERR_INVALID_ARG, check_message(h.flags, h.first_bad)); break; }
+    e = dalloc(&d_col, c->nnz);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_col, col, sizeof(int32_t) * c->nnz, cudaMemcpyDefault, c->st);
+    if (e == cudaSuccess) e = reset_check(c);
+    if (e == cudaSuccess) e = launch_check(c->d_xy, c->d_rp, d_col, n, c->nnz, c->d_check, c->st);
+    if (e == cudaSuccess) e = read_check(c, &h);
+    if (e != cudaSuccess) { s = cuda_fail(nullptr, e, "create: check rows"); break; }
+    if (h.flags) { s = fail(nullptr, F2M_ERR_INVALID_ARG, check_message(h.flags, h.first_bad)); break; }
+    c->ec_cap = c->nnz + (c->nnz >> 3) + 4096;
+    e = dalloc(&c->d_ec, c->ec_cap);
+    if (e == cudaSuccess) e = launch_build_ec(c->d_xy, c->d_rp, d_col, n, c->d_ec, c->st);
+    if (e == cudaSuccess) e = dalloc(&c->d_x2, c->ec_cap);
+    if (e == cudaSuccess) e = dalloc(&c->d_lam[0], n);
+    if (e == cudaSuccess) e = dalloc(&c->d_lam[1], n);
+    if (e == cudaSuccess) e = dalloc(&c->d_lam2, n);
+    if (e == cudaSuccess) e = dalloc(&c->d_gdp, 1);
+    if (e == cudaSuccess) e = dalloc(&c->d_scalar, 1);
+    if (e == cudaSuccess) e = dalloc(&c->d_bad, 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_lam[0], 0, sizeof(int32_t) * n, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_lam[1], 0, sizeof(int32_t) * n, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_x2, 0, c->ec_cap, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) { s = cuda_fail(nullptr, e, "create: device setup"); break; }
+  } while (0);
+  dfree(d_col);
+  if (s != F2M_OK) {
+    f2m_destroy(c);
+    return s;
+  }
+  *out = c;
+  return F2M_OK;
+}
+
+__global__ void f2m_range_kernel(const int32_t* lam, int32_t n, long long limit, CheckCtl* ctl) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    const long long x = lam[v];
+    if (x >= limit || x <= -limit) {
+      atomicOr(&ctl->flags, 1);
+      atomicMin(&ctl->first_bad, (int)v);
+    }
+  }
+}
+
+extern "C" f2m_status f2m_set_lambda(f2m_ctx* c, const int32_t* lambda, int32_t frac_bits) {
+  if (!c || !lambda) return fail(c, F2M_ERR_INVALID_ARG, "NULL argument");
+  const int32_t F = c->p.frac_bits;
+  if (frac_bits != F && frac_bits != F + 1) return fail(c, F2M_ERR_INVALID_ARG, "frac_bits must be F or F+1");
+  int32_t* dst = frac_bits == F ? c->d_lam[c->cur] : c->d_lam2;
+  CK(c, cudaMemcpyAsync(dst, lambda, sizeof(int32_t) * c->n, cudaMemcpyDefault, c->st));
+  CK(c, reset_check(c));
+  const long long limit = frac_bits == F ? kLamLimit : 2 * kLamLimit;
+  f2m_range_kernel<<<(c->n + 255) / 256, 256, 0, c->st>>>(dst, c->n, limit, c->d_check);
+  CK(c, cudaGetLastError());
+  CheckCtl h{};
+  CK(c, read_check(c, &h));
+  if (h.flags) return fail(c, F2M_ERR_INVALID_ARG, "lambda out of range at node " + std::to_string(h.first_bad));
+  c->fb_cur = frac_bits;
+  return F2M_OK;
+}
+
+// lambda (device) and its fractional bits
+static const int32_t* cur_lambda(f2m_ctx* c, int32_t* fb) {
+  *fb = c->fb_cur;
+  return c->fb_cur == c->p.frac_bits ? c->d_lam[c->cur] : c->d_lam2;
+}
+
+static f2m_status gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, bool want_trace,
+                            int64_t trace_cap, double* ms) {
+  const int32_t F = c->p.frac_bits;
+  if (c->fb_cur != F) {  // continue from the finisher's lambda: floor to F bits
+    CK(c, launch_halve(c->d_lam2, c->d_lam[c->cur], c->n, c->st));
+    c->fb_cur = F;
+  }
+  if (want_trace && trace_cap > c->trace_cap) {
+    dfree(c->d_trace_b2);
+    dfree(c->d_trace_ch);
+    CK(c, dalloc(&c->d_trace_b2, trace_cap));
+    CK(c, dalloc(&c->d_trace_ch, trace_cap));
+    c->trace_cap = trace_cap;
+  }
+  CK(c, cudaMemsetAsync(c->d_gdp, 0, sizeof(GdpCtl), c->st));
+  CK(c, cudaEventRecord(c->ev0, c->st));
+  CK(c, launch_gdp(c->d_rp, c->d_ec, c->d_lam[c->cur], c->d_lam[c->cur ^ 1], c->n, F,
+                   c->p.damping_shift, max_sweeps, c->d_gdp, want_trace ? c->d_trace_b2 : nullptr,
+                   want_trace ? c->d_trace_ch : nullptr, want_trace ? trace_cap : 0,
+                   c->p.barrier_budget_cycles, c->num_sms, c->st));
+  CK(c, cudaEventRecord(c->ev1, c->st));
+  GdpCtl h{};
+  CK(c, cudaMemcpyAsync(&h, c->d_gdp, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  if (ms) *ms += elapsed_ms(c);
+  *sweeps = h.sweeps;
+  const bool ovf = (h.status & kGdpOverflow) != 0;
+  // the sweep that overflowed leaves lambda at its input; otherwise the last output
+  const long long used = ovf ? h.sweeps - 1 : h.sweeps;
+  if (used & 1) c->cur ^= 1;
+  if (h.status & kGdpTimeout) return fail(c, F2M_ERR_TIMEOUT, "device-wide barrier wait exceeded its budget");
+  if (ovf) return fail(c, F2M_ERR_OVERFLOW, "|lambda| reached 2^29");
+  if (!h.fixed_point) return F2M_ERR_NOT_CONVERGED;
+  return F2M_OK;
+}
+
+extern "C" f2m_status f2m_gdp(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, int64_t* trace_bound2,
+                              int64_t* trace_changed, int64_t trace_cap) {
+  if (!c || max_sweeps < 0) return fail(c, F2M_ERR_INVALID_ARG, "bad argument");
+  int64_t sw = 0;
+  const bool want = trace_cap > 0 && (trace_bound2 || trace_changed);
+  f2m_status s = gdp_phase(c, max_sweeps, &sw, want, trace_cap, nullptr);
+  if (sweeps) *sweeps = sw;
+  if (want && (s == F2M_OK || s == F2M_ERR_NOT_CONVERGED || s == F2M_ERR_OVERFLOW)) {
+    const int64_t k = sw < trace_cap ? sw : trace_cap;
+    if (k > 0 && trace_bound2)
+      CK(c, cudaMemcpyAsync(trace_bound2, c->d_trace_b2, sizeof(int64_t) * k, cudaMemcpyDefault, c->st));
+    if (k > 0 && trace_changed)
+      CK(c, cudaMemcpyAsync(trace_changed, c->d_trace_ch, sizeof(int64_t) * k, cudaMemcpyDefault, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+  }
+  return s;
+}
+
+// pricing scan into d_pairs (grown until every pair fits); count in c->npairs
+static f2m_status price_internal(f2m_ctx* c, double* ms) {
+  if (!c->d_pts) {
+    CK(c, dalloc(&c->d_pts, c->n));
+    CK(c, dalloc(&c->d_count, 1));
+    CK(c, dalloc(&c->d_tile, 1));
+  }
+  if (!c->d_pairs) {
+    c->pairs_cap = c->p.pricing_cap;
+    CK(c, dalloc(&c->d_pairs, c->pairs_cap));
+  }
+  int32_t fb = 0;
+  const int32_t* lam = cur_lambda(c, &fb);
+  for (;;) {
+    CK(c, cudaEventRecord(c->ev0, c->st));
+    CK(c, launch_pricing(c->d_xy, lam, c->d_rp, c->d_ec, c->n, fb, c->d_pts, c->d_pairs,
+                         c->pairs_cap, c->d_count, c->d_tile, c->num_sms, c->st));
+    CK(c, cudaEventRecord(c->ev1, c->st));
+    unsigned long long cnt = 0;
+    CK(c, cudaMemcpyAsync(&cnt, c->d_count, sizeof(cnt), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    if (ms) *ms += elapsed_ms(c);
+    c->npairs = (int64_t)cnt;
+    if ((int64_t)cnt <= c->pairs_cap) return F2M_OK;
+    dfree(c->d_pairs);
+    c->pairs_cap = (int64_t)cnt + ((int64_t)cnt >> 2) + 1024;
+    CK(c, dalloc(&c->d_pairs, c->pairs_cap));
+  }
+}
+
+extern "C" f2m_status f2m_price(f2m_ctx* c, int64_t* count, int32_t* pairs, int64_t cap) {
+  if (!c || !count) return fail(c, F2M_ERR_INVALID_ARG, "NULL argument");
+  f2m_status s = price_internal(c, nullptr);
+  if (s != F2M_OK) return s;
+  *count = c->npairs;
+  if (pairs && c->npairs > 0 && c->npairs <= cap) {
+    CK(c, cudaMemcpyAsync(pairs, c->d_pairs, sizeof(int2) * c->npairs, cudaMemcpyDefault, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+  }
+  return F2M_OK;
+}
+
+// CSR u pairs (device array of npairs int2)
+static f2m_status merge_internal(f2m_ctx* c, const int2* d_pairs, int64_t npairs, double* ms) {
+  const int32_t n = c->n;
+  if (!c->d_deg) {
+    CK(c, dalloc(&c->d_deg, n + 1));
+    CK(c, dalloc(&c->d_tmp_rp, n + 1));
+    CK(c, dalloc(&c->d_new_rp, n + 1));
+    CK(c, dalloc(&c->d_block_sums, (int64_t)scan_scratch_ints(n)));
+  }
+  const int64_t need = c->nnz + 2 * npairs;
+  if (need >= INT_MAX) return fail(c, F2M_ERR_INVALID_ARG, "graph would exceed 2^31 entries");
+  if (need > c->tmp_col_cap) {
+    dfree(c->d_tmp_col);
+    c->tmp_col_cap = need + (need >> 3);
+    CK(c, dalloc(&c->d_tmp_col, c->tmp_col_cap));
+  }
+  MergeBuffers mb{c->d_deg, c->d_tmp_rp, c->d_tmp_col, c->d_new_rp, c->d_block_sums, c->d_check};
+  CK(c, reset_check(c));
+  CK(c, cudaEventRecord(c->ev0, c->st));
+  CK(c, launch_merge_count(c->d_rp, d_pairs, npairs, n, mb, c->st));
+  CK(c, launch_merge_fill(c->d_rp, c->d_ec, d_pairs, npairs, n, mb, c->st));
+  if (need > c->ec_cap) {  // old entries now live in tmp_col: the edge array can be replaced
+    CK(c, cudaStreamSynchronize(c->st));
+    dfree(c->d_ec);
+    dfree(c->d_x2);
+    c->ec_cap = need + (need >> 3);
+    CK(c, dalloc(&c->d_ec, c->ec_cap));
+    CK(c, dalloc(&c->d_x2, c->ec_cap));
+  }
+  CK(c, launch_merge_finish(c->d_xy, n, mb, c->d_ec, c->st));
+  CK(c, cudaMemcpyAsync(c->d_rp, c->d_new_rp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToDevice, c->st));
+  CK(c, cudaEventRecord(c->ev1, c->st));
+  int32_t nnz_h = 0;
+  CK(c, cudaMemcpyAsync(&nnz_h, c->d_new_rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st));
+  CheckCtl h{};
+  CK(c, read_check(c, &h));
+  if (ms) *ms += elapsed_ms(c);
+  c->nnz = nnz_h;
+  if (h.flags) return fail(c, F2M_ERR_INVALID_ARG, check_message(h.flags, h.first_bad));
+  return F2M_OK;
+}
+
+extern "C" f2m_status f2m_add_edges(f2m_ctx* c, const int32_t* pairs, int64_t npairs) {
+  if (!c || (npairs > 0 && !pairs) || npairs < 0) return fail(c, F2M_ERR_INVALID_ARG, "bad argument");
+  if (npairs == 0) return F2M_OK;
+  int2* d = nullptr;
+  CK(c, dalloc(&d, npairs));
+  cudaError_t e = cudaMemcpyAsync(d, pairs, sizeof(int2) * npairs, cudaMemcpyDefault, c->st);
+  if (e != cudaSuccess) { dfree(d); return cuda_fail(c, e, "add_edges: upload"); }
+  f2m_status s = merge_internal(c, d, npairs, nullptr);
+  cudaStreamSynchronize(c->st);
+  dfree(d);
+  return s;
+}
+
+static f2m_status extract_internal(f2m_ctx* c, int64_t* bad, double* ms) {
+  int32_t fb = 0;
+  const int32_t* lam = cur_lambda(c, &fb);
+  CK(c, cudaEventRecord(c->ev0, c->st));
+  CK(c, launch_extract(c->d_rp, c->d_ec, lam, c->n, fb, c->d_x2, c->d_bad, c->st));
+  CK(c, cudaEventRecord(c->ev1, c->st));
+  unsigned long long b = 0;
+  CK(c, cudaMemcpyAsync(&b, c->d_bad, sizeof(b), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  if (ms) *ms += elapsed_ms(c);
+  *bad = (int64_t)b;
+  return F2M_OK;
+}
+
+extern "C" f2m_status f2m_extract(f2m_ctx* c, uint8_t* x2, int64_t* bad) {
+  if (!c || !bad) return fail(c, F2M_ERR_INVALID_ARG, "NULL argument");
+  f2m_status s = extract_internal(c, bad, nullptr);
+  if (s != F2M_OK) return s;
+  if (x2) {
+    CK(c, cudaMemcpyAsync(x2, c->d_x2, c->nnz, cudaMemcpyDefault, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+  }
+  return F2M_OK;
+}
+
+static f2m_status bound_internal(f2m_ctx* c, int64_t* b2) {
+  int32_t fb = 0;
+  const int32_t* lam = cur_lambda(c, &fb);
+  CK(c, launch_bound(c->d_rp, c->d_ec, lam, c->n, fb, c->d_scalar, c->st));
+  long long h = 0;
+  CK(c, cudaMemcpyAsync(&h, c->d_scalar, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  *b2 = h;
+  return F2M_OK;
+}
+
+static f2m_status finisher_internal(f2m_ctx* c, int64_t* aug) {
+  const int32_t n = c->n;
+  std::vector<int32_t> rp(n + 1), lam(n), lam2(n);
+  std::vector<int2> ec(c->nnz);
+  std::vector<uint8_t> x2(c->nnz);
+  CK(c, cudaMemcpyAsync(rp.data(), c->d_rp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaMemcpyAsync(ec.data(), c->d_ec, sizeof(int2) * c->nnz, cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaMemcpyAsync(lam.data(), c->d_lam[c->cur], sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  const int r = host_finisher(n, rp.data(), ec.data(), lam.data(), c->p.frac_bits, x2.data(),
+                              lam2.data(), aug);
+  if (r == 7) return fail(c, F2M_ERR_INFEASIBLE, "no fractional 2-matching exists on the candidate graph");
+  if (r == 5) return fail(c, F2M_ERR_OVERFLOW, "finisher lambda out of range");
+  if (r != 0) return fail(c, F2M_ERR_INVALID_ARG, "finisher: CSR not symmetric");
+  CK(c, cudaMemcpyAsync(c->d_x2, x2.data(), c->nnz, cudaMemcpyHostToDevice, c->st));
+  CK(c, cudaMemcpyAsync(c->d_lam2, lam2.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  c->fb_cur = c->p.frac_bits + 1;
+  return F2M_OK;
+}
+
+// The solve loop; its decisions match the CPU oracle's step for step:
+//   GDP phase -> (pricing rounds left: scan with the GDP lambda; pairs found ->
+//   merge, next phase) -> rule (7) -> finisher if some row is off -> scan with
+//   the final lambda (unless that lambda was just scanned) -> none: certified;
+//   else merge and continue GDP from lambda (F bits).
+extern "C" f2m_status f2m_solve(f2m_ctx* c, f2m_info* info_out) {
+  if (!c) return fail(c, F2M_ERR_INVALID_ARG, "NULL context");
+  const auto t0 = std::chrono::steady_clock::now();
+  f2m_info info;
+  std::memset(&info, 0, sizeof(info));
+  const int32_t F = c->p.frac_bits;
+  info.frac_bits = F;
+  f2m_status status = F2M_OK;
+  for (;;) {
+    int64_t sw = 0;
+    f2m_status s = gdp_phase(c, c->p.max_iters, &sw, false, 0, &info.ms_gdp);
+    info.iterations += sw;
+    info.phases += 1;
+    if (s != F2M_OK && s != F2M_ERR_NOT_CONVERGED) { status = s; break; }
+
+    bool clean = false;
+    if (c->p.pricing && info.pricing_rounds < c->p.max_pricing_rounds) {
+      s = price_internal(c, &info.ms_pricing);
+      if (s != F2M_OK) { status = s; break; }
+      info.pricing_rounds += 1;
+      if (c->npairs > 0) {
+        s = merge_internal(c, c->d_pairs, c->npairs, &info.ms_merge);
+        if (s != F2M_OK) { status = s; break; }
+        info.edges_added += c->npairs;
+        continue;
+      }
+      clean = true;
+    }
+
+    int64_t bad = 0;
+    s = extract_internal(c, &bad, &info.ms_extract);
+    if (s != F2M_OK) { status = s; break; }
+    if (bad > 0) {
+      if (!c->p.finisher) {
+        status = F2M_ERR_NOT_CONVERGED;
+        fail(c, status, std::to_string(bad) + " nodes violate the degree constraint and the finisher is off");
+        break;
+      }
+      const auto f0 = std::chrono::steady_clock::now();
+      int64_t aug = 0;
+      s = finisher_internal(c, &aug);
+      info.ms_finish += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - f0).count();
+      info.finisher_calls += 1;
+      info.augmentations += aug;
+      if (s != F2M_OK) { status = s; break; }
+    }
+    info.frac_bits = c->fb_cur;
+    info.certified = 1;
+    if (!c->p.pricing) break;
+    if (c->fb_cur == F && clean) { info.certified = 2; break; }
+    if (info.pricing_rounds >= c->p.max_pricing_rounds) {
+      status = F2M_ERR_NOT_CONVERGED;
+      fail(c, status, "pricing rounds exhausted");
+      break;
+    }
+    s = price_internal(c, &info.ms_pricing);
+    if (s != F2M_OK) { status = s; break; }
+    info.pricing_rounds += 1;
+    if (c->npairs == 0) { info.certified = 2; break; }
+    s = merge_internal(c, c->d_pairs, c->npairs, &info.ms_merge);
+    if (s != F2M_OK) { status = s; break; }
+    info.edges_added += c->npairs;
+    info.certified = 0;
+    info.frac_bits = F;
+  }
+  if (status == F2M_OK || status == F2M_ERR_NOT_CONVERGED) {
+    int64_t b2 = 0;
+    if (bound_internal(c, &b2) == F2M_OK) info.bound2 = b2;
+    info.frac_bits = c->fb_cur;
+  }
+  info.nnz = c->nnz;
+  info.status = status;
+  info.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (info_out) *info_out = info;
+  return status;
+}
+
+extern "C" f2m_status f2m_get_lambda(f2m_ctx* c, int32_t* lambda, int32_t* frac_bits) {
+  if (!c) return fail(c, F2M_ERR_INVALID_ARG, "NULL context");
+  int32_t fb = 0;
+  const int32_t* lam = cur_lambda(c, &fb);
+  if (frac_bits) *frac_bits = fb;
+  if (lambda) {
+    CK(c, cudaMemcpyAsync(lambda, lam, sizeof(int32_t) * c->n, cudaMemcpyDefault, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+  }
+  return F2M_OK;
+}
+
+extern "C" f2m_status f2m_get_bound(f2m_ctx* c, int64_t* bound2, int32_t* frac_bits) {
+  if (!c || !bound2) return fail(c, F2M_ERR_INVALID_ARG, "NULL argument");
+  if (frac_bits) *frac_bits = c->fb_cur;
+  return bound_internal(c, bound2);
+}
+
+extern "C" f2m_status f2m_get_x(f2m_ctx* c, int64_t* nnz_inout, int32_t* row_ptr, int32_t* col,
+                                uint8_t* x2, int32_t* cost) {
+  if (!c || !nnz_inout) return fail(c, F2M_ERR_INVALID_ARG, "NULL argument");
+  const int64_t cap = *nnz_inout;
+  *nnz_inout = c->nnz;
+  if (!row_ptr && !col && !x2 && !cost) return F2M_OK;
+  if ((col || x2 || cost) && cap < c->nnz) return fail(c, F2M_ERR_INVALID_ARG, "capacity below nnz");
+  if (row_ptr) CK(c, cudaMemcpyAsync(row_ptr, c->d_rp, sizeof(int32_t) * (c->n + 1), cudaMemcpyDefault, c->st));
+  if (x2 && c->nnz) CK(c, cudaMemcpyAsync(x2, c->d_x2, c->nnz, cudaMemcpyDefault, c->st));
+  if ((col || cost) && c->nnz) {
+    if (c->out_cap < c->nnz) {
+      dfree(c->d_out_a);
+      dfree(c->d_out_b);
+      c->out_cap = c->nnz;
+      CK(c, dalloc(&c->d_out_a, c->out_cap));
+      CK(c, dalloc(&c->d_out_b, c->out_cap));
+    }
+    CK(c, launch_split_ec(c->d_ec, c->nnz, c->d_out_a, c->d_out_b, c->st));
+    if (col) CK(c, cudaMemcpyAsync(col, c->d_out_a, sizeof(int32_t) * c->nnz, cudaMemcpyDefault, c->st));
+    if (cost) CK(c, cudaMemcpyAsync(cost, c->d_out_b, sizeof(int32_t) * c->nnz, cudaMemcpyDefault, c->st));
+  }
+  CK(c, cudaStreamSynchronize(c->st));
+  return F2M_OK;
+}

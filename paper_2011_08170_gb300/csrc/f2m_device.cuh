@@ -1,0 +1,81 @@
+// Device helpers shared by the f2m kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace f2m {
+
+// Edge cost c(u,v): the nearest integer to sqrt(d2), d2 = dx^2 + dy^2 (TSPLIB
+// EUC_2D, the input convention of Section 5.1).  Integer-exact: s is the floor
+// of sqrt(4*d2) (a double square root as first guess, then corrected in
+// integers), and nint(sqrt(d2)) = floor((s + 1) / 2).  No tie exists: an
+// integer d2 never equals (r + 1/2)^2.
+__device__ __forceinline__ int32_t exact_cost(int32_t dx, int32_t dy) {
+  long long d2 = (long long)dx * dx + (long long)dy * dy;
+  long long q = 4 * d2;  // < 2^43, exact in double
+  long long s = (long long)sqrt((double)q);
+  while (s * s > q) --s;
+  while ((s + 1) * (s + 1) <= q) ++s;
+  return (int32_t)((s + 1) >> 1);
+}
+
+__device__ __forceinline__ int32_t exact_cost(int2 a, int2 b) { return exact_cost(a.x - b.x, a.y - b.y); }
+
+// Keep the three smallest values seen, a <= b <= c (values only; ties are
+// irrelevant to Eq. 10, which needs the 2nd and 3rd values, not the edges).
+__device__ __forceinline__ void top3_insert(int z, int& a, int& b, int& c) {
+  if (z < c) {
+    c = z;
+    if (c < b) { int t = b; b = c; c = t; }
+    if (b < a) { int t = a; a = b; b = t; }
+  }
+}
+
+// Load that bypasses L1: lambda is rewritten by other SMs between sweeps.
+__device__ __forceinline__ int ld_cg(const int* p) { return __ldcg(p); }
+
+// Device-wide barrier for a cooperative launch, bounded: a block whose wait
+// runs past `budget` clock cycles gives up and reports false.  One arrival
+// counter plus a generation word; the last block to arrive resets the counter
+// and bumps the generation.
+__device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* gen,
+                                             unsigned int nblocks, long long budget) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned int* vgen = gen;
+    unsigned int g = *vgen;
+    __threadfence();
+    unsigned int prev = atomicAdd(count, 1u);
+    if (prev == nblocks - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      long long t0 = clock64();
+      while (*vgen == g) {
+        if (clock64() - t0 > budget) { ok = 0; break; }
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned warp_sum_u(unsigned v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace f2m

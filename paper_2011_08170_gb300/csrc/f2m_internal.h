@@ -1,0 +1,107 @@
+// Internal declarations of the f2m library (not part of the C ABI).
+//
+// Device data layout (one instance, n nodes, nnz directed CSR entries):
+//   xy    int2[n]          point coordinates, each in [0, 2^20)
+//   rp    int32[n+1]       CSR row offsets (both directions of every edge stored)
+//   ec    int2[nnz]        per entry {col, cost}: 8 bytes streamed per entry
+//   lam   int32[2][n]      lambda, Jacobi double buffer (units 2^-F)
+//   lam2  int32[n]         lambda of the finisher (units 2^-(F+1))
+//   x2    uint8[nnz]       primal x in half units
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace f2m {
+
+constexpr int32_t kCoordLimit = 1 << 20;   // coordinates in [0, 2^20)
+constexpr int64_t kLamLimit = 1LL << 29;   // |lambda| < 2^29 in units 2^-F
+
+// Control block of the persistent GDP kernel (device memory, zeroed per phase).
+struct GdpCtl {
+  unsigned int bar_count;      // arrivals at the current barrier
+  unsigned int bar_gen;        // barrier generation
+  int status;                  // bit 0: lambda overflow, bit 1: barrier timeout
+  int fixed_point;             // 1 if the last sweep changed no lambda
+  long long slot_b2[3];        // per-sweep bound2 accumulators (ring of 3)
+  unsigned long long slot_ch[3];  // per-sweep changed counts (ring of 3)
+  long long sweeps;            // sweeps completed
+  long long pad1;
+};
+
+constexpr int kGdpOverflow = 1;
+constexpr int kGdpTimeout = 2;
+
+// Validation result written by the create-time check kernel.
+struct CheckCtl {
+  int flags;                   // bit set per violated rule
+  int first_bad;               // smallest offending node (or entry)
+};
+
+enum CheckBits {
+  kBadRowPtr = 1,
+  kBadCol = 2,
+  kUnsorted = 4,
+  kSelfLoop = 8,
+  kAsymmetric = 16,
+  kLowDegree = 32,
+  kBadCoord = 64,
+  kBadPair = 128,
+};
+
+// ---- launchers (each enqueues on `st`) -------------------------------------
+
+// validation of the input CSR and points; ctl must be zeroed (first_bad = INT_MAX)
+cudaError_t launch_check(const int2* xy, const int32_t* rp, const int32_t* col, int32_t n,
+                         int64_t nnz, CheckCtl* ctl, cudaStream_t st);
+// ec[e] = {col[e], c(row(e), col[e])}
+cudaError_t launch_build_ec(const int2* xy, const int32_t* rp, const int32_t* col, int32_t n,
+                            int2* ec, cudaStream_t st);
+// one persistent cooperative GDP phase
+cudaError_t launch_gdp(const int32_t* rp, const int2* ec, int32_t* lam0, int32_t* lam1, int32_t n,
+                       int32_t F, int32_t shift, int64_t max_sweeps, GdpCtl* ctl,
+                       long long* trace_b2, unsigned long long* trace_ch, int64_t trace_cap,
+                       long long budget, int num_sms, cudaStream_t st);
+// bound2 at lam with fb fractional bits, into *out (zeroed by the launcher)
+cudaError_t launch_bound(const int32_t* rp, const int2* ec, const int32_t* lam, int32_t n,
+                         int32_t fb, long long* out, cudaStream_t st);
+// rule (7) extraction; *bad zeroed by the launcher
+cudaError_t launch_extract(const int32_t* rp, const int2* ec, const int32_t* lam, int32_t n,
+                           int32_t fb, uint8_t* x2, unsigned long long* bad, cudaStream_t st);
+// lam_out = lam_in >> 1 (F+1 bits -> F bits, floor)
+cudaError_t launch_halve(const int32_t* lam_in, int32_t* lam_out, int32_t n, cudaStream_t st);
+// all-pairs pricing scan: pairs (u < v) outside the CSR with z < 0
+cudaError_t launch_pricing(const int2* xy, const int32_t* lam, const int32_t* rp, const int2* ec,
+                           int32_t n, int32_t fb, float4* pts, int2* pairs, int64_t cap,
+                           unsigned long long* count, unsigned int* tile_counter, int num_sms,
+                           cudaStream_t st);
+// CSR union with pairs; sizes: see graph.cu.  Returns the new nnz through *new_nnz_dev.
+struct MergeBuffers {
+  int32_t* deg;        // [n+1]
+  int32_t* tmp_rp;     // [n+1]
+  int32_t* tmp_col;    // [nnz + 2*npairs]
+  int32_t* new_rp;     // [n+1]
+  int32_t* block_sums; // scan scratch
+  CheckCtl* ctl;
+};
+cudaError_t launch_merge_count(const int32_t* rp, const int2* pairs, int64_t npairs, int32_t n,
+                               MergeBuffers& mb, cudaStream_t st);
+cudaError_t launch_merge_fill(const int32_t* rp, const int2* ec, const int2* pairs, int64_t npairs,
+                              int32_t n, MergeBuffers& mb, cudaStream_t st);
+cudaError_t launch_merge_finish(const int2* xy, int32_t n, MergeBuffers& mb, int2* ec_out,
+                                cudaStream_t st);
+// exclusive scan of in[0..m) into out[0..m], out[m] = total (m+1 outputs)
+cudaError_t launch_scan(const int32_t* in, int32_t* out, int32_t m, int32_t* block_sums,
+                        cudaStream_t st);
+size_t scan_scratch_ints(int32_t m);
+// split ec into col / cost arrays
+cudaError_t launch_split_ec(const int2* ec, int64_t nnz, int32_t* col, int32_t* cost,
+                            cudaStream_t st);
+
+// ---- host finisher (finisher.cpp) --------------------------------------------
+// Exact min-cost flow on the bipartite double cover; see finisher.cpp.
+// Returns 0 ok, 7 infeasible, 5 overflow.
+int host_finisher(int32_t n, const int32_t* rp, const int2* ec, const int32_t* lam, int32_t F,
+                  uint8_t* x2, int32_t* lam2, int64_t* augmentations);
+
+}  // namespace f2m

@@ -1,0 +1,149 @@
+// Pricing scan: every pair u < v outside the candidate CSR with
+//   z_uv = c_uv * 2^fb - lambda_u - lambda_v < 0.
+// The paper solves on a top-N nearest-neighbour graph and notes that it can
+// miss optimal edges (Section 5.3); this scan finds every such edge so the
+// final duals are feasible for the complete graph.
+//
+// N-body tiling: the pair triangle is cut into TILE x TILE tile pairs (bi <= bj)
+// handed out by an atomic counter; a CTA keeps TILE j-points in shared memory
+// and each thread P i-points in registers.  Per pair an fp32 filter runs:
+//   t = s_u + s_v,   e = dy^2 + (dx^2 - t^2)   (two FMAs),   pass if e < 1,
+// with s_v = max(lambda_v * 2^-fb + 1/4, 0) * (1 + 2^-19).
+// No false negatives: z < 0 implies c < T = (lambda_u + lambda_v) 2^-fb, hence
+// sqrt(d2) < c + 1/2 < T + 1/2 <= r_u + r_v with r = max(lambda 2^-fb + 1/4, 0).
+// The rounding of r, s and t is below 2^-22 relative, so t >= (r_u + r_v)
+// (1 + 2^-20) and t^2 exceeds d2 by more than 2^-20 t^2, while the two FMAs
+// err by at most 2^-23 t^2; d2 < 1 (duplicate points) passes trivially.  Pairs
+// that pass are decided exactly in integers (exact cost, int64 z), then
+// checked against the CSR row by binary search, then appended.
+#include <climits>
+
+#include "f2m_device.cuh"
+#include "f2m_internal.h"
+
+namespace f2m {
+
+constexpr int kPriceThreads = 256;
+constexpr int kPriceP = 4;
+constexpr int kPriceTile = kPriceThreads * kPriceP;
+
+__global__ void pricing_prep_kernel(const int2* __restrict__ xy, const int32_t* __restrict__ lam,
+                                    int32_t n, int32_t fb, float4* __restrict__ pts) {
+  const float scale = ldexpf(1.0f, -fb);
+  const float grow = 1.0f + ldexpf(1.0f, -19);
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    const int2 p = xy[v];
+    float r = fmaxf((float)lam[v] * scale + 0.25f, 0.0f);
+    pts[v] = make_float4((float)p.x, (float)p.y, r * grow, 0.0f);
+  }
+}
+
+// exact decision for a pair that passed the filter
+__device__ __noinline__ void pricing_confirm(int i, int j, int32_t n, const int2* __restrict__ xy,
+                                             const int32_t* __restrict__ lam,
+                                             const int32_t* __restrict__ rp,
+                                             const int2* __restrict__ ec, int32_t fb, int2* pairs,
+                                             long long cap, unsigned long long* count) {
+  if (j <= i || j >= n) return;  // each unordered pair once; tail of the last tile
+  const long long S = (long long)lam[i] + lam[j];
+  if (S <= 0) return;
+  const long long c = exact_cost(xy[i], xy[j]);
+  if ((c << fb) - S >= 0) return;
+  int lo = rp[i], hi = rp[i + 1] - 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const int cm = ec[mid].x;
+    if (cm == j) return;  // already a candidate edge
+    if (cm < j) lo = mid + 1; else hi = mid - 1;
+  }
+  const unsigned long long k = atomicAdd(count, 1ull);
+  if ((long long)k < cap) pairs[k] = make_int2(i, j);
+}
+
+__global__ void __launch_bounds__(kPriceThreads)
+pricing_kernel(const float4* __restrict__ pts, const int2* __restrict__ xy,
+               const int32_t* __restrict__ lam, const int32_t* __restrict__ rp,
+               const int2* __restrict__ ec, int32_t n, int32_t fb, int2* pairs, long long cap,
+               unsigned long long* count, unsigned int* tile_counter, int ntiles) {
+  __shared__ float4 sj[kPriceTile];
+  __shared__ int s_tp;
+  const long long total = (long long)ntiles * (ntiles + 1) / 2;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_tp = (int)atomicAdd(tile_counter, 1u);
+    __syncthreads();
+    long long tp = s_tp;
+    if (tp >= total) break;
+    int bi = 0;
+    while (tp >= ntiles - bi) { tp -= ntiles - bi; ++bi; }
+    const int bj = bi + (int)tp;
+
+    float xi[kPriceP], yi[kPriceP], si[kPriceP];
+#pragma unroll
+    for (int p = 0; p < kPriceP; ++p) {
+      const int i = bi * kPriceTile + p * kPriceThreads + threadIdx.x;
+      if (i < n) {
+        const float4 q = pts[i];
+        xi[p] = q.x; yi[p] = q.y; si[p] = q.z;
+      } else {
+        xi[p] = 1e18f; yi[p] = 1e18f; si[p] = 0.0f;
+      }
+    }
+    for (int k = threadIdx.x; k < kPriceTile; k += kPriceThreads) {
+      const int j = bj * kPriceTile + k;
+      sj[k] = j < n ? pts[j] : make_float4(-1e18f, -1e18f, 0.0f, 0.0f);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < kPriceTile; ++k) {
+      const float4 q = sj[k];
+      float e[kPriceP];
+#pragma unroll
+      for (int p = 0; p < kPriceP; ++p) {
+        const float dx = q.x - xi[p], dy = q.y - yi[p], t = q.z + si[p];
+        e[p] = fmaf(dy, dy, fmaf(dx, dx, -t * t));
+      }
+      float m = e[0];
+#pragma unroll
+      for (int p = 1; p < kPriceP; ++p) m = fminf(m, e[p]);
+      if (m < 1.0f) {
+        const int j = bj * kPriceTile + k;
+#pragma unroll
+        for (int p = 0; p < kPriceP; ++p)
+          if (e[p] < 1.0f)
+            pricing_confirm(bi * kPriceTile + p * kPriceThreads + threadIdx.x, j, n, xy, lam, rp, ec,
+                            fb, pairs, cap, count);
+      }
+    }
+  }
+}
+
+cudaError_t launch_pricing(const int2* xy, const int32_t* lam, const int32_t* rp, const int2* ec,
+                           int32_t n, int32_t fb, float4* pts, int2* pairs, int64_t cap,
+                           unsigned long long* count, unsigned int* tile_counter, int num_sms,
+                           cudaStream_t st) {
+  cudaError_t err = cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
+  if (err == cudaSuccess) err = cudaMemsetAsync(tile_counter, 0, sizeof(unsigned int), st);
+  if (err != cudaSuccess) return err;
+  {
+    const int threads = 256;
+    int blocks = (int)((n + threads - 1) / threads);
+    if (blocks > 4096) blocks = 4096;
+    pricing_prep_kernel<<<blocks, threads, 0, st>>>(xy, lam, n, fb, pts);
+  }
+  const int ntiles = (n + kPriceTile - 1) / kPriceTile;
+  const long long total = (long long)ntiles * (ntiles + 1) / 2;
+  int per_sm = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pricing_kernel, kPriceThreads, 0);
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1) per_sm = 1;
+  long long grid = (long long)num_sms * per_sm;
+  if (grid > total) grid = total;
+  if (grid < 1) grid = 1;
+  pricing_kernel<<<(int)grid, kPriceThreads, 0, st>>>(pts, xy, lam, rp, ec, n, fb, pairs, cap,
+                                                      count, tile_counter, ntiles);
+  return cudaGetLastError();
+}
+
+}  // namespace f2m

@@ -1,0 +1,331 @@
+"""CUDA path vs the CPU oracle, through the C ABI.  Every comparison is bit-exact.
+
+Steps covered: cost table (a1), GDP sweeps with their per-sweep bound and
+changed count (a2-a5), sign extraction (a6), pricing scan (a7), CSR merge
+(a8), and the whole solve (lambda, x, bound, iteration and round counts).
+Sizes span several tiles of every kernel with ragged tails; the full-size
+workload is checked on sampled outputs and by the certificate.
+"""
+import numpy as np
+import pytest
+
+import instances as I
+import paper_2011_08170_gb300 as f2m
+from paper_2011_08170_gb300 import build as B
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return f2m.load()
+
+
+@pytest.fixture(scope="module")
+def O(oracle_lib):
+    return oracle_lib
+
+
+def inst(kind, n, seed, k):
+    return I.make_instance(kind, n, seed, k)
+
+
+def complete_csr(n):
+    rp = np.arange(0, n * (n - 1) + 1, n - 1, dtype=np.int32)
+    col = np.array([j for i in range(n) for j in range(n) if j != i], dtype=np.int32)
+    return rp, col
+
+
+CASES = [("uniform", 1000, 0, 10), ("mixture", 2500, 3, 10), ("uniform", 777, 5, 6),
+         ("mixture", 5000, 1, 12)]
+
+
+# ---- a1: cost table ---------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,n,seed,k", CASES)
+def test_cost_table(lib, O, kind, n, seed, k):
+    d = inst(kind, n, seed, k)
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"])
+    rp, col, x2, cost = f2m.f2m_get_x(ctx)
+    assert np.array_equal(rp, d["row_ptr"]) and np.array_equal(col, d["col"])
+    assert np.array_equal(cost, O.cost_table(d["xy"], d["row_ptr"], d["col"]))
+
+
+def test_cost_extremes(lib, O):
+    # corners of [0, 2^20)^2, duplicate points, and distances near half-integers
+    M = (1 << 20) - 1
+    xy = np.array([[0, 0], [M, M], [0, M], [M, 0], [0, 0], [3, 4], [1000, 1001], [M, M - 1]],
+                  dtype=np.int32)
+    rp, col = complete_csr(8)
+    ctx = f2m.f2m_create(xy, rp, col)
+    _, _, _, cost = f2m.f2m_get_x(ctx)
+    assert np.array_equal(cost, O.cost_table(xy, rp, col))
+
+
+# ---- a2-a5: GDP sweeps ------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,n,seed,k", CASES)
+def test_gdp_phase_trace(lib, O, kind, n, seed, k):
+    d = inst(kind, n, seed, k)
+    cost = O.cost_table(d["xy"], d["row_ptr"], d["col"])
+    st_o, lam_o, it_o, tb_o, tc_o = O.gdp(d["row_ptr"], d["col"], cost, np.zeros(n, np.int32),
+                                          8, 2, 100000, trace=True)
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"])
+    st, sweeps, tb, tc = f2m.f2m_gdp(ctx, 100000, trace_cap=it_o)
+    lam, fb = f2m.f2m_get_lambda(ctx)
+    assert (st == f2m.F2M_OK) == (st_o == O.OR_OK)
+    assert sweeps == it_o and fb == 8
+    assert np.array_equal(lam, lam_o)
+    assert np.array_equal(tb, tb_o) and np.array_equal(tc, tc_o)
+
+
+@pytest.mark.parametrize("shift", [1, 2, 3])
+def test_single_sweeps_from_random_lambda(lib, O, shift):
+    d = inst("mixture", 3000, 7, 10)
+    n = 3000
+    cost = O.cost_table(d["xy"], d["row_ptr"], d["col"])
+    rng = np.random.default_rng(shift)
+    params = f2m.f2m_default_params(damping_shift=shift)
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], params)
+    for trial in range(3):
+        lam = rng.integers(-(1 << 24), 1 << 24, size=n).astype(np.int32)
+        f2m.f2m_set_lambda(ctx, lam, 8)
+        st_o, lam_o, b2_o, ch_o = O.sweep(d["row_ptr"], d["col"], cost, lam, 8, shift)
+        st, sweeps, tb, tc = f2m.f2m_gdp(ctx, 1, trace_cap=1)
+        out, _ = f2m.f2m_get_lambda(ctx)
+        assert sweeps == 1 and np.array_equal(out, lam_o)
+        assert tb[0] == b2_o and tc[0] == ch_o
+
+
+def test_golden_rectangle_on_gpu(lib, O):
+    import json, os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "rectangle_3x4.json")))
+    xy = np.array(g["xy"], dtype=np.int32)
+    rp, col = complete_csr(4)
+    ctx = f2m.f2m_create(xy, rp, col)
+    st, sweeps, tb, tc = f2m.f2m_gdp(ctx, 100, trace_cap=10)
+    assert st == f2m.F2M_OK and sweeps == g["iterations"]
+    assert list(tb) == g["bound2_per_sweep"] and list(tc) == g["changed_per_sweep"]
+    info = f2m.f2m_solve(ctx)
+    assert info.certified == 2 and info.bound2 / (2 * (1 << info.frac_bits)) == g["opt"]
+
+
+# ---- a6: extraction ----------------------------------------------------------------------
+
+@pytest.mark.parametrize("fb", [8, 9])
+def test_extraction(lib, O, fb):
+    d = inst("uniform", 2000, 4, 10)
+    n = 2000
+    cost = O.cost_table(d["xy"], d["row_ptr"], d["col"])
+    _, lam, *_ = O.gdp(d["row_ptr"], d["col"], cost, np.zeros(n, np.int32), 8, 2, 100000)
+    if fb == 9:
+        lam = lam * 2 + np.random.default_rng(0).integers(-1, 2, size=n).astype(np.int32)
+    bad_o, x2_o = O.extract(d["row_ptr"], d["col"], cost, lam, fb)
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"])
+    f2m.f2m_set_lambda(ctx, lam, fb)
+    bad, x2 = f2m.f2m_extract(ctx)
+    assert bad == bad_o and np.array_equal(x2, x2_o)
+
+
+# ---- a7: pricing --------------------------------------------------------------------------
+
+def _sorted_pairs(p):
+    p = np.asarray(p).reshape(-1, 2)
+    return p[np.lexsort((p[:, 1], p[:, 0]))]
+
+
+@pytest.mark.parametrize("kind,n,seed,k,fb", [("mixture", 2500, 1, 6, 8), ("uniform", 3333, 2, 4, 9),
+                                              ("uniform", 1024, 3, 5, 8), ("mixture", 1025, 4, 5, 8)])
+def test_pricing_random_lambda(lib, O, kind, n, seed, k, fb):
+    d = inst(kind, n, seed, k)
+    rng = np.random.default_rng(seed)
+    scale = 30000 if kind == "uniform" else 8000
+    lam = rng.integers(-scale, scale * 3, size=n).astype(np.int32) << fb
+    lam = (lam + rng.integers(0, 1 << fb, size=n)).astype(np.int32)
+    cnt_o, pairs_o = O.pricing(d["xy"], d["row_ptr"], d["col"], lam, fb)
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"])
+    f2m.f2m_set_lambda(ctx, lam, fb)
+    cnt, pairs = f2m.f2m_price(ctx)
+    assert cnt == cnt_o > 0
+    assert np.array_equal(_sorted_pairs(pairs), pairs_o)
+
+
+def test_pricing_boundary_z_minus_one_and_zero(lib, O):
+    # lambdas set so that many outside pairs have z exactly 0 or -1: the fp32
+    # filter must keep every z = -1 pair and the exact test must drop z = 0
+    n = 2048
+    d = inst("uniform", n, 11, 4)
+    xy = d["xy"]
+    rng = np.random.default_rng(5)
+    fb = 8
+    lam = np.zeros(n, np.int64)
+    # pair node 2i with node 2i+1: lam split so that lam_u + lam_v = c*2^fb + {0, 1}
+    for i in range(0, n - 1, 2):
+        c = int(O.nint_sqrt(np.array([int(((xy[i] - xy[i + 1]).astype(np.int64) ** 2).sum())]))[0])
+        tot = (c << fb) + (i // 2) % 2
+        a = int(rng.integers(0, tot + 1))
+        lam[i], lam[i + 1] = a, tot - a
+    lam = lam.astype(np.int32)
+    cnt_o, pairs_o = O.pricing(xy, d["row_ptr"], d["col"], lam, fb)
+    ctx = f2m.f2m_create(xy, d["row_ptr"], d["col"])
+    f2m.f2m_set_lambda(ctx, lam, fb)
+    cnt, pairs = f2m.f2m_price(ctx)
+    assert cnt == cnt_o and cnt > 0
+    assert np.array_equal(_sorted_pairs(pairs), pairs_o)
+
+
+def test_pricing_nothing_to_find(lib, O):
+    d = inst("uniform", 1500, 2, 10)
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"])
+    cnt, _ = f2m.f2m_price(ctx)  # lambda = 0: every z >= 0
+    assert cnt == 0
+
+
+def test_pricing_buffer_grows(lib, O):
+    d = inst("uniform", 1200, 3, 4)
+    n = 1200
+    lam = np.full(n, 200000 << 8, dtype=np.int32)  # every pair negative
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], f2m.f2m_default_params(pricing_cap=16))
+    f2m.f2m_set_lambda(ctx, lam, 8)
+    cnt, pairs = f2m.f2m_price(ctx)
+    cnt_o, pairs_o = O.pricing(d["xy"], d["row_ptr"], d["col"], lam, 8)
+    assert cnt == cnt_o and np.array_equal(_sorted_pairs(pairs), pairs_o)
+
+
+# ---- a8: merge -----------------------------------------------------------------------------
+
+def test_merge(lib, O):
+    d = inst("mixture", 3000, 9, 6)
+    rng = np.random.default_rng(1)
+    u = rng.integers(0, 3000, size=5000)
+    v = rng.integers(0, 3000, size=5000)
+    keep = u != v
+    pairs = np.stack([np.minimum(u, v), np.maximum(u, v)], 1)[keep].astype(np.int32)
+    pairs = np.unique(pairs, axis=0)
+    rp_o, col_o = O.merge(d["row_ptr"], d["col"], pairs)
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"])
+    f2m.f2m_add_edges(ctx, pairs[rng.permutation(len(pairs))])
+    rp, col, _, cost = f2m.f2m_get_x(ctx)
+    assert np.array_equal(rp, rp_o) and np.array_equal(col, col_o)
+    assert np.array_equal(cost, O.cost_table(d["xy"], rp_o, col_o))
+    # adding pairs already present (either direction) changes nothing
+    f2m.f2m_add_edges(ctx, pairs[:100, ::-1].copy())
+    rp2, col2, _, _ = f2m.f2m_get_x(ctx)
+    assert np.array_equal(rp2, rp_o) and np.array_equal(col2, col_o)
+
+
+# ---- the whole solve ------------------------------------------------------------------------
+
+def _compare_solve(O, d, **kw):
+    r = O.solve(d["xy"], d["row_ptr"], d["col"], max_iters=kw.get("max_iters", 1000000))
+    params = f2m.f2m_default_params(max_iters=kw.get("max_iters", 1000000))
+    s = f2m.solve(d["xy"], d["row_ptr"], d["col"], params=params)
+    i = s.info
+    assert i["status"] == r.status == 0
+    for k in ("iterations", "phases", "pricing_rounds", "edges_added", "finisher_calls",
+              "augmentations", "bound2", "frac_bits", "certified"):
+        assert i[k] == getattr(r, k), k
+    assert np.array_equal(s.row_ptr, r.row_ptr) and np.array_equal(s.col, r.col)
+    assert np.array_equal(s.lam, r.lam) and np.array_equal(s.x2, r.x2)
+    assert O.certify(d["xy"], s.row_ptr, s.col, s.x2, s.lam, s.frac_bits, i["bound2"]) == 0
+    return s, r
+
+
+@pytest.mark.parametrize("kind,n,seed,k", [("uniform", 1000, 0, 10), ("mixture", 1000, 0, 10),
+                                           ("mixture", 3000, 2, 10), ("uniform", 2000, 1, 6)])
+def test_solve_bit_exact(lib, O, kind, n, seed, k):
+    s, r = _compare_solve(O, inst(kind, n, seed, k))
+    assert s.info["certified"] == 2
+
+
+def test_solve_complete_graph_small(lib, O):
+    rng = np.random.default_rng(3)
+    xy = rng.integers(0, 1000, size=(40, 2)).astype(np.int32)
+    rp, col = complete_csr(40)
+    _compare_solve(O, {"xy": xy, "row_ptr": rp, "col": col})
+
+
+def test_solve_warm_start_and_resume(lib, O):
+    d = inst("uniform", 1500, 8, 10)
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"])
+    st, sweeps, *_ = f2m.f2m_gdp(ctx, 200)
+    lam_mid, fb = f2m.f2m_get_lambda(ctx)
+    # resume in a new context from the checkpoint: same as running straight on
+    a = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"])
+    f2m.f2m_gdp(a, 200)
+    f2m.f2m_gdp(a, 100000)
+    b = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"])
+    f2m.f2m_set_lambda(b, lam_mid, fb)
+    f2m.f2m_gdp(b, 100000)
+    assert np.array_equal(f2m.f2m_get_lambda(a)[0], f2m.f2m_get_lambda(b)[0])
+    info = f2m.f2m_solve(b)
+    r = O.solve(d["xy"], d["row_ptr"], d["col"], lam0=lam_mid)
+    assert info.bound2 == r.bound2 and info.certified == 2
+
+
+# ---- error paths (no fault: statuses only) --------------------------------------------------
+
+def test_invalid_csr_rejected(lib):
+    d = inst("uniform", 300, 0, 6)
+    rp, col, xy = d["row_ptr"].copy(), d["col"].copy(), d["xy"].copy()
+    bad = []
+    c1 = col.copy(); c1[rp[5]] = 5; bad.append((xy, rp, c1, "self-loop"))
+    c2 = col.copy(); c2[rp[7]], c2[rp[7] + 1] = c2[rp[7] + 1], c2[rp[7]]; bad.append((xy, rp, c2, "sorted"))
+    x3 = xy.copy(); x3[3, 0] = 1 << 20; bad.append((x3, rp, col, "coordinate"))
+    c4 = col.copy(); c4[rp[9]] = 299 if c4[rp[9]] != 299 else 298; bad.append((xy, rp, c4, ""))
+    for x, r, c, word in bad:
+        with pytest.raises(f2m.F2MError) as e:
+            f2m.f2m_create(x, r, c)
+        assert e.value.status == f2m.F2M_ERR_INVALID_ARG and word in str(e.value)
+
+
+def test_iteration_cap_gives_not_converged(lib):
+    d = inst("uniform", 1000, 0, 10)
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"])
+    st, sweeps, *_ = f2m.f2m_gdp(ctx, 3)
+    assert st == f2m.F2M_ERR_NOT_CONVERGED and sweeps == 3
+
+
+def test_overflow_status(lib, O):
+    d = inst("uniform", 1000, 0, 10)
+    n = 1000
+    # node 0 high, its neighbours low: its adjusted lengths stay at c * 2^F and
+    # the update pushes lambda_0 past 2^29 on the first sweep
+    lam = np.zeros(n, dtype=np.int32)
+    lam[0] = (1 << 29) - 5
+    lam[d["col"][d["row_ptr"][0]:d["row_ptr"][1]]] = -(1 << 29) + 5
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"])
+    f2m.f2m_set_lambda(ctx, lam, 8)
+    st, sweeps, tb, tc = f2m.f2m_gdp(ctx, 10, trace_cap=10)
+    cost = O.cost_table(d["xy"], d["row_ptr"], d["col"])
+    st_o, lam_o, it_o, tb_o, tc_o = O.gdp(d["row_ptr"], d["col"], cost, lam, 8, 2, 10, trace=True)
+    assert st == f2m.F2M_ERR_OVERFLOW and st_o == O.OR_OVERFLOW and sweeps == it_o
+    assert np.array_equal(f2m.f2m_get_lambda(ctx)[0], lam_o)
+    with pytest.raises(f2m.F2MError):
+        f2m.f2m_set_lambda(ctx, np.full(n, 1 << 29, np.int32), 8)
+
+
+def test_barrier_wait_budget_runs_out_and_context_recovers(lib):
+    # a zero spin budget makes every non-last block give up at its first
+    # barrier: the kernel returns a TIMEOUT status instead of waiting
+    d = inst("uniform", 20000, 0, 10)
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], f2m.f2m_default_params(barrier_budget_cycles=0))
+    st, sweeps, *_ = f2m.f2m_gdp(ctx, 50)
+    assert st == f2m.F2M_ERR_TIMEOUT
+    ok = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"])
+    st, sweeps, *_ = f2m.f2m_gdp(ok, 5)
+    assert st == f2m.F2M_ERR_NOT_CONVERGED and sweeps == 5
+
+
+def test_infeasible_candidate_graph(lib):
+    # K_{3,5}: right side needs 10 units, left side offers 6.  GDP pushes lambda
+    # of the right nodes up without bound; either the overflow guard or the
+    # finisher reports it.
+    xy = np.array([[0, 0], [0, 10], [0, 20]] + [[100, 7 * i] for i in range(5)], dtype=np.int32)
+    rows = [[3, 4, 5, 6, 7]] * 3 + [[0, 1, 2]] * 5
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    col = np.concatenate(rows).astype(np.int32)
+    ctx = f2m.f2m_create(xy, rp, col, f2m.f2m_default_params(pricing=0, max_iters=2000))
+    info = f2m.f2m_solve(ctx, raise_on_error=False)
+    assert info.status in (f2m.F2M_ERR_INFEASIBLE, f2m.F2M_ERR_OVERFLOW)
