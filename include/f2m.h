@@ -187,6 +187,10 @@ f2m_status f2m_get_bound(f2m_ctx* ctx, int64_t* bound2, int32_t* frac_bits);
 f2m_status f2m_get_x(f2m_ctx* ctx, int64_t* nnz_inout, int32_t* row_ptr, int32_t* col,
                      uint8_t* x2, int32_t* cost);
 
+/* Number of kernel launches this library has made in this process (all
+ * contexts, all threads).  A diagnostic with no counterpart in the paper. */
+int64_t f2m_kernel_launches(void);
+
 /* Static text for a status code. */
 const char* f2m_status_string(f2m_status s);
 

@@ -33,7 +33,8 @@ F2M_ERR_TIMEOUT = 8
 # every symbol the header declares
 EXPORTS = ["f2m_default_params", "f2m_create", "f2m_destroy", "f2m_set_lambda", "f2m_solve",
            "f2m_gdp", "f2m_price", "f2m_add_edges", "f2m_extract", "f2m_get_lambda",
-           "f2m_get_bound", "f2m_get_x", "f2m_status_string", "f2m_last_error"]
+           "f2m_get_bound", "f2m_get_x", "f2m_status_string", "f2m_last_error",
+           "f2m_kernel_launches"]
 
 
 class f2m_params(C.Structure):
@@ -94,6 +95,8 @@ def load(path: str = LIB_PATH):
     L.f2m_status_string.restype = C.c_char_p
     L.f2m_last_error.argtypes = [vp]
     L.f2m_last_error.restype = C.c_char_p
+    L.f2m_kernel_launches.argtypes = []
+    L.f2m_kernel_launches.restype = C.c_int64
     for name in ("f2m_create", "f2m_set_lambda", "f2m_solve", "f2m_gdp", "f2m_price",
                  "f2m_add_edges", "f2m_extract", "f2m_get_lambda", "f2m_get_bound", "f2m_get_x"):
         getattr(L, name).restype = C.c_int
@@ -320,3 +323,8 @@ def f2m_status_string(status: int) -> str:
 
 def f2m_last_error(ctx: Ctx | None = None) -> str:
     return load().f2m_last_error(ctx.handle if ctx is not None else None).decode()
+
+
+def f2m_kernel_launches() -> int:
+    """Kernel launches made by the library so far in this process."""
+    return int(load().f2m_kernel_launches())

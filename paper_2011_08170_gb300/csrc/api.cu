@@ -6,6 +6,7 @@
 // context's stream; the host reads back one small status block per step.  The
 // exception is the exact finisher (finisher.cpp), a min-cost flow that runs on
 // the host when the sign rule (7) leaves some node with a row sum other than 2.
+#include <atomic>
 #include <chrono>
 #include <climits>
 #include <cstdio>
@@ -18,6 +19,14 @@
 #include "f2m_internal.h"
 
 using namespace f2m;
+
+static std::atomic<long long> g_kernel_launches{0};
+
+namespace f2m {
+void count_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace f2m
+
+extern "C" int64_t f2m_kernel_launches(void) { return g_kernel_launches.load(); }
 
 struct f2m_ctx {
   int32_t n = 0;
@@ -273,6 +282,7 @@ extern "C" f2m_status f2m_set_lambda(f2m_ctx* c, const int32_t* lambda, int32_t 
   CK(c, reset_check(c));
   const long long limit = frac_bits == F ? kLamLimit : 2 * kLamLimit;
   f2m_range_kernel<<<(c->n + 255) / 256, 256, 0, c->st>>>(dst, c->n, limit, c->d_check);
+  count_launch();
   CK(c, cudaGetLastError());
   CheckCtl h{};
   CK(c, read_check(c, &h));

@@ -49,6 +49,9 @@ enum CheckBits {
   kBadPair = 128,
 };
 
+// process-wide count of kernel launches made by this library (api.cu)
+void count_launch();
+
 // ---- launchers (each enqueues on `st`) -------------------------------------
 
 // validation of the input CSR and points; ctl must be zeroed (first_bad = INT_MAX)

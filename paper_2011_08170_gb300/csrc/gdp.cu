@@ -146,8 +146,10 @@ static cudaError_t launch_gdp_g(const int32_t* rp, const int2* ec, int32_t* lam0
   void* args[] = {(void*)&rp, (void*)&ec, (void*)&lam0, (void*)&lam1, (void*)&n, (void*)&F,
                   (void*)&shift, (void*)&ms, (void*)&ctl, (void*)&trace_b2, (void*)&trace_ch,
                   (void*)&tc, (void*)&budget};
-  return cudaLaunchCooperativeKernel((const void*)gdp_persistent_kernel<G>, dim3(grid),
-                                     dim3(threads), args, 0, st);
+  err = cudaLaunchCooperativeKernel((const void*)gdp_persistent_kernel<G>, dim3(grid),
+                                    dim3(threads), args, 0, st);
+  count_launch();
+  return err;
 }
 
 cudaError_t launch_gdp(const int32_t* rp, const int2* ec, int32_t* lam0, int32_t* lam1, int32_t n,
@@ -193,6 +195,7 @@ cudaError_t launch_bound(const int32_t* rp, const int2* ec, const int32_t* lam, 
   int blocks = (int)((n + threads - 1) / threads);
   if (blocks > 4096) blocks = 4096;
   bound_kernel<<<blocks, threads, 0, st>>>(rp, ec, lam, n, fb, out);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -226,6 +229,7 @@ cudaError_t launch_extract(const int32_t* rp, const int2* ec, const int32_t* lam
   int blocks = (int)((n + threads - 1) / threads);
   if (blocks > 4096) blocks = 4096;
   extract_kernel<<<blocks, threads, 0, st>>>(rp, ec, lam, n, fb, x2, bad);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -240,6 +244,7 @@ cudaError_t launch_halve(const int32_t* lam_in, int32_t* lam_out, int32_t n, cud
   int blocks = (int)((n + threads - 1) / threads);
   if (blocks > 4096) blocks = 4096;
   halve_kernel<<<blocks, threads, 0, st>>>(lam_in, lam_out, n);
+  count_launch();
   return cudaGetLastError();
 }
 

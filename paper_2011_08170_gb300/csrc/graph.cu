@@ -70,8 +70,10 @@ cudaError_t launch_check(const int2* xy, const int32_t* rp, const int32_t* col, 
   // two passes; the host reads ctl between them (pass 2 trusts the row offsets)
   if (col == nullptr) {
     check_rowptr_kernel<<<grid_for(n, 256), 256, 0, st>>>(xy, rp, n, nnz, ctl);
+    count_launch();
   } else {
     check_rows_kernel<<<grid_for(n, 256), 256, 0, st>>>(rp, col, n, ctl);
+    count_launch();
   }
   return cudaGetLastError();
 }
@@ -100,6 +102,7 @@ cudaError_t launch_build_ec(const int2* xy, const int32_t* rp, const int32_t* co
   if (err != cudaSuccess) return err;
   if (nnz_host == 0) return cudaSuccess;
   build_ec_kernel<<<grid_for(nnz_host, 256), 256, 0, st>>>(xy, rp, col, n, nnz_host, ec);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -189,8 +192,11 @@ cudaError_t launch_scan(const int32_t* in, int32_t* out, int32_t m, int32_t* blo
   const int nb = (m + kScanBlock - 1) / kScanBlock;
   if (nb == 0) return cudaMemsetAsync(out, 0, sizeof(int32_t), st);
   scan_blocks_kernel<<<nb, kScanThreads, 0, st>>>(in, out, m, block_sums);
+  count_launch();
   scan_sums_kernel<<<1, kScanThreads, 0, st>>>(block_sums, nb, out + m);
+  count_launch();
   scan_add_kernel<<<nb, 256, 0, st>>>(out, m, block_sums);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -216,8 +222,11 @@ __global__ void merge_count_kernel(const int2* __restrict__ pairs, long long npa
 cudaError_t launch_merge_count(const int32_t* rp, const int2* pairs, int64_t npairs, int32_t n,
                                MergeBuffers& mb, cudaStream_t st) {
   merge_degree_kernel<<<grid_for(n, 256), 256, 0, st>>>(rp, n, mb.deg);
-  if (npairs > 0)
+  count_launch();
+  if (npairs > 0) {
     merge_count_kernel<<<grid_for(npairs, 256), 256, 0, st>>>(pairs, npairs, n, mb.deg, mb.ctl);
+    count_launch();
+  }
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   return launch_scan(mb.deg, mb.tmp_rp, n, mb.block_sums, st);
@@ -247,9 +256,12 @@ __global__ void merge_scatter_kernel(const int2* __restrict__ pairs, long long n
 cudaError_t launch_merge_fill(const int32_t* rp, const int2* ec, const int2* pairs, int64_t npairs,
                               int32_t n, MergeBuffers& mb, cudaStream_t st) {
   merge_copy_kernel<<<grid_for(n, 256), 256, 0, st>>>(rp, ec, n, mb.tmp_rp, mb.tmp_col, mb.deg);
-  if (npairs > 0)
+  count_launch();
+  if (npairs > 0) {
     merge_scatter_kernel<<<grid_for(npairs, 256), 256, 0, st>>>(pairs, npairs, n, mb.tmp_col,
                                                                 mb.deg);
+    count_launch();
+  }
   return cudaGetLastError();
 }
 
@@ -288,12 +300,14 @@ __global__ void merge_compact_kernel(const int2* __restrict__ xy, const int32_t*
 cudaError_t launch_merge_finish(const int2* xy, int32_t n, MergeBuffers& mb, int2* ec_out,
                                 cudaStream_t st) {
   merge_sort_rows_kernel<<<grid_for(n, 128), 128, 0, st>>>(mb.tmp_rp, mb.tmp_col, n, mb.deg);
+  count_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   err = launch_scan(mb.deg, mb.new_rp, n, mb.block_sums, st);
   if (err != cudaSuccess) return err;
   merge_compact_kernel<<<grid_for(n, 128), 128, 0, st>>>(xy, mb.tmp_rp, mb.tmp_col, n, mb.new_rp,
                                                          ec_out);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -310,6 +324,7 @@ cudaError_t launch_split_ec(const int2* ec, int64_t nnz, int32_t* col, int32_t* 
                             cudaStream_t st) {
   if (nnz == 0) return cudaSuccess;
   split_ec_kernel<<<grid_for(nnz, 256), 256, 0, st>>>(ec, nnz, col, cost);
+  count_launch();
   return cudaGetLastError();
 }
 

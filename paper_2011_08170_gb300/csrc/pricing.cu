@@ -131,6 +131,7 @@ cudaError_t launch_pricing(const int2* xy, const int32_t* lam, const int32_t* rp
     int blocks = (int)((n + threads - 1) / threads);
     if (blocks > 4096) blocks = 4096;
     pricing_prep_kernel<<<blocks, threads, 0, st>>>(xy, lam, n, fb, pts);
+    count_launch();
   }
   const int ntiles = (n + kPriceTile - 1) / kPriceTile;
   const long long total = (long long)ntiles * (ntiles + 1) / 2;
@@ -143,6 +144,7 @@ cudaError_t launch_pricing(const int2* xy, const int32_t* lam, const int32_t* rp
   if (grid < 1) grid = 1;
   pricing_kernel<<<(int)grid, kPriceThreads, 0, st>>>(pts, xy, lam, rp, ec, n, fb, pairs, cap,
                                                       count, tile_counter, ntiles);
+  count_launch();
   return cudaGetLastError();
 }
 
