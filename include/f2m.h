@@ -169,6 +169,39 @@ f2m_status f2m_add_edges(f2m_ctx* ctx, const int32_t* pairs, int64_t npairs);
  *   bad  out: number of nodes whose row of x2 does not sum to 4. */
 f2m_status f2m_extract(f2m_ctx* ctx, uint8_t* x2, int64_t* bad);
 
+/* One GDP phase that allocates no memory, for callers that cannot allocate
+ * device memory where they run it: cudaFree waits for the whole device, which a
+ * caller driving other streams cannot afford; a framework that has reserved the
+ * device memory for its own pool leaves nothing for cudaMalloc; a latency-bound
+ * loop may forbid allocation once started.  The paper has no counterpart of
+ * this entry point; it exists for those callers.
+ * It runs the same sweeps as f2m_gdp (same results, bit for bit), but its
+ * scratch (the second lambda buffer and the kernel's control block) lives in a
+ * fixed file-scope device array of about 1 MiB that every GPU loading this
+ * library holds until the process exits.  It calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ *   row_ptr   [n+1] int32, device: the candidate CSR (rules of f2m_create; not
+ *             re-checked here).
+ *   ec        [nnz][2] int32, device: per CSR entry {column, cost c_e}.
+ *   n         4 <= n <= 262,144 (the size of the scratch array); larger n
+ *             returns INVALID_ARG with the limit in errbuf.
+ *   frac_bits, damping_shift   as in f2m_params (1..8).
+ *   lambda    [n] int32, device, in/out: the start lambda, replaced by the
+ *             result (units 2^-frac_bits).
+ *   sweeps    host out: sweeps run.
+ *   bound2    NULL or host out: bound2 at the lambda the last sweep started from.
+ *   stream    cudaStream_t as void*, NULL = legacy default stream.
+ *   errbuf    NULL or a caller buffer of errlen bytes for a message.
+ * The first call on each device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  Every call reuses the same array and clears what must start at
+ * zero; calls that overlap on the GPU (other streams or threads) race on it.
+ * Returns OK, NOT_CONVERGED, OVERFLOW, TIMEOUT, INVALID_ARG, CUDA. */
+f2m_status f2m_gdp_noalloc(const int32_t* row_ptr, const int32_t* ec, int32_t n,
+                           int32_t frac_bits, int32_t damping_shift, int64_t max_sweeps,
+                           int32_t* lambda, int64_t* sweeps, int64_t* bound2, void* stream,
+                           char* errbuf, int64_t errlen);
+
 /* ---- results ----------------------------------------------------------------- */
 
 /* lambda [n] int32 (host or device) in units 2^-(*frac_bits). */

@@ -34,7 +34,7 @@ F2M_ERR_TIMEOUT = 8
 EXPORTS = ["f2m_default_params", "f2m_create", "f2m_destroy", "f2m_set_lambda", "f2m_solve",
            "f2m_gdp", "f2m_price", "f2m_add_edges", "f2m_extract", "f2m_get_lambda",
            "f2m_get_bound", "f2m_get_x", "f2m_status_string", "f2m_last_error",
-           "f2m_kernel_launches"]
+           "f2m_kernel_launches", "f2m_gdp_noalloc"]
 
 
 class f2m_params(C.Structure):
@@ -95,6 +95,9 @@ def load(path: str = LIB_PATH):
     L.f2m_status_string.restype = C.c_char_p
     L.f2m_last_error.argtypes = [vp]
     L.f2m_last_error.restype = C.c_char_p
+    L.f2m_gdp_noalloc.argtypes = [vp, vp, i32, i32, i32, i64, vp, C.POINTER(i64),
+                                  C.POINTER(i64), vp, C.c_char_p, i64]
+    L.f2m_gdp_noalloc.restype = C.c_int
     L.f2m_kernel_launches.argtypes = []
     L.f2m_kernel_launches.restype = C.c_int64
     for name in ("f2m_create", "f2m_set_lambda", "f2m_solve", "f2m_gdp", "f2m_price",
@@ -328,3 +331,16 @@ def f2m_last_error(ctx: Ctx | None = None) -> str:
 def f2m_kernel_launches() -> int:
     """Kernel launches made by the library so far in this process."""
     return int(load().f2m_kernel_launches())
+
+
+def f2m_gdp_noalloc(row_ptr, ec, lam, max_sweeps: int, frac_bits: int = 8, damping_shift: int = 2,
+                    stream=None):
+    """GDP phase without allocation; row_ptr, ec ([nnz, 2] {col, cost}) and lam are
+    CUDA tensors, lam is updated in place.  Returns (status, sweeps, bound2, message)."""
+    n = int(row_ptr.shape[0]) - 1
+    sw, b2 = C.c_int64(), C.c_int64()
+    buf = C.create_string_buffer(512)
+    st = load().f2m_gdp_noalloc(row_ptr.data_ptr(), ec.data_ptr(), n, frac_bits, damping_shift,
+                                max_sweeps, lam.data_ptr(), C.byref(sw), C.byref(b2),
+                                _stream_handle(stream), buf, len(buf))
+    return st, sw.value, b2.value, buf.value.decode()
