@@ -75,8 +75,14 @@ typedef struct {
   int64_t pricing_cap;          /* initial pair-buffer capacity; default 1 << 20 */
   int64_t barrier_budget_cycles;/* spin budget of one device-wide barrier wait; default 4e9 */
   int32_t finisher;             /* 1 = exact finisher when rule (7) gives an infeasible x (default) */
-  uint32_t flags;               /* reserved, 0 */
+  uint32_t flags;               /* F2M_FLAG_* bits; default 0 */
 } f2m_params;
+
+/* f2m_params.flags: run GDP with the streaming kernel (CSR read from global
+ * memory every sweep, caller node order) instead of the default shared-memory
+ * tiled kernel (nodes renumbered along a Morton curve, each CTA's rows, own
+ * lambda and halo held in shared memory).  Both give identical results. */
+#define F2M_FLAG_STREAMING_GDP 1u
 
 typedef struct {
   int64_t iterations;           /* GDP sweeps, all phases */

@@ -84,7 +84,7 @@ def lib():
         L.or_extract.restype = C.c_int64
         L.or_extract.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _i32p, C.c_int32, _u8p]
         L.or_finisher.restype = C.c_int
-        L.or_finisher.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _i32p, C.c_int32, _u8p,
+        L.or_finisher.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _i32p, _i32p, C.c_int32, _u8p,
                                   _i32p, C.POINTER(C.c_int64)]
         L.or_pricing_rows.restype = C.c_int64
         L.or_pricing_rows.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _i32p, C.c_int32,
@@ -156,14 +156,14 @@ def extract(row_ptr, col, cost, lam, fb=8):
     return int(bad), x2
 
 
-def finisher(row_ptr, col, cost, lam, F=8):
+def finisher(xy, row_ptr, col, cost, lam, F=8):
     """Exact min-cost-flow finisher: returns (status, x2, lam2 at F+1 bits, augmentations)."""
     x2 = np.zeros(np.asarray(col).size, dtype=np.uint8)
     lam = _i32(lam)
     lam2 = np.zeros_like(lam)
     aug = C.c_int64()
-    st = lib().or_finisher(lam.size, _i32(row_ptr), _i32(col), _i32(cost), lam, F, x2, lam2,
-                           C.byref(aug))
+    st = lib().or_finisher(lam.size, _i32(xy).reshape(-1), _i32(row_ptr), _i32(col), _i32(cost), lam,
+                           F, x2, lam2, C.byref(aug))
     return st, x2, lam2, aug.value
 
 

@@ -163,13 +163,18 @@ int64_t or_extract(int32_t n, const int32_t* row_ptr, const int32_t* col,
  * Reduced cost of a residual arc i -> j: C(i, j) - pi(i) + pi(j).
  * Warm start: pi(L_v) = lam_v, pi(R_v) = -lam_v (reduced cost of an arc = z_e),
  * arcs with z_e < 0 saturated, so every residual reduced cost is >= 0.
- * Successive shortest paths: repeatedly take the smallest-id node with positive
- * excess, run Dijkstra (ties by node id) to the first node with negative
- * excess, push one unit, raise pi(i) by d(t) - d(i) on nodes settled before t. */
+ * Successive shortest paths: repeatedly take the node with positive excess and
+ * the smallest key, run Dijkstra (ties by key) to the first node with negative
+ * excess, push one unit, raise pi(i) by d(t) - d(i) on nodes settled before t.
+ * Key of a node: 2*rank(v) for L_v and 2*rank(v) + 1 for R_v, where rank(v) is
+ * the position of v when points are ordered by Morton code (bit b of x at bit
+ * 2b, bit b of y at bit 2b+1), ties by node id -- so that successive paths are
+ * searched in nearby parts of the plane.  (The paper gives no finisher; this
+ * order is a stated choice.) */
 
-typedef struct { int64_t d; int32_t v; } or_hitem;
+typedef struct { int64_t d; int32_t key; int32_t v; } or_hitem;
 
-static int or_hless(or_hitem a, or_hitem b) { return a.d < b.d || (a.d == b.d && a.v < b.v); }
+static int or_hless(or_hitem a, or_hitem b) { return a.d < b.d || (a.d == b.d && a.key < b.key); }
 
 static void or_hpush(or_hitem* h, int64_t* sz, or_hitem it) {
   int64_t i = (*sz)++;
@@ -195,6 +200,32 @@ static or_hitem or_hpop(or_hitem* h, int64_t* sz) {
   return top;
 }
 
+typedef struct { uint64_t code; int32_t v; } or_mkey;
+
+static int cmp_mkey(const void* a, const void* b) {
+  const or_mkey* x = (const or_mkey*)a;
+  const or_mkey* y = (const or_mkey*)b;
+  if (x->code != y->code) return (x->code > y->code) - (x->code < y->code);
+  return (x->v > y->v) - (x->v < y->v);
+}
+
+/* rank[v] = position of point v in (Morton code, id) order */
+static void or_morton_rank(int32_t n, const int32_t* xy, int32_t* rank) {
+  or_mkey* k = (or_mkey*)malloc(sizeof(or_mkey) * (size_t)(n > 0 ? n : 1));
+  for (int32_t v = 0; v < n; ++v) {
+    uint64_t code = 0;
+    for (int b = 0; b < 20; ++b) {
+      code |= (uint64_t)(((uint32_t)xy[2 * (int64_t)v] >> b) & 1u) << (2 * b);
+      code |= (uint64_t)(((uint32_t)xy[2 * (int64_t)v + 1] >> b) & 1u) << (2 * b + 1);
+    }
+    k[v].code = code;
+    k[v].v = v;
+  }
+  qsort(k, (size_t)n, sizeof(or_mkey), cmp_mkey);
+  for (int32_t r = 0; r < n; ++r) rank[k[r].v] = r;
+  free(k);
+}
+
 static int32_t or_find(const int32_t* row_ptr, const int32_t* col, int32_t u, int32_t v) {
   int32_t lo = row_ptr[u], hi = row_ptr[u + 1] - 1;
   while (lo <= hi) {
@@ -205,8 +236,8 @@ static int32_t or_find(const int32_t* row_ptr, const int32_t* col, int32_t u, in
   return -1;
 }
 
-int or_finisher(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* cost,
-                const int32_t* lam, int32_t F, uint8_t* x2, int32_t* lam2,
+int or_finisher(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int32_t* col,
+                const int32_t* cost, const int32_t* lam, int32_t F, uint8_t* x2, int32_t* lam2,
                 int64_t* augmentations) {
   int64_t nnz = row_ptr[n];
   int32_t N = 2 * n;
@@ -221,9 +252,18 @@ int or_finisher(int32_t n, const int32_t* row_ptr, const int32_t* col, const int
   int64_t* done = (int64_t*)calloc((size_t)N, sizeof(int64_t));   /* stamp: settled */
   int32_t* settled = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
   or_hitem* heap = (or_hitem*)malloc(sizeof(or_hitem) * (size_t)(nnz + N + 1));
+  int32_t* key = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);   /* tie-break key per node */
+  int32_t* by_key = (int32_t*)malloc(sizeof(int32_t) * (size_t)N); /* node with each key */
   int status = OR_OK;
   int64_t aug = 0;
 
+  or_morton_rank(n, xy, key);
+  for (int32_t v = 0; v < n; ++v) {
+    int32_t r = key[v];
+    key[v] = 2 * r;
+    key[n + v] = 2 * r + 1;
+  }
+  for (int32_t i = 0; i < N; ++i) by_key[key[i]] = i;
   for (int32_t u = 0; u < n; ++u)
     for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
       rev[e] = or_find(row_ptr, col, col[e], u);
@@ -243,15 +283,16 @@ int or_finisher(int32_t n, const int32_t* row_ptr, const int32_t* col, const int
   }
 
   int64_t stamp = 0;
-  int32_t src = 0;
+  int32_t next = 0; /* next key to look at for a source */
   for (;;) {
-    while (src < N && ex[src] <= 0) ++src;
-    if (src >= N) break;
+    while (next < N && ex[by_key[next]] <= 0) ++next;
+    if (next >= N) break;
+    int32_t src = by_key[next];
     ++stamp;
     int64_t hs = 0, ns = 0;
     int32_t t = -1;
     dist[src] = 0; seen[src] = stamp; par[src] = -1;
-    or_hpush(heap, &hs, (or_hitem){0, src});
+    or_hpush(heap, &hs, (or_hitem){0, key[src], src});
     while (hs > 0) {
       or_hitem it = or_hpop(heap, &hs);
       int32_t i = it.v;
@@ -267,7 +308,7 @@ int or_finisher(int32_t n, const int32_t* row_ptr, const int32_t* col, const int
           int64_t nd = dist[i] + rc;
           if (done[j] != stamp && (seen[j] != stamp || nd < dist[j])) {
             seen[j] = stamp; dist[j] = nd; par[j] = e;
-            or_hpush(heap, &hs, (or_hitem){nd, j});
+            or_hpush(heap, &hs, (or_hitem){nd, key[j], j});
           }
         }
       } else { /* R_v: reverse arcs of saturated entries (u -> v) */
@@ -280,7 +321,7 @@ int or_finisher(int32_t n, const int32_t* row_ptr, const int32_t* col, const int
           int64_t nd = dist[i] + rc;
           if (done[j] != stamp && (seen[j] != stamp || nd < dist[j])) {
             seen[j] = stamp; dist[j] = nd; par[j] = e;
-            or_hpush(heap, &hs, (or_hitem){nd, j});
+            or_hpush(heap, &hs, (or_hitem){nd, key[j], j});
           }
         }
       }
@@ -312,6 +353,7 @@ int or_finisher(int32_t n, const int32_t* row_ptr, const int32_t* col, const int
     }
   }
   *augmentations = aug;
+  free(key); free(by_key);
   free(rev); free(own); free(y); free(pi); free(ex); free(dist); free(par);
   free(seen); free(done); free(settled); free(heap);
   return status;
@@ -487,7 +529,7 @@ or_result* or_solve(int32_t n, const int32_t* xy, const int32_t* row_ptr,
     if (bad > 0) {
       if (!p->finisher) { status = OR_NOT_CONVERGED; info->bound2 = or_bound2(n, r->row_ptr, r->col, cost, lam, F); break; }
       int64_t aug = 0;
-      st = or_finisher(n, r->row_ptr, r->col, cost, lam, F, r->x2, lam2, &aug);
+      st = or_finisher(n, xy, r->row_ptr, r->col, cost, lam, F, r->x2, lam2, &aug);
       info->finisher_calls += 1;
       info->augmentations += aug;
       if (st != OR_OK) { status = st; break; }

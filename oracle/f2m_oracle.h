@@ -70,10 +70,11 @@ int64_t or_extract(int32_t n, const int32_t* row_ptr, const int32_t* col,
                    const int32_t* cost, const int32_t* lam, int32_t fb, uint8_t* x2);
 
 /* Exact finisher: min-cost flow on the bipartite double cover of the CSR graph,
- * warm-started from lam (F bits); successive shortest paths.  Writes x2 (half
- * units) and lam2 (units 2^-(F+1)).  Returns OR_OK, OR_INFEASIBLE or OR_OVERFLOW. */
-int or_finisher(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* cost,
-                const int32_t* lam, int32_t F, uint8_t* x2, int32_t* lam2,
+ * warm-started from lam (F bits); successive shortest paths, sources and ties
+ * in (Morton code of the point, id) order.  Writes x2 (half units) and lam2
+ * (units 2^-(F+1)).  Returns OR_OK, OR_INFEASIBLE or OR_OVERFLOW. */
+int or_finisher(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int32_t* col,
+                const int32_t* cost, const int32_t* lam, int32_t F, uint8_t* x2, int32_t* lam2,
                 int64_t* augmentations);
 
 /* Pricing: every pair u < v that is not an edge of the CSR and has

@@ -66,8 +66,70 @@ struct f2m_ctx {
   long long* d_scalar = nullptr;
   unsigned long long* d_bad = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  GdpPlan plan;         // renumbering and tiles of the shared-memory GDP kernel
+  // exact finisher: device scratch, pinned host mirrors, host work arrays
+  int32_t* d_twin = nullptr;
+  uint8_t* d_fy = nullptr;
+  uint8_t* d_fx = nullptr;
+  int64_t fin_cap = 0;          // entries the finisher buffers hold
+  int64_t fin_version = -1;     // plan version mirrored on the host
+  int32_t* h_irp = nullptr;
+  int2* h_iec = nullptr;
+  int32_t* h_twin = nullptr;
+  uint8_t* h_y = nullptr;
+  uint8_t* h_x = nullptr;
+  int32_t* h_exl = nullptr;
+  int32_t* h_lam = nullptr;
+  int32_t* h_lam2 = nullptr;
+  FinisherWork* fin_work = nullptr;
   std::string err;
 };
+
+static void free_finisher_buffers(f2m_ctx* c) {
+  if (c->d_twin) cudaFree(c->d_twin);
+  if (c->d_fy) cudaFree(c->d_fy);
+  if (c->d_fx) cudaFree(c->d_fx);
+  void* hp[] = {c->h_irp, c->h_iec, c->h_twin, c->h_y, c->h_x, c->h_exl, c->h_lam, c->h_lam2};
+  for (void* q : hp)
+    if (q) cudaFreeHost(q);
+  c->d_twin = nullptr; c->d_fy = nullptr; c->d_fx = nullptr;
+  c->h_irp = nullptr; c->h_iec = nullptr; c->h_twin = nullptr; c->h_y = nullptr; c->h_x = nullptr;
+  c->h_exl = nullptr; c->h_lam = nullptr; c->h_lam2 = nullptr;
+  c->fin_cap = 0;
+  c->fin_version = -1;
+}
+
+// device and pinned host buffers for `cap` entries (node-sized ones once)
+static cudaError_t alloc_finisher_buffers(f2m_ctx* c, int64_t cap) {
+  const int32_t n = c->n;
+  const bool first = c->h_irp == nullptr;
+  if (c->d_twin) cudaFree(c->d_twin);
+  if (c->d_fy) cudaFree(c->d_fy);
+  if (c->d_fx) cudaFree(c->d_fx);
+  if (c->h_iec) cudaFreeHost(c->h_iec);
+  if (c->h_twin) cudaFreeHost(c->h_twin);
+  if (c->h_y) cudaFreeHost(c->h_y);
+  if (c->h_x) cudaFreeHost(c->h_x);
+  c->d_twin = nullptr; c->d_fy = nullptr; c->d_fx = nullptr;
+  c->h_iec = nullptr; c->h_twin = nullptr; c->h_y = nullptr; c->h_x = nullptr;
+  c->fin_cap = 0;
+  c->fin_version = -1;
+  cudaError_t e = cudaMalloc((void**)&c->d_twin, sizeof(int32_t) * cap);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_fy, cap);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_fx, cap);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_iec, sizeof(int2) * cap);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_twin, sizeof(int32_t) * cap);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_y, cap);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_x, cap);
+  if (e == cudaSuccess && first) {
+    e = cudaMallocHost((void**)&c->h_irp, sizeof(int32_t) * (n + 1));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_exl, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_lam, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_lam2, sizeof(int32_t) * n);
+  }
+  if (e == cudaSuccess) c->fin_cap = cap;
+  return e;
+}
 
 static thread_local std::string g_create_error;
 
@@ -149,6 +211,9 @@ extern "C" void f2m_destroy(f2m_ctx* c) {
   dfree(c->d_count); dfree(c->d_tile); dfree(c->d_deg); dfree(c->d_tmp_rp); dfree(c->d_new_rp);
   dfree(c->d_block_sums); dfree(c->d_tmp_col); dfree(c->d_out_a); dfree(c->d_out_b);
   dfree(c->d_check); dfree(c->d_scalar); dfree(c->d_bad);
+  free_finisher_buffers(c);
+  if (c->fin_work) finisher_work_free(c->fin_work);
+  plan_free(c->plan);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   delete c;
@@ -240,6 +305,15 @@ extern "C" f2m_status f2m_create(const int32_t* xy, int32_t n, const int32_t* ro
     c->ec_cap = c->nnz + (c->nnz >> 3) + 4096;
     e = dalloc(&c->d_ec, c->ec_cap);
     if (e == cudaSuccess) e = launch_build_ec(c->d_xy, c->d_rp, d_col, n, c->d_ec, c->st);
+    if (e == cudaSuccess) e = plan_renumber(c->d_xy, n, c->plan, c->st);
+    if (e == cudaSuccess)
+      e = plan_build(c->d_rp, c->d_ec, n, c->nnz, c->num_sms, !(p.flags & F2M_FLAG_STREAMING_GDP),
+                     c->plan, c->st);
+    if (e == cudaSuccess && p.finisher) {
+      e = alloc_finisher_buffers(c, c->ec_cap);
+      c->fin_work = finisher_work_new();
+      finisher_work_reserve(c->fin_work, n);
+    }
     if (e == cudaSuccess) e = dalloc(&c->d_x2, c->ec_cap);
     if (e == cudaSuccess) e = dalloc(&c->d_lam[0], n);
     if (e == cudaSuccess) e = dalloc(&c->d_lam[1], n);
@@ -313,10 +387,24 @@ static f2m_status gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, boo
   }
   CK(c, cudaMemsetAsync(c->d_gdp, 0, sizeof(GdpCtl), c->st));
   CK(c, cudaEventRecord(c->ev0, c->st));
-  CK(c, launch_gdp(c->d_rp, c->d_ec, c->d_lam[c->cur], c->d_lam[c->cur ^ 1], c->n, F,
-                   c->p.damping_shift, max_sweeps, c->d_gdp, want_trace ? c->d_trace_b2 : nullptr,
-                   want_trace ? c->d_trace_ch : nullptr, want_trace ? trace_cap : 0,
-                   c->p.barrier_budget_cycles, c->num_sms, c->st));
+  bool tiled = c->plan.valid;
+  if (tiled) {
+    cudaError_t e = launch_gdp_tiled(c->plan, c->d_lam[c->cur], F, c->p.damping_shift, max_sweeps,
+                                     c->d_gdp, want_trace ? c->d_trace_b2 : nullptr,
+                                     want_trace ? c->d_trace_ch : nullptr, want_trace ? trace_cap : 0,
+                                     c->p.barrier_budget_cycles, c->st);
+    if (e == cudaErrorCooperativeLaunchTooLarge) {
+      cudaGetLastError();
+      tiled = false;  // the tiles do not fit on this device now: streaming kernel
+    } else {
+      CK(c, e);
+    }
+  }
+  if (!tiled)
+    CK(c, launch_gdp(c->d_rp, c->d_ec, c->d_lam[c->cur], c->d_lam[c->cur ^ 1], c->n, F,
+                     c->p.damping_shift, max_sweeps, c->d_gdp, want_trace ? c->d_trace_b2 : nullptr,
+                     want_trace ? c->d_trace_ch : nullptr, want_trace ? trace_cap : 0,
+                     c->p.barrier_budget_cycles, c->num_sms, c->st));
   CK(c, cudaEventRecord(c->ev1, c->st));
   GdpCtl h{};
   CK(c, cudaMemcpyAsync(&h, c->d_gdp, sizeof(h), cudaMemcpyDeviceToHost, c->st));
@@ -326,7 +414,12 @@ static f2m_status gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, boo
   const bool ovf = (h.status & kGdpOverflow) != 0;
   // the sweep that overflowed leaves lambda at its input; otherwise the last output
   const long long used = ovf ? h.sweeps - 1 : h.sweeps;
-  if (used & 1) c->cur ^= 1;
+  if (tiled) {
+    if (!(h.status & kGdpTimeout))
+      CK(c, plan_scatter_lambda(c->plan, (int)(used & 1), c->d_lam[c->cur], c->st));
+  } else if (used & 1) {
+    c->cur ^= 1;
+  }
   if (h.status & kGdpTimeout) return fail(c, F2M_ERR_TIMEOUT, "device-wide barrier wait exceeded its budget");
   if (ovf) return fail(c, F2M_ERR_OVERFLOW, "|lambda| reached 2^29");
   if (!h.fixed_point) return F2M_ERR_NOT_CONVERGED;
@@ -424,14 +517,16 @@ static f2m_status merge_internal(f2m_ctx* c, const int2* d_pairs, int64_t npairs
   }
   CK(c, launch_merge_finish(c->d_xy, n, mb, c->d_ec, c->st));
   CK(c, cudaMemcpyAsync(c->d_rp, c->d_new_rp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToDevice, c->st));
-  CK(c, cudaEventRecord(c->ev1, c->st));
   int32_t nnz_h = 0;
   CK(c, cudaMemcpyAsync(&nnz_h, c->d_new_rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st));
   CheckCtl h{};
   CK(c, read_check(c, &h));
-  if (ms) *ms += elapsed_ms(c);
   c->nnz = nnz_h;
   if (h.flags) return fail(c, F2M_ERR_INVALID_ARG, check_message(h.flags, h.first_bad));
+  CK(c, plan_build(c->d_rp, c->d_ec, n, c->nnz, c->num_sms, !(c->p.flags & F2M_FLAG_STREAMING_GDP),
+                   c->plan, c->st));
+  CK(c, cudaEventRecord(c->ev1, c->st));
+  if (ms) *ms += elapsed_ms(c);
   return F2M_OK;
 }
 
@@ -484,24 +579,44 @@ static f2m_status bound_internal(f2m_ctx* c, int64_t* b2) {
   return F2M_OK;
 }
 
+// Exact finisher: device prep (twin arcs, initial flow, surpluses) on the
+// renumbered CSR, successive shortest paths on the host, results scattered back
+// to caller order on the device.
 static f2m_status finisher_internal(f2m_ctx* c, int64_t* aug) {
   const int32_t n = c->n;
-  std::vector<int32_t> rp(n + 1), lam(n), lam2(n);
-  std::vector<int2> ec(c->nnz);
-  std::vector<uint8_t> x2(c->nnz);
-  CK(c, cudaMemcpyAsync(rp.data(), c->d_rp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, c->st));
-  CK(c, cudaMemcpyAsync(ec.data(), c->d_ec, sizeof(int2) * c->nnz, cudaMemcpyDeviceToHost, c->st));
-  CK(c, cudaMemcpyAsync(lam.data(), c->d_lam[c->cur], sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->st));
+  const int32_t F = c->p.frac_bits;
+  GdpPlan& P = c->plan;
+  if (c->fin_cap < c->nnz) CK(c, alloc_finisher_buffers(c, c->ec_cap));
+  if (!c->fin_work) c->fin_work = finisher_work_new();
+  if (c->fin_version != P.version) {  // the graph changed: mirror it again
+    CK(c, fin_build_twin(P, c->d_twin, c->st));
+    CK(c, cudaMemcpyAsync(c->h_irp, P.irp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaMemcpyAsync(c->h_iec, P.iec, sizeof(int2) * c->nnz, cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaMemcpyAsync(c->h_twin, c->d_twin, sizeof(int32_t) * c->nnz, cudaMemcpyDeviceToHost, c->st));
+  }
+  int32_t* d_lam_int = P.ilam[0];   // free outside a GDP phase
+  int32_t* d_lam2_int = P.ilam[1];
+  int32_t* d_exl = P.tmp;
+  CK(c, fin_prepare(P, c->d_lam[c->cur], F, d_lam_int, c->d_fy, d_exl, c->st));
+  CK(c, cudaMemcpyAsync(c->h_y, c->d_fy, c->nnz, cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaMemcpyAsync(c->h_exl, d_exl, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaMemcpyAsync(c->h_lam, d_lam_int, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->st));
   CK(c, cudaStreamSynchronize(c->st));
-  const int r = host_finisher(n, rp.data(), ec.data(), lam.data(), c->p.frac_bits, x2.data(),
-                              lam2.data(), aug);
+  if (c->fin_version != P.version) {
+    for (int64_t e = 0; e < c->nnz; ++e)
+      if (c->h_twin[e] < 0) return fail(c, F2M_ERR_INVALID_ARG, "finisher: CSR not symmetric");
+    c->fin_version = P.version;
+  }
+  const int r = host_finisher(n, c->h_irp, c->h_iec, c->h_twin, c->h_y, c->h_exl, c->h_lam, F,
+                              c->h_x, c->h_lam2, aug, c->fin_work);
   if (r == 7) return fail(c, F2M_ERR_INFEASIBLE, "no fractional 2-matching exists on the candidate graph");
   if (r == 5) return fail(c, F2M_ERR_OVERFLOW, "finisher lambda out of range");
-  if (r != 0) return fail(c, F2M_ERR_INVALID_ARG, "finisher: CSR not symmetric");
-  CK(c, cudaMemcpyAsync(c->d_x2, x2.data(), c->nnz, cudaMemcpyHostToDevice, c->st));
-  CK(c, cudaMemcpyAsync(c->d_lam2, lam2.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->st));
+  if (r != 0) return fail(c, F2M_ERR_INVALID_ARG, "finisher failed");
+  CK(c, cudaMemcpyAsync(c->d_fx, c->h_x, c->nnz, cudaMemcpyHostToDevice, c->st));
+  CK(c, cudaMemcpyAsync(d_lam2_int, c->h_lam2, sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->st));
+  CK(c, fin_scatter(P, c->d_rp, c->d_fx, d_lam2_int, c->d_x2, c->d_lam2, c->st));
   CK(c, cudaStreamSynchronize(c->st));
-  c->fb_cur = c->p.frac_bits + 1;
+  c->fb_cur = F + 1;
   return F2M_OK;
 }
 

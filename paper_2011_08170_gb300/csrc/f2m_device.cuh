@@ -66,6 +66,35 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* 
   return s_ok != 0;
 }
 
+// Device-wide barrier on a monotone arrival counter (cooperative launch only).
+// Barrier number k (k = 1, 2, ...) completes when the counter reaches
+// k * gridDim.x.  Arrival is one release-ordered atomic add (it publishes the
+// block's earlier writes); waiting is acquire-ordered polling of the counter,
+// bounded by `budget` clock cycles (false on time-out).  The counter never
+// needs resetting, so the last block to arrive does no extra work.
+__device__ __forceinline__ bool grid_barrier_counted(unsigned int* count, unsigned int target,
+                                                     long long budget) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned int v;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(v) : "l"(count) : "memory");
+    v += 1;
+    if ((int)(v - target) < 0) {
+      const long long t0 = clock64();
+      for (;;) {
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+        if ((int)(v - target) >= 0) break;
+        if (clock64() - t0 > budget) { ok = 0; break; }
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 __device__ __forceinline__ long long warp_sum_ll(long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -76,6 +105,37 @@ __device__ __forceinline__ unsigned warp_sum_u(unsigned v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Exclusive prefix sum over the block (blockDim.x a multiple of 32, <= 1024);
+// s_warp needs 33 ints.  total receives the block sum.
+__device__ __forceinline__ int block_exclusive_scan(int x, int* s_warp, int& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_warp[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    int w = lane < nw ? s_warp[lane] : 0;
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < nw) s_warp[lane] = wi - w;
+    if (lane == nw - 1) s_warp[32] = wi;
+  }
+  __syncthreads();
+  total = s_warp[32];
+  const int r = s_warp[warp] + inc - x;
+  __syncthreads();
+  return r;
 }
 
 }  // namespace f2m

@@ -101,10 +101,72 @@ size_t scan_scratch_ints(int32_t m);
 cudaError_t launch_split_ec(const int2* ec, int64_t nnz, int32_t* col, int32_t* cost,
                             cudaStream_t st);
 
-// ---- host finisher (finisher.cpp) --------------------------------------------
-// Exact min-cost flow on the bipartite double cover; see finisher.cpp.
+// ---- shared-memory tiled GDP (gdp_tiled.cu) ----------------------------------------
+// Spatial renumbering and per-CTA plan; see gdp_tiled.cu.
+struct GdpPlan {
+  int32_t n = 0;
+  int64_t version = 0;           // bumped whenever the internal CSR is rebuilt
+  bool valid = false;            // the tiled kernel can run this CSR
+  int32_t B = 0, threads = 0;    // CTAs (one node range each) and threads per CTA
+  int32_t maxO = 0, maxE = 0, maxH = 0;
+  int32_t halo_total = 0;
+  size_t smem = 0;               // dynamic shared memory per CTA
+  int32_t* perm = nullptr;       // internal -> caller node
+  int32_t* inv = nullptr;        // caller -> internal node
+  int32_t* irp = nullptr;        // internal CSR offsets
+  int2* iec = nullptr;           // internal {col, cost}
+  int2* lec = nullptr;           // {local index, cost}
+  int32_t* part = nullptr;       // [B+1] node range of each CTA
+  int32_t* hoff = nullptr;       // [B+1] halo offsets
+  int32_t* hcount = nullptr;
+  int32_t* halo = nullptr;       // halo node ids (internal)
+  int32_t* tmp = nullptr;
+  int32_t* stats = nullptr;
+  int32_t* ilam[2] = {nullptr, nullptr};  // lambda in internal order (Jacobi pair)
+  uint64_t* keys = nullptr;
+  uint64_t* keys2 = nullptr;
+  int32_t* idx = nullptr;
+  void* sort_tmp = nullptr;
+  int32_t* scan_tmp = nullptr;
+  int64_t irp_cap = 0, iec_cap = 0, lec_cap = 0, tmp_cap = 0, halo_cap = 0, scan_cap = 0;
+  int64_t ilam_cap[2] = {0, 0};
+};
+cudaError_t sort_pairs_u64(void* temp, size_t& temp_bytes, const uint64_t* keys_in,
+                           uint64_t* keys_out, const int32_t* vals_in, int32_t* vals_out,
+                           int32_t count, int end_bit, cudaStream_t st);
+cudaError_t plan_renumber(const int2* xy, int32_t n, GdpPlan& p, cudaStream_t st);
+// internal CSR (always) and, if `tiles`, the per-CTA tiles of the shared-memory kernel
+cudaError_t plan_build(const int32_t* rp, const int2* ec, int32_t n, int64_t nnz, int num_sms,
+                       bool tiles, GdpPlan& p, cudaStream_t st);
+// dst[i] = src[perm[i]]  /  dst[perm[i]] = src[i]
+cudaError_t gather_perm(const int32_t* src, const int32_t* perm, int32_t n, int32_t* dst,
+                        cudaStream_t st);
+cudaError_t scatter_perm(const int32_t* src, const int32_t* perm, int32_t n, int32_t* dst,
+                         cudaStream_t st);
+void plan_free(GdpPlan& p);
+// gathers lam_in (caller order) into ilam[0], then one cooperative tiled launch
+cudaError_t launch_gdp_tiled(GdpPlan& p, const int32_t* lam_in, int32_t F, int32_t shift,
+                             int64_t max_sweeps, GdpCtl* ctl, long long* trace_b2,
+                             unsigned long long* trace_ch, int64_t trace_cap, long long budget,
+                             cudaStream_t st);
+// lam_out (caller order) = ilam[which]
+cudaError_t plan_scatter_lambda(const GdpPlan& p, int which, int32_t* lam_out, cudaStream_t st);
+
+// ---- exact finisher (finisher_prep.cu on the device, finisher.cpp on the host) ---
+cudaError_t fin_build_twin(const GdpPlan& p, int32_t* twin, cudaStream_t st);
+cudaError_t fin_prepare(const GdpPlan& p, const int32_t* lam_caller, int32_t F, int32_t* lam_int,
+                        uint8_t* y, int32_t* exl, cudaStream_t st);
+cudaError_t fin_scatter(const GdpPlan& p, const int32_t* rp, const uint8_t* x_int,
+                        const int32_t* lam2_int, uint8_t* x_out, int32_t* lam2_out, cudaStream_t st);
+struct FinisherWork;
+FinisherWork* finisher_work_new();
+void finisher_work_reserve(FinisherWork* w, int32_t n);  // host work arrays for n nodes
+void finisher_work_free(FinisherWork* w);
+// Min-cost flow on the bipartite double cover, internal node order; see
+// finisher.cpp.  y is the initial flow (updated), exl the left surpluses.
 // Returns 0 ok, 7 infeasible, 5 overflow.
-int host_finisher(int32_t n, const int32_t* rp, const int2* ec, const int32_t* lam, int32_t F,
-                  uint8_t* x2, int32_t* lam2, int64_t* augmentations);
+int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t* twin, uint8_t* y,
+                  const int32_t* exl, const int32_t* lam, int32_t F, uint8_t* x2, int32_t* lam2,
+                  int64_t* augmentations, FinisherWork* w);
 
 }  // namespace f2m

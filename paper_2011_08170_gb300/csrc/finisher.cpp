@@ -16,164 +16,189 @@
 // arc's reduced cost C - pi(tail) + pi(head) is the adjusted length z_e (Eq. 9);
 // arcs with z_e < 0 start saturated, so no residual arc has negative reduced
 // cost.  Successive shortest paths then move one unit per step from the
-// lowest-numbered node with surplus to the nearest node with deficit (Dijkstra
-// on reduced costs, heap order (distance, node)), and raise pi by
-// d(t) - d(i) on the nodes settled before t.  The rules are fixed, so the
-// result is deterministic.
+// surplus node with the smallest key to the nearest node with deficit
+// (Dijkstra on reduced costs, heap order (distance, key)), and raise pi by
+// d(t) - d(i) on the nodes settled before t.  The key orders nodes along a
+// Morton curve of their points (ties by caller id), left copy before right
+// copy, so successive searches stay in nearby memory.  The rules are fixed,
+// so the result is deterministic.
+//
+// Layout: the graph arrives in the renumbered node order prepared on the
+// device (finisher_prep.cu): internal node i is the i-th point in (Morton
+// code, caller id) order, every row keeps the caller's column order.  Node
+// ids here: L_i = i, R_i = n + i; key(L_i) = 2i, key(R_i) = 2i + 1.
 #include <cstdint>
-#include <queue>
-#include <utility>
 #include <vector>
 
 #include "f2m_internal.h"
 
 namespace f2m {
 
-namespace {
+struct FinisherWork {
+  std::vector<int64_t> pi, dist;
+  std::vector<int32_t> excess, via, pred, order;
+  std::vector<int32_t> sources;  // surplus nodes in key order
+  std::vector<uint32_t> reached, closed;
+  uint32_t round = 0;
+  struct Item {
+    int64_t d;
+    int32_t key;   // the tie-break
+    int32_t node;  // internal id
+  };
+  std::vector<Item> heap;
 
-struct Network {
-  int32_t n = 0;
-  int64_t m = 0;
-  std::vector<int32_t> head_of;   // per arc: v of L_u -> R_v
-  std::vector<int32_t> tail_of;   // per arc: u
-  std::vector<int64_t> cost;      // per arc: c * 2^F
-  std::vector<int32_t> twin;      // per arc: the arc of the opposite direction (v -> u)
-  std::vector<uint8_t> flow;      // per arc: 0 or 1
-  std::vector<int32_t> off;       // CSR offsets shared by L_u (out arcs) and R_u (in arcs)
+  static bool less(const Item& a, const Item& b) { return a.d < b.d || (a.d == b.d && a.key < b.key); }
+  void push(const Item& it) {
+    heap.push_back(it);
+    size_t i = heap.size() - 1;
+    while (i > 0) {
+      const size_t p = (i - 1) / 2;
+      if (!less(heap[i], heap[p])) break;
+      const Item t = heap[i]; heap[i] = heap[p]; heap[p] = t;
+      i = p;
+    }
+  }
+  Item pop() {
+    const Item top = heap[0];
+    heap[0] = heap.back();
+    heap.pop_back();
+    size_t i = 0;
+    const size_t m = heap.size();
+    for (;;) {
+      const size_t l = 2 * i + 1, r = l + 1;
+      size_t s = i;
+      if (l < m && less(heap[l], heap[s])) s = l;
+      if (r < m && less(heap[r], heap[s])) s = r;
+      if (s == i) break;
+      const Item t = heap[i]; heap[i] = heap[s]; heap[s] = t;
+      i = s;
+    }
+    return top;
+  }
 };
 
-}  // namespace
+FinisherWork* finisher_work_new() { return new FinisherWork(); }
 
-int host_finisher(int32_t n, const int32_t* rp, const int2* ec, const int32_t* lam, int32_t F,
-                  uint8_t* x2, int32_t* lam2, int64_t* augmentations) {
-  Network g;
-  g.n = n;
-  g.m = rp[n];
-  g.off.assign(rp, rp + n + 1);
-  g.head_of.resize(g.m);
-  g.tail_of.resize(g.m);
-  g.cost.resize(g.m);
-  g.twin.resize(g.m);
-  g.flow.assign(g.m, 0);
-  for (int32_t u = 0; u < n; ++u) {
-    for (int32_t a = rp[u]; a < rp[u + 1]; ++a) {
-      g.head_of[a] = ec[a].x;
-      g.tail_of[a] = u;
-      g.cost[a] = (int64_t)ec[a].y << F;
-    }
+void finisher_work_reserve(FinisherWork* w, int32_t n) {
+  const size_t N = 2 * (size_t)n;
+  if (w->pi.size() >= N) return;
+  w->pi.assign(N, 0);
+  w->dist.assign(N, 0);
+  w->excess.assign(N, 0);
+  w->via.assign(N, 0);
+  w->pred.assign(N, 0);
+  w->reached.assign(N, 0);
+  w->closed.assign(N, 0);
+  w->round = 0;
+  w->order.reserve(1024);
+  w->heap.reserve(4096);
+  w->sources.reserve(N / 16 + 64);
+}
+void finisher_work_free(FinisherWork* w) { delete w; }
+
+int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t* twin, uint8_t* y,
+                  const int32_t* exl, const int32_t* lam, int32_t F, uint8_t* x2, int32_t* lam2,
+                  int64_t* augmentations, FinisherWork* w) {
+  const int32_t N = 2 * n;
+  finisher_work_reserve(w, n);
+  int64_t* pi = w->pi.data();
+  int64_t* dist = w->dist.data();
+  int32_t* excess = w->excess.data();
+  int32_t* via = w->via.data();
+  int32_t* pred = w->pred.data();
+  uint32_t* reached = w->reached.data();
+  uint32_t* closed = w->closed.data();
+  for (int32_t i = 0; i < n; ++i) {
+    pi[i] = lam[i];
+    pi[n + i] = -(int64_t)lam[i];
+    excess[i] = exl[i];       // L_i: supply 2 minus outflow
+    excess[n + i] = -exl[i];  // R_i: inflow minus demand 2 (z is symmetric)
   }
-  // twin arcs: rows are sorted, so walk row v for each u in increasing order
-  {
-    std::vector<int32_t> pos(g.off.begin(), g.off.end() - 1);
-    for (int32_t u = 0; u < n; ++u) {
-      for (int32_t a = rp[u]; a < rp[u + 1]; ++a) {
-        const int32_t v = g.head_of[a];
-        // entries of row v are visited in increasing u, which is their column order
-        int32_t b = pos[v];
-        while (b < rp[v + 1] && g.head_of[b] < u) ++b;
-        if (b >= rp[v + 1] || g.head_of[b] != u) return 1;  // not symmetric
-        g.twin[a] = b;
-        pos[v] = b + 1;
-      }
-    }
-  }
-  const int32_t N = 2 * n;  // node ids: L_v = v, R_v = n + v
-  std::vector<int64_t> pi(N), excess(N);
-  for (int32_t v = 0; v < n; ++v) {
-    pi[v] = lam[v];
-    pi[n + v] = -(int64_t)lam[v];
-  }
-  std::vector<int32_t> outflow(n, 0), inflow(n, 0);
-  for (int64_t a = 0; a < g.m; ++a) {
-    const int64_t z = g.cost[a] - lam[g.tail_of[a]] - lam[g.head_of[a]];
-    if (z < 0) {
-      g.flow[a] = 1;
-      ++outflow[g.tail_of[a]];
-      ++inflow[g.head_of[a]];
-    }
-  }
-  for (int32_t v = 0; v < n; ++v) {
-    excess[v] = 2 - outflow[v];
-    excess[n + v] = inflow[v] - 2;
+  auto key_of = [&](int32_t node) { return node < n ? 2 * node : 2 * (node - n) + 1; };
+
+  // Surplus only shrinks (a path ends at a deficit node), so the nodes that
+  // will ever be sources are those with surplus now, taken in key order, each
+  // until its surplus is used up.
+  std::vector<int32_t>& src = w->sources;
+  src.clear();
+  for (int32_t i = 0; i < n; ++i) {
+    if (excess[i] > 0) src.push_back(i);
+    if (excess[n + i] > 0) src.push_back(n + i);
   }
 
-  std::vector<int64_t> dist(N);
-  std::vector<int32_t> via(N);            // arc used to reach the node
-  std::vector<uint32_t> reached(N, 0), closed(N, 0);
-  std::vector<int32_t> order;
-  order.reserve(1024);
-  typedef std::pair<int64_t, int32_t> Item;
-  std::priority_queue<Item, std::vector<Item>, std::greater<Item>> pq;
-  uint32_t round = 0;
   int64_t pushes = 0;
-  int32_t next_src = 0;
   int status = 0;
-
+  size_t next_src = 0;
   for (;;) {
-    while (next_src < N && excess[next_src] <= 0) ++next_src;
-    if (next_src >= N) break;
-    const int32_t s = next_src;
-    ++round;
-    order.clear();
-    while (!pq.empty()) pq.pop();
+    int32_t s = -1;
+    while (next_src < src.size()) {
+      const int32_t node = src[next_src];
+      if (excess[node] > 0) { s = node; break; }
+      ++next_src;
+    }
+    if (s < 0) break;
+    if (++w->round == 0) {  // stamp wrap: clear and restart
+      w->reached.assign(N, 0);
+      w->closed.assign(N, 0);
+      w->round = 1;
+    }
+    const uint32_t round = w->round;
+    w->order.clear();
+    w->heap.clear();
     dist[s] = 0;
     reached[s] = round;
-    via[s] = -1;
-    pq.push(Item(0, s));
+    pred[s] = -1;
+    w->push({0, key_of(s), s});
     int32_t t = -1;
-    while (!pq.empty()) {
-      const Item top = pq.top();
-      pq.pop();
-      const int32_t i = top.second;
-      if (closed[i] == round || top.first != dist[i]) continue;
+    while (!w->heap.empty()) {
+      const FinisherWork::Item top = w->pop();
+      const int32_t i = top.node;
+      if (closed[i] == round || top.d != dist[i]) continue;
       closed[i] = round;
       if (excess[i] < 0) { t = i; break; }
-      order.push_back(i);
+      w->order.push_back(i);
       if (i < n) {
-        // out arcs of L_i with no flow: L_i -> R_head
-        for (int32_t a = g.off[i]; a < g.off[i + 1]; ++a) {
-          if (g.flow[a]) continue;
-          const int32_t j = n + g.head_of[a];
-          const int64_t d = dist[i] + g.cost[a] - pi[i] + pi[j];
+        // out arcs of L_i without flow: L_i -> R_j
+        for (int32_t e = irp[i]; e < irp[i + 1]; ++e) {
+          if (y[e]) continue;
+          const int32_t j = n + iec[e].x;
+          const int64_t d = dist[i] + ((int64_t)iec[e].y << F) - pi[i] + pi[j];
           if (closed[j] != round && (reached[j] != round || d < dist[j])) {
-            reached[j] = round; dist[j] = d; via[j] = a;
-            pq.push(Item(d, j));
+            reached[j] = round; dist[j] = d; via[j] = e; pred[j] = i;
+            w->push({d, key_of(j), j});
           }
         }
       } else {
-        // R_v: reverse arcs of saturated arcs u -> v, i.e. the twins of row v
+        // R_v: reverse arcs of saturated arcs u -> v (the twins of row v)
         const int32_t v = i - n;
-        for (int32_t b = g.off[v]; b < g.off[v + 1]; ++b) {
-          const int32_t a = g.twin[b];  // arc (head_of[b] -> v)
-          if (!g.flow[a]) continue;
-          const int32_t j = g.tail_of[a];
-          const int64_t d = dist[i] - g.cost[a] - pi[i] + pi[j];
+        for (int32_t f = irp[v]; f < irp[v + 1]; ++f) {
+          const int32_t a = twin[f];
+          if (!y[a]) continue;
+          const int32_t j = iec[f].x;  // L_u, the tail of arc a
+          const int64_t d = dist[i] - ((int64_t)iec[f].y << F) - pi[i] + pi[j];
           if (closed[j] != round && (reached[j] != round || d < dist[j])) {
-            reached[j] = round; dist[j] = d; via[j] = a;
-            pq.push(Item(d, j));
+            reached[j] = round; dist[j] = d; via[j] = a; pred[j] = i;
+            w->push({d, key_of(j), j});
           }
         }
       }
     }
     if (t < 0) { status = 7; break; }
-    for (int32_t j = t; j != s;) {
-      const int32_t a = via[j];
-      if (j >= n) { g.flow[a] = 1; j = g.tail_of[a]; }
-      else { g.flow[a] = 0; j = n + g.head_of[a]; }
-    }
+    for (int32_t j = t; j != s; j = pred[j]) y[via[j]] = (uint8_t)(j >= n);  // push one unit
     excess[s] -= 1;
     excess[t] += 1;
     ++pushes;
     const int64_t dt = dist[t];
-    for (int32_t i : order) pi[i] += dt - dist[i];
+    for (int32_t i : w->order) pi[i] += dt - dist[i];
   }
   *augmentations = pushes;
   if (status != 0) return status;
-  for (int64_t a = 0; a < g.m; ++a) x2[a] = (uint8_t)(g.flow[a] + g.flow[g.twin[a]]);
-  for (int32_t v = 0; v < n; ++v) {
-    const int64_t l2 = pi[v] - pi[n + v];
+  const int64_t nnz = irp[n];
+  for (int64_t e = 0; e < nnz; ++e) x2[e] = (uint8_t)(y[e] + y[twin[e]]);
+  for (int32_t i = 0; i < n; ++i) {
+    const int64_t l2 = pi[i] - pi[n + i];
     if (l2 >= 2 * kLamLimit || l2 <= -2 * kLamLimit) status = 5;
-    lam2[v] = (int32_t)l2;
+    lam2[i] = (int32_t)l2;
   }
   return status;
 }

@@ -114,35 +114,6 @@ constexpr int kScanBlock = kScanThreads * kScanItems;
 
 size_t scan_scratch_ints(int32_t m) { return (size_t)((m + kScanBlock - 1) / kScanBlock) + 1; }
 
-__device__ int block_exclusive_scan(int x, int* s_warp, int& total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int inc = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += y;
-  }
-  if (lane == 31) s_warp[warp] = inc;
-  __syncthreads();
-  if (warp == 0) {
-    const int nw = blockDim.x >> 5;
-    int w = lane < nw ? s_warp[lane] : 0;
-    int wi = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, wi, o);
-      if (lane >= o) wi += y;
-    }
-    if (lane < nw) s_warp[lane] = wi - w;
-    if (lane == nw - 1) s_warp[32] = wi;
-  }
-  __syncthreads();
-  total = s_warp[32];
-  const int r = s_warp[warp] + inc - x;
-  __syncthreads();
-  return r;
-}
-
 __global__ void __launch_bounds__(kScanThreads)
 scan_blocks_kernel(const int32_t* __restrict__ in, int32_t* __restrict__ out, int32_t m,
                    int32_t* __restrict__ block_sums) {

@@ -65,13 +65,15 @@ def test_cost_extremes(lib, O):
 
 # ---- a2-a5: GDP sweeps ------------------------------------------------------------------
 
+# flags 0: shared-memory tiled kernel on renumbered nodes; 1: streaming kernel
+@pytest.mark.parametrize("flags", [0, 1])
 @pytest.mark.parametrize("kind,n,seed,k", CASES)
-def test_gdp_phase_trace(lib, O, kind, n, seed, k):
+def test_gdp_phase_trace(lib, O, kind, n, seed, k, flags):
     d = inst(kind, n, seed, k)
     cost = O.cost_table(d["xy"], d["row_ptr"], d["col"])
     st_o, lam_o, it_o, tb_o, tc_o = O.gdp(d["row_ptr"], d["col"], cost, np.zeros(n, np.int32),
                                           8, 2, 100000, trace=True)
-    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"])
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], f2m.f2m_default_params(flags=flags))
     st, sweeps, tb, tc = f2m.f2m_gdp(ctx, 100000, trace_cap=it_o)
     lam, fb = f2m.f2m_get_lambda(ctx)
     assert (st == f2m.F2M_OK) == (st_o == O.OR_OK)
@@ -80,13 +82,14 @@ def test_gdp_phase_trace(lib, O, kind, n, seed, k):
     assert np.array_equal(tb, tb_o) and np.array_equal(tc, tc_o)
 
 
+@pytest.mark.parametrize("flags", [0, 1])
 @pytest.mark.parametrize("shift", [1, 2, 3])
-def test_single_sweeps_from_random_lambda(lib, O, shift):
+def test_single_sweeps_from_random_lambda(lib, O, shift, flags):
     d = inst("mixture", 3000, 7, 10)
     n = 3000
     cost = O.cost_table(d["xy"], d["row_ptr"], d["col"])
     rng = np.random.default_rng(shift)
-    params = f2m.f2m_default_params(damping_shift=shift)
+    params = f2m.f2m_default_params(damping_shift=shift, flags=flags)
     ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], params)
     for trial in range(3):
         lam = rng.integers(-(1 << 24), 1 << 24, size=n).astype(np.int32)
@@ -219,7 +222,7 @@ def test_merge(lib, O):
 
 def _compare_solve(O, d, **kw):
     r = O.solve(d["xy"], d["row_ptr"], d["col"], max_iters=kw.get("max_iters", 1000000))
-    params = f2m.f2m_default_params(max_iters=kw.get("max_iters", 1000000))
+    params = f2m.f2m_default_params(max_iters=kw.get("max_iters", 1000000), flags=kw.get("flags", 0))
     s = f2m.solve(d["xy"], d["row_ptr"], d["col"], params=params)
     i = s.info
     assert i["status"] == r.status == 0
@@ -232,10 +235,11 @@ def _compare_solve(O, d, **kw):
     return s, r
 
 
+@pytest.mark.parametrize("flags", [0, 1])
 @pytest.mark.parametrize("kind,n,seed,k", [("uniform", 1000, 0, 10), ("mixture", 1000, 0, 10),
                                            ("mixture", 3000, 2, 10), ("uniform", 2000, 1, 6)])
-def test_solve_bit_exact(lib, O, kind, n, seed, k):
-    s, r = _compare_solve(O, inst(kind, n, seed, k))
+def test_solve_bit_exact(lib, O, kind, n, seed, k, flags):
+    s, r = _compare_solve(O, inst(kind, n, seed, k), flags=flags)
     assert s.info["certified"] == 2
 
 
@@ -329,3 +333,44 @@ def test_infeasible_candidate_graph(lib):
     ctx = f2m.f2m_create(xy, rp, col, f2m.f2m_default_params(pricing=0, max_iters=2000))
     info = f2m.f2m_solve(ctx, raise_on_error=False)
     assert info.status in (f2m.F2M_ERR_INFEASIBLE, f2m.F2M_ERR_OVERFLOW)
+
+
+def test_tiled_path_on_tiny_and_clustered_graphs(lib, O):
+    # few nodes per CTA, duplicate points, dense clusters: renumbering ties and
+    # halos that cover most of the graph
+    rng = np.random.default_rng(9)
+    xy = np.concatenate([rng.integers(0, 50, size=(300, 2)), rng.integers(0, 10 ** 6, size=(200, 2)),
+                         np.repeat([[777, 777]], 12, axis=0)]).astype(np.int32)
+    rp, col = I.knn_csr(xy, 8)
+    cost = O.cost_table(xy, rp, col)
+    st_o, lam_o, it_o, tb_o, tc_o = O.gdp(rp, col, cost, np.zeros(len(xy), np.int32), 8, 2, 100000, trace=True)
+    ctx = f2m.f2m_create(xy, rp, col)
+    st, sweeps, tb, tc = f2m.f2m_gdp(ctx, 100000, trace_cap=it_o)
+    assert sweeps == it_o and np.array_equal(f2m.f2m_get_lambda(ctx)[0], lam_o)
+    assert np.array_equal(tb, tb_o) and np.array_equal(tc, tc_o)
+    _compare_solve(O, {"xy": xy, "row_ptr": rp, "col": col})
+
+
+def test_gdp_full_size_sampled(lib, O):
+    # the 100,000-node workload: the first 40 sweeps bit-exact against the
+    # oracle, then the fixed point checked node by node on a sample
+    d = inst("uniform", 100000, 0, 10)
+    n = 100000
+    cost = O.cost_table(d["xy"], d["row_ptr"], d["col"])
+    st_o, lam_o, it_o, tb_o, tc_o = O.gdp(d["row_ptr"], d["col"], cost, np.zeros(n, np.int32),
+                                          8, 2, 40, trace=True)
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"])
+    st, sweeps, tb, tc = f2m.f2m_gdp(ctx, 40, trace_cap=40)
+    assert sweeps == 40 and np.array_equal(f2m.f2m_get_lambda(ctx)[0], lam_o)
+    assert np.array_equal(tb, tb_o) and np.array_equal(tc, tc_o)
+    st, sweeps, *_ = f2m.f2m_gdp(ctx, 10 ** 6)
+    assert st == f2m.F2M_OK
+    lam, _ = f2m.f2m_get_lambda(ctx)
+    rp, col = d["row_ptr"], d["col"]
+    for v in np.random.default_rng(0).choice(n, 300, replace=False):
+        row = slice(rp[v], rp[v + 1])
+        z = np.sort((cost[row].astype(np.int64) << 8) - lam[v] - lam[col[row]])
+        assert abs(int(z[1]) + int(z[2])) < 4  # a fixed point of the update
+    # one more oracle sweep from the GPU fixed point changes nothing
+    st1, lam1, b2, ch = O.sweep(rp, col, cost, lam, 8, 2)
+    assert ch == 0 and np.array_equal(lam1, lam)

@@ -254,13 +254,13 @@ def test_finisher_reaches_candidate_optimum(oracle_lib):
     st, lam, it, _, _ = oracle_lib.gdp(rp, col, cost, np.zeros(2000, np.int32), 8, 2, 50000)
     bad, _ = oracle_lib.extract(rp, col, cost, lam, 8)
     assert bad > 0  # the sign rule alone is not enough here
-    fst, x2, lam2, aug = oracle_lib.finisher(rp, col, cost, lam, 8)
+    fst, x2, lam2, aug = oracle_lib.finisher(xy, rp, col, cost, lam, 8)
     assert fst == 0 and aug > 0
     b2 = oracle_lib.bound2(rp, col, cost, lam2, 9)
     assert oracle_lib.certify(xy, rp, col, x2, lam2, 9, b2, full_scan=False) == 0
     assert abs(b2 / 1024.0 - highs_opt(xy, rp, col)) < 1e-6 * b2 / 1024.0
     # started from lambda = 0 it reaches the same optimum
-    fst0, x20, lam20, aug0 = oracle_lib.finisher(rp, col, cost, np.zeros(2000, np.int32), 8)
+    fst0, x20, lam20, aug0 = oracle_lib.finisher(xy, rp, col, cost, np.zeros(2000, np.int32), 8)
     assert fst0 == 0 and oracle_lib.bound2(rp, col, cost, lam20, 9) == b2 and aug0 > aug
 
 
@@ -271,7 +271,7 @@ def test_finisher_infeasible_graph(oracle_lib):
     rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
     col = np.concatenate(rows).astype(np.int32)
     cost = oracle_lib.cost_table(xy, rp, col)
-    st, *_ = oracle_lib.finisher(rp, col, cost, np.zeros(8, np.int32), 8)
+    st, *_ = oracle_lib.finisher(xy, rp, col, cost, np.zeros(8, np.int32), 8)
     assert st == oracle_lib.OR_INFEASIBLE
 
 
