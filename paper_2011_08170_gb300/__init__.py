@@ -30,6 +30,8 @@ F2M_ERR_PRICING_OVERFLOW = 6
 F2M_ERR_INFEASIBLE = 7
 F2M_ERR_TIMEOUT = 8
 
+F2M_FLAG_STREAMING_GDP = 1
+
 # every symbol the header declares
 EXPORTS = ["f2m_default_params", "f2m_create", "f2m_destroy", "f2m_set_lambda", "f2m_solve",
            "f2m_gdp", "f2m_price", "f2m_add_edges", "f2m_extract", "f2m_get_lambda",
@@ -42,7 +44,7 @@ class f2m_params(C.Structure):
                 ("max_iters", C.c_int64), ("max_pricing_rounds", C.c_int32),
                 ("pricing", C.c_int32), ("pricing_cap", C.c_int64),
                 ("barrier_budget_cycles", C.c_int64), ("finisher", C.c_int32),
-                ("flags", C.c_uint32)]
+                ("flags", C.c_uint32), ("gdp_lanes", C.c_int32), ("gdp_ctas_per_sm", C.c_int32)]
 
 
 class f2m_info(C.Structure):

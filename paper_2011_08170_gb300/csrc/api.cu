@@ -181,6 +181,8 @@ extern "C" void f2m_default_params(f2m_params* p) {
   p->barrier_budget_cycles = 4000000000LL;
   p->finisher = 1;
   p->flags = 0;
+  p->gdp_lanes = 0;
+  p->gdp_ctas_per_sm = 0;
 }
 
 extern "C" const char* f2m_status_string(f2m_status s) {
@@ -222,6 +224,10 @@ extern "C" void f2m_destroy(f2m_ctx* c) {
 static f2m_status check_params(const f2m_params& p) {
   if (p.frac_bits < 1 || p.frac_bits > 8) return fail(nullptr, F2M_ERR_INVALID_ARG, "frac_bits must be in 1..8");
   if (p.damping_shift < 1 || p.damping_shift > 8) return fail(nullptr, F2M_ERR_INVALID_ARG, "damping_shift must be in 1..8");
+  if (p.gdp_lanes != 0 && p.gdp_lanes != 1)
+    return fail(nullptr, F2M_ERR_INVALID_ARG, "gdp_lanes must be 0 or 1");
+  if (p.gdp_ctas_per_sm < 0 || p.gdp_ctas_per_sm > 2)
+    return fail(nullptr, F2M_ERR_INVALID_ARG, "gdp_ctas_per_sm must be 0, 1 or 2");
   if (p.max_iters < 0 || p.max_pricing_rounds < 0 || p.pricing_cap < 1 || p.barrier_budget_cycles < 0)
     return fail(nullptr, F2M_ERR_INVALID_ARG, "negative cap or budget");
   return F2M_OK;
@@ -308,7 +314,7 @@ extern "C" f2m_status f2m_create(const int32_t* xy, int32_t n, const int32_t* ro
     if (e == cudaSuccess) e = plan_renumber(c->d_xy, n, c->plan, c->st);
     if (e == cudaSuccess)
       e = plan_build(c->d_rp, c->d_ec, n, c->nnz, c->num_sms, !(p.flags & F2M_FLAG_STREAMING_GDP),
-                     c->plan, c->st);
+                     p.frac_bits, p.gdp_ctas_per_sm, c->plan, c->st);
     if (e == cudaSuccess && p.finisher) {
       e = alloc_finisher_buffers(c, c->ec_cap);
       c->fin_work = finisher_work_new();
@@ -389,7 +395,7 @@ static f2m_status gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, boo
   CK(c, cudaEventRecord(c->ev0, c->st));
   bool tiled = c->plan.valid;
   if (tiled) {
-    cudaError_t e = launch_gdp_tiled(c->plan, c->d_lam[c->cur], F, c->p.damping_shift, max_sweeps,
+    cudaError_t e = launch_gdp_tiled(c->plan, c->d_lam[c->cur], c->p.damping_shift, max_sweeps,
                                      c->d_gdp, want_trace ? c->d_trace_b2 : nullptr,
                                      want_trace ? c->d_trace_ch : nullptr, want_trace ? trace_cap : 0,
                                      c->p.barrier_budget_cycles, c->st);
@@ -416,7 +422,7 @@ static f2m_status gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, boo
   const long long used = ovf ? h.sweeps - 1 : h.sweeps;
   if (tiled) {
     if (!(h.status & kGdpTimeout))
-      CK(c, plan_scatter_lambda(c->plan, (int)(used & 1), c->d_lam[c->cur], c->st));
+      CK(c, plan_scatter_lambda(c->plan, (int)(used % 3), c->d_lam[c->cur], c->st));
   } else if (used & 1) {
     c->cur ^= 1;
   }
@@ -524,7 +530,7 @@ static f2m_status merge_internal(f2m_ctx* c, const int2* d_pairs, int64_t npairs
   c->nnz = nnz_h;
   if (h.flags) return fail(c, F2M_ERR_INVALID_ARG, check_message(h.flags, h.first_bad));
   CK(c, plan_build(c->d_rp, c->d_ec, n, c->nnz, c->num_sms, !(c->p.flags & F2M_FLAG_STREAMING_GDP),
-                   c->plan, c->st));
+                   c->p.frac_bits, c->p.gdp_ctas_per_sm, c->plan, c->st));
   CK(c, cudaEventRecord(c->ev1, c->st));
   if (ms) *ms += elapsed_ms(c);
   return F2M_OK;

@@ -32,6 +32,13 @@ __device__ __forceinline__ void top3_insert(int z, int& a, int& b, int& c) {
   }
 }
 
+// Branch-free form of the same insertion: the three smallest of {a, b, c, z}.
+__device__ __forceinline__ void top3_insert_minmax(int z, int& a, int& b, int& c) {
+  c = min(c, max(b, z));
+  b = min(b, max(a, z));
+  a = min(a, z);
+}
+
 // Load that bypasses L1: lambda is rewritten by other SMs between sweeps.
 __device__ __forceinline__ int ld_cg(const int* p) { return __ldcg(p); }
 
@@ -93,6 +100,23 @@ __device__ __forceinline__ bool grid_barrier_counted(unsigned int* count, unsign
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// Split form of the counted barrier, for thread 0 of each block: arrive
+// publishes this block's earlier writes (release) without waiting for a reply;
+// wait polls (acquire) until `target` arrivals, bounded by `budget` cycles.
+__device__ __forceinline__ void grid_arrive_counted(unsigned int* count) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+}
+__device__ __forceinline__ bool grid_wait_counted(unsigned int* count, unsigned int target,
+                                                  long long budget) {
+  unsigned int v;
+  const long long t0 = clock64();
+  for (;;) {
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+    if ((int)(v - target) >= 0) return true;
+    if (clock64() - t0 > budget) return false;
+  }
 }
 
 __device__ __forceinline__ long long warp_sum_ll(long long v) {

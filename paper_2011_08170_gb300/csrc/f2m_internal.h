@@ -27,6 +27,10 @@ struct GdpCtl {
   unsigned long long slot_ch[3];  // per-sweep changed counts (ring of 3)
   long long sweeps;            // sweeps completed
   long long pad1;
+  // ring of 4 per-sweep slots used by the tiled kernel (stop test lagged by two sweeps)
+  long long q_b2[4];
+  unsigned long long q_ch[4];
+  int q_ovf[4];
 };
 
 constexpr int kGdpOverflow = 1;
@@ -108,28 +112,33 @@ struct GdpPlan {
   int64_t version = 0;           // bumped whenever the internal CSR is rebuilt
   bool valid = false;            // the tiled kernel can run this CSR
   int32_t B = 0, threads = 0;    // CTAs (one node range each) and threads per CTA
-  int32_t maxO = 0, maxE = 0, maxH = 0;
+  int32_t maxO = 0, maxS = 0, maxH = 0;  // max own nodes, sliced entries, halo per CTA
   int32_t halo_total = 0;
   size_t smem = 0;               // dynamic shared memory per CTA
   int32_t* perm = nullptr;       // internal -> caller node
   int32_t* inv = nullptr;        // caller -> internal node
   int32_t* irp = nullptr;        // internal CSR offsets
   int2* iec = nullptr;           // internal {col, cost}
-  int2* lec = nullptr;           // {local index, cost}
+  int2* lec = nullptr;           // sliced {local index, cost * 2^F} per CTA
+  int32_t* scount = nullptr;     // [B+1] sliced entries per CTA
+  int32_t* soff = nullptr;       // [B+1] their offsets
+  int32_t* order = nullptr;      // [n] node of each slot (degree-descending per CTA)
+  int2* slc = nullptr;           // [n] per-CTA slice table {offset, depth}
   int32_t* part = nullptr;       // [B+1] node range of each CTA
   int32_t* hoff = nullptr;       // [B+1] halo offsets
   int32_t* hcount = nullptr;
   int32_t* halo = nullptr;       // halo node ids (internal)
   int32_t* tmp = nullptr;
   int32_t* stats = nullptr;
-  int32_t* ilam[2] = {nullptr, nullptr};  // lambda in internal order (Jacobi pair)
+  int32_t* ilam[3] = {nullptr, nullptr, nullptr};  // lambda in internal order (ring of 3)
   uint64_t* keys = nullptr;
   uint64_t* keys2 = nullptr;
   int32_t* idx = nullptr;
   void* sort_tmp = nullptr;
   int32_t* scan_tmp = nullptr;
   int64_t irp_cap = 0, iec_cap = 0, lec_cap = 0, tmp_cap = 0, halo_cap = 0, scan_cap = 0;
-  int64_t ilam_cap[2] = {0, 0};
+  int64_t order_cap = 0, slc_cap = 0;
+  int64_t ilam_cap[3] = {0, 0, 0};
 };
 cudaError_t sort_pairs_u64(void* temp, size_t& temp_bytes, const uint64_t* keys_in,
                            uint64_t* keys_out, const int32_t* vals_in, int32_t* vals_out,
@@ -137,7 +146,7 @@ cudaError_t sort_pairs_u64(void* temp, size_t& temp_bytes, const uint64_t* keys_
 cudaError_t plan_renumber(const int2* xy, int32_t n, GdpPlan& p, cudaStream_t st);
 // internal CSR (always) and, if `tiles`, the per-CTA tiles of the shared-memory kernel
 cudaError_t plan_build(const int32_t* rp, const int2* ec, int32_t n, int64_t nnz, int num_sms,
-                       bool tiles, GdpPlan& p, cudaStream_t st);
+                       bool tiles, int32_t F, int32_t ctas_per_sm, GdpPlan& p, cudaStream_t st);
 // dst[i] = src[perm[i]]  /  dst[perm[i]] = src[i]
 cudaError_t gather_perm(const int32_t* src, const int32_t* perm, int32_t n, int32_t* dst,
                         cudaStream_t st);
@@ -145,10 +154,9 @@ cudaError_t scatter_perm(const int32_t* src, const int32_t* perm, int32_t n, int
                          cudaStream_t st);
 void plan_free(GdpPlan& p);
 // gathers lam_in (caller order) into ilam[0], then one cooperative tiled launch
-cudaError_t launch_gdp_tiled(GdpPlan& p, const int32_t* lam_in, int32_t F, int32_t shift,
-                             int64_t max_sweeps, GdpCtl* ctl, long long* trace_b2,
-                             unsigned long long* trace_ch, int64_t trace_cap, long long budget,
-                             cudaStream_t st);
+cudaError_t launch_gdp_tiled(GdpPlan& p, const int32_t* lam_in, int32_t shift, int64_t max_sweeps,
+                             GdpCtl* ctl, long long* trace_b2, unsigned long long* trace_ch,
+                             int64_t trace_cap, long long budget, cudaStream_t st);
 // lam_out (caller order) = ilam[which]
 cudaError_t plan_scatter_lambda(const GdpPlan& p, int which, int32_t* lam_out, cudaStream_t st);
 

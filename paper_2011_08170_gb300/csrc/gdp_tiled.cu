@@ -106,17 +106,49 @@ __global__ void partition_kernel(const int32_t* __restrict__ irp, int32_t n, int
   }
 }
 
-// stats: [0] max own nodes, [1] max entries, [2] max halo, [3] 1 if some CTA's
-// outside references exceed the sort capacity (the tiled form is then off)
+// Degree-descending order of a CTA's own nodes (ties by local id), sorted in
+// shared memory; key = (2047 - min(deg, 2047)) << 20 | local.
+__device__ void sort_own_by_degree(const int32_t* __restrict__ irp, int lo, int own, int* s_key) {
+  const int tid = threadIdx.x, T = blockDim.x;
+  int P = 1;
+  while (P < own) P <<= 1;
+  for (int i = tid; i < P; i += T) {
+    if (i < own) {
+      const int d = irp[lo + i + 1] - irp[lo + i];
+      s_key[i] = ((2047 - min(d, 2047)) << 20) | i;
+    } else {
+      s_key[i] = INT_MAX;
+    }
+  }
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < P; i += T) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const int a = s_key[i], c = s_key[ixj];
+          const bool up = (i & k) == 0;
+          if ((a > c) == up) { s_key[i] = c; s_key[ixj] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Pass 1, one CTA per node range: the sorted distinct outside nodes (halo) go
+// to tmp[E0, E0 + H); hcount[b] = H; scount[b] = sliced entry count.
+// stats: [0] max own nodes, [1] max sliced entries, [2] max halo, [3] 1 if some
+// CTA does not fit the sort buffer (the tiled form is then off).
 __global__ void plan_halo_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ iec,
                                  const int32_t* __restrict__ part, int32_t sort_cap,
                                  int32_t* __restrict__ tmp, int32_t* __restrict__ hcount,
-                                 int32_t* __restrict__ stats) {
+                                 int32_t* __restrict__ scount, int32_t* __restrict__ stats) {
   extern __shared__ int s_sort[];
   __shared__ int s_cnt;
   __shared__ int s_warp[33];
   const int b = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
-  const int lo = part[b], hi = part[b + 1];
+  const int lo = part[b], hi = part[b + 1], own = hi - lo;
   const int E0 = irp[lo], E1 = irp[hi];
   if (tid == 0) s_cnt = 0;
   __syncthreads();
@@ -129,15 +161,14 @@ __global__ void plan_halo_kernel(const int32_t* __restrict__ irp, const int2* __
   }
   __syncthreads();
   const int m = s_cnt;
-  if (m > sort_cap) {
-    if (tid == 0) { atomicOr(&stats[3], 1); hcount[b] = 0; }
+  if (m > sort_cap || own > sort_cap) {
+    if (tid == 0) { atomicOr(&stats[3], 1); hcount[b] = 0; scount[b] = 0; }
     return;
   }
   int P = 1;
   while (P < m) P <<= 1;
   for (int i = m + tid; i < P; i += T) s_sort[i] = INT_MAX;
   __syncthreads();
-  // bitonic sort of s_sort[0, P)
   for (int k = 2; k <= P; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = tid; i < P; i += T) {
@@ -160,58 +191,116 @@ __global__ void plan_halo_kernel(const int32_t* __restrict__ irp, const int2* __
   int o = block_exclusive_scan(cnt, s_warp, total);
   for (int i = i0; i < i1; ++i)
     if (i == 0 || s_sort[i] != s_sort[i - 1]) tmp[E0 + o++] = s_sort[i];
+  __syncthreads();
+  // sliced size: 32 slots per slice, each slice as deep as its first (largest) row
+  sort_own_by_degree(irp, lo, own, s_sort);
+  int sz = 0;
+  for (int s = tid; s * 32 < own; s += T) {
+    const int first = s_sort[s * 32] & 0xFFFFF;
+    sz += 32 * (irp[lo + first + 1] - irp[lo + first]);
+  }
+  int ssum = 0;
+  block_exclusive_scan(sz, s_warp, ssum);
   if (tid == 0) {
     hcount[b] = total;
-    atomicMax(&stats[0], hi - lo);
-    atomicMax(&stats[1], E1 - E0);
+    scount[b] = ssum;
+    atomicMax(&stats[0], own);
+    atomicMax(&stats[1], ssum);
     atomicMax(&stats[2], total);
   }
 }
 
+// Pass 2: node order, slice table and sliced entries of each CTA.
+//   order[lo + p]  = local node handled by slot p (degree-descending)
+//   slc[lo + s]    = {offset of slice s in the CTA's entries, slice depth}
+//   lec[soff[b] + base + k*32 + lane] = {local index, cost * 2^F} of entry k of
+//   the node in slot 32 s + lane; short rows are padded with {zero slot, 2^30}.
 __global__ void plan_map_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ iec,
                                 const int32_t* __restrict__ part, const int32_t* __restrict__ tmp,
-                                const int32_t* __restrict__ hoff, int32_t* __restrict__ halo,
-                                int2* __restrict__ lec) {
+                                const int32_t* __restrict__ hoff, const int32_t* __restrict__ soff,
+                                int32_t F, int32_t* __restrict__ halo, int32_t* __restrict__ order,
+                                int2* __restrict__ slc, int2* __restrict__ lec) {
+  extern __shared__ int s_key[];
+  __shared__ int s_warp[33];
   const int b = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
   const int lo = part[b], hi = part[b + 1], own = hi - lo;
-  const int E0 = irp[lo], E1 = irp[hi];
+  const int E0 = irp[lo];
   const int hb = hoff[b], H = hoff[b + 1] - hb;
+  const int zero_slot = own + H;
   const int32_t* list = tmp + E0;
   for (int h = tid; h < H; h += T) halo[hb + h] = list[h];
-  for (int e = E0 + tid; e < E1; e += T) {
-    const int2 q = iec[e];
-    int local;
-    if (q.x >= lo && q.x < hi) {
-      local = q.x - lo;
-    } else {
-      int a = 0, z = H;  // lower bound of q.x in list[0, H)
-      while (a < z) {
-        const int mid = (a + z) >> 1;
-        if (list[mid] < q.x) a = mid + 1; else z = mid;
+  sort_own_by_degree(irp, lo, own, s_key);
+  const int nsl = (own + 31) / 32;
+  // slice offsets: exclusive scan of 32 * depth over slices (chunked per thread)
+  const int chunk = (nsl + T - 1) / T;
+  const int s0 = min(nsl, tid * chunk), s1 = min(nsl, s0 + chunk);
+  int sz = 0;
+  for (int s = s0; s < s1; ++s) {
+    const int first = s_key[s * 32] & 0xFFFFF;
+    sz += 32 * (irp[lo + first + 1] - irp[lo + first]);
+  }
+  int total = 0;
+  int base = block_exclusive_scan(sz, s_warp, total);
+  for (int s = s0; s < s1; ++s) {
+    const int first = s_key[s * 32] & 0xFFFFF;
+    const int depth = irp[lo + first + 1] - irp[lo + first];
+    slc[lo + s] = make_int2(base, depth);
+    base += 32 * depth;
+  }
+  __syncthreads();
+  int2* out = lec + soff[b];
+  for (int p = tid; p < nsl * 32; p += T) {
+    const int s = p >> 5, lane = p & 31;
+    const int2 sl = slc[lo + s];
+    if (p < own) {
+      const int vl = s_key[p] & 0xFFFFF;
+      order[lo + p] = vl;
+      const int a = irp[lo + vl], d = irp[lo + vl + 1] - a;
+      for (int k = 0; k < sl.y; ++k) {
+        int2 q;
+        if (k < d) {
+          const int2 r = iec[a + k];
+          int local;
+          if (r.x >= lo && r.x < hi) {
+            local = r.x - lo;
+          } else {
+            int x = 0, z = H;  // lower bound of r.x in the halo list
+            while (x < z) {
+              const int mid = (x + z) >> 1;
+              if (list[mid] < r.x) x = mid + 1; else z = mid;
+            }
+            local = own + x;
+          }
+          q = make_int2(local, r.y << F);  // cost in units 2^-F
+        } else {
+          q = make_int2(zero_slot, 1 << 30);
+        }
+        out[sl.x + k * 32 + lane] = q;
       }
-      local = own + a;
+    } else {
+      for (int k = 0; k < sl.y; ++k) out[sl.x + k * 32 + lane] = make_int2(zero_slot, 1 << 30);
     }
-    lec[e] = make_int2(local, q.y);
   }
 }
 
 // ---- the tiled persistent kernel ------------------------------------------------------
 
-template <int G>
-__global__ void __launch_bounds__(1024)
-gdp_tiled_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ lec,
-                 const int32_t* __restrict__ part, const int32_t* __restrict__ hoff,
-                 const int32_t* __restrict__ halo, int32_t* lam0, int32_t* lam1, int32_t F,
+__global__ void __launch_bounds__(1024, 1)
+gdp_tiled_kernel(const int32_t* __restrict__ part, const int32_t* __restrict__ hoff,
+                 const int32_t* __restrict__ soff, const int32_t* __restrict__ halo,
+                 const int32_t* __restrict__ order, const int2* __restrict__ slc,
+                 const int2* __restrict__ lec, int32_t* lam0, int32_t* lam1, int32_t* lam2,
                  int32_t shift, long long max_sweeps, GdpCtl* ctl, long long* trace_b2,
-                 unsigned long long* trace_ch, long long trace_cap, long long budget, int32_t maxE,
+                 unsigned long long* trace_ch, long long trace_cap, long long budget, int32_t maxS,
                  int32_t maxO, int32_t maxH) {
   extern __shared__ __align__(16) unsigned char smem[];
-  int2* s_lec = reinterpret_cast<int2*>(smem);
-  int* s_rp = reinterpret_cast<int*>(s_lec + maxE);
-  int* s_lamA = s_rp + maxO + 1;
-  int* s_lamB = s_lamA + maxO;
-  int* s_hl = s_lamB + maxO;
-  int* s_hid = s_hl + maxH;
+  const int maxSl = (maxO + 31) / 32;
+  int2* s_lec = reinterpret_cast<int2*>(smem);            // sliced {local index, cost * 2^F}
+  int2* s_slc = s_lec + maxS;                              // {offset, depth} per slice
+  int* s_order = reinterpret_cast<int*>(s_slc + maxSl);    // node of each slot
+  int* s_bufA = s_order + maxO;                            // [own lambda | halo lambda | 0]
+  int* s_bufB = s_bufA + maxO + maxH + 1;
+  int* s_hid = s_bufB + maxO + maxH + 1;                   // halo node ids
   __shared__ long long s_b2[32];
   __shared__ unsigned s_ch[32];
   __shared__ int s_ovf[32];
@@ -219,99 +308,106 @@ gdp_tiled_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ lec,
 
   const int tid = threadIdx.x, T = blockDim.x, b = blockIdx.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = T >> 5;
-  const int sub = lane & (G - 1);
-  const unsigned gmask = (G >= 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
-  const int ngroups = T / G, grp = tid / G;
   const long long div = 1LL << shift;
 
   const int lo = part[b], hi = part[b + 1], own = hi - lo;
-  const int E0 = irp[lo], ents = irp[hi] - E0;
   const int hb = hoff[b], H = hoff[b + 1] - hb;
-  for (int e = tid; e < ents; e += T) s_lec[e] = lec[E0 + e];
-  for (int i = tid; i <= own; i += T) s_rp[i] = irp[lo + i] - E0;
+  const int S0 = soff[b], S = soff[b + 1] - S0;
+  const int nsl = (own + 31) / 32;
+  for (int e = tid; e < S; e += T) s_lec[e] = lec[S0 + e];
+  for (int s = tid; s < nsl; s += T) s_slc[s] = slc[lo + s];
+  for (int p = tid; p < own; p += T) s_order[p] = order[lo + p];
   for (int h = tid; h < H; h += T) s_hid[h] = halo[hb + h];
-  for (int i = tid; i < own; i += T) s_lamA[i] = lam0[lo + i];
+  for (int i = tid; i < own; i += T) s_bufA[i] = lam0[lo + i];
+  if (tid == 0) {
+    s_bufA[own + H] = 0;  // the zero slot padded entries point at
+    s_bufB[own + H] = 0;
+  }
   __syncthreads();
 
   volatile GdpCtl* vc = ctl;
+  // Sweep t reads lambda from buffer t % 3 and publishes into (t + 1) % 3.
+  // Its totals go to slot t % 4 after the block has arrived at barrier t, so
+  // they are complete once barrier t + 1 has passed: sweep t + 2 reads them and
+  // applies the stop test after its own work (that sweep and the one before
+  // are then discarded: the first publishes nothing, the second published
+  // values equal to its input at a fixed point and never overwrote the input
+  // of an overflowing sweep, which lives in a third buffer).
   long long t = 0;
+  bool natural_end = true;
   for (; t < max_sweeps; ++t) {
-    const int* s_in = (t & 1) ? s_lamB : s_lamA;
-    int* s_out = (t & 1) ? s_lamA : s_lamB;
-    const int32_t* lin = (t & 1) ? lam1 : lam0;
-    int32_t* lout = (t & 1) ? lam0 : lam1;
-    // the previous sweep's totals, complete since the last barrier; used after this sweep
+    int* s_in = (t & 1) ? s_bufB : s_bufA;   // own part holds lambda of sweep t
+    int* s_out = (t & 1) ? s_bufA : s_bufB;
+    const int r3 = (int)(t % 3);
+    const int32_t* lin = r3 == 0 ? lam0 : (r3 == 1 ? lam1 : lam2);
+    int32_t* lout = r3 == 0 ? lam1 : (r3 == 1 ? lam2 : lam0);
     unsigned long long pch = 1;
-    int pst = 0;
+    int povf = 0;
     long long pb2 = 0;
-    if (tid == 0 && t > 0) {
-      const int s = (int)((t - 1) % 3);
-      pch = vc->slot_ch[s];
-      pst = vc->status;
-      pb2 = vc->slot_b2[s];
+    if (tid == 0 && t >= 2) {
+      const int s = (int)((t - 2) % 4);
+      pch = vc->q_ch[s];
+      povf = vc->q_ovf[s];
+      pb2 = vc->q_b2[s];
     }
-    for (int h = tid; h < H; h += T) s_hl[h] = ld_cg(lin + s_hid[h]);
+    for (int h = tid; h < H; h += T) s_in[own + h] = ld_cg(lin + s_hid[h]);
     __syncthreads();
 
     long long b2 = 0;
     unsigned ch = 0;
     int ovf = 0;
-    for (int vl = grp; vl < own; vl += ngroups) {
+    for (int p = tid; p < own; p += T) {
+      const int2 sl = s_slc[p >> 5];
+      const int vl = s_order[p];
       const int lv = s_in[vl];
-      const int beg = s_rp[vl], end = s_rp[vl + 1];
+      const int2* ent = s_lec + sl.x + (p & 31);
       int a = INT_MAX, bb = INT_MAX, c = INT_MAX;
-      for (int e = beg + sub; e < end; e += G) {
-        const int2 q = s_lec[e];
-        const int lu = q.x < own ? s_in[q.x] : s_hl[q.x - own];
-        const int z = (q.y << F) - lv - lu;  // Eq. 9
-        b2 += min(z, 0);
-        top3_insert(z, a, bb, c);
+      long long neg = 0;
+      for (int k = 0; k < sl.y; ++k) {
+        const int2 q = ent[k * 32];
+        const int z = q.y - lv - s_in[q.x];  // Eq. 9
+        neg += min(z, 0);
+        top3_insert_minmax(z, a, bb, c);
       }
-      if (G > 1) {
-#pragma unroll
-        for (int o = 1; o < G; o <<= 1) {
-          const int pa = __shfl_xor_sync(gmask, a, o);
-          const int pb = __shfl_xor_sync(gmask, bb, o);
-          const int pc = __shfl_xor_sync(gmask, c, o);
-          top3_insert(pa, a, bb, c);
-          top3_insert(pb, a, bb, c);
-          top3_insert(pc, a, bb, c);
-        }
-      }
-      if (sub == 0) {
-        const long long d = ((long long)bb + (long long)c) / div;  // Eq. 10, truncated toward 0
-        const long long nl = (long long)lv + d;
-        ovf |= (nl >= kLamLimit || nl <= -kLamLimit);
-        s_out[vl] = (int32_t)nl;
-        ch += (d != 0);
-        b2 += 4LL * lv;
-      }
+      const long long d = ((long long)bb + (long long)c) / div;  // Eq. 10, truncated toward 0
+      const long long nl = (long long)lv + d;
+      ovf |= (nl >= kLamLimit || nl <= -kLamLimit);
+      s_out[vl] = (int32_t)nl;
+      ch += (d != 0);
+      b2 += neg + 4LL * lv;
     }
-    // decide about sweep t-1 now that this sweep's work has hidden the read
+    // stop test for sweep t-2
     if (tid == 0) {
       int stop = 0;
-      if (t > 0) {
-        stop = (pst != 0) || (pch == 0);
+      if (t >= 2) {
+        stop = povf || (pch == 0);
         if (b == 0) {
-          if (t - 1 < trace_cap) {
-            trace_b2[t - 1] = pb2;
-            trace_ch[t - 1] = pch;
+          if (t - 2 < trace_cap) {
+            trace_b2[t - 2] = pb2;
+            trace_ch[t - 2] = pch;
           }
-          const int r = (int)((t + 1) % 3);  // last read during sweep t-1
-          vc->slot_b2[r] = 0;
-          vc->slot_ch[r] = 0;
           if (stop) {
-            vc->sweeps = t;
-            vc->fixed_point = (pch == 0) && (pst == 0);
+            vc->sweeps = t - 1;
+            vc->fixed_point = (pch == 0) && !povf;
+            if (povf) atomicOr(&ctl->status, kGdpOverflow);
           }
         }
+      }
+      if (b == 0) {  // slot (t+1) % 4 was last read during sweep t-1; next written in sweep t+1
+        const int r = (int)((t + 1) % 4);
+        vc->q_b2[r] = 0;
+        vc->q_ch[r] = 0;
+        vc->q_ovf[r] = 0;
       }
       s_stop = stop;
     }
     __syncthreads();
-    if (s_stop) break;  // sweep t is discarded: nothing published
+    if (s_stop) { natural_end = false; break; }  // sweep t is discarded: nothing published
     for (int i = tid; i < own; i += T) lout[lo + i] = s_out[i];
+    __syncthreads();
+    if (tid == 0) grid_arrive_counted(&ctl->bar_count);
 
+    // totals of sweep t, while the other blocks arrive
     b2 = warp_sum_ll(b2);
     ch = warp_sum_u(ch);
     ovf = __any_sync(0xffffffffu, ovf);
@@ -325,28 +421,50 @@ gdp_tiled_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ lec,
       y = warp_sum_u(y);
       o = __any_sync(0xffffffffu, o);
       if (lane == 0) {
-        const int s = (int)(t % 3);
-        atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->slot_b2[s]), (unsigned long long)x);
-        if (y) atomicAdd(&ctl->slot_ch[s], (unsigned long long)y);
-        if (o) atomicOr(&ctl->status, kGdpOverflow);
+        const int s = (int)(t % 4);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->q_b2[s]), (unsigned long long)x);
+        if (y) atomicAdd(&ctl->q_ch[s], (unsigned long long)y);
+        if (o) atomicOr(&ctl->q_ovf[s], 1);
+        if (!grid_wait_counted(&ctl->bar_count, (unsigned)(t + 1) * gridDim.x, budget)) {
+          atomicOr(&ctl->status, kGdpTimeout);
+          s_stop = 1;
+        } else {
+          s_stop = 0;
+        }
       }
     }
-    if (!grid_barrier_counted(&ctl->bar_count, (unsigned)(t + 1) * gridDim.x, budget)) {
-      if (tid == 0) atomicOr(&ctl->status, kGdpTimeout);
-      break;
-    }
+    __syncthreads();
+    if (s_stop) { natural_end = false; break; }
   }
-  if (t == max_sweeps && b == 0 && tid == 0) {  // ran to the cap: settle the last sweep
-    if (t > 0) {
-      const int s = (int)((t - 1) % 3);
-      const unsigned long long pch = vc->slot_ch[s];
-      if (t - 1 < trace_cap) {
-        trace_b2[t - 1] = vc->slot_b2[s];
-        trace_ch[t - 1] = pch;
+  if (natural_end) {
+    // ran to the cap: one more barrier so the last sweep's totals are complete
+    __syncthreads();
+    if (tid == 0) grid_arrive_counted(&ctl->bar_count);
+    if (tid == 0 && b == 0) {
+      const bool ok = grid_wait_counted(&ctl->bar_count, (unsigned)(t + 1) * gridDim.x, budget);
+      if (!ok) {
+        atomicOr(&ctl->status, kGdpTimeout);
+      } else {
+        long long done = t;  // sweeps counted so far
+        for (long long u = (t >= 2 ? t - 2 : 0); u < t; ++u) {
+          const int s = (int)(u % 4);
+          const unsigned long long chu = vc->q_ch[s];
+          const int ovu = vc->q_ovf[s];
+          if (u < trace_cap) {
+            trace_b2[u] = vc->q_b2[s];
+            trace_ch[u] = chu;
+          }
+          if (ovu || chu == 0) {
+            done = u + 1;
+            vc->fixed_point = (chu == 0) && !ovu;
+            if (ovu) atomicOr(&ctl->status, kGdpOverflow);
+            break;
+          }
+          vc->fixed_point = 0;
+        }
+        vc->sweeps = done;
       }
-      vc->fixed_point = (pch == 0) && (vc->status == 0);
     }
-    vc->sweeps = t;
   }
 }
 
@@ -368,7 +486,8 @@ static cudaError_t grow(T** p, int64_t* cap, int64_t need) {
 
 void plan_free(GdpPlan& p) {
   void* ptrs[] = {p.perm, p.inv, p.irp, p.iec, p.lec, p.part, p.hoff, p.hcount, p.halo, p.tmp,
-                  p.stats, p.ilam[0], p.ilam[1], p.keys, p.keys2, p.idx, p.sort_tmp, p.scan_tmp};
+                  p.stats, p.ilam[0], p.ilam[1], p.ilam[2], p.keys, p.keys2, p.idx, p.sort_tmp,
+                  p.scan_tmp, p.scount, p.soff, p.order, p.slc};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   p = GdpPlan();
@@ -417,15 +536,15 @@ cudaError_t scatter_perm(const int32_t* src, const int32_t* perm, int32_t n, int
 }
 
 cudaError_t plan_build(const int32_t* rp, const int2* ec, int32_t n, int64_t nnz, int num_sms,
-                       bool tiles, GdpPlan& p, cudaStream_t st) {
+                       bool tiles, int32_t F, int32_t ctas_per_sm, GdpPlan& p, cudaStream_t st) {
   p.valid = false;
   p.version += 1;
   PCK(grow(&p.irp, &p.irp_cap, (int64_t)n + 1));
   PCK(grow(&p.iec, &p.iec_cap, nnz));
-  PCK(grow(&p.lec, &p.lec_cap, nnz));
   PCK(grow(&p.tmp, &p.tmp_cap, nnz));
   PCK(grow(&p.ilam[0], &p.ilam_cap[0], n));
   PCK(grow(&p.ilam[1], &p.ilam_cap[1], n));
+  PCK(grow(&p.ilam[2], &p.ilam_cap[2], n));
   PCK(grow(&p.scan_tmp, &p.scan_cap, (int64_t)scan_scratch_ints(n) + 1));
   // internal CSR: rows in renumbered order, columns renumbered
   int32_t* ideg = p.ilam[1];  // free until the phase starts
@@ -444,11 +563,22 @@ cudaError_t plan_build(const int32_t* rp, const int2* ec, int32_t n, int64_t nnz
   PCK(cudaGetDevice(&dev));
   PCK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   PCK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    const int per_sm = attempt == 0 ? 2 : 1;
-    const int threads = attempt == 0 ? 512 : 1024;
-    int B = num_sms * per_sm;
-    if ((int64_t)B > (int64_t)n / 8) B = (int)((int64_t)n / 8 > 1 ? (int64_t)n / 8 : 1);
+  // Candidate shapes, tried in order: the whole graph in one CTA when it fits
+  // (n up to ~1.5k), then 1 CTA x 1024 threads per SM, then 2 CTAs x 512
+  // threads per SM (ctas_per_sm forces one of the last two).
+  const int64_t one_cta = 8LL * nnz + 4LL * (n + 1) + 8LL * n + 1024;
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    int per_sm, threads, B;
+    if (attempt == 0) {
+      if (ctas_per_sm != 0 || one_cta > smem_optin - 4096) continue;
+      per_sm = 1; threads = 1024; B = 1;
+    } else {
+      per_sm = attempt == 1 ? 1 : 2;  // one CTA per SM synchronises slightly faster
+      threads = attempt == 1 ? 1024 : 512;
+      if (ctas_per_sm != 0 && ctas_per_sm != per_sm) continue;
+      B = num_sms * per_sm;
+      if ((int64_t)B > (int64_t)n / 8) B = (int)((int64_t)n / 8 > 1 ? (int64_t)n / 8 : 1);
+    }
     int64_t cap = 0;
     if (p.part) cudaFree(p.part);
     p.part = nullptr;
@@ -456,6 +586,12 @@ cudaError_t plan_build(const int32_t* rp, const int2* ec, int32_t n, int64_t nnz
     if (p.hcount) cudaFree(p.hcount);
     p.hcount = nullptr;
     PCK(grow(&p.hcount, &cap, B + 1)); cap = 0;
+    if (p.scount) cudaFree(p.scount);
+    p.scount = nullptr;
+    PCK(grow(&p.scount, &cap, B + 1)); cap = 0;
+    if (p.soff) cudaFree(p.soff);
+    p.soff = nullptr;
+    PCK(grow(&p.soff, &cap, B + 1)); cap = 0;
     if (p.hoff) cudaFree(p.hoff);
     p.hoff = nullptr;
     PCK(grow(&p.hoff, &cap, B + 1));
@@ -469,27 +605,38 @@ cudaError_t plan_build(const int32_t* rp, const int2* ec, int32_t n, int64_t nnz
     PCK(cudaGetLastError());
     const size_t sort_smem = kPlanSortCap * sizeof(int32_t);
     PCK(cudaFuncSetAttribute(plan_halo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem));
-    plan_halo_kernel<<<B, 512, sort_smem, st>>>(p.irp, p.iec, p.part, kPlanSortCap, p.tmp, p.hcount, p.stats);
+    plan_halo_kernel<<<B, 512, sort_smem, st>>>(p.irp, p.iec, p.part, kPlanSortCap, p.tmp, p.hcount,
+                                                p.scount, p.stats);
     count_launch();
     PCK(cudaGetLastError());
     int32_t stats[4];
     PCK(cudaMemcpyAsync(stats, p.stats, sizeof(stats), cudaMemcpyDeviceToHost, st));
     PCK(cudaStreamSynchronize(st));
     if (stats[3]) return cudaSuccess;  // too many outside references: streaming kernel
-    const int64_t smem = 8LL * stats[1] + 4LL * (stats[0] + 1) + 8LL * stats[0] + 8LL * stats[2];
+    const int64_t maxSl = (stats[0] + 31) / 32;
+    const int64_t smem = 8LL * stats[1] + 8LL * maxSl + 4LL * stats[0] +
+                         8LL * (stats[0] + stats[2] + 1) + 4LL * stats[2];
     if (smem > smem_optin || smem * per_sm > smem_sm - 2048 * per_sm) continue;
     PCK(launch_scan(p.hcount, p.hoff, B, p.scan_tmp, st));
-    int32_t htot = 0;
-    PCK(cudaMemcpyAsync(&htot, p.hoff + B, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    PCK(launch_scan(p.scount, p.soff, B, p.scan_tmp, st));
+    int32_t tot[2] = {0, 0};
+    PCK(cudaMemcpyAsync(&tot[0], p.hoff + B, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    PCK(cudaMemcpyAsync(&tot[1], p.soff + B, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     PCK(cudaStreamSynchronize(st));
+    const int32_t htot = tot[0];
     PCK(grow(&p.halo, &p.halo_cap, htot > 0 ? htot : 1));
-    plan_map_kernel<<<B, 512, 0, st>>>(p.irp, p.iec, p.part, p.tmp, p.hoff, p.halo, p.lec);
+    PCK(grow(&p.lec, &p.lec_cap, tot[1] > 0 ? tot[1] : 1));
+    PCK(grow(&p.order, &p.order_cap, n));
+    PCK(grow(&p.slc, &p.slc_cap, n));
+    PCK(cudaFuncSetAttribute(plan_map_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem));
+    plan_map_kernel<<<B, 512, sort_smem, st>>>(p.irp, p.iec, p.part, p.tmp, p.hoff, p.soff, F, p.halo,
+                                               p.order, p.slc, p.lec);
     count_launch();
     PCK(cudaGetLastError());
     p.B = B;
     p.threads = threads;
     p.maxO = stats[0];
-    p.maxE = stats[1];
+    p.maxS = stats[1];
     p.maxH = stats[2];
     p.smem = (size_t)smem;
     p.halo_total = htot;
@@ -499,13 +646,13 @@ cudaError_t plan_build(const int32_t* rp, const int2* ec, int32_t n, int64_t nnz
   return cudaSuccess;  // does not fit: streaming kernel
 }
 
-template <int G>
-static cudaError_t launch_tiled_g(GdpPlan& p, int32_t F, int32_t shift, int64_t max_sweeps,
-                                  GdpCtl* ctl, long long* trace_b2, unsigned long long* trace_ch,
-                                  int64_t trace_cap, long long budget, cudaStream_t st) {
-  PCK(cudaFuncSetAttribute(gdp_tiled_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
+cudaError_t launch_gdp_tiled(GdpPlan& p, const int32_t* lam_in, int32_t shift, int64_t max_sweeps,
+                             GdpCtl* ctl, long long* trace_b2, unsigned long long* trace_ch,
+                             int64_t trace_cap, long long budget, cudaStream_t st) {
+  PCK(gather_perm(lam_in, p.perm, p.n, p.ilam[0], st));
+  PCK(cudaFuncSetAttribute(gdp_tiled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
   int per_sm = 0;
-  PCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gdp_tiled_kernel<G>, p.threads, p.smem));
+  PCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gdp_tiled_kernel, p.threads, p.smem));
   int dev = 0, sms = 0;
   PCK(cudaGetDevice(&dev));
   PCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -513,22 +660,15 @@ static cudaError_t launch_tiled_g(GdpPlan& p, int32_t F, int32_t shift, int64_t 
   long long ms = max_sweeps, tc = trace_cap;
   int32_t* l0 = p.ilam[0];
   int32_t* l1 = p.ilam[1];
-  void* args[] = {(void*)&p.irp, (void*)&p.lec, (void*)&p.part, (void*)&p.hoff, (void*)&p.halo,
-                  (void*)&l0, (void*)&l1, (void*)&F, (void*)&shift, (void*)&ms, (void*)&ctl,
-                  (void*)&trace_b2, (void*)&trace_ch, (void*)&tc, (void*)&budget, (void*)&p.maxE,
-                  (void*)&p.maxO, (void*)&p.maxH};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)gdp_tiled_kernel<G>, dim3(p.B),
+  int32_t* l2 = p.ilam[2];
+  void* args[] = {(void*)&p.part, (void*)&p.hoff, (void*)&p.soff, (void*)&p.halo, (void*)&p.order,
+                  (void*)&p.slc, (void*)&p.lec, (void*)&l0, (void*)&l1, (void*)&l2, (void*)&shift,
+                  (void*)&ms, (void*)&ctl, (void*)&trace_b2, (void*)&trace_ch, (void*)&tc,
+                  (void*)&budget, (void*)&p.maxS, (void*)&p.maxO, (void*)&p.maxH};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)gdp_tiled_kernel, dim3(p.B),
                                               dim3(p.threads), args, p.smem, st);
   count_launch();
   return e;
-}
-
-cudaError_t launch_gdp_tiled(GdpPlan& p, const int32_t* lam_in, int32_t F, int32_t shift,
-                             int64_t max_sweeps, GdpCtl* ctl, long long* trace_b2,
-                             unsigned long long* trace_ch, int64_t trace_cap, long long budget,
-                             cudaStream_t st) {
-  PCK(gather_perm(lam_in, p.perm, p.n, p.ilam[0], st));
-  return launch_tiled_g<4>(p, F, shift, max_sweeps, ctl, trace_b2, trace_ch, trace_cap, budget, st);
 }
 
 cudaError_t plan_scatter_lambda(const GdpPlan& p, int which, int32_t* lam_out, cudaStream_t st) {
