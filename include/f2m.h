@@ -78,7 +78,7 @@ typedef struct {
   uint32_t flags;               /* F2M_FLAG_* bits; default 0 */
   int32_t gdp_lanes;            /* lanes per node in the tiled GDP kernel: 1 (one thread per node); 0 = auto */
   int32_t gdp_ctas_per_sm;      /* tiled GDP CTAs per SM: 1 (x1024 threads), 2 (x512); 0 = auto
-                                   (auto also allows a single CTA when the graph fits one) */
+                                   */
 } f2m_params;
 
 /* f2m_params.flags: run GDP with the streaming kernel (CSR read from global

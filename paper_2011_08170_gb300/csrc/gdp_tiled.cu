@@ -563,22 +563,15 @@ cudaError_t plan_build(const int32_t* rp, const int2* ec, int32_t n, int64_t nnz
   PCK(cudaGetDevice(&dev));
   PCK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   PCK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-  // Candidate shapes, tried in order: the whole graph in one CTA when it fits
-  // (n up to ~1.5k), then 1 CTA x 1024 threads per SM, then 2 CTAs x 512
-  // threads per SM (ctas_per_sm forces one of the last two).
-  const int64_t one_cta = 8LL * nnz + 4LL * (n + 1) + 8LL * n + 1024;
-  for (int attempt = 0; attempt < 3; ++attempt) {
-    int per_sm, threads, B;
-    if (attempt == 0) {
-      if (ctas_per_sm != 0 || one_cta > smem_optin - 4096) continue;
-      per_sm = 1; threads = 1024; B = 1;
-    } else {
-      per_sm = attempt == 1 ? 1 : 2;  // one CTA per SM synchronises slightly faster
-      threads = attempt == 1 ? 1024 : 512;
-      if (ctas_per_sm != 0 && ctas_per_sm != per_sm) continue;
-      B = num_sms * per_sm;
-      if ((int64_t)B > (int64_t)n / 8) B = (int)((int64_t)n / 8 > 1 ? (int64_t)n / 8 : 1);
-    }
+  // Candidate shapes, tried in order: 1 CTA x 1024 threads per SM, then 2 CTAs
+  // x 512 threads per SM (ctas_per_sm forces one).  Small graphs use fewer
+  // CTAs (at least 8 nodes each).
+  for (int attempt = 1; attempt < 3; ++attempt) {
+    const int per_sm = attempt == 1 ? 1 : 2;
+    const int threads = attempt == 1 ? 1024 : 512;
+    if (ctas_per_sm != 0 && ctas_per_sm != per_sm) continue;
+    int B = num_sms * per_sm;
+    if ((int64_t)B > (int64_t)n / 8) B = (int)((int64_t)n / 8 > 1 ? (int64_t)n / 8 : 1);
     int64_t cap = 0;
     if (p.part) cudaFree(p.part);
     p.part = nullptr;
