@@ -33,7 +33,21 @@ WORKLOADS = {
     "c1": dict(kind="uniform", n=1000, k=10, seed=0),
     "c2": dict(kind="uniform", n=100_000, k=10, seed=0),
     "c3": dict(kind="mixture", n=200_000, k=12, seed=0),
+    "c4": dict(kind="batch", n=0, k=10, seed=0, count=256, nmin=1000, nmax=20000),
 }
+
+
+def batch_specs(w, rank=0):
+    """Instance i: seed i (+ 1000 * rank), n = round(exp(U[ln nmin, ln nmax])) from a
+    SplitMix64 draw of seed 0, uniform if i is even, clustered if odd."""
+    import instances as I
+    key = I.stream_key(w["seed"] + 1000 * rank, 77)
+    u = I.draws(key, 0, w["count"]) >> np.uint64(11)
+    frac = u.astype(np.float64) * (2.0 ** -53)
+    lo, hi = np.log(w["nmin"]), np.log(w["nmax"])
+    ns = np.floor(np.exp(lo + frac * (hi - lo)) + 0.5).astype(int)
+    return [("uniform" if i % 2 == 0 else "mixture", int(ns[i]), i + 1000 * rank, w["k"])
+            for i in range(w["count"])]
 METRIC = "ms to certified F2M optimum"
 GDP_BYTES_PER_ENTRY = 8   # {col, cost} streamed per directed entry
 GDP_BYTES_PER_NODE = 12   # row_ptr + lambda read + lambda write
@@ -41,6 +55,10 @@ PRICING_OPS_PER_PAIR = 7  # 2 FADD (dx, dy), FADD (t), FMUL (t^2), 2 FFMA, FSETP
 
 
 def workload_name(w):
+    if w["kind"] == "batch":
+        return (f"batch of {w['count']} instances, n log-uniform in [{w['nmin']}, {w['nmax']}], "
+                f"uniform/clustered alternating, k={w['k']}, int32 rounded-Euclidean costs, "
+                f"full O(n^2) pricing per instance, all certified")
     return (f"{w['kind']} n={w['n']} k={w['k']} seed={w['seed']}, int32 rounded-Euclidean costs, "
             f"full O(n^2) pricing, certified")
 
@@ -198,6 +216,8 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, w, rank)
+    if w["kind"] == "batch":
+        return run_batch(args, w, rank, world, local)
 
     import torch
     import instances as I
@@ -332,6 +352,117 @@ def main():
                                               "ms_finish": line["breakdown_ms"]["ms_finish"]})
         line["cpu_baseline"] = {"value": est, "unit": "ms", "cores": 1, "kind": "oracle",
                                 "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_batch(args, w, rank, world, local):
+    """Batch workload: one step = f2m_solve_batch over all instances, from lambda = 0."""
+    import torch
+    import instances as I
+    import paper_2011_08170_gb300 as f2m
+    from paper_2011_08170_gb300 import build as B
+
+    B.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    specs = batch_specs(w, rank)
+    ds = [I.make_instance(*sp) for sp in specs]
+    insts = [(d["xy"], d["row_ptr"], d["col"]) for d in ds]
+    ns = np.array([d["xy"].shape[0] for d in ds])
+    nnzs = np.array([int(d["row_ptr"][-1]) for d in ds])
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        b = f2m.f2m_create_batch(insts, stream=stream)
+        f2m.f2m_solve_batch(b)
+        f2m.f2m_destroy_batch(b)
+    bs = [f2m.f2m_create_batch(insts, stream=stream) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = f2m.f2m_kernel_launches()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    res = []
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        evs[i][0].record(stream)
+        res.append(f2m.f2m_solve_batch(bs[i]))
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    launches = f2m.f2m_kernel_launches() - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    for b in bs:
+        f2m.f2m_destroy_batch(b)
+    ms = sum(step_ms) / len(step_ms)
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    infos, tot = res[0]
+    assert tot.status == 0 and tot.certified == 2, tot.as_dict()
+    # end to end: create from host arrays, solve, read every instance back
+    e2e_ms = []
+    h2d = sum(x.nbytes + r.nbytes + c.nbytes for x, r, c in insts)
+    d2h = 0
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b = f2m.f2m_create_batch(insts, stream=stream)
+        f2m.f2m_solve_batch(b)
+        d2h = 0
+        for j in range(len(insts)):
+            lam, _ = f2m.f2m_batch_get_lambda(b, j)
+            rp, col, x2 = f2m.f2m_batch_get_x(b, j)
+            d2h += lam.nbytes + rp.nbytes + col.nbytes + x2.nbytes
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        f2m.f2m_destroy_batch(b)
+    e2e = statistics.median(e2e_ms)
+    peaks = load_peaks()
+    sweeps = np.array([i.iterations for i in infos])
+    gdp_bytes = float(np.sum(sweeps * (GDP_BYTES_PER_ENTRY * nnzs + GDP_BYTES_PER_NODE * ns)))
+    ms_gdp = statistics.median(r[1].ms_gdp for r in res)
+    ms_pr = statistics.median(r[1].ms_pricing for r in res)
+    gdp_gbs = gdp_bytes / (ms_gdp * 1e-3) / 1e9
+    pairs = float(sum(int(i.pricing_rounds) * n * (n - 1) / 2 for i, n in zip(infos, ns)))
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    num_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = num_sms * 128 * sm_mhz * 1e6 / 1e12
+    pr_tops = pairs * PRICING_OPS_PER_PAIR / (ms_pr * 1e-3) / 1e12 if ms_pr > 0 else 0.0
+    roofline = {"kernel": "gdp_batch_kernel", "bound": "hbm", "achieved": gdp_gbs,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gdp_gbs / peaks["hbm_gbs"],
+                "traffic": load_traffic(args.workload).get("gdp_batch_kernel"),
+                "peak_source": "MEASURED_PEAKS.json" if not peaks.get("_fallback") else "fallback",
+                "gdp_working_set_mb": float(np.sum(GDP_BYTES_PER_ENTRY * nnzs + GDP_BYTES_PER_NODE * ns)) / 1e6,
+                "pricing_tops": pr_tops, "pricing_frac_of_alu": pr_tops / alu_peak}
+    line = {"metric": METRIC + " (all instances of the batch)", "value": ms, "unit": "ms",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": workload_name(w), "instances": int(len(ns)), "sum_n": int(ns.sum()),
+                       "sum_nnz": int(nnzs.sum()), "l2": "working set larger than L2; flushed before every step",
+                       "parallelism": f"replicas x{world}"},
+            "breakdown_ms": {k: statistics.median(getattr(r[1], k) for r in res)
+                             for k in ("ms_gdp", "ms_pricing", "ms_merge", "ms_extract", "ms_finish", "ms_total")},
+            "solve": {"sweeps_total": int(sweeps.sum()), "sweeps_max": int(sweeps.max()),
+                      "phases": int(tot.phases), "pricing_scans": int(tot.pricing_rounds),
+                      "edges_added": int(tot.edges_added), "finisher_calls": int(tot.finisher_calls),
+                      "augmentations": int(tot.augmentations)},
+            "e2e": {"value": e2e, "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "roofline": roofline, "clocks": clk, "gpu_launches": int(launches)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -211,6 +211,42 @@ f2m_status f2m_gdp_noalloc(const int32_t* row_ptr, const int32_t* ec, int32_t n,
                            int32_t* lambda, int64_t* sweeps, int64_t* bound2, void* stream,
                            char* errbuf, int64_t errlen);
 
+/* ---- batched solves: many independent instances in one context --------------- */
+
+typedef struct f2m_batch f2m_batch;  /* opaque, library-owned */
+
+/* Creates a batch of `count` instances, solved together: every device step of
+ * f2m_solve_batch (one persistent GDP launch per phase, with instances that
+ * reached their fixed point frozen; one pricing scan over the pair tiles of the
+ * instances that need one; one merge; one extraction; one finisher call) covers
+ * all instances, and each instance's lambda, x and bound are those of its own
+ * f2m_solve (the instances are kept apart as contiguous node ranges).
+ *   n        [count] int32, HOST: nodes per instance, each >= 4, sum < 2^24.
+ *   xy       [sum n][2] int32, host or device: the points, instance after instance.
+ *   row_ptr  [sum (n_i + 1)] int32, host or device: each instance's own row_ptr
+ *            (local, starting at 0), back to back.
+ *   col      [sum nnz_i] int32, host or device: each instance's columns in its
+ *            own numbering, back to back.  Rules per instance as in f2m_create.
+ * Errors as f2m_create; the message is in f2m_last_error(NULL). */
+f2m_status f2m_create_batch(int32_t count, const int32_t* n, const int32_t* xy,
+                            const int32_t* row_ptr, const int32_t* col, const f2m_params* params,
+                            void* stream, f2m_batch** out);
+
+/* Solves every instance.  info: NULL or [count] (host) per-instance results
+ * (augmentations = -1: counted for the batch only); total: NULL or the batch
+ * totals (ms_* for the whole batch, iterations = sum of sweeps, frac_bits = -1).
+ * Returns OK when every instance is certified. */
+f2m_status f2m_solve_batch(f2m_batch* batch, f2m_info* info, f2m_info* total);
+
+/* Results of instance i after f2m_solve_batch: lambda [n_i] in units
+ * 2^-(*frac_bits); the instance's final candidate graph (local numbering) and
+ * x in half units, as f2m_get_x.  Pointers host or device. */
+f2m_status f2m_batch_get_lambda(f2m_batch* batch, int32_t i, int32_t* lambda, int32_t* frac_bits);
+f2m_status f2m_batch_get_x(f2m_batch* batch, int32_t i, int64_t* nnz_inout, int32_t* row_ptr,
+                           int32_t* col, uint8_t* x2);
+const char* f2m_batch_last_error(const f2m_batch* batch);
+void f2m_destroy_batch(f2m_batch* batch);
+
 /* ---- results ----------------------------------------------------------------- */
 
 /* lambda [n] int32 (host or device) in units 2^-(*frac_bits). */

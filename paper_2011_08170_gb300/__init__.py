@@ -36,7 +36,8 @@ F2M_FLAG_STREAMING_GDP = 1
 EXPORTS = ["f2m_default_params", "f2m_create", "f2m_destroy", "f2m_set_lambda", "f2m_solve",
            "f2m_gdp", "f2m_price", "f2m_add_edges", "f2m_extract", "f2m_get_lambda",
            "f2m_get_bound", "f2m_get_x", "f2m_status_string", "f2m_last_error",
-           "f2m_kernel_launches", "f2m_gdp_noalloc"]
+           "f2m_kernel_launches", "f2m_gdp_noalloc", "f2m_create_batch", "f2m_solve_batch",
+           "f2m_batch_get_lambda", "f2m_batch_get_x", "f2m_batch_last_error", "f2m_destroy_batch"]
 
 
 class f2m_params(C.Structure):
@@ -100,6 +101,18 @@ def load(path: str = LIB_PATH):
     L.f2m_gdp_noalloc.argtypes = [vp, vp, i32, i32, i32, i64, vp, C.POINTER(i64),
                                   C.POINTER(i64), vp, C.c_char_p, i64]
     L.f2m_gdp_noalloc.restype = C.c_int
+    L.f2m_create_batch.argtypes = [i32, vp, vp, vp, vp, C.POINTER(f2m_params), vp, C.POINTER(vp)]
+    L.f2m_create_batch.restype = C.c_int
+    L.f2m_solve_batch.argtypes = [vp, vp, C.POINTER(f2m_info)]
+    L.f2m_solve_batch.restype = C.c_int
+    L.f2m_batch_get_lambda.argtypes = [vp, i32, vp, C.POINTER(i32)]
+    L.f2m_batch_get_lambda.restype = C.c_int
+    L.f2m_batch_get_x.argtypes = [vp, i32, C.POINTER(i64), vp, vp, vp]
+    L.f2m_batch_get_x.restype = C.c_int
+    L.f2m_batch_last_error.argtypes = [vp]
+    L.f2m_batch_last_error.restype = C.c_char_p
+    L.f2m_destroy_batch.argtypes = [vp]
+    L.f2m_destroy_batch.restype = None
     L.f2m_kernel_launches.argtypes = []
     L.f2m_kernel_launches.restype = C.c_int64
     for name in ("f2m_create", "f2m_set_lambda", "f2m_solve", "f2m_gdp", "f2m_price",
@@ -346,3 +359,79 @@ def f2m_gdp_noalloc(row_ptr, ec, lam, max_sweeps: int, frac_bits: int = 8, dampi
                                 max_sweeps, lam.data_ptr(), C.byref(sw), C.byref(b2),
                                 _stream_handle(stream), buf, len(buf))
     return st, sw.value, b2.value, buf.value.decode()
+
+
+class Batch:
+    """Owns one f2m_batch*; destroyed with the object."""
+
+    def __init__(self, handle, ns):
+        self.handle = handle
+        self.ns = list(ns)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.f2m_destroy_batch(self.handle)
+            self.handle = None
+
+
+def _bcheck(b, st):
+    if st != F2M_OK:
+        L = load()
+        msg = L.f2m_batch_last_error(b.handle if isinstance(b, Batch) else None)
+        name = L.f2m_status_string(st).decode()
+        raise F2MError(st, f"{name}: {(msg or b'').decode()}")
+
+
+def f2m_create_batch(instances, params: f2m_params | None = None, stream=None) -> Batch:
+    """instances: list of (xy [n, 2], row_ptr [n + 1], col [nnz]) numpy arrays."""
+    L = load()
+    ns = np.array([len(rp) - 1 for _, rp, _ in instances], dtype=np.int32)
+    xy = np.ascontiguousarray(np.concatenate([np.asarray(x, np.int32).reshape(-1, 2) for x, _, _ in instances]))
+    rp = np.ascontiguousarray(np.concatenate([np.asarray(r, np.int32) for _, r, _ in instances]))
+    col = np.ascontiguousarray(np.concatenate([np.asarray(c, np.int32) for _, _, c in instances]))
+    h = C.c_void_p()
+    st = L.f2m_create_batch(len(ns), ns.ctypes.data, xy.ctypes.data, rp.ctypes.data, col.ctypes.data,
+                            C.byref(params) if params is not None else None, _stream_handle(stream),
+                            C.byref(h))
+    if st != F2M_OK:
+        raise F2MError(st, f"{L.f2m_status_string(st).decode()}: {L.f2m_last_error(None).decode()}")
+    return Batch(h.value, ns)
+
+
+def f2m_solve_batch(b: Batch, raise_on_error: bool = True):
+    """Returns (per-instance f2m_info list, batch total f2m_info)."""
+    infos = (f2m_info * len(b.ns))()
+    tot = f2m_info()
+    st = load().f2m_solve_batch(b.handle, infos, C.byref(tot))
+    if raise_on_error:
+        _bcheck(b, st)
+    return list(infos), tot
+
+
+def f2m_batch_get_lambda(b: Batch, i: int):
+    lam = np.zeros(b.ns[i], np.int32)
+    fb = C.c_int32()
+    _bcheck(b, load().f2m_batch_get_lambda(b.handle, i, lam.ctypes.data, C.byref(fb)))
+    return lam, fb.value
+
+
+def f2m_batch_get_x(b: Batch, i: int):
+    L = load()
+    nnz = C.c_int64(0)
+    _bcheck(b, L.f2m_batch_get_x(b.handle, i, C.byref(nnz), None, None, None))
+    rp = np.zeros(b.ns[i] + 1, np.int32)
+    col = np.zeros(max(nnz.value, 1), np.int32)
+    x2 = np.zeros(max(nnz.value, 1), np.uint8)
+    _bcheck(b, L.f2m_batch_get_x(b.handle, i, C.byref(nnz), rp.ctypes.data, col.ctypes.data, x2.ctypes.data))
+    return rp, col[:nnz.value], x2[:nnz.value]
+
+
+def f2m_batch_last_error(b: Batch | None = None) -> str:
+    r = load().f2m_batch_last_error(b.handle if b is not None else None)
+    return (r or b"").decode()
+
+
+def f2m_destroy_batch(b: Batch) -> None:
+    if b.handle:
+        load().f2m_destroy_batch(b.handle)
+        b.handle = None

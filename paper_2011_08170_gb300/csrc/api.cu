@@ -6,6 +6,7 @@
 // context's stream; the host reads back one small status block per step.  The
 // exception is the exact finisher (finisher.cpp), a min-cost flow that runs on
 // the host when the sign rule (7) leaves some node with a row sum other than 2.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <climits>
@@ -13,9 +14,11 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/f2m.h"
+#include "ctx_internal.h"
 #include "f2m_internal.h"
 
 using namespace f2m;
@@ -28,62 +31,7 @@ void count_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
 
 extern "C" int64_t f2m_kernel_launches(void) { return g_kernel_launches.load(); }
 
-struct f2m_ctx {
-  int32_t n = 0;
-  int64_t nnz = 0;
-  int64_t ec_cap = 0;
-  cudaStream_t st = nullptr;
-  f2m_params p{};
-  int num_sms = 0;
-  int2* d_xy = nullptr;
-  int32_t* d_rp = nullptr;
-  int2* d_ec = nullptr;
-  uint8_t* d_x2 = nullptr;
-  int32_t* d_lam[2] = {nullptr, nullptr};
-  int32_t* d_lam2 = nullptr;
-  int cur = 0;          // d_lam[cur] holds lambda in units 2^-F
-  int32_t fb_cur = 8;   // F, or F+1 while d_lam2 holds the current lambda
-  GdpCtl* d_gdp = nullptr;
-  long long* d_trace_b2 = nullptr;
-  unsigned long long* d_trace_ch = nullptr;
-  int64_t trace_cap = 0;
-  float4* d_pts = nullptr;
-  int2* d_pairs = nullptr;
-  int64_t pairs_cap = 0;
-  int64_t npairs = 0;   // pairs held in d_pairs after the last scan
-  unsigned long long* d_count = nullptr;
-  unsigned int* d_tile = nullptr;
-  int32_t* d_deg = nullptr;
-  int32_t* d_tmp_rp = nullptr;
-  int32_t* d_new_rp = nullptr;
-  int32_t* d_block_sums = nullptr;
-  int32_t* d_tmp_col = nullptr;
-  int64_t tmp_col_cap = 0;
-  int32_t* d_out_a = nullptr;  // split scratch for f2m_get_x
-  int32_t* d_out_b = nullptr;
-  int64_t out_cap = 0;
-  CheckCtl* d_check = nullptr;
-  long long* d_scalar = nullptr;
-  unsigned long long* d_bad = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  GdpPlan plan;         // renumbering and tiles of the shared-memory GDP kernel
-  // exact finisher: device scratch, pinned host mirrors, host work arrays
-  int32_t* d_twin = nullptr;
-  uint8_t* d_fy = nullptr;
-  uint8_t* d_fx = nullptr;
-  int64_t fin_cap = 0;          // entries the finisher buffers hold
-  int64_t fin_version = -1;     // plan version mirrored on the host
-  int32_t* h_irp = nullptr;
-  int2* h_iec = nullptr;
-  int32_t* h_twin = nullptr;
-  uint8_t* h_y = nullptr;
-  uint8_t* h_x = nullptr;
-  int32_t* h_exl = nullptr;
-  int32_t* h_lam = nullptr;
-  int32_t* h_lam2 = nullptr;
-  FinisherWork* fin_work = nullptr;
-  std::string err;
-};
+
 
 static void free_finisher_buffers(f2m_ctx* c) {
   if (c->d_twin) cudaFree(c->d_twin);
@@ -133,35 +81,20 @@ static cudaError_t alloc_finisher_buffers(f2m_ctx* c, int64_t cap) {
 
 static thread_local std::string g_create_error;
 
-static f2m_status fail(f2m_ctx* ctx, f2m_status s, const std::string& msg) {
+namespace f2m {
+
+f2m_status fail(f2m_ctx* ctx, f2m_status s, const std::string& msg) {
   if (ctx) ctx->err = msg; else g_create_error = msg;
   return s;
 }
 
-static f2m_status cuda_fail(f2m_ctx* ctx, cudaError_t e, const char* what) {
+f2m_status cuda_fail(f2m_ctx* ctx, cudaError_t e, const char* what) {
   std::string m = std::string(what) + ": " + cudaGetErrorString(e);
   if (e == cudaErrorMemoryAllocation) return fail(ctx, F2M_ERR_OOM, m);
   return fail(ctx, F2M_ERR_CUDA, m);
 }
 
-#define CK(ctx, call)                                          \
-  do {                                                         \
-    cudaError_t e_ = (call);                                   \
-    if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
-  } while (0)
-
-template <typename T>
-static cudaError_t dalloc(T** p, int64_t count) {
-  *p = nullptr;
-  size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
-  return cudaMalloc((void**)p, bytes);
-}
-
-template <typename T>
-static void dfree(T*& p) {
-  if (p) cudaFree((void*)p);
-  p = nullptr;
-}
+}  // namespace f2m
 
 static float elapsed_ms(f2m_ctx* c) {
   float ms = 0.f;
@@ -207,7 +140,8 @@ extern "C" const char* f2m_last_error(const f2m_ctx* ctx) {
 extern "C" void f2m_destroy(f2m_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
-  dfree(c->d_xy); dfree(c->d_rp); dfree(c->d_ec); dfree(c->d_x2);
+  dfree(c->d_xy); dfree(c->d_rp); dfree(c->d_ec); dfree(c->d_x2); dfree(c->d_tiles);
+  dfree(c->d_seg_off); dfree(c->d_fin_include);
   dfree(c->d_lam[0]); dfree(c->d_lam[1]); dfree(c->d_lam2); dfree(c->d_gdp);
   dfree(c->d_trace_b2); dfree(c->d_trace_ch); dfree(c->d_pts); dfree(c->d_pairs);
   dfree(c->d_count); dfree(c->d_tile); dfree(c->d_deg); dfree(c->d_tmp_rp); dfree(c->d_new_rp);
@@ -221,7 +155,7 @@ extern "C" void f2m_destroy(f2m_ctx* c) {
   delete c;
 }
 
-static f2m_status check_params(const f2m_params& p) {
+f2m_status f2m::check_params_internal(const f2m_params& p) {
   if (p.frac_bits < 1 || p.frac_bits > 8) return fail(nullptr, F2M_ERR_INVALID_ARG, "frac_bits must be in 1..8");
   if (p.damping_shift < 1 || p.damping_shift > 8) return fail(nullptr, F2M_ERR_INVALID_ARG, "damping_shift must be in 1..8");
   if (p.gdp_lanes != 0 && p.gdp_lanes != 1)
@@ -261,6 +195,12 @@ static cudaError_t read_check(f2m_ctx* c, CheckCtl* h) {
 extern "C" f2m_status f2m_create(const int32_t* xy, int32_t n, const int32_t* row_ptr,
                                  const int32_t* col, const f2m_params* params, void* stream,
                                  f2m_ctx** out) {
+  return create_internal(xy, n, row_ptr, col, params, stream, std::vector<int32_t>{0, n}, out);
+}
+
+f2m_status f2m::create_internal(const int32_t* xy, int32_t n, const int32_t* row_ptr,
+                                const int32_t* col, const f2m_params* params, void* stream,
+                                const std::vector<int32_t>& seg_off, f2m_ctx** out) {
   if (!out) return fail(nullptr, F2M_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   g_create_error.clear();
@@ -268,13 +208,14 @@ extern "C" f2m_status f2m_create(const int32_t* xy, int32_t n, const int32_t* ro
   if (n < 4 || n >= (1 << 24)) return fail(nullptr, F2M_ERR_INVALID_ARG, "n must be in [4, 2^24)");
   f2m_params p;
   if (params) p = *params; else f2m_default_params(&p);
-  if (check_params(p) != F2M_OK) return F2M_ERR_INVALID_ARG;
+  if (check_params_internal(p) != F2M_OK) return F2M_ERR_INVALID_ARG;
 
   f2m_ctx* c = new (std::nothrow) f2m_ctx();
   if (!c) return fail(nullptr, F2M_ERR_OOM, "host allocation");
   c->n = n;
   c->p = p;
   c->st = (cudaStream_t)stream;
+  c->seg_off = seg_off;
   c->fb_cur = p.frac_bits;
   f2m_status s = F2M_OK;
   int32_t* d_col = nullptr;
@@ -311,7 +252,7 @@ extern "C" f2m_status f2m_create(const int32_t* xy, int32_t n, const int32_t* ro
     c->ec_cap = c->nnz + (c->nnz >> 3) + 4096;
     e = dalloc(&c->d_ec, c->ec_cap);
     if (e == cudaSuccess) e = launch_build_ec(c->d_xy, c->d_rp, d_col, n, c->d_ec, c->st);
-    if (e == cudaSuccess) e = plan_renumber(c->d_xy, n, c->plan, c->st);
+    if (e == cudaSuccess) e = plan_renumber(c->d_xy, n, c->seg_off, c->plan, c->st);
     if (e == cudaSuccess)
       e = plan_build(c->d_rp, c->d_ec, n, c->nnz, c->num_sms, !(p.flags & F2M_FLAG_STREAMING_GDP),
                      p.frac_bits, p.gdp_ctas_per_sm, c->plan, c->st);
@@ -372,12 +313,12 @@ extern "C" f2m_status f2m_set_lambda(f2m_ctx* c, const int32_t* lambda, int32_t 
 }
 
 // lambda (device) and its fractional bits
-static const int32_t* cur_lambda(f2m_ctx* c, int32_t* fb) {
+const int32_t* f2m::cur_lambda(f2m_ctx* c, int32_t* fb) {
   *fb = c->fb_cur;
   return c->fb_cur == c->p.frac_bits ? c->d_lam[c->cur] : c->d_lam2;
 }
 
-static f2m_status gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, bool want_trace,
+f2m_status f2m::gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, bool want_trace,
                             int64_t trace_cap, double* ms) {
   const int32_t F = c->p.frac_bits;
   if (c->fb_cur != F) {  // continue from the finisher's lambda: floor to F bits
@@ -451,7 +392,23 @@ extern "C" f2m_status f2m_gdp(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, i
 }
 
 // pricing scan into d_pairs (grown until every pair fits); count in c->npairs
-static f2m_status price_internal(f2m_ctx* c, double* ms) {
+// Tile pairs of the pair triangle of every segment selected for this scan.
+static void build_tiles(const f2m_ctx* c, std::vector<int4>& tiles) {
+  tiles.clear();
+  const int32_t nseg = (int32_t)c->seg_off.size() - 1;
+  for (int32_t s = 0; s < nseg; ++s) {
+    if (!c->seg_scan.empty() && !c->seg_scan[s]) continue;
+    const int32_t a = c->seg_off[s], b = c->seg_off[s + 1];
+    for (int32_t i0 = a; i0 < b; i0 += kPricingTile)
+      for (int32_t j0 = i0; j0 < b; j0 += kPricingTile)
+        tiles.push_back(make_int4(i0, i0 + kPricingTile < b ? i0 + kPricingTile : b, j0,
+                                  j0 + kPricingTile < b ? j0 + kPricingTile : b));
+  }
+}
+
+// pricing scan into d_pairs (grown until every pair fits); count in c->npairs,
+// per-segment counts in c->seg_pairs
+f2m_status f2m::price_internal(f2m_ctx* c, double* ms) {
   if (!c->d_pts) {
     CK(c, dalloc(&c->d_pts, c->n));
     CK(c, dalloc(&c->d_count, 1));
@@ -461,23 +418,48 @@ static f2m_status price_internal(f2m_ctx* c, double* ms) {
     c->pairs_cap = c->p.pricing_cap;
     CK(c, dalloc(&c->d_pairs, c->pairs_cap));
   }
+  std::vector<int4> tiles;
+  build_tiles(c, tiles);
+  if ((int64_t)tiles.size() > c->tiles_cap) {
+    dfree(c->d_tiles);
+    c->tiles_cap = (int64_t)tiles.size() + 64;
+    CK(c, dalloc(&c->d_tiles, c->tiles_cap));
+  }
+  if (!tiles.empty())
+    CK(c, cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, c->st));
   int32_t fb = 0;
   const int32_t* lam = cur_lambda(c, &fb);
+  const int32_t nseg = (int32_t)c->seg_off.size() - 1;
   for (;;) {
     CK(c, cudaEventRecord(c->ev0, c->st));
-    CK(c, launch_pricing(c->d_xy, lam, c->d_rp, c->d_ec, c->n, fb, c->d_pts, c->d_pairs,
-                         c->pairs_cap, c->d_count, c->d_tile, c->num_sms, c->st));
+    CK(c, launch_pricing(c->d_xy, lam, c->d_rp, c->d_ec, c->n, fb, c->d_pts, c->d_tiles,
+                         (int32_t)tiles.size(), c->d_pairs, c->pairs_cap, c->d_count, c->d_tile,
+                         c->num_sms, c->st));
     CK(c, cudaEventRecord(c->ev1, c->st));
     unsigned long long cnt = 0;
     CK(c, cudaMemcpyAsync(&cnt, c->d_count, sizeof(cnt), cudaMemcpyDeviceToHost, c->st));
     CK(c, cudaStreamSynchronize(c->st));
     if (ms) *ms += elapsed_ms(c);
     c->npairs = (int64_t)cnt;
-    if ((int64_t)cnt <= c->pairs_cap) return F2M_OK;
+    if ((int64_t)cnt <= c->pairs_cap) break;
     dfree(c->d_pairs);
     c->pairs_cap = (int64_t)cnt + ((int64_t)cnt >> 2) + 1024;
     CK(c, dalloc(&c->d_pairs, c->pairs_cap));
   }
+  c->seg_pairs.assign(nseg, 0);
+  if (nseg == 1) {
+    c->seg_pairs[0] = c->npairs;
+  } else if (c->npairs > 0) {
+    std::vector<int2> h(c->npairs);
+    CK(c, cudaMemcpyAsync(h.data(), c->d_pairs, sizeof(int2) * c->npairs, cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    for (const int2& q : h) {
+      const int32_t s = (int32_t)(std::upper_bound(c->seg_off.begin(), c->seg_off.end(), q.x) -
+                                  c->seg_off.begin()) - 1;
+      c->seg_pairs[s] += 1;
+    }
+  }
+  return F2M_OK;
 }
 
 extern "C" f2m_status f2m_price(f2m_ctx* c, int64_t* count, int32_t* pairs, int64_t cap) {
@@ -493,7 +475,7 @@ extern "C" f2m_status f2m_price(f2m_ctx* c, int64_t* count, int32_t* pairs, int6
 }
 
 // CSR u pairs (device array of npairs int2)
-static f2m_status merge_internal(f2m_ctx* c, const int2* d_pairs, int64_t npairs, double* ms) {
+f2m_status f2m::merge_internal(f2m_ctx* c, const int2* d_pairs, int64_t npairs, double* ms) {
   const int32_t n = c->n;
   if (!c->d_deg) {
     CK(c, dalloc(&c->d_deg, n + 1));
@@ -549,7 +531,7 @@ extern "C" f2m_status f2m_add_edges(f2m_ctx* c, const int32_t* pairs, int64_t np
   return s;
 }
 
-static f2m_status extract_internal(f2m_ctx* c, int64_t* bad, double* ms) {
+f2m_status f2m::extract_internal(f2m_ctx* c, int64_t* bad, double* ms) {
   int32_t fb = 0;
   const int32_t* lam = cur_lambda(c, &fb);
   CK(c, cudaEventRecord(c->ev0, c->st));
@@ -574,7 +556,7 @@ extern "C" f2m_status f2m_extract(f2m_ctx* c, uint8_t* x2, int64_t* bad) {
   return F2M_OK;
 }
 
-static f2m_status bound_internal(f2m_ctx* c, int64_t* b2) {
+f2m_status f2m::bound_internal(f2m_ctx* c, int64_t* b2) {
   int32_t fb = 0;
   const int32_t* lam = cur_lambda(c, &fb);
   CK(c, launch_bound(c->d_rp, c->d_ec, lam, c->n, fb, c->d_scalar, c->st));
@@ -588,7 +570,7 @@ static f2m_status bound_internal(f2m_ctx* c, int64_t* b2) {
 // Exact finisher: device prep (twin arcs, initial flow, surpluses) on the
 // renumbered CSR, successive shortest paths on the host, results scattered back
 // to caller order on the device.
-static f2m_status finisher_internal(f2m_ctx* c, int64_t* aug) {
+f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug) {
   const int32_t n = c->n;
   const int32_t F = c->p.frac_bits;
   GdpPlan& P = c->plan;
@@ -604,6 +586,9 @@ static f2m_status finisher_internal(f2m_ctx* c, int64_t* aug) {
   int32_t* d_lam2_int = P.ilam[1];
   int32_t* d_exl = P.tmp;
   CK(c, fin_prepare(P, c->d_lam[c->cur], F, d_lam_int, c->d_fy, d_exl, c->st));
+  if (c->d_fin_include)
+    CK(c, launch_batch_mask_surplus(d_exl, c->d_seg_off, (int32_t)c->seg_off.size() - 1,
+                                    c->d_fin_include, n, c->st));
   CK(c, cudaMemcpyAsync(c->h_y, c->d_fy, c->nnz, cudaMemcpyDeviceToHost, c->st));
   CK(c, cudaMemcpyAsync(c->h_exl, d_exl, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->st));
   CK(c, cudaMemcpyAsync(c->h_lam, d_lam_int, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->st));
@@ -613,14 +598,18 @@ static f2m_status finisher_internal(f2m_ctx* c, int64_t* aug) {
       if (c->h_twin[e] < 0) return fail(c, F2M_ERR_INVALID_ARG, "finisher: CSR not symmetric");
     c->fin_version = P.version;
   }
+  static const int32_t hw = (int32_t)std::thread::hardware_concurrency();
+  const int32_t nseg = (int32_t)c->seg_off.size() - 1;
   const int r = host_finisher(n, c->h_irp, c->h_iec, c->h_twin, c->h_y, c->h_exl, c->h_lam, F,
-                              c->h_x, c->h_lam2, aug, c->fin_work);
+                              c->h_x, c->h_lam2, c->seg_off.data(), nseg, hw > 1 ? hw : 1, aug,
+                              c->fin_work);
   if (r == 7) return fail(c, F2M_ERR_INFEASIBLE, "no fractional 2-matching exists on the candidate graph");
   if (r == 5) return fail(c, F2M_ERR_OVERFLOW, "finisher lambda out of range");
   if (r != 0) return fail(c, F2M_ERR_INVALID_ARG, "finisher failed");
   CK(c, cudaMemcpyAsync(c->d_fx, c->h_x, c->nnz, cudaMemcpyHostToDevice, c->st));
   CK(c, cudaMemcpyAsync(d_lam2_int, c->h_lam2, sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->st));
-  CK(c, fin_scatter(P, c->d_rp, c->d_fx, d_lam2_int, c->d_x2, c->d_lam2, c->st));
+  CK(c, fin_scatter(P, c->d_rp, c->d_fx, d_lam2_int, c->d_x2, c->d_lam2, c->d_seg_off,
+                    (int32_t)c->seg_off.size() - 1, c->d_fin_include, c->st));
   CK(c, cudaStreamSynchronize(c->st));
   c->fb_cur = F + 1;
   return F2M_OK;

@@ -1,0 +1,547 @@
+// Batched solve: many independent F2M instances in one context.
+//
+// The instances become one disjoint union of segments (instance s = nodes
+// [seg_off[s], seg_off[s+1]) of the union).  Every device step of a solve
+// covers all instances at once -- one persistent GDP launch per phase
+// (gdp_batch_kernel, converged instances frozen), one pricing scan over the
+// tile pairs of the instances that need one, one merge, one extraction, one
+// finisher call -- and the host keeps, per instance, the state of the solve
+// loop of f2m_solve.  Since no step mixes instances, each instance's lambda,
+// x and bound are those of its own solve (the finisher is told which
+// instances it may touch).
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/f2m.h"
+#include "ctx_internal.h"
+#include "f2m_internal.h"
+
+using namespace f2m;
+
+struct f2m_batch {
+  f2m_ctx* u = nullptr;            // the union context
+  int32_t count = 0;
+  std::vector<int32_t> n;          // nodes per instance
+  // device scratch of the batch GDP phase
+  uint8_t* d_active = nullptr;
+  unsigned long long* d_seg_ch = nullptr;
+  long long* d_seg_sweeps = nullptr;
+  int4* d_tiles = nullptr;          // node tiles of the batch kernel
+  int32_t ntiles = 0;
+  int32_t grid = 0;
+  int64_t tiles_version = -1;
+  long long* d_seg_b2 = nullptr;
+  unsigned long long* d_seg_bad = nullptr;
+  int32_t* d_tmp_a = nullptr;       // output staging
+  int32_t* d_tmp_b = nullptr;
+  int64_t tmp_cap = 0;
+  uint8_t* d_mask = nullptr;        // per-segment mask for the masked steps
+  // results, snapshotted when an instance finishes (later steps for other
+  // instances move entries and rescale lambda)
+  int32_t* d_res_lam = nullptr;     // [N] lambda, units 2^-res_fb[s]
+  int32_t* d_res_rp = nullptr;      // [N + count] local row offsets per instance
+  int2* d_res_ec = nullptr;         // arena of {col (union id), cost}
+  uint8_t* d_res_x2 = nullptr;      // arena of x in half units
+  int64_t res_cap = 0, res_used = 0;
+  std::vector<int64_t> res_eoff, res_nnz, res_b2;
+  std::vector<int32_t> res_fb;
+  std::vector<uint8_t> res_done;
+};
+
+namespace {
+
+f2m_status bfail(f2m_batch* b, f2m_status s, const std::string& msg) {
+  return fail(b ? b->u : nullptr, s, msg);
+}
+
+}  // namespace
+
+extern "C" void f2m_destroy_batch(f2m_batch* b) {
+  if (!b) return;
+  if (b->u) {
+    cudaStreamSynchronize(b->u->st);
+    f2m_destroy(b->u);
+  }
+  dfree(b->d_active); dfree(b->d_seg_ch); dfree(b->d_seg_sweeps); dfree(b->d_tiles);
+  dfree(b->d_seg_b2); dfree(b->d_seg_bad); dfree(b->d_tmp_a); dfree(b->d_tmp_b);
+  dfree(b->d_mask); dfree(b->d_res_lam); dfree(b->d_res_rp); dfree(b->d_res_ec); dfree(b->d_res_x2);
+  delete b;
+}
+
+extern "C" f2m_status f2m_create_batch(int32_t count, const int32_t* n, const int32_t* xy,
+                                       const int32_t* row_ptr, const int32_t* col,
+                                       const f2m_params* params, void* stream, f2m_batch** out) {
+  if (!out) return fail(nullptr, F2M_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !n || !xy || !row_ptr || !col)
+    return fail(nullptr, F2M_ERR_INVALID_ARG, "count < 1 or NULL array");
+  std::vector<int32_t> seg_off(count + 1, 0);
+  for (int32_t s = 0; s < count; ++s) {
+    if (n[s] < 4) return fail(nullptr, F2M_ERR_INVALID_ARG, "instance " + std::to_string(s) + ": n < 4");
+    if ((int64_t)seg_off[s] + n[s] >= (1 << 24))
+      return fail(nullptr, F2M_ERR_INVALID_ARG, "total nodes must stay below 2^24");
+    seg_off[s + 1] = seg_off[s] + n[s];
+  }
+  const int32_t N = seg_off[count];
+  cudaStream_t st = (cudaStream_t)stream;
+  // per-instance entry counts: the last offset of each local row_ptr
+  std::vector<int32_t> eoff(count + 1, 0);
+  {
+    std::vector<int32_t> rp_all(N + count);
+    cudaError_t e = cudaMemcpyAsync(rp_all.data(), row_ptr, sizeof(int32_t) * (N + count),
+                                    cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "create_batch: read row_ptr");
+    for (int32_t s = 0; s < count; ++s) {
+      const int64_t nz = rp_all[seg_off[s + 1] + s];
+      if (nz < 0 || (int64_t)eoff[s] + nz >= INT32_MAX)
+        return fail(nullptr, F2M_ERR_INVALID_ARG, "instance " + std::to_string(s) + ": bad row_ptr");
+      eoff[s + 1] = eoff[s] + (int32_t)nz;
+    }
+  }
+  const int64_t nnz = eoff[count];
+  // union CSR on the device
+  int32_t *d_rpl = nullptr, *d_coll = nullptr, *d_rp = nullptr, *d_col = nullptr, *d_so = nullptr,
+          *d_eo = nullptr;
+  CheckCtl* d_chk = nullptr;
+  f2m_status s = F2M_OK;
+  do {
+    cudaError_t e = dalloc(&d_rpl, N + count);
+    if (e == cudaSuccess) e = dalloc(&d_coll, nnz);
+    if (e == cudaSuccess) e = dalloc(&d_rp, N + 1);
+    if (e == cudaSuccess) e = dalloc(&d_col, nnz);
+    if (e == cudaSuccess) e = dalloc(&d_so, count + 1);
+    if (e == cudaSuccess) e = dalloc(&d_eo, count + 1);
+    if (e == cudaSuccess) e = dalloc(&d_chk, 1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_rpl, row_ptr, sizeof(int32_t) * (N + count), cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_coll, col, sizeof(int32_t) * nnz, cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_so, seg_off.data(), sizeof(int32_t) * (count + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_eo, eoff.data(), sizeof(int32_t) * (count + 1), cudaMemcpyHostToDevice, st);
+    CheckCtl h0{0, INT32_MAX};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_chk, &h0, sizeof(h0), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_batch_union(d_rpl, d_coll, d_so, d_eo, count, N, nnz, d_rp, d_col, d_chk, st);
+    CheckCtl h{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_chk, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { s = cuda_fail(nullptr, e, "create_batch: union"); break; }
+    if (h.flags) {
+      s = fail(nullptr, F2M_ERR_INVALID_ARG,
+               std::string(h.flags & 2 ? "column index outside its instance" : "row_ptr out of range") +
+                   " (at " + std::to_string(h.first_bad) + ")");
+      break;
+    }
+    f2m_ctx* u = nullptr;
+    s = create_internal(xy, N, d_rp, d_col, params, stream, seg_off, &u);
+    if (s != F2M_OK) break;
+    f2m_batch* b = new (std::nothrow) f2m_batch();
+    if (!b) { f2m_destroy(u); s = fail(nullptr, F2M_ERR_OOM, "host allocation"); break; }
+    b->u = u;
+    b->count = count;
+    b->n.assign(n, n + count);
+    e = dalloc(&u->d_seg_off, count + 1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(u->d_seg_off, seg_off.data(), sizeof(int32_t) * (count + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = dalloc(&b->d_active, count);
+    if (e == cudaSuccess) e = dalloc(&b->d_seg_ch, 3LL * count);
+    if (e == cudaSuccess) e = dalloc(&b->d_seg_sweeps, count);
+    if (e == cudaSuccess) e = dalloc(&b->d_seg_b2, count);
+    if (e == cudaSuccess) e = dalloc(&b->d_seg_bad, count);
+    if (e == cudaSuccess) e = dalloc(&u->d_fin_include, count);
+    if (e == cudaSuccess) e = cudaMemsetAsync(u->d_fin_include, 1, count, st);
+    if (e == cudaSuccess) e = dalloc(&b->d_mask, count);
+    if (e == cudaSuccess) e = dalloc(&b->d_res_lam, N);
+    if (e == cudaSuccess) e = dalloc(&b->d_res_rp, (int64_t)N + count);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { f2m_destroy_batch(b); s = cuda_fail(nullptr, e, "create_batch: setup"); break; }
+    *out = b;
+  } while (0);
+  dfree(d_rpl); dfree(d_coll); dfree(d_rp); dfree(d_col); dfree(d_so); dfree(d_eo); dfree(d_chk);
+  return s;
+}
+
+// One GDP phase over the segments flagged in `active` (host, one byte each);
+// adds each segment's sweeps to sweeps_out.
+static f2m_status batch_gdp_phase(f2m_batch* b, const std::vector<uint8_t>& active,
+                                  std::vector<int64_t>& sweeps_out, double* ms) {
+  f2m_ctx* c = b->u;
+  GdpPlan& P = c->plan;
+  const int32_t F = c->p.frac_bits;
+  if (c->fb_cur != F) {  // continue from the finisher's lambda: floor to F bits
+    CK(c, launch_halve(c->d_lam2, c->d_lam[c->cur], c->n, c->st));
+    c->fb_cur = F;
+  }
+  if (b->tiles_version != P.version) {  // tiles over the current renumbered CSR
+    std::vector<int32_t> irp(c->n + 1);
+    CK(c, cudaMemcpyAsync(irp.data(), P.irp, sizeof(int32_t) * (c->n + 1), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    std::vector<int4> tiles;
+    for (int32_t s = 0; s < b->count; ++s) {
+      int32_t v = c->seg_off[s];
+      const int32_t end = c->seg_off[s + 1];
+      while (v < end) {
+        const int32_t start = v, e0 = irp[v];
+        while (v < end && v - start < kBatchTileNodes && irp[v + 1] - e0 <= kBatchTileEntries) ++v;
+        if (v == start)
+          return fail(c, F2M_ERR_INVALID_ARG, "a node has more candidate edges than a batch tile holds");
+        tiles.push_back(make_int4(start, v, s, e0));
+      }
+    }
+    dfree(b->d_tiles);
+    CK(c, dalloc(&b->d_tiles, (int64_t)tiles.size()));
+    CK(c, cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, c->st));
+    int per_sm = batch_blocks_per_sm();
+    if (per_sm < 1) return fail(c, F2M_ERR_CUDA, "batch kernel does not fit an SM");
+    if (per_sm > 2) per_sm = 2;
+    if (c->p.gdp_ctas_per_sm > 0 && c->p.gdp_ctas_per_sm < per_sm) per_sm = c->p.gdp_ctas_per_sm;
+    int32_t B = c->num_sms * per_sm;
+    if (B > (int32_t)tiles.size()) B = (int32_t)tiles.size();
+    b->ntiles = (int32_t)tiles.size();
+    b->grid = B;
+    b->tiles_version = P.version;
+  }
+  int32_t* l0 = P.ilam[0];
+  int32_t* l1 = P.ilam[1];
+  CK(c, gather_perm(c->d_lam[c->cur], P.perm, c->n, l0, c->st));
+  CK(c, cudaMemcpyAsync(l1, l0, sizeof(int32_t) * c->n, cudaMemcpyDeviceToDevice, c->st));
+  CK(c, cudaMemcpyAsync(b->d_active, active.data(), b->count, cudaMemcpyHostToDevice, c->st));
+  CK(c, cudaMemsetAsync(b->d_seg_ch, 0, sizeof(unsigned long long) * 3 * b->count, c->st));
+  CK(c, cudaMemsetAsync(b->d_seg_sweeps, 0, sizeof(long long) * b->count, c->st));
+  CK(c, cudaMemsetAsync(c->d_gdp, 0, sizeof(GdpCtl), c->st));
+  CK(c, cudaEventRecord(c->ev0, c->st));
+  CK(c, launch_gdp_batch(P.irp, P.iec, b->d_tiles, b->ntiles, b->grid, b->count, b->d_active,
+                         b->d_seg_ch, b->d_seg_sweeps, l0, l1, F, c->p.damping_shift, c->p.max_iters,
+                         c->d_gdp, c->p.barrier_budget_cycles, c->st));
+  CK(c, cudaEventRecord(c->ev1, c->st));
+  GdpCtl h{};
+  std::vector<long long> sw(b->count);
+  std::vector<uint8_t> still(b->count);
+  CK(c, cudaMemcpyAsync(&h, c->d_gdp, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaMemcpyAsync(sw.data(), b->d_seg_sweeps, sizeof(long long) * b->count, cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaMemcpyAsync(still.data(), b->d_active, b->count, cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  float t_ms = 0.f;
+  cudaEventElapsedTime(&t_ms, c->ev0, c->ev1);
+  if (ms) *ms += t_ms;
+  if (h.status & kGdpTimeout) return fail(c, F2M_ERR_TIMEOUT, "device-wide barrier wait exceeded its budget");
+  if (h.status & kGdpOverflow) return fail(c, F2M_ERR_OVERFLOW, "|lambda| reached 2^29 in some instance");
+  for (int32_t s = 0; s < b->count; ++s) {
+    if (!active[s]) continue;
+    sweeps_out[s] += still[s] ? h.sweeps : sw[s];  // unfrozen ones ran to the cap
+  }
+  CK(c, scatter_perm(h.sweeps & 1 ? l1 : l0, P.perm, c->n, c->d_lam[c->cur], c->st));
+  return F2M_OK;
+}
+
+// Copy the results of the instances flagged in `done` out of the union state.
+static f2m_status snapshot(f2m_batch* b, const std::vector<uint8_t>& done) {
+  f2m_ctx* c = b->u;
+  const int32_t K = b->count;
+  int32_t fb = 0;
+  const int32_t* lam = cur_lambda(c, &fb);
+  CK(c, launch_batch_extract_bound(c->d_rp, c->d_ec, lam, c->n, fb, c->d_seg_off, K, c->d_x2,
+                                   b->d_seg_b2, b->d_seg_bad, nullptr, c->st));
+  std::vector<long long> b2(K);
+  std::vector<int32_t> rp(c->n + 1);
+  CK(c, cudaMemcpyAsync(b2.data(), b->d_seg_b2, sizeof(long long) * K, cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaMemcpyAsync(rp.data(), c->d_rp, sizeof(int32_t) * (c->n + 1), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  int64_t need = b->res_used;
+  for (int32_t s = 0; s < K; ++s)
+    if (done[s]) need += rp[c->seg_off[s + 1]] - rp[c->seg_off[s]];
+  if (need > b->res_cap) {  // grow the arenas, keeping what they hold
+    const int64_t cap = need + (need >> 2) + 1024;
+    int2* ec = nullptr;
+    uint8_t* x2 = nullptr;
+    CK(c, dalloc(&ec, cap));
+    CK(c, dalloc(&x2, cap));
+    if (b->res_used) {
+      CK(c, cudaMemcpyAsync(ec, b->d_res_ec, sizeof(int2) * b->res_used, cudaMemcpyDeviceToDevice, c->st));
+      CK(c, cudaMemcpyAsync(x2, b->d_res_x2, b->res_used, cudaMemcpyDeviceToDevice, c->st));
+      CK(c, cudaStreamSynchronize(c->st));
+    }
+    dfree(b->d_res_ec);
+    dfree(b->d_res_x2);
+    b->d_res_ec = ec;
+    b->d_res_x2 = x2;
+    b->res_cap = cap;
+  }
+  for (int32_t s = 0; s < K; ++s) {
+    if (!done[s]) continue;
+    const int32_t v0 = c->seg_off[s], ns = c->seg_off[s + 1] - v0;
+    const int64_t e0 = rp[v0], nz = rp[v0 + ns] - e0;
+    CK(c, cudaMemcpyAsync(b->d_res_lam + v0, lam + v0, sizeof(int32_t) * ns, cudaMemcpyDeviceToDevice, c->st));
+    CK(c, cudaMemcpyAsync(b->d_res_rp + v0 + s, c->d_rp + v0, sizeof(int32_t) * (ns + 1), cudaMemcpyDeviceToDevice, c->st));
+    if (nz) {
+      CK(c, cudaMemcpyAsync(b->d_res_ec + b->res_used, c->d_ec + e0, sizeof(int2) * nz, cudaMemcpyDeviceToDevice, c->st));
+      CK(c, cudaMemcpyAsync(b->d_res_x2 + b->res_used, c->d_x2 + e0, nz, cudaMemcpyDeviceToDevice, c->st));
+    }
+    b->res_eoff[s] = b->res_used;
+    b->res_nnz[s] = nz;
+    b->res_b2[s] = b2[s];
+    b->res_fb[s] = fb;
+    b->res_done[s] = 1;
+    b->res_used += nz;
+  }
+  CK(c, cudaStreamSynchronize(c->st));
+  return F2M_OK;
+}
+
+// The solve loop of f2m_solve, kept per instance; every device step covers
+// all instances that are at that step.
+extern "C" f2m_status f2m_solve_batch(f2m_batch* b, f2m_info* info_out, f2m_info* total_out) {
+  if (!b) return fail(nullptr, F2M_ERR_INVALID_ARG, "NULL batch");
+  f2m_ctx* c = b->u;
+  const auto t0 = std::chrono::steady_clock::now();
+  const int32_t K = b->count;
+  enum { GDP = 0, EXTRACT = 1, DONE = 2 };
+  std::vector<int> state(K, GDP);
+  std::vector<uint8_t> clean(K, 0), active(K, 0), include(K, 0), done_now(K, 0);
+  std::vector<int64_t> sweeps(K, 0), phases(K, 0), rounds(K, 0), added(K, 0), fin_calls(K, 0);
+  std::vector<int32_t> certified(K, 0), inst_status(K, F2M_OK);
+  b->res_eoff.assign(K, 0);
+  b->res_nnz.assign(K, 0);
+  b->res_b2.assign(K, 0);
+  b->res_fb.assign(K, c->p.frac_bits);
+  b->res_done.assign(K, 0);
+  b->res_used = 0;
+  f2m_info tot;
+  std::memset(&tot, 0, sizeof(tot));
+  f2m_status status = F2M_OK;
+  auto any_in = [&](int st) {
+    for (int s : state)
+      if (s == st) return true;
+    return false;
+  };
+  while (status == F2M_OK && (any_in(GDP) || any_in(EXTRACT))) {
+    if (any_in(GDP)) {
+      for (int32_t s = 0; s < K; ++s) active[s] = state[s] == GDP;
+      status = batch_gdp_phase(b, active, sweeps, &tot.ms_gdp);
+      if (status != F2M_OK) break;
+      tot.phases += 1;
+      c->seg_scan.assign(K, 0);
+      bool any_scan = false;
+      for (int32_t s = 0; s < K; ++s) {
+        if (!active[s]) continue;
+        phases[s] += 1;
+        clean[s] = 0;
+        if (c->p.pricing && rounds[s] < c->p.max_pricing_rounds) {
+          c->seg_scan[s] = 1;
+          any_scan = true;
+        } else {
+          state[s] = EXTRACT;
+        }
+      }
+      if (any_scan) {  // pricing with the GDP lambda
+        status = price_internal(c, &tot.ms_pricing);
+        if (status != F2M_OK) break;
+        tot.pricing_rounds += 1;
+        for (int32_t s = 0; s < K; ++s) {
+          if (!c->seg_scan[s]) continue;
+          rounds[s] += 1;
+          if (c->seg_pairs[s] > 0) {
+            added[s] += c->seg_pairs[s];  // another GDP phase
+          } else {
+            clean[s] = 1;
+            state[s] = EXTRACT;
+          }
+        }
+        if (c->npairs > 0) {
+          status = merge_internal(c, c->d_pairs, c->npairs, &tot.ms_merge);
+          if (status != F2M_OK) break;
+          tot.edges_added += c->npairs;
+        }
+      }
+      if (any_in(GDP)) continue;  // the others wait at EXTRACT
+    }
+    // rule (7) for the instances at EXTRACT; the finisher for those with defects
+    int32_t fb = 0;
+    const int32_t* lam = cur_lambda(c, &fb);
+    for (int32_t s = 0; s < K; ++s) done_now[s] = state[s] == EXTRACT;
+    CK(c, cudaMemcpyAsync(b->d_mask, done_now.data(), K, cudaMemcpyHostToDevice, c->st));
+    CK(c, cudaEventRecord(c->ev0, c->st));
+    CK(c, launch_batch_extract_bound(c->d_rp, c->d_ec, lam, c->n, fb, c->d_seg_off, K, c->d_x2,
+                                     b->d_seg_b2, b->d_seg_bad, b->d_mask, c->st));
+    CK(c, cudaEventRecord(c->ev1, c->st));
+    std::vector<unsigned long long> bad(K);
+    CK(c, cudaMemcpyAsync(bad.data(), b->d_seg_bad, sizeof(unsigned long long) * K, cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+      tot.ms_extract += ms;
+    }
+    bool any_bad = false;
+    for (int32_t s = 0; s < K; ++s) {
+      include[s] = state[s] == EXTRACT && bad[s] > 0;
+      any_bad |= include[s] != 0;
+    }
+    if (any_bad) {
+      if (!c->p.finisher) {
+        status = F2M_ERR_NOT_CONVERGED;
+        fail(c, status, "some instance violates the degree constraint and the finisher is off");
+        break;
+      }
+      CK(c, cudaMemcpyAsync(c->d_fin_include, include.data(), K, cudaMemcpyHostToDevice, c->st));
+      const auto f0 = std::chrono::steady_clock::now();
+      int64_t aug = 0;
+      status = finisher_internal(c, &aug);
+      tot.ms_finish += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - f0).count();
+      if (status != F2M_OK) break;
+      tot.finisher_calls += 1;
+      tot.augmentations += aug;
+      for (int32_t s = 0; s < K; ++s) fin_calls[s] += include[s];
+    }
+    // pricing with the final lambda where it changed since the clean scan
+    c->seg_scan.assign(K, 0);
+    bool any_scan = false;
+    std::fill(done_now.begin(), done_now.end(), 0);
+    for (int32_t s = 0; s < K; ++s) {
+      if (state[s] != EXTRACT) continue;
+      certified[s] = 1;
+      if (!c->p.pricing) { done_now[s] = 1; continue; }
+      if (clean[s] && !include[s]) { certified[s] = 2; done_now[s] = 1; continue; }
+      if (rounds[s] >= c->p.max_pricing_rounds) {
+        done_now[s] = 1;
+        inst_status[s] = F2M_ERR_NOT_CONVERGED;
+        continue;
+      }
+      c->seg_scan[s] = 1;
+      any_scan = true;
+    }
+    if (any_scan) {
+      status = price_internal(c, &tot.ms_pricing);
+      if (status != F2M_OK) break;
+      tot.pricing_rounds += 1;
+      for (int32_t s = 0; s < K; ++s) {
+        if (!c->seg_scan[s]) continue;
+        rounds[s] += 1;
+        if (c->seg_pairs[s] == 0) {
+          certified[s] = 2;
+          done_now[s] = 1;
+        } else {
+          added[s] += c->seg_pairs[s];
+          certified[s] = 0;
+          state[s] = GDP;
+        }
+      }
+    }
+    status = snapshot(b, done_now);  // before merges move the entries
+    if (status != F2M_OK) break;
+    for (int32_t s = 0; s < K; ++s)
+      if (done_now[s]) state[s] = DONE;
+    if (any_scan && c->npairs > 0) {
+      status = merge_internal(c, c->d_pairs, c->npairs, &tot.ms_merge);
+      if (status != F2M_OK) break;
+      tot.edges_added += c->npairs;
+    }
+  }
+  CK(c, cudaMemsetAsync(c->d_fin_include, 1, K, c->st));
+  c->seg_scan.clear();
+  CK(c, cudaStreamSynchronize(c->st));
+  for (int32_t s = 0; s < K; ++s) {
+    tot.iterations += sweeps[s];
+    tot.bound2 += b->res_b2[s];
+  }
+  tot.frac_bits = -1;  // per instance
+  tot.nnz = b->res_used;
+  tot.certified = 2;
+  for (int32_t s = 0; s < K; ++s) {
+    tot.certified = std::min(tot.certified, certified[s]);
+    if (status == F2M_OK && inst_status[s] != F2M_OK) status = (f2m_status)inst_status[s];
+  }
+  tot.status = status;
+  tot.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (info_out) {
+    for (int32_t s = 0; s < K; ++s) {
+      f2m_info& f = info_out[s];
+      std::memset(&f, 0, sizeof(f));
+      f.iterations = sweeps[s];
+      f.phases = phases[s];
+      f.pricing_rounds = rounds[s];
+      f.edges_added = added[s];
+      f.finisher_calls = fin_calls[s];
+      f.augmentations = -1;  // counted for the whole batch only
+      f.bound2 = b->res_b2[s];
+      f.frac_bits = b->res_fb[s];
+      f.certified = certified[s];
+      f.status = status == F2M_OK ? inst_status[s] : status;
+      f.nnz = b->res_nnz[s];
+    }
+  }
+  if (total_out) *total_out = tot;
+  return status;
+}
+
+static f2m_status stage(f2m_batch* b, int64_t cap) {
+  f2m_ctx* c = b->u;
+  if (b->tmp_cap >= cap) return F2M_OK;
+  dfree(b->d_tmp_a);
+  dfree(b->d_tmp_b);
+  CK(c, dalloc(&b->d_tmp_a, cap));
+  CK(c, dalloc(&b->d_tmp_b, cap));
+  b->tmp_cap = cap;
+  return F2M_OK;
+}
+
+__global__ void f2m_offset_kernel(const int32_t* __restrict__ in, int64_t count, int32_t sub,
+                                  int32_t* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = in[i] - sub;
+}
+
+extern "C" f2m_status f2m_batch_get_lambda(f2m_batch* b, int32_t i, int32_t* lambda, int32_t* frac_bits) {
+  if (!b || i < 0 || i >= b->count) return bfail(b, F2M_ERR_INVALID_ARG, "bad batch or index");
+  if ((int32_t)b->res_done.size() != b->count || !b->res_done[i])
+    return bfail(b, F2M_ERR_INVALID_ARG, "instance has no result yet");
+  f2m_ctx* c = b->u;
+  if (frac_bits) *frac_bits = b->res_fb[i];
+  if (lambda) {
+    CK(c, cudaMemcpyAsync(lambda, b->d_res_lam + c->seg_off[i], sizeof(int32_t) * b->n[i], cudaMemcpyDefault, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+  }
+  return F2M_OK;
+}
+
+extern "C" f2m_status f2m_batch_get_x(f2m_batch* b, int32_t i, int64_t* nnz_inout, int32_t* row_ptr,
+                                      int32_t* col, uint8_t* x2) {
+  if (!b || i < 0 || i >= b->count || !nnz_inout) return bfail(b, F2M_ERR_INVALID_ARG, "bad batch or index");
+  if ((int32_t)b->res_done.size() != b->count || !b->res_done[i])
+    return bfail(b, F2M_ERR_INVALID_ARG, "instance has no result yet");
+  f2m_ctx* c = b->u;
+  const int64_t nz = b->res_nnz[i];
+  const int64_t cap = *nnz_inout;
+  *nnz_inout = nz;
+  if (!row_ptr && !col && !x2) return F2M_OK;
+  if ((col || x2) && cap < nz) return bfail(b, F2M_ERR_INVALID_ARG, "capacity below nnz");
+  f2m_status s = stage(b, std::max<int64_t>(nz, b->n[i] + 1));
+  if (s != F2M_OK) return s;
+  const int32_t* rp = b->d_res_rp + c->seg_off[i] + i;
+  if (row_ptr) {
+    int32_t r0 = 0;
+    CK(c, cudaMemcpyAsync(&r0, rp, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    f2m_offset_kernel<<<64, 256, 0, c->st>>>(rp, b->n[i] + 1, r0, b->d_tmp_a);
+    count_launch();
+    CK(c, cudaGetLastError());
+    CK(c, cudaMemcpyAsync(row_ptr, b->d_tmp_a, sizeof(int32_t) * (b->n[i] + 1), cudaMemcpyDefault, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+  }
+  if (col && nz) {
+    CK(c, launch_split_ec(b->d_res_ec + b->res_eoff[i], nz, b->d_tmp_b, nullptr, c->st));
+    f2m_offset_kernel<<<256, 256, 0, c->st>>>(b->d_tmp_b, nz, c->seg_off[i], b->d_tmp_a);
+    count_launch();
+    CK(c, cudaGetLastError());
+    CK(c, cudaMemcpyAsync(col, b->d_tmp_a, sizeof(int32_t) * nz, cudaMemcpyDefault, c->st));
+  }
+  if (x2 && nz) CK(c, cudaMemcpyAsync(x2, b->d_res_x2 + b->res_eoff[i], nz, cudaMemcpyDefault, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  return F2M_OK;
+}
+
+extern "C" const char* f2m_batch_last_error(const f2m_batch* b) {
+  return f2m_last_error(b ? b->u : nullptr);
+}

@@ -1,0 +1,120 @@
+// Internal view of the f2m context, shared by the translation units that drive
+// it (api.cu: one instance; batch.cu: many instances as one disjoint union).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/f2m.h"
+#include "f2m_internal.h"
+
+struct f2m_ctx {
+  // segments: contiguous node ranges that are separate instances (a batch);
+  // one segment [0, n) for a single instance.  Pricing pairs stay inside a
+  // segment; the tiled / batch GDP kernels freeze converged segments.
+  std::vector<int32_t> seg_off{0};      // [nseg+1] node offsets
+  std::vector<uint8_t> seg_scan;        // segments the next pricing scan covers (empty: all)
+  std::vector<int64_t> seg_pairs;       // pairs per segment found by the last scan
+  int32_t* d_seg_off = nullptr;         // device copy of seg_off (batches)
+  uint8_t* d_fin_include = nullptr;     // per segment: the finisher may change it (NULL = all)
+  int4* d_tiles = nullptr;              // pricing tile-pair list
+  int64_t tiles_cap = 0;
+
+  int32_t n = 0;
+  int64_t nnz = 0;
+  int64_t ec_cap = 0;
+  cudaStream_t st = nullptr;
+  f2m_params p{};
+  int num_sms = 0;
+  int2* d_xy = nullptr;
+  int32_t* d_rp = nullptr;
+  int2* d_ec = nullptr;
+  uint8_t* d_x2 = nullptr;
+  int32_t* d_lam[2] = {nullptr, nullptr};
+  int32_t* d_lam2 = nullptr;
+  int cur = 0;          // d_lam[cur] holds lambda in units 2^-F
+  int32_t fb_cur = 8;   // F, or F+1 while d_lam2 holds the current lambda
+  f2m::GdpCtl* d_gdp = nullptr;
+  long long* d_trace_b2 = nullptr;
+  unsigned long long* d_trace_ch = nullptr;
+  int64_t trace_cap = 0;
+  float4* d_pts = nullptr;
+  int2* d_pairs = nullptr;
+  int64_t pairs_cap = 0;
+  int64_t npairs = 0;   // pairs held in d_pairs after the last scan
+  unsigned long long* d_count = nullptr;
+  unsigned int* d_tile = nullptr;
+  int32_t* d_deg = nullptr;
+  int32_t* d_tmp_rp = nullptr;
+  int32_t* d_new_rp = nullptr;
+  int32_t* d_block_sums = nullptr;
+  int32_t* d_tmp_col = nullptr;
+  int64_t tmp_col_cap = 0;
+  int32_t* d_out_a = nullptr;  // split scratch for f2m_get_x
+  int32_t* d_out_b = nullptr;
+  int64_t out_cap = 0;
+  f2m::CheckCtl* d_check = nullptr;
+  long long* d_scalar = nullptr;
+  unsigned long long* d_bad = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  f2m::GdpPlan plan;         // renumbering and tiles of the shared-memory GDP kernel
+  // exact finisher: device scratch, pinned host mirrors, host work arrays
+  int32_t* d_twin = nullptr;
+  uint8_t* d_fy = nullptr;
+  uint8_t* d_fx = nullptr;
+  int64_t fin_cap = 0;          // entries the finisher buffers hold
+  int64_t fin_version = -1;     // plan version mirrored on the host
+  int32_t* h_irp = nullptr;
+  int2* h_iec = nullptr;
+  int32_t* h_twin = nullptr;
+  uint8_t* h_y = nullptr;
+  uint8_t* h_x = nullptr;
+  int32_t* h_exl = nullptr;
+  int32_t* h_lam = nullptr;
+  int32_t* h_lam2 = nullptr;
+  f2m::FinisherWork* fin_work = nullptr;
+  std::string err;
+};
+
+namespace f2m {
+
+f2m_status fail(f2m_ctx* ctx, f2m_status s, const std::string& msg);
+f2m_status cuda_fail(f2m_ctx* ctx, cudaError_t e, const char* what);
+
+#define CK(ctx, call)                                          \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, int64_t count) {
+  *p = nullptr;
+  size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
+  return cudaMalloc((void**)p, bytes);
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+f2m_status check_params_internal(const f2m_params& p);
+const int32_t* cur_lambda(f2m_ctx* c, int32_t* fb);
+f2m_status gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, bool want_trace,
+                     int64_t trace_cap, double* ms);
+f2m_status price_internal(f2m_ctx* c, double* ms);
+f2m_status merge_internal(f2m_ctx* c, const int2* d_pairs, int64_t npairs, double* ms);
+f2m_status extract_internal(f2m_ctx* c, int64_t* bad, double* ms);
+f2m_status bound_internal(f2m_ctx* c, int64_t* b2);
+f2m_status finisher_internal(f2m_ctx* c, int64_t* aug);
+// create a context for the graph, renumbering within segments when seg_off has
+// more than one segment (seg_off[0] = 0, seg_off.back() = n)
+f2m_status create_internal(const int32_t* xy, int32_t n, const int32_t* row_ptr, const int32_t* col,
+                           const f2m_params* params, void* stream,
+                           const std::vector<int32_t>& seg_off, f2m_ctx** out);
+
+}  // namespace f2m

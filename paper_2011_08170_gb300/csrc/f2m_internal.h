@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace f2m {
 
 constexpr int32_t kCoordLimit = 1 << 20;   // coordinates in [0, 2^20)
@@ -78,10 +80,12 @@ cudaError_t launch_extract(const int32_t* rp, const int2* ec, const int32_t* lam
 // lam_out = lam_in >> 1 (F+1 bits -> F bits, floor)
 cudaError_t launch_halve(const int32_t* lam_in, int32_t* lam_out, int32_t n, cudaStream_t st);
 // all-pairs pricing scan: pairs (u < v) outside the CSR with z < 0
+// Tile pairs {i0, i1, j0, j1}: test i in [i0, i1) against j in [j0, j1), j > i.
+constexpr int kPricingTile = 1024;
 cudaError_t launch_pricing(const int2* xy, const int32_t* lam, const int32_t* rp, const int2* ec,
-                           int32_t n, int32_t fb, float4* pts, int2* pairs, int64_t cap,
-                           unsigned long long* count, unsigned int* tile_counter, int num_sms,
-                           cudaStream_t st);
+                           int32_t n, int32_t fb, float4* pts, const int4* tiles, int32_t ntiles,
+                           int2* pairs, int64_t cap, unsigned long long* count,
+                           unsigned int* tile_counter, int num_sms, cudaStream_t st);
 // CSR union with pairs; sizes: see graph.cu.  Returns the new nnz through *new_nnz_dev.
 struct MergeBuffers {
   int32_t* deg;        // [n+1]
@@ -143,7 +147,9 @@ struct GdpPlan {
 cudaError_t sort_pairs_u64(void* temp, size_t& temp_bytes, const uint64_t* keys_in,
                            uint64_t* keys_out, const int32_t* vals_in, int32_t* vals_out,
                            int32_t count, int end_bit, cudaStream_t st);
-cudaError_t plan_renumber(const int2* xy, int32_t n, GdpPlan& p, cudaStream_t st);
+// Morton renumbering inside each segment [seg_off[s], seg_off[s+1]) (segments stay contiguous)
+cudaError_t plan_renumber(const int2* xy, int32_t n, const std::vector<int32_t>& seg_off, GdpPlan& p,
+                          cudaStream_t st);
 // internal CSR (always) and, if `tiles`, the per-CTA tiles of the shared-memory kernel
 cudaError_t plan_build(const int32_t* rp, const int2* ec, int32_t n, int64_t nnz, int num_sms,
                        bool tiles, int32_t F, int32_t ctas_per_sm, GdpPlan& p, cudaStream_t st);
@@ -164,17 +170,43 @@ cudaError_t plan_scatter_lambda(const GdpPlan& p, int which, int32_t* lam_out, c
 cudaError_t fin_build_twin(const GdpPlan& p, int32_t* twin, cudaStream_t st);
 cudaError_t fin_prepare(const GdpPlan& p, const int32_t* lam_caller, int32_t F, int32_t* lam_int,
                         uint8_t* y, int32_t* exl, cudaStream_t st);
+// include (device, per segment; NULL = all): x of excluded segments is kept
 cudaError_t fin_scatter(const GdpPlan& p, const int32_t* rp, const uint8_t* x_int,
-                        const int32_t* lam2_int, uint8_t* x_out, int32_t* lam2_out, cudaStream_t st);
+                        const int32_t* lam2_int, uint8_t* x_out, int32_t* lam2_out,
+                        const int32_t* seg_off, int32_t nseg, const uint8_t* include,
+                        cudaStream_t st);
+// ---- batched solver (batch_kernels.cu) --------------------------------------------
+constexpr int kBatchTileEntries = 4096;  // entries per tile of the batch kernel
+constexpr int kBatchTileNodes = 1536;    // nodes per tile
+// tiles {first node, end node, segment, first entry} over the renumbered CSR
+cudaError_t launch_gdp_batch(const int32_t* irp, const int2* iec, const int4* tiles, int32_t ntiles,
+                             int32_t B, int32_t nseg, uint8_t* active, unsigned long long* seg_ch,
+                             long long* seg_sweeps, int32_t* lam0, int32_t* lam1, int32_t F,
+                             int32_t shift, int64_t max_sweeps, GdpCtl* ctl, long long budget,
+                             cudaStream_t st);
+int batch_blocks_per_sm();
+cudaError_t launch_batch_extract_bound(const int32_t* rp, const int2* ec, const int32_t* lam,
+                                       int32_t n, int32_t fb, const int32_t* seg_off, int32_t nseg,
+                                       uint8_t* x2, long long* seg_b2, unsigned long long* seg_bad,
+                                       const uint8_t* seg_write, cudaStream_t st);
+cudaError_t launch_batch_union(const int32_t* rp_local, const int32_t* col_local,
+                               const int32_t* seg_off, const int32_t* eoff, int32_t nseg, int32_t n,
+                               int64_t nnz, int32_t* rp, int32_t* col, CheckCtl* ctl,
+                               cudaStream_t st);
+cudaError_t launch_batch_mask_surplus(int32_t* exl, const int32_t* seg_off, int32_t nseg,
+                                      const uint8_t* include, int32_t n, cudaStream_t st);
+
 struct FinisherWork;
 FinisherWork* finisher_work_new();
 void finisher_work_reserve(FinisherWork* w, int32_t n);  // host work arrays for n nodes
 void finisher_work_free(FinisherWork* w);
 // Min-cost flow on the bipartite double cover, internal node order; see
 // finisher.cpp.  y is the initial flow (updated), exl the left surpluses.
-// Returns 0 ok, 7 infeasible, 5 overflow.
+// Segments [seg_off[s], seg_off[s+1]) are independent and go to up to
+// `threads` host threads.  Returns 0 ok, 7 infeasible, 5 overflow.
 int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t* twin, uint8_t* y,
                   const int32_t* exl, const int32_t* lam, int32_t F, uint8_t* x2, int32_t* lam2,
-                  int64_t* augmentations, FinisherWork* w);
+                  const int32_t* seg_off, int32_t nseg, int32_t threads, int64_t* augmentations,
+                  FinisherWork* w);
 
 }  // namespace f2m

@@ -27,25 +27,25 @@
 // device (finisher_prep.cu): internal node i is the i-th point in (Morton
 // code, caller id) order, every row keeps the caller's column order.  Node
 // ids here: L_i = i, R_i = n + i; key(L_i) = 2i, key(R_i) = 2i + 1.
+#include <algorithm>
+#include <atomic>
 #include <cstdint>
+#include <thread>
 #include <vector>
 
 #include "f2m_internal.h"
 
 namespace f2m {
 
-struct FinisherWork {
-  std::vector<int64_t> pi, dist;
-  std::vector<int32_t> excess, via, pred, order;
-  std::vector<int32_t> sources;  // surplus nodes in key order
-  std::vector<uint32_t> reached, closed;
-  uint32_t round = 0;
+// Search state of one worker: heap, settled list and visit stamps.
+struct Searcher {
   struct Item {
     int64_t d;
     int32_t key;   // the tie-break
     int32_t node;  // internal id
   };
   std::vector<Item> heap;
+  std::vector<int32_t> order;
 
   static bool less(const Item& a, const Item& b) { return a.d < b.d || (a.d == b.d && a.key < b.key); }
   void push(const Item& it) {
@@ -77,7 +77,16 @@ struct FinisherWork {
   }
 };
 
+struct FinisherWork {
+  std::vector<int64_t> pi, dist;
+  std::vector<int32_t> excess, via, pred;
+  std::vector<uint32_t> reached, closed;  // search stamps; every search takes a fresh one
+  std::atomic<uint32_t> stamp{0};
+  std::vector<Searcher> workers;
+};
+
 FinisherWork* finisher_work_new() { return new FinisherWork(); }
+void finisher_work_free(FinisherWork* w) { delete w; }
 
 void finisher_work_reserve(FinisherWork* w, int32_t n) {
   const size_t N = 2 * (size_t)n;
@@ -89,18 +98,16 @@ void finisher_work_reserve(FinisherWork* w, int32_t n) {
   w->pred.assign(N, 0);
   w->reached.assign(N, 0);
   w->closed.assign(N, 0);
-  w->round = 0;
-  w->order.reserve(1024);
-  w->heap.reserve(4096);
-  w->sources.reserve(N / 16 + 64);
+  w->stamp.store(0);
 }
-void finisher_work_free(FinisherWork* w) { delete w; }
 
-int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t* twin, uint8_t* y,
-                  const int32_t* exl, const int32_t* lam, int32_t F, uint8_t* x2, int32_t* lam2,
-                  int64_t* augmentations, FinisherWork* w) {
-  const int32_t N = 2 * n;
-  finisher_work_reserve(w, n);
+namespace {
+
+// Successive shortest paths for the sources of one segment [lo, hi) (internal
+// ids), in key order.  Paths never leave the segment (no arc does).
+int solve_segment(int32_t n, int32_t lo, int32_t hi, const int32_t* irp, const int2* iec,
+                  const int32_t* twin, uint8_t* y, int32_t F, FinisherWork* w, Searcher& sr,
+                  int64_t* pushes_out) {
   int64_t* pi = w->pi.data();
   int64_t* dist = w->dist.data();
   int32_t* excess = w->excess.data();
@@ -108,99 +115,124 @@ int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t*
   int32_t* pred = w->pred.data();
   uint32_t* reached = w->reached.data();
   uint32_t* closed = w->closed.data();
+  auto key_of = [&](int32_t node) { return node < n ? 2 * node : 2 * (node - n) + 1; };
+  int64_t pushes = 0;
+  for (int32_t i = lo; i < hi; ++i) {
+    for (int side = 0; side < 2; ++side) {
+      const int32_t s = side == 0 ? i : n + i;  // key order: L_i (2i) before R_i (2i+1)
+      while (excess[s] > 0) {
+        const uint32_t round = w->stamp.fetch_add(1) + 1;
+        sr.order.clear();
+        sr.heap.clear();
+        dist[s] = 0;
+        reached[s] = round;
+        pred[s] = -1;
+        sr.push({0, key_of(s), s});
+        int32_t t = -1;
+        while (!sr.heap.empty()) {
+          const Searcher::Item top = sr.pop();
+          const int32_t v = top.node;
+          if (closed[v] == round || top.d != dist[v]) continue;
+          closed[v] = round;
+          if (excess[v] < 0) { t = v; break; }
+          sr.order.push_back(v);
+          if (v < n) {
+            // out arcs of L_v without flow: L_v -> R_j
+            for (int32_t e = irp[v]; e < irp[v + 1]; ++e) {
+              if (y[e]) continue;
+              const int32_t j = n + iec[e].x;
+              const int64_t d = dist[v] + ((int64_t)iec[e].y << F) - pi[v] + pi[j];
+              if (closed[j] != round && (reached[j] != round || d < dist[j])) {
+                reached[j] = round; dist[j] = d; via[j] = e; pred[j] = v;
+                sr.push({d, key_of(j), j});
+              }
+            }
+          } else {
+            // R_u: reverse arcs of saturated arcs x -> u (the twins of row u)
+            const int32_t u = v - n;
+            for (int32_t f = irp[u]; f < irp[u + 1]; ++f) {
+              const int32_t a = twin[f];
+              if (!y[a]) continue;
+              const int32_t j = iec[f].x;  // L_x, the tail of arc a
+              const int64_t d = dist[v] - ((int64_t)iec[f].y << F) - pi[v] + pi[j];
+              if (closed[j] != round && (reached[j] != round || d < dist[j])) {
+                reached[j] = round; dist[j] = d; via[j] = a; pred[j] = v;
+                sr.push({d, key_of(j), j});
+              }
+            }
+          }
+        }
+        if (t < 0) return 7;
+        for (int32_t j = t; j != s; j = pred[j]) y[via[j]] = (uint8_t)(j >= n);  // push one unit
+        excess[s] -= 1;
+        excess[t] += 1;
+        ++pushes;
+        const int64_t dt = dist[t];
+        for (int32_t v : sr.order) pi[v] += dt - dist[v];
+      }
+    }
+  }
+  *pushes_out += pushes;
+  return 0;
+}
+
+}  // namespace
+
+int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t* twin, uint8_t* y,
+                  const int32_t* exl, const int32_t* lam, int32_t F, uint8_t* x2, int32_t* lam2,
+                  const int32_t* seg_off, int32_t nseg, int32_t threads, int64_t* augmentations,
+                  FinisherWork* w) {
+  finisher_work_reserve(w, n);
+  if (w->stamp.load() > (1u << 31)) {  // far from wrapping: clear the stamps and restart
+    std::fill(w->reached.begin(), w->reached.end(), 0u);
+    std::fill(w->closed.begin(), w->closed.end(), 0u);
+    w->stamp.store(0);
+  }
+  int64_t* pi = w->pi.data();
+  int32_t* excess = w->excess.data();
   for (int32_t i = 0; i < n; ++i) {
     pi[i] = lam[i];
     pi[n + i] = -(int64_t)lam[i];
     excess[i] = exl[i];       // L_i: supply 2 minus outflow
     excess[n + i] = -exl[i];  // R_i: inflow minus demand 2 (z is symmetric)
   }
-  auto key_of = [&](int32_t node) { return node < n ? 2 * node : 2 * (node - n) + 1; };
-
-  // Surplus only shrinks (a path ends at a deficit node), so the nodes that
-  // will ever be sources are those with surplus now, taken in key order, each
-  // until its surplus is used up.
-  std::vector<int32_t>& src = w->sources;
-  src.clear();
-  for (int32_t i = 0; i < n; ++i) {
-    if (excess[i] > 0) src.push_back(i);
-    if (excess[n + i] > 0) src.push_back(n + i);
+  // segments are independent: whole segments go to workers
+  int32_t nw = threads < 1 ? 1 : threads;
+  if (nw > nseg) nw = nseg;
+  if ((int32_t)w->workers.size() < nw) w->workers.resize(nw);
+  std::atomic<int32_t> next{0};
+  std::atomic<int> status{0};
+  std::vector<int64_t> pushes(nw, 0);
+  auto run = [&](int32_t k) {
+    for (;;) {
+      const int32_t sgi = next.fetch_add(1);
+      if (sgi >= nseg || status.load() != 0) break;
+      const int r = solve_segment(n, seg_off[sgi], seg_off[sgi + 1], irp, iec, twin, y, F, w,
+                                  w->workers[k], &pushes[k]);
+      if (r != 0) status.store(r);
+    }
+  };
+  if (nw == 1) {
+    run(0);
+  } else {
+    std::vector<std::thread> pool;
+    for (int32_t k = 1; k < nw; ++k) pool.emplace_back(run, k);
+    run(0);
+    for (std::thread& th : pool) th.join();
   }
-
-  int64_t pushes = 0;
-  int status = 0;
-  size_t next_src = 0;
-  for (;;) {
-    int32_t s = -1;
-    while (next_src < src.size()) {
-      const int32_t node = src[next_src];
-      if (excess[node] > 0) { s = node; break; }
-      ++next_src;
-    }
-    if (s < 0) break;
-    if (++w->round == 0) {  // stamp wrap: clear and restart
-      w->reached.assign(N, 0);
-      w->closed.assign(N, 0);
-      w->round = 1;
-    }
-    const uint32_t round = w->round;
-    w->order.clear();
-    w->heap.clear();
-    dist[s] = 0;
-    reached[s] = round;
-    pred[s] = -1;
-    w->push({0, key_of(s), s});
-    int32_t t = -1;
-    while (!w->heap.empty()) {
-      const FinisherWork::Item top = w->pop();
-      const int32_t i = top.node;
-      if (closed[i] == round || top.d != dist[i]) continue;
-      closed[i] = round;
-      if (excess[i] < 0) { t = i; break; }
-      w->order.push_back(i);
-      if (i < n) {
-        // out arcs of L_i without flow: L_i -> R_j
-        for (int32_t e = irp[i]; e < irp[i + 1]; ++e) {
-          if (y[e]) continue;
-          const int32_t j = n + iec[e].x;
-          const int64_t d = dist[i] + ((int64_t)iec[e].y << F) - pi[i] + pi[j];
-          if (closed[j] != round && (reached[j] != round || d < dist[j])) {
-            reached[j] = round; dist[j] = d; via[j] = e; pred[j] = i;
-            w->push({d, key_of(j), j});
-          }
-        }
-      } else {
-        // R_v: reverse arcs of saturated arcs u -> v (the twins of row v)
-        const int32_t v = i - n;
-        for (int32_t f = irp[v]; f < irp[v + 1]; ++f) {
-          const int32_t a = twin[f];
-          if (!y[a]) continue;
-          const int32_t j = iec[f].x;  // L_u, the tail of arc a
-          const int64_t d = dist[i] - ((int64_t)iec[f].y << F) - pi[i] + pi[j];
-          if (closed[j] != round && (reached[j] != round || d < dist[j])) {
-            reached[j] = round; dist[j] = d; via[j] = a; pred[j] = i;
-            w->push({d, key_of(j), j});
-          }
-        }
-      }
-    }
-    if (t < 0) { status = 7; break; }
-    for (int32_t j = t; j != s; j = pred[j]) y[via[j]] = (uint8_t)(j >= n);  // push one unit
-    excess[s] -= 1;
-    excess[t] += 1;
-    ++pushes;
-    const int64_t dt = dist[t];
-    for (int32_t i : w->order) pi[i] += dt - dist[i];
-  }
-  *augmentations = pushes;
-  if (status != 0) return status;
+  int64_t total = 0;
+  for (int64_t p : pushes) total += p;
+  *augmentations = total;
+  if (status.load() != 0) return status.load();
+  int st = 0;
   const int64_t nnz = irp[n];
   for (int64_t e = 0; e < nnz; ++e) x2[e] = (uint8_t)(y[e] + y[twin[e]]);
   for (int32_t i = 0; i < n; ++i) {
     const int64_t l2 = pi[i] - pi[n + i];
-    if (l2 >= 2 * kLamLimit || l2 <= -2 * kLamLimit) status = 5;
+    if (l2 >= 2 * kLamLimit || l2 <= -2 * kLamLimit) st = 5;
     lam2[i] = (int32_t)l2;
   }
-  return status;
+  return st;
 }
 
 }  // namespace f2m

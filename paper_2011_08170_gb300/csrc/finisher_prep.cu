@@ -56,8 +56,18 @@ __global__ void fin_init_kernel(const int32_t* __restrict__ irp, const int2* __r
 
 __global__ void fin_scatter_x_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ irp,
                                      const int32_t* __restrict__ perm, int32_t n,
-                                     const uint8_t* __restrict__ x_int, uint8_t* __restrict__ x_out) {
+                                     const uint8_t* __restrict__ x_int, uint8_t* __restrict__ x_out,
+                                     const int32_t* __restrict__ seg_off, int32_t nseg,
+                                     const uint8_t* __restrict__ include) {
   F2M_GRID_STRIDE(i, n) {
+    if (include) {  // segments the finisher left alone keep their x
+      int lo = 0, hi = nseg - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (seg_off[mid] <= (int)i) lo = mid; else hi = mid - 1;
+      }
+      if (!include[lo]) continue;
+    }
     const int dst = rp[perm[i]], src = irp[i], cnt = irp[i + 1] - src;
     for (int k = 0; k < cnt; ++k) x_out[dst + k] = x_int[src + k];
   }
@@ -78,8 +88,11 @@ cudaError_t fin_prepare(const GdpPlan& p, const int32_t* lam_caller, int32_t F, 
 }
 
 cudaError_t fin_scatter(const GdpPlan& p, const int32_t* rp, const uint8_t* x_int,
-                        const int32_t* lam2_int, uint8_t* x_out, int32_t* lam2_out, cudaStream_t st) {
-  fin_scatter_x_kernel<<<grid_for(p.n, 128), 128, 0, st>>>(rp, p.irp, p.perm, p.n, x_int, x_out);
+                        const int32_t* lam2_int, uint8_t* x_out, int32_t* lam2_out,
+                        const int32_t* seg_off, int32_t nseg, const uint8_t* include,
+                        cudaStream_t st) {
+  fin_scatter_x_kernel<<<grid_for(p.n, 128), 128, 0, st>>>(rp, p.irp, p.perm, p.n, x_int, x_out,
+                                                           seg_off, nseg, include);
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

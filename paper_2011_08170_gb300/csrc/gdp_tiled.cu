@@ -22,6 +22,7 @@
 //    sweep t and applied after it, hiding that read behind the sweep; a sweep
 //    computed after the stop condition is discarded (nothing is published).
 #include <climits>
+#include <vector>
 
 #include "f2m_device.cuh"
 #include "f2m_internal.h"
@@ -41,15 +42,23 @@ static inline int grid_for(long long items, int threads) {
 
 // ---- spatial renumbering ---------------------------------------------------------
 
-// key = Morton code: bit b of x at position 2b, bit b of y at 2b+1 (x, y < 2^20)
-__global__ void morton_kernel(const int2* __restrict__ xy, int32_t n, uint64_t* key, int32_t* idx) {
+// key = segment * 2^40 + Morton code (bit b of x at position 2b, bit b of y at
+// 2b+1; x, y < 2^20), so nodes stay grouped by segment (instance) and follow a
+// Morton curve inside each
+__global__ void morton_kernel(const int2* __restrict__ xy, int32_t n, const int32_t* __restrict__ seg_off,
+                              int32_t nseg, uint64_t* key, int32_t* idx) {
   F2M_GRID_STRIDE(v, n) {
     const unsigned x = (unsigned)xy[v].x, y = (unsigned)xy[v].y;
     uint64_t code = 0;
 #pragma unroll
     for (int b = 0; b < 20; ++b)
       code |= ((uint64_t)((x >> b) & 1u) << (2 * b)) | ((uint64_t)((y >> b) & 1u) << (2 * b + 1));
-    key[v] = code;
+    int lo = 0, hi = nseg - 1;  // segment of v: last s with seg_off[s] <= v
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (seg_off[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    key[v] = ((uint64_t)lo << 40) | code;
     idx[v] = (int32_t)v;
   }
 }
@@ -499,20 +508,32 @@ void plan_free(GdpPlan& p) {
     if (e_ != cudaSuccess) return e_;      \
   } while (0)
 
-cudaError_t plan_renumber(const int2* xy, int32_t n, GdpPlan& p, cudaStream_t st) {
+cudaError_t plan_renumber(const int2* xy, int32_t n, const std::vector<int32_t>& seg_off, GdpPlan& p,
+                          cudaStream_t st) {
   int64_t cap = 0;
+  const int32_t nseg = (int32_t)seg_off.size() - 1;
+  int32_t* d_seg = nullptr;
+  PCK(cudaMalloc((void**)&d_seg, sizeof(int32_t) * seg_off.size()));
+  cudaError_t e0 = cudaMemcpyAsync(d_seg, seg_off.data(), sizeof(int32_t) * seg_off.size(),
+                                   cudaMemcpyHostToDevice, st);
+  if (e0 != cudaSuccess) { cudaFree(d_seg); return e0; }
+  int end_bit = 40;
+  while ((1LL << (end_bit - 40)) < nseg) ++end_bit;
   PCK(grow(&p.perm, &cap, n)); cap = 0;
   PCK(grow(&p.inv, &cap, n)); cap = 0;
   PCK(grow(&p.keys, &cap, n)); cap = 0;
   PCK(grow(&p.keys2, &cap, n)); cap = 0;
   PCK(grow(&p.idx, &cap, n));
-  morton_kernel<<<grid_for(n, 256), 256, 0, st>>>(xy, n, p.keys, p.idx);
+  morton_kernel<<<grid_for(n, 256), 256, 0, st>>>(xy, n, d_seg, nseg, p.keys, p.idx);
   count_launch();
-  PCK(cudaGetLastError());
+  cudaError_t e1 = cudaGetLastError();
+  if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(st);
+  cudaFree(d_seg);
+  PCK(e1);
   size_t bytes = 0;
-  PCK(sort_pairs_u64(nullptr, bytes, p.keys, p.keys2, p.idx, p.perm, n, 40, st));
+  PCK(sort_pairs_u64(nullptr, bytes, p.keys, p.keys2, p.idx, p.perm, n, end_bit, st));
   PCK(cudaMalloc(&p.sort_tmp, bytes > 0 ? bytes : 1));
-  PCK(sort_pairs_u64(p.sort_tmp, bytes, p.keys, p.keys2, p.idx, p.perm, n, 40, st));
+  PCK(sort_pairs_u64(p.sort_tmp, bytes, p.keys, p.keys2, p.idx, p.perm, n, end_bit, st));
   count_launch();
   invert_perm_kernel<<<grid_for(n, 256), 256, 0, st>>>(p.perm, n, p.inv);
   count_launch();

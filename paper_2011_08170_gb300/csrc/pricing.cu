@@ -4,8 +4,8 @@
 // miss optimal edges (Section 5.3); this scan finds every such edge so the
 // final duals are feasible for the complete graph.
 //
-// N-body tiling: the pair triangle is cut into TILE x TILE tile pairs (bi <= bj)
-// handed out by an atomic counter; a CTA keeps TILE j-points in shared memory
+// N-body tiling: the host lists tile pairs (TILE x TILE blocks of the pair
+// triangle of each segment, i.e. instance), handed out by an atomic counter; a CTA keeps TILE j-points in shared memory
 // and each thread P i-points in registers.  Per pair an fp32 filter runs:
 //   t = s_u + s_v,   e = dy^2 + (dx^2 - t^2)   (two FMAs),   pass if e < 1,
 // with s_v = max(lambda_v * 2^-fb + 1/4, 0) * (1 + 2^-19).
@@ -26,6 +26,7 @@ namespace f2m {
 constexpr int kPriceThreads = 256;
 constexpr int kPriceP = 4;
 constexpr int kPriceTile = kPriceThreads * kPriceP;
+static_assert(kPriceTile == kPricingTile, "tile size shared with the tile-list builder");
 
 __global__ void pricing_prep_kernel(const int2* __restrict__ xy, const int32_t* __restrict__ lam,
                                     int32_t n, int32_t fb, float4* __restrict__ pts) {
@@ -64,26 +65,24 @@ __device__ __noinline__ void pricing_confirm(int i, int j, int32_t n, const int2
 __global__ void __launch_bounds__(kPriceThreads)
 pricing_kernel(const float4* __restrict__ pts, const int2* __restrict__ xy,
                const int32_t* __restrict__ lam, const int32_t* __restrict__ rp,
-               const int2* __restrict__ ec, int32_t n, int32_t fb, int2* pairs, long long cap,
-               unsigned long long* count, unsigned int* tile_counter, int ntiles) {
+               const int2* __restrict__ ec, int32_t n, int32_t fb, const int4* __restrict__ tiles,
+               int32_t ntiles, int2* pairs, long long cap, unsigned long long* count,
+               unsigned int* tile_counter) {
   __shared__ float4 sj[kPriceTile];
   __shared__ int s_tp;
-  const long long total = (long long)ntiles * (ntiles + 1) / 2;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_tp = (int)atomicAdd(tile_counter, 1u);
     __syncthreads();
-    long long tp = s_tp;
-    if (tp >= total) break;
-    int bi = 0;
-    while (tp >= ntiles - bi) { tp -= ntiles - bi; ++bi; }
-    const int bj = bi + (int)tp;
+    const int tp = s_tp;
+    if (tp >= ntiles) break;
+    const int4 tl = tiles[tp];  // i in [x, y), j in [z, w)
 
     float xi[kPriceP], yi[kPriceP], si[kPriceP];
 #pragma unroll
     for (int p = 0; p < kPriceP; ++p) {
-      const int i = bi * kPriceTile + p * kPriceThreads + threadIdx.x;
-      if (i < n) {
+      const int i = tl.x + p * kPriceThreads + threadIdx.x;
+      if (i < tl.y) {
         const float4 q = pts[i];
         xi[p] = q.x; yi[p] = q.y; si[p] = q.z;
       } else {
@@ -91,8 +90,8 @@ pricing_kernel(const float4* __restrict__ pts, const int2* __restrict__ xy,
       }
     }
     for (int k = threadIdx.x; k < kPriceTile; k += kPriceThreads) {
-      const int j = bj * kPriceTile + k;
-      sj[k] = j < n ? pts[j] : make_float4(-1e18f, -1e18f, 0.0f, 0.0f);
+      const int j = tl.z + k;
+      sj[k] = j < tl.w ? pts[j] : make_float4(-1e18f, -1e18f, 0.0f, 0.0f);
     }
     __syncthreads();
 #pragma unroll 4
@@ -108,11 +107,11 @@ pricing_kernel(const float4* __restrict__ pts, const int2* __restrict__ xy,
 #pragma unroll
       for (int p = 1; p < kPriceP; ++p) m = fminf(m, e[p]);
       if (m < 1.0f) {
-        const int j = bj * kPriceTile + k;
+        const int j = tl.z + k;
 #pragma unroll
         for (int p = 0; p < kPriceP; ++p)
           if (e[p] < 1.0f)
-            pricing_confirm(bi * kPriceTile + p * kPriceThreads + threadIdx.x, j, n, xy, lam, rp, ec,
+            pricing_confirm(tl.x + p * kPriceThreads + threadIdx.x, j, min(n, tl.w), xy, lam, rp, ec,
                             fb, pairs, cap, count);
       }
     }
@@ -120,9 +119,9 @@ pricing_kernel(const float4* __restrict__ pts, const int2* __restrict__ xy,
 }
 
 cudaError_t launch_pricing(const int2* xy, const int32_t* lam, const int32_t* rp, const int2* ec,
-                           int32_t n, int32_t fb, float4* pts, int2* pairs, int64_t cap,
-                           unsigned long long* count, unsigned int* tile_counter, int num_sms,
-                           cudaStream_t st) {
+                           int32_t n, int32_t fb, float4* pts, const int4* tiles, int32_t ntiles,
+                           int2* pairs, int64_t cap, unsigned long long* count,
+                           unsigned int* tile_counter, int num_sms, cudaStream_t st) {
   cudaError_t err = cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
   if (err == cudaSuccess) err = cudaMemsetAsync(tile_counter, 0, sizeof(unsigned int), st);
   if (err != cudaSuccess) return err;
@@ -133,17 +132,15 @@ cudaError_t launch_pricing(const int2* xy, const int32_t* lam, const int32_t* rp
     pricing_prep_kernel<<<blocks, threads, 0, st>>>(xy, lam, n, fb, pts);
     count_launch();
   }
-  const int ntiles = (n + kPriceTile - 1) / kPriceTile;
-  const long long total = (long long)ntiles * (ntiles + 1) / 2;
+  if (ntiles == 0) return cudaGetLastError();
   int per_sm = 0;
   err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pricing_kernel, kPriceThreads, 0);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) per_sm = 1;
   long long grid = (long long)num_sms * per_sm;
-  if (grid > total) grid = total;
-  if (grid < 1) grid = 1;
-  pricing_kernel<<<(int)grid, kPriceThreads, 0, st>>>(pts, xy, lam, rp, ec, n, fb, pairs, cap,
-                                                      count, tile_counter, ntiles);
+  if (grid > ntiles) grid = ntiles;
+  pricing_kernel<<<(int)grid, kPriceThreads, 0, st>>>(pts, xy, lam, rp, ec, n, fb, tiles, ntiles,
+                                                      pairs, cap, count, tile_counter);
   count_launch();
   return cudaGetLastError();
 }
