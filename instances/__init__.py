@@ -213,3 +213,41 @@ def make_instance(kind: str, n: int, seed: int, k: int) -> dict:
     row_ptr, col = knn_csr(xy, k)
     return {"kind": kind, "n": n, "seed": seed, "k": k, "xy": xy,
             "row_ptr": row_ptr, "col": col, "sha256": points_sha256(xy)}
+
+
+TAG_MLP_INIT = 6
+TAG_FLOATS = 7
+
+
+def uniform_floats(seed: int, count: int, lo: float, hi: float, tag: int = TAG_FLOATS) -> np.ndarray:
+    """``count`` float32 values uniform in [lo, hi): the top 24 bits of each draw
+    scaled by 2^-24 (exact in float32), then lo + (hi - lo) * u in float64."""
+    u = (draws(stream_key(seed, tag), 0, count) >> np.uint64(40)).astype(np.float64) * (2.0 ** -24)
+    return (lo + (hi - lo) * u).astype(np.float32)
+
+
+# layout of the warm-start network's flat parameter vector (float32):
+# W1 [128][16], b1 [128], W2 [128][128], b2 [128], w3 [128], b3 [1]
+MLP_SIZES = (("W1", (128, 16)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)),
+             ("w3", (128,)), ("b3", (1,)))
+MLP_NPARAMS = sum(int(np.prod(s)) for _, s in MLP_SIZES)
+
+
+def mlp_init(seed: int) -> np.ndarray:
+    """Seeded initial parameters of the 16-128-128-1 network (float32 [18817]).
+
+    Weights of a layer with fan-in m are uniform in [-sqrt(6/m), sqrt(6/m)) (He
+    uniform, for ReLU); biases are zero except b3 = 0.5 (a neutral starting
+    guess for lambda_v / s_v).
+    """
+    out = np.zeros(MLP_NPARAMS, dtype=np.float32)
+    off = 0
+    for i, (name, shape) in enumerate(MLP_SIZES):
+        cnt = int(np.prod(shape))
+        if name.startswith("W") or name == "w3":
+            a = np.sqrt(6.0 / shape[-1]) if name != "w3" else np.sqrt(6.0 / 128)
+            out[off:off + cnt] = uniform_floats(seed * 16 + i, cnt, -a, a, tag=TAG_MLP_INIT)
+        elif name == "b3":
+            out[off] = 0.5
+        off += cnt
+    return out

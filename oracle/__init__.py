@@ -102,6 +102,7 @@ def lib():
         L.or_certify.restype = C.c_int
         L.or_certify.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _u8p, _i32p, C.c_int32,
                                  C.c_int64, C.c_int32]
+        L.or_knn.argtypes = [C.c_int32, _i32p, C.c_int32, _i32p, _i64p]
         _lib = L
     return _lib
 
@@ -250,3 +251,27 @@ def certify(xy, row_ptr, col, x2, lam, fb, bound2, full_scan=True) -> int:
     return int(lib().or_certify(row_ptr.size - 1, xy.reshape(-1), row_ptr, col,
                                 np.ascontiguousarray(x2, dtype=np.uint8), _i32(lam), fb,
                                 int(bound2), int(full_scan)))
+
+
+def knn(xy, k):
+    """k nearest neighbours by exact int64 squared distance, ties by smaller index
+    (brute force, f2m_oracle.c): (nbr int32 [n, k], d2 int64 [n, k])."""
+    xy = _i32(xy)
+    n = xy.shape[0]
+    nbr = np.zeros(n * k, dtype=np.int32)
+    d2 = np.zeros(n * k, dtype=np.int64)
+    lib().or_knn(n, xy.reshape(-1), k, nbr, d2)
+    return nbr.reshape(n, k), d2.reshape(n, k)
+
+
+def knn_csr(xy, k):
+    """Symmetrised k-nearest-neighbour candidate graph (Section 5.3): u ~ w when
+    either lists the other; rows sorted by column.  (row_ptr int32, col int32)."""
+    nbr, _ = knn(xy, k)
+    n = nbr.shape[0]
+    u = np.repeat(np.arange(n, dtype=np.int64), k)
+    w = nbr.reshape(-1).astype(np.int64)
+    pairs = np.unique(np.concatenate([u * n + w, w * n + u]))
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(pairs // n, minlength=n), out=row_ptr[1:])
+    return row_ptr.astype(np.int32), (pairs % n).astype(np.int32)

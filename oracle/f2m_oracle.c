@@ -571,3 +571,29 @@ void or_result_free(or_result* r) {
   if (!r) return;
   free(r->row_ptr); free(r->col); free(r->x2); free(r->lam); free(r);
 }
+
+/* ---- k nearest neighbours (brute force) ------------------------------------ */
+
+void or_knn(int32_t n, const int32_t* xy, int32_t k, int32_t* nbr, int64_t* d2) {
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t* bi = nbr + (int64_t)i * k;
+    int64_t* bd = d2 + (int64_t)i * k;
+    int32_t cnt = 0;
+    for (int32_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      const int64_t dx = (int64_t)xy[2 * j] - xy[2 * i];
+      const int64_t dy = (int64_t)xy[2 * j + 1] - xy[2 * i + 1];
+      const int64_t d = dx * dx + dy * dy;
+      /* (d, j) belongs in the list if it precedes the current k-th entry */
+      if (cnt == k && !(d < bd[k - 1] || (d == bd[k - 1] && j < bi[k - 1]))) continue;
+      int32_t p = cnt < k ? cnt++ : k - 1;
+      while (p > 0 && (d < bd[p - 1] || (d == bd[p - 1] && j < bi[p - 1]))) {
+        bd[p] = bd[p - 1];
+        bi[p] = bi[p - 1];
+        --p;
+      }
+      bd[p] = d;
+      bi[p] = j;
+    }
+  }
+}

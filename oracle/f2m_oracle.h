@@ -131,6 +131,14 @@ void or_result_copy(const or_result* r, int32_t* row_ptr, int32_t* col, uint8_t*
                     int32_t* lam);
 void or_result_free(or_result* r);
 
+/* k nearest neighbours of every point (the candidate graph of Section 5.3 and
+ * the warm-start features): the k other points with the smallest exact squared
+ * distance dx^2 + dy^2 (int64), ties broken by smaller index; copies of the
+ * point at distance 0 count, the point itself does not.  Brute force over all
+ * pairs.  nbr[i*k + j] and d2[i*k + j], j = 0..k-1, in that order.  Needs
+ * n > k. */
+void or_knn(int32_t n, const int32_t* xy, int32_t k, int32_t* nbr, int64_t* d2);
+
 /* Certificate (independent of the solver): returns 0 when all checks pass,
  * else the number of the first failed check (see certify.c). */
 int or_certify(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int32_t* col,
