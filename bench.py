@@ -211,6 +211,10 @@ def main():
     ap.add_argument("--impl", default="gdp", choices=["gdp", "reference"])
     ap.add_argument("--ref-budget", type=float, default=6.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--instances", type=int, default=None,
+                    help="batch workloads: solve only the first N instances (profiling)")
+    ap.add_argument("--batch-shape", type=int, default=-1,
+                    help="batch workloads: fixed kernel shape instead of the autotuner's")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     rank, world, local = dist_env()
@@ -373,17 +377,20 @@ def run_batch(args, w, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     specs = batch_specs(w, rank)
+    if args.instances:
+        specs = specs[:args.instances]
     ds = [I.make_instance(*sp) for sp in specs]
+    params = f2m.f2m_default_params(batch_shape=args.batch_shape)
     insts = [(d["xy"], d["row_ptr"], d["col"]) for d in ds]
     ns = np.array([d["xy"].shape[0] for d in ds])
     nnzs = np.array([int(d["row_ptr"][-1]) for d in ds])
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
-        b = f2m.f2m_create_batch(insts, stream=stream)
+        b = f2m.f2m_create_batch(insts, params=params, stream=stream)
         f2m.f2m_solve_batch(b)
         f2m.f2m_destroy_batch(b)
-    bs = [f2m.f2m_create_batch(insts, stream=stream) for _ in range(args.steps)]
+    bs = [f2m.f2m_create_batch(insts, params=params, stream=stream) for _ in range(args.steps)]
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -420,7 +427,7 @@ def run_batch(args, w, rank, world, local):
         flush.fill_(i & 0xFF)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        b = f2m.f2m_create_batch(insts, stream=stream)
+        b = f2m.f2m_create_batch(insts, params=params, stream=stream)
         f2m.f2m_solve_batch(b)
         d2h = 0
         for j in range(len(insts)):
@@ -452,7 +459,9 @@ def run_batch(args, w, rank, world, local):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
-            "config": {"workload": workload_name(w), "instances": int(len(ns)), "sum_n": int(ns.sum()),
+            "config": {"workload": workload_name(w) if not args.instances else
+                       workload_name(w) + f" (first {len(ns)} instances)", "instances": int(len(ns)),
+                       "sum_n": int(ns.sum()), "kernel_shape": int(tot.batch_shape), "graph": bool(tot.batch_graph),
                        "sum_nnz": int(nnzs.sum()), "l2": "working set larger than L2; flushed before every step",
                        "parallelism": f"replicas x{world}"},
             "breakdown_ms": {k: statistics.median(getattr(r[1], k) for r in res)

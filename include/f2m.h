@@ -77,8 +77,11 @@ typedef struct {
   int32_t finisher;             /* 1 = exact finisher when rule (7) gives an infeasible x (default) */
   uint32_t flags;               /* F2M_FLAG_* bits; default 0 */
   int32_t gdp_lanes;            /* lanes per node in the tiled GDP kernel: 1 (one thread per node); 0 = auto */
-  int32_t gdp_ctas_per_sm;      /* tiled GDP CTAs per SM: 1 (x1024 threads), 2 (x512); 0 = auto
-                                   */
+  int32_t gdp_ctas_per_sm;      /* tiled GDP CTAs per SM: 1 (x1024 threads), 2 (x512); 0 = auto */
+  int32_t batch_shape;          /* batched GDP kernel shape (threads, copy stages, CTAs per SM):
+                                   -1 = picked by the autotuner (default), 0..4 = a fixed one */
+  int32_t batch_graph;          /* 1 = replay each batched GDP phase from a captured CUDA graph
+                                   (default), 0 = launch directly; same results */
 } f2m_params;
 
 /* f2m_params.flags: run GDP with the streaming kernel (CSR read from global
@@ -99,6 +102,8 @@ typedef struct {
   int32_t frac_bits;            /* of bound2 and lambda: F, or F+1 after the finisher */
   int32_t certified;            /* 0 none, 1 optimal on the candidate graph, 2 optimal on all pairs */
   int32_t status;               /* f2m_status of the solve */
+  int32_t batch_shape;          /* batch totals: shape index of the batched GDP kernel; else -1 */
+  int32_t batch_graph;          /* batch totals: 1 if the GDP phases ran from a captured graph */
   int32_t reserved;
   double ms_gdp;                /* device time of the GDP phases */
   double ms_pricing;            /* device time of the pricing scans */
@@ -246,6 +251,91 @@ f2m_status f2m_batch_get_x(f2m_batch* batch, int32_t i, int64_t* nnz_inout, int3
                            int32_t* col, uint8_t* x2);
 const char* f2m_batch_last_error(const f2m_batch* batch);
 void f2m_destroy_batch(f2m_batch* batch);
+
+/* ---- candidate graph and learned warm start ------------------------------------ */
+
+/* k nearest neighbours of every point (the top-N nearest-neighbour candidate
+ * graph of Section 5.3): the k other points with the smallest exact squared
+ * distance dx^2 + dy^2 (int64), ties broken by smaller index; a copy of the
+ * point (distance 0) counts, the point itself does not.
+ *   xy      [n][2] int32, host or device; coordinates in [0, 2^20).
+ *   n, k    1 <= k <= 32, n > k.
+ *   nbr     [n][k] int32, host or device (caller-owned): row v lists v's
+ *           neighbours nearest first.
+ *   d2      NULL or [n][k] int64, host or device: their squared distances.
+ *   stream  cudaStream_t as void*.
+ * Errors: INVALID_ARG, OOM, CUDA (message in f2m_last_error(NULL)). */
+f2m_status f2m_knn(const int32_t* xy, int32_t n, int32_t k, int32_t* nbr, int64_t* d2, void* stream);
+
+/* The symmetrised k-NN candidate CSR that f2m_create takes: u ~ w when either
+ * lists the other among its k nearest; rows sorted ascending.
+ *   row_ptr  [n+1] int32, host or device.
+ *   col      [2 n k] int32 (capacity), host or device; the first *nnz used.
+ *   nnz      host out: entries written.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+f2m_status f2m_knn_csr(const int32_t* xy, int32_t n, int32_t k, int32_t* row_ptr, int32_t* col,
+                       int64_t* nnz, void* stream);
+
+/* Features of the learned warm start: for node v the distances to its 16
+ * nearest other points (as f2m_knn), ascending, divided by
+ * s_v = max(1, their mean).
+ *   feat   [n][16] float, host or device.   scale  [n] float: s_v.
+ * Needs n > 16.  Errors: INVALID_ARG, OOM, CUDA. */
+f2m_status f2m_features(const int32_t* xy, int32_t n, float* feat, float* scale, void* stream);
+
+/* The warm-start network: 16 -> 128 -> 128 -> 1 with ReLU after both hidden
+ * layers; it predicts lambda_v / s_v from the features of v.  The paper lets
+ * the iteration start anywhere (Section 3); GDP from the predicted start is the
+ * same exact method and certifies the same optimum.  Products run on the
+ * tensor cores with bfloat16 inputs (features, W1, W2, the first hidden layer,
+ * and in training the hidden-layer gradients, the second hidden layer and
+ * dL/dy) and fp32 accumulation; master weights are fp32.
+ * Parameter vector (float [F2M_MLP_NPARAMS]): W1 [128][16] (output-major),
+ * b1 [128], W2 [128][128], b2 [128], w3 [128], b3. */
+#define F2M_MLP_NPARAMS 18817
+typedef struct f2m_mlp f2m_mlp;   /* opaque, library-owned */
+
+/* params: [F2M_MLP_NPARAMS] float, host or device (copied).  All work of the
+ * network runs on `stream`.  Errors: INVALID_ARG (NULL or a non-finite value),
+ * OOM, CUDA (message in f2m_last_error(NULL)). */
+f2m_status f2m_mlp_create(const float* params, void* stream, f2m_mlp** out);
+void f2m_mlp_destroy(f2m_mlp* mlp);
+/* Current fp32 parameters into out [F2M_MLP_NPARAMS] (host or device). */
+f2m_status f2m_mlp_get_params(f2m_mlp* mlp, float* out);
+const char* f2m_mlp_last_error(const f2m_mlp* mlp);
+
+/* Network output y [count] for features [count][16] (both host or device). */
+f2m_status f2m_mlp_forward(f2m_mlp* mlp, const float* feat, int64_t count, float* y);
+
+/* Loss L = mean over the count samples of (y - target)^2 and its gradient with
+ * respect to the parameters (grad [F2M_MLP_NPARAMS], loss: one float; host or
+ * device).  One forward and backward pass, no update.  count >= 1. */
+f2m_status f2m_mlp_grad(f2m_mlp* mlp, const float* feat, const float* target, int64_t count,
+                        float* grad, float* loss);
+
+typedef struct {
+  int32_t epochs;        /* passes over the samples */
+  int32_t batch;         /* samples per Adam step (>= 128) */
+  float lr;              /* Adam step size of the first step */
+  float lr_final_frac;   /* step size decays linearly to lr * lr_final_frac at the last step */
+  float beta1, beta2, eps;
+  uint64_t seed;         /* sample order: a fresh SplitMix64-keyed shuffle per epoch */
+} f2m_train_params;
+
+/* Trains the network in place with Adam (Kingma and Ba) on mean squared error:
+ * each epoch shuffles the samples and takes ceil(count / batch) steps.
+ *   feat [count][16], target [count]: host or device.
+ *   epoch_loss  NULL or [epochs] float (host): mean loss of each epoch.
+ * Adam's moments and step count carry over between calls. */
+f2m_status f2m_mlp_train(f2m_mlp* mlp, const float* feat, const float* target, int64_t count,
+                         const f2m_train_params* tp, float* epoch_loss);
+
+/* Warm start of a context: features of its points, the network, and
+ * lambda0_v = rint(2^F * s_v * y_v), clamped to |lambda0| <= 2^27, set as the
+ * context's lambda (units 2^-F).  Runs on the context's stream.
+ *   ms  NULL or out: device time of the features, network and rounding.
+ * Errors: INVALID_ARG (n <= 16), OOM, CUDA, TIMEOUT. */
+f2m_status f2m_warm_start(f2m_ctx* ctx, f2m_mlp* mlp, double* ms);
 
 /* ---- results ----------------------------------------------------------------- */
 

@@ -37,7 +37,12 @@ EXPORTS = ["f2m_default_params", "f2m_create", "f2m_destroy", "f2m_set_lambda", 
            "f2m_gdp", "f2m_price", "f2m_add_edges", "f2m_extract", "f2m_get_lambda",
            "f2m_get_bound", "f2m_get_x", "f2m_status_string", "f2m_last_error",
            "f2m_kernel_launches", "f2m_gdp_noalloc", "f2m_create_batch", "f2m_solve_batch",
-           "f2m_batch_get_lambda", "f2m_batch_get_x", "f2m_batch_last_error", "f2m_destroy_batch"]
+           "f2m_batch_get_lambda", "f2m_batch_get_x", "f2m_batch_last_error", "f2m_destroy_batch",
+           "f2m_knn", "f2m_knn_csr", "f2m_features", "f2m_mlp_create", "f2m_mlp_destroy",
+           "f2m_mlp_get_params", "f2m_mlp_last_error", "f2m_mlp_forward", "f2m_mlp_grad",
+           "f2m_mlp_train", "f2m_warm_start"]
+
+F2M_MLP_NPARAMS = 18817
 
 
 class f2m_params(C.Structure):
@@ -45,7 +50,14 @@ class f2m_params(C.Structure):
                 ("max_iters", C.c_int64), ("max_pricing_rounds", C.c_int32),
                 ("pricing", C.c_int32), ("pricing_cap", C.c_int64),
                 ("barrier_budget_cycles", C.c_int64), ("finisher", C.c_int32),
-                ("flags", C.c_uint32), ("gdp_lanes", C.c_int32), ("gdp_ctas_per_sm", C.c_int32)]
+                ("flags", C.c_uint32), ("gdp_lanes", C.c_int32), ("gdp_ctas_per_sm", C.c_int32),
+                ("batch_shape", C.c_int32), ("batch_graph", C.c_int32)]
+
+
+class f2m_train_params(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float),
+                ("lr_final_frac", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float), ("seed", C.c_uint64)]
 
 
 class f2m_info(C.Structure):
@@ -53,7 +65,8 @@ class f2m_info(C.Structure):
                 ("pricing_rounds", C.c_int64), ("edges_added", C.c_int64),
                 ("finisher_calls", C.c_int64), ("augmentations", C.c_int64),
                 ("bound2", C.c_int64), ("nnz", C.c_int64), ("frac_bits", C.c_int32),
-                ("certified", C.c_int32), ("status", C.c_int32), ("reserved", C.c_int32),
+                ("certified", C.c_int32), ("status", C.c_int32), ("batch_shape", C.c_int32),
+                ("batch_graph", C.c_int32), ("reserved", C.c_int32),
                 ("ms_gdp", C.c_double), ("ms_pricing", C.c_double), ("ms_merge", C.c_double),
                 ("ms_extract", C.c_double), ("ms_finish", C.c_double), ("ms_total", C.c_double)]
 
@@ -113,6 +126,22 @@ def load(path: str = LIB_PATH):
     L.f2m_batch_last_error.restype = C.c_char_p
     L.f2m_destroy_batch.argtypes = [vp]
     L.f2m_destroy_batch.restype = None
+    L.f2m_knn.argtypes = [vp, i32, i32, vp, vp, vp]
+    L.f2m_knn_csr.argtypes = [vp, i32, i32, vp, vp, C.POINTER(i64), vp]
+    L.f2m_features.argtypes = [vp, i32, vp, vp, vp]
+    L.f2m_mlp_create.argtypes = [vp, vp, C.POINTER(vp)]
+    L.f2m_mlp_destroy.argtypes = [vp]
+    L.f2m_mlp_destroy.restype = None
+    L.f2m_mlp_get_params.argtypes = [vp, vp]
+    L.f2m_mlp_last_error.argtypes = [vp]
+    L.f2m_mlp_last_error.restype = C.c_char_p
+    L.f2m_mlp_forward.argtypes = [vp, vp, i64, vp]
+    L.f2m_mlp_grad.argtypes = [vp, vp, vp, i64, vp, vp]
+    L.f2m_mlp_train.argtypes = [vp, vp, vp, i64, C.POINTER(f2m_train_params), vp]
+    L.f2m_warm_start.argtypes = [vp, vp, C.POINTER(C.c_double)]
+    for name in ("f2m_knn", "f2m_knn_csr", "f2m_features", "f2m_mlp_create", "f2m_mlp_get_params",
+                 "f2m_mlp_forward", "f2m_mlp_grad", "f2m_mlp_train", "f2m_warm_start"):
+        getattr(L, name).restype = C.c_int
     L.f2m_kernel_launches.argtypes = []
     L.f2m_kernel_launches.restype = C.c_int64
     for name in ("f2m_create", "f2m_set_lambda", "f2m_solve", "f2m_gdp", "f2m_price",
@@ -435,3 +464,143 @@ def f2m_destroy_batch(b: Batch) -> None:
     if b.handle:
         load().f2m_destroy_batch(b.handle)
         b.handle = None
+
+
+# ---- candidate graph and learned warm start -----------------------------------------
+
+def _gcheck(st):
+    if st != F2M_OK:
+        L = load()
+        raise F2MError(st, f"{L.f2m_status_string(st).decode()}: {L.f2m_last_error(None).decode()}")
+
+
+def f2m_knn(xy, k: int, stream=None, with_d2: bool = True):
+    """(nbr int32 [n, k], d2 int64 [n, k] or None): exact k nearest neighbours."""
+    xy = np.ascontiguousarray(xy, dtype=np.int32)
+    n = xy.shape[0]
+    nbr = np.zeros((n, k), np.int32)
+    d2 = np.zeros((n, k), np.int64) if with_d2 else None
+    _gcheck(load().f2m_knn(xy.ctypes.data, n, k, nbr.ctypes.data,
+                           d2.ctypes.data if with_d2 else None, _stream_handle(stream)))
+    return nbr, d2
+
+
+def f2m_knn_csr(xy, k: int, stream=None):
+    """(row_ptr, col) of the symmetrised k-NN candidate graph."""
+    xy = np.ascontiguousarray(xy, dtype=np.int32)
+    n = xy.shape[0]
+    rp = np.zeros(n + 1, np.int32)
+    col = np.zeros(2 * n * k, np.int32)
+    nnz = C.c_int64()
+    _gcheck(load().f2m_knn_csr(xy.ctypes.data, n, k, rp.ctypes.data, col.ctypes.data, C.byref(nnz),
+                               _stream_handle(stream)))
+    return rp, col[:nnz.value].copy()
+
+
+def f2m_features(xy, stream=None, device=None):
+    """(feat float32 [n, 16], scale float32 [n]) of the warm start; torch tensors
+    on `device` when given (xy may then be a CUDA tensor), else numpy."""
+    if device is not None:
+        import torch
+        xy_t = torch.as_tensor(np.asarray(xy, np.int32) if not hasattr(xy, "data_ptr") else xy,
+                               device=device).to(torch.int32).contiguous()
+        n = int(xy_t.shape[0])
+        feat = torch.zeros((n, 16), dtype=torch.float32, device=device)
+        scale = torch.zeros(n, dtype=torch.float32, device=device)
+        _gcheck(load().f2m_features(xy_t.data_ptr(), n, feat.data_ptr(), scale.data_ptr(),
+                                    _stream_handle(stream)))
+        return feat, scale
+    xy = np.ascontiguousarray(xy, dtype=np.int32)
+    n = xy.shape[0]
+    feat = np.zeros((n, 16), np.float32)
+    scale = np.zeros(n, np.float32)
+    _gcheck(load().f2m_features(xy.ctypes.data, n, feat.ctypes.data, scale.ctypes.data,
+                                _stream_handle(stream)))
+    return feat, scale
+
+
+class Mlp:
+    """Owns one f2m_mlp*; destroyed with the object."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.f2m_mlp_destroy(self.handle)
+            self.handle = None
+
+
+def _mcheck(m, st):
+    if st != F2M_OK:
+        L = load()
+        msg = L.f2m_mlp_last_error(m.handle) if isinstance(m, Mlp) else L.f2m_last_error(None)
+        raise F2MError(st, f"{L.f2m_status_string(st).decode()}: {(msg or b'').decode()}")
+
+
+def f2m_mlp_create(params, stream=None) -> Mlp:
+    L = load()
+    p, keep = _ptr(params if hasattr(params, "data_ptr") else np.asarray(params, np.float32))
+    h = C.c_void_p()
+    st = L.f2m_mlp_create(p, _stream_handle(stream), C.byref(h))
+    _mcheck(None, st)
+    return Mlp(h.value)
+
+
+def f2m_mlp_destroy(m: Mlp) -> None:
+    if m.handle:
+        load().f2m_mlp_destroy(m.handle)
+        m.handle = None
+
+
+def f2m_mlp_get_params(m: Mlp) -> np.ndarray:
+    out = np.zeros(F2M_MLP_NPARAMS, np.float32)
+    _mcheck(m, load().f2m_mlp_get_params(m.handle, out.ctypes.data))
+    return out
+
+
+def f2m_mlp_last_error(m: Mlp) -> str:
+    return (load().f2m_mlp_last_error(m.handle) or b"").decode()
+
+
+def f2m_mlp_forward(m: Mlp, feat):
+    """y [count]: numpy for numpy input, a CUDA tensor for a CUDA tensor input."""
+    if hasattr(feat, "data_ptr"):
+        import torch
+        feat = feat.to(torch.float32).contiguous()
+        y = torch.zeros(feat.shape[0], dtype=torch.float32, device=feat.device)
+        _mcheck(m, load().f2m_mlp_forward(m.handle, feat.data_ptr(), feat.shape[0], y.data_ptr()))
+        return y
+    feat = np.ascontiguousarray(feat, np.float32)
+    y = np.zeros(feat.shape[0], np.float32)
+    _mcheck(m, load().f2m_mlp_forward(m.handle, feat.ctypes.data, feat.shape[0], y.ctypes.data))
+    return y
+
+
+def f2m_mlp_grad(m: Mlp, feat, target):
+    """(loss, grad float32 [F2M_MLP_NPARAMS]) of the mean squared error."""
+    fp, kf = _ptr(feat if hasattr(feat, "data_ptr") else np.asarray(feat, np.float32))
+    tp, kt = _ptr(target if hasattr(target, "data_ptr") else np.asarray(target, np.float32))
+    grad = np.zeros(F2M_MLP_NPARAMS, np.float32)
+    loss = np.zeros(1, np.float32)
+    _mcheck(m, load().f2m_mlp_grad(m.handle, fp, tp, int(feat.shape[0]), grad.ctypes.data, loss.ctypes.data))
+    return float(loss[0]), grad
+
+
+def f2m_mlp_train(m: Mlp, feat, target, epochs: int = 1, batch: int = 38912, lr: float = 1e-3,
+                  lr_final_frac: float = 1.0, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+                  seed: int = 0):
+    """Trains in place; returns the mean loss of each epoch (numpy float32)."""
+    fp, kf = _ptr(feat if hasattr(feat, "data_ptr") else np.asarray(feat, np.float32))
+    tq, kt = _ptr(target if hasattr(target, "data_ptr") else np.asarray(target, np.float32))
+    tpar = f2m_train_params(epochs, batch, lr, lr_final_frac, beta1, beta2, eps, seed)
+    out = np.zeros(max(epochs, 1), np.float32)
+    _mcheck(m, load().f2m_mlp_train(m.handle, fp, tq, int(feat.shape[0]), C.byref(tpar), out.ctypes.data))
+    return out[:epochs]
+
+
+def f2m_warm_start(ctx: Ctx, m: Mlp) -> float:
+    """Sets the context's lambda from the network; returns the device ms it took."""
+    ms = C.c_double()
+    _check(ctx, load().f2m_warm_start(ctx.handle, m.handle, C.byref(ms)))
+    return ms.value

@@ -27,6 +27,7 @@ static std::atomic<long long> g_kernel_launches{0};
 
 namespace f2m {
 void count_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(long long k) { g_kernel_launches.fetch_add(k, std::memory_order_relaxed); }
 }  // namespace f2m
 
 extern "C" int64_t f2m_kernel_launches(void) { return g_kernel_launches.load(); }
@@ -116,6 +117,8 @@ extern "C" void f2m_default_params(f2m_params* p) {
   p->flags = 0;
   p->gdp_lanes = 0;
   p->gdp_ctas_per_sm = 0;
+  p->batch_shape = -1;
+  p->batch_graph = 1;
 }
 
 extern "C" const char* f2m_status_string(f2m_status s) {
@@ -162,6 +165,10 @@ f2m_status f2m::check_params_internal(const f2m_params& p) {
     return fail(nullptr, F2M_ERR_INVALID_ARG, "gdp_lanes must be 0 or 1");
   if (p.gdp_ctas_per_sm < 0 || p.gdp_ctas_per_sm > 2)
     return fail(nullptr, F2M_ERR_INVALID_ARG, "gdp_ctas_per_sm must be 0, 1 or 2");
+  if (p.batch_shape < -1 || p.batch_shape >= batch_num_shapes())
+    return fail(nullptr, F2M_ERR_INVALID_ARG, "batch_shape must be -1 or a shape index");
+  if (p.batch_graph != 0 && p.batch_graph != 1)
+    return fail(nullptr, F2M_ERR_INVALID_ARG, "batch_graph must be 0 or 1");
   if (p.max_iters < 0 || p.max_pricing_rounds < 0 || p.pricing_cap < 1 || p.barrier_budget_cycles < 0)
     return fail(nullptr, F2M_ERR_INVALID_ARG, "negative cap or budget");
   return F2M_OK;
@@ -627,6 +634,7 @@ extern "C" f2m_status f2m_solve(f2m_ctx* c, f2m_info* info_out) {
   std::memset(&info, 0, sizeof(info));
   const int32_t F = c->p.frac_bits;
   info.frac_bits = F;
+  info.batch_shape = -1;
   f2m_status status = F2M_OK;
   for (;;) {
     int64_t sw = 0;

@@ -10,6 +10,9 @@
 // x and bound are those of its own solve (the finisher is told which
 // instances it may touch).
 #include <algorithm>
+#include <array>
+#include <map>
+#include <mutex>
 #include <chrono>
 #include <cstring>
 #include <new>
@@ -30,10 +33,23 @@ struct f2m_batch {
   uint8_t* d_active = nullptr;
   unsigned long long* d_seg_ch = nullptr;
   long long* d_seg_sweeps = nullptr;
-  int4* d_tiles = nullptr;          // node tiles of the batch kernel
+  int4* d_tiles = nullptr;          // node tiles of the batch kernel (+ sentinel)
   int32_t ntiles = 0;
   int32_t grid = 0;
+  int32_t shape = -1;               // batch kernel shape in use
   int64_t tiles_version = -1;
+  // captured GDP phase (replayed on a private stream)
+  cudaStream_t gs = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int64_t graph_version = -1;       // tiles_version the graph belongs to
+  const int32_t* graph_lam = nullptr;
+  long long graph_kernels = 0;      // kernels per replay
+  bool graph_failed = false;
+  cudaEvent_t e_in = nullptr, e_out = nullptr;
+  uint8_t* h_active = nullptr;      // pinned copies read / written by the phase
+  GdpCtl* h_ctl = nullptr;
+  long long* h_sw = nullptr;
+  uint8_t* h_still = nullptr;
   long long* d_seg_b2 = nullptr;
   unsigned long long* d_seg_bad = nullptr;
   int32_t* d_tmp_a = nullptr;       // output staging
@@ -69,6 +85,14 @@ extern "C" void f2m_destroy_batch(f2m_batch* b) {
   dfree(b->d_active); dfree(b->d_seg_ch); dfree(b->d_seg_sweeps); dfree(b->d_tiles);
   dfree(b->d_seg_b2); dfree(b->d_seg_bad); dfree(b->d_tmp_a); dfree(b->d_tmp_b);
   dfree(b->d_mask); dfree(b->d_res_lam); dfree(b->d_res_rp); dfree(b->d_res_ec); dfree(b->d_res_x2);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->gs) cudaStreamDestroy(b->gs);
+  if (b->e_in) cudaEventDestroy(b->e_in);
+  if (b->e_out) cudaEventDestroy(b->e_out);
+  if (b->h_active) cudaFreeHost(b->h_active);
+  if (b->h_ctl) cudaFreeHost(b->h_ctl);
+  if (b->h_sw) cudaFreeHost(b->h_sw);
+  if (b->h_still) cudaFreeHost(b->h_still);
   delete b;
 }
 
@@ -154,12 +178,161 @@ extern "C" f2m_status f2m_create_batch(int32_t count, const int32_t* n, const in
     if (e == cudaSuccess) e = dalloc(&b->d_mask, count);
     if (e == cudaSuccess) e = dalloc(&b->d_res_lam, N);
     if (e == cudaSuccess) e = dalloc(&b->d_res_rp, (int64_t)N + count);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->gs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->e_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->e_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_active, count);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_ctl, sizeof(GdpCtl));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_sw, sizeof(long long) * count);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_still, count);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { f2m_destroy_batch(b); s = cuda_fail(nullptr, e, "create_batch: setup"); break; }
     *out = b;
   } while (0);
   dfree(d_rpl); dfree(d_coll); dfree(d_rp); dfree(d_col); dfree(d_so); dfree(d_eo); dfree(d_chk);
   return s;
+}
+
+// ---- GDP phase: tiles, kernel shape (autotuned), captured launch ----------------------
+
+// Process-wide choice of the autotuner, keyed by (SMs, instances, nodes,
+// entries / 2^16): a batch of the same shape created again skips the trials.
+static std::mutex g_tune_mu;
+static std::map<std::array<long long, 4>, int> g_tune;
+
+// tiles of at most te entries and tn nodes over the current renumbered CSR,
+// with the sentinel {n, n, -1, nnz}; replaces *d_tiles
+static f2m_status batch_tiles(f2m_batch* b, int te, int tn, int4** d_tiles, int32_t* ntiles) {
+  f2m_ctx* c = b->u;
+  GdpPlan& P = c->plan;
+  std::vector<int32_t> irp(c->n + 1);
+  CK(c, cudaMemcpyAsync(irp.data(), P.irp, sizeof(int32_t) * (c->n + 1), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  std::vector<int4> tiles;
+  for (int32_t s = 0; s < b->count; ++s) {
+    int32_t v = c->seg_off[s];
+    const int32_t end = c->seg_off[s + 1];
+    while (v < end) {
+      const int32_t start = v, e0 = irp[v];
+      while (v < end && v - start < tn && irp[v + 1] - e0 <= te) ++v;
+      if (v == start)
+        return fail(c, F2M_ERR_INVALID_ARG, "a node has more candidate edges than a batch tile holds");
+      tiles.push_back(make_int4(start, v, s, e0));
+    }
+  }
+  *ntiles = (int32_t)tiles.size();
+  tiles.push_back(make_int4(c->n, c->n, -1, irp[c->n]));
+  dfree(*d_tiles);
+  CK(c, dalloc(d_tiles, (int64_t)tiles.size()));
+  CK(c, cudaMemcpyAsync(*d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, c->st));
+  return F2M_OK;
+}
+
+// CTAs of a cooperative launch of `shape` over ntiles tiles (0: the shape does not run)
+static int32_t batch_grid(f2m_batch* b, int shape, int32_t ntiles) {
+  const int sms = b->u->num_sms;
+  int per_sm = batch_shape_blocks(shape, 1);
+  for (int it = 0; it < 4 && per_sm > 0; ++it) {  // the tile table grows as the grid shrinks
+    const int32_t G = sms * per_sm;
+    const int32_t mcap = (ntiles + G - 1) / G;
+    const int p2 = batch_shape_blocks(shape, mcap);
+    if (p2 >= per_sm) break;
+    per_sm = p2;
+  }
+  if (per_sm < 1) return 0;
+  int32_t G = sms * per_sm;
+  if (G > ntiles) G = ntiles;
+  return G;
+}
+
+// Device work of one phase on stream st: lambda into the renumbered double
+// buffer, the active flags (pinned host -> device), the persistent kernel,
+// the results back to pinned host memory, lambda back to caller order.
+static cudaError_t enqueue_phase(f2m_batch* b, cudaStream_t st, int shape, int32_t G, const int4* d_tiles,
+                                 int32_t ntiles, int64_t max_sweeps, const uint8_t* d_active_src_host_or_null) {
+  f2m_ctx* c = b->u;
+  GdpPlan& P = c->plan;
+  int32_t* l0 = P.ilam[0];
+  int32_t* l1 = P.ilam[1];
+  cudaError_t e = gather_perm(c->d_lam[c->cur], P.perm, c->n, l0, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(l1, l0, sizeof(int32_t) * c->n, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) {
+    if (d_active_src_host_or_null)
+      e = cudaMemcpyAsync(b->d_active, d_active_src_host_or_null, b->count, cudaMemcpyHostToDevice, st);
+    else
+      e = cudaMemsetAsync(b->d_active, 1, b->count, st);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_seg_ch, 0, sizeof(unsigned long long) * 3 * b->count, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_seg_sweeps, 0, sizeof(long long) * b->count, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_gdp, 0, sizeof(GdpCtl), st);
+  if (e == cudaSuccess)
+    e = launch_gdp_batch(shape, P.irp, P.iec, d_tiles, ntiles, G, b->count, b->d_active, b->d_seg_ch,
+                         b->d_seg_sweeps, l0, l1, c->p.frac_bits, c->p.damping_shift, max_sweeps, c->d_gdp,
+                         c->p.barrier_budget_cycles, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_ctl, c->d_gdp, sizeof(GdpCtl), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->h_sw, b->d_seg_sweeps, sizeof(long long) * b->count, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_still, b->d_active, b->count, cudaMemcpyDeviceToHost, st);
+  return e;
+}
+
+// Autotuner: time a few sweeps of every shape that runs on this batch (from
+// the current lambda, all instances active, nothing kept) and keep the
+// fastest per sweep.
+static f2m_status batch_autotune(f2m_batch* b) {
+  f2m_ctx* c = b->u;
+  const std::array<long long, 4> key = {c->num_sms, b->count, c->n, c->nnz >> 16};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      b->shape = it->second;
+      return F2M_OK;
+    }
+  }
+  int best = -1;
+  double best_t = 0;
+  int4* d_t = nullptr;
+  f2m_status st_out = F2M_OK;
+  for (int sh = 0; sh < batch_num_shapes() && st_out == F2M_OK; ++sh) {
+    int te = 0, tn = 0;
+    batch_shape_tile(sh, &te, &tn);
+    int32_t nt = 0;
+    st_out = batch_tiles(b, te, tn, &d_t, &nt);
+    if (st_out != F2M_OK) break;
+    const int32_t G = batch_grid(b, sh, nt);
+    if (G < 1) continue;
+    double t = 0;
+    for (int rep = 0; rep < 2; ++rep) {  // the first run only warms up
+      const int64_t sweeps = rep == 0 ? 2 : 24;
+      cudaError_t e = cudaEventRecord(c->ev0, c->st);
+      if (e == cudaSuccess) e = enqueue_phase(b, c->st, sh, G, d_t, nt, sweeps, nullptr);
+      if (e == cudaSuccess) e = cudaEventRecord(c->ev1, c->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+      if (e != cudaSuccess) {
+        st_out = cuda_fail(c, e, "batch autotune");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+      if (b->h_ctl->status & kGdpTimeout) {
+        st_out = fail(c, F2M_ERR_TIMEOUT, "device-wide barrier wait exceeded its budget");
+        break;
+      }
+      t = ms / (double)(b->h_ctl->sweeps > 0 ? b->h_ctl->sweeps : 1);
+    }
+    if (st_out == F2M_OK && (best < 0 || t < best_t)) {
+      best = sh;
+      best_t = t;
+    }
+  }
+  dfree(d_t);
+  if (st_out != F2M_OK) return st_out;
+  if (best < 0) return fail(c, F2M_ERR_CUDA, "no batch kernel shape fits this device");
+  b->shape = best;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = best;
+  return F2M_OK;
 }
 
 // One GDP phase over the segments flagged in `active` (host, one byte each);
@@ -173,65 +346,78 @@ static f2m_status batch_gdp_phase(f2m_batch* b, const std::vector<uint8_t>& acti
     CK(c, launch_halve(c->d_lam2, c->d_lam[c->cur], c->n, c->st));
     c->fb_cur = F;
   }
-  if (b->tiles_version != P.version) {  // tiles over the current renumbered CSR
-    std::vector<int32_t> irp(c->n + 1);
-    CK(c, cudaMemcpyAsync(irp.data(), P.irp, sizeof(int32_t) * (c->n + 1), cudaMemcpyDeviceToHost, c->st));
-    CK(c, cudaStreamSynchronize(c->st));
-    std::vector<int4> tiles;
-    for (int32_t s = 0; s < b->count; ++s) {
-      int32_t v = c->seg_off[s];
-      const int32_t end = c->seg_off[s + 1];
-      while (v < end) {
-        const int32_t start = v, e0 = irp[v];
-        while (v < end && v - start < kBatchTileNodes && irp[v + 1] - e0 <= kBatchTileEntries) ++v;
-        if (v == start)
-          return fail(c, F2M_ERR_INVALID_ARG, "a node has more candidate edges than a batch tile holds");
-        tiles.push_back(make_int4(start, v, s, e0));
-      }
+  if (b->tiles_version != P.version) {
+    f2m_status s = F2M_OK;
+    if (c->p.batch_shape >= 0) {
+      b->shape = c->p.batch_shape;
+    } else if (b->shape < 0) {
+      s = batch_autotune(b);
+      if (s != F2M_OK) return s;
     }
-    dfree(b->d_tiles);
-    CK(c, dalloc(&b->d_tiles, (int64_t)tiles.size()));
-    CK(c, cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, c->st));
-    int per_sm = batch_blocks_per_sm();
-    if (per_sm < 1) return fail(c, F2M_ERR_CUDA, "batch kernel does not fit an SM");
-    if (per_sm > 2) per_sm = 2;
-    if (c->p.gdp_ctas_per_sm > 0 && c->p.gdp_ctas_per_sm < per_sm) per_sm = c->p.gdp_ctas_per_sm;
-    int32_t B = c->num_sms * per_sm;
-    if (B > (int32_t)tiles.size()) B = (int32_t)tiles.size();
-    b->ntiles = (int32_t)tiles.size();
-    b->grid = B;
+    int te = 0, tn = 0;
+    batch_shape_tile(b->shape, &te, &tn);
+    s = batch_tiles(b, te, tn, &b->d_tiles, &b->ntiles);
+    if (s != F2M_OK) return s;
+    b->grid = batch_grid(b, b->shape, b->ntiles);
+    if (b->grid < 1) return fail(c, F2M_ERR_CUDA, "the batch kernel shape does not fit an SM");
     b->tiles_version = P.version;
   }
-  int32_t* l0 = P.ilam[0];
-  int32_t* l1 = P.ilam[1];
-  CK(c, gather_perm(c->d_lam[c->cur], P.perm, c->n, l0, c->st));
-  CK(c, cudaMemcpyAsync(l1, l0, sizeof(int32_t) * c->n, cudaMemcpyDeviceToDevice, c->st));
-  CK(c, cudaMemcpyAsync(b->d_active, active.data(), b->count, cudaMemcpyHostToDevice, c->st));
-  CK(c, cudaMemsetAsync(b->d_seg_ch, 0, sizeof(unsigned long long) * 3 * b->count, c->st));
-  CK(c, cudaMemsetAsync(b->d_seg_sweeps, 0, sizeof(long long) * b->count, c->st));
-  CK(c, cudaMemsetAsync(c->d_gdp, 0, sizeof(GdpCtl), c->st));
-  CK(c, cudaEventRecord(c->ev0, c->st));
-  CK(c, launch_gdp_batch(P.irp, P.iec, b->d_tiles, b->ntiles, b->grid, b->count, b->d_active,
-                         b->d_seg_ch, b->d_seg_sweeps, l0, l1, F, c->p.damping_shift, c->p.max_iters,
-                         c->d_gdp, c->p.barrier_budget_cycles, c->st));
-  CK(c, cudaEventRecord(c->ev1, c->st));
-  GdpCtl h{};
-  std::vector<long long> sw(b->count);
-  std::vector<uint8_t> still(b->count);
-  CK(c, cudaMemcpyAsync(&h, c->d_gdp, sizeof(h), cudaMemcpyDeviceToHost, c->st));
-  CK(c, cudaMemcpyAsync(sw.data(), b->d_seg_sweeps, sizeof(long long) * b->count, cudaMemcpyDeviceToHost, c->st));
-  CK(c, cudaMemcpyAsync(still.data(), b->d_active, b->count, cudaMemcpyDeviceToHost, c->st));
+  std::memcpy(b->h_active, active.data(), b->count);
+  const bool graph = c->p.batch_graph && !b->graph_failed;
+  if (graph && (!b->gexec || b->graph_version != b->tiles_version || b->graph_lam != c->d_lam[c->cur])) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    const long long before = f2m_kernel_launches();
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->gs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e2 = enqueue_phase(b, b->gs, b->shape, b->grid, b->d_tiles, b->ntiles, c->p.max_iters,
+                                     b->h_active);
+      if (e2 == cudaSuccess)
+        e2 = launch_batch_scatter_final(P.ilam[0], P.ilam[1], c->d_gdp, P.perm, c->n, c->d_lam[c->cur], b->gs);
+      e = cudaStreamEndCapture(b->gs, &g);
+      if (e == cudaSuccess && e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    b->graph_kernels = f2m_kernel_launches() - before;
+    count_launches(-b->graph_kernels);  // captured, not launched
+    if (e != cudaSuccess) {  // capture not available here: launch directly from now on
+      cudaGetLastError();
+      if (b->gexec) cudaGraphExecDestroy(b->gexec);
+      b->gexec = nullptr;
+      b->graph_failed = true;
+    } else {
+      b->graph_version = b->tiles_version;
+      b->graph_lam = c->d_lam[c->cur];
+    }
+  }
+  if (graph && b->gexec) {
+    CK(c, cudaEventRecord(b->e_in, c->st));
+    CK(c, cudaStreamWaitEvent(b->gs, b->e_in, 0));
+    CK(c, cudaEventRecord(c->ev0, b->gs));
+    CK(c, cudaGraphLaunch(b->gexec, b->gs));
+    CK(c, cudaEventRecord(c->ev1, b->gs));
+    CK(c, cudaEventRecord(b->e_out, b->gs));
+    CK(c, cudaStreamWaitEvent(c->st, b->e_out, 0));
+    count_launches(b->graph_kernels);
+  } else {
+    CK(c, cudaEventRecord(c->ev0, c->st));
+    CK(c, enqueue_phase(b, c->st, b->shape, b->grid, b->d_tiles, b->ntiles, c->p.max_iters, b->h_active));
+    CK(c, launch_batch_scatter_final(P.ilam[0], P.ilam[1], c->d_gdp, P.perm, c->n, c->d_lam[c->cur], c->st));
+    CK(c, cudaEventRecord(c->ev1, c->st));
+  }
   CK(c, cudaStreamSynchronize(c->st));
   float t_ms = 0.f;
   cudaEventElapsedTime(&t_ms, c->ev0, c->ev1);
   if (ms) *ms += t_ms;
+  const GdpCtl h = *b->h_ctl;
   if (h.status & kGdpTimeout) return fail(c, F2M_ERR_TIMEOUT, "device-wide barrier wait exceeded its budget");
   if (h.status & kGdpOverflow) return fail(c, F2M_ERR_OVERFLOW, "|lambda| reached 2^29 in some instance");
   for (int32_t s = 0; s < b->count; ++s) {
     if (!active[s]) continue;
-    sweeps_out[s] += still[s] ? h.sweeps : sw[s];  // unfrozen ones ran to the cap
+    sweeps_out[s] += b->h_still[s] ? h.sweeps : b->h_sw[s];  // unfrozen ones ran to the cap
   }
-  CK(c, scatter_perm(h.sweeps & 1 ? l1 : l0, P.perm, c->n, c->d_lam[c->cur], c->st));
   return F2M_OK;
 }
 
@@ -447,6 +633,8 @@ extern "C" f2m_status f2m_solve_batch(f2m_batch* b, f2m_info* info_out, f2m_info
   }
   tot.frac_bits = -1;  // per instance
   tot.nnz = b->res_used;
+  tot.batch_shape = b->shape;
+  tot.batch_graph = b->gexec != nullptr ? 1 : 0;
   tot.certified = 2;
   for (int32_t s = 0; s < K; ++s) {
     tot.certified = std::min(tot.certified, certified[s]);
@@ -469,6 +657,7 @@ extern "C" f2m_status f2m_solve_batch(f2m_batch* b, f2m_info* info_out, f2m_info
       f.certified = certified[s];
       f.status = status == F2M_OK ? inst_status[s] : status;
       f.nnz = b->res_nnz[s];
+      f.batch_shape = -1;
     }
   }
   if (total_out) *total_out = tot;

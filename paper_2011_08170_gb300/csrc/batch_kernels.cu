@@ -37,73 +37,217 @@ __device__ __forceinline__ int segment_of(const int32_t* seg_off, int nseg, int 
   return lo;
 }
 
-// Tiles: contiguous node ranges of one segment with at most kTileEntries
-// entries and kTileNodes nodes, dealt round-robin to the CTAs every sweep.
-// Per tile the CTA (1) loads every entry with all its threads (many independent
-// loads in flight), forms w_e = c_e 2^F - lambda_u and stages it in shared
-// memory, then (2) one thread per node takes the top-3 of w_e - lambda_v over
-// its row.  Freezing is decided by block 0 after barrier t from the per-segment
-// changed counts of sweep t and seen by the other blocks from sweep t+2 on (a
-// segment converged at sweep t computes one more sweep, which changes nothing).
-template <int T>
-__global__ void __launch_bounds__(T)
+// Tiles: contiguous node ranges of one segment with at most TE entries and TN
+// nodes (per kernel shape); tile k goes to CTA k mod G every sweep.
+// The tile table has a sentinel after the last tile, so tile k's entries are
+// [tiles[k].w, tiles[k+1].w) and its nodes [tiles[k].x, tiles[k].y).
+//
+// A tile's {col, cost} entries and row offsets are moved into shared memory by
+// the bulk-copy engine (cp.async.bulk, completion counted in bytes on an
+// mbarrier), S stages deep: while the CTA works on one tile the next S-1 are in
+// flight.  The copies do not depend on lambda, so the issuing thread runs ahead
+// across the end of a sweep (the grid barrier) into the next one.  Per tile:
+// (1) all threads form w_e = c_e 2^F - lambda_u (lambda gathered from L2) into
+// shared memory, (2) one thread per node takes the top-3 of w_e - lambda_v
+// (Eq. 9) and applies Eq. 10.  Segments that changed nothing in sweep t are
+// frozen by block 0 after barrier t; a CTA may still run a frozen segment's
+// tile once more from a stale flag, which rewrites the same fixed point.
+// bytes of one copy stage: entries and row offsets, each rounded out to 16 bytes
+__host__ __device__ constexpr int stage_ec_bytes(int te) { return (te + 2) * 8; }
+__host__ __device__ constexpr int stage_rp_bytes(int tn) { return (tn + 8) * 4; }
+__host__ __device__ constexpr int stage_bytes(int te, int tn) { return stage_ec_bytes(te) + stage_rp_bytes(tn); }
+
+__device__ __forceinline__ void mbar_init1(uint32_t mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// bounded wait: false after `limit` polls
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, long long limit) {
+  for (long long i = 0; i < limit; ++i)
+    if (mbar_try(mbar, parity)) return true;
+  return false;
+}
+// L2 policies: the CSR stream (larger than L2, read once per sweep) is evicted
+// first so that lambda, gathered at random within an instance, stays resident
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar,
+                                         uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(mbar), "l"(pol)
+      : "memory");
+}
+// lambda load that bypasses L1 (other SMs rewrite it between sweeps) and is kept in L2
+__device__ __forceinline__ int ld_lam(const int32_t* p, uint64_t pol) {
+  int v;
+  asm volatile("ld.global.cg.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol) : "memory");
+  return v;
+}
+
+constexpr long long kBulkWaitLimit = 1LL << 24;
+
+template <int T, int S, int TE, int TN, int MINB>
+__global__ void __launch_bounds__(T, MINB)
 gdp_batch_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ iec,
                  const int4* __restrict__ tiles, int32_t ntiles, int32_t nseg, uint8_t* active,
                  unsigned long long* seg_ch, long long* seg_sweeps, int32_t* lam0, int32_t* lam1,
-                 int32_t F, int32_t shift, long long max_sweeps, GdpCtl* ctl, long long budget) {
-  __shared__ int s_w[kBatchTileEntries];
-  __shared__ int s_rp[kBatchTileNodes + 1];
+                 int32_t F, int32_t shift, long long max_sweeps, GdpCtl* ctl, long long budget, int32_t mcap) {
+  constexpr int kStageEcBytes = stage_ec_bytes(TE);
+  constexpr int kStageBytes = stage_bytes(TE, TN);
+  static_assert(kStageBytes % 16 == 0 && kStageEcBytes % 16 == 0, "stage alignment");
+  extern __shared__ __align__(128) uint8_t smem[];
   __shared__ unsigned s_tot[32];
   __shared__ int s_ovf[32];
   __shared__ unsigned s_tile_ch;
-  __shared__ int s_stop, s_act;
-  const int tid = threadIdx.x, b = blockIdx.x;
+  __shared__ int s_stop, s_hdr[S];
+  __shared__ __align__(8) unsigned long long s_full[S];
+  const int tid = threadIdx.x, b = blockIdx.x, G = gridDim.x;
   const int lane = tid & 31, warp = tid >> 5;
   constexpr int nwarps = T / 32;
   const long long div = 1LL << shift;
   volatile GdpCtl* vc = ctl;
   volatile uint8_t* vact = active;
 
+  int* s_w = reinterpret_cast<int*>(smem + S * kStageBytes);
+  int4* s_mt = reinterpret_cast<int4*>(smem + S * kStageBytes + TE * 4);
+  int* s_me1 = reinterpret_cast<int*>(s_mt + mcap);
+  uint8_t* s_act = reinterpret_cast<uint8_t*>(s_me1 + mcap);
+  const int my = b < ntiles ? (ntiles - 1 - b) / G + 1 : 0;  // tiles of this CTA
+
+  for (int i = tid; i < my; i += T) {
+    const int k = b + i * G;
+    const int4 tl = tiles[k];
+    s_mt[i] = tl;
+    s_me1[i] = tiles[k + 1].w;
+    s_act[i] = vact[tl.z];
+  }
+  if (tid == 0) {
+    for (int st = 0; st < S; ++st) mbar_init1((uint32_t)__cvta_generic_to_shared(&s_full[st]));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  const uint64_t pol_stream = policy_evict_first(), pol_lam = policy_evict_last();
+  // issuing thread: next tile of its own walk over (sweep, my tile)
+  int p_i = 0;
+  auto produce = [&](long long q) {
+    const int st = (int)(q % S);
+    for (;;) {
+      if (p_i >= my) {  // end of a sweep
+        s_hdr[st] = -1;
+        p_i = 0;
+        return;
+      }
+      const int i = p_i++;
+      if (!s_act[i]) continue;
+      const int4 tl = s_mt[i];
+      const int e1 = s_me1[i];
+      const int a0 = tl.w & ~1, a1 = (e1 + 1) & ~1;
+      const int r0 = tl.x & ~3, r1 = (tl.y + 4) & ~3;
+      const uint32_t ecb = (uint32_t)(a1 - a0) * 8u, rpb = (uint32_t)(r1 - r0) * 4u;
+      const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&s_full[st]);
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(smem + st * kStageBytes);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(mb, ecb + rpb);
+      bulk_g2s(dst, iec + a0, ecb, mb, pol_stream);
+      bulk_g2s(dst + kStageEcBytes, irp + r0, rpb, mb, pol_stream);
+      s_hdr[st] = i;
+      return;
+    }
+  };
+
+  long long q = 0;  // slots issued
+  if (tid == 0)
+    for (; q < S - 1; ++q) produce(q);
+  uint32_t phase_bits = 0;  // completed uses of each stage, mod 2
   long long t = 0;
-  for (; t < max_sweeps; ++t) {
+  unsigned ch = 0;
+  int ovf = 0;
+  bool timed_out = false;  // this thread's wait for slot j_end gave up
+  long long j_end = 0;
+  if (tid == 0) s_stop = 0;
+  __syncthreads();
+
+  for (long long j = 0;; ++j) {
+    if (tid == 0) produce(q++);
+    const int st = (int)(j % S);
+    const int i = s_hdr[st];
     const int32_t* lin = (t & 1) ? lam1 : lam0;
     int32_t* lout = (t & 1) ? lam0 : lam1;
-    unsigned ch = 0;
-    int ovf = 0;
-    for (int k = b; k < ntiles; k += gridDim.x) {
-      const int4 tl = tiles[k];  // nodes [x, y), segment z, first entry w
-      if (tid == 0) { s_act = vact[tl.z]; s_tile_ch = 0; }
-      __syncthreads();
-      if (!s_act) { __syncthreads(); continue; }
-      const int v0 = tl.x, nv = tl.y - tl.x, E0 = tl.w;
-      const int ne = __ldg(irp + tl.y) - E0;
-      for (int i = tid; i <= nv; i += T) s_rp[i] = __ldg(irp + v0 + i) - E0;
+    if (i >= 0) {
+      const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&s_full[st]);
+      const bool ok = mbar_wait_bounded(mb, (phase_bits >> st) & 1u, kBulkWaitLimit);
+      phase_bits ^= 1u << st;
+      const int4 tl = s_mt[i];
+      const int v0 = tl.x, nv = tl.y - tl.x, E0 = tl.w, ne = s_me1[i] - tl.w;
+      const int2* sec = reinterpret_cast<const int2*>(smem + st * kStageBytes) + (E0 - (E0 & ~1));
+      const int* srp = reinterpret_cast<const int*>(smem + st * kStageBytes + kStageEcBytes) + (v0 - (v0 & ~3));
+      if (tid == 0) s_tile_ch = 0;
+      if (ok) {
 #pragma unroll 4
-      for (int e = tid; e < ne; e += T) {
-        const int2 q = __ldg(iec + E0 + e);
-        s_w[e] = (q.y << F) - ld_cg(lin + q.x);
-      }
-      __syncthreads();
-      for (int i = tid; i < nv; i += T) {
-        const int lv = ld_cg(lin + v0 + i);
-        int a = INT_MAX, bb = INT_MAX, c = INT_MAX;
-        for (int e = s_rp[i]; e < s_rp[i + 1]; ++e) top3_insert_minmax(s_w[e] - lv, a, bb, c);  // Eq. 9
-        const long long d = ((long long)bb + (long long)c) / div;  // Eq. 10, truncated toward 0
-        const long long nl = (long long)lv + d;
-        ovf |= (nl >= kLamLimit || nl <= -kLamLimit);
-        lout[v0 + i] = (int32_t)nl;
-        if (d != 0) {
-          atomicAdd(&s_tile_ch, 1u);
-          ++ch;
+        for (int e = tid; e < ne; e += T) {
+          const int2 w = sec[e];
+          s_w[e] = (w.y << F) - ld_lam(lin + w.x, pol_lam);
         }
       }
       __syncthreads();
+      if (ok) {
+        for (int k = tid; k < nv; k += T) {
+          const int lv = ld_lam(lin + v0 + k, pol_lam);
+          int a = INT_MAX, bb = INT_MAX, c = INT_MAX;
+          const int e_end = srp[k + 1] - E0;
+          for (int e = srp[k] - E0; e < e_end; ++e) top3_insert_minmax(s_w[e] - lv, a, bb, c);  // Eq. 9
+          const long long d = ((long long)bb + (long long)c) / div;  // Eq. 10, truncated toward 0
+          const long long nl = (long long)lv + d;
+          ovf |= (nl >= kLamLimit || nl <= -kLamLimit);
+          lout[v0 + k] = (int32_t)nl;
+          if (d != 0) {
+            atomicAdd(&s_tile_ch, 1u);
+            ++ch;
+          }
+        }
+      }
+      if (!ok) s_stop = 1;  // a copy never landed: stop after this tile
+      __syncthreads();
       if (tid == 0 && s_tile_ch)
         atomicAdd(&seg_ch[(size_t)tl.z * 3 + (t % 3)], (unsigned long long)s_tile_ch);
+      if (s_stop) {
+        if (tid == 0) atomicOr(&ctl->status, kGdpTimeout);
+        timed_out = !ok;
+        j_end = j;
+        break;
+      }
+      continue;
     }
+    // end of sweep t: totals, grid barrier, freezes, stop test
     ch = warp_sum_u(ch);
     ovf = __any_sync(0xffffffffu, ovf);
-    if (lane == 0) { s_tot[warp] = ch; s_ovf[warp] = ovf; }
+    if (lane == 0) {
+      s_tot[warp] = ch;
+      s_ovf[warp] = ovf;
+    }
     __syncthreads();
     if (warp == 0) {
       unsigned y = lane < nwarps ? s_tot[lane] : 0;
@@ -115,58 +259,150 @@ gdp_batch_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ iec,
         if (o) atomicOr(&ctl->status, kGdpOverflow);
       }
     }
-    if (!grid_barrier_counted(&ctl->bar_count, (unsigned)(t + 1) * gridDim.x, budget)) {
+    ch = 0;
+    ovf = 0;
+    bool stop = false;
+    if (!grid_barrier_counted(&ctl->bar_count, (unsigned)(t + 1) * G, budget)) {
       if (tid == 0) atomicOr(&ctl->status, kGdpTimeout);
-      break;
+      stop = true;
     }
-    if (b == 0) {  // coordinator: freezes and slot resets for every segment
-      for (int s = tid; s < nseg; s += T) {
-        volatile unsigned long long* slot = seg_ch + (size_t)s * 3;
-        if (vact[s] && slot[t % 3] == 0) {
-          vact[s] = 0;
-          seg_sweeps[s] = t + 1;
+    if (b == 0 && !stop) {  // coordinator: freezes and slot resets for every segment
+      for (int sgi = tid; sgi < nseg; sgi += T) {
+        volatile unsigned long long* slot = seg_ch + (size_t)sgi * 3;
+        if (vact[sgi] && slot[t % 3] == 0) {
+          vact[sgi] = 0;
+          seg_sweeps[sgi] = t + 1;
         }
         slot[(t + 2) % 3] = 0;
       }
     }
+    for (int k = tid; k < my; k += T) s_act[k] = vact[s_mt[k].z];
     if (tid == 0) {
       const unsigned long long chg = vc->slot_ch[t % 3];
-      const int st = vc->status;
+      const int stv = vc->status;
       if (b == 0) {
         vc->slot_ch[(t + 2) % 3] = 0;
         vc->sweeps = t + 1;
         vc->fixed_point = (chg == 0);
       }
-      s_stop = (st != 0) || (chg == 0);
+      s_stop = stop || (stv != 0) || (chg == 0) || (t + 1 >= max_sweeps);
     }
     __syncthreads();
-    if (s_stop) break;
+    if (s_stop) {
+      j_end = j;
+      break;
+    }
+    ++t;
+  }
+  // Wait (bounded) for the copies still in flight before the shared memory goes
+  // away: the issued slots after the last one consumed, and that one too if
+  // its own wait gave up.  Consecutive slots use distinct stages, and a stage's
+  // parity bit counts the uses already consumed.
+  if (tid == 0) {
+    for (long long sl = timed_out ? j_end : j_end + 1; sl < q; ++sl) {
+      const int stg = (int)(sl % S);
+      if (s_hdr[stg] < 0) continue;
+      uint32_t par = (phase_bits >> stg) & 1u;
+      if (sl == j_end) par ^= 1u;  // already toggled when it was consumed
+      mbar_wait_bounded((uint32_t)__cvta_generic_to_shared(&s_full[stg]), par, kBulkWaitLimit);
+    }
   }
 }
 
-constexpr int kBatchThreads = 512;
+// Shapes of the batch kernel the autotuner picks from: threads per CTA, copy
+// stages, CTAs per SM, tile entries, tile nodes.
+struct BatchShapeDef {
+  int threads, stages, per_sm, te, tn;
+};
+constexpr BatchShapeDef kBatchShapes[] = {
+    {512, 2, 2, 4096, 1536}, {512, 2, 4, 2048, 768}, {256, 2, 4, 2048, 768}, {512, 3, 3, 2048, 768},
+    {1024, 3, 1, 4096, 1536}, {256, 2, 6, 1024, 384}, {512, 4, 2, 2048, 768}};
+constexpr int kNumBatchShapes = (int)(sizeof(kBatchShapes) / sizeof(kBatchShapes[0]));
 
-cudaError_t launch_gdp_batch(const int32_t* irp, const int2* iec, const int4* tiles, int32_t ntiles,
-                             int32_t B, int32_t nseg, uint8_t* active, unsigned long long* seg_ch,
+#define F2M_BATCH_SHAPE(i)                                                                          \
+  (const void*)gdp_batch_kernel<kBatchShapes[i].threads, kBatchShapes[i].stages, kBatchShapes[i].te, \
+                                kBatchShapes[i].tn, kBatchShapes[i].per_sm>
+
+static const void* batch_kernel_of(int shape) {
+  switch (shape) {
+    case 0: return F2M_BATCH_SHAPE(0);
+    case 1: return F2M_BATCH_SHAPE(1);
+    case 2: return F2M_BATCH_SHAPE(2);
+    case 3: return F2M_BATCH_SHAPE(3);
+    case 4: return F2M_BATCH_SHAPE(4);
+    case 5: return F2M_BATCH_SHAPE(5);
+    case 6: return F2M_BATCH_SHAPE(6);
+  }
+  return nullptr;
+}
+#undef F2M_BATCH_SHAPE
+
+// dynamic shared memory: stages, w buffer, per-CTA tile table (int4 + int + flag)
+static size_t batch_smem(int shape, int mcap) {
+  const BatchShapeDef& d = kBatchShapes[shape];
+  return (size_t)d.stages * stage_bytes(d.te, d.tn) + (size_t)d.te * 4 + (size_t)mcap * 21 + 16;
+}
+
+int batch_shape_tile(int shape, int* te, int* tn) {
+  if (shape < 0 || shape >= kNumBatchShapes) return 0;
+  *te = kBatchShapes[shape].te;
+  *tn = kBatchShapes[shape].tn;
+  return 1;
+}
+
+int batch_num_shapes() { return kNumBatchShapes; }
+
+int batch_shape_blocks(int shape, int mcap) {
+  if (shape < 0 || shape >= kNumBatchShapes) return 0;
+  const void* k = batch_kernel_of(shape);
+  const size_t sm = batch_smem(shape, mcap);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kBatchShapes[shape].threads, sm) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm < kBatchShapes[shape].per_sm ? per_sm : kBatchShapes[shape].per_sm;
+}
+
+cudaError_t launch_gdp_batch(int shape, const int32_t* irp, const int2* iec, const int4* tiles, int32_t ntiles,
+                             int32_t G, int32_t nseg, uint8_t* active, unsigned long long* seg_ch,
                              long long* seg_sweeps, int32_t* lam0, int32_t* lam1, int32_t F,
                              int32_t shift, int64_t max_sweeps, GdpCtl* ctl, long long budget,
                              cudaStream_t st) {
+  if (shape < 0 || shape >= kNumBatchShapes || G < 1) return cudaErrorInvalidValue;
   long long ms = max_sweeps;
+  int32_t mcap = (ntiles + G - 1) / G;
+  if (mcap < 1) mcap = 1;
+  const size_t sm = batch_smem(shape, mcap);
+  const void* k = batch_kernel_of(shape);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
   void* args[] = {(void*)&irp, (void*)&iec, (void*)&tiles, (void*)&ntiles, (void*)&nseg,
                   (void*)&active, (void*)&seg_ch, (void*)&seg_sweeps, (void*)&lam0, (void*)&lam1,
-                  (void*)&F, (void*)&shift, (void*)&ms, (void*)&ctl, (void*)&budget};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)gdp_batch_kernel<kBatchThreads>, dim3(B),
-                                              dim3(kBatchThreads), args, 0, st);
+                  (void*)&F, (void*)&shift, (void*)&ms, (void*)&ctl, (void*)&budget, (void*)&mcap};
+  e = cudaLaunchCooperativeKernel(k, dim3(G), dim3(kBatchShapes[shape].threads), args, sm, st);
   count_launch();
   return e;
 }
 
-int batch_blocks_per_sm() {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gdp_batch_kernel<kBatchThreads>,
-                                                    kBatchThreads, 0) != cudaSuccess)
-    return 0;
-  return per_sm;
+// dst[perm[i]] = (ctl->sweeps odd ? lam1 : lam0)[i]: the buffer a GDP phase
+// ended in, chosen on the device so that a captured phase needs no host decision
+__global__ void batch_scatter_final_kernel(const int32_t* __restrict__ lam0, const int32_t* __restrict__ lam1,
+                                           const GdpCtl* ctl, const int32_t* __restrict__ perm, int32_t n,
+                                           int32_t* __restrict__ dst) {
+  const int32_t* src = (ctl->sweeps & 1) ? lam1 : lam0;
+  F2M_GRID_STRIDE(i, n) dst[perm[i]] = src[i];
+}
+
+cudaError_t launch_batch_scatter_final(const int32_t* lam0, const int32_t* lam1, const GdpCtl* ctl,
+                                       const int32_t* perm, int32_t n, int32_t* dst, cudaStream_t st) {
+  batch_scatter_final_kernel<<<grid_for(n, 256), 256, 0, st>>>(lam0, lam1, ctl, perm, n, dst);
+  count_launch();
+  return cudaGetLastError();
 }
 
 // ---- segmented helpers -------------------------------------------------------------

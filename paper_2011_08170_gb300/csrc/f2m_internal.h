@@ -57,12 +57,15 @@ enum CheckBits {
 
 // process-wide count of kernel launches made by this library (api.cu)
 void count_launch();
+void count_launches(long long k);  // k launches replayed from a captured graph
 
 // ---- launchers (each enqueues on `st`) -------------------------------------
 
 // validation of the input CSR and points; ctl must be zeroed (first_bad = INT_MAX)
 cudaError_t launch_check(const int2* xy, const int32_t* rp, const int32_t* col, int32_t n,
                          int64_t nnz, CheckCtl* ctl, cudaStream_t st);
+// coordinates in [0, 2^20) (flag kBadCoord); ctl zeroed with first_bad = INT_MAX
+cudaError_t launch_check_points(const int2* xy, int32_t n, CheckCtl* ctl, cudaStream_t st);
 // ec[e] = {col[e], c(row(e), col[e])}
 cudaError_t launch_build_ec(const int2* xy, const int32_t* rp, const int32_t* col, int32_t n,
                             int2* ec, cudaStream_t st);
@@ -176,15 +179,20 @@ cudaError_t fin_scatter(const GdpPlan& p, const int32_t* rp, const uint8_t* x_in
                         const int32_t* seg_off, int32_t nseg, const uint8_t* include,
                         cudaStream_t st);
 // ---- batched solver (batch_kernels.cu) --------------------------------------------
-constexpr int kBatchTileEntries = 4096;  // entries per tile of the batch kernel
-constexpr int kBatchTileNodes = 1536;    // nodes per tile
-// tiles {first node, end node, segment, first entry} over the renumbered CSR
-cudaError_t launch_gdp_batch(const int32_t* irp, const int2* iec, const int4* tiles, int32_t ntiles,
-                             int32_t B, int32_t nseg, uint8_t* active, unsigned long long* seg_ch,
+// tiles {first node, end node, segment, first entry} over the renumbered CSR,
+// followed by a sentinel {n, n, -1, nnz}; one cooperative launch of G CTAs of
+// the given shape (see batch_kernels.cu)
+int batch_num_shapes();
+// lambda of the buffer a batch GDP phase ended in, scattered to caller order
+cudaError_t launch_batch_scatter_final(const int32_t* lam0, const int32_t* lam1, const GdpCtl* ctl,
+                                       const int32_t* perm, int32_t n, int32_t* dst, cudaStream_t st);
+int batch_shape_blocks(int shape, int mcap);  // CTAs per SM, 0 if the shape does not run
+int batch_shape_tile(int shape, int* te, int* tn);  // tile entries and nodes of a shape
+cudaError_t launch_gdp_batch(int shape, const int32_t* irp, const int2* iec, const int4* tiles, int32_t ntiles,
+                             int32_t G, int32_t nseg, uint8_t* active, unsigned long long* seg_ch,
                              long long* seg_sweeps, int32_t* lam0, int32_t* lam1, int32_t F,
                              int32_t shift, int64_t max_sweeps, GdpCtl* ctl, long long budget,
                              cudaStream_t st);
-int batch_blocks_per_sm();
 cudaError_t launch_batch_extract_bound(const int32_t* rp, const int2* ec, const int32_t* lam,
                                        int32_t n, int32_t fb, const int32_t* seg_off, int32_t nseg,
                                        uint8_t* x2, long long* seg_b2, unsigned long long* seg_bad,
@@ -209,4 +217,42 @@ int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t*
                   const int32_t* seg_off, int32_t nseg, int32_t threads, int64_t* augmentations,
                   FinisherWork* w);
 
+
+// ---- k nearest neighbours and warm-start features (knn.cu) -------------------------
+constexpr int kKnnMax = 32;    // largest k of the k-NN kernel
+constexpr int kFeatures = 16;  // neighbour distances per node in the warm-start features
+// exact k-NN lists (ties by index): nbr [n][k], d2 [n][k] (may be NULL); device pointers
+cudaError_t knn_device(const int2* d_xy, int32_t n, int32_t k, int32_t* d_nbr, long long* d_d2,
+                       cudaStream_t st);
+// symmetrised k-NN CSR; d_col holds up to 2 n k entries; *nnz_out on the host (synchronises)
+cudaError_t knn_csr_device(const int2* d_xy, int32_t n, int32_t k, int32_t* d_row_ptr, int32_t* d_col,
+                           int64_t* nnz_out, cudaStream_t st);
+// feat [n][16] = sorted 16-NN distances / s, s = max(1, their mean)
+cudaError_t features_device(const int2* d_xy, int32_t n, float* d_feat, float* d_scale, cudaStream_t st);
+
+// ---- warm-start network (mlp.cu) ----------------------------------------------------
+// flat fp32 parameters: W1 [128][16], b1 [128], W2 [128][128], b2 [128], w3 [128], b3
+constexpr int kOW1 = 0, kOb1 = 2048, kOW2 = 2176, kOb2 = 18560, kOw3 = 18688, kOb3 = 18816;
+constexpr int kMlpParams = 18817;
+constexpr int kImgW1Bytes = 128 * 16 * 2;   // bf16 operand image of W1
+constexpr int kImgW2Bytes = 128 * 128 * 2;  // bf16 operand image of W2 (and of W2^T)
+constexpr int kMlpImgBytes = kImgW1Bytes + 2 * kImgW2Bytes;
+constexpr int kLambda0Limit = 1 << 27;      // |lambda0| clamp of the warm start
+struct MlpAdam {
+  float lr, beta1, beta2, eps, lr_final_frac;
+  long long total_steps;  // linear decay of lr to lr * lr_final_frac over this many steps
+  long long log_base;     // the loss of step t goes to loss_log[t - 1 - log_base]
+};
+cudaError_t mlp_pack(const float* master, uint8_t* img, cudaStream_t st);
+int mlp_grid(int num_sms, long long count);
+cudaError_t mlp_forward(const uint8_t* img, const float* master, const float* feat, long long count,
+                        float* y, const float* scale, int32_t* lam, int32_t F, int num_sms, int* status,
+                        cudaStream_t st);
+cudaError_t mlp_train_launch(const uint8_t* img, const float* master, const float* feat, const float* target,
+                             const int32_t* perm, long long s0, long long count, float two_over_b,
+                             float* partial, int grid, long long* step_ctr, int* status, cudaStream_t st);
+cudaError_t mlp_reduce_launch(const float* partial, int nparts, float* grad, float* master, float* m1,
+                              float* m2, uint8_t* img, const long long* step_ctr, const MlpAdam& hp,
+                              float* loss_log, cudaStream_t st);
+cudaError_t mlp_perm_keys(uint64_t key, long long n, uint64_t* keys, int32_t* idx, cudaStream_t st);
 }  // namespace f2m

@@ -36,6 +36,14 @@ __global__ void check_rowptr_kernel(const int2* xy, const int32_t* rp, int32_t n
   }
 }
 
+// coordinates only (for calls that take points without a graph)
+__global__ void check_points_kernel(const int2* xy, int32_t n, CheckCtl* ctl) {
+  F2M_GRID_STRIDE(v, n) {
+    const int2 p = xy[v];
+    if (p.x < 0 || p.y < 0 || p.x >= kCoordLimit || p.y >= kCoordLimit) flag(ctl, kBadCoord, v);
+  }
+}
+
 // pass 2 (row offsets valid): columns, order, self-loops, degree, symmetry
 __global__ void check_rows_kernel(const int32_t* rp, const int32_t* col, int32_t n, CheckCtl* ctl) {
   F2M_GRID_STRIDE(v, n) {
@@ -63,6 +71,12 @@ __global__ void check_rows_kernel(const int32_t* rp, const int32_t* col, int32_t
       }
     }
   }
+}
+
+cudaError_t launch_check_points(const int2* xy, int32_t n, CheckCtl* ctl, cudaStream_t st) {
+  check_points_kernel<<<grid_for(n, 256), 256, 0, st>>>(xy, n, ctl);
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_check(const int2* xy, const int32_t* rp, const int32_t* col, int32_t n,

@@ -1,0 +1,235 @@
+"""GPU parity of the candidate-graph builder and the learned warm start.
+
+* k nearest neighbours and the symmetrised candidate CSR: bit-exact against the
+  oracle's brute force (integer and index work).
+* features: within float32 rounding of the oracle (float64).
+* network forward and gradient: the oracle rounds the same tensor-core operands
+  to bfloat16 and accumulates in float64, the kernels accumulate in float32.
+  A bfloat16 rounding can then land on the other side of a tie for a handful of
+  elements (probability about 1e-4 per rounding); such a flip moves one output
+  by a few parts in 10^3.  The tests therefore bound the typical error tightly
+  (almost every output within 1e-5 relative) and every error loosely; a wrong
+  index, a transposed operand or a dropped k-step moves every output by far more.
+* one Adam step: the first step moves each parameter by lr * g / (|g| + eps).
+* warm start: lambda0 of the context equals the oracle's rint(2^F s y) to the
+  precision of y (float32 against float64, about 1e-6 relative); the solve from
+  it certifies the same optimum as the cold start, bit-exactly against the
+  oracle from the same lambda0.
+"""
+import numpy as np
+import pytest
+
+import instances as I
+import oracle
+import paper_2011_08170_gb300 as f2m
+from oracle import learned as L
+from paper_2011_08170_gb300 import build as B
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return f2m.load()
+
+
+# ---- k nearest neighbours --------------------------------------------------------------
+
+def _grid_with_copies():
+    g = np.array([(i * 3, j * 3) for i in range(7) for j in range(7)], dtype=np.int32)
+    return np.concatenate([g, g[[7, 7, 20]]])
+
+
+@pytest.mark.parametrize("case", ["uniform", "mixture", "ties", "tiny", "corner", "dense"])
+@pytest.mark.parametrize("k", [3, 10, 16, 32])
+def test_knn_matches_oracle(lib, oracle_lib, case, k):
+    if case == "uniform":
+        xy = I.uniform_points(3000, 1)
+    elif case == "mixture":
+        xy = I.mixture_points(4000, 2)
+    elif case == "ties":
+        xy = _grid_with_copies()
+    elif case == "tiny":
+        xy = I.uniform_points(k + 1, 3)
+    elif case == "corner":  # points at the edges of the coordinate range
+        xy = np.array([(0, 0), (0, (1 << 20) - 1), ((1 << 20) - 1, 0), ((1 << 20) - 1, (1 << 20) - 1)]
+                      + [(i * 37 % 1000, (1 << 20) - 1 - i) for i in range(60)], dtype=np.int32)
+    else:  # everything in one cell of the grid
+        xy = (I.uniform_points(2000, 4) // 4000).astype(np.int32)
+    if xy.shape[0] <= k:
+        pytest.skip("n <= k")
+    nbr, d2 = f2m.f2m_knn(xy, k)
+    onbr, od2 = oracle.knn(xy, k)
+    assert np.array_equal(d2, od2)
+    assert np.array_equal(nbr, onbr)
+
+
+@pytest.mark.parametrize("kind,n,seed,k", [("uniform", 5000, 7, 10), ("mixture", 6000, 8, 12),
+                                           ("uniform", 12, 9, 3)])
+def test_knn_csr_matches_oracle_and_input_builder(lib, oracle_lib, kind, n, seed, k):
+    xy = I.uniform_points(n, seed) if kind == "uniform" else I.mixture_points(n, seed)
+    rp, col = f2m.f2m_knn_csr(xy, k)
+    orp, ocol = oracle.knn_csr(xy, k)
+    assert np.array_equal(rp, orp) and np.array_equal(col, ocol)
+    irp, icol = I.knn_csr(xy, k)
+    assert np.array_equal(rp, irp) and np.array_equal(col, icol)
+
+
+def test_knn_rejects_bad_input(lib):
+    xy = I.uniform_points(100, 1)
+    with pytest.raises(f2m.F2MError) as e:
+        f2m.f2m_knn(xy, 33)
+    assert e.value.status == f2m.F2M_ERR_INVALID_ARG
+    bad = xy.copy()
+    bad[5, 0] = 1 << 20
+    with pytest.raises(f2m.F2MError) as e:
+        f2m.f2m_knn(bad, 10)
+    assert e.value.status == f2m.F2M_ERR_INVALID_ARG
+    with pytest.raises(f2m.F2MError):
+        f2m.f2m_knn(xy[:10], 10)
+
+
+# ---- features --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,n,seed", [("uniform", 3000, 1), ("mixture", 5000, 2), ("uniform", 17, 3)])
+def test_features_match_oracle(lib, oracle_lib, kind, n, seed):
+    xy = I.uniform_points(n, seed) if kind == "uniform" else I.mixture_points(n, seed)
+    feat, scale = f2m.f2m_features(xy)
+    _, d2 = oracle.knn(xy, 16)
+    of, os_ = L.features(d2)
+    assert np.allclose(scale, os_, rtol=2e-7, atol=0)
+    assert np.allclose(feat, of, rtol=4e-7, atol=1e-7)
+
+
+def test_features_all_copies(lib):
+    xy = np.full((40, 2), 12345, dtype=np.int32)
+    feat, scale = f2m.f2m_features(xy)
+    assert np.all(scale == 1.0) and np.all(feat == 0.0)
+
+
+# ---- the network --------------------------------------------------------------------------
+
+def _batch(B_, seed):
+    feat = I.uniform_floats(seed, B_ * 16, 0.2, 2.5).reshape(B_, 16)
+    feat.sort(axis=1)
+    target = I.uniform_floats(seed + 1, B_, 0.2, 0.6)
+    return feat, target
+
+
+def _assert_close_outputs(got, ref):
+    err = np.abs(got.astype(np.float64) - ref)
+    scale = 1.0 + np.abs(ref)
+    assert np.median(err / scale) < 1e-6
+    assert np.mean(err > 1e-5 * scale) < 0.01
+    assert np.all(err < 1e-2 * scale)
+
+
+@pytest.mark.parametrize("count", [1, 127, 128, 129, 1000, 50000])
+def test_forward_matches_oracle(lib, count):
+    p = I.mlp_init(1)
+    feat, _ = _batch(count, 3)
+    m = f2m.f2m_mlp_create(p)
+    y = f2m.f2m_mlp_forward(m, feat)
+    ref, _ = L.forward(p.astype(np.float64), feat.astype(np.float64), rounding=True)
+    _assert_close_outputs(y, ref)
+
+
+def _assert_close_grad(g, ref):
+    d = g.astype(np.float64) - ref
+    assert np.linalg.norm(d) <= 2e-3 * np.linalg.norm(ref)
+    assert np.max(np.abs(d)) <= 1e-2 * np.max(np.abs(ref))
+    # every block of the parameter vector is checked on its own scale
+    for a, b in ((0, 2048), (2048, 2176), (2176, 18560), (18560, 18688), (18688, 18816), (18816, 18817)):
+        assert np.linalg.norm(d[a:b]) <= 5e-3 * np.linalg.norm(ref[a:b]) + 1e-12, (a, b)
+
+
+@pytest.mark.parametrize("count", [128, 300, 5000, 60000])
+def test_gradient_matches_oracle(lib, count):
+    p = I.mlp_init(2)
+    feat, target = _batch(count, 5)
+    m = f2m.f2m_mlp_create(p)
+    loss, g = f2m.f2m_mlp_grad(m, feat, target)
+    rloss, rg = L.backward(p.astype(np.float64), feat.astype(np.float64), target.astype(np.float64),
+                           rounding=True)
+    assert abs(loss - rloss) <= 1e-4 * rloss
+    _assert_close_grad(g, rg)
+
+
+def test_one_adam_step_matches_oracle(lib):
+    p = I.mlp_init(3)
+    feat, target = _batch(3000, 7)
+    m = f2m.f2m_mlp_create(p)
+    lr = 1e-3
+    f2m.f2m_mlp_train(m, feat, target, epochs=1, batch=4096, lr=lr)
+    got = f2m.f2m_mlp_get_params(m).astype(np.float64)
+    _, rg = L.backward(p.astype(np.float64), feat.astype(np.float64), target.astype(np.float64), rounding=True)
+    ref, _, _ = L.adam(p.astype(np.float64), np.zeros_like(rg), np.zeros_like(rg), rg, 1, lr)
+    step = np.abs(got - p)
+    assert np.all(step <= lr * (1 + 1e-3) + 1e-7)
+    sure = np.abs(rg) > 1e-2 * np.max(np.abs(rg))
+    assert sure.sum() > 1000
+    assert np.all(np.abs(got[sure] - ref[sure]) <= 2e-3 * lr + 1e-7)
+
+
+def test_training_trajectory_matches_oracle(lib):
+    # full-batch steps (no shuffle involved): 25 Adam steps on the GPU follow
+    # the oracle's steps (same bfloat16 roundings, float64 sums) closely
+    feat, target = _batch(4096, 13)
+    p = I.mlp_init(6)
+    m = f2m.f2m_mlp_create(p)
+    losses = f2m.f2m_mlp_train(m, feat, target, epochs=25, batch=4096, lr=2e-3, lr_final_frac=1.0)
+    q = p.astype(np.float64)
+    m1 = np.zeros_like(q)
+    m2 = np.zeros_like(q)
+    ref = []
+    for t in range(1, 26):
+        loss, g = L.backward(q, feat.astype(np.float64), target.astype(np.float64), rounding=True)
+        ref.append(loss)
+        q, m1, m2 = L.adam(q, m1, m2, g, t, 2e-3)
+    ref = np.array(ref)
+    assert np.all(np.abs(losses - ref) <= 0.03 * ref), (losses, ref)
+    assert np.allclose(f2m.f2m_mlp_get_params(m), q, rtol=0, atol=3e-3)
+
+
+def test_training_reduces_loss(lib):
+    # a smooth target of the features, 800 Adam steps with shuffling (the
+    # float64 oracle reaches about 0.11 of the target variance on this run)
+    feat, _ = _batch(40000, 9)
+    target = (0.3 * feat[:, 0] + 0.2 * feat[:, 1] - 0.05 * feat[:, 15]).astype(np.float32)
+    m = f2m.f2m_mlp_create(I.mlp_init(4))
+    losses = f2m.f2m_mlp_train(m, feat, target, epochs=20, batch=1024, lr=2e-3, lr_final_frac=0.1, seed=1)
+    assert np.all(losses > 0) and losses.shape == (20,)
+    assert losses[-1] < 0.25 * np.var(target) and losses[-1] < 0.01 * losses[0]
+    # a second call continues (Adam state and step count carry over)
+    more = f2m.f2m_mlp_train(m, feat, target, epochs=3, batch=1024, lr=2e-4, seed=2)
+    assert np.all(more > 0) and more[-1] < 1.5 * losses[-1]
+
+
+# ---- warm start of a solve ------------------------------------------------------------------
+
+def test_warm_start_lambda_and_solve(lib, oracle_lib):
+    d = I.make_instance("mixture", 3000, 11, 10)
+    p = I.mlp_init(5)
+    m = f2m.f2m_mlp_create(p)
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"])
+    f2m.f2m_warm_start(ctx, m)
+    lam0, fb = f2m.f2m_get_lambda(ctx)
+    assert fb == 8
+    _, d2 = oracle.knn(d["xy"], 16)
+    of, os_ = L.features(d2)
+    y, _ = L.forward(p.astype(np.float64), of.astype(np.float32).astype(np.float64), rounding=True)
+    ref = L.warm_lambda(y, os_, 8)
+    # y agrees to about 1e-6 relative; lambda0 = 2^8 s y is ~1e6 units here
+    diff = np.abs(lam0.astype(np.int64) - ref)
+    tight = diff <= 1 + 4e-6 * np.abs(ref)
+    assert np.mean(tight) > 0.99 and np.all(diff <= 1 + 1e-3 * np.abs(ref))
+    # the solve from lambda0 is the exact method: bit-exact with the oracle from
+    # the same start, and the same optimum as the cold start
+    info = f2m.f2m_solve(ctx).as_dict()
+    lam, fbw = f2m.f2m_get_lambda(ctx)
+    r = oracle_lib.solve(d["xy"], d["row_ptr"], d["col"], lam0=lam0)
+    assert info["iterations"] == r.iterations and info["bound2"] == r.bound2
+    assert np.array_equal(lam, r.lam) and fbw == r.frac_bits
+    cold = f2m.solve(d["xy"], d["row_ptr"], d["col"])
+    assert info["bound2"] / 2.0 ** info["frac_bits"] == cold.info["bound2"] / 2.0 ** cold.info["frac_bits"]
