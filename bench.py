@@ -34,6 +34,7 @@ WORKLOADS = {
     "c2": dict(kind="uniform", n=100_000, k=10, seed=0),
     "c3": dict(kind="mixture", n=200_000, k=12, seed=0),
     "c4": dict(kind="batch", n=0, k=10, seed=0, count=256, nmin=1000, nmax=20000),
+    "c5": dict(kind="warm", n=0, k=0, seed=0, sizes=(("mixture", 100_000, 10), ("mixture", 200_000, 12))),
 }
 
 
@@ -55,6 +56,10 @@ PRICING_OPS_PER_PAIR = 7  # 2 FADD (dx, dy), FADD (t), FMUL (t^2), 2 FFMA, FSETP
 
 
 def workload_name(w):
+    if w["kind"] == "warm":
+        return ("learned warm start vs cold start: mixture n=100000 k=10 and n=200000 k=12, seed 0, "
+                "network trained on 2000 solved n=20000 instances (paper_2011_08170_gb300/warm_start_mlp.npy), "
+                "both solves certified optimal on all pairs")
     if w["kind"] == "batch":
         return (f"batch of {w['count']} instances, n log-uniform in [{w['nmin']}, {w['nmax']}], "
                 f"uniform/clustered alternating, k={w['k']}, int32 rounded-Euclidean costs, "
@@ -222,6 +227,8 @@ def main():
         return run_reference(args, w, rank)
     if w["kind"] == "batch":
         return run_batch(args, w, rank, world, local)
+    if w["kind"] == "warm":
+        return run_warm(args, w, rank, world, local)
 
     import torch
     import instances as I
@@ -472,6 +479,103 @@ def run_batch(args, w, rank, world, local):
                       "augmentations": int(tot.augmentations)},
             "e2e": {"value": e2e, "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "roofline": roofline, "clocks": clk, "gpu_launches": int(launches)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_warm(args, w, rank, world, local):
+    """Warm-start workload: per instance, a cold solve (lambda = 0) and a warm one
+    (features + network + rounding, then the same solve), both certified.  The
+    value is the warm solve's ms summed over the instances, the network's time
+    included; the cold sum is reported beside it."""
+    import torch
+    import instances as I
+    import paper_2011_08170_gb300 as f2m
+    from paper_2011_08170_gb300 import build as B
+    from paper_2011_08170_gb300 import warm_start as W
+
+    B.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    ds = [I.make_instance(kind, n, w["seed"] + rank, k) for kind, n, k in w["sizes"]]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    m = f2m.f2m_mlp_create(W.load_weights(), stream=stream)
+
+    def one(d, warm):
+        ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1)
+        e0.record(stream)
+        wms = f2m.f2m_warm_start(ctx, m) if warm else 0.0
+        info = f2m.f2m_solve(ctx).as_dict()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        f2m.f2m_destroy(ctx)
+        assert info["status"] == 0 and info["certified"] == 2, info
+        return e0.elapsed_time(e1), wms, info
+
+    for _ in range(args.warmup):
+        for d in ds:
+            one(d, False)
+            one(d, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = f2m.f2m_kernel_launches()
+    per = {i: {"cold": [], "warm": [], "net": []} for i in range(len(ds))}
+    infos = {}
+    for _ in range(args.steps):
+        for i, d in enumerate(ds):
+            tc, _, ic = one(d, False)
+            tw, wms, iw = one(d, True)
+            per[i]["cold"].append(tc)
+            per[i]["warm"].append(tw)
+            per[i]["net"].append(wms)
+            infos[i] = (ic, iw)
+    launches = f2m.f2m_kernel_launches() - launches0
+    clk = clocks.stop()
+    warm_ms = sum(statistics.median(per[i]["warm"]) for i in per)
+    cold_ms = sum(statistics.median(per[i]["cold"]) for i in per)
+    rows = []
+    for i, (kind, n, k) in enumerate(w["sizes"]):
+        ic, iw = infos[i]
+        same = ic["bound2"] / 2.0 ** ic["frac_bits"] == iw["bound2"] / 2.0 ** iw["frac_bits"]
+        assert same, (ic, iw)
+        rows.append({"instance": f"{kind} n={n} k={k}", "cold_ms": statistics.median(per[i]["cold"]),
+                     "warm_ms": statistics.median(per[i]["warm"]), "network_ms": statistics.median(per[i]["net"]),
+                     "cold_sweeps": ic["iterations"], "warm_sweeps": iw["iterations"],
+                     "cold_phases": ic["phases"], "warm_phases": iw["phases"], "same_optimum": same})
+    # end to end through the ABI with host buffers: create, warm start, solve, read back
+    e2e = 0.0
+    h2d = d2h = 0
+    for d in ds:
+        t0 = time.perf_counter()
+        ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], stream=stream)
+        f2m.f2m_warm_start(ctx, m)
+        f2m.f2m_solve(ctx)
+        rp_o, col_o, x2_o, cost_o = f2m.f2m_get_x(ctx)
+        lam_o, _ = f2m.f2m_get_lambda(ctx)
+        torch.cuda.synchronize()
+        e2e += (time.perf_counter() - t0) * 1e3
+        h2d += d["xy"].nbytes + d["row_ptr"].nbytes + d["col"].nbytes
+        d2h += rp_o.nbytes + col_o.nbytes + x2_o.nbytes + cost_o.nbytes + lam_o.nbytes
+        f2m.f2m_destroy(ctx)
+    line = {"metric": METRIC + " (learned warm start, sum over the instances)", "value": warm_ms, "unit": "ms",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": warm_ms + cold_ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": workload_name(w), "l2": "flushed before every solve (256 MB device write)",
+                       "parallelism": f"replicas x{world}"},
+            "cold_start_ms": cold_ms, "instances": rows,
+            "e2e": {"value": e2e, "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "clocks": clk, "gpu_launches": int(launches)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

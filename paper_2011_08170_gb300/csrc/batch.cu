@@ -232,17 +232,18 @@ static f2m_status batch_tiles(f2m_batch* b, int te, int tn, int4** d_tiles, int3
 static int32_t batch_grid(f2m_batch* b, int shape, int32_t ntiles) {
   const int sms = b->u->num_sms;
   int per_sm = batch_shape_blocks(shape, 1);
+  const int32_t units = batch_shape_units(shape);
   for (int it = 0; it < 4 && per_sm > 0; ++it) {  // the tile table grows as the grid shrinks
     const int32_t G = sms * per_sm;
-    const int32_t mcap = (ntiles + G - 1) / G;
+    const int32_t mcap = (int32_t)((ntiles + (int64_t)G * units - 1) / ((int64_t)G * units));
     const int p2 = batch_shape_blocks(shape, mcap);
     if (p2 >= per_sm) break;
     per_sm = p2;
   }
   if (per_sm < 1) return 0;
   int32_t G = sms * per_sm;
-  if (G > ntiles) G = ntiles;
-  return G;
+  if ((int64_t)G * units > ntiles) G = (int32_t)((ntiles + units - 1) / units);
+  return G < 1 ? 1 : G;
 }
 
 // Device work of one phase on stream st: lambda into the renumbered double
@@ -304,7 +305,7 @@ static f2m_status batch_autotune(f2m_batch* b) {
     if (G < 1) continue;
     double t = 0;
     for (int rep = 0; rep < 2; ++rep) {  // the first run only warms up
-      const int64_t sweeps = rep == 0 ? 2 : 24;
+      const int64_t sweeps = rep == 0 ? 4 : 48;
       cudaError_t e = cudaEventRecord(c->ev0, c->st);
       if (e == cudaSuccess) e = enqueue_phase(b, c->st, sh, G, d_t, nt, sweeps, nullptr);
       if (e == cudaSuccess) e = cudaEventRecord(c->ev1, c->st);

@@ -309,38 +309,270 @@ gdp_batch_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ iec,
   }
 }
 
+// Warp-tile form: every warp streams its own small tiles (tile k goes to warp
+// k mod GW of the grid) through its own S copy stages, forms w_e in place in
+// the stage (phase 1, lanes over entries) and takes the top-3 per row (phase
+// 2, lanes over rows), synchronising only within the warp.  The warps of a CTA
+// meet once per sweep, for the totals and the grid barrier.
+template <int W, int S, int TE, int TN, int MINB>
+__global__ void __launch_bounds__(W * 32, MINB)
+gdp_batch_warp_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ iec,
+                      const int4* __restrict__ tiles, int32_t ntiles, int32_t nseg, uint8_t* active,
+                      unsigned long long* seg_ch, long long* seg_sweeps, int32_t* lam0, int32_t* lam1,
+                      int32_t F, int32_t shift, long long max_sweeps, GdpCtl* ctl, long long budget,
+                      int32_t mcap) {
+  constexpr int kStageEcBytes = stage_ec_bytes(TE);
+  constexpr int kStageBytes = stage_bytes(TE, TN);
+  static_assert(kStageBytes % 16 == 0 && kStageEcBytes % 16 == 0, "stage alignment");
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ unsigned s_tot[W];
+  __shared__ int s_ovf[W];
+  __shared__ int s_stop, s_abort;
+  __shared__ int s_hdr[W * S];
+  __shared__ __align__(8) unsigned long long s_full[W * S];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int GW = gridDim.x * W, gw = blockIdx.x * W + warp;
+  const long long div = 1LL << shift;
+  volatile GdpCtl* vc = ctl;
+  volatile uint8_t* vact = active;
+
+  uint8_t* my_stage = smem + (size_t)warp * S * kStageBytes;
+  int4* s_mt = reinterpret_cast<int4*>(smem + (size_t)W * S * kStageBytes);  // [W][mcap]
+  int* s_me1 = reinterpret_cast<int*>(s_mt + W * mcap);
+  uint8_t* s_act = reinterpret_cast<uint8_t*>(s_me1 + W * mcap);
+  const int my = gw < ntiles ? (ntiles - 1 - gw) / GW + 1 : 0;
+  int4* m_mt = s_mt + warp * mcap;
+  int* m_me1 = s_me1 + warp * mcap;
+  uint8_t* m_act = s_act + warp * mcap;
+
+  for (int i = lane; i < my; i += 32) {
+    const int k = gw + i * GW;
+    const int4 tl = tiles[k];
+    m_mt[i] = tl;
+    m_me1[i] = tiles[k + 1].w;
+    m_act[i] = vact[tl.z];
+  }
+  if (lane == 0)
+    for (int st = 0; st < S; ++st) mbar_init1((uint32_t)__cvta_generic_to_shared(&s_full[warp * S + st]));
+  if (tid == 0) {
+    s_stop = 0;
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  const uint64_t pol_stream = policy_evict_first(), pol_lam = policy_evict_last();
+  int p_i = 0;  // lane 0: next tile of this warp's walk over (sweep, my tile)
+  auto produce = [&](long long q) {
+    const int st = (int)(q % S);
+    for (;;) {
+      if (p_i >= my) {
+        s_hdr[warp * S + st] = -1;  // end of a sweep
+        p_i = 0;
+        return;
+      }
+      const int i = p_i++;
+      if (!m_act[i]) continue;
+      const int4 tl = m_mt[i];
+      const int e1 = m_me1[i];
+      const int a0 = tl.w & ~1, a1 = (e1 + 1) & ~1;
+      const int r0 = tl.x & ~3, r1 = (tl.y + 4) & ~3;
+      const uint32_t ecb = (uint32_t)(a1 - a0) * 8u, rpb = (uint32_t)(r1 - r0) * 4u;
+      const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&s_full[warp * S + st]);
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(my_stage + st * kStageBytes);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(mb, ecb + rpb);
+      bulk_g2s(dst, iec + a0, ecb, mb, pol_stream);
+      bulk_g2s(dst + kStageEcBytes, irp + r0, rpb, mb, pol_stream);
+      s_hdr[warp * S + st] = i;
+      return;
+    }
+  };
+
+  long long q = 0;  // slots issued (lane 0)
+  if (lane == 0)
+    for (; q < S - 1; ++q) produce(q);
+  __syncwarp();
+  uint32_t phase_bits = 0;
+  long long j = 0;          // first slot not consumed
+  bool timed_out = false;   // the wait for slot j gave up
+  unsigned ch_w = 0;        // lane 0: nodes changed by this warp in the sweep
+  int ovf = 0;
+
+  for (long long t = 0;; ++t) {
+    const int32_t* lin = (t & 1) ? lam1 : lam0;
+    int32_t* lout = (t & 1) ? lam0 : lam1;
+    for (;;) {  // this warp's tiles of sweep t
+      if (lane == 0) produce(q++);
+      __syncwarp();
+      const int st = (int)(j % S);
+      const int i = s_hdr[warp * S + st];
+      if (i < 0) {
+        ++j;
+        break;
+      }
+      const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&s_full[warp * S + st]);
+      const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(mb, (phase_bits >> st) & 1u, kBulkWaitLimit));
+      if (!ok) {
+        timed_out = true;
+        if (lane == 0) atomicOr(&s_abort, 1);
+        break;
+      }
+      phase_bits ^= 1u << st;
+      const int4 tl = m_mt[i];
+      const int v0 = tl.x, nv = tl.y - tl.x, E0 = tl.w, ne = m_me1[i] - tl.w;
+      int2* sec = reinterpret_cast<int2*>(my_stage + st * kStageBytes) + (E0 - (E0 & ~1));
+      const int* srp = reinterpret_cast<const int*>(my_stage + st * kStageBytes + kStageEcBytes) + (v0 - (v0 & ~3));
+#pragma unroll 4
+      for (int e = lane; e < ne; e += 32) {  // w_e = c_e 2^F - lambda_u, in place of the column
+        const int2 w = sec[e];
+        sec[e].x = (w.y << F) - ld_lam(lin + w.x, pol_lam);
+      }
+      __syncwarp();
+      unsigned chg = 0;
+      for (int k = lane; k < nv; k += 32) {
+        const int lv = ld_lam(lin + v0 + k, pol_lam);
+        int a = INT_MAX, bb = INT_MAX, c = INT_MAX;
+        const int e_end = srp[k + 1] - E0;
+        for (int e = srp[k] - E0; e < e_end; ++e) top3_insert_minmax(sec[e].x - lv, a, bb, c);  // Eq. 9
+        const long long d = ((long long)bb + (long long)c) / div;  // Eq. 10, truncated toward 0
+        const long long nl = (long long)lv + d;
+        ovf |= (nl >= kLamLimit || nl <= -kLamLimit);
+        lout[v0 + k] = (int32_t)nl;
+        chg += (d != 0);
+      }
+      chg = __reduce_add_sync(0xffffffffu, chg);
+      __syncwarp();
+      if (lane == 0 && chg) {
+        atomicAdd(&seg_ch[(size_t)tl.z * 3 + (t % 3)], (unsigned long long)chg);
+        ch_w += chg;
+      }
+      ++j;
+    }
+    // end of sweep t for the whole CTA: totals, grid barrier, freezes, stop test
+    ovf = __any_sync(0xffffffffu, ovf);
+    if (lane == 0) {
+      s_tot[warp] = ch_w;
+      s_ovf[warp] = ovf;
+    }
+    ch_w = 0;
+    ovf = 0;
+    __syncthreads();
+    if (warp == 0) {
+      unsigned y = lane < W ? s_tot[lane] : 0;
+      int o = lane < W ? s_ovf[lane] : 0;
+      y = __reduce_add_sync(0xffffffffu, y);
+      o = __any_sync(0xffffffffu, o);
+      if (lane == 0) {
+        if (y) atomicAdd(&ctl->slot_ch[t % 3], (unsigned long long)y);
+        if (o) atomicOr(&ctl->status, kGdpOverflow);
+        if (s_abort) atomicOr(&ctl->status, kGdpTimeout);
+      }
+    }
+    bool stop = s_abort != 0;
+    if (!stop && !grid_barrier_counted(&ctl->bar_count, (unsigned)(t + 1) * gridDim.x, budget)) {
+      if (tid == 0) atomicOr(&ctl->status, kGdpTimeout);
+      stop = true;
+    }
+    if (blockIdx.x == 0 && !stop) {
+      for (int sgi = tid; sgi < nseg; sgi += W * 32) {
+        volatile unsigned long long* slot = seg_ch + (size_t)sgi * 3;
+        if (vact[sgi] && slot[t % 3] == 0) {
+          vact[sgi] = 0;
+          seg_sweeps[sgi] = t + 1;
+        }
+        slot[(t + 2) % 3] = 0;
+      }
+    }
+    for (int idx = tid; idx < W * mcap; idx += W * 32) {
+      const int ww = idx / mcap, ii = idx % mcap;
+      const int gww = blockIdx.x * W + ww;
+      const int myw = gww < ntiles ? (ntiles - 1 - gww) / GW + 1 : 0;
+      if (ii < myw) s_act[idx] = vact[s_mt[idx].z];
+    }
+    if (tid == 0) {
+      const unsigned long long chg = vc->slot_ch[t % 3];
+      const int stv = vc->status;
+      if (blockIdx.x == 0) {
+        vc->slot_ch[(t + 2) % 3] = 0;
+        vc->sweeps = t + 1;
+        vc->fixed_point = (chg == 0);
+      }
+      s_stop = stop || (stv != 0) || (chg == 0) || (t + 1 >= max_sweeps);
+    }
+    __syncthreads();
+    if (s_stop) break;
+  }
+  // lane 0 waits (bounded) for this warp's copies still in flight: slots j..q-1
+  if (lane == 0) {
+    for (long long sl = j; sl < q; ++sl) {
+      const int stg = (int)(sl % S);
+      if (s_hdr[warp * S + stg] < 0) continue;
+      mbar_wait_bounded((uint32_t)__cvta_generic_to_shared(&s_full[warp * S + stg]), (phase_bits >> stg) & 1u,
+                        kBulkWaitLimit);
+    }
+  }
+  (void)timed_out;
+}
+
 // Shapes of the batch kernel the autotuner picks from: threads per CTA, copy
-// stages, CTAs per SM, tile entries, tile nodes.
+// stages, CTAs per SM, tile entries, tile nodes, and whether tiles go to warps
+// (gdp_batch_warp_kernel) or to CTAs (gdp_batch_kernel).
 struct BatchShapeDef {
-  int threads, stages, per_sm, te, tn;
+  int threads, stages, per_sm, te, tn, warp_tiles;
 };
 constexpr BatchShapeDef kBatchShapes[] = {
-    {512, 2, 2, 4096, 1536}, {512, 2, 4, 2048, 768}, {256, 2, 4, 2048, 768}, {512, 3, 3, 2048, 768},
-    {1024, 3, 1, 4096, 1536}, {256, 2, 6, 1024, 384}, {512, 4, 2, 2048, 768}};
+    {512, 2, 2, 4096, 1536, 0}, {512, 2, 4, 2048, 768, 0}, {256, 2, 4, 2048, 768, 0},
+    {512, 3, 3, 2048, 768, 0},  {1024, 3, 1, 4096, 1536, 0}, {256, 2, 6, 1024, 384, 0},
+    {512, 4, 2, 2048, 768, 0},  {1024, 2, 1, 256, 96, 1},    {512, 2, 2, 256, 96, 1},
+    {768, 3, 1, 256, 96, 1},    {512, 2, 1, 512, 176, 1},    {512, 3, 1, 256, 96, 1}};
 constexpr int kNumBatchShapes = (int)(sizeof(kBatchShapes) / sizeof(kBatchShapes[0]));
 
-#define F2M_BATCH_SHAPE(i)                                                                          \
-  (const void*)gdp_batch_kernel<kBatchShapes[i].threads, kBatchShapes[i].stages, kBatchShapes[i].te, \
-                                kBatchShapes[i].tn, kBatchShapes[i].per_sm>
+template <int I>
+static const void* batch_shape_ptr() {
+  constexpr BatchShapeDef d = kBatchShapes[I];
+  if constexpr (d.warp_tiles)
+    return (const void*)gdp_batch_warp_kernel<d.threads / 32, d.stages, d.te, d.tn, d.per_sm>;
+  else
+    return (const void*)gdp_batch_kernel<d.threads, d.stages, d.te, d.tn, d.per_sm>;
+}
 
 static const void* batch_kernel_of(int shape) {
   switch (shape) {
-    case 0: return F2M_BATCH_SHAPE(0);
-    case 1: return F2M_BATCH_SHAPE(1);
-    case 2: return F2M_BATCH_SHAPE(2);
-    case 3: return F2M_BATCH_SHAPE(3);
-    case 4: return F2M_BATCH_SHAPE(4);
-    case 5: return F2M_BATCH_SHAPE(5);
-    case 6: return F2M_BATCH_SHAPE(6);
+    case 0: return batch_shape_ptr<0>();
+    case 1: return batch_shape_ptr<1>();
+    case 2: return batch_shape_ptr<2>();
+    case 3: return batch_shape_ptr<3>();
+    case 4: return batch_shape_ptr<4>();
+    case 5: return batch_shape_ptr<5>();
+    case 6: return batch_shape_ptr<6>();
+    case 7: return batch_shape_ptr<7>();
+    case 8: return batch_shape_ptr<8>();
+    case 9: return batch_shape_ptr<9>();
+    case 10: return batch_shape_ptr<10>();
+    case 11: return batch_shape_ptr<11>();
   }
   return nullptr;
 }
-#undef F2M_BATCH_SHAPE
+static_assert(kNumBatchShapes == 12, "one case per shape");
 
-// dynamic shared memory: stages, w buffer, per-CTA tile table (int4 + int + flag)
+// dynamic shared memory: stages (per CTA, or per warp), the w buffer of the CTA
+// form, and the tile table (int4 + int + flag per tile; per warp in the warp form)
 static size_t batch_smem(int shape, int mcap) {
   const BatchShapeDef& d = kBatchShapes[shape];
+  if (d.warp_tiles) {
+    const int w = d.threads / 32;
+    return (size_t)w * d.stages * stage_bytes(d.te, d.tn) + (size_t)w * mcap * 21 + 16;
+  }
   return (size_t)d.stages * stage_bytes(d.te, d.tn) + (size_t)d.te * 4 + (size_t)mcap * 21 + 16;
+}
+
+// tile-table capacity per CTA (CTA form) or per warp (warp form)
+static int32_t batch_mcap(int shape, int32_t ntiles, int32_t G) {
+  const BatchShapeDef& d = kBatchShapes[shape];
+  const long long units = d.warp_tiles ? (long long)G * (d.threads / 32) : G;
+  long long m = (ntiles + units - 1) / units;
+  return (int32_t)(m < 1 ? 1 : m);
 }
 
 int batch_shape_tile(int shape, int* te, int* tn) {
@@ -351,6 +583,11 @@ int batch_shape_tile(int shape, int* te, int* tn) {
 }
 
 int batch_num_shapes() { return kNumBatchShapes; }
+
+int batch_shape_units(int shape) {
+  if (shape < 0 || shape >= kNumBatchShapes) return 1;
+  return kBatchShapes[shape].warp_tiles ? kBatchShapes[shape].threads / 32 : 1;
+}
 
 int batch_shape_blocks(int shape, int mcap) {
   if (shape < 0 || shape >= kNumBatchShapes) return 0;
@@ -375,8 +612,7 @@ cudaError_t launch_gdp_batch(int shape, const int32_t* irp, const int2* iec, con
                              cudaStream_t st) {
   if (shape < 0 || shape >= kNumBatchShapes || G < 1) return cudaErrorInvalidValue;
   long long ms = max_sweeps;
-  int32_t mcap = (ntiles + G - 1) / G;
-  if (mcap < 1) mcap = 1;
+  const int32_t mcap = batch_mcap(shape, ntiles, G);
   const size_t sm = batch_smem(shape, mcap);
   const void* k = batch_kernel_of(shape);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

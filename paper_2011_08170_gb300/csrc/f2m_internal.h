@@ -188,6 +188,7 @@ cudaError_t launch_batch_scatter_final(const int32_t* lam0, const int32_t* lam1,
                                        const int32_t* perm, int32_t n, int32_t* dst, cudaStream_t st);
 int batch_shape_blocks(int shape, int mcap);  // CTAs per SM, 0 if the shape does not run
 int batch_shape_tile(int shape, int* te, int* tn);  // tile entries and nodes of a shape
+int batch_shape_units(int shape);  // tile owners per CTA: 1 (CTA form) or its warps (warp form)
 cudaError_t launch_gdp_batch(int shape, const int32_t* irp, const int2* iec, const int4* tiles, int32_t ntiles,
                              int32_t G, int32_t nseg, uint8_t* active, unsigned long long* seg_ch,
                              long long* seg_sweeps, int32_t* lam0, int32_t* lam1, int32_t F,

@@ -84,3 +84,12 @@ def test_library_compiled_for_sm103a():
     text = open(os.path.join(ROOT, "paper_2011_08170_gb300", "build.py")).read()
     assert "arch=compute_103a,code=sm_103a" in text
     assert os.path.exists(B.LIB)
+
+
+def test_committed_warm_start_weights():
+    import os
+    import numpy as np
+    import instances as I
+    p = os.path.join(os.path.dirname(__file__), "..", "paper_2011_08170_gb300", "warm_start_mlp.npy")
+    w = np.load(p)
+    assert w.dtype == np.float32 and w.shape == (I.MLP_NPARAMS,) and np.all(np.isfinite(w))

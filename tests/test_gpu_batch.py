@@ -102,3 +102,12 @@ def test_batch_rejects_cross_instance_column(lib):
         f2m.f2m_create_batch([(ds[0]["xy"], ds[0]["row_ptr"], ds[0]["col"]),
                               (ds[1]["xy"], ds[1]["row_ptr"], bad)])
     assert e.value.status == f2m.F2M_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("shape", list(range(12)))
+def test_every_kernel_shape_gives_the_same_result(lib, oracle_lib, shape):
+    # each shape of the batched GDP kernel (the autotuner's candidates): same
+    # sweeps, lambda and x as the single solves
+    ds = make_batch([("uniform", 700, 31, 10), ("mixture", 1300, 32, 10), ("uniform", 2100, 33, 6),
+                     ("mixture", 450, 34, 10)])
+    compare(oracle_lib, ds, f2m.f2m_default_params(batch_shape=shape))
