@@ -114,24 +114,31 @@ gdp_batch_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ iec,
                  const int4* __restrict__ tiles, int32_t ntiles, int32_t nseg, uint8_t* active,
                  unsigned long long* seg_ch, long long* seg_sweeps, int32_t* lam0, int32_t* lam1,
                  int32_t F, int32_t shift, long long max_sweeps, GdpCtl* ctl, long long budget, int32_t mcap) {
+  // Software pipeline over the CTA's tiles: while the top-3 phase of tile j
+  // runs, the lambda gathers of tile j+1 (same sweep) are in flight, and the
+  // copies of tiles j+2 .. j+S-1 are landing.
+  static_assert(S >= 3, "the look-ahead tile needs a copy issued one tile earlier");
   constexpr int kStageEcBytes = stage_ec_bytes(TE);
   constexpr int kStageBytes = stage_bytes(TE, TN);
+  constexpr int KE = (TE + T - 1) / T;  // entries per thread in phase 1
+  constexpr int KN = (TN + T - 1) / T;  // own lambdas per thread in phase 1
   static_assert(kStageBytes % 16 == 0 && kStageEcBytes % 16 == 0, "stage alignment");
+  static_assert((2 * TE + 2 * TN) % 4 == 0, "tile table alignment");
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ unsigned s_tot[32];
   __shared__ int s_ovf[32];
-  __shared__ unsigned s_tile_ch;
-  __shared__ int s_stop, s_hdr[S];
+  __shared__ unsigned s_tile_ch[2];  // changed counts of tiles j and j+1 (by j & 1)
+  __shared__ int s_stop, s_abort, s_hdr[S];
   __shared__ __align__(8) unsigned long long s_full[S];
   const int tid = threadIdx.x, b = blockIdx.x, G = gridDim.x;
   const int lane = tid & 31, warp = tid >> 5;
   constexpr int nwarps = T / 32;
-  const long long div = 1LL << shift;
   volatile GdpCtl* vc = ctl;
   volatile uint8_t* vact = active;
 
-  int* s_w = reinterpret_cast<int*>(smem + S * kStageBytes);
-  int4* s_mt = reinterpret_cast<int4*>(smem + S * kStageBytes + TE * 4);
+  int* s_w = reinterpret_cast<int*>(smem + S * kStageBytes);  // [2][TE] w of a prepared tile
+  int* s_lv = s_w + 2 * TE;                                     // [2][TN] its own lambdas
+  int4* s_mt = reinterpret_cast<int4*>(s_lv + 2 * TN);
   int* s_me1 = reinterpret_cast<int*>(s_mt + mcap);
   uint8_t* s_act = reinterpret_cast<uint8_t*>(s_me1 + mcap);
   const int my = b < ntiles ? (ntiles - 1 - b) / G + 1 : 0;  // tiles of this CTA
@@ -146,14 +153,20 @@ gdp_batch_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ iec,
   if (tid == 0) {
     for (int st = 0; st < S; ++st) mbar_init1((uint32_t)__cvta_generic_to_shared(&s_full[st]));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_stop = 0;
+    s_abort = 0;
+    s_tile_ch[0] = 0;
+    s_tile_ch[1] = 0;
   }
   __syncthreads();
 
   const uint64_t pol_stream = policy_evict_first(), pol_lam = policy_evict_last();
-  // issuing thread: next tile of its own walk over (sweep, my tile)
-  int p_i = 0;
-  auto produce = [&](long long q) {
-    const int st = (int)(q % S);
+  // The issuing thread is the CTA's last thread (rows go to the first nv
+  // threads, so it usually has none): it issues while the others run phase 2.
+  const bool issuer = tid == T - 1;
+  int p_i = 0;  // issuing thread: next tile of its walk over (sweep, my tile)
+  auto produce = [&](long long qq) {
+    const int st = (int)(qq % S);
     for (;;) {
       if (p_i >= my) {  // end of a sweep
         s_hdr[st] = -1;
@@ -178,70 +191,140 @@ gdp_batch_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ iec,
     }
   };
 
-  long long q = 0;  // slots issued
-  if (tid == 0)
+  long long q = 0;  // slots issued (issuing thread)
+  if (issuer)
     for (; q < S - 1; ++q) produce(q);
-  uint32_t phase_bits = 0;  // completed uses of each stage, mod 2
+  uint32_t phase_bits = 0;  // consumed uses of each stage, mod 2
+  long long waited = 0;     // slots [0, waited) whose copies are known complete (or were END)
+  // wait for the copy of slot sl (a tile); the result is the same in every thread
+  auto wait_slot = [&](long long sl) -> bool {
+    const int st = (int)(sl % S);
+    const bool ok1 = mbar_wait_bounded((uint32_t)__cvta_generic_to_shared(&s_full[st]), (phase_bits >> st) & 1u,
+                                       kBulkWaitLimit);
+    const bool ok = __syncthreads_and(ok1) != 0;
+    if (ok) {
+      phase_bits ^= 1u << st;
+      waited = sl + 1;
+    }
+    return ok;
+  };
+  int g[KE], c[KE], gl[KN];
+  // phase 1, first half: the gathers of tile i from stage st into registers
+  auto gather = [&](int i, int st, const int32_t* lin) {
+    const int4 tl = s_mt[i];
+    const int E0 = tl.w, ne = s_me1[i] - tl.w, v0 = tl.x, nv = tl.y - tl.x;
+    const int2* sec = reinterpret_cast<const int2*>(smem + st * kStageBytes) + (E0 - (E0 & ~1));
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+      const int e = tid + k * T;
+      if (e < ne) {
+        const int2 w = sec[e];
+        c[k] = w.y;
+        g[k] = ld_lam(lin + w.x, pol_lam);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < KN; ++k) {
+      const int v = tid + k * T;
+      if (v < nv) gl[k] = ld_lam(lin + v0 + v, pol_lam);
+    }
+  };
+  // phase 1, second half: w_e = c_e 2^F - lambda_u and the own lambdas into buffer bf
+  auto settle = [&](int i, int bf) {
+    const int4 tl = s_mt[i];
+    const int ne = s_me1[i] - tl.w, nv = tl.y - tl.x;
+    int* w = s_w + bf * TE;
+    int* lv = s_lv + bf * TN;
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+      const int e = tid + k * T;
+      if (e < ne) w[e] = (c[k] << F) - g[k];
+    }
+#pragma unroll
+    for (int k = 0; k < KN; ++k) {
+      const int v = tid + k * T;
+      if (v < nv) lv[v] = gl[k];
+    }
+  };
+
   long long t = 0;
   unsigned ch = 0;
   int ovf = 0;
-  bool timed_out = false;  // this thread's wait for slot j_end gave up
-  long long j_end = 0;
-  if (tid == 0) s_stop = 0;
+  bool prepared = false;  // slot j went through phase 1 (into buffer j & 1)
   __syncthreads();
 
   for (long long j = 0;; ++j) {
-    if (tid == 0) produce(q++);
     const int st = (int)(j % S);
     const int i = s_hdr[st];
     const int32_t* lin = (t & 1) ? lam1 : lam0;
     int32_t* lout = (t & 1) ? lam0 : lam1;
     if (i >= 0) {
-      const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&s_full[st]);
-      const bool ok = mbar_wait_bounded(mb, (phase_bits >> st) & 1u, kBulkWaitLimit);
-      phase_bits ^= 1u << st;
+      const int bj = (int)(j & 1);
+      if (!prepared) {  // first tile after a sweep boundary
+        if (!wait_slot(j)) {
+          if (tid == 0) s_abort = 1;
+          break;
+        }
+        gather(i, st, lin);
+        settle(i, bj);
+        __syncthreads();
+      }
+      // look ahead: the next slot's copy was issued at least one tile ago
+      const int st1 = (int)((j + 1) % S);
+      const int i1 = s_hdr[st1];
+      bool pre = false;
+      if (i1 >= 0) {
+        if (!wait_slot(j + 1)) {
+          if (tid == 0) s_abort = 1;
+          break;
+        }
+        gather(i1, st1, lin);
+        pre = true;
+      }
+      if (issuer) produce(q++);  // slot j + S - 1 into the stage tile j - 1 freed
+      // phase 2 of tile j: top-3 per row (Eq. 9), update (Eq. 10)
       const int4 tl = s_mt[i];
-      const int v0 = tl.x, nv = tl.y - tl.x, E0 = tl.w, ne = s_me1[i] - tl.w;
-      const int2* sec = reinterpret_cast<const int2*>(smem + st * kStageBytes) + (E0 - (E0 & ~1));
+      const int v0 = tl.x, nv = tl.y - tl.x, E0 = tl.w;
       const int* srp = reinterpret_cast<const int*>(smem + st * kStageBytes + kStageEcBytes) + (v0 - (v0 & ~3));
-      if (tid == 0) s_tile_ch = 0;
-      if (ok) {
-#pragma unroll 4
-        for (int e = tid; e < ne; e += T) {
-          const int2 w = sec[e];
-          s_w[e] = (w.y << F) - ld_lam(lin + w.x, pol_lam);
+      const int* w = s_w + bj * TE;
+      const int* lvb = s_lv + bj * TN;
+      unsigned tch = 0;
+      for (int k = tid; k < nv; k += T) {
+        const int lv = lvb[k];
+        // two independent top-3 chains over alternate entries, merged (Eq. 9)
+        int a = INT_MAX, bb = INT_MAX, cc = INT_MAX, a1 = INT_MAX, b1 = INT_MAX, c1 = INT_MAX;
+        const int e_end = srp[k + 1] - E0;
+        int e = srp[k] - E0;
+        for (; e + 1 < e_end; e += 2) {
+          top3_insert_minmax(w[e] - lv, a, bb, cc);
+          top3_insert_minmax(w[e + 1] - lv, a1, b1, c1);
         }
+        if (e < e_end) top3_insert_minmax(w[e] - lv, a, bb, cc);
+        top3_merge(a1, b1, c1, a, bb, cc);
+        const long long d = gdp_step(bb, cc, shift);  // Eq. 10, truncated toward 0
+        const long long nl = (long long)lv + d;
+        ovf |= (nl >= kLamLimit || nl <= -kLamLimit);
+        lout[v0 + k] = (int32_t)nl;
+        tch += (d != 0);
       }
+      if (pre) settle(i1, bj ^ 1);
+      tch = __reduce_add_sync(0xffffffffu, tch);
+      if (lane == 0 && tch) atomicAdd(&s_tile_ch[bj], tch);
+      ch += (lane == 0) ? tch : 0;
       __syncthreads();
-      if (ok) {
-        for (int k = tid; k < nv; k += T) {
-          const int lv = ld_lam(lin + v0 + k, pol_lam);
-          int a = INT_MAX, bb = INT_MAX, c = INT_MAX;
-          const int e_end = srp[k + 1] - E0;
-          for (int e = srp[k] - E0; e < e_end; ++e) top3_insert_minmax(s_w[e] - lv, a, bb, c);  // Eq. 9
-          const long long d = ((long long)bb + (long long)c) / div;  // Eq. 10, truncated toward 0
-          const long long nl = (long long)lv + d;
-          ovf |= (nl >= kLamLimit || nl <= -kLamLimit);
-          lout[v0 + k] = (int32_t)nl;
-          if (d != 0) {
-            atomicAdd(&s_tile_ch, 1u);
-            ++ch;
-          }
-        }
+      // the count of tile j is complete; its slot is reset before any thread can
+      // reach tile j + 2, which reuses it (tile j + 1 passes a barrier first)
+      if (tid == 0) {
+        if (s_tile_ch[bj]) atomicAdd(&seg_ch[(size_t)tl.z * 3 + (t % 3)], (unsigned long long)s_tile_ch[bj]);
+        s_tile_ch[bj] = 0;
       }
-      if (!ok) s_stop = 1;  // a copy never landed: stop after this tile
-      __syncthreads();
-      if (tid == 0 && s_tile_ch)
-        atomicAdd(&seg_ch[(size_t)tl.z * 3 + (t % 3)], (unsigned long long)s_tile_ch);
-      if (s_stop) {
-        if (tid == 0) atomicOr(&ctl->status, kGdpTimeout);
-        timed_out = !ok;
-        j_end = j;
-        break;
-      }
+      prepared = pre;
       continue;
     }
     // end of sweep t: totals, grid barrier, freezes, stop test
+    if (issuer) produce(q++);
+    prepared = false;
+    if (waited == j) waited = j + 1;  // an END slot has no copy
     ch = warp_sum_u(ch);
     ovf = __any_sync(0xffffffffu, ovf);
     if (lane == 0) {
@@ -288,23 +371,20 @@ gdp_batch_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ iec,
       s_stop = stop || (stv != 0) || (chg == 0) || (t + 1 >= max_sweeps);
     }
     __syncthreads();
-    if (s_stop) {
-      j_end = j;
-      break;
-    }
+    if (s_stop) break;
     ++t;
   }
+  if (s_abort && tid == 0) atomicOr(&ctl->status, kGdpTimeout);
+  __syncthreads();
   // Wait (bounded) for the copies still in flight before the shared memory goes
-  // away: the issued slots after the last one consumed, and that one too if
-  // its own wait gave up.  Consecutive slots use distinct stages, and a stage's
-  // parity bit counts the uses already consumed.
-  if (tid == 0) {
-    for (long long sl = timed_out ? j_end : j_end + 1; sl < q; ++sl) {
+  // away: every issued slot from `waited` on.  Consecutive slots use distinct
+  // stages, and a stage's parity bit counts the uses already waited for.
+  if (issuer) {
+    for (long long sl = waited; sl < q; ++sl) {
       const int stg = (int)(sl % S);
       if (s_hdr[stg] < 0) continue;
-      uint32_t par = (phase_bits >> stg) & 1u;
-      if (sl == j_end) par ^= 1u;  // already toggled when it was consumed
-      mbar_wait_bounded((uint32_t)__cvta_generic_to_shared(&s_full[stg]), par, kBulkWaitLimit);
+      mbar_wait_bounded((uint32_t)__cvta_generic_to_shared(&s_full[stg]), (phase_bits >> stg) & 1u, kBulkWaitLimit);
+      phase_bits ^= 1u << stg;
     }
   }
 }
@@ -332,7 +412,6 @@ gdp_batch_warp_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ 
   __shared__ __align__(8) unsigned long long s_full[W * S];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int GW = gridDim.x * W, gw = blockIdx.x * W + warp;
-  const long long div = 1LL << shift;
   volatile GdpCtl* vc = ctl;
   volatile uint8_t* vact = active;
 
@@ -432,10 +511,16 @@ gdp_batch_warp_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ 
       unsigned chg = 0;
       for (int k = lane; k < nv; k += 32) {
         const int lv = ld_lam(lin + v0 + k, pol_lam);
-        int a = INT_MAX, bb = INT_MAX, c = INT_MAX;
+        int a = INT_MAX, bb = INT_MAX, c = INT_MAX, a1 = INT_MAX, b1 = INT_MAX, c1 = INT_MAX;
         const int e_end = srp[k + 1] - E0;
-        for (int e = srp[k] - E0; e < e_end; ++e) top3_insert_minmax(sec[e].x - lv, a, bb, c);  // Eq. 9
-        const long long d = ((long long)bb + (long long)c) / div;  // Eq. 10, truncated toward 0
+        int e = srp[k] - E0;
+        for (; e + 1 < e_end; e += 2) {  // Eq. 9, two chains over alternate entries
+          top3_insert_minmax(sec[e].x - lv, a, bb, c);
+          top3_insert_minmax(sec[e + 1].x - lv, a1, b1, c1);
+        }
+        if (e < e_end) top3_insert_minmax(sec[e].x - lv, a, bb, c);
+        top3_merge(a1, b1, c1, a, bb, c);
+        const long long d = gdp_step(bb, c, shift);  // Eq. 10, truncated toward 0
         const long long nl = (long long)lv + d;
         ovf |= (nl >= kLamLimit || nl <= -kLamLimit);
         lout[v0 + k] = (int32_t)nl;
@@ -522,10 +607,10 @@ struct BatchShapeDef {
   int threads, stages, per_sm, te, tn, warp_tiles;
 };
 constexpr BatchShapeDef kBatchShapes[] = {
-    {512, 2, 2, 4096, 1536, 0}, {512, 2, 4, 2048, 768, 0}, {256, 2, 4, 2048, 768, 0},
-    {512, 3, 3, 2048, 768, 0},  {1024, 3, 1, 4096, 1536, 0}, {256, 2, 6, 1024, 384, 0},
-    {512, 4, 2, 2048, 768, 0},  {1024, 2, 1, 256, 96, 1},    {512, 2, 2, 256, 96, 1},
-    {768, 3, 1, 256, 96, 1},    {512, 2, 1, 512, 176, 1},    {512, 3, 1, 256, 96, 1}};
+    {512, 3, 2, 2048, 768, 0},  {512, 3, 3, 1024, 384, 0},  {256, 3, 4, 1024, 384, 0},
+    {256, 3, 6, 512, 192, 0},   {1024, 3, 1, 2048, 768, 0}, {256, 3, 3, 2048, 768, 0},
+    {512, 4, 2, 1024, 384, 0},  {1024, 2, 1, 256, 96, 1},   {512, 2, 2, 256, 96, 1},
+    {768, 3, 1, 256, 96, 1},    {512, 2, 1, 512, 176, 1},   {512, 3, 1, 256, 96, 1}};
 constexpr int kNumBatchShapes = (int)(sizeof(kBatchShapes) / sizeof(kBatchShapes[0]));
 
 template <int I>
@@ -564,7 +649,7 @@ static size_t batch_smem(int shape, int mcap) {
     const int w = d.threads / 32;
     return (size_t)w * d.stages * stage_bytes(d.te, d.tn) + (size_t)w * mcap * 21 + 16;
   }
-  return (size_t)d.stages * stage_bytes(d.te, d.tn) + (size_t)d.te * 4 + (size_t)mcap * 21 + 16;
+  return (size_t)d.stages * stage_bytes(d.te, d.tn) + (size_t)(2 * d.te + 2 * d.tn) * 4 + (size_t)mcap * 21 + 16;
 }
 
 // tile-table capacity per CTA (CTA form) or per warp (warp form)

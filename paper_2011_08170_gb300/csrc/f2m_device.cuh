@@ -39,6 +39,20 @@ __device__ __forceinline__ void top3_insert_minmax(int z, int& a, int& b, int& c
   a = min(a, z);
 }
 
+// Eq. 10 step: trunc((z2 + z3) / 2^shift) toward zero, exactly, by shifts
+// (a 64-bit division by a run-time divisor is a long software routine)
+__device__ __forceinline__ long long gdp_step(int z2, int z3, int shift) {
+  const long long s = (long long)z2 + (long long)z3;
+  return s >= 0 ? (s >> shift) : -((-s) >> shift);
+}
+
+// Top-3 of two partial top-3 sets (each ascending): the 3 smallest of their union.
+__device__ __forceinline__ void top3_merge(int a1, int b1, int c1, int& a, int& b, int& c) {
+  top3_insert_minmax(a1, a, b, c);
+  top3_insert_minmax(b1, a, b, c);
+  top3_insert_minmax(c1, a, b, c);
+}
+
 // Load that bypasses L1: lambda is rewritten by other SMs between sweeps.
 __device__ __forceinline__ int ld_cg(const int* p) { return __ldcg(p); }
 

@@ -39,7 +39,6 @@ gdp_persistent_kernel(const int32_t* __restrict__ rp, const int2* __restrict__ e
   const long long per_block = blockDim.x / G;
   const long long gid = (long long)blockIdx.x * per_block + tid / G;
   const long long ngroups = (long long)gridDim.x * per_block;
-  const long long div = 1LL << shift;
   const int nwarps = blockDim.x >> 5;
 
   for (long long t = 0; t < max_sweeps; ++t) {
@@ -71,7 +70,7 @@ gdp_persistent_kernel(const int32_t* __restrict__ rp, const int2* __restrict__ e
         }
       }
       if (sub == 0) {
-        const long long d = ((long long)b + (long long)c) / div;  // Eq. 10, truncated toward 0
+        const long long d = gdp_step(b, c, shift);  // Eq. 10, truncated toward 0
         const long long nl = (long long)lv + d;
         ovf |= (nl >= kLamLimit || nl <= -kLamLimit);
         lout[v] = (int32_t)nl;

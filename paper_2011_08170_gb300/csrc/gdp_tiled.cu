@@ -317,7 +317,6 @@ gdp_tiled_kernel(const int32_t* __restrict__ part, const int32_t* __restrict__ h
 
   const int tid = threadIdx.x, T = blockDim.x, b = blockIdx.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = T >> 5;
-  const long long div = 1LL << shift;
 
   const int lo = part[b], hi = part[b + 1], own = hi - lo;
   const int hb = hoff[b], H = hoff[b + 1] - hb;
@@ -370,15 +369,25 @@ gdp_tiled_kernel(const int32_t* __restrict__ part, const int32_t* __restrict__ h
       const int vl = s_order[p];
       const int lv = s_in[vl];
       const int2* ent = s_lec + sl.x + (p & 31);
-      int a = INT_MAX, bb = INT_MAX, c = INT_MAX;
+      int a = INT_MAX, bb = INT_MAX, c = INT_MAX, a1 = INT_MAX, b1 = INT_MAX, c1 = INT_MAX;
       long long neg = 0;
-      for (int k = 0; k < sl.y; ++k) {
-        const int2 q = ent[k * 32];
+      int k = 0;
+      for (; k + 1 < sl.y; k += 2) {  // two top-3 chains over alternate entries, merged
+        const int2 q = ent[k * 32], q1 = ent[(k + 1) * 32];
         const int z = q.y - lv - s_in[q.x];  // Eq. 9
+        const int z1 = q1.y - lv - s_in[q1.x];
+        neg += min(z, 0) + min(z1, 0);
+        top3_insert_minmax(z, a, bb, c);
+        top3_insert_minmax(z1, a1, b1, c1);
+      }
+      if (k < sl.y) {
+        const int2 q = ent[k * 32];
+        const int z = q.y - lv - s_in[q.x];
         neg += min(z, 0);
         top3_insert_minmax(z, a, bb, c);
       }
-      const long long d = ((long long)bb + (long long)c) / div;  // Eq. 10, truncated toward 0
+      top3_merge(a1, b1, c1, a, bb, c);
+      const long long d = gdp_step(bb, c, shift);  // Eq. 10, truncated toward 0
       const long long nl = (long long)lv + d;
       ovf |= (nl >= kLamLimit || nl <= -kLamLimit);
       s_out[vl] = (int32_t)nl;
