@@ -33,16 +33,24 @@ struct f2m_batch {
   uint8_t* d_active = nullptr;
   unsigned long long* d_seg_ch = nullptr;
   long long* d_seg_sweeps = nullptr;
-  int4* d_tiles = nullptr;          // node tiles of the batch kernel (+ sentinel)
-  int32_t ntiles = 0;
-  int32_t grid = 0;
+  // tiles of the chosen kernel shape over the current CSR, all instances (host)
+  std::vector<int4> tiles_all;
+  std::vector<int32_t> e1_all;
   int32_t shape = -1;               // batch kernel shape in use
+  int32_t grid = 0;
   int64_t tiles_version = -1;
-  // captured GDP phase (replayed on a private stream)
+  // the list of one launch: pinned host copy -> device (captured launch reads them)
+  int4* h_tiles = nullptr;
+  int32_t* h_e1 = nullptr;
+  BatchChunk* h_chunk = nullptr;
+  int4* d_tiles = nullptr;
+  int32_t* d_e1 = nullptr;
+  BatchChunk* d_chunk = nullptr;
+  int32_t tiles_cap = 0;
+  // captured launch (list upload, resets, kernel, read-backs), replayed on a private stream
   cudaStream_t gs = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int64_t graph_version = -1;       // tiles_version the graph belongs to
-  const int32_t* graph_lam = nullptr;
   long long graph_kernels = 0;      // kernels per replay
   bool graph_failed = false;
   cudaEvent_t e_in = nullptr, e_out = nullptr;
@@ -82,7 +90,11 @@ extern "C" void f2m_destroy_batch(f2m_batch* b) {
     cudaStreamSynchronize(b->u->st);
     f2m_destroy(b->u);
   }
-  dfree(b->d_active); dfree(b->d_seg_ch); dfree(b->d_seg_sweeps); dfree(b->d_tiles);
+  dfree(b->d_active); dfree(b->d_seg_ch); dfree(b->d_seg_sweeps); dfree(b->d_tiles); dfree(b->d_e1);
+  dfree(b->d_chunk);
+  if (b->h_tiles) cudaFreeHost(b->h_tiles);
+  if (b->h_e1) cudaFreeHost(b->h_e1);
+  if (b->h_chunk) cudaFreeHost(b->h_chunk);
   dfree(b->d_seg_b2); dfree(b->d_seg_bad); dfree(b->d_tmp_a); dfree(b->d_tmp_b);
   dfree(b->d_mask); dfree(b->d_res_lam); dfree(b->d_res_rp); dfree(b->d_res_ec); dfree(b->d_res_x2);
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
@@ -185,6 +197,8 @@ extern "C" f2m_status f2m_create_batch(int32_t count, const int32_t* n, const in
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_ctl, sizeof(GdpCtl));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_sw, sizeof(long long) * count);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_still, count);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_chunk, sizeof(BatchChunk));
+    if (e == cudaSuccess) e = dalloc(&b->d_chunk, 1);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { f2m_destroy_batch(b); s = cuda_fail(nullptr, e, "create_batch: setup"); break; }
     *out = b;
@@ -195,20 +209,16 @@ extern "C" f2m_status f2m_create_batch(int32_t count, const int32_t* n, const in
 
 // ---- GDP phase: tiles, kernel shape (autotuned), captured launch ----------------------
 
-// Process-wide choice of the autotuner, keyed by (SMs, instances, nodes,
-// entries / 2^16): a batch of the same shape created again skips the trials.
-static std::mutex g_tune_mu;
-static std::map<std::array<long long, 4>, int> g_tune;
-
-// tiles of at most te entries and tn nodes over the current renumbered CSR,
-// with the sentinel {n, n, -1, nnz}; replaces *d_tiles
-static f2m_status batch_tiles(f2m_batch* b, int te, int tn, int4** d_tiles, int32_t* ntiles) {
+// tiles of at most te entries and tn nodes over the current renumbered CSR
+// (host lists: {first node, end node, instance, first entry} and end entries)
+static f2m_status batch_tiles(f2m_batch* b, int te, int tn, std::vector<int4>& tiles, std::vector<int32_t>& e1) {
   f2m_ctx* c = b->u;
   GdpPlan& P = c->plan;
   std::vector<int32_t> irp(c->n + 1);
   CK(c, cudaMemcpyAsync(irp.data(), P.irp, sizeof(int32_t) * (c->n + 1), cudaMemcpyDeviceToHost, c->st));
   CK(c, cudaStreamSynchronize(c->st));
-  std::vector<int4> tiles;
+  tiles.clear();
+  e1.clear();
   for (int32_t s = 0; s < b->count; ++s) {
     int32_t v = c->seg_off[s];
     const int32_t end = c->seg_off[s + 1];
@@ -218,17 +228,37 @@ static f2m_status batch_tiles(f2m_batch* b, int te, int tn, int4** d_tiles, int3
       if (v == start)
         return fail(c, F2M_ERR_INVALID_ARG, "a node has more candidate edges than a batch tile holds");
       tiles.push_back(make_int4(start, v, s, e0));
+      e1.push_back(irp[v]);
     }
   }
-  *ntiles = (int32_t)tiles.size();
-  tiles.push_back(make_int4(c->n, c->n, -1, irp[c->n]));
-  dfree(*d_tiles);
-  CK(c, dalloc(d_tiles, (int64_t)tiles.size()));
-  CK(c, cudaMemcpyAsync(*d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, c->st));
   return F2M_OK;
 }
 
-// CTAs of a cooperative launch of `shape` over ntiles tiles (0: the shape does not run)
+// room for `need` tiles in the pinned and device list buffers (drops the captured graph)
+static f2m_status batch_list_reserve(f2m_batch* b, int32_t need) {
+  f2m_ctx* c = b->u;
+  if (need <= b->tiles_cap) return F2M_OK;
+  CK(c, cudaStreamSynchronize(c->st));
+  CK(c, cudaStreamSynchronize(b->gs));
+  if (b->h_tiles) cudaFreeHost(b->h_tiles);
+  if (b->h_e1) cudaFreeHost(b->h_e1);
+  b->h_tiles = nullptr;
+  b->h_e1 = nullptr;
+  dfree(b->d_tiles);
+  dfree(b->d_e1);
+  b->tiles_cap = 0;
+  const int32_t cap = need + need / 8 + 64;
+  CK(c, cudaMallocHost((void**)&b->h_tiles, sizeof(int4) * cap));
+  CK(c, cudaMallocHost((void**)&b->h_e1, sizeof(int32_t) * cap));
+  CK(c, dalloc(&b->d_tiles, cap));
+  CK(c, dalloc(&b->d_e1, cap));
+  b->tiles_cap = cap;
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  b->gexec = nullptr;
+  return F2M_OK;
+}
+
+// CTAs of a cooperative launch of `shape` over up to ntiles tiles (0: the shape does not run)
 static int32_t batch_grid(f2m_batch* b, int shape, int32_t ntiles) {
   const int sms = b->u->num_sms;
   int per_sm = batch_shape_blocks(shape, 1);
@@ -246,36 +276,62 @@ static int32_t batch_grid(f2m_batch* b, int shape, int32_t ntiles) {
   return G < 1 ? 1 : G;
 }
 
-// Device work of one phase on stream st: lambda into the renumbered double
-// buffer, the active flags (pinned host -> device), the persistent kernel,
-// the results back to pinned host memory, lambda back to caller order.
-static cudaError_t enqueue_phase(f2m_batch* b, cudaStream_t st, int shape, int32_t G, const int4* d_tiles,
-                                 int32_t ntiles, int64_t max_sweeps, const uint8_t* d_active_src_host_or_null) {
+// One launch on stream st: the list and parameters (pinned host -> device),
+// per-launch resets, the persistent kernel, the results back to pinned memory.
+static cudaError_t enqueue_launch(f2m_batch* b, cudaStream_t st, int shape, int32_t G, int32_t max_tiles) {
   f2m_ctx* c = b->u;
   GdpPlan& P = c->plan;
-  int32_t* l0 = P.ilam[0];
-  int32_t* l1 = P.ilam[1];
-  cudaError_t e = gather_perm(c->d_lam[c->cur], P.perm, c->n, l0, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(l1, l0, sizeof(int32_t) * c->n, cudaMemcpyDeviceToDevice, st);
-  if (e == cudaSuccess) {
-    if (d_active_src_host_or_null)
-      e = cudaMemcpyAsync(b->d_active, d_active_src_host_or_null, b->count, cudaMemcpyHostToDevice, st);
-    else
-      e = cudaMemsetAsync(b->d_active, 1, b->count, st);
-  }
+  cudaError_t e = cudaMemcpyAsync(b->d_chunk, b->h_chunk, sizeof(BatchChunk), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_tiles, b->h_tiles, sizeof(int4) * b->tiles_cap, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_e1, b->h_e1, sizeof(int32_t) * b->tiles_cap, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_seg_ch, 0, sizeof(unsigned long long) * 3 * b->count, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_seg_sweeps, 0, sizeof(long long) * b->count, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_gdp, 0, sizeof(GdpCtl), st);
   if (e == cudaSuccess)
-    e = launch_gdp_batch(shape, P.irp, P.iec, d_tiles, ntiles, G, b->count, b->d_active, b->d_seg_ch,
-                         b->d_seg_sweeps, l0, l1, c->p.frac_bits, c->p.damping_shift, max_sweeps, c->d_gdp,
-                         c->p.barrier_budget_cycles, st);
+    e = launch_gdp_batch(shape, P.irp, P.iec, b->d_tiles, b->d_e1, b->d_chunk, max_tiles, G, b->count,
+                         b->d_active, b->d_seg_ch, b->d_seg_sweeps, P.ilam[0], P.ilam[1], c->p.frac_bits,
+                         c->p.damping_shift, c->d_gdp, c->p.barrier_budget_cycles, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_ctl, c->d_gdp, sizeof(GdpCtl), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->h_sw, b->d_seg_sweeps, sizeof(long long) * b->count, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_still, b->d_active, b->count, cudaMemcpyDeviceToHost, st);
   return e;
 }
+
+// start of a phase: lambda into the renumbered double buffer, active flags, sweep records
+static cudaError_t enqueue_phase_start(f2m_batch* b, cudaStream_t st, const uint8_t* h_active) {
+  f2m_ctx* c = b->u;
+  GdpPlan& P = c->plan;
+  cudaError_t e = gather_perm(c->d_lam[c->cur], P.perm, c->n, P.ilam[0], st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(P.ilam[1], P.ilam[0], sizeof(int32_t) * c->n, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) {
+    if (h_active)
+      e = cudaMemcpyAsync(b->d_active, h_active, b->count, cudaMemcpyHostToDevice, st);
+    else
+      e = cudaMemsetAsync(b->d_active, 1, b->count, st);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_seg_sweeps, 0, sizeof(long long) * b->count, st);
+  return e;
+}
+
+// the list of one launch: the tiles of the instances flagged in `act`
+static int32_t fill_list(f2m_batch* b, const std::vector<int4>& tiles, const std::vector<int32_t>& e1,
+                         const uint8_t* act) {
+  int32_t m = 0;
+  for (size_t k = 0; k < tiles.size(); ++k) {
+    if (act && !act[tiles[k].z]) continue;
+    b->h_tiles[m] = tiles[k];
+    b->h_e1[m] = e1[k];
+    ++m;
+  }
+  return m;
+}
+
+// Process-wide choice of the autotuner, keyed by (SMs, instances, nodes,
+// entries / 2^16): a batch of the same shape created again skips the trials.
+static std::mutex g_tune_mu;
+static std::map<std::array<long long, 4>, int> g_tune;
 
 // Autotuner: time a few sweeps of every shape that runs on this batch (from
 // the current lambda, all instances active, nothing kept) and keep the
@@ -293,42 +349,37 @@ static f2m_status batch_autotune(f2m_batch* b) {
   }
   int best = -1;
   double best_t = 0;
-  int4* d_t = nullptr;
-  f2m_status st_out = F2M_OK;
-  for (int sh = 0; sh < batch_num_shapes() && st_out == F2M_OK; ++sh) {
+  std::vector<int4> tiles;
+  std::vector<int32_t> e1;
+  for (int sh = 0; sh < batch_num_shapes(); ++sh) {
     int te = 0, tn = 0;
     batch_shape_tile(sh, &te, &tn);
-    int32_t nt = 0;
-    st_out = batch_tiles(b, te, tn, &d_t, &nt);
-    if (st_out != F2M_OK) break;
+    f2m_status s = batch_tiles(b, te, tn, tiles, e1);
+    if (s != F2M_OK) return s;
+    const int32_t nt = (int32_t)tiles.size();
     const int32_t G = batch_grid(b, sh, nt);
     if (G < 1) continue;
+    s = batch_list_reserve(b, nt);
+    if (s != F2M_OK) return s;
+    fill_list(b, tiles, e1, nullptr);
     double t = 0;
     for (int rep = 0; rep < 2; ++rep) {  // the first run only warms up
-      const int64_t sweeps = rep == 0 ? 4 : 48;
-      cudaError_t e = cudaEventRecord(c->ev0, c->st);
-      if (e == cudaSuccess) e = enqueue_phase(b, c->st, sh, G, d_t, nt, sweeps, nullptr);
-      if (e == cudaSuccess) e = cudaEventRecord(c->ev1, c->st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
-      if (e != cudaSuccess) {
-        st_out = cuda_fail(c, e, "batch autotune");
-        break;
-      }
+      *b->h_chunk = BatchChunk{nt, 0, 0, rep == 0 ? 4 : 48};
+      CK(c, enqueue_phase_start(b, c->st, nullptr));
+      CK(c, cudaEventRecord(c->ev0, c->st));
+      CK(c, enqueue_launch(b, c->st, sh, G, nt));
+      CK(c, cudaEventRecord(c->ev1, c->st));
+      CK(c, cudaStreamSynchronize(c->st));
       float ms = 0.f;
       cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-      if (b->h_ctl->status & kGdpTimeout) {
-        st_out = fail(c, F2M_ERR_TIMEOUT, "device-wide barrier wait exceeded its budget");
-        break;
-      }
+      if (b->h_ctl->status & kGdpTimeout) return fail(c, F2M_ERR_TIMEOUT, "device-wide barrier wait exceeded its budget");
       t = ms / (double)(b->h_ctl->sweeps > 0 ? b->h_ctl->sweeps : 1);
     }
-    if (st_out == F2M_OK && (best < 0 || t < best_t)) {
+    if (best < 0 || t < best_t) {
       best = sh;
       best_t = t;
     }
   }
-  dfree(d_t);
-  if (st_out != F2M_OK) return st_out;
   if (best < 0) return fail(c, F2M_ERR_CUDA, "no batch kernel shape fits this device");
   b->shape = best;
   std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -336,8 +387,12 @@ static f2m_status batch_autotune(f2m_batch* b) {
   return F2M_OK;
 }
 
-// One GDP phase over the segments flagged in `active` (host, one byte each);
-// adds each segment's sweeps to sweeps_out.
+// Sweeps per launch of a phase: after each launch the list is rebuilt from the
+// instances still active (even, so that every launch starts from buffer 0).
+constexpr long long kSweepsPerLaunch = 256;
+
+// One GDP phase over the instances flagged in `active` (host, one byte each);
+// adds each instance's sweeps to sweeps_out.
 static f2m_status batch_gdp_phase(f2m_batch* b, const std::vector<uint8_t>& active,
                                   std::vector<int64_t>& sweeps_out, double* ms) {
   f2m_ctx* c = b->u;
@@ -357,25 +412,28 @@ static f2m_status batch_gdp_phase(f2m_batch* b, const std::vector<uint8_t>& acti
     }
     int te = 0, tn = 0;
     batch_shape_tile(b->shape, &te, &tn);
-    s = batch_tiles(b, te, tn, &b->d_tiles, &b->ntiles);
+    s = batch_tiles(b, te, tn, b->tiles_all, b->e1_all);
     if (s != F2M_OK) return s;
-    b->grid = batch_grid(b, b->shape, b->ntiles);
+    s = batch_list_reserve(b, (int32_t)b->tiles_all.size());
+    if (s != F2M_OK) return s;
+    b->grid = batch_grid(b, b->shape, (int32_t)b->tiles_all.size());
     if (b->grid < 1) return fail(c, F2M_ERR_CUDA, "the batch kernel shape does not fit an SM");
     b->tiles_version = P.version;
   }
+  const int32_t max_tiles = (int32_t)b->tiles_all.size();
   std::memcpy(b->h_active, active.data(), b->count);
+  CK(c, enqueue_phase_start(b, c->st, b->h_active));
+  // capture one launch once per tile version; every launch of every phase replays it
   const bool graph = c->p.batch_graph && !b->graph_failed;
-  if (graph && (!b->gexec || b->graph_version != b->tiles_version || b->graph_lam != c->d_lam[c->cur])) {
+  if (graph && (!b->gexec || b->graph_version != b->tiles_version)) {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
+    CK(c, cudaStreamSynchronize(c->st));
     const long long before = f2m_kernel_launches();
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->gs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t e2 = enqueue_phase(b, b->gs, b->shape, b->grid, b->d_tiles, b->ntiles, c->p.max_iters,
-                                     b->h_active);
-      if (e2 == cudaSuccess)
-        e2 = launch_batch_scatter_final(P.ilam[0], P.ilam[1], c->d_gdp, P.perm, c->n, c->d_lam[c->cur], b->gs);
+      const cudaError_t e2 = enqueue_launch(b, b->gs, b->shape, b->grid, max_tiles);
       e = cudaStreamEndCapture(b->gs, &g);
       if (e == cudaSuccess && e2 != cudaSuccess) e = e2;
     }
@@ -390,35 +448,55 @@ static f2m_status batch_gdp_phase(f2m_batch* b, const std::vector<uint8_t>& acti
       b->graph_failed = true;
     } else {
       b->graph_version = b->tiles_version;
-      b->graph_lam = c->d_lam[c->cur];
     }
   }
-  if (graph && b->gexec) {
-    CK(c, cudaEventRecord(b->e_in, c->st));
-    CK(c, cudaStreamWaitEvent(b->gs, b->e_in, 0));
-    CK(c, cudaEventRecord(c->ev0, b->gs));
-    CK(c, cudaGraphLaunch(b->gexec, b->gs));
-    CK(c, cudaEventRecord(c->ev1, b->gs));
-    CK(c, cudaEventRecord(b->e_out, b->gs));
-    CK(c, cudaStreamWaitEvent(c->st, b->e_out, 0));
-    count_launches(b->graph_kernels);
-  } else {
-    CK(c, cudaEventRecord(c->ev0, c->st));
-    CK(c, enqueue_phase(b, c->st, b->shape, b->grid, b->d_tiles, b->ntiles, c->p.max_iters, b->h_active));
-    CK(c, launch_batch_scatter_final(P.ilam[0], P.ilam[1], c->d_gdp, P.perm, c->n, c->d_lam[c->cur], c->st));
-    CK(c, cudaEventRecord(c->ev1, c->st));
+  std::vector<uint8_t> act(active.begin(), active.end());
+  long long t_base = 0;
+  for (;;) {
+    const int32_t nt = fill_list(b, b->tiles_all, b->e1_all, act.data());
+    const long long left = c->p.max_iters - t_base;
+    *b->h_chunk = BatchChunk{nt, 0, t_base, left < kSweepsPerLaunch ? left : kSweepsPerLaunch};
+    if (b->gexec) {
+      CK(c, cudaEventRecord(b->e_in, c->st));
+      CK(c, cudaStreamWaitEvent(b->gs, b->e_in, 0));
+      CK(c, cudaEventRecord(c->ev0, b->gs));
+      CK(c, cudaGraphLaunch(b->gexec, b->gs));
+      CK(c, cudaEventRecord(c->ev1, b->gs));
+      CK(c, cudaEventRecord(b->e_out, b->gs));
+      CK(c, cudaStreamWaitEvent(c->st, b->e_out, 0));
+      count_launches(b->graph_kernels);
+    } else {
+      CK(c, cudaEventRecord(c->ev0, c->st));
+      CK(c, enqueue_launch(b, c->st, b->shape, b->grid, max_tiles));
+      CK(c, cudaEventRecord(c->ev1, c->st));
+    }
+    CK(c, cudaStreamSynchronize(c->st));
+    float t_ms = 0.f;
+    cudaEventElapsedTime(&t_ms, c->ev0, c->ev1);
+    if (ms) *ms += t_ms;
+    const GdpCtl h = *b->h_ctl;
+    if (h.status & kGdpTimeout) return fail(c, F2M_ERR_TIMEOUT, "device-wide barrier wait exceeded its budget");
+    if (h.status & kGdpOverflow) return fail(c, F2M_ERR_OVERFLOW, "|lambda| reached 2^29 in some instance");
+    bool any = false;
+    for (int32_t s = 0; s < b->count; ++s) {
+      if (!act[s]) continue;
+      if (!b->h_still[s]) {
+        sweeps_out[s] += b->h_sw[s];  // froze in this launch (the record includes t_base)
+        act[s] = 0;
+      } else {
+        any = true;
+      }
+    }
+    t_base += h.sweeps;
+    const bool more = any && !h.fixed_point && t_base < c->p.max_iters && (h.sweeps & 1) == 0;
+    if (!more) {
+      for (int32_t s = 0; s < b->count; ++s)
+        if (act[s]) sweeps_out[s] += t_base;  // ran to the cap
+      break;
+    }
   }
-  CK(c, cudaStreamSynchronize(c->st));
-  float t_ms = 0.f;
-  cudaEventElapsedTime(&t_ms, c->ev0, c->ev1);
-  if (ms) *ms += t_ms;
-  const GdpCtl h = *b->h_ctl;
-  if (h.status & kGdpTimeout) return fail(c, F2M_ERR_TIMEOUT, "device-wide barrier wait exceeded its budget");
-  if (h.status & kGdpOverflow) return fail(c, F2M_ERR_OVERFLOW, "|lambda| reached 2^29 in some instance");
-  for (int32_t s = 0; s < b->count; ++s) {
-    if (!active[s]) continue;
-    sweeps_out[s] += b->h_still[s] ? h.sweeps : b->h_sw[s];  // unfrozen ones ran to the cap
-  }
+  // lambda back to caller order from the buffer the last launch ended in
+  CK(c, launch_batch_scatter_final(P.ilam[0], P.ilam[1], c->d_gdp, P.perm, c->n, c->d_lam[c->cur], c->st));
   return F2M_OK;
 }
 

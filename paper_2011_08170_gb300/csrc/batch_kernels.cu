@@ -39,8 +39,10 @@ __device__ __forceinline__ int segment_of(const int32_t* seg_off, int nseg, int 
 
 // Tiles: contiguous node ranges of one segment with at most TE entries and TN
 // nodes (per kernel shape); tile k goes to CTA k mod G every sweep.
-// The tile table has a sentinel after the last tile, so tile k's entries are
-// [tiles[k].w, tiles[k+1].w) and its nodes [tiles[k].x, tiles[k].y).
+// Tile k's nodes are [tiles[k].x, tiles[k].y), its entries [tiles[k].w,
+// tiles_e1[k]); the list holds only the tiles of instances still active when
+// the launch was prepared (a phase is run as several launches, each over a
+// fresh list, so that the tiles of converged instances stop taking turns).
 //
 // A tile's {col, cost} entries and row offsets are moved into shared memory by
 // the bulk-copy engine (cp.async.bulk, completion counted in bytes on an
@@ -111,9 +113,12 @@ constexpr long long kBulkWaitLimit = 1LL << 24;
 template <int T, int S, int TE, int TN, int MINB>
 __global__ void __launch_bounds__(T, MINB)
 gdp_batch_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ iec,
-                 const int4* __restrict__ tiles, int32_t ntiles, int32_t nseg, uint8_t* active,
+                 const int4* __restrict__ tiles, const int32_t* __restrict__ tiles_e1,
+                 const BatchChunk* __restrict__ chunk, int32_t nseg, uint8_t* active,
                  unsigned long long* seg_ch, long long* seg_sweeps, int32_t* lam0, int32_t* lam1,
-                 int32_t F, int32_t shift, long long max_sweeps, GdpCtl* ctl, long long budget, int32_t mcap) {
+                 int32_t F, int32_t shift, GdpCtl* ctl, long long budget, int32_t mcap) {
+  const int32_t ntiles = chunk->ntiles;
+  const long long t_base = chunk->t_base, max_sweeps = chunk->max_sweeps;
   // Software pipeline over the CTA's tiles: while the top-3 phase of tile j
   // runs, the lambda gathers of tile j+1 (same sweep) are in flight, and the
   // copies of tiles j+2 .. j+S-1 are landing.
@@ -147,7 +152,7 @@ gdp_batch_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ iec,
     const int k = b + i * G;
     const int4 tl = tiles[k];
     s_mt[i] = tl;
-    s_me1[i] = tiles[k + 1].w;
+    s_me1[i] = tiles_e1[k];
     s_act[i] = vact[tl.z];
   }
   if (tid == 0) {
@@ -354,7 +359,7 @@ gdp_batch_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ iec,
         volatile unsigned long long* slot = seg_ch + (size_t)sgi * 3;
         if (vact[sgi] && slot[t % 3] == 0) {
           vact[sgi] = 0;
-          seg_sweeps[sgi] = t + 1;
+          seg_sweeps[sgi] = t_base + t + 1;
         }
         slot[(t + 2) % 3] = 0;
       }
@@ -397,10 +402,12 @@ gdp_batch_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ iec,
 template <int W, int S, int TE, int TN, int MINB>
 __global__ void __launch_bounds__(W * 32, MINB)
 gdp_batch_warp_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ iec,
-                      const int4* __restrict__ tiles, int32_t ntiles, int32_t nseg, uint8_t* active,
+                      const int4* __restrict__ tiles, const int32_t* __restrict__ tiles_e1,
+                      const BatchChunk* __restrict__ chunk, int32_t nseg, uint8_t* active,
                       unsigned long long* seg_ch, long long* seg_sweeps, int32_t* lam0, int32_t* lam1,
-                      int32_t F, int32_t shift, long long max_sweeps, GdpCtl* ctl, long long budget,
-                      int32_t mcap) {
+                      int32_t F, int32_t shift, GdpCtl* ctl, long long budget, int32_t mcap) {
+  const int32_t ntiles = chunk->ntiles;
+  const long long t_base = chunk->t_base, max_sweeps = chunk->max_sweeps;
   constexpr int kStageEcBytes = stage_ec_bytes(TE);
   constexpr int kStageBytes = stage_bytes(TE, TN);
   static_assert(kStageBytes % 16 == 0 && kStageEcBytes % 16 == 0, "stage alignment");
@@ -428,7 +435,7 @@ gdp_batch_warp_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ 
     const int k = gw + i * GW;
     const int4 tl = tiles[k];
     m_mt[i] = tl;
-    m_me1[i] = tiles[k + 1].w;
+    m_me1[i] = tiles_e1[k];
     m_act[i] = vact[tl.z];
   }
   if (lane == 0)
@@ -564,7 +571,7 @@ gdp_batch_warp_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ 
         volatile unsigned long long* slot = seg_ch + (size_t)sgi * 3;
         if (vact[sgi] && slot[t % 3] == 0) {
           vact[sgi] = 0;
-          seg_sweeps[sgi] = t + 1;
+          seg_sweeps[sgi] = t_base + t + 1;
         }
         slot[(t + 2) % 3] = 0;
       }
@@ -690,28 +697,27 @@ int batch_shape_blocks(int shape, int mcap) {
   return per_sm < kBatchShapes[shape].per_sm ? per_sm : kBatchShapes[shape].per_sm;
 }
 
-cudaError_t launch_gdp_batch(int shape, const int32_t* irp, const int2* iec, const int4* tiles, int32_t ntiles,
-                             int32_t G, int32_t nseg, uint8_t* active, unsigned long long* seg_ch,
-                             long long* seg_sweeps, int32_t* lam0, int32_t* lam1, int32_t F,
-                             int32_t shift, int64_t max_sweeps, GdpCtl* ctl, long long budget,
-                             cudaStream_t st) {
+cudaError_t launch_gdp_batch(int shape, const int32_t* irp, const int2* iec, const int4* tiles,
+                             const int32_t* tiles_e1, const BatchChunk* chunk, int32_t max_tiles, int32_t G,
+                             int32_t nseg, uint8_t* active, unsigned long long* seg_ch, long long* seg_sweeps,
+                             int32_t* lam0, int32_t* lam1, int32_t F, int32_t shift, GdpCtl* ctl,
+                             long long budget, cudaStream_t st) {
   if (shape < 0 || shape >= kNumBatchShapes || G < 1) return cudaErrorInvalidValue;
-  long long ms = max_sweeps;
-  const int32_t mcap = batch_mcap(shape, ntiles, G);
+  const int32_t mcap = batch_mcap(shape, max_tiles, G);
   const size_t sm = batch_smem(shape, mcap);
   const void* k = batch_kernel_of(shape);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  void* args[] = {(void*)&irp, (void*)&iec, (void*)&tiles, (void*)&ntiles, (void*)&nseg,
+  void* args[] = {(void*)&irp, (void*)&iec, (void*)&tiles, (void*)&tiles_e1, (void*)&chunk, (void*)&nseg,
                   (void*)&active, (void*)&seg_ch, (void*)&seg_sweeps, (void*)&lam0, (void*)&lam1,
-                  (void*)&F, (void*)&shift, (void*)&ms, (void*)&ctl, (void*)&budget, (void*)&mcap};
+                  (void*)&F, (void*)&shift, (void*)&ctl, (void*)&budget, (void*)&mcap};
   e = cudaLaunchCooperativeKernel(k, dim3(G), dim3(kBatchShapes[shape].threads), args, sm, st);
   count_launch();
   return e;
 }
 
-// dst[perm[i]] = (ctl->sweeps odd ? lam1 : lam0)[i]: the buffer a GDP phase
-// ended in, chosen on the device so that a captured phase needs no host decision
+// dst[perm[i]] = (ctl->sweeps odd ? lam1 : lam0)[i]: the buffer a GDP launch
+// ended in, chosen on the device so that no host decision is needed
 __global__ void batch_scatter_final_kernel(const int32_t* __restrict__ lam0, const int32_t* __restrict__ lam1,
                                            const GdpCtl* ctl, const int32_t* __restrict__ perm, int32_t n,
                                            int32_t* __restrict__ dst) {

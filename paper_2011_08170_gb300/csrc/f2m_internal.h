@@ -179,9 +179,17 @@ cudaError_t fin_scatter(const GdpPlan& p, const int32_t* rp, const uint8_t* x_in
                         const int32_t* seg_off, int32_t nseg, const uint8_t* include,
                         cudaStream_t st);
 // ---- batched solver (batch_kernels.cu) --------------------------------------------
-// tiles {first node, end node, segment, first entry} over the renumbered CSR,
-// followed by a sentinel {n, n, -1, nnz}; one cooperative launch of G CTAs of
-// the given shape (see batch_kernels.cu)
+// Parameters of one launch of a batched GDP kernel, read from device memory so
+// that a captured launch can be replayed with new values.
+struct BatchChunk {
+  int32_t ntiles;        // tiles in the list (those of the instances still active)
+  int32_t pad;
+  long long t_base;      // sweeps run by earlier launches of this phase
+  long long max_sweeps;  // sweeps this launch may run
+};
+// tiles {first node, end node, segment, first entry} over the renumbered CSR
+// with their end entries in tiles_e1; one cooperative launch of G CTAs of the
+// given shape (see batch_kernels.cu); max_tiles sizes the per-CTA tile table
 int batch_num_shapes();
 // lambda of the buffer a batch GDP phase ended in, scattered to caller order
 cudaError_t launch_batch_scatter_final(const int32_t* lam0, const int32_t* lam1, const GdpCtl* ctl,
@@ -189,11 +197,11 @@ cudaError_t launch_batch_scatter_final(const int32_t* lam0, const int32_t* lam1,
 int batch_shape_blocks(int shape, int mcap);  // CTAs per SM, 0 if the shape does not run
 int batch_shape_tile(int shape, int* te, int* tn);  // tile entries and nodes of a shape
 int batch_shape_units(int shape);  // tile owners per CTA: 1 (CTA form) or its warps (warp form)
-cudaError_t launch_gdp_batch(int shape, const int32_t* irp, const int2* iec, const int4* tiles, int32_t ntiles,
-                             int32_t G, int32_t nseg, uint8_t* active, unsigned long long* seg_ch,
-                             long long* seg_sweeps, int32_t* lam0, int32_t* lam1, int32_t F,
-                             int32_t shift, int64_t max_sweeps, GdpCtl* ctl, long long budget,
-                             cudaStream_t st);
+cudaError_t launch_gdp_batch(int shape, const int32_t* irp, const int2* iec, const int4* tiles,
+                             const int32_t* tiles_e1, const BatchChunk* chunk, int32_t max_tiles, int32_t G,
+                             int32_t nseg, uint8_t* active, unsigned long long* seg_ch, long long* seg_sweeps,
+                             int32_t* lam0, int32_t* lam1, int32_t F, int32_t shift, GdpCtl* ctl,
+                             long long budget, cudaStream_t st);
 cudaError_t launch_batch_extract_bound(const int32_t* rp, const int2* ec, const int32_t* lam,
                                        int32_t n, int32_t fb, const int32_t* seg_off, int32_t nseg,
                                        uint8_t* x2, long long* seg_b2, unsigned long long* seg_bad,
