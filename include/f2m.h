@@ -90,6 +90,13 @@ typedef struct {
  * lambda and halo held in shared memory).  Both give identical results. */
 #define F2M_FLAG_STREAMING_GDP 1u
 
+/* f2m_params.flags: run the shared-memory tiled GDP kernel with one sweep per
+ * device-wide barrier instead of the default two (the default keeps each
+ * CTA's halo rows and a second halo ring, computes the halo rows' sweep
+ * redundantly, and meets the other CTAs once per two sweeps).  Identical
+ * results either way. */
+#define F2M_FLAG_ONE_SWEEP_GDP 2u
+
 typedef struct {
   int64_t iterations;           /* GDP sweeps, all phases */
   int64_t phases;               /* GDP phases */

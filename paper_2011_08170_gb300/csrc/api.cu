@@ -152,6 +152,7 @@ extern "C" void f2m_destroy(f2m_ctx* c) {
   dfree(c->d_check); dfree(c->d_scalar); dfree(c->d_bad);
   free_finisher_buffers(c);
   if (c->fin_work) finisher_work_free(c->fin_work);
+  plan2_free(c->plan);
   plan_free(c->plan);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -263,6 +264,8 @@ f2m_status f2m::create_internal(const int32_t* xy, int32_t n, const int32_t* row
     if (e == cudaSuccess)
       e = plan_build(c->d_rp, c->d_ec, n, c->nnz, c->num_sms, !(p.flags & F2M_FLAG_STREAMING_GDP),
                      p.frac_bits, p.gdp_ctas_per_sm, c->plan, c->st);
+    if (e == cudaSuccess && seg_off.size() == 2 && !(p.flags & F2M_FLAG_ONE_SWEEP_GDP))
+      e = plan_build2(c->plan, p.frac_bits, c->st);
     if (e == cudaSuccess && p.finisher) {
       e = alloc_finisher_buffers(c, c->ec_cap);
       c->fin_work = finisher_work_new();
@@ -341,12 +344,24 @@ f2m_status f2m::gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, bool 
   }
   CK(c, cudaMemsetAsync(c->d_gdp, 0, sizeof(GdpCtl), c->st));
   CK(c, cudaEventRecord(c->ev0, c->st));
+  long long* tb = want_trace ? c->d_trace_b2 : nullptr;
+  unsigned long long* tc = want_trace ? reinterpret_cast<unsigned long long*>(c->d_trace_ch) : nullptr;
+  const int64_t tcap = want_trace ? trace_cap : 0;
+  bool two = c->plan.valid2;  // two sweeps per barrier
   bool tiled = c->plan.valid;
-  if (tiled) {
+  if (two) {
+    cudaError_t e = launch_gdp_tiled2(c->plan, c->d_lam[c->cur], c->p.damping_shift, max_sweeps, c->d_gdp, tb,
+                                      tc, tcap, c->p.barrier_budget_cycles, c->st);
+    if (e == cudaErrorCooperativeLaunchTooLarge) {
+      cudaGetLastError();
+      two = false;
+    } else {
+      CK(c, e);
+    }
+  }
+  if (!two && tiled) {
     cudaError_t e = launch_gdp_tiled(c->plan, c->d_lam[c->cur], c->p.damping_shift, max_sweeps,
-                                     c->d_gdp, want_trace ? c->d_trace_b2 : nullptr,
-                                     want_trace ? c->d_trace_ch : nullptr, want_trace ? trace_cap : 0,
-                                     c->p.barrier_budget_cycles, c->st);
+                                     c->d_gdp, tb, tc, tcap, c->p.barrier_budget_cycles, c->st);
     if (e == cudaErrorCooperativeLaunchTooLarge) {
       cudaGetLastError();
       tiled = false;  // the tiles do not fit on this device now: streaming kernel
@@ -354,24 +369,45 @@ f2m_status f2m::gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, bool 
       CK(c, e);
     }
   }
-  if (!tiled)
+  if (!two && !tiled)
     CK(c, launch_gdp(c->d_rp, c->d_ec, c->d_lam[c->cur], c->d_lam[c->cur ^ 1], c->n, F,
-                     c->p.damping_shift, max_sweeps, c->d_gdp, want_trace ? c->d_trace_b2 : nullptr,
-                     want_trace ? c->d_trace_ch : nullptr, want_trace ? trace_cap : 0,
+                     c->p.damping_shift, max_sweeps, c->d_gdp, tb, tc, tcap,
                      c->p.barrier_budget_cycles, c->num_sms, c->st));
   CK(c, cudaEventRecord(c->ev1, c->st));
   GdpCtl h{};
   CK(c, cudaMemcpyAsync(&h, c->d_gdp, sizeof(h), cudaMemcpyDeviceToHost, c->st));
   CK(c, cudaStreamSynchronize(c->st));
   if (ms) *ms += elapsed_ms(c);
+  if (two && !(h.status & kGdpTimeout)) {
+    CK(c, plan_scatter_lambda(c->plan, (int)h.pad1, c->d_lam[c->cur], c->st));
+    if (h.status & kGdpOddOverflow) {
+      // the second sweep of a round overflowed: replay that round from its
+      // input with the one-sweep kernel, which leaves lambda at the input of
+      // the overflowing sweep
+      const long long base = h.sweeps - 2;
+      CK(c, cudaMemsetAsync(c->d_gdp, 0, sizeof(GdpCtl), c->st));
+      CK(c, launch_gdp_tiled(c->plan, c->d_lam[c->cur], c->p.damping_shift, 2, c->d_gdp,
+                             tb ? tb + base : nullptr, tc ? tc + base : nullptr,
+                             tcap > base ? tcap - base : 0, c->p.barrier_budget_cycles, c->st));
+      GdpCtl h2{};
+      CK(c, cudaMemcpyAsync(&h2, c->d_gdp, sizeof(h2), cudaMemcpyDeviceToHost, c->st));
+      CK(c, cudaStreamSynchronize(c->st));
+      const bool ovf2 = (h2.status & kGdpOverflow) != 0;
+      if (!(h2.status & kGdpTimeout))
+        CK(c, plan_scatter_lambda(c->plan, (int)((ovf2 ? h2.sweeps - 1 : h2.sweeps) % 3), c->d_lam[c->cur], c->st));
+      h.status = (h.status & ~kGdpOddOverflow) | h2.status;
+      h.sweeps = base + h2.sweeps;
+      h.fixed_point = h2.fixed_point;
+    }
+  }
   *sweeps = h.sweeps;
   const bool ovf = (h.status & kGdpOverflow) != 0;
   // the sweep that overflowed leaves lambda at its input; otherwise the last output
   const long long used = ovf ? h.sweeps - 1 : h.sweeps;
-  if (tiled) {
+  if (!two && tiled) {
     if (!(h.status & kGdpTimeout))
       CK(c, plan_scatter_lambda(c->plan, (int)(used % 3), c->d_lam[c->cur], c->st));
-  } else if (used & 1) {
+  } else if (!two && (used & 1)) {
     c->cur ^= 1;
   }
   if (h.status & kGdpTimeout) return fail(c, F2M_ERR_TIMEOUT, "device-wide barrier wait exceeded its budget");
@@ -520,6 +556,10 @@ f2m_status f2m::merge_internal(f2m_ctx* c, const int2* d_pairs, int64_t npairs, 
   if (h.flags) return fail(c, F2M_ERR_INVALID_ARG, check_message(h.flags, h.first_bad));
   CK(c, plan_build(c->d_rp, c->d_ec, n, c->nnz, c->num_sms, !(c->p.flags & F2M_FLAG_STREAMING_GDP),
                    c->p.frac_bits, c->p.gdp_ctas_per_sm, c->plan, c->st));
+  if (c->seg_off.size() == 2 && !(c->p.flags & F2M_FLAG_ONE_SWEEP_GDP))
+    CK(c, plan_build2(c->plan, c->p.frac_bits, c->st));
+  else
+    c->plan.valid2 = false;
   CK(c, cudaEventRecord(c->ev1, c->st));
   if (ms) *ms += elapsed_ms(c);
   return F2M_OK;

@@ -37,6 +37,7 @@ struct GdpCtl {
 
 constexpr int kGdpOverflow = 1;
 constexpr int kGdpTimeout = 2;
+constexpr int kGdpOddOverflow = 4;  // two-sweep kernel: the second sweep of a round overflowed
 
 // Validation result written by the create-time check kernel.
 struct CheckCtl {
@@ -146,6 +147,24 @@ struct GdpPlan {
   int64_t irp_cap = 0, iec_cap = 0, lec_cap = 0, tmp_cap = 0, halo_cap = 0, scan_cap = 0;
   int64_t order_cap = 0, slc_cap = 0;
   int64_t ilam_cap[3] = {0, 0, 0};
+  // two-sweep form (gdp_tiled2.cu): H1 rows and the H2 ring per CTA
+  bool valid2 = false;
+  int32_t maxS2 = 0, maxSl2 = 0, maxL2 = 0, maxHH2 = 0;  // max sliced entries, slices, lambda slots, halo
+  size_t smem2 = 0;
+  int32_t* h2count = nullptr;    // [B+1] H2 per CTA
+  int32_t* hhcount = nullptr;    // [B+1] H1 + H2 per CTA
+  int32_t* s2count = nullptr;    // [B+1] sliced entries (own + H1 rows)
+  int32_t* nslc = nullptr;       // [B+1] slices (own + H1)
+  int32_t* hoff2 = nullptr;      // [B+1] offsets of the H1|H2 lists
+  int32_t* soff2 = nullptr;      // [B+1] offsets of the sliced entries
+  int32_t* sloff2 = nullptr;     // [B+1] slice offsets
+  int32_t* halo2 = nullptr;      // H1 then H2 node ids per CTA
+  int32_t* order2 = nullptr;     // local node of each slot
+  int2* slc2 = nullptr;          // {offset, depth} per slice
+  int2* lec2 = nullptr;          // sliced {local index, cost * 2^F}
+  int32_t* tmp2 = nullptr;       // H2 lists during the build
+  int32_t* stats2 = nullptr;
+  int64_t cap2_small = 0, halo2_cap = 0, order2_cap = 0, slc2_cap = 0, lec2_cap = 0, tmp2_cap = 0;
 };
 cudaError_t sort_pairs_u64(void* temp, size_t& temp_bytes, const uint64_t* keys_in,
                            uint64_t* keys_out, const int32_t* vals_in, int32_t* vals_out,
@@ -166,6 +185,13 @@ void plan_free(GdpPlan& p);
 cudaError_t launch_gdp_tiled(GdpPlan& p, const int32_t* lam_in, int32_t shift, int64_t max_sweeps,
                              GdpCtl* ctl, long long* trace_b2, unsigned long long* trace_ch,
                              int64_t trace_cap, long long budget, cudaStream_t st);
+// two-sweep form on top of a valid one-sweep plan of 1024-thread CTAs (valid2 false if it does not fit)
+cudaError_t plan_build2(GdpPlan& p, int32_t F, cudaStream_t st);
+void plan2_free(GdpPlan& p);
+// gathers lam_in into ilam[0], one cooperative launch; the result is in ilam[ctl->pad1]
+cudaError_t launch_gdp_tiled2(GdpPlan& p, const int32_t* lam_in, int32_t shift, int64_t max_sweeps, GdpCtl* ctl,
+                              long long* trace_b2, unsigned long long* trace_ch, int64_t trace_cap,
+                              long long budget, cudaStream_t st);
 // lam_out (caller order) = ilam[which]
 cudaError_t plan_scatter_lambda(const GdpPlan& p, int which, int32_t* lam_out, cudaStream_t st);
 

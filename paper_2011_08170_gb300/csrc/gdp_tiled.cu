@@ -294,6 +294,8 @@ __global__ void plan_map_kernel(const int32_t* __restrict__ irp, const int2* __r
 
 // ---- the tiled persistent kernel ------------------------------------------------------
 
+// BOUND: also sum the dual bound of every sweep (only traces need it)
+template <bool BOUND>
 __global__ void __launch_bounds__(1024, 1)
 gdp_tiled_kernel(const int32_t* __restrict__ part, const int32_t* __restrict__ hoff,
                  const int32_t* __restrict__ soff, const int32_t* __restrict__ halo,
@@ -376,14 +378,14 @@ gdp_tiled_kernel(const int32_t* __restrict__ part, const int32_t* __restrict__ h
         const int2 q = ent[k * 32], q1 = ent[(k + 1) * 32];
         const int z = q.y - lv - s_in[q.x];  // Eq. 9
         const int z1 = q1.y - lv - s_in[q1.x];
-        neg += min(z, 0) + min(z1, 0);
+        if (BOUND) neg += min(z, 0) + min(z1, 0);
         top3_insert_minmax(z, a, bb, c);
         top3_insert_minmax(z1, a1, b1, c1);
       }
       if (k < sl.y) {
         const int2 q = ent[k * 32];
         const int z = q.y - lv - s_in[q.x];
-        neg += min(z, 0);
+        if (BOUND) neg += min(z, 0);
         top3_insert_minmax(z, a, bb, c);
       }
       top3_merge(a1, b1, c1, a, bb, c);
@@ -392,7 +394,7 @@ gdp_tiled_kernel(const int32_t* __restrict__ part, const int32_t* __restrict__ h
       ovf |= (nl >= kLamLimit || nl <= -kLamLimit);
       s_out[vl] = (int32_t)nl;
       ch += (d != 0);
-      b2 += neg + 4LL * lv;
+      if (BOUND) b2 += neg + 4LL * lv;
     }
     // stop test for sweep t-2
     if (tid == 0) {
@@ -673,9 +675,10 @@ cudaError_t launch_gdp_tiled(GdpPlan& p, const int32_t* lam_in, int32_t shift, i
                              GdpCtl* ctl, long long* trace_b2, unsigned long long* trace_ch,
                              int64_t trace_cap, long long budget, cudaStream_t st) {
   PCK(gather_perm(lam_in, p.perm, p.n, p.ilam[0], st));
-  PCK(cudaFuncSetAttribute(gdp_tiled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
+  const void* kern = trace_cap > 0 ? (const void*)gdp_tiled_kernel<true> : (const void*)gdp_tiled_kernel<false>;
+  PCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
   int per_sm = 0;
-  PCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gdp_tiled_kernel, p.threads, p.smem));
+  PCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, p.threads, p.smem));
   int dev = 0, sms = 0;
   PCK(cudaGetDevice(&dev));
   PCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -688,8 +691,7 @@ cudaError_t launch_gdp_tiled(GdpPlan& p, const int32_t* lam_in, int32_t shift, i
                   (void*)&p.slc, (void*)&p.lec, (void*)&l0, (void*)&l1, (void*)&l2, (void*)&shift,
                   (void*)&ms, (void*)&ctl, (void*)&trace_b2, (void*)&trace_ch, (void*)&tc,
                   (void*)&budget, (void*)&p.maxS, (void*)&p.maxO, (void*)&p.maxH};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)gdp_tiled_kernel, dim3(p.B),
-                                              dim3(p.threads), args, p.smem, st);
+  cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(p.B), dim3(p.threads), args, p.smem, st);
   count_launch();
   return e;
 }

@@ -65,8 +65,9 @@ def test_cost_extremes(lib, O):
 
 # ---- a2-a5: GDP sweeps ------------------------------------------------------------------
 
-# flags 0: shared-memory tiled kernel on renumbered nodes; 1: streaming kernel
-@pytest.mark.parametrize("flags", [0, 1])
+# flags 0: shared-memory tiled kernel, two sweeps per barrier; 2: the same, one
+# sweep per barrier; 1: streaming kernel
+@pytest.mark.parametrize("flags", [0, 1, 2])
 @pytest.mark.parametrize("kind,n,seed,k", CASES)
 def test_gdp_phase_trace(lib, O, kind, n, seed, k, flags):
     d = inst(kind, n, seed, k)
@@ -82,7 +83,7 @@ def test_gdp_phase_trace(lib, O, kind, n, seed, k, flags):
     assert np.array_equal(tb, tb_o) and np.array_equal(tc, tc_o)
 
 
-@pytest.mark.parametrize("flags", [0, 1])
+@pytest.mark.parametrize("flags", [0, 1, 2])
 @pytest.mark.parametrize("shift", [1, 2, 3])
 def test_single_sweeps_from_random_lambda(lib, O, shift, flags):
     d = inst("mixture", 3000, 7, 10)
@@ -235,7 +236,7 @@ def _compare_solve(O, d, **kw):
     return s, r
 
 
-@pytest.mark.parametrize("flags", [0, 1])
+@pytest.mark.parametrize("flags", [0, 1, 2])
 @pytest.mark.parametrize("kind,n,seed,k", [("uniform", 1000, 0, 10), ("mixture", 1000, 0, 10),
                                            ("mixture", 3000, 2, 10), ("uniform", 2000, 1, 6)])
 def test_solve_bit_exact(lib, O, kind, n, seed, k, flags):
@@ -308,6 +309,34 @@ def test_overflow_status(lib, O):
     assert np.array_equal(f2m.f2m_get_lambda(ctx)[0], lam_o)
     with pytest.raises(f2m.F2MError):
         f2m.f2m_set_lambda(ctx, np.full(n, 1 << 29, np.int32), 8)
+
+
+def test_overflow_in_either_sweep_of_a_round(lib, O):
+    # K_{3,7} has no fractional 2-matching: GDP raises lambda without bound and
+    # overflows after 6,607,469 sweeps (oracle).  Starting 10 or 11 sweeps
+    # before that (the oracle's state there) puts the overflow in the second or
+    # the first sweep of a two-sweep round; both kernels must stop exactly where
+    # the oracle does, with the oracle's lambda and traces.
+    m = 7
+    xy = np.array([[0, 0], [0, 10], [0, 20]] + [[100, 7 * i] for i in range(m)], dtype=np.int32)
+    rows = [list(range(3, 3 + m))] * 3 + [[0, 1, 2]] * m
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    col = np.concatenate(rows).astype(np.int32)
+    cost = O.cost_table(xy, rp, col)
+    st_full, _, it_full, _, _ = O.gdp(rp, col, cost, np.zeros(len(xy), np.int32), 8, 2, 10 ** 7, trace=False)
+    assert st_full == O.OR_OVERFLOW and it_full == 6607470
+    for back in (10, 11):
+        st0, lam0, it0, _, _ = O.gdp(rp, col, cost, np.zeros(len(xy), np.int32), 8, 2, it_full - back, trace=False)
+        assert st0 == O.OR_NOT_CONVERGED
+        st_o, lam_o, it_o, tb_o, tc_o = O.gdp(rp, col, cost, lam0, 8, 2, 50, trace=True)
+        assert st_o == O.OR_OVERFLOW and it_o == back
+        for flags in (0, 2):
+            ctx = f2m.f2m_create(xy, rp, col, f2m.f2m_default_params(flags=flags, pricing=0))
+            f2m.f2m_set_lambda(ctx, lam0, 8)
+            st, sweeps, tb, tc = f2m.f2m_gdp(ctx, 50, trace_cap=50)
+            assert st == f2m.F2M_ERR_OVERFLOW and sweeps == it_o, (back, flags, st, sweeps)
+            assert np.array_equal(f2m.f2m_get_lambda(ctx)[0], lam_o), (back, flags)
+            assert np.array_equal(tb, tb_o) and np.array_equal(tc, tc_o)
 
 
 def test_barrier_wait_budget_runs_out_and_context_recovers(lib):
