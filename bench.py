@@ -218,6 +218,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--instances", type=int, default=None,
                     help="batch workloads: solve only the first N instances (profiling)")
+    ap.add_argument("--pricing", type=int, default=1, choices=[1, 2],
+                    help="1: full scan of all pairs (the headline); 2: the scan with far tile pairs skipped")
     ap.add_argument("--batch-shape", type=int, default=-1,
                     help="batch workloads: fixed kernel shape instead of the autotuner's")
     args = ap.parse_args()
@@ -248,11 +250,13 @@ def main():
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     # warm-up solves (also load the module, JIT nothing)
+    params = f2m.f2m_default_params(pricing=args.pricing)
     for _ in range(args.warmup):
-        ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], stream=stream)
+        ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], params=params, stream=stream)
         f2m.f2m_solve(ctx)
         f2m.f2m_destroy(ctx)
-    ctxs = [f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], stream=stream) for _ in range(args.steps)]
+    ctxs = [f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], params=params, stream=stream)
+            for _ in range(args.steps)]
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -298,7 +302,7 @@ def main():
         flush.fill_(i & 0xFF)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx = f2m.f2m_create(xy_h, rp_h, col_h, stream=stream)
+        ctx = f2m.f2m_create(xy_h, rp_h, col_h, params=params, stream=stream)
         info = f2m.f2m_solve(ctx)
         rp_o, col_o, x2_o, cost_o = f2m.f2m_get_x(ctx)
         lam_o, _ = f2m.f2m_get_lambda(ctx)
@@ -343,7 +347,9 @@ def main():
     line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": workload_name(w), "n": n, "k": w["k"], "nnz": nnz0,
+            "config": {"workload": workload_name(w) + ("" if args.pricing == 1 else
+                                                       "; pricing skips tile pairs too far apart to hold z < 0"),
+                       "pricing": "full" if args.pricing == 1 else "culled", "n": n, "k": w["k"], "nnz": nnz0,
                        "l2": "flushed before every timed step (256 MB device write)",
                        "parallelism": f"replicas x{world}"},
             "breakdown_ms": {k: statistics.median(i[k] for i in infos)
@@ -387,7 +393,7 @@ def run_batch(args, w, rank, world, local):
     if args.instances:
         specs = specs[:args.instances]
     ds = [I.make_instance(*sp) for sp in specs]
-    params = f2m.f2m_default_params(batch_shape=args.batch_shape)
+    params = f2m.f2m_default_params(batch_shape=args.batch_shape, pricing=args.pricing)
     insts = [(d["xy"], d["row_ptr"], d["col"]) for d in ds]
     ns = np.array([d["xy"].shape[0] for d in ds])
     nnzs = np.array([int(d["row_ptr"][-1]) for d in ds])

@@ -71,7 +71,10 @@ typedef struct {
   int32_t damping_shift;        /* delta = trunc((z2+z3) / 2^shift); 1..8; default 2 */
   int64_t max_iters;            /* sweeps per GDP phase; default 1,000,000 */
   int32_t max_pricing_rounds;   /* pricing scans per solve; default 64 */
-  int32_t pricing;              /* 0 = solve on the candidate graph only, 1 = full scan (default) */
+  int32_t pricing;              /* 0 = solve on the candidate graph only, 1 = full scan of all
+                                   n(n-1)/2 pairs (default), 2 = the same scan skipping tile pairs
+                                   whose bounding boxes are too far apart to hold a pair with z < 0
+                                   (same pairs found, same results) */
   int64_t pricing_cap;          /* initial pair-buffer capacity; default 1 << 20 */
   int64_t barrier_budget_cycles;/* spin budget of one device-wide barrier wait; default 4e9 */
   int32_t finisher;             /* 1 = exact finisher when rule (7) gives an infeasible x (default) */

@@ -147,6 +147,7 @@ extern "C" void f2m_destroy(f2m_ctx* c) {
   dfree(c->d_seg_off); dfree(c->d_fin_include);
   dfree(c->d_lam[0]); dfree(c->d_lam[1]); dfree(c->d_lam2); dfree(c->d_gdp);
   dfree(c->d_trace_b2); dfree(c->d_trace_ch); dfree(c->d_pts); dfree(c->d_pairs);
+  dfree(c->d_ranges); dfree(c->d_boxes); dfree(c->d_smax);
   dfree(c->d_count); dfree(c->d_tile); dfree(c->d_deg); dfree(c->d_tmp_rp); dfree(c->d_new_rp);
   dfree(c->d_block_sums); dfree(c->d_tmp_col); dfree(c->d_out_a); dfree(c->d_out_b);
   dfree(c->d_check); dfree(c->d_scalar); dfree(c->d_bad);
@@ -172,6 +173,7 @@ f2m_status f2m::check_params_internal(const f2m_params& p) {
     return fail(nullptr, F2M_ERR_INVALID_ARG, "batch_graph must be 0 or 1");
   if (p.max_iters < 0 || p.max_pricing_rounds < 0 || p.pricing_cap < 1 || p.barrier_budget_cycles < 0)
     return fail(nullptr, F2M_ERR_INVALID_ARG, "negative cap or budget");
+  if (p.pricing < 0 || p.pricing > 2) return fail(nullptr, F2M_ERR_INVALID_ARG, "pricing must be 0, 1 or 2");
   return F2M_OK;
 }
 
@@ -463,6 +465,62 @@ f2m_status f2m::price_internal(f2m_ctx* c, double* ms) {
   }
   std::vector<int4> tiles;
   build_tiles(c, tiles);
+  int32_t fb = 0;
+  const int32_t* lam = cur_lambda(c, &fb);
+  const int32_t nseg = (int32_t)c->seg_off.size() - 1;
+  // full scan: points in caller order; culled scan: in the renumbered (Morton)
+  // order, so that a tile is a compact patch with a small bounding box
+  const bool culled = c->p.pricing == 2;
+  CK(c, cudaEventRecord(c->ev0, c->st));
+  CK(c, launch_pricing_prep(c->d_xy, lam, culled ? c->plan.perm : nullptr, c->n, fb, c->d_pts, c->st));
+  if (culled && !tiles.empty()) {
+    // A pair (u, v) can have z < 0 only if its distance is below s_u + s_v
+    // (the filter's radii, see pricing.cu), so a tile pair whose bounding
+    // boxes are at least max s + max s apart holds none: it is skipped.
+    // the point ranges of the tiles: per segment, steps of kPricingTile from its start
+    std::vector<int2> ranges;
+    std::vector<int32_t> base(nseg + 1, 0);
+    for (int32_t sg = 0; sg < nseg; ++sg) {
+      base[sg] = (int32_t)ranges.size();
+      for (int32_t i0 = c->seg_off[sg]; i0 < c->seg_off[sg + 1]; i0 += kPricingTile)
+        ranges.push_back(make_int2(i0, std::min(i0 + kPricingTile, c->seg_off[sg + 1])));
+    }
+    auto range_id = [&](int32_t i0) {
+      const int32_t sg = (int32_t)(std::upper_bound(c->seg_off.begin(), c->seg_off.end(), i0) - c->seg_off.begin()) - 1;
+      return base[sg] + (i0 - c->seg_off[sg]) / kPricingTile;
+    };
+    std::vector<int32_t> rid_of(tiles.size()), cid_of(tiles.size());
+    for (size_t k = 0; k < tiles.size(); ++k) {
+      rid_of[k] = range_id(tiles[k].x);
+      cid_of[k] = range_id(tiles[k].z);
+    }
+    if ((int64_t)ranges.size() > c->ranges_cap) {
+      dfree(c->d_ranges);
+      dfree(c->d_boxes);
+      dfree(c->d_smax);
+      c->ranges_cap = (int64_t)ranges.size() + 64;
+      CK(c, dalloc(&c->d_ranges, c->ranges_cap));
+      CK(c, dalloc(&c->d_boxes, c->ranges_cap));
+      CK(c, dalloc(&c->d_smax, c->ranges_cap));
+    }
+    CK(c, cudaMemcpyAsync(c->d_ranges, ranges.data(), sizeof(int2) * ranges.size(), cudaMemcpyHostToDevice, c->st));
+    CK(c, launch_pricing_boxes(c->d_pts, c->d_ranges, (int32_t)ranges.size(), c->d_boxes, c->d_smax, c->st));
+    std::vector<float4> box(ranges.size());
+    std::vector<float> smax(ranges.size());
+    CK(c, cudaMemcpyAsync(box.data(), c->d_boxes, sizeof(float4) * box.size(), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaMemcpyAsync(smax.data(), c->d_smax, sizeof(float) * smax.size(), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    std::vector<int4> kept;
+    kept.reserve(tiles.size());
+    for (size_t k = 0; k < tiles.size(); ++k) {
+      const float4 a = box[rid_of[k]], b = box[cid_of[k]];
+      const double gx = std::max(0.0, std::max((double)a.x - b.z, (double)b.x - a.z));
+      const double gy = std::max(0.0, std::max((double)a.y - b.w, (double)b.y - a.w));
+      const double r = (double)smax[rid_of[k]] + (double)smax[cid_of[k]];
+      if (gx * gx + gy * gy < r * r * (1.0 + 1e-9) + 1.0) kept.push_back(tiles[k]);
+    }
+    tiles.swap(kept);
+  }
   if ((int64_t)tiles.size() > c->tiles_cap) {
     dfree(c->d_tiles);
     c->tiles_cap = (int64_t)tiles.size() + 64;
@@ -470,14 +528,13 @@ f2m_status f2m::price_internal(f2m_ctx* c, double* ms) {
   }
   if (!tiles.empty())
     CK(c, cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, c->st));
-  int32_t fb = 0;
-  const int32_t* lam = cur_lambda(c, &fb);
-  const int32_t nseg = (int32_t)c->seg_off.size() - 1;
+  bool first = true;
   for (;;) {
-    CK(c, cudaEventRecord(c->ev0, c->st));
-    CK(c, launch_pricing(c->d_xy, lam, c->d_rp, c->d_ec, c->n, fb, c->d_pts, c->d_tiles,
-                         (int32_t)tiles.size(), c->d_pairs, c->pairs_cap, c->d_count, c->d_tile,
-                         c->num_sms, c->st));
+    if (!first) CK(c, cudaEventRecord(c->ev0, c->st));
+    first = false;
+    CK(c, launch_pricing_scan(c->d_pts, c->d_xy, lam, c->d_rp, c->d_ec, c->n, fb, c->d_tiles,
+                              (int32_t)tiles.size(), c->d_pairs, c->pairs_cap, c->d_count, c->d_tile,
+                              c->num_sms, c->st));
     CK(c, cudaEventRecord(c->ev1, c->st));
     unsigned long long cnt = 0;
     CK(c, cudaMemcpyAsync(&cnt, c->d_count, sizeof(cnt), cudaMemcpyDeviceToHost, c->st));

@@ -21,6 +21,10 @@ struct f2m_ctx {
   uint8_t* d_fin_include = nullptr;     // per segment: the finisher may change it (NULL = all)
   int4* d_tiles = nullptr;              // pricing tile-pair list
   int64_t tiles_cap = 0;
+  int2* d_ranges = nullptr;             // culled pricing: point ranges of the tiles,
+  float4* d_boxes = nullptr;            // their bounding boxes
+  float* d_smax = nullptr;              // and largest filter radii
+  int64_t ranges_cap = 0;
 
   int32_t n = 0;
   int64_t nnz = 0;

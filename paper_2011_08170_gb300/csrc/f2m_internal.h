@@ -86,10 +86,17 @@ cudaError_t launch_halve(const int32_t* lam_in, int32_t* lam_out, int32_t n, cud
 // all-pairs pricing scan: pairs (u < v) outside the CSR with z < 0
 // Tile pairs {i0, i1, j0, j1}: test i in [i0, i1) against j in [j0, j1), j > i.
 constexpr int kPricingTile = 1024;
-cudaError_t launch_pricing(const int2* xy, const int32_t* lam, const int32_t* rp, const int2* ec,
-                           int32_t n, int32_t fb, float4* pts, const int4* tiles, int32_t ntiles,
-                           int2* pairs, int64_t cap, unsigned long long* count,
-                           unsigned int* tile_counter, int num_sms, cudaStream_t st);
+// pts[v] = {x, y, s, node perm[v]} (perm NULL: node v), s the filter radius of the node
+cudaError_t launch_pricing_prep(const int2* xy, const int32_t* lam, const int32_t* perm, int32_t n, int32_t fb,
+                                float4* pts, cudaStream_t st);
+// bounding box {min x, min y, max x, max y} and largest s of each point range
+cudaError_t launch_pricing_boxes(const float4* pts, const int2* ranges, int32_t nranges, float4* box, float* smax,
+                                 cudaStream_t st);
+// the scan over the tile pairs (positions in pts); count and pairs (nodes, u < v)
+cudaError_t launch_pricing_scan(const float4* pts, const int2* xy, const int32_t* lam, const int32_t* rp,
+                                const int2* ec, int32_t n, int32_t fb, const int4* tiles, int32_t ntiles,
+                                int2* pairs, int64_t cap, unsigned long long* count, unsigned int* tile_counter,
+                                int num_sms, cudaStream_t st);
 // CSR union with pairs; sizes: see graph.cu.  Returns the new nnz through *new_nnz_dev.
 struct MergeBuffers {
   int32_t* deg;        // [n+1]

@@ -28,25 +28,78 @@ constexpr int kPriceP = 4;
 constexpr int kPriceTile = kPriceThreads * kPriceP;
 static_assert(kPriceTile == kPricingTile, "tile size shared with the tile-list builder");
 
+// pts[v] = {x, y, s, node} of node perm[v] (perm NULL: node v); the node id is
+// carried in the last component's bits
 __global__ void pricing_prep_kernel(const int2* __restrict__ xy, const int32_t* __restrict__ lam,
-                                    int32_t n, int32_t fb, float4* __restrict__ pts) {
+                                    const int32_t* __restrict__ perm, int32_t n, int32_t fb,
+                                    float4* __restrict__ pts) {
   const float scale = ldexpf(1.0f, -fb);
   const float grow = 1.0f + ldexpf(1.0f, -19);
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
        v += (long long)gridDim.x * blockDim.x) {
-    const int2 p = xy[v];
-    float r = fmaxf((float)lam[v] * scale + 0.25f, 0.0f);
-    pts[v] = make_float4((float)p.x, (float)p.y, r * grow, 0.0f);
+    const int u = perm ? perm[v] : (int)v;
+    const int2 p = xy[u];
+    float r = fmaxf((float)lam[u] * scale + 0.25f, 0.0f);
+    pts[v] = make_float4((float)p.x, (float)p.y, r * grow, __int_as_float(u));
   }
 }
 
-// exact decision for a pair that passed the filter
-__device__ __noinline__ void pricing_confirm(int i, int j, int32_t n, const int2* __restrict__ xy,
+// bounding box and largest s of each listed point range: {min x, min y, max x, max y}, s
+__global__ void pricing_boxes_kernel(const float4* __restrict__ pts, const int2* __restrict__ ranges,
+                                     float4* __restrict__ box, float* __restrict__ smax) {
+  const int2 rg = ranges[blockIdx.x];
+  float x0 = 3e38f, y0 = 3e38f, x1 = -3e38f, y1 = -3e38f, sm = 0.f;
+  for (int i = rg.x + threadIdx.x; i < rg.y; i += blockDim.x) {
+    const float4 q = pts[i];
+    x0 = fminf(x0, q.x);
+    y0 = fminf(y0, q.y);
+    x1 = fmaxf(x1, q.x);
+    y1 = fmaxf(y1, q.y);
+    sm = fmaxf(sm, q.z);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    x0 = fminf(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+    y0 = fminf(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+    x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+    y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+    sm = fmaxf(sm, __shfl_xor_sync(0xffffffffu, sm, o));
+  }
+  __shared__ float4 sb[32];
+  __shared__ float ss[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    sb[warp] = make_float4(x0, y0, x1, y1);
+    ss[warp] = sm;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float4 b = sb[0];
+    float m = ss[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      b.x = fminf(b.x, sb[w].x);
+      b.y = fminf(b.y, sb[w].y);
+      b.z = fmaxf(b.z, sb[w].z);
+      b.w = fmaxf(b.w, sb[w].w);
+      m = fmaxf(m, ss[w]);
+    }
+    box[blockIdx.x] = b;
+    smax[blockIdx.x] = m;
+  }
+}
+
+// exact decision for a pair that passed the filter: positions ii < jj in the
+// point array (each unordered pair once), nodes i and j
+__device__ __noinline__ void pricing_confirm(int ii, int jj, int i, int j, int32_t n, const int2* __restrict__ xy,
                                              const int32_t* __restrict__ lam,
                                              const int32_t* __restrict__ rp,
                                              const int2* __restrict__ ec, int32_t fb, int2* pairs,
                                              long long cap, unsigned long long* count) {
-  if (j <= i || j >= n) return;  // each unordered pair once; tail of the last tile
+  if (jj <= ii || jj >= n) return;  // each unordered pair once; tail of the last tile
+  if (j < i) {
+    const int t = i;
+    i = j;
+    j = t;
+  }
   const long long S = (long long)lam[i] + lam[j];
   if (S <= 0) return;
   const long long c = exact_cost(xy[i], xy[j]);
@@ -79,19 +132,20 @@ pricing_kernel(const float4* __restrict__ pts, const int2* __restrict__ xy,
     const int4 tl = tiles[tp];  // i in [x, y), j in [z, w)
 
     float xi[kPriceP], yi[kPriceP], si[kPriceP];
+    int ni[kPriceP];
 #pragma unroll
     for (int p = 0; p < kPriceP; ++p) {
       const int i = tl.x + p * kPriceThreads + threadIdx.x;
       if (i < tl.y) {
         const float4 q = pts[i];
-        xi[p] = q.x; yi[p] = q.y; si[p] = q.z;
+        xi[p] = q.x; yi[p] = q.y; si[p] = q.z; ni[p] = __float_as_int(q.w);
       } else {
-        xi[p] = 1e18f; yi[p] = 1e18f; si[p] = 0.0f;
+        xi[p] = 1e18f; yi[p] = 1e18f; si[p] = 0.0f; ni[p] = 0;
       }
     }
     for (int k = threadIdx.x; k < kPriceTile; k += kPriceThreads) {
       const int j = tl.z + k;
-      sj[k] = j < tl.w ? pts[j] : make_float4(-1e18f, -1e18f, 0.0f, 0.0f);
+      sj[k] = j < tl.w ? pts[j] : make_float4(-1e18f, -1e18f, 0.0f, __int_as_float(0));
     }
     __syncthreads();
 #pragma unroll 4
@@ -111,28 +165,39 @@ pricing_kernel(const float4* __restrict__ pts, const int2* __restrict__ xy,
 #pragma unroll
         for (int p = 0; p < kPriceP; ++p)
           if (e[p] < 1.0f)
-            pricing_confirm(tl.x + p * kPriceThreads + threadIdx.x, j, min(n, tl.w), xy, lam, rp, ec,
-                            fb, pairs, cap, count);
+            pricing_confirm(tl.x + p * kPriceThreads + threadIdx.x, j, ni[p], __float_as_int(q.w),
+                            min(n, tl.w), xy, lam, rp, ec, fb, pairs, cap, count);
       }
     }
   }
 }
 
-cudaError_t launch_pricing(const int2* xy, const int32_t* lam, const int32_t* rp, const int2* ec,
-                           int32_t n, int32_t fb, float4* pts, const int4* tiles, int32_t ntiles,
-                           int2* pairs, int64_t cap, unsigned long long* count,
-                           unsigned int* tile_counter, int num_sms, cudaStream_t st) {
+cudaError_t launch_pricing_prep(const int2* xy, const int32_t* lam, const int32_t* perm, int32_t n, int32_t fb,
+                                float4* pts, cudaStream_t st) {
+  const int threads = 256;
+  int blocks = (int)((n + threads - 1) / threads);
+  if (blocks > 4096) blocks = 4096;
+  pricing_prep_kernel<<<blocks, threads, 0, st>>>(xy, lam, perm, n, fb, pts);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pricing_boxes(const float4* pts, const int2* ranges, int32_t nranges, float4* box, float* smax,
+                                 cudaStream_t st) {
+  if (nranges <= 0) return cudaSuccess;
+  pricing_boxes_kernel<<<nranges, 256, 0, st>>>(pts, ranges, box, smax);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pricing_scan(const float4* pts, const int2* xy, const int32_t* lam, const int32_t* rp,
+                                const int2* ec, int32_t n, int32_t fb, const int4* tiles, int32_t ntiles,
+                                int2* pairs, int64_t cap, unsigned long long* count, unsigned int* tile_counter,
+                                int num_sms, cudaStream_t st) {
   cudaError_t err = cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
   if (err == cudaSuccess) err = cudaMemsetAsync(tile_counter, 0, sizeof(unsigned int), st);
   if (err != cudaSuccess) return err;
-  {
-    const int threads = 256;
-    int blocks = (int)((n + threads - 1) / threads);
-    if (blocks > 4096) blocks = 4096;
-    pricing_prep_kernel<<<blocks, threads, 0, st>>>(xy, lam, n, fb, pts);
-    count_launch();
-  }
-  if (ntiles == 0) return cudaGetLastError();
+  if (ntiles == 0) return cudaSuccess;
   int per_sm = 0;
   err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pricing_kernel, kPriceThreads, 0);
   if (err != cudaSuccess) return err;

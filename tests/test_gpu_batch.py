@@ -65,6 +65,12 @@ def test_batch_with_pricing_rounds_and_waiting_instances(lib, oracle_lib):
     assert max(i.phases for i in infos) > 1 and min(i.phases for i in infos) == 1
 
 
+def test_batch_with_culled_pricing(lib, oracle_lib):
+    ds = make_batch([("uniform", 600, 11, 4), ("mixture", 900, 12, 10), ("uniform", 1200, 13, 5),
+                     ("mixture", 400, 14, 4)])
+    compare(oracle_lib, ds, f2m.f2m_default_params(pricing=2))
+
+
 def test_batch_matches_oracle_optimum(lib, oracle_lib):
     ds = make_batch([("uniform", 800, 21, 8), ("mixture", 1100, 22, 10), ("uniform", 500, 23, 6)])
     b = f2m.f2m_create_batch([(d["xy"], d["row_ptr"], d["col"]) for d in ds])

@@ -139,23 +139,27 @@ def _sorted_pairs(p):
     return p[np.lexsort((p[:, 1], p[:, 0]))]
 
 
+# pricing 1: full scan; 2: the scan with far tile pairs skipped (same pairs)
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("kind,n,seed,k,fb", [("mixture", 2500, 1, 6, 8), ("uniform", 3333, 2, 4, 9),
-                                              ("uniform", 1024, 3, 5, 8), ("mixture", 1025, 4, 5, 8)])
-def test_pricing_random_lambda(lib, O, kind, n, seed, k, fb):
+                                              ("uniform", 1024, 3, 5, 8), ("mixture", 1025, 4, 5, 8),
+                                              ("mixture", 20000, 5, 6, 8)])
+def test_pricing_random_lambda(lib, O, kind, n, seed, k, fb, mode):
     d = inst(kind, n, seed, k)
     rng = np.random.default_rng(seed)
     scale = 30000 if kind == "uniform" else 8000
     lam = rng.integers(-scale, scale * 3, size=n).astype(np.int32) << fb
     lam = (lam + rng.integers(0, 1 << fb, size=n)).astype(np.int32)
     cnt_o, pairs_o = O.pricing(d["xy"], d["row_ptr"], d["col"], lam, fb)
-    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"])
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], f2m.f2m_default_params(pricing=mode))
     f2m.f2m_set_lambda(ctx, lam, fb)
     cnt, pairs = f2m.f2m_price(ctx)
     assert cnt == cnt_o > 0
     assert np.array_equal(_sorted_pairs(pairs), pairs_o)
 
 
-def test_pricing_boundary_z_minus_one_and_zero(lib, O):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_pricing_boundary_z_minus_one_and_zero(lib, O, mode):
     # lambdas set so that many outside pairs have z exactly 0 or -1: the fp32
     # filter must keep every z = -1 pair and the exact test must drop z = 0
     n = 2048
@@ -172,25 +176,27 @@ def test_pricing_boundary_z_minus_one_and_zero(lib, O):
         lam[i], lam[i + 1] = a, tot - a
     lam = lam.astype(np.int32)
     cnt_o, pairs_o = O.pricing(xy, d["row_ptr"], d["col"], lam, fb)
-    ctx = f2m.f2m_create(xy, d["row_ptr"], d["col"])
+    ctx = f2m.f2m_create(xy, d["row_ptr"], d["col"], f2m.f2m_default_params(pricing=mode))
     f2m.f2m_set_lambda(ctx, lam, fb)
     cnt, pairs = f2m.f2m_price(ctx)
     assert cnt == cnt_o and cnt > 0
     assert np.array_equal(_sorted_pairs(pairs), pairs_o)
 
 
-def test_pricing_nothing_to_find(lib, O):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_pricing_nothing_to_find(lib, O, mode):
     d = inst("uniform", 1500, 2, 10)
-    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"])
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], f2m.f2m_default_params(pricing=mode))
     cnt, _ = f2m.f2m_price(ctx)  # lambda = 0: every z >= 0
     assert cnt == 0
 
 
-def test_pricing_buffer_grows(lib, O):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_pricing_buffer_grows(lib, O, mode):
     d = inst("uniform", 1200, 3, 4)
     n = 1200
     lam = np.full(n, 200000 << 8, dtype=np.int32)  # every pair negative
-    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], f2m.f2m_default_params(pricing_cap=16))
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], f2m.f2m_default_params(pricing_cap=16, pricing=mode))
     f2m.f2m_set_lambda(ctx, lam, 8)
     cnt, pairs = f2m.f2m_price(ctx)
     cnt_o, pairs_o = O.pricing(d["xy"], d["row_ptr"], d["col"], lam, 8)
@@ -223,7 +229,8 @@ def test_merge(lib, O):
 
 def _compare_solve(O, d, **kw):
     r = O.solve(d["xy"], d["row_ptr"], d["col"], max_iters=kw.get("max_iters", 1000000))
-    params = f2m.f2m_default_params(max_iters=kw.get("max_iters", 1000000), flags=kw.get("flags", 0))
+    params = f2m.f2m_default_params(max_iters=kw.get("max_iters", 1000000), flags=kw.get("flags", 0),
+                                    pricing=kw.get("pricing", 1))
     s = f2m.solve(d["xy"], d["row_ptr"], d["col"], params=params)
     i = s.info
     assert i["status"] == r.status == 0
@@ -241,6 +248,12 @@ def _compare_solve(O, d, **kw):
                                            ("mixture", 3000, 2, 10), ("uniform", 2000, 1, 6)])
 def test_solve_bit_exact(lib, O, kind, n, seed, k, flags):
     s, r = _compare_solve(O, inst(kind, n, seed, k), flags=flags)
+    assert s.info["certified"] == 2
+
+
+@pytest.mark.parametrize("kind,n,seed,k", [("uniform", 2000, 1, 6), ("mixture", 5000, 3, 4)])
+def test_solve_bit_exact_with_culled_pricing(lib, O, kind, n, seed, k):
+    s, r = _compare_solve(O, inst(kind, n, seed, k), pricing=2)
     assert s.info["certified"] == 2
 
 
