@@ -74,17 +74,17 @@ def lib():
         L.or_nint_sqrt_array.argtypes = [C.c_int64, _i64p, _i64p]
         L.or_cost_table.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _i32p]
         L.or_sweep.restype = C.c_int
-        L.or_sweep.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _i32p, C.c_int32, C.c_int32,
+        L.or_sweep.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_void_p, _i32p, C.c_int32, C.c_int32,
                                _i32p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.or_bound2.restype = C.c_int64
-        L.or_bound2.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _i32p, C.c_int32]
+        L.or_bound2.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_void_p, _i32p, C.c_int32]
         L.or_gdp.restype = C.c_int
-        L.or_gdp.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_int32, C.c_int32, C.c_int64,
+        L.or_gdp.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_void_p, C.c_int32, C.c_int32, C.c_int64,
                              _i32p, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p, C.c_int64]
         L.or_extract.restype = C.c_int64
-        L.or_extract.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _i32p, C.c_int32, _u8p]
+        L.or_extract.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_void_p, _i32p, C.c_int32, _u8p]
         L.or_finisher.restype = C.c_int
-        L.or_finisher.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _i32p, _i32p, C.c_int32, _u8p,
+        L.or_finisher.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _i32p, C.c_void_p, _i32p, C.c_int32, _u8p,
                                   _i32p, C.POINTER(C.c_int64)]
         L.or_pricing_rows.restype = C.c_int64
         L.or_pricing_rows.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _i32p, C.c_int32,
@@ -92,7 +92,7 @@ def lib():
         L.or_merge.restype = C.c_int64
         L.or_merge.argtypes = [C.c_int32, _i32p, _i32p, C.c_int64, _i32p, _i32p, _i32p]
         L.or_solve.restype = C.c_void_p
-        L.or_solve.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_void_p,
+        L.or_solve.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_void_p, C.c_void_p,
                                C.POINTER(_Params), C.POINTER(_Info), C.c_void_p, C.c_void_p,
                                C.c_int64]
         L.or_result_nnz.restype = C.c_int64
@@ -100,7 +100,7 @@ def lib():
         L.or_result_copy.argtypes = [C.c_void_p, _i32p, _i32p, _u8p, _i32p]
         L.or_result_free.argtypes = [C.c_void_p]
         L.or_certify.restype = C.c_int
-        L.or_certify.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _u8p, _i32p, C.c_int32,
+        L.or_certify.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_void_p, _u8p, _i32p, C.c_int32,
                                  C.c_int64, C.c_int32]
         L.or_knn.argtypes = [C.c_int32, _i32p, C.c_int32, _i32p, _i64p]
         _lib = L
@@ -109,6 +109,24 @@ def lib():
 
 def _i32(a):
     return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _degrees(b, n):
+    """Degree requirements b_v as a contiguous int32 array, or None for b_v = 2
+    (the fractional 2-matching).  A scalar b means b_v = b for every node."""
+    if b is None:
+        return None
+    b = np.asarray(b)
+    if b.ndim == 0:
+        b = np.full(n, int(b), dtype=np.int32)
+    b = _i32(b)
+    if b.size != n:
+        raise ValueError("b must hold one degree requirement per node")
+    return b
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
 
 
 def nint_sqrt(d2) -> np.ndarray:
@@ -125,46 +143,55 @@ def cost_table(xy, row_ptr, col) -> np.ndarray:
     return out
 
 
-def sweep(row_ptr, col, cost, lam, F=8, shift=2):
-    """One Jacobi GDP sweep: returns (status, lam_new, bound2, changed)."""
+def sweep(row_ptr, col, cost, lam, F=8, shift=2, b=None):
+    """One Jacobi GDP sweep: returns (status, lam_new, bound2, changed).
+    b: degree requirements (None: 2 everywhere; see or_sweep)."""
     row_ptr, col, cost, lam = _i32(row_ptr), _i32(col), _i32(cost), _i32(lam)
+    bb = _degrees(b, lam.size)
     out = np.empty_like(lam)
     b2, ch = C.c_int64(), C.c_int64()
-    st = lib().or_sweep(lam.size, row_ptr, col, cost, lam, F, shift, out, C.byref(b2), C.byref(ch))
+    st = lib().or_sweep(lam.size, row_ptr, col, cost, _ptr(bb), lam, F, shift, out, C.byref(b2),
+                        C.byref(ch))
     return st, out, b2.value, ch.value
 
 
-def bound2(row_ptr, col, cost, lam, fb=8) -> int:
-    return int(lib().or_bound2(row_ptr.size - 1, _i32(row_ptr), _i32(col), _i32(cost), _i32(lam), fb))
+def bound2(row_ptr, col, cost, lam, fb=8, b=None) -> int:
+    n = row_ptr.size - 1
+    bb = _degrees(b, n)
+    return int(lib().or_bound2(n, _i32(row_ptr), _i32(col), _i32(cost), _ptr(bb), _i32(lam), fb))
 
 
-def gdp(row_ptr, col, cost, lam0, F=8, shift=2, max_iters=100000, trace=False):
+def gdp(row_ptr, col, cost, lam0, F=8, shift=2, max_iters=100000, trace=False, b=None):
     """GDP phase: returns (status, lam, iters, trace_bound2, trace_changed)."""
     lam = _i32(lam0).copy()
+    bb = _degrees(b, lam.size)
     it = C.c_int64()
     tb = np.zeros(max_iters if trace else 1, dtype=np.int64)
     tc = np.zeros_like(tb)
-    st = lib().or_gdp(lam.size, _i32(row_ptr), _i32(col), _i32(cost), F, shift, max_iters, lam,
+    st = lib().or_gdp(lam.size, _i32(row_ptr), _i32(col), _i32(cost), _ptr(bb), F, shift, max_iters, lam,
                       C.byref(it), tb.ctypes.data if trace else None,
                       tc.ctypes.data if trace else None, max_iters if trace else 0)
     k = it.value
     return st, lam, k, (tb[:k] if trace else None), (tc[:k] if trace else None)
 
 
-def extract(row_ptr, col, cost, lam, fb=8):
+def extract(row_ptr, col, cost, lam, fb=8, b=None):
+    n = row_ptr.size - 1
+    bb = _degrees(b, n)
     x2 = np.zeros(np.asarray(col).size, dtype=np.uint8)
-    bad = lib().or_extract(row_ptr.size - 1, _i32(row_ptr), _i32(col), _i32(cost), _i32(lam), fb, x2)
+    bad = lib().or_extract(n, _i32(row_ptr), _i32(col), _i32(cost), _ptr(bb), _i32(lam), fb, x2)
     return int(bad), x2
 
 
-def finisher(xy, row_ptr, col, cost, lam, F=8):
+def finisher(xy, row_ptr, col, cost, lam, F=8, b=None):
     """Exact min-cost-flow finisher: returns (status, x2, lam2 at F+1 bits, augmentations)."""
     x2 = np.zeros(np.asarray(col).size, dtype=np.uint8)
     lam = _i32(lam)
+    bb = _degrees(b, lam.size)
     lam2 = np.zeros_like(lam)
     aug = C.c_int64()
-    st = lib().or_finisher(lam.size, _i32(xy).reshape(-1), _i32(row_ptr), _i32(col), _i32(cost), lam,
-                           F, x2, lam2, C.byref(aug))
+    st = lib().or_finisher(lam.size, _i32(xy).reshape(-1), _i32(row_ptr), _i32(col), _i32(cost),
+                           _ptr(bb), lam, F, x2, lam2, C.byref(aug))
     return st, x2, lam2, aug.value
 
 
@@ -217,15 +244,16 @@ class OracleResult:
 
 
 def solve(xy, row_ptr, col, lam0=None, F=8, shift=2, max_iters=200000, max_pricing_rounds=64,
-          pricing=True, finisher=True, trace_cap=0) -> OracleResult:
+          pricing=True, finisher=True, trace_cap=0, b=None) -> OracleResult:
     xy, row_ptr, col = _i32(xy), _i32(row_ptr), _i32(col)
     n = row_ptr.size - 1
+    bb = _degrees(b, n)
     p = _Params(F, shift, max_iters, max_pricing_rounds, int(pricing), int(finisher))
     info = _Info()
     lam0a = None if lam0 is None else _i32(lam0)
     tb = np.zeros(max(trace_cap, 1), dtype=np.int64)
     tc = np.zeros_like(tb)
-    h = lib().or_solve(n, xy.reshape(-1), row_ptr, col,
+    h = lib().or_solve(n, xy.reshape(-1), row_ptr, col, _ptr(bb),
                        None if lam0a is None else lam0a.ctypes.data, C.byref(p), C.byref(info),
                        tb.ctypes.data if trace_cap else None,
                        tc.ctypes.data if trace_cap else None, trace_cap)
@@ -245,10 +273,11 @@ def solve(xy, row_ptr, col, lam0=None, F=8, shift=2, max_iters=200000, max_prici
                         tb[:k] if trace_cap else None, tc[:k] if trace_cap else None)
 
 
-def certify(xy, row_ptr, col, x2, lam, fb, bound2, full_scan=True) -> int:
+def certify(xy, row_ptr, col, x2, lam, fb, bound2, full_scan=True, b=None) -> int:
     """0 if (x2, lam) is certified optimal (see certify.c), else the failed check number."""
     xy, row_ptr, col = _i32(xy), _i32(row_ptr), _i32(col)
-    return int(lib().or_certify(row_ptr.size - 1, xy.reshape(-1), row_ptr, col,
+    bb = _degrees(b, row_ptr.size - 1)
+    return int(lib().or_certify(row_ptr.size - 1, xy.reshape(-1), row_ptr, col, _ptr(bb),
                                 np.ascontiguousarray(x2, dtype=np.uint8), _i32(lam), fb,
                                 int(bound2), int(full_scan)))
 

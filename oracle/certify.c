@@ -7,10 +7,11 @@
  * of the points (the F2M LP of Section 4):
  *   1  every x2 is 0, 1 or 2;
  *   2  x2 agrees on both directions of an edge;
- *   3  every node has row sum 4, i.e. sum of x over delta(v) = 2;
+ *   3  every node has row sum 2 b_v, i.e. sum of x over delta(v) = b_v (b_v = 2
+ *      for the fractional 2-matching; other b_v for a fractional b-matching);
  *   4  complementary slackness with z = c*2^fb - lam_u - lam_v (rule (7)):
  *      x = 1 -> z <= 0, x = 1/2 -> z == 0, x = 0 -> z >= 0;
- *   5  bound2 = 4*sum(lam) + sum over directed entries of min(0, z);
+ *   5  bound2 = 2*sum(b_v lam_v) + sum over directed entries of min(0, z);
  *   6  primal cost equals the dual bound: sum_dir x2 * c * 2^fb == 2 * bound2;
  *   7  (full_scan) no pair outside the graph has z < 0, so the duals
  *      mu_e = max(0, -z_e) with lambda are feasible for the complete graph.
@@ -40,12 +41,13 @@ static int64_t cert_len(const int32_t* xy, int32_t u, int32_t v) {
 }
 
 int or_certify(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int32_t* col,
-               const uint8_t* x2, const int32_t* lam, int32_t fb, int64_t bound2,
+               const int32_t* b, const uint8_t* x2, const int32_t* lam, int32_t fb, int64_t bound2,
                int32_t full_scan) {
   int64_t b2 = 0, primal = 0;
   for (int32_t u = 0; u < n; ++u) {
     int32_t s = 0;
-    b2 += 4 * (int64_t)lam[u];
+    const int32_t bu = b ? b[u] : 2;
+    b2 += 2 * (int64_t)bu * lam[u];
     for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
       int32_t v = col[e];
       if (x2[e] > 2) return 1;
@@ -62,7 +64,7 @@ int or_certify(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int32
       if (z < 0) b2 += z;
       primal += (int64_t)x2[e] * c * ((int64_t)1 << fb);
     }
-    if (s != 4) return 3;
+    if (s != 2 * bu) return 3;
   }
   if (b2 != bound2) return 5;
   if (primal != 2 * bound2) return 6;

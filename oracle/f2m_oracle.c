@@ -69,7 +69,7 @@ static int cmp_i64(const void* a, const void* b) {
 }
 
 int or_sweep(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* cost,
-             const int32_t* lam_old, int32_t F, int32_t shift, int32_t* lam_new,
+             const int32_t* b, const int32_t* lam_old, int32_t F, int32_t shift, int32_t* lam_new,
              int64_t* bound2, int64_t* changed) {
   int32_t maxdeg = 0;
   for (int32_t v = 0; v < n; ++v)
@@ -79,17 +79,19 @@ int or_sweep(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_
   int status = OR_OK;
   for (int32_t v = 0; v < n; ++v) {
     int32_t deg = row_ptr[v + 1] - row_ptr[v];
-    if (deg < 3) { status = OR_INVALID; break; }
+    int32_t bv = b ? b[v] : 2;
+    if (bv < 1 || deg < bv + 1) { status = OR_INVALID; break; }
     for (int32_t j = 0; j < deg; ++j) {
       int32_t e = row_ptr[v] + j;
       /* Eq. (9): adjusted length of edge (v, col[e]) */
       z[j] = ((int64_t)cost[e] << F) - lam_old[v] - lam_old[col[e]];
       if (z[j] < 0) b2 += z[j];
     }
-    b2 += 4 * (int64_t)lam_old[v];
-    /* Eq. (10): 2nd and 3rd shortest adjusted edges at v */
+    b2 += 2 * (int64_t)bv * lam_old[v];
+    /* Eq. (10): 2nd and 3rd shortest adjusted edges at v; for a degree
+     * requirement b_v (Section 3), the b_v-th and (b_v+1)-th */
     qsort(z, (size_t)deg, sizeof(int64_t), cmp_i64);
-    int64_t delta = (z[1] + z[2]) / ((int64_t)1 << shift); /* C division: toward zero */
+    int64_t delta = (z[bv - 1] + z[bv]) / ((int64_t)1 << shift); /* C division: toward zero */
     int64_t nl = (int64_t)lam_old[v] + delta;
     if (nl >= OR_LAM_LIMIT || nl <= -OR_LAM_LIMIT) status = OR_OVERFLOW;
     lam_new[v] = (int32_t)nl;
@@ -102,10 +104,10 @@ int or_sweep(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_
 }
 
 int64_t or_bound2(int32_t n, const int32_t* row_ptr, const int32_t* col,
-                  const int32_t* cost, const int32_t* lam, int32_t fb) {
+                  const int32_t* cost, const int32_t* b, const int32_t* lam, int32_t fb) {
   int64_t b2 = 0;
   for (int32_t v = 0; v < n; ++v) {
-    b2 += 4 * (int64_t)lam[v];
+    b2 += 2 * (int64_t)(b ? b[v] : 2) * lam[v];
     for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
       int64_t z = ((int64_t)cost[e] << fb) - lam[v] - lam[col[e]];
       if (z < 0) b2 += z;
@@ -115,14 +117,14 @@ int64_t or_bound2(int32_t n, const int32_t* row_ptr, const int32_t* col,
 }
 
 int or_gdp(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* cost,
-           int32_t F, int32_t shift, int64_t max_iters, int32_t* lam, int64_t* iters,
+           const int32_t* b, int32_t F, int32_t shift, int64_t max_iters, int32_t* lam, int64_t* iters,
            int64_t* trace_bound2, int64_t* trace_changed, int64_t trace_cap) {
   int32_t* nxt = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
   int status = OR_NOT_CONVERGED;
   int64_t it = 0;
   while (it < max_iters) {
     int64_t b2, ch;
-    int st = or_sweep(n, row_ptr, col, cost, lam, F, shift, nxt, &b2, &ch);
+    int st = or_sweep(n, row_ptr, col, cost, b, lam, F, shift, nxt, &b2, &ch);
     if (it < trace_cap) {
       if (trace_bound2) trace_bound2[it] = b2;
       if (trace_changed) trace_changed[it] = ch;
@@ -140,7 +142,7 @@ int or_gdp(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t*
 /* ---- rule (7): primal from the signs of the adjusted lengths -------------- */
 
 int64_t or_extract(int32_t n, const int32_t* row_ptr, const int32_t* col,
-                   const int32_t* cost, const int32_t* lam, int32_t fb, uint8_t* x2) {
+                   const int32_t* cost, const int32_t* b, const int32_t* lam, int32_t fb, uint8_t* x2) {
   int64_t bad = 0;
   for (int32_t v = 0; v < n; ++v) {
     int32_t s = 0;
@@ -149,15 +151,16 @@ int64_t or_extract(int32_t n, const int32_t* row_ptr, const int32_t* col,
       x2[e] = (uint8_t)(z < 0 ? 2 : (z == 0 ? 1 : 0));
       s += x2[e];
     }
-    if (s != 4) ++bad;
+    if (s != 2 * (b ? b[v] : 2)) ++bad;
   }
   return bad;
 }
 
 /* ---- exact finisher: min-cost flow on the bipartite double cover ----------
  * Node ids: left copy L_v = v, right copy R_v = n + v.  Entry e = (u -> v) is
- * the arc L_u -> R_v, capacity 1, cost C_e = c_e * 2^F.  Every L has supply 2,
- * every R demand 2.  x_uv = (y(L_u R_v) + y(L_v R_u)) / 2 is an optimal F2M
+ * the arc L_u -> R_v, capacity 1, cost C_e = c_e * 2^F.  Every L_v has supply b_v
+ * (2 for the fractional 2-matching), every R_v demand b_v.
+ * x_uv = (y(L_u R_v) + y(L_v R_u)) / 2 is an optimal F2M
  * point and lambda_v = (pi(L_v) - pi(R_v)) / 2 an optimal dual (units 2^-F),
  * i.e. pi(L_v) - pi(R_v) in units 2^-(F+1).
  * Reduced cost of a residual arc i -> j: C(i, j) - pi(i) + pi(j).
@@ -237,8 +240,8 @@ static int32_t or_find(const int32_t* row_ptr, const int32_t* col, int32_t u, in
 }
 
 int or_finisher(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int32_t* col,
-                const int32_t* cost, const int32_t* lam, int32_t F, uint8_t* x2, int32_t* lam2,
-                int64_t* augmentations) {
+                const int32_t* cost, const int32_t* b, const int32_t* lam, int32_t F, uint8_t* x2,
+                int32_t* lam2, int64_t* augmentations) {
   int64_t nnz = row_ptr[n];
   int32_t N = 2 * n;
   int32_t* rev = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
@@ -278,8 +281,9 @@ int or_finisher(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int3
   for (int32_t u = 0; u < n; ++u) {
     int64_t out = 0, in = 0;
     for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) { out += y[e]; in += y[rev[e]]; }
-    ex[u] = 2 - out;      /* L_u: supply 2 minus outflow */
-    ex[n + u] = in - 2;   /* R_u: inflow minus demand 2 */
+    const int64_t bu = b ? b[u] : 2;
+    ex[u] = bu - out;      /* L_u: supply b_u minus outflow */
+    ex[n + u] = in - bu;   /* R_u: inflow minus demand b_u */
   }
 
   int64_t stamp = 0;
@@ -476,7 +480,7 @@ static void or_add_pairs(or_result* r, const int32_t* xy, int32_t** cost, int64_
 }
 
 or_result* or_solve(int32_t n, const int32_t* xy, const int32_t* row_ptr,
-                    const int32_t* col, const int32_t* lam0, const or_params* p,
+                    const int32_t* col, const int32_t* b, const int32_t* lam0, const or_params* p,
                     or_info* info, int64_t* trace_bound2, int64_t* trace_changed,
                     int64_t trace_cap) {
   or_result* r = (or_result*)calloc(1, sizeof(or_result));
@@ -504,7 +508,7 @@ or_result* or_solve(int32_t n, const int32_t* xy, const int32_t* row_ptr,
     int64_t it = 0;
     int64_t off = info->iterations;
     int64_t tcap = trace_cap > off ? trace_cap - off : 0;
-    int st = or_gdp(n, r->row_ptr, r->col, cost, F, p->damping_shift, p->max_iters, lam, &it,
+    int st = or_gdp(n, r->row_ptr, r->col, cost, b, F, p->damping_shift, p->max_iters, lam, &it,
                     trace_bound2 ? trace_bound2 + off : NULL,
                     trace_changed ? trace_changed + off : NULL, tcap);
     info->iterations += it;
@@ -524,12 +528,12 @@ or_result* or_solve(int32_t n, const int32_t* xy, const int32_t* row_ptr,
     }
 
     int32_t fb = F;
-    int64_t bad = or_extract(n, r->row_ptr, r->col, cost, lam, F, r->x2);
+    int64_t bad = or_extract(n, r->row_ptr, r->col, cost, b, lam, F, r->x2);
     memcpy(r->lam, lam, sizeof(int32_t) * (size_t)n);
     if (bad > 0) {
-      if (!p->finisher) { status = OR_NOT_CONVERGED; info->bound2 = or_bound2(n, r->row_ptr, r->col, cost, lam, F); break; }
+      if (!p->finisher) { status = OR_NOT_CONVERGED; info->bound2 = or_bound2(n, r->row_ptr, r->col, cost, b, lam, F); break; }
       int64_t aug = 0;
-      st = or_finisher(n, xy, r->row_ptr, r->col, cost, lam, F, r->x2, lam2, &aug);
+      st = or_finisher(n, xy, r->row_ptr, r->col, cost, b, lam, F, r->x2, lam2, &aug);
       info->finisher_calls += 1;
       info->augmentations += aug;
       if (st != OR_OK) { status = st; break; }
@@ -537,7 +541,7 @@ or_result* or_solve(int32_t n, const int32_t* xy, const int32_t* row_ptr,
       memcpy(r->lam, lam2, sizeof(int32_t) * (size_t)n);
     }
     info->frac_bits = fb;
-    info->bound2 = or_bound2(n, r->row_ptr, r->col, cost, r->lam, fb);
+    info->bound2 = or_bound2(n, r->row_ptr, r->col, cost, b, r->lam, fb);
     info->certified = 1;
     if (!p->pricing) break;
     if (fb == F && clean) { info->certified = 2; break; } /* same lambda already priced */

@@ -47,35 +47,41 @@ void or_cost_table(int32_t n, const int32_t* xy, const int32_t* row_ptr,
  *   delta_v = trunc((z(2) + z(3)) / 2^shift),  lam_new_v = lam_old_v + delta_v.
  * Also returns bound2 = 4*sum(lam_old) + sum over directed entries of min(0, z)
  * (twice the Lagrangian bound at lam_old, units 2^-F) and changed = #{delta != 0}.
- * Returns OR_OVERFLOW if some |lam_new| >= 2^29, OR_INVALID on a row of degree < 3. */
+ * b (NULL: every b_v = 2) generalises to the fractional b-matching LP
+ * (sum of x over delta(v) = b_v, Section 3's LP3 with b-th and (b+1)-th order
+ * statistics): z(b_v) and z(b_v + 1) replace z(2) and z(3), and the bound
+ * term 4*lam_v becomes 2*b_v*lam_v.  The same b parameter below has the same
+ * meaning.
+ * Returns OR_OVERFLOW if some |lam_new| >= 2^29, OR_INVALID on a row of degree
+ * below b_v + 1. */
 int or_sweep(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* cost,
-             const int32_t* lam_old, int32_t F, int32_t shift, int32_t* lam_new,
+             const int32_t* b, const int32_t* lam_old, int32_t F, int32_t shift, int32_t* lam_new,
              int64_t* bound2, int64_t* changed);
 
 /* twice the Lagrangian bound at lam (units 2^-fb) over the CSR edges */
 int64_t or_bound2(int32_t n, const int32_t* row_ptr, const int32_t* col,
-                  const int32_t* cost, const int32_t* lam, int32_t fb);
+                  const int32_t* cost, const int32_t* b, const int32_t* lam, int32_t fb);
 
 /* GDP phase: sweeps until a sweep changes nothing or max_iters sweeps ran.
  * lam is updated in place.  iters = sweeps run.  trace_bound2 / trace_changed
  * (may be NULL) receive per-sweep values for the first trace_cap sweeps.
  * Returns OR_OK on a fixed point, OR_NOT_CONVERGED at the cap, OR_OVERFLOW. */
 int or_gdp(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* cost,
-           int32_t F, int32_t shift, int64_t max_iters, int32_t* lam, int64_t* iters,
+           const int32_t* b, int32_t F, int32_t shift, int64_t max_iters, int32_t* lam, int64_t* iters,
            int64_t* trace_bound2, int64_t* trace_changed, int64_t trace_cap);
 
 /* Sign rule (7): x2_e = 2 if z_e < 0, 1 if z_e == 0, 0 if z_e > 0 (half units).
- * Returns the number of nodes whose row sum of x2 differs from 4. */
+ * Returns the number of nodes whose row sum of x2 differs from 2 b_v. */
 int64_t or_extract(int32_t n, const int32_t* row_ptr, const int32_t* col,
-                   const int32_t* cost, const int32_t* lam, int32_t fb, uint8_t* x2);
+                   const int32_t* cost, const int32_t* b, const int32_t* lam, int32_t fb, uint8_t* x2);
 
 /* Exact finisher: min-cost flow on the bipartite double cover of the CSR graph,
  * warm-started from lam (F bits); successive shortest paths, sources and ties
  * in (Morton code of the point, id) order.  Writes x2 (half units) and lam2
  * (units 2^-(F+1)).  Returns OR_OK, OR_INFEASIBLE or OR_OVERFLOW. */
 int or_finisher(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int32_t* col,
-                const int32_t* cost, const int32_t* lam, int32_t F, uint8_t* x2, int32_t* lam2,
-                int64_t* augmentations);
+                const int32_t* cost, const int32_t* b, const int32_t* lam, int32_t F, uint8_t* x2,
+                int32_t* lam2, int64_t* augmentations);
 
 /* Pricing: every pair u < v that is not an edge of the CSR and has
  * c(u,v)*2^fb < lam_u + lam_v.  Writes up to cap pairs (u, v) in ascending
@@ -122,7 +128,7 @@ typedef struct or_result or_result;
 /* lam0: initial lambda (F bits) or NULL for zero.  trace arrays as in or_gdp
  * (one entry per sweep, all phases concatenated). */
 or_result* or_solve(int32_t n, const int32_t* xy, const int32_t* row_ptr,
-                    const int32_t* col, const int32_t* lam0, const or_params* p,
+                    const int32_t* col, const int32_t* b, const int32_t* lam0, const or_params* p,
                     or_info* info, int64_t* trace_bound2, int64_t* trace_changed,
                     int64_t trace_cap);
 int64_t or_result_nnz(const or_result* r);
@@ -142,7 +148,7 @@ void or_knn(int32_t n, const int32_t* xy, int32_t k, int32_t* nbr, int64_t* d2);
 /* Certificate (independent of the solver): returns 0 when all checks pass,
  * else the number of the first failed check (see certify.c). */
 int or_certify(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int32_t* col,
-               const uint8_t* x2, const int32_t* lam, int32_t fb, int64_t bound2,
+               const int32_t* b, const uint8_t* x2, const int32_t* lam, int32_t fb, int64_t bound2,
                int32_t full_scan);
 
 #ifdef __cplusplus
