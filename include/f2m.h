@@ -60,7 +60,7 @@ typedef enum {
   F2M_ERR_NOT_CONVERGED = 4,    /* iteration or pricing-round cap reached */
   F2M_ERR_OVERFLOW = 5,         /* some |lambda| reached 2^29 (units 2^-F) */
   F2M_ERR_PRICING_OVERFLOW = 6, /* pair buffer too small (handled inside f2m_solve) */
-  F2M_ERR_INFEASIBLE = 7,       /* no fractional 2-matching on the candidate graph */
+  F2M_ERR_INFEASIBLE = 7,       /* no fractional 2-matching (b-matching) on the candidate graph */
   F2M_ERR_TIMEOUT = 8           /* a device-wide barrier wait ran past its budget */
 } f2m_status;
 
@@ -151,6 +151,21 @@ void f2m_destroy(f2m_ctx* ctx);
  *   lambda  [n] int32, host or device, units 2^-frac_bits; |lambda| < 2^29.
  * Errors: INVALID_ARG (range), CUDA. */
 f2m_status f2m_set_lambda(f2m_ctx* ctx, const int32_t* lambda, int32_t frac_bits);
+
+/* Sets per-node degree requirements: the fractional b-matching LP
+ * (sum of x over delta(v) = b_v, 0 <= x <= 1), the LP3 class of Section 3 with
+ * binary coefficients and integral right sides (Eq. 8).  The GDP update then
+ * takes the b_v-th and (b_v+1)-th smallest adjusted values of row v in place
+ * of Eq. 10's 2nd and 3rd, the bound becomes 2*sum(b_v lambda_v) + sum over
+ * directed entries of min(0, z), rule (7) extraction checks row sums 2 b_v, and
+ * the finisher's supplies and demands are b_v.  Pricing is unchanged.
+ *   b  [n] int32, host or device, copied; 1 <= b_v <= deg(v) - 1 for the
+ *      graph held now (pricing only adds edges).  NULL restores b_v = 2.
+ * Single-instance contexts only.  While b is set, GDP phases run on the
+ * streaming kernel (the shared-memory kernels hold Eq. 10's top-3 only).
+ * Errors: INVALID_ARG (range, with the first offending node in
+ * f2m_last_error; the previous b stays), OOM, CUDA. */
+f2m_status f2m_set_degrees(f2m_ctx* ctx, const int32_t* b);
 
 /* Full solve from the current lambda (see the header comment).  info may be
  * NULL.  Returns F2M_OK when certified (info->certified = 2 with pricing on, 1

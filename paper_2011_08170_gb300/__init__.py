@@ -41,7 +41,7 @@ EXPORTS = ["f2m_default_params", "f2m_create", "f2m_destroy", "f2m_set_lambda", 
            "f2m_batch_get_lambda", "f2m_batch_get_x", "f2m_batch_last_error", "f2m_destroy_batch",
            "f2m_knn", "f2m_knn_csr", "f2m_features", "f2m_mlp_create", "f2m_mlp_destroy",
            "f2m_mlp_get_params", "f2m_mlp_last_error", "f2m_mlp_forward", "f2m_mlp_grad",
-           "f2m_mlp_train", "f2m_warm_start"]
+           "f2m_mlp_train", "f2m_warm_start", "f2m_set_degrees"]
 
 F2M_MLP_NPARAMS = 18817
 
@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH):
     L.f2m_destroy.argtypes = [vp]
     L.f2m_destroy.restype = None
     L.f2m_set_lambda.argtypes = [vp, vp, i32]
+    L.f2m_set_degrees.argtypes = [vp, vp]
     L.f2m_solve.argtypes = [vp, C.POINTER(f2m_info)]
     L.f2m_gdp.argtypes = [vp, i64, C.POINTER(i64), vp, vp, i64]
     L.f2m_price.argtypes = [vp, C.POINTER(i64), vp, i64]
@@ -145,7 +146,7 @@ def load(path: str = LIB_PATH):
         getattr(L, name).restype = C.c_int
     L.f2m_kernel_launches.argtypes = []
     L.f2m_kernel_launches.restype = C.c_int64
-    for name in ("f2m_create", "f2m_set_lambda", "f2m_solve", "f2m_gdp", "f2m_price",
+    for name in ("f2m_create", "f2m_set_lambda", "f2m_set_degrees", "f2m_solve", "f2m_gdp", "f2m_price",
                  "f2m_add_edges", "f2m_extract", "f2m_get_lambda", "f2m_get_bound", "f2m_get_x"):
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -252,6 +253,15 @@ def f2m_set_lambda(ctx: Ctx, lam, frac_bits: int) -> None:
     _check(ctx, load().f2m_set_lambda(ctx.handle, p, frac_bits))
 
 
+def f2m_set_degrees(ctx: Ctx, b) -> None:
+    """Degree requirements b_v (fractional b-matching); a scalar sets every b_v,
+    None restores b_v = 2."""
+    if b is not None and not hasattr(b, "data_ptr") and np.ndim(b) == 0:
+        b = np.full(ctx.n, int(b), np.int32)
+    p, keep = _ptr(None if b is None else _as(b, np.int32))
+    _check(ctx, load().f2m_set_degrees(ctx.handle, p))
+
+
 def f2m_solve(ctx: Ctx, raise_on_error: bool = True) -> f2m_info:
     info = f2m_info()
     st = load().f2m_solve(ctx.handle, C.byref(info))
@@ -351,10 +361,14 @@ class Solution:
         return self.info["bound2"] / (2.0 * (1 << self.info["frac_bits"]))
 
 
-def solve(xy, row_ptr, col, lam0=None, params: f2m_params | None = None, stream=None) -> Solution:
-    """Create, optionally warm-start, solve, and read back everything."""
+def solve(xy, row_ptr, col, lam0=None, params: f2m_params | None = None, stream=None,
+          b=None) -> Solution:
+    """Create, optionally set degree requirements b (fractional b-matching) and
+    warm-start, solve, and read back everything."""
     ctx = f2m_create(xy, row_ptr, col, params, stream)
     try:
+        if b is not None:
+            f2m_set_degrees(ctx, b)
         if lam0 is not None:
             f2m_set_lambda(ctx, lam0, (params.frac_bits if params is not None else 8))
         info = f2m_solve(ctx)

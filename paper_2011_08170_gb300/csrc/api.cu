@@ -150,7 +150,7 @@ extern "C" void f2m_destroy(f2m_ctx* c) {
   dfree(c->d_ranges); dfree(c->d_boxes); dfree(c->d_smax);
   dfree(c->d_count); dfree(c->d_tile); dfree(c->d_deg); dfree(c->d_tmp_rp); dfree(c->d_new_rp);
   dfree(c->d_block_sums); dfree(c->d_tmp_col); dfree(c->d_out_a); dfree(c->d_out_b);
-  dfree(c->d_check); dfree(c->d_scalar); dfree(c->d_bad);
+  dfree(c->d_check); dfree(c->d_scalar); dfree(c->d_bad); dfree(c->d_b);
   free_finisher_buffers(c);
   if (c->fin_work) finisher_work_free(c->fin_work);
   plan2_free(c->plan);
@@ -181,9 +181,10 @@ static std::string check_message(int flags, int first) {
   static const char* names[] = {"row_ptr not monotone or not ending at nnz", "column index out of range",
                                 "row not sorted ascending or duplicate column", "self-loop",
                                 "CSR not symmetric", "node degree below 3",
-                                "coordinate outside [0, 2^20)", "pair out of range or u == v"};
+                                "coordinate outside [0, 2^20)", "pair out of range or u == v",
+                                "degree requirement b_v outside [1, deg(v) - 1]"};
   std::string m;
-  for (int b = 0; b < 8; ++b)
+  for (int b = 0; b < 9; ++b)
     if (flags & (1 << b)) {
       if (!m.empty()) m += "; ";
       m += names[b];
@@ -324,6 +325,32 @@ extern "C" f2m_status f2m_set_lambda(f2m_ctx* c, const int32_t* lambda, int32_t 
   return F2M_OK;
 }
 
+extern "C" f2m_status f2m_set_degrees(f2m_ctx* c, const int32_t* b) {
+  if (!c) return fail(c, F2M_ERR_INVALID_ARG, "NULL context");
+  if (c->seg_off.size() != 2) return fail(c, F2M_ERR_INVALID_ARG, "degree requirements apply to a single-instance context");
+  if (!b) {
+    dfree(c->d_b);
+    c->b_max = 2;
+    return F2M_OK;
+  }
+  int32_t* d = nullptr;
+  CK(c, dalloc(&d, c->n));
+  cudaError_t e = cudaMemcpyAsync(d, b, sizeof(int32_t) * c->n, cudaMemcpyDefault, c->st);
+  if (e == cudaSuccess) e = reset_check(c);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_bad, 0, sizeof(unsigned long long), c->st);
+  if (e == cudaSuccess) e = launch_check_degrees(c->d_rp, d, c->n, c->d_check, c->d_bad, c->st);
+  unsigned long long bmax = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bmax, c->d_bad, sizeof(bmax), cudaMemcpyDeviceToHost, c->st);
+  CheckCtl h{};
+  if (e == cudaSuccess) e = read_check(c, &h);
+  if (e != cudaSuccess) { dfree(d); return cuda_fail(c, e, "set_degrees"); }
+  if (h.flags) { dfree(d); return fail(c, F2M_ERR_INVALID_ARG, check_message(h.flags, h.first_bad)); }
+  dfree(c->d_b);
+  c->d_b = d;
+  c->b_max = (int32_t)bmax;
+  return F2M_OK;
+}
+
 // lambda (device) and its fractional bits
 const int32_t* f2m::cur_lambda(f2m_ctx* c, int32_t* fb) {
   *fb = c->fb_cur;
@@ -349,8 +376,10 @@ f2m_status f2m::gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, bool 
   long long* tb = want_trace ? c->d_trace_b2 : nullptr;
   unsigned long long* tc = want_trace ? reinterpret_cast<unsigned long long*>(c->d_trace_ch) : nullptr;
   const int64_t tcap = want_trace ? trace_cap : 0;
-  bool two = c->plan.valid2;  // two sweeps per barrier
-  bool tiled = c->plan.valid;
+  // the shared-memory kernels hold Eq. 10's top-3; degree requirements other
+  // than 2 run on the streaming kernel
+  bool two = c->plan.valid2 && !c->d_b;  // two sweeps per barrier
+  bool tiled = c->plan.valid && !c->d_b;
   if (two) {
     cudaError_t e = launch_gdp_tiled2(c->plan, c->d_lam[c->cur], c->p.damping_shift, max_sweeps, c->d_gdp, tb,
                                       tc, tcap, c->p.barrier_budget_cycles, c->st);
@@ -372,7 +401,7 @@ f2m_status f2m::gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, bool 
     }
   }
   if (!two && !tiled)
-    CK(c, launch_gdp(c->d_rp, c->d_ec, c->d_lam[c->cur], c->d_lam[c->cur ^ 1], c->n, F,
+    CK(c, launch_gdp(c->d_rp, c->d_ec, c->d_b, c->b_max, c->d_lam[c->cur], c->d_lam[c->cur ^ 1], c->n, F,
                      c->p.damping_shift, max_sweeps, c->d_gdp, tb, tc, tcap,
                      c->p.barrier_budget_cycles, c->num_sms, c->st));
   CK(c, cudaEventRecord(c->ev1, c->st));
@@ -639,7 +668,7 @@ f2m_status f2m::extract_internal(f2m_ctx* c, int64_t* bad, double* ms) {
   int32_t fb = 0;
   const int32_t* lam = cur_lambda(c, &fb);
   CK(c, cudaEventRecord(c->ev0, c->st));
-  CK(c, launch_extract(c->d_rp, c->d_ec, lam, c->n, fb, c->d_x2, c->d_bad, c->st));
+  CK(c, launch_extract(c->d_rp, c->d_ec, c->d_b, lam, c->n, fb, c->d_x2, c->d_bad, c->st));
   CK(c, cudaEventRecord(c->ev1, c->st));
   unsigned long long b = 0;
   CK(c, cudaMemcpyAsync(&b, c->d_bad, sizeof(b), cudaMemcpyDeviceToHost, c->st));
@@ -663,7 +692,7 @@ extern "C" f2m_status f2m_extract(f2m_ctx* c, uint8_t* x2, int64_t* bad) {
 f2m_status f2m::bound_internal(f2m_ctx* c, int64_t* b2) {
   int32_t fb = 0;
   const int32_t* lam = cur_lambda(c, &fb);
-  CK(c, launch_bound(c->d_rp, c->d_ec, lam, c->n, fb, c->d_scalar, c->st));
+  CK(c, launch_bound(c->d_rp, c->d_ec, c->d_b, lam, c->n, fb, c->d_scalar, c->st));
   long long h = 0;
   CK(c, cudaMemcpyAsync(&h, c->d_scalar, sizeof(h), cudaMemcpyDeviceToHost, c->st));
   CK(c, cudaStreamSynchronize(c->st));
@@ -689,7 +718,7 @@ f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug) {
   int32_t* d_lam_int = P.ilam[0];   // free outside a GDP phase
   int32_t* d_lam2_int = P.ilam[1];
   int32_t* d_exl = P.tmp;
-  CK(c, fin_prepare(P, c->d_lam[c->cur], F, d_lam_int, c->d_fy, d_exl, c->st));
+  CK(c, fin_prepare(P, c->d_lam[c->cur], c->d_b, F, d_lam_int, c->d_fy, d_exl, c->st));
   if (c->d_fin_include)
     CK(c, launch_batch_mask_surplus(d_exl, c->d_seg_off, (int32_t)c->seg_off.size() - 1,
                                     c->d_fin_include, n, c->st));
@@ -707,7 +736,9 @@ f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug) {
   const int r = host_finisher(n, c->h_irp, c->h_iec, c->h_twin, c->h_y, c->h_exl, c->h_lam, F,
                               c->h_x, c->h_lam2, c->seg_off.data(), nseg, hw > 1 ? hw : 1, aug,
                               c->fin_work);
-  if (r == 7) return fail(c, F2M_ERR_INFEASIBLE, "no fractional 2-matching exists on the candidate graph");
+  if (r == 7)
+    return fail(c, F2M_ERR_INFEASIBLE, c->d_b ? "no fractional b-matching exists on the candidate graph"
+                                              : "no fractional 2-matching exists on the candidate graph");
   if (r == 5) return fail(c, F2M_ERR_OVERFLOW, "finisher lambda out of range");
   if (r != 0) return fail(c, F2M_ERR_INVALID_ARG, "finisher failed");
   CK(c, cudaMemcpyAsync(c->d_fx, c->h_x, c->nnz, cudaMemcpyHostToDevice, c->st));

@@ -54,6 +54,7 @@ enum CheckBits {
   kLowDegree = 32,
   kBadCoord = 64,
   kBadPair = 128,
+  kBadDegreeReq = 256,
 };
 
 // process-wide count of kernel launches made by this library (api.cu)
@@ -67,20 +68,28 @@ cudaError_t launch_check(const int2* xy, const int32_t* rp, const int32_t* col, 
                          int64_t nnz, CheckCtl* ctl, cudaStream_t st);
 // coordinates in [0, 2^20) (flag kBadCoord); ctl zeroed with first_bad = INT_MAX
 cudaError_t launch_check_points(const int2* xy, int32_t n, CheckCtl* ctl, cudaStream_t st);
+// degree requirements 1 <= b_v <= deg(v) - 1 (flag kBadDegreeReq); the
+// largest b_v into *bmax (zeroed by the caller)
+cudaError_t launch_check_degrees(const int32_t* rp, const int32_t* bdeg, int32_t n, CheckCtl* ctl,
+                                 unsigned long long* bmax, cudaStream_t st);
 // ec[e] = {col[e], c(row(e), col[e])}
 cudaError_t launch_build_ec(const int2* xy, const int32_t* rp, const int32_t* col, int32_t n,
                             int2* ec, cudaStream_t st);
-// one persistent cooperative GDP phase
-cudaError_t launch_gdp(const int32_t* rp, const int2* ec, int32_t* lam0, int32_t* lam1, int32_t n,
-                       int32_t F, int32_t shift, int64_t max_sweeps, GdpCtl* ctl,
-                       long long* trace_b2, unsigned long long* trace_ch, int64_t trace_cap,
-                       long long budget, int num_sms, cudaStream_t st);
+// one persistent cooperative GDP phase; bdeg: degree requirements b_v in
+// caller order (NULL: b_v = 2, the fractional 2-matching) -- likewise below
+// (bmax: the largest b_v, which picks the selection method)
+cudaError_t launch_gdp(const int32_t* rp, const int2* ec, const int32_t* bdeg, int32_t bmax,
+                       int32_t* lam0, int32_t* lam1, int32_t n, int32_t F, int32_t shift,
+                       int64_t max_sweeps, GdpCtl* ctl, long long* trace_b2,
+                       unsigned long long* trace_ch, int64_t trace_cap, long long budget,
+                       int num_sms, cudaStream_t st);
 // bound2 at lam with fb fractional bits, into *out (zeroed by the launcher)
-cudaError_t launch_bound(const int32_t* rp, const int2* ec, const int32_t* lam, int32_t n,
-                         int32_t fb, long long* out, cudaStream_t st);
+cudaError_t launch_bound(const int32_t* rp, const int2* ec, const int32_t* bdeg, const int32_t* lam,
+                         int32_t n, int32_t fb, long long* out, cudaStream_t st);
 // rule (7) extraction; *bad zeroed by the launcher
-cudaError_t launch_extract(const int32_t* rp, const int2* ec, const int32_t* lam, int32_t n,
-                           int32_t fb, uint8_t* x2, unsigned long long* bad, cudaStream_t st);
+cudaError_t launch_extract(const int32_t* rp, const int2* ec, const int32_t* bdeg, const int32_t* lam,
+                           int32_t n, int32_t fb, uint8_t* x2, unsigned long long* bad,
+                           cudaStream_t st);
 // lam_out = lam_in >> 1 (F+1 bits -> F bits, floor)
 cudaError_t launch_halve(const int32_t* lam_in, int32_t* lam_out, int32_t n, cudaStream_t st);
 // all-pairs pricing scan: pairs (u < v) outside the CSR with z < 0
@@ -204,8 +213,9 @@ cudaError_t plan_scatter_lambda(const GdpPlan& p, int which, int32_t* lam_out, c
 
 // ---- exact finisher (finisher_prep.cu on the device, finisher.cpp on the host) ---
 cudaError_t fin_build_twin(const GdpPlan& p, int32_t* twin, cudaStream_t st);
-cudaError_t fin_prepare(const GdpPlan& p, const int32_t* lam_caller, int32_t F, int32_t* lam_int,
-                        uint8_t* y, int32_t* exl, cudaStream_t st);
+// bdeg_caller: degree requirements in caller order (NULL: 2)
+cudaError_t fin_prepare(const GdpPlan& p, const int32_t* lam_caller, const int32_t* bdeg_caller,
+                        int32_t F, int32_t* lam_int, uint8_t* y, int32_t* exl, cudaStream_t st);
 // include (device, per segment; NULL = all): x of excluded segments is kept
 cudaError_t fin_scatter(const GdpPlan& p, const int32_t* rp, const uint8_t* x_int,
                         const int32_t* lam2_int, uint8_t* x_out, int32_t* lam2_out,

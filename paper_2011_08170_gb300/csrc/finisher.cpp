@@ -10,7 +10,9 @@
 // L_u -> R_v of capacity 1 and cost C = c_uv * 2^F.  From an optimal flow y and
 // optimal potentials pi:  x_uv = (y(L_u R_v) + y(L_v R_u)) / 2  and
 // lambda_v = (pi(L_v) - pi(R_v)) / 2 are optimal for F2M (the latter is
-// returned in units 2^-(F+1) as pi(L_v) - pi(R_v)).
+// returned in units 2^-(F+1) as pi(L_v) - pi(R_v)).  With degree requirements
+// b_v (fractional b-matching) the supplies and demands are b_v; the caller's
+// surpluses exl carry them, so nothing here depends on the value 2.
 //
 // Warm start from the GDP duals: pi(L_v) = lambda_v, pi(R_v) = -lambda_v, so an
 // arc's reduced cost C - pi(tail) + pi(head) is the adjusted length z_e (Eq. 9);
@@ -193,8 +195,8 @@ int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t*
   for (int32_t i = 0; i < n; ++i) {
     pi[i] = lam[i];
     pi[n + i] = -(int64_t)lam[i];
-    excess[i] = exl[i];       // L_i: supply 2 minus outflow
-    excess[n + i] = -exl[i];  // R_i: inflow minus demand 2 (z is symmetric)
+    excess[i] = exl[i];       // L_i: supply b_i minus outflow
+    excess[n + i] = -exl[i];  // R_i: inflow minus demand b_i (z is symmetric)
   }
   // segments are independent: whole segments go to workers
   int32_t nw = threads < 1 ? 1 : threads;

@@ -6,8 +6,9 @@
 // the caller's layout.  These kernels build what it needs in one pass each:
 //   twin[e]  for e = (i -> j), the entry of (j -> i);
 //   y[e]     = 1 if z_e < 0 (arcs of negative reduced cost start saturated);
-//   exl[i]   = 2 - #{e in row i : y[e]} (surplus of the left copy of i; the
-//            right copy has the opposite value since z is symmetric);
+//   exl[i]   = b_i - #{e in row i : y[e]} (surplus of the left copy of i,
+//            b_i = 2 for the fractional 2-matching; the right copy has the
+//            opposite value since z is symmetric);
 // and map its output (x in half units, lambda at F+1 bits) back to caller order.
 #include "f2m_device.cuh"
 #include "f2m_internal.h"
@@ -39,7 +40,8 @@ __global__ void fin_twin_kernel(const int32_t* __restrict__ irp, const int2* __r
 }
 
 __global__ void fin_init_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ iec,
-                                const int32_t* __restrict__ lam, int32_t n, int32_t F,
+                                const int32_t* __restrict__ lam, const int32_t* __restrict__ bdeg,
+                                const int32_t* __restrict__ perm, int32_t n, int32_t F,
                                 uint8_t* __restrict__ y, int32_t* __restrict__ exl) {
   F2M_GRID_STRIDE(i, n) {
     const long long li = lam[i];
@@ -50,7 +52,7 @@ __global__ void fin_init_kernel(const int32_t* __restrict__ irp, const int2* __r
       y[e] = (uint8_t)(z < 0);
       cnt += (z < 0);
     }
-    exl[i] = 2 - cnt;
+    exl[i] = (bdeg ? bdeg[perm[i]] : 2) - cnt;
   }
 }
 
@@ -79,10 +81,11 @@ cudaError_t fin_build_twin(const GdpPlan& p, int32_t* twin, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t fin_prepare(const GdpPlan& p, const int32_t* lam_caller, int32_t F, int32_t* lam_int,
-                        uint8_t* y, int32_t* exl, cudaStream_t st) {
+cudaError_t fin_prepare(const GdpPlan& p, const int32_t* lam_caller, const int32_t* bdeg_caller,
+                        int32_t F, int32_t* lam_int, uint8_t* y, int32_t* exl, cudaStream_t st) {
   gather_perm(lam_caller, p.perm, p.n, lam_int, st);
-  fin_init_kernel<<<grid_for(p.n, 128), 128, 0, st>>>(p.irp, p.iec, lam_int, p.n, F, y, exl);
+  fin_init_kernel<<<grid_for(p.n, 128), 128, 0, st>>>(p.irp, p.iec, lam_int, bdeg_caller, p.perm,
+                                                      p.n, F, y, exl);
   count_launch();
   return cudaGetLastError();
 }

@@ -116,7 +116,7 @@ extern "C" f2m_status f2m_gdp_noalloc(const int32_t* row_ptr, const int32_t* ec,
   int32_t* lam_other = base + kCtlInts;
   e = cudaMemsetAsync(ctl, 0, sizeof(GdpCtl), st);
   if (e != cudaSuccess) return cuda_msg(errbuf, errlen, "clear control block", e);
-  e = launch_gdp(row_ptr, reinterpret_cast<const int2*>(ec), lambda, lam_other, n, frac_bits,
+  e = launch_gdp(row_ptr, reinterpret_cast<const int2*>(ec), nullptr, 2, lambda, lam_other, n, frac_bits,
                  damping_shift, max_sweeps, ctl, nullptr, nullptr, 0, 4000000000LL, num_sms, st);
   if (e != cudaSuccess) return cuda_msg(errbuf, errlen, "launch", e);
   GdpCtl h;

@@ -79,6 +79,24 @@ cudaError_t launch_check_points(const int2* xy, int32_t n, CheckCtl* ctl, cudaSt
   return cudaGetLastError();
 }
 
+// degree requirements: 1 <= b_v and b_v + 1 <= deg(v) (the (b_v+1)-th value of
+// the row must exist, Section 3)
+__global__ void check_degrees_kernel(const int32_t* rp, const int32_t* bdeg, int32_t n, CheckCtl* ctl,
+                                     unsigned long long* bmax) {
+  F2M_GRID_STRIDE(v, n) {
+    const int bv = bdeg[v];
+    if (bv < 1 || (long long)bv + 1 > (long long)rp[v + 1] - rp[v]) flag(ctl, kBadDegreeReq, v);
+    else atomicMax(bmax, (unsigned long long)bv);
+  }
+}
+
+cudaError_t launch_check_degrees(const int32_t* rp, const int32_t* bdeg, int32_t n, CheckCtl* ctl,
+                                 unsigned long long* bmax, cudaStream_t st) {
+  check_degrees_kernel<<<grid_for(n, 256), 256, 0, st>>>(rp, bdeg, n, ctl, bmax);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_check(const int2* xy, const int32_t* rp, const int32_t* col, int32_t n,
                          int64_t nnz, CheckCtl* ctl, cudaStream_t st) {
   // two passes; the host reads ctl between them (pass 2 trusts the row offsets)
