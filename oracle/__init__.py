@@ -54,7 +54,7 @@ _u8p = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
 class _Params(C.Structure):
     _fields_ = [("frac_bits", C.c_int32), ("damping_shift", C.c_int32),
                 ("max_iters", C.c_int64), ("max_pricing_rounds", C.c_int32),
-                ("pricing", C.c_int32), ("finisher", C.c_int32)]
+                ("pricing", C.c_int32), ("finisher", C.c_int32), ("update", C.c_int32)]
 
 
 class _Info(C.Structure):
@@ -103,6 +103,18 @@ def lib():
         L.or_certify.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_void_p, _u8p, _i32p, C.c_int32,
                                  C.c_int64, C.c_int32]
         L.or_knn.argtypes = [C.c_int32, _i32p, C.c_int32, _i32p, _i64p]
+        L.or_splitmix64.restype = C.c_uint64
+        L.or_splitmix64.argtypes = [C.c_uint64]
+        L.or_color_greedy.restype = C.c_int32
+        L.or_color_greedy.argtypes = [C.c_int32, _i32p, _i32p, _i32p]
+        L.or_gs_sweep.restype = C.c_int
+        L.or_gs_sweep.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_void_p, _i32p, C.c_int32,
+                                  _i32p, C.c_int32, C.c_int32, C.POINTER(C.c_int64),
+                                  C.POINTER(C.c_int64)]
+        L.or_gdp_gs.restype = C.c_int
+        L.or_gdp_gs.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_void_p, _i32p, C.c_int32,
+                                C.c_int32, C.c_int32, C.c_int64, _i32p, C.POINTER(C.c_int64),
+                                C.c_void_p, C.c_void_p, C.c_int64]
         _lib = L
     return _lib
 
@@ -171,6 +183,45 @@ def gdp(row_ptr, col, cost, lam0, F=8, shift=2, max_iters=100000, trace=False, b
     st = lib().or_gdp(lam.size, _i32(row_ptr), _i32(col), _i32(cost), _ptr(bb), F, shift, max_iters, lam,
                       C.byref(it), tb.ctypes.data if trace else None,
                       tc.ctypes.data if trace else None, max_iters if trace else 0)
+    k = it.value
+    return st, lam, k, (tb[:k] if trace else None), (tc[:k] if trace else None)
+
+
+def splitmix64(seed: int) -> int:
+    return int(lib().or_splitmix64(seed))
+
+
+def color_greedy(row_ptr, col):
+    """Greedy colouring in (degree, splitmix64, id) priority: (ncolors, color int32 [n])."""
+    row_ptr, col = _i32(row_ptr), _i32(col)
+    color = np.zeros(row_ptr.size - 1, dtype=np.int32)
+    nc = lib().or_color_greedy(row_ptr.size - 1, row_ptr, col, color)
+    return int(nc), color
+
+
+def gs_sweep(row_ptr, col, cost, lam, color, ncolors, F=8, shift=1, b=None):
+    """One class-by-class sweep: returns (status, lam_new, bound2 at the input, changed)."""
+    row_ptr, col, cost = _i32(row_ptr), _i32(col), _i32(cost)
+    out = _i32(lam).copy()
+    bb = _degrees(b, out.size)
+    b2, ch = C.c_int64(), C.c_int64()
+    st = lib().or_gs_sweep(out.size, row_ptr, col, cost, _ptr(bb), _i32(color), ncolors, out, F,
+                           shift, C.byref(b2), C.byref(ch))
+    return st, out, b2.value, ch.value
+
+
+def gdp_gs(row_ptr, col, cost, lam0, color, ncolors, F=8, shift=1, max_iters=100000, trace=False,
+           b=None):
+    """Class-by-class GDP phase: returns (status, lam, iters, trace_bound2, trace_changed)."""
+    lam = _i32(lam0).copy()
+    bb = _degrees(b, lam.size)
+    it = C.c_int64()
+    tb = np.zeros(max_iters if trace else 1, dtype=np.int64)
+    tc = np.zeros_like(tb)
+    st = lib().or_gdp_gs(lam.size, _i32(row_ptr), _i32(col), _i32(cost), _ptr(bb), _i32(color),
+                         ncolors, F, shift, max_iters, lam, C.byref(it),
+                         tb.ctypes.data if trace else None, tc.ctypes.data if trace else None,
+                         max_iters if trace else 0)
     k = it.value
     return st, lam, k, (tb[:k] if trace else None), (tc[:k] if trace else None)
 
@@ -244,11 +295,12 @@ class OracleResult:
 
 
 def solve(xy, row_ptr, col, lam0=None, F=8, shift=2, max_iters=200000, max_pricing_rounds=64,
-          pricing=True, finisher=True, trace_cap=0, b=None) -> OracleResult:
+          pricing=True, finisher=True, trace_cap=0, b=None, classes=False) -> OracleResult:
+    """classes: class-by-class (Gauss-Seidel) sweeps instead of Jacobi."""
     xy, row_ptr, col = _i32(xy), _i32(row_ptr), _i32(col)
     n = row_ptr.size - 1
     bb = _degrees(b, n)
-    p = _Params(F, shift, max_iters, max_pricing_rounds, int(pricing), int(finisher))
+    p = _Params(F, shift, max_iters, max_pricing_rounds, int(pricing), int(finisher), int(classes))
     info = _Info()
     lam0a = None if lam0 is None else _i32(lam0)
     tb = np.zeros(max(trace_cap, 1), dtype=np.int64)

@@ -139,6 +139,125 @@ int or_gdp(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t*
   return status;
 }
 
+/* ---- colour classes and the class-by-class (Gauss-Seidel) sweep -----------
+ * Section 5.1 computes every node's gradient in parallel from one lambda
+ * (Jacobi, or_sweep).  The variant below updates one colour class at a time, a
+ * class being an independent set of the graph: nodes of a class share no edge,
+ * so their updates do not interact, and each node reads the current lambda of
+ * its neighbours.  With the full step (shift = 1) each class update maximises
+ * the Lagrangian over that class's duals with the others fixed, so the bound
+ * never decreases from sweep to sweep.  The paper does not describe this
+ * variant; it is a stated extension.
+ *
+ * Colouring: greedy, each node taking the smallest colour not held by an
+ * already-coloured neighbour, nodes taken in priority order: larger degree
+ * first, then larger h(v), then smaller id, where h(v) is the first output of
+ * SplitMix64 (Steele, Lea and Flood 2014) seeded with v. */
+
+uint64_t or_splitmix64(uint64_t seed) {
+  uint64_t z = seed + 0x9e3779b97f4a7c15ULL;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+static const int32_t* g_color_rp; /* qsort context for cmp_priority */
+
+static int cmp_priority(const void* a, const void* b) {
+  int32_t u = *(const int32_t*)a, v = *(const int32_t*)b;
+  int32_t du = g_color_rp[u + 1] - g_color_rp[u], dv = g_color_rp[v + 1] - g_color_rp[v];
+  if (du != dv) return du > dv ? -1 : 1;
+  uint64_t hu = or_splitmix64((uint64_t)u), hv = or_splitmix64((uint64_t)v);
+  if (hu != hv) return hu > hv ? -1 : 1;
+  return (u > v) - (u < v);
+}
+
+int32_t or_color_greedy(int32_t n, const int32_t* row_ptr, const int32_t* col, int32_t* color) {
+  int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t maxdeg = 0;
+  for (int32_t v = 0; v < n; ++v) {
+    order[v] = v;
+    color[v] = -1;
+    if (row_ptr[v + 1] - row_ptr[v] > maxdeg) maxdeg = row_ptr[v + 1] - row_ptr[v];
+  }
+  g_color_rp = row_ptr;
+  qsort(order, (size_t)n, sizeof(int32_t), cmp_priority);
+  uint8_t* used = (uint8_t*)calloc((size_t)maxdeg + 2, 1);
+  int32_t ncolors = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t v = order[i];
+    for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+      int32_t c = color[col[e]];
+      if (c >= 0 && c <= maxdeg) used[c] = 1;
+    }
+    int32_t c = 0;
+    while (used[c]) ++c;
+    color[v] = c;
+    if (c + 1 > ncolors) ncolors = c + 1;
+    for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+      int32_t cc = color[col[e]];
+      if (cc >= 0 && cc <= maxdeg) used[cc] = 0;
+    }
+  }
+  free(used);
+  free(order);
+  return ncolors;
+}
+
+int or_gs_sweep(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* cost,
+                const int32_t* b, const int32_t* color, int32_t ncolors, int32_t* lam, int32_t F,
+                int32_t shift, int64_t* bound2, int64_t* changed) {
+  int32_t maxdeg = 0;
+  for (int32_t v = 0; v < n; ++v)
+    if (row_ptr[v + 1] - row_ptr[v] > maxdeg) maxdeg = row_ptr[v + 1] - row_ptr[v];
+  int64_t* z = (int64_t*)malloc(sizeof(int64_t) * (size_t)(maxdeg > 0 ? maxdeg : 1));
+  *bound2 = or_bound2(n, row_ptr, col, cost, b, lam, F); /* at the sweep's input */
+  int64_t ch = 0;
+  int status = OR_OK;
+  for (int32_t c = 0; c < ncolors && status != OR_INVALID; ++c) {
+    for (int32_t v = 0; v < n; ++v) {
+      if (color[v] != c) continue;
+      int32_t deg = row_ptr[v + 1] - row_ptr[v];
+      int32_t bv = b ? b[v] : 2;
+      if (bv < 1 || deg < bv + 1) { status = OR_INVALID; break; }
+      for (int32_t j = 0; j < deg; ++j) {
+        int32_t e = row_ptr[v] + j;
+        z[j] = ((int64_t)cost[e] << F) - lam[v] - lam[col[e]]; /* Eq. (9), current lambda */
+      }
+      qsort(z, (size_t)deg, sizeof(int64_t), cmp_i64);
+      int64_t delta = (z[bv - 1] + z[bv]) / ((int64_t)1 << shift); /* Eq. (10) / Section 3 */
+      int64_t nl = (int64_t)lam[v] + delta;
+      if (delta != 0) ++ch;
+      if (nl >= OR_LAM_LIMIT || nl <= -OR_LAM_LIMIT) { status = OR_OVERFLOW; continue; } /* keeps its value */
+      lam[v] = (int32_t)nl;
+    }
+  }
+  free(z);
+  *changed = ch;
+  return status;
+}
+
+int or_gdp_gs(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* cost,
+              const int32_t* b, const int32_t* color, int32_t ncolors, int32_t F, int32_t shift,
+              int64_t max_iters, int32_t* lam, int64_t* iters, int64_t* trace_bound2,
+              int64_t* trace_changed, int64_t trace_cap) {
+  int status = OR_NOT_CONVERGED;
+  int64_t it = 0;
+  while (it < max_iters) {
+    int64_t b2, ch;
+    int st = or_gs_sweep(n, row_ptr, col, cost, b, color, ncolors, lam, F, shift, &b2, &ch);
+    if (it < trace_cap) {
+      if (trace_bound2) trace_bound2[it] = b2;
+      if (trace_changed) trace_changed[it] = ch;
+    }
+    ++it;
+    if (st != OR_OK) { status = st; break; }
+    if (ch == 0) { status = OR_OK; break; }
+  }
+  *iters = it;
+  return status;
+}
+
 /* ---- rule (7): primal from the signs of the adjusted lengths -------------- */
 
 int64_t or_extract(int32_t n, const int32_t* row_ptr, const int32_t* col,
@@ -508,9 +627,20 @@ or_result* or_solve(int32_t n, const int32_t* xy, const int32_t* row_ptr,
     int64_t it = 0;
     int64_t off = info->iterations;
     int64_t tcap = trace_cap > off ? trace_cap - off : 0;
-    int st = or_gdp(n, r->row_ptr, r->col, cost, b, F, p->damping_shift, p->max_iters, lam, &it,
-                    trace_bound2 ? trace_bound2 + off : NULL,
-                    trace_changed ? trace_changed + off : NULL, tcap);
+    int st;
+    if (p->update == OR_UPDATE_CLASSES) {
+      /* colour the current graph (pricing may have added edges) */
+      int32_t* color = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+      int32_t nc = or_color_greedy(n, r->row_ptr, r->col, color);
+      st = or_gdp_gs(n, r->row_ptr, r->col, cost, b, color, nc, F, p->damping_shift, p->max_iters,
+                     lam, &it, trace_bound2 ? trace_bound2 + off : NULL,
+                     trace_changed ? trace_changed + off : NULL, tcap);
+      free(color);
+    } else {
+      st = or_gdp(n, r->row_ptr, r->col, cost, b, F, p->damping_shift, p->max_iters, lam, &it,
+                  trace_bound2 ? trace_bound2 + off : NULL,
+                  trace_changed ? trace_changed + off : NULL, tcap);
+    }
     info->iterations += it;
     info->phases += 1;
     if (st == OR_OVERFLOW || st == OR_INVALID) { status = st; break; }

@@ -101,6 +101,27 @@ int64_t or_merge(int32_t n, const int32_t* row_ptr, const int32_t* col, int64_t 
                  const int32_t* pairs, int32_t* out_row_ptr, int32_t* out_col);
 
 /* Full solve, Section 4-5 with pricing and finisher (see f2m_oracle.c). */
+/* Colour classes and the class-by-class (Gauss-Seidel) variant of the sweep.
+ * or_splitmix64: first output of SplitMix64 seeded with `seed`.
+ * or_color_greedy: greedy colouring (smallest colour unused by coloured
+ *   neighbours) in priority order: larger degree, then larger
+ *   or_splitmix64(v), then smaller v.  Returns the number of colours.
+ * or_gs_sweep: one sweep updating lam IN PLACE class 0, 1, ..., ncolors-1, each
+ *   node of the class from the current lambda (Eq. 9; Eq. 10 or its b_v form).
+ *   bound2 = the bound at the input lambda (as or_bound2); changed = #{delta != 0}.
+ *   A node whose new value would reach |lambda| >= 2^29 keeps its value, the
+ *   sweep completes and OR_OVERFLOW is returned; OR_INVALID on a short row.
+ * or_gdp_gs: sweeps until one changes nothing or max_iters (as or_gdp). */
+uint64_t or_splitmix64(uint64_t seed);
+int32_t or_color_greedy(int32_t n, const int32_t* row_ptr, const int32_t* col, int32_t* color);
+int or_gs_sweep(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* cost,
+                const int32_t* b, const int32_t* color, int32_t ncolors, int32_t* lam, int32_t F,
+                int32_t shift, int64_t* bound2, int64_t* changed);
+int or_gdp_gs(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* cost,
+              const int32_t* b, const int32_t* color, int32_t ncolors, int32_t F, int32_t shift,
+              int64_t max_iters, int32_t* lam, int64_t* iters, int64_t* trace_bound2,
+              int64_t* trace_changed, int64_t trace_cap);
+
 typedef struct {
   int32_t frac_bits;        /* F */
   int32_t damping_shift;    /* shift in delta = trunc((z2+z3)/2^shift) */
@@ -108,7 +129,11 @@ typedef struct {
   int32_t max_pricing_rounds;
   int32_t pricing;          /* 0 off, 1 full */
   int32_t finisher;         /* 0 off, 1 on */
+  int32_t update;           /* OR_UPDATE_JACOBI or OR_UPDATE_CLASSES */
 } or_params;
+
+#define OR_UPDATE_JACOBI 0   /* Section 5.1: all nodes from one lambda (or_gdp) */
+#define OR_UPDATE_CLASSES 1  /* colour class by colour class (or_gdp_gs) */
 
 typedef struct {
   int64_t iterations;       /* total sweeps over all phases */
