@@ -100,6 +100,19 @@ typedef struct {
  * results either way. */
 #define F2M_FLAG_ONE_SWEEP_GDP 2u
 
+/* f2m_params.flags: class-by-class GDP sweeps (a Gauss-Seidel form of the
+ * parallel update of Section 5.1; the paper does not describe it).  The graph
+ * is coloured greedily -- each node takes the smallest colour not held by a
+ * higher-priority neighbour, priority = larger degree, then larger
+ * SplitMix64(v) (the generator's first output seeded with v), then smaller v --
+ * and a sweep updates class 0, 1, ... in turn, every node of a class from the
+ * current lambda of its neighbours, in place.  With damping_shift = 1 each
+ * class update is exact block coordinate ascent and the bound never falls.
+ * A node whose new value would reach 2^29 keeps its value and the phase stops
+ * with OVERFLOW after that sweep.  The colouring is redone whenever the graph
+ * changes.  Single-instance contexts; batches ignore the flag. */
+#define F2M_FLAG_CLASS_SWEEPS 4u
+
 typedef struct {
   int64_t iterations;           /* GDP sweeps, all phases */
   int64_t phases;               /* GDP phases */
@@ -166,6 +179,13 @@ f2m_status f2m_set_lambda(f2m_ctx* ctx, const int32_t* lambda, int32_t frac_bits
  * Errors: INVALID_ARG (range, with the first offending node in
  * f2m_last_error; the previous b stays), OOM, CUDA. */
 f2m_status f2m_set_degrees(f2m_ctx* ctx, const int32_t* b);
+
+/* The colouring of the current candidate graph used by F2M_FLAG_CLASS_SWEEPS
+ * (computed now if the graph changed since the last one).
+ *   color    [n] int32, host or device, written: the class of every node.
+ *   ncolors  written: the number of classes.
+ * Either pointer may be NULL.  Errors: INVALID_ARG (NULL ctx), OOM, CUDA. */
+f2m_status f2m_get_colors(f2m_ctx* ctx, int32_t* color, int32_t* ncolors);
 
 /* Full solve from the current lambda (see the header comment).  info may be
  * NULL.  Returns F2M_OK when certified (info->certified = 2 with pricing on, 1

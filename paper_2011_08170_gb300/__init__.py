@@ -32,6 +32,7 @@ F2M_ERR_TIMEOUT = 8
 
 F2M_FLAG_STREAMING_GDP = 1
 F2M_FLAG_ONE_SWEEP_GDP = 2
+F2M_FLAG_CLASS_SWEEPS = 4
 
 # every symbol the header declares
 EXPORTS = ["f2m_default_params", "f2m_create", "f2m_destroy", "f2m_set_lambda", "f2m_solve",
@@ -41,7 +42,7 @@ EXPORTS = ["f2m_default_params", "f2m_create", "f2m_destroy", "f2m_set_lambda", 
            "f2m_batch_get_lambda", "f2m_batch_get_x", "f2m_batch_last_error", "f2m_destroy_batch",
            "f2m_knn", "f2m_knn_csr", "f2m_features", "f2m_mlp_create", "f2m_mlp_destroy",
            "f2m_mlp_get_params", "f2m_mlp_last_error", "f2m_mlp_forward", "f2m_mlp_grad",
-           "f2m_mlp_train", "f2m_warm_start", "f2m_set_degrees"]
+           "f2m_mlp_train", "f2m_warm_start", "f2m_set_degrees", "f2m_get_colors"]
 
 F2M_MLP_NPARAMS = 18817
 
@@ -101,6 +102,7 @@ def load(path: str = LIB_PATH):
     L.f2m_destroy.restype = None
     L.f2m_set_lambda.argtypes = [vp, vp, i32]
     L.f2m_set_degrees.argtypes = [vp, vp]
+    L.f2m_get_colors.argtypes = [vp, vp, C.POINTER(i32)]
     L.f2m_solve.argtypes = [vp, C.POINTER(f2m_info)]
     L.f2m_gdp.argtypes = [vp, i64, C.POINTER(i64), vp, vp, i64]
     L.f2m_price.argtypes = [vp, C.POINTER(i64), vp, i64]
@@ -146,7 +148,7 @@ def load(path: str = LIB_PATH):
         getattr(L, name).restype = C.c_int
     L.f2m_kernel_launches.argtypes = []
     L.f2m_kernel_launches.restype = C.c_int64
-    for name in ("f2m_create", "f2m_set_lambda", "f2m_set_degrees", "f2m_solve", "f2m_gdp", "f2m_price",
+    for name in ("f2m_create", "f2m_set_lambda", "f2m_set_degrees", "f2m_get_colors", "f2m_solve", "f2m_gdp", "f2m_price",
                  "f2m_add_edges", "f2m_extract", "f2m_get_lambda", "f2m_get_bound", "f2m_get_x"):
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -260,6 +262,15 @@ def f2m_set_degrees(ctx: Ctx, b) -> None:
         b = np.full(ctx.n, int(b), np.int32)
     p, keep = _ptr(None if b is None else _as(b, np.int32))
     _check(ctx, load().f2m_set_degrees(ctx.handle, p))
+
+
+def f2m_get_colors(ctx: Ctx, device=None):
+    """Colouring of the class-by-class sweeps: (ncolors, color int32 [n])."""
+    color = _out(ctx.n, np.int32, device)
+    nc = C.c_int32()
+    p, keep = _ptr(color)
+    _check(ctx, load().f2m_get_colors(ctx.handle, p, C.byref(nc)))
+    return nc.value, color
 
 
 def f2m_solve(ctx: Ctx, raise_on_error: bool = True) -> f2m_info:

@@ -155,6 +155,7 @@ extern "C" void f2m_destroy(f2m_ctx* c) {
   if (c->fin_work) finisher_work_free(c->fin_work);
   plan2_free(c->plan);
   plan_free(c->plan);
+  class_plan_free(c->classes);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   delete c;
@@ -351,6 +352,20 @@ extern "C" f2m_status f2m_set_degrees(f2m_ctx* c, const int32_t* b) {
   return F2M_OK;
 }
 
+extern "C" f2m_status f2m_get_colors(f2m_ctx* c, int32_t* color, int32_t* ncolors) {
+  if (!c) return fail(c, F2M_ERR_INVALID_ARG, "NULL context");
+  if (c->classes.version != c->plan.version) {
+    CK(c, color_classes(c->d_rp, c->d_ec, c->n, c->classes, c->st));
+    c->classes.version = c->plan.version;
+  }
+  if (color) {
+    CK(c, cudaMemcpyAsync(color, c->classes.color, sizeof(int32_t) * c->n, cudaMemcpyDefault, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+  }
+  if (ncolors) *ncolors = c->classes.ncolors;
+  return F2M_OK;
+}
+
 // lambda (device) and its fractional bits
 const int32_t* f2m::cur_lambda(f2m_ctx* c, int32_t* fb) {
   *fb = c->fb_cur;
@@ -371,11 +386,31 @@ f2m_status f2m::gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, bool 
     CK(c, dalloc(&c->d_trace_ch, trace_cap));
     c->trace_cap = trace_cap;
   }
-  CK(c, cudaMemsetAsync(c->d_gdp, 0, sizeof(GdpCtl), c->st));
-  CK(c, cudaEventRecord(c->ev0, c->st));
   long long* tb = want_trace ? c->d_trace_b2 : nullptr;
   unsigned long long* tc = want_trace ? reinterpret_cast<unsigned long long*>(c->d_trace_ch) : nullptr;
   const int64_t tcap = want_trace ? trace_cap : 0;
+  if (c->p.flags & F2M_FLAG_CLASS_SWEEPS) {
+    CK(c, cudaEventRecord(c->ev0, c->st));
+    if (c->classes.version != c->plan.version) {  // colour the graph held now
+      CK(c, color_classes(c->d_rp, c->d_ec, c->n, c->classes, c->st));
+      c->classes.version = c->plan.version;
+    }
+    CK(c, cudaMemsetAsync(c->d_gdp, 0, sizeof(GdpCtl), c->st));
+    CK(c, launch_gdp_classes(c->d_rp, c->d_ec, c->d_b, c->b_max, c->d_lam[c->cur], c->classes, c->n,
+                             F, c->p.damping_shift, max_sweeps, c->d_gdp, tb, tc, tcap,
+                             c->p.barrier_budget_cycles, c->num_sms, c->st));
+    CK(c, cudaEventRecord(c->ev1, c->st));
+    GdpCtl h{};
+    CK(c, cudaMemcpyAsync(&h, c->d_gdp, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    if (ms) *ms += elapsed_ms(c);
+    *sweeps = h.sweeps;
+    if (h.status & kGdpTimeout) return fail(c, F2M_ERR_TIMEOUT, "device-wide barrier wait exceeded its budget");
+    if (h.status & kGdpOverflow) return fail(c, F2M_ERR_OVERFLOW, "|lambda| reached 2^29");
+    return h.fixed_point ? F2M_OK : F2M_ERR_NOT_CONVERGED;
+  }
+  CK(c, cudaMemsetAsync(c->d_gdp, 0, sizeof(GdpCtl), c->st));
+  CK(c, cudaEventRecord(c->ev0, c->st));
   // the shared-memory kernels hold Eq. 10's top-3; degree requirements other
   // than 2 run on the streaming kernel
   bool two = c->plan.valid2 && !c->d_b;  // two sweeps per barrier

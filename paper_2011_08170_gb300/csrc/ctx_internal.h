@@ -66,6 +66,7 @@ struct f2m_ctx {
   unsigned long long* d_bad = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   f2m::GdpPlan plan;         // renumbering and tiles of the shared-memory GDP kernel
+  f2m::ClassPlan classes;    // colour classes of the class-by-class GDP
   // exact finisher: device scratch, pinned host mirrors, host work arrays
   int32_t* d_twin = nullptr;
   uint8_t* d_fy = nullptr;

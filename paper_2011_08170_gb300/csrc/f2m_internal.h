@@ -129,6 +129,29 @@ size_t scan_scratch_ints(int32_t m);
 cudaError_t launch_split_ec(const int2* ec, int64_t nnz, int32_t* col, int32_t* cost,
                             cudaStream_t st);
 
+// ---- class-by-class GDP (gdp_classes.cu) ------------------------------------------
+// greedy colouring of the caller-order CSR and the nodes grouped by class
+struct ClassPlan {
+  int32_t* color = nullptr;      // [n] colour of each node
+  int32_t* order = nullptr;      // [n] nodes grouped by class
+  int32_t* off = nullptr;        // [ncolors+1] class offsets into order
+  unsigned int* ctl = nullptr;   // round counters
+  int32_t cap = 0;
+  int32_t ncolors = 0;
+  int32_t rounds = 0;            // Jones-Plassmann rounds of the last colouring
+  int64_t version = -1;          // GdpPlan::version of the graph coloured
+  std::vector<int32_t> h_off;
+};
+cudaError_t color_classes(const int32_t* rp, const int2* ec, int32_t n, ClassPlan& cp,
+                          cudaStream_t st);
+void class_plan_free(ClassPlan& cp);
+// one class-by-class phase, lambda updated in place (bdeg / bmax as launch_gdp)
+cudaError_t launch_gdp_classes(const int32_t* rp, const int2* ec, const int32_t* bdeg, int32_t bmax,
+                               int32_t* lam, const ClassPlan& cp, int32_t n, int32_t F,
+                               int32_t shift, int64_t max_sweeps, GdpCtl* ctl, long long* trace_b2,
+                               unsigned long long* trace_ch, int64_t trace_cap, long long budget,
+                               int num_sms, cudaStream_t st);
+
 // ---- shared-memory tiled GDP (gdp_tiled.cu) ----------------------------------------
 // Spatial renumbering and per-CTA plan; see gdp_tiled.cu.
 struct GdpPlan {
