@@ -2,6 +2,8 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1]
     python bench.py --impl reference ...     # the CPU oracle on the same workload
+    python bench.py --update classes --shift 1   # class-by-class GDP sweeps (variant)
+    python bench.py --degrees 1:4                # fractional b-matching, b_v in 1..4 (variant)
 
 A step is one full f2m_solve from lambda = 0 on a fresh context: GDP phases,
 pricing scans over all n(n-1)/2 pairs, CSR merges, sign extraction and the
@@ -222,6 +224,12 @@ def main():
                     help="1: full scan of all pairs (the headline); 2: the scan with far tile pairs skipped")
     ap.add_argument("--batch-shape", type=int, default=-1,
                     help="batch workloads: fixed kernel shape instead of the autotuner's")
+    ap.add_argument("--update", default="jacobi", choices=["jacobi", "classes"],
+                    help="single instance: Jacobi sweeps (Section 5.1, the headline) or class-by-class sweeps")
+    ap.add_argument("--shift", type=int, default=2, help="damping shift of the GDP step")
+    ap.add_argument("--degrees", default=None,
+                    help="single instance: degree requirements b_v drawn uniformly from LO:HI (capped at "
+                         "deg(v) - 1), the fractional b-matching LP instead of F2M")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     rank, world, local = dist_env()
@@ -249,14 +257,29 @@ def main():
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
+    # variants: class-by-class sweeps, degree requirements
+    flags = f2m.F2M_FLAG_CLASS_SWEEPS if args.update == "classes" else 0
+    b = None
+    if args.degrees:
+        lo, hi = (int(t) for t in args.degrees.split(":"))
+        key = I.stream_key(w["seed"] + rank, 91)
+        draw = (I.draws(key, 0, n) % np.uint64(hi - lo + 1)).astype(np.int64) + lo
+        b = np.minimum(draw, np.diff(d["row_ptr"]) - 1).astype(np.int32)
+    variant = args.update != "jacobi" or b is not None or args.shift != 2
+
+    def make_ctx(xy, rp, col):
+        c = f2m.f2m_create(xy, rp, col, params=params, stream=stream)
+        if b is not None:
+            f2m.f2m_set_degrees(c, b)
+        return c
+
     # warm-up solves (also load the module, JIT nothing)
-    params = f2m.f2m_default_params(pricing=args.pricing)
+    params = f2m.f2m_default_params(pricing=args.pricing, flags=flags, damping_shift=args.shift)
     for _ in range(args.warmup):
-        ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], params=params, stream=stream)
+        ctx = make_ctx(d["xy"], d["row_ptr"], d["col"])
         f2m.f2m_solve(ctx)
         f2m.f2m_destroy(ctx)
-    ctxs = [f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], params=params, stream=stream)
-            for _ in range(args.steps)]
+    ctxs = [make_ctx(d["xy"], d["row_ptr"], d["col"]) for _ in range(args.steps)]
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -302,7 +325,7 @@ def main():
         flush.fill_(i & 0xFF)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx = f2m.f2m_create(xy_h, rp_h, col_h, params=params, stream=stream)
+        ctx = make_ctx(xy_h, rp_h, col_h)
         info = f2m.f2m_solve(ctx)
         rp_o, col_o, x2_o, cost_o = f2m.f2m_get_x(ctx)
         lam_o, _ = f2m.f2m_get_lambda(ctx)
@@ -329,10 +352,12 @@ def main():
     alu_peak = num_sms * 128 * sm_mhz * 1e6 / 1e12  # Tops/s at the sampled clock
     pr_tops = pr_pairs * PRICING_OPS_PER_PAIR / (ms_pr * 1e-3) / 1e12 if ms_pr > 0 else 0.0
     traffic = load_traffic(args.workload)
+    gdp_kernel = ("gdp_classes_kernel" if args.update == "classes" else
+                  "gdp_persistent_kernel" if b is not None else "gdp_tiled2_kernel")
     if ms_gdp >= ms_pr:
-        roofline = {"kernel": "gdp_tiled2_kernel", "bound": "hbm", "achieved": gdp_gbs,
+        roofline = {"kernel": gdp_kernel, "bound": "hbm", "achieved": gdp_gbs,
                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gdp_gbs / peaks["hbm_gbs"],
-                    "traffic": traffic.get("gdp_tiled2_kernel"),
+                    "traffic": traffic.get(gdp_kernel),
                     "note": "algorithmic bytes of the sweep over its time; the working set is shared-memory "
                             "and L2 resident, so this is an effective rate (DRAM sees the CSR once per phase)"}
     else:
@@ -352,6 +377,9 @@ def main():
             "config": {"workload": workload_name(w) + ("" if args.pricing == 1 else
                                                        "; pricing skips tile pairs too far apart to hold z < 0"),
                        "pricing": "full" if args.pricing == 1 else "culled", "n": n, "k": w["k"], "nnz": nnz0,
+                       "update": args.update, "damping_shift": args.shift,
+                       "degrees": ("2 (F2M)" if b is None else
+                                   f"b_v uniform in {args.degrees.replace(':', '..')}, capped at deg(v)-1"),
                        "l2": "flushed before every timed step (256 MB device write)",
                        "parallelism": f"replicas x{world}"},
             "breakdown_ms": {k: statistics.median(i[k] for i in infos)
@@ -365,7 +393,7 @@ def main():
             "e2e": {"value": e2e, "unit": "ms", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "roofline": roofline, "clocks": clk, "gpu_launches": int(launches)}
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and not variant:
         est, sample = cpu_oracle_estimate(d, {"iterations": inf0["iterations"],
                                               "pricing_rounds": inf0["pricing_rounds"],
                                               "ms_finish": line["breakdown_ms"]["ms_finish"]})
