@@ -292,7 +292,22 @@ int64_t or_extract(int32_t n, const int32_t* row_ptr, const int32_t* col,
  * the position of v when points are ordered by Morton code (bit b of x at bit
  * 2b, bit b of y at bit 2b+1), ties by node id -- so that successive paths are
  * searched in nearby parts of the plane.  (The paper gives no finisher; this
- * order is a stated choice.) */
+ * order is a stated choice.)
+ *
+ * Two phases, so that the first can run block by block in parallel with a
+ * result that does not depend on the schedule.  Block k holds the nodes of rank
+ * in [k*OR_FIN_BLOCK, (k+1)*OR_FIN_BLOCK), both copies.
+ *   Phase 1, for each block in turn: its sources in key order, each searched as
+ *   above except that (a) a node outside the block is never settled: if a heap
+ *   item of an outside node comes to the top, or the heap empties, the search
+ *   is dropped with nothing changed and the next source of the block is taken;
+ *   (b) reduced costs of arcs into outside nodes use those nodes' potentials as
+ *   they were when phase 1 began.  Potentials only grow, so every residual
+ *   reduced cost stays >= 0; arcs and potentials a block reads are changed by
+ *   that block alone, so the blocks do not depend on one another's progress.
+ *   Phase 2: the plain search over all nodes in key order for what is left. */
+
+#define OR_FIN_BLOCK 2048
 
 typedef struct { int64_t d; int32_t key; int32_t v; } or_hitem;
 
@@ -405,66 +420,90 @@ int or_finisher(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int3
     ex[n + u] = in - bu;   /* R_u: inflow minus demand b_u */
   }
 
+  int64_t* pi0 = (int64_t*)malloc(sizeof(int64_t) * (size_t)N); /* potentials at phase 1's start */
+  memcpy(pi0, pi, sizeof(int64_t) * (size_t)N);
+  int32_t* rank = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  for (int32_t v = 0; v < n; ++v) rank[v] = key[v] / 2;
+  const int32_t nblocks = (n + OR_FIN_BLOCK - 1) / OR_FIN_BLOCK;
+
   int64_t stamp = 0;
-  int32_t next = 0; /* next key to look at for a source */
-  for (;;) {
-    while (next < N && ex[by_key[next]] <= 0) ++next;
-    if (next >= N) break;
-    int32_t src = by_key[next];
-    ++stamp;
-    int64_t hs = 0, ns = 0;
-    int32_t t = -1;
-    dist[src] = 0; seen[src] = stamp; par[src] = -1;
-    or_hpush(heap, &hs, (or_hitem){0, key[src], src});
-    while (hs > 0) {
-      or_hitem it = or_hpop(heap, &hs);
-      int32_t i = it.v;
-      if (done[i] == stamp || it.d != dist[i]) continue;
-      done[i] = stamp;
-      if (ex[i] < 0) { t = i; break; }
-      settled[ns++] = i;
-      if (i < n) { /* L_i: forward arcs with no flow */
-        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-          if (y[e]) continue;
-          int32_t j = n + col[e];
-          int64_t rc = ((int64_t)cost[e] << F) - pi[i] + pi[j];
-          int64_t nd = dist[i] + rc;
-          if (done[j] != stamp && (seen[j] != stamp || nd < dist[j])) {
-            seen[j] = stamp; dist[j] = nd; par[j] = e;
-            or_hpush(heap, &hs, (or_hitem){nd, key[j], j});
+  for (int32_t phase = 1; phase <= 2 && status == OR_OK; ++phase) {
+    for (int32_t blk = 0; blk < (phase == 1 ? nblocks : 1) && status == OR_OK; ++blk) {
+      /* phase 1: keys of block blk; phase 2: every key */
+      const int32_t k0 = phase == 1 ? 2 * blk * OR_FIN_BLOCK : 0;
+      int32_t k1 = phase == 1 ? 2 * (blk + 1) * OR_FIN_BLOCK : N;
+      if (k1 > N) k1 = N;
+      for (int32_t next = k0; next < k1 && status == OR_OK; ++next) {
+        const int32_t src = by_key[next];
+        while (ex[src] > 0) {
+          ++stamp;
+          int64_t hs = 0, ns = 0;
+          int32_t t = -1;
+          dist[src] = 0; seen[src] = stamp; par[src] = -1;
+          or_hpush(heap, &hs, (or_hitem){0, key[src], src});
+          while (hs > 0) {
+            or_hitem it = or_hpop(heap, &hs);
+            int32_t i = it.v;
+            if (phase == 1 && rank[i < n ? i : i - n] / OR_FIN_BLOCK != blk) break; /* dropped */
+            if (done[i] == stamp || it.d != dist[i]) continue;
+            done[i] = stamp;
+            if (ex[i] < 0) { t = i; break; }
+            settled[ns++] = i;
+            if (i < n) { /* L_i: forward arcs with no flow */
+              for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                if (y[e]) continue;
+                int32_t j = n + col[e];
+                int32_t out = phase == 1 && rank[col[e]] / OR_FIN_BLOCK != blk;
+                int64_t rc = ((int64_t)cost[e] << F) - pi[i] + (out ? pi0[j] : pi[j]);
+                int64_t nd = dist[i] + rc;
+                if (out) { or_hpush(heap, &hs, (or_hitem){nd, key[j], j}); continue; }
+                if (done[j] != stamp && (seen[j] != stamp || nd < dist[j])) {
+                  seen[j] = stamp; dist[j] = nd; par[j] = e;
+                  or_hpush(heap, &hs, (or_hitem){nd, key[j], j});
+                }
+              }
+            } else { /* R_v: reverse arcs of saturated entries (u -> v) */
+              int32_t v = i - n;
+              for (int32_t f = row_ptr[v]; f < row_ptr[v + 1]; ++f) {
+                int32_t e = rev[f]; /* entry (col[f] -> v) */
+                if (!y[e]) continue;
+                int32_t j = col[f];
+                int32_t out = phase == 1 && rank[j] / OR_FIN_BLOCK != blk;
+                int64_t rc = -((int64_t)cost[e] << F) - pi[i] + (out ? pi0[j] : pi[j]);
+                int64_t nd = dist[i] + rc;
+                if (out) { or_hpush(heap, &hs, (or_hitem){nd, key[j], j}); continue; }
+                if (done[j] != stamp && (seen[j] != stamp || nd < dist[j])) {
+                  seen[j] = stamp; dist[j] = nd; par[j] = e;
+                  or_hpush(heap, &hs, (or_hitem){nd, key[j], j});
+                }
+              }
+            }
           }
-        }
-      } else { /* R_v: reverse arcs of saturated entries (u -> v) */
-        int32_t v = i - n;
-        for (int32_t f = row_ptr[v]; f < row_ptr[v + 1]; ++f) {
-          int32_t e = rev[f]; /* entry (col[f] -> v) */
-          if (!y[e]) continue;
-          int32_t j = col[f];
-          int64_t rc = -((int64_t)cost[e] << F) - pi[i] + pi[j];
-          int64_t nd = dist[i] + rc;
-          if (done[j] != stamp && (seen[j] != stamp || nd < dist[j])) {
-            seen[j] = stamp; dist[j] = nd; par[j] = e;
-            or_hpush(heap, &hs, (or_hitem){nd, key[j], j});
+          if (t < 0) {
+            if (phase == 1) break;  /* dropped or nothing reachable: left to phase 2 */
+            status = OR_INFEASIBLE;
+            break;
+          }
+          /* push one unit along the path, walking back from t to src */
+          for (int32_t j = t; j != src;) {
+            int32_t e = par[j];
+            if (j >= n) { y[e] = 1; j = own[e]; }      /* reached R_v by L_u -> R_v, e = (u -> v) */
+            else { y[e] = 0; j = n + col[e]; }         /* reached L_u by R_v -> L_u, e = (u -> v) */
+          }
+          ex[src] -= 1;
+          ex[t] += 1;
+          ++aug;
+          int64_t dt = dist[t];
+          for (int64_t k = 0; k < ns; ++k) {
+            int32_t i = settled[k];
+            pi[i] += dt - dist[i];
           }
         }
       }
     }
-    if (t < 0) { status = OR_INFEASIBLE; break; }
-    /* push one unit along the path, walking back from t to src */
-    for (int32_t j = t; j != src;) {
-      int32_t e = par[j];
-      if (j >= n) { y[e] = 1; j = own[e]; }      /* reached R_v by L_u -> R_v, e = (u -> v) */
-      else { y[e] = 0; j = n + col[e]; }         /* reached L_u by R_v -> L_u, e = (u -> v) */
-    }
-    ex[src] -= 1;
-    ex[t] += 1;
-    ++aug;
-    int64_t dt = dist[t];
-    for (int64_t k = 0; k < ns; ++k) {
-      int32_t i = settled[k];
-      pi[i] += dt - dist[i];
-    }
   }
+  free(pi0);
+  free(rank);
 
   if (status == OR_OK) {
     for (int32_t u = 0; u < n; ++u)

@@ -264,6 +264,21 @@ def test_finisher_reaches_candidate_optimum(oracle_lib):
     assert fst0 == 0 and oracle_lib.bound2(rp, col, cost, lam20, 9) == b2 and aug0 > aug
 
 
+@pytest.mark.parametrize("kind,n,seed", [("uniform", 9000, 3), ("mixture", 7000, 4)])
+def test_blocked_finisher_reaches_candidate_optimum(oracle_lib, kind, n, seed):
+    # several finisher blocks (2048 nodes each): phase 1 per block, phase 2 for the rest
+    inst = I.make_instance(kind, n, seed, 10)
+    xy, rp, col = inst["xy"], inst["row_ptr"], inst["col"]
+    cost = oracle_lib.cost_table(xy, rp, col)
+    st, lam, it, _, _ = oracle_lib.gdp(rp, col, cost, np.zeros(n, np.int32), 8, 2, 100000)
+    bad, _ = oracle_lib.extract(rp, col, cost, lam, 8)
+    fst, x2, lam2, aug = oracle_lib.finisher(xy, rp, col, cost, lam, 8)
+    assert fst == 0 and aug >= bad // 2 > 0
+    b2 = oracle_lib.bound2(rp, col, cost, lam2, 9)
+    assert oracle_lib.certify(xy, rp, col, x2, lam2, 9, b2, full_scan=False) == 0
+    assert abs(b2 / 1024.0 - highs_opt(xy, rp, col)) < 1e-6 * b2 / 1024.0
+
+
 def test_finisher_infeasible_graph(oracle_lib):
     # K_{3,5}: the five right nodes need 10 units of x, the three left nodes supply 6
     xy = np.array([[0, 0], [0, 10], [0, 20]] + [[100, 7 * i] for i in range(5)], dtype=np.int32)
