@@ -381,7 +381,7 @@ int or_finisher(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int3
   int32_t* rev = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
   int32_t* own = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1)); /* row of e */
   uint8_t* y = (uint8_t*)calloc((size_t)(nnz > 0 ? nnz : 1), 1);
-  int64_t* pi = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
+  int64_t* pi = (int64_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(int64_t));
   int64_t* ex = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
   int64_t* dist = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
   int32_t* par = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);   /* entry used to reach */

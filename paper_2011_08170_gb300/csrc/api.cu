@@ -37,12 +37,11 @@ extern "C" int64_t f2m_kernel_launches(void) { return g_kernel_launches.load(); 
 static void free_finisher_buffers(f2m_ctx* c) {
   if (c->d_twin) cudaFree(c->d_twin);
   if (c->d_fy) cudaFree(c->d_fy);
-  if (c->d_fx) cudaFree(c->d_fx);
-  void* hp[] = {c->h_irp, c->h_iec, c->h_twin, c->h_y, c->h_x, c->h_exl, c->h_lam, c->h_lam2};
+  void* hp[] = {c->h_irp, c->h_iec, c->h_twin, c->h_y, c->h_exl, c->h_lam, c->h_lam2};
   for (void* q : hp)
     if (q) cudaFreeHost(q);
-  c->d_twin = nullptr; c->d_fy = nullptr; c->d_fx = nullptr;
-  c->h_irp = nullptr; c->h_iec = nullptr; c->h_twin = nullptr; c->h_y = nullptr; c->h_x = nullptr;
+  c->d_twin = nullptr; c->d_fy = nullptr;
+  c->h_irp = nullptr; c->h_iec = nullptr; c->h_twin = nullptr; c->h_y = nullptr;
   c->h_exl = nullptr; c->h_lam = nullptr; c->h_lam2 = nullptr;
   c->fin_cap = 0;
   c->fin_version = -1;
@@ -54,22 +53,18 @@ static cudaError_t alloc_finisher_buffers(f2m_ctx* c, int64_t cap) {
   const bool first = c->h_irp == nullptr;
   if (c->d_twin) cudaFree(c->d_twin);
   if (c->d_fy) cudaFree(c->d_fy);
-  if (c->d_fx) cudaFree(c->d_fx);
   if (c->h_iec) cudaFreeHost(c->h_iec);
   if (c->h_twin) cudaFreeHost(c->h_twin);
   if (c->h_y) cudaFreeHost(c->h_y);
-  if (c->h_x) cudaFreeHost(c->h_x);
-  c->d_twin = nullptr; c->d_fy = nullptr; c->d_fx = nullptr;
-  c->h_iec = nullptr; c->h_twin = nullptr; c->h_y = nullptr; c->h_x = nullptr;
+  c->d_twin = nullptr; c->d_fy = nullptr;
+  c->h_iec = nullptr; c->h_twin = nullptr; c->h_y = nullptr;
   c->fin_cap = 0;
   c->fin_version = -1;
   cudaError_t e = cudaMalloc((void**)&c->d_twin, sizeof(int32_t) * cap);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_fy, cap);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_fx, cap);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_iec, sizeof(int2) * cap);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_twin, sizeof(int32_t) * cap);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_y, cap);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_x, cap);
   if (e == cudaSuccess && first) {
     e = cudaMallocHost((void**)&c->h_irp, sizeof(int32_t) * (n + 1));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_exl, sizeof(int32_t) * n);
@@ -744,8 +739,10 @@ f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug) {
   GdpPlan& P = c->plan;
   if (c->fin_cap < c->nnz) CK(c, alloc_finisher_buffers(c, c->ec_cap));
   if (!c->fin_work) c->fin_work = finisher_work_new();
-  if (c->fin_version != P.version) {  // the graph changed: mirror it again
-    CK(c, fin_build_twin(P, c->d_twin, c->st));
+  const bool mirror = c->fin_version != P.version;
+  if (mirror) {  // the graph changed: mirror it again
+    CK(c, cudaMemsetAsync(c->d_bad, 0, sizeof(unsigned long long), c->st));
+    CK(c, fin_build_twin(P, c->d_twin, c->d_bad, c->st));
     CK(c, cudaMemcpyAsync(c->h_irp, P.irp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, c->st));
     CK(c, cudaMemcpyAsync(c->h_iec, P.iec, sizeof(int2) * c->nnz, cudaMemcpyDeviceToHost, c->st));
     CK(c, cudaMemcpyAsync(c->h_twin, c->d_twin, sizeof(int32_t) * c->nnz, cudaMemcpyDeviceToHost, c->st));
@@ -757,28 +754,29 @@ f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug) {
   if (c->d_fin_include)
     CK(c, launch_batch_mask_surplus(d_exl, c->d_seg_off, (int32_t)c->seg_off.size() - 1,
                                     c->d_fin_include, n, c->st));
+  unsigned long long missing = 0;
   CK(c, cudaMemcpyAsync(c->h_y, c->d_fy, c->nnz, cudaMemcpyDeviceToHost, c->st));
   CK(c, cudaMemcpyAsync(c->h_exl, d_exl, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->st));
   CK(c, cudaMemcpyAsync(c->h_lam, d_lam_int, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->st));
+  if (mirror) CK(c, cudaMemcpyAsync(&missing, c->d_bad, sizeof(missing), cudaMemcpyDeviceToHost, c->st));
   CK(c, cudaStreamSynchronize(c->st));
-  if (c->fin_version != P.version) {
-    for (int64_t e = 0; e < c->nnz; ++e)
-      if (c->h_twin[e] < 0) return fail(c, F2M_ERR_INVALID_ARG, "finisher: CSR not symmetric");
+  if (mirror) {
+    if (missing) return fail(c, F2M_ERR_INVALID_ARG, "finisher: CSR not symmetric");
     c->fin_version = P.version;
   }
   static const int32_t hw = (int32_t)std::thread::hardware_concurrency();
   const int32_t nseg = (int32_t)c->seg_off.size() - 1;
   const int r = host_finisher(n, c->h_irp, c->h_iec, c->h_twin, c->h_y, c->h_exl, c->h_lam, F,
-                              c->h_x, c->h_lam2, c->seg_off.data(), nseg, hw > 1 ? hw : 1, aug,
+                              c->h_lam2, c->seg_off.data(), nseg, hw > 1 ? hw : 1, aug,
                               c->fin_work);
   if (r == 7)
     return fail(c, F2M_ERR_INFEASIBLE, c->d_b ? "no fractional b-matching exists on the candidate graph"
                                               : "no fractional 2-matching exists on the candidate graph");
   if (r == 5) return fail(c, F2M_ERR_OVERFLOW, "finisher lambda out of range");
   if (r != 0) return fail(c, F2M_ERR_INVALID_ARG, "finisher failed");
-  CK(c, cudaMemcpyAsync(c->d_fx, c->h_x, c->nnz, cudaMemcpyHostToDevice, c->st));
+  CK(c, cudaMemcpyAsync(c->d_fy, c->h_y, c->nnz, cudaMemcpyHostToDevice, c->st));
   CK(c, cudaMemcpyAsync(d_lam2_int, c->h_lam2, sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->st));
-  CK(c, fin_scatter(P, c->d_rp, c->d_fx, d_lam2_int, c->d_x2, c->d_lam2, c->d_seg_off,
+  CK(c, fin_scatter(P, c->d_rp, c->d_fy, c->d_twin, d_lam2_int, c->d_x2, c->d_lam2, c->d_seg_off,
                     (int32_t)c->seg_off.size() - 1, c->d_fin_include, c->st));
   CK(c, cudaStreamSynchronize(c->st));
   c->fb_cur = F + 1;

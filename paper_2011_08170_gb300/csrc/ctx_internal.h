@@ -70,14 +70,12 @@ struct f2m_ctx {
   // exact finisher: device scratch, pinned host mirrors, host work arrays
   int32_t* d_twin = nullptr;
   uint8_t* d_fy = nullptr;
-  uint8_t* d_fx = nullptr;
   int64_t fin_cap = 0;          // entries the finisher buffers hold
   int64_t fin_version = -1;     // plan version mirrored on the host
   int32_t* h_irp = nullptr;
   int2* h_iec = nullptr;
   int32_t* h_twin = nullptr;
   uint8_t* h_y = nullptr;
-  uint8_t* h_x = nullptr;
   int32_t* h_exl = nullptr;
   int32_t* h_lam = nullptr;
   int32_t* h_lam2 = nullptr;

@@ -235,15 +235,19 @@ cudaError_t launch_gdp_tiled2(GdpPlan& p, const int32_t* lam_in, int32_t shift, 
 cudaError_t plan_scatter_lambda(const GdpPlan& p, int which, int32_t* lam_out, cudaStream_t st);
 
 // ---- exact finisher (finisher_prep.cu on the device, finisher.cpp on the host) ---
-cudaError_t fin_build_twin(const GdpPlan& p, int32_t* twin, cudaStream_t st);
+// twin[e] for every internal entry; *missing (zeroed by the caller) counts
+// entries without a reverse entry
+cudaError_t fin_build_twin(const GdpPlan& p, int32_t* twin, unsigned long long* missing, cudaStream_t st);
 // bdeg_caller: degree requirements in caller order (NULL: 2)
 cudaError_t fin_prepare(const GdpPlan& p, const int32_t* lam_caller, const int32_t* bdeg_caller,
                         int32_t F, int32_t* lam_int, uint8_t* y, int32_t* exl, cudaStream_t st);
-// include (device, per segment; NULL = all): x of excluded segments is kept
-cudaError_t fin_scatter(const GdpPlan& p, const int32_t* rp, const uint8_t* x_int,
-                        const int32_t* lam2_int, uint8_t* x_out, int32_t* lam2_out,
-                        const int32_t* seg_off, int32_t nseg, const uint8_t* include,
-                        cudaStream_t st);
+// x (half units, caller order) = y[e] + y[twin[e]] of the final flow; lambda
+// at F+1 bits to caller order.  include (device, per segment; NULL = all): x
+// of excluded segments is kept
+cudaError_t fin_scatter(const GdpPlan& p, const int32_t* rp, const uint8_t* y_int,
+                        const int32_t* twin, const int32_t* lam2_int, uint8_t* x_out,
+                        int32_t* lam2_out, const int32_t* seg_off, int32_t nseg,
+                        const uint8_t* include, cudaStream_t st);
 // ---- batched solver (batch_kernels.cu) --------------------------------------------
 // Parameters of one launch of a batched GDP kernel, read from device memory so
 // that a captured launch can be replayed with new values.
@@ -284,11 +288,12 @@ FinisherWork* finisher_work_new();
 void finisher_work_reserve(FinisherWork* w, int32_t n);  // host work arrays for n nodes
 void finisher_work_free(FinisherWork* w);
 // Min-cost flow on the bipartite double cover, internal node order; see
-// finisher.cpp.  y is the initial flow (updated), exl the left surpluses.
-// Segments [seg_off[s], seg_off[s+1]) are independent and go to up to
-// `threads` host threads.  Returns 0 ok, 7 infeasible, 5 overflow.
+// finisher.cpp.  y is the initial flow (updated to the optimal one), exl the
+// left surpluses, lam2 receives pi(L) - pi(R) (F+1 bits).  Blocks and segments
+// [seg_off[s], seg_off[s+1]) go to up to `threads` host threads.  Returns 0 ok,
+// 7 infeasible, 5 overflow.
 int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t* twin, uint8_t* y,
-                  const int32_t* exl, const int32_t* lam, int32_t F, uint8_t* x2, int32_t* lam2,
+                  const int32_t* exl, const int32_t* lam, int32_t F, int32_t* lam2,
                   const int32_t* seg_off, int32_t nseg, int32_t threads, int64_t* augmentations,
                   FinisherWork* w);
 

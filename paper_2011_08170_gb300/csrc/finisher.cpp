@@ -25,6 +25,17 @@
 // copy, so successive searches stay in nearby memory.  The rules are fixed,
 // so the result is deterministic.
 //
+// Two phases.  Phase 1 splits every segment into blocks of kFinBlock nodes
+// (consecutive internal ids, both copies) and runs the blocks on worker
+// threads: a block's sources in key order, each search restricted to the
+// block -- when a heap item of an outside node comes to the top, or the heap
+// runs dry, the search is dropped with nothing changed and the block moves to
+// its next source -- with arcs into outside nodes priced at the potentials of
+// phase 1's start.  Potentials only grow, so every residual reduced cost stays
+// non-negative; the arcs and potentials a block reads are written by that
+// block alone, so the result does not depend on the schedule.  Phase 2 runs
+// the plain search per segment for what phase 1 left.
+//
 // Layout: the graph arrives in the renumbered node order prepared on the
 // device (finisher_prep.cu): internal node i is the i-th point in (Morton
 // code, caller id) order, every row keeps the caller's column order.  Node
@@ -79,6 +90,8 @@ struct Searcher {
   }
 };
 
+constexpr int32_t kFinBlock = 2048;  // nodes per phase-1 block
+
 struct FinisherWork {
   std::vector<int64_t> pi, dist;
   std::vector<int32_t> excess, via, pred;
@@ -105,11 +118,15 @@ void finisher_work_reserve(FinisherWork* w, int32_t n) {
 
 namespace {
 
-// Successive shortest paths for the sources of one segment [lo, hi) (internal
-// ids), in key order.  Paths never leave the segment (no arc does).
-int solve_segment(int32_t n, int32_t lo, int32_t hi, const int32_t* irp, const int2* iec,
-                  const int32_t* twin, uint8_t* y, int32_t F, FinisherWork* w, Searcher& sr,
-                  int64_t* pushes_out) {
+// Successive shortest paths for the sources of nodes [lo, hi) (internal ids),
+// in key order.  lam0 == nullptr: [lo, hi) is a whole segment, which no arc
+// leaves (phase 2).  Otherwise [lo, hi) is a phase-1 block: outside nodes are
+// priced with their potentials at phase 1's start (lam0 for a left copy,
+// -lam0 for a right one) and never settled, and a search that would settle
+// one (or finds nothing) is dropped.
+int solve_range(int32_t n, int32_t lo, int32_t hi, const int32_t* lam0, const int32_t* irp,
+                const int2* iec, const int32_t* twin, uint8_t* y, int32_t F, FinisherWork* w,
+                Searcher& sr, int64_t* pushes_out) {
   int64_t* pi = w->pi.data();
   int64_t* dist = w->dist.data();
   int32_t* excess = w->excess.data();
@@ -118,6 +135,11 @@ int solve_segment(int32_t n, int32_t lo, int32_t hi, const int32_t* irp, const i
   uint32_t* reached = w->reached.data();
   uint32_t* closed = w->closed.data();
   auto key_of = [&](int32_t node) { return node < n ? 2 * node : 2 * (node - n) + 1; };
+  auto outside = [&](int32_t node) {
+    const int32_t i = node < n ? node : node - n;
+    return i < lo || i >= hi;
+  };
+  auto pi0 = [&](int32_t node) { return node < n ? (int64_t)lam0[node] : -(int64_t)lam0[node - n]; };
   int64_t pushes = 0;
   for (int32_t i = lo; i < hi; ++i) {
     for (int side = 0; side < 2; ++side) {
@@ -134,6 +156,7 @@ int solve_segment(int32_t n, int32_t lo, int32_t hi, const int32_t* irp, const i
         while (!sr.heap.empty()) {
           const Searcher::Item top = sr.pop();
           const int32_t v = top.node;
+          if (lam0 && outside(v)) break;  // dropped
           if (closed[v] == round || top.d != dist[v]) continue;
           closed[v] = round;
           if (excess[v] < 0) { t = v; break; }
@@ -143,6 +166,10 @@ int solve_segment(int32_t n, int32_t lo, int32_t hi, const int32_t* irp, const i
             for (int32_t e = irp[v]; e < irp[v + 1]; ++e) {
               if (y[e]) continue;
               const int32_t j = n + iec[e].x;
+              if (lam0 && outside(j)) {
+                sr.push({dist[v] + ((int64_t)iec[e].y << F) - pi[v] + pi0(j), key_of(j), j});
+                continue;
+              }
               const int64_t d = dist[v] + ((int64_t)iec[e].y << F) - pi[v] + pi[j];
               if (closed[j] != round && (reached[j] != round || d < dist[j])) {
                 reached[j] = round; dist[j] = d; via[j] = e; pred[j] = v;
@@ -156,6 +183,10 @@ int solve_segment(int32_t n, int32_t lo, int32_t hi, const int32_t* irp, const i
               const int32_t a = twin[f];
               if (!y[a]) continue;
               const int32_t j = iec[f].x;  // L_x, the tail of arc a
+              if (lam0 && outside(j)) {
+                sr.push({dist[v] - ((int64_t)iec[f].y << F) - pi[v] + pi0(j), key_of(j), j});
+                continue;
+              }
               const int64_t d = dist[v] - ((int64_t)iec[f].y << F) - pi[v] + pi[j];
               if (closed[j] != round && (reached[j] != round || d < dist[j])) {
                 reached[j] = round; dist[j] = d; via[j] = a; pred[j] = v;
@@ -164,7 +195,10 @@ int solve_segment(int32_t n, int32_t lo, int32_t hi, const int32_t* irp, const i
             }
           }
         }
-        if (t < 0) return 7;
+        if (t < 0) {
+          if (lam0) break;  // dropped or nothing found: left to phase 2
+          return 7;
+        }
         for (int32_t j = t; j != s; j = pred[j]) y[via[j]] = (uint8_t)(j >= n);  // push one unit
         excess[s] -= 1;
         excess[t] += 1;
@@ -178,39 +212,21 @@ int solve_segment(int32_t n, int32_t lo, int32_t hi, const int32_t* irp, const i
   return 0;
 }
 
-}  // namespace
-
-int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t* twin, uint8_t* y,
-                  const int32_t* exl, const int32_t* lam, int32_t F, uint8_t* x2, int32_t* lam2,
-                  const int32_t* seg_off, int32_t nseg, int32_t threads, int64_t* augmentations,
-                  FinisherWork* w) {
-  finisher_work_reserve(w, n);
-  if (w->stamp.load() > (1u << 31)) {  // far from wrapping: clear the stamps and restart
-    std::fill(w->reached.begin(), w->reached.end(), 0u);
-    std::fill(w->closed.begin(), w->closed.end(), 0u);
-    w->stamp.store(0);
-  }
-  int64_t* pi = w->pi.data();
-  int32_t* excess = w->excess.data();
-  for (int32_t i = 0; i < n; ++i) {
-    pi[i] = lam[i];
-    pi[n + i] = -(int64_t)lam[i];
-    excess[i] = exl[i];       // L_i: supply b_i minus outflow
-    excess[n + i] = -exl[i];  // R_i: inflow minus demand b_i (z is symmetric)
-  }
-  // segments are independent: whole segments go to workers
+// runs items 0 .. count-1 on up to `threads` workers (dynamic hand-out)
+template <typename Fn>
+int run_items(int32_t count, int32_t threads, FinisherWork* w, std::vector<int64_t>& pushes, Fn fn) {
   int32_t nw = threads < 1 ? 1 : threads;
-  if (nw > nseg) nw = nseg;
+  if (nw > count) nw = count;
+  if (nw < 1) return 0;
   if ((int32_t)w->workers.size() < nw) w->workers.resize(nw);
+  if ((int32_t)pushes.size() < nw) pushes.resize(nw, 0);
   std::atomic<int32_t> next{0};
   std::atomic<int> status{0};
-  std::vector<int64_t> pushes(nw, 0);
   auto run = [&](int32_t k) {
     for (;;) {
-      const int32_t sgi = next.fetch_add(1);
-      if (sgi >= nseg || status.load() != 0) break;
-      const int r = solve_segment(n, seg_off[sgi], seg_off[sgi + 1], irp, iec, twin, y, F, w,
-                                  w->workers[k], &pushes[k]);
+      const int32_t item = next.fetch_add(1);
+      if (item >= count || status.load() != 0) break;
+      const int r = fn(item, w->workers[k], &pushes[k]);
       if (r != 0) status.store(r);
     }
   };
@@ -222,19 +238,56 @@ int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t*
     run(0);
     for (std::thread& th : pool) th.join();
   }
+  return status.load();
+}
+
+}  // namespace
+
+int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t* twin, uint8_t* y,
+                  const int32_t* exl, const int32_t* lam, int32_t F, int32_t* lam2,
+                  const int32_t* seg_off, int32_t nseg, int32_t threads, int64_t* augmentations,
+                  FinisherWork* w) {
+  finisher_work_reserve(w, n);
+  if (w->stamp.load() > (1u << 31)) {  // far from wrapping: clear the stamps and restart
+    std::fill(w->reached.begin(), w->reached.end(), 0u);
+    std::fill(w->closed.begin(), w->closed.end(), 0u);
+    w->stamp.store(0);
+  }
+  int64_t* pi = w->pi.data();
+  int32_t* excess = w->excess.data();
+  // phase 1: blocks of every segment, each first setting its own nodes'
+  // potentials (lam, -lam) and surpluses; phase 2: whole segments
+  std::vector<int2> blocks;
+  for (int32_t sg = 0; sg < nseg; ++sg)
+    for (int32_t b0 = seg_off[sg]; b0 < seg_off[sg + 1]; b0 += kFinBlock)
+      blocks.push_back(make_int2(b0, std::min(b0 + kFinBlock, seg_off[sg + 1])));
+  std::vector<int64_t> pushes;
+  int r = run_items((int32_t)blocks.size(), threads, w, pushes,
+                    [&](int32_t k, Searcher& sr, int64_t* p) {
+                      for (int32_t i = blocks[k].x; i < blocks[k].y; ++i) {
+                        pi[i] = lam[i];
+                        pi[n + i] = -(int64_t)lam[i];
+                        excess[i] = exl[i];       // L_i: supply b_i minus outflow
+                        excess[n + i] = -exl[i];  // R_i: inflow minus demand b_i (z is symmetric)
+                      }
+                      return solve_range(n, blocks[k].x, blocks[k].y, lam, irp, iec, twin, y, F, w, sr, p);
+                    });
+  if (r == 0)
+    r = run_items(nseg, threads, w, pushes, [&](int32_t k, Searcher& sr, int64_t* p) {
+      const int q = solve_range(n, seg_off[k], seg_off[k + 1], nullptr, irp, iec, twin, y, F, w, sr, p);
+      if (q != 0) return q;
+      int st = 0;
+      for (int32_t i = seg_off[k]; i < seg_off[k + 1]; ++i) {
+        const int64_t l2 = pi[i] - pi[n + i];
+        if (l2 >= 2 * kLamLimit || l2 <= -2 * kLamLimit) st = 5;
+        lam2[i] = (int32_t)l2;
+      }
+      return st;
+    });
   int64_t total = 0;
   for (int64_t p : pushes) total += p;
   *augmentations = total;
-  if (status.load() != 0) return status.load();
-  int st = 0;
-  const int64_t nnz = irp[n];
-  for (int64_t e = 0; e < nnz; ++e) x2[e] = (uint8_t)(y[e] + y[twin[e]]);
-  for (int32_t i = 0; i < n; ++i) {
-    const int64_t l2 = pi[i] - pi[n + i];
-    if (l2 >= 2 * kLamLimit || l2 <= -2 * kLamLimit) st = 5;
-    lam2[i] = (int32_t)l2;
-  }
-  return st;
+  return r;
 }
 
 }  // namespace f2m

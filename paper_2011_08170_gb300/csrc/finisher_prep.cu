@@ -9,7 +9,8 @@
 //   exl[i]   = b_i - #{e in row i : y[e]} (surplus of the left copy of i,
 //            b_i = 2 for the fractional 2-matching; the right copy has the
 //            opposite value since z is symmetric);
-// and map its output (x in half units, lambda at F+1 bits) back to caller order.
+// and map its output back to caller order: x in half units, y[e] + y[twin[e]]
+// of the final flow, and lambda at F+1 bits.
 #include "f2m_device.cuh"
 #include "f2m_internal.h"
 
@@ -27,7 +28,7 @@ static inline int grid_for(long long items, int threads) {
 }
 
 __global__ void fin_twin_kernel(const int32_t* __restrict__ irp, const int2* __restrict__ iec,
-                                int32_t n, int32_t* __restrict__ twin) {
+                                int32_t n, int32_t* __restrict__ twin, unsigned long long* missing) {
   F2M_GRID_STRIDE(i, n) {
     for (int e = irp[i]; e < irp[i + 1]; ++e) {
       const int j = iec[e].x;
@@ -35,6 +36,7 @@ __global__ void fin_twin_kernel(const int32_t* __restrict__ irp, const int2* __r
       const int f1 = irp[j + 1];
       while (f < f1 && iec[f].x != (int)i) ++f;
       twin[e] = f < f1 ? f : -1;
+      if (f >= f1) atomicAdd(missing, 1ull);
     }
   }
 }
@@ -58,7 +60,8 @@ __global__ void fin_init_kernel(const int32_t* __restrict__ irp, const int2* __r
 
 __global__ void fin_scatter_x_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ irp,
                                      const int32_t* __restrict__ perm, int32_t n,
-                                     const uint8_t* __restrict__ x_int, uint8_t* __restrict__ x_out,
+                                     const uint8_t* __restrict__ y, const int32_t* __restrict__ twin,
+                                     uint8_t* __restrict__ x_out,
                                      const int32_t* __restrict__ seg_off, int32_t nseg,
                                      const uint8_t* __restrict__ include) {
   F2M_GRID_STRIDE(i, n) {
@@ -71,12 +74,12 @@ __global__ void fin_scatter_x_kernel(const int32_t* __restrict__ rp, const int32
       if (!include[lo]) continue;
     }
     const int dst = rp[perm[i]], src = irp[i], cnt = irp[i + 1] - src;
-    for (int k = 0; k < cnt; ++k) x_out[dst + k] = x_int[src + k];
+    for (int k = 0; k < cnt; ++k) x_out[dst + k] = (uint8_t)(y[src + k] + y[twin[src + k]]);
   }
 }
 
-cudaError_t fin_build_twin(const GdpPlan& p, int32_t* twin, cudaStream_t st) {
-  fin_twin_kernel<<<grid_for(p.n, 128), 128, 0, st>>>(p.irp, p.iec, p.n, twin);
+cudaError_t fin_build_twin(const GdpPlan& p, int32_t* twin, unsigned long long* missing, cudaStream_t st) {
+  fin_twin_kernel<<<grid_for(p.n, 128), 128, 0, st>>>(p.irp, p.iec, p.n, twin, missing);
   count_launch();
   return cudaGetLastError();
 }
@@ -90,11 +93,11 @@ cudaError_t fin_prepare(const GdpPlan& p, const int32_t* lam_caller, const int32
   return cudaGetLastError();
 }
 
-cudaError_t fin_scatter(const GdpPlan& p, const int32_t* rp, const uint8_t* x_int,
-                        const int32_t* lam2_int, uint8_t* x_out, int32_t* lam2_out,
-                        const int32_t* seg_off, int32_t nseg, const uint8_t* include,
-                        cudaStream_t st) {
-  fin_scatter_x_kernel<<<grid_for(p.n, 128), 128, 0, st>>>(rp, p.irp, p.perm, p.n, x_int, x_out,
+cudaError_t fin_scatter(const GdpPlan& p, const int32_t* rp, const uint8_t* y_int,
+                        const int32_t* twin, const int32_t* lam2_int, uint8_t* x_out,
+                        int32_t* lam2_out, const int32_t* seg_off, int32_t nseg,
+                        const uint8_t* include, cudaStream_t st) {
+  fin_scatter_x_kernel<<<grid_for(p.n, 128), 128, 0, st>>>(rp, p.irp, p.perm, p.n, y_int, twin, x_out,
                                                            seg_off, nseg, include);
   count_launch();
   cudaError_t e = cudaGetLastError();
