@@ -224,6 +224,8 @@ def main():
                     help="1: full scan of all pairs (the headline); 2: the scan with far tile pairs skipped")
     ap.add_argument("--batch-shape", type=int, default=-1,
                     help="batch workloads: fixed kernel shape instead of the autotuner's")
+    ap.add_argument("--batch-clusters", action="store_true",
+                    help="batch workloads: one thread-block cluster per instance instead of the streaming kernels")
     ap.add_argument("--update", default="jacobi", choices=["jacobi", "classes"],
                     help="single instance: Jacobi sweeps (Section 5.1, the headline) or class-by-class sweeps")
     ap.add_argument("--shift", type=int, default=2, help="damping shift of the GDP step")
@@ -423,7 +425,8 @@ def run_batch(args, w, rank, world, local):
     if args.instances:
         specs = specs[:args.instances]
     ds = [I.make_instance(*sp) for sp in specs]
-    params = f2m.f2m_default_params(batch_shape=args.batch_shape, pricing=args.pricing)
+    params = f2m.f2m_default_params(batch_shape=args.batch_shape, pricing=args.pricing,
+                                    flags=f2m.F2M_FLAG_BATCH_CLUSTERS if args.batch_clusters else 0)
     insts = [(d["xy"], d["row_ptr"], d["col"]) for d in ds]
     ns = np.array([d["xy"].shape[0] for d in ds])
     nnzs = np.array([int(d["row_ptr"][-1]) for d in ds])
@@ -505,6 +508,7 @@ def run_batch(args, w, rank, world, local):
             "config": {"workload": workload_name(w) if not args.instances else
                        workload_name(w) + f" (first {len(ns)} instances)", "instances": int(len(ns)),
                        "sum_n": int(ns.sum()), "kernel_shape": int(tot.batch_shape), "graph": bool(tot.batch_graph),
+                       "gdp_path": "clusters" if args.batch_clusters else "streaming",
                        "sum_nnz": int(nnzs.sum()), "l2": "working set larger than L2; flushed before every step",
                        "parallelism": f"replicas x{world}"},
             "breakdown_ms": {k: statistics.median(getattr(r[1], k) for r in res)

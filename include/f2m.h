@@ -113,6 +113,16 @@ typedef struct {
  * changes.  Single-instance contexts; batches ignore the flag. */
 #define F2M_FLAG_CLASS_SWEEPS 4u
 
+/* f2m_params.flags (batches, with batch_shape -1): run batched GDP phases on
+ * thread-block clusters instead of the default streaming batch kernels (the
+ * union CSR streamed from HBM every sweep, one device-wide barrier per sweep):
+ * every instance gets a cluster of 1-16 CTAs that holds its rows and lambda in
+ * shared memory, with the hardware cluster barrier per sweep and neighbours'
+ * lambda read through distributed shared memory.  A batch with an instance too
+ * large for 16 CTAs (2048 nodes, 24,000 entries each) uses the streaming
+ * kernels.  Same results either way. */
+#define F2M_FLAG_BATCH_CLUSTERS 8u
+
 typedef struct {
   int64_t iterations;           /* GDP sweeps, all phases */
   int64_t phases;               /* GDP phases */

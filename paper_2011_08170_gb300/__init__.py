@@ -33,6 +33,7 @@ F2M_ERR_TIMEOUT = 8
 F2M_FLAG_STREAMING_GDP = 1
 F2M_FLAG_ONE_SWEEP_GDP = 2
 F2M_FLAG_CLASS_SWEEPS = 4
+F2M_FLAG_BATCH_CLUSTERS = 8
 
 # every symbol the header declares
 EXPORTS = ["f2m_default_params", "f2m_create", "f2m_destroy", "f2m_set_lambda", "f2m_solve",

@@ -74,6 +74,24 @@ struct f2m_batch {
   std::vector<int64_t> res_eoff, res_nnz, res_b2;
   std::vector<int32_t> res_fb;
   std::vector<uint8_t> res_done;
+  // cluster path (gdp_cluster.cu): one thread-block cluster per instance
+  struct ClusterClass {
+    int32_t C = 0, threads = 0, emax = 0, nmax = 0;
+  };
+  int64_t cl_version = -1;          // GdpPlan::version the cluster plan belongs to
+  bool cl_ok = false;               // every instance fits a cluster that fits the device
+  std::vector<int32_t> cl_class_of; // class (0..4: C = 1, 2, 4, 8, 16) per instance
+  std::vector<ClusterInst> cl_inst; // per instance
+  ClusterClass cl_cls[5];
+  int2* d_pk = nullptr;             // packed rows of every instance
+  int64_t pk_cap = 0;
+  ClusterInst* d_cl_all = nullptr;  // all instances (packing)
+  ClusterInst* d_cl_list = nullptr; // a phase's lists, class by class
+  ClusterInst* h_cl_list = nullptr;
+  ClusterOut* d_cl_out = nullptr;
+  ClusterOut* h_cl_out = nullptr;
+  cudaStream_t cl_st[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t cl_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -105,6 +123,13 @@ extern "C" void f2m_destroy_batch(f2m_batch* b) {
   if (b->h_ctl) cudaFreeHost(b->h_ctl);
   if (b->h_sw) cudaFreeHost(b->h_sw);
   if (b->h_still) cudaFreeHost(b->h_still);
+  dfree(b->d_pk); dfree(b->d_cl_all); dfree(b->d_cl_list); dfree(b->d_cl_out);
+  if (b->h_cl_list) cudaFreeHost(b->h_cl_list);
+  if (b->h_cl_out) cudaFreeHost(b->h_cl_out);
+  for (cudaStream_t& q : b->cl_st)
+    if (q) cudaStreamDestroy(q);
+  for (cudaEvent_t& q : b->cl_ev)
+    if (q) cudaEventDestroy(q);
   delete b;
 }
 
@@ -393,6 +418,120 @@ constexpr long long kSweepsPerLaunch = 256;
 
 // One GDP phase over the instances flagged in `active` (host, one byte each);
 // adds each instance's sweeps to sweeps_out.
+// Cluster plan for the current graph: the cluster size of every instance
+// (the smallest of 1, 2, 4, 8, 16 CTAs whose node and entry shares fit one
+// CTA's shared memory), the per-class launch shape, and the packed rows.
+static f2m_status cluster_plan(f2m_batch* b) {
+  f2m_ctx* c = b->u;
+  GdpPlan& P = c->plan;
+  const int32_t K = b->count;
+  b->cl_ok = false;
+  b->cl_version = P.version;
+  std::vector<int32_t> irp(c->n + 1);
+  CK(c, cudaMemcpyAsync(irp.data(), P.irp, sizeof(int32_t) * (c->n + 1), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  b->cl_class_of.assign(K, -1);
+  b->cl_inst.resize(K);
+  for (auto& q : b->cl_cls) q = f2m_batch::ClusterClass{};
+  for (int32_t s = 0; s < K; ++s) {
+    const int32_t node0 = c->seg_off[s], n = c->seg_off[s + 1] - node0;
+    for (int k = 0; k < 5; ++k) {
+      const int32_t C = 1 << k, per = (n + C - 1) / C;
+      if (per > kClusterNodes) continue;
+      int32_t emax = 0;
+      for (int32_t r = 0; r < C; ++r) {
+        const int32_t a = std::min(node0 + r * per, node0 + n), e = std::min(a + per, node0 + n);
+        emax = std::max(emax, irp[e] - irp[a]);
+      }
+      if (emax > kClusterEntries) continue;
+      b->cl_class_of[s] = k;
+      b->cl_inst[s] = ClusterInst{node0, n, per, s};
+      auto& q = b->cl_cls[k];
+      q.C = C;
+      q.emax = std::max(q.emax, emax);
+      q.nmax = std::max(q.nmax, per);
+      break;
+    }
+    if (b->cl_class_of[s] < 0) return F2M_OK;  // too large: the streaming kernels
+  }
+  for (auto& q : b->cl_cls) {
+    if (q.C == 0) continue;
+    q.threads = std::min(1024, std::max(128, (q.nmax + 31) / 32 * 32));
+    if (cluster_max_smem_ok(q.C, q.threads, q.emax, q.nmax) < 1) return F2M_OK;
+  }
+  if (!b->d_cl_all) {
+    CK(c, dalloc(&b->d_cl_all, K));
+    CK(c, dalloc(&b->d_cl_list, K));
+    CK(c, dalloc(&b->d_cl_out, K));
+    CK(c, cudaMallocHost((void**)&b->h_cl_list, sizeof(ClusterInst) * K));
+    CK(c, cudaMallocHost((void**)&b->h_cl_out, sizeof(ClusterOut) * K));
+    for (cudaStream_t& q : b->cl_st) CK(c, cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+    for (cudaEvent_t& q : b->cl_ev) CK(c, cudaEventCreateWithFlags(&q, cudaEventDisableTiming));
+  }
+  if (b->pk_cap < c->nnz) {
+    dfree(b->d_pk);
+    b->pk_cap = c->ec_cap;
+    CK(c, dalloc(&b->d_pk, b->pk_cap));
+  }
+  CK(c, cudaMemcpyAsync(b->d_cl_all, b->cl_inst.data(), sizeof(ClusterInst) * K, cudaMemcpyHostToDevice, c->st));
+  CK(c, cluster_pack(P.irp, P.iec, b->d_cl_all, K, c->p.frac_bits, b->d_pk, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  b->cl_ok = true;
+  return F2M_OK;
+}
+
+// A GDP phase with one cluster per active instance: the classes run side by
+// side on their own streams; every instance stops at its own fixed point.
+static f2m_status batch_cluster_phase(f2m_batch* b, const std::vector<uint8_t>& active,
+                                      std::vector<int64_t>& sweeps_out, double* ms) {
+  f2m_ctx* c = b->u;
+  GdpPlan& P = c->plan;
+  const int32_t K = b->count;
+  CK(c, enqueue_phase_start(b, c->st, nullptr));
+  CK(c, cudaMemsetAsync(b->d_cl_out, 0, sizeof(ClusterOut) * K, c->st));
+  // lists of the active instances per class, larger instances first
+  int32_t off[6] = {0, 0, 0, 0, 0, 0};
+  int32_t m = 0;
+  for (int k = 0; k < 5; ++k) {
+    off[k] = m;
+    const int32_t m0 = m;
+    for (int32_t s = 0; s < K; ++s)
+      if (active[s] && b->cl_class_of[s] == k) b->h_cl_list[m++] = b->cl_inst[s];
+    std::sort(b->h_cl_list + m0, b->h_cl_list + m,
+              [](const ClusterInst& x, const ClusterInst& y) { return x.n > y.n || (x.n == y.n && x.seg < y.seg); });
+  }
+  off[5] = m;
+  if (m > 0) CK(c, cudaMemcpyAsync(b->d_cl_list, b->h_cl_list, sizeof(ClusterInst) * m, cudaMemcpyHostToDevice, c->st));
+  CK(c, cudaEventRecord(c->ev0, c->st));
+  CK(c, cudaEventRecord(b->cl_ev[5], c->st));
+  for (int k = 4; k >= 0; --k) {  // the largest clusters first
+    const int32_t cnt = off[k + 1] - off[k];
+    if (cnt == 0) continue;
+    const auto& q = b->cl_cls[k];
+    CK(c, cudaStreamWaitEvent(b->cl_st[k], b->cl_ev[5], 0));
+    CK(c, launch_gdp_cluster(q.C, q.threads, P.irp, b->d_pk, b->d_cl_list + off[k], cnt, P.ilam[0],
+                             c->p.damping_shift, c->p.max_iters, b->d_cl_out, q.emax, q.nmax,
+                             b->cl_st[k]));
+    CK(c, cudaEventRecord(b->cl_ev[k], b->cl_st[k]));
+    CK(c, cudaStreamWaitEvent(c->st, b->cl_ev[k], 0));
+  }
+  CK(c, cudaEventRecord(c->ev1, c->st));
+  CK(c, cudaMemcpyAsync(b->h_cl_out, b->d_cl_out, sizeof(ClusterOut) * K, cudaMemcpyDeviceToHost, c->st));
+  CK(c, scatter_perm(P.ilam[0], P.perm, c->n, c->d_lam[c->cur], c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  float t_ms = 0.f;
+  cudaEventElapsedTime(&t_ms, c->ev0, c->ev1);
+  if (ms) *ms += t_ms;
+  int st = 0;
+  for (int32_t s = 0; s < K; ++s) {
+    if (!active[s]) continue;
+    st |= b->h_cl_out[s].status;
+    sweeps_out[s] += b->h_cl_out[s].sweeps;
+  }
+  if (st & kGdpOverflow) return fail(c, F2M_ERR_OVERFLOW, "|lambda| reached 2^29 in some instance");
+  return F2M_OK;
+}
+
 static f2m_status batch_gdp_phase(f2m_batch* b, const std::vector<uint8_t>& active,
                                   std::vector<int64_t>& sweeps_out, double* ms) {
   f2m_ctx* c = b->u;
@@ -401,6 +540,15 @@ static f2m_status batch_gdp_phase(f2m_batch* b, const std::vector<uint8_t>& acti
   if (c->fb_cur != F) {  // continue from the finisher's lambda: floor to F bits
     CK(c, launch_halve(c->d_lam2, c->d_lam[c->cur], c->n, c->st));
     c->fb_cur = F;
+  }
+  // clusters when asked for, unless a streaming-kernel shape is given or some
+  // instance does not fit a cluster
+  if (c->p.batch_shape < 0 && (c->p.flags & F2M_FLAG_BATCH_CLUSTERS)) {
+    if (b->cl_version != P.version) {
+      f2m_status s = cluster_plan(b);
+      if (s != F2M_OK) return s;
+    }
+    if (b->cl_ok) return batch_cluster_phase(b, active, sweeps_out, ms);
   }
   if (b->tiles_version != P.version) {
     f2m_status s = F2M_OK;

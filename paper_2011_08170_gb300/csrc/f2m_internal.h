@@ -248,6 +248,32 @@ cudaError_t fin_scatter(const GdpPlan& p, const int32_t* rp, const uint8_t* y_in
                         const int32_t* twin, const int32_t* lam2_int, uint8_t* x_out,
                         int32_t* lam2_out, const int32_t* seg_off, int32_t nseg,
                         const uint8_t* include, cudaStream_t st);
+// ---- batched GDP on thread-block clusters (gdp_cluster.cu) ------------------------
+struct ClusterInst {
+  int32_t node0;  // first internal node of the instance
+  int32_t n;      // its nodes
+  int32_t per;    // nodes per CTA (the last CTAs may hold fewer, or none)
+  int32_t seg;    // instance id
+};
+struct ClusterOut {
+  long long sweeps;
+  int status;     // kGdpOverflow bit
+  int fixed;      // 1 if the last sweep changed nothing
+};
+constexpr int kClusterNodes = 2048;      // most nodes one CTA holds
+constexpr int kClusterEntries = 24000;   // most entries one CTA holds
+size_t cluster_smem(int32_t emax, int32_t nmax);
+// pk[e] = {owner rank << 16 | local index, cost << F} for the listed instances' entries
+cudaError_t cluster_pack(const int32_t* irp, const int2* iec, const ClusterInst* d_insts, int32_t ninst,
+                         int32_t F, int2* pk, cudaStream_t st);
+// one cluster of C CTAs per listed instance; ilam (internal order) in and out; out zeroed
+cudaError_t launch_gdp_cluster(int32_t C, int32_t threads, const int32_t* irp, const int2* pk,
+                               const ClusterInst* d_insts, int32_t ninst, int32_t* ilam,
+                               int32_t shift, int64_t max_sweeps, ClusterOut* out,
+                               int32_t emax, int32_t nmax, cudaStream_t st);
+// clusters of this shape that fit on the device at once (0: none)
+int32_t cluster_max_smem_ok(int32_t C, int32_t threads, int32_t emax, int32_t nmax);
+
 // ---- batched solver (batch_kernels.cu) --------------------------------------------
 // Parameters of one launch of a batched GDP kernel, read from device memory so
 // that a captured launch can be replayed with new values.

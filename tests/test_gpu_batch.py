@@ -117,3 +117,40 @@ def test_every_kernel_shape_gives_the_same_result(lib, oracle_lib, shape):
     ds = make_batch([("uniform", 700, 31, 10), ("mixture", 1300, 32, 10), ("uniform", 2100, 33, 6),
                      ("mixture", 450, 34, 10)])
     compare(oracle_lib, ds, f2m.f2m_default_params(batch_shape=shape))
+
+
+CLUSTERS = f2m.f2m_default_params(flags=f2m.F2M_FLAG_BATCH_CLUSTERS)
+
+
+def test_cluster_sizes_match_single_solves(lib, oracle_lib):
+    # instance sizes that take clusters of 1, 2, 4, 8 and 16 CTAs (at most 2048
+    # nodes and 24,000 entries per CTA)
+    ds = make_batch([("uniform", 1500, 31, 10), ("mixture", 3000, 32, 10), ("uniform", 6000, 33, 10),
+                     ("mixture", 12000, 34, 10), ("uniform", 20000, 35, 10), ("uniform", 37, 36, 6)])
+    compare(oracle_lib, ds, CLUSTERS)
+
+
+def test_cluster_batch_with_pricing_rounds(lib, oracle_lib):
+    ds = make_batch([("uniform", 600, 11, 4), ("mixture", 900, 12, 10), ("uniform", 1200, 13, 5),
+                     ("mixture", 400, 14, 4), ("uniform", 1000, 0, 10)])
+    compare(oracle_lib, ds, CLUSTERS)
+
+
+def test_cluster_and_streaming_batch_paths_agree(lib):
+    ds = make_batch([("uniform", 4000, 41, 10), ("mixture", 9000, 42, 8), ("uniform", 700, 43, 5)])
+    res = []
+    for flags in (0, f2m.F2M_FLAG_BATCH_CLUSTERS):
+        b = f2m.f2m_create_batch([(d["xy"], d["row_ptr"], d["col"]) for d in ds],
+                                 f2m.f2m_default_params(flags=flags))
+        infos, tot = f2m.f2m_solve_batch(b)
+        assert tot.status == 0
+        res.append([(i.iterations, i.phases, i.bound2, f2m.f2m_batch_get_lambda(b, k)[0].tobytes(),
+                     f2m.f2m_batch_get_x(b, k)[2].tobytes()) for k, i in enumerate(infos)])
+    assert res[0] == res[1]
+
+
+def test_instance_too_large_for_a_cluster(lib, oracle_lib):
+    # 40,000 nodes need more than 16 CTAs of 2048 nodes: the batch runs on the
+    # streaming kernels and still equals the single solves
+    ds = make_batch([("uniform", 40000, 51, 10), ("mixture", 2000, 52, 10)])
+    compare(oracle_lib, ds, CLUSTERS)
