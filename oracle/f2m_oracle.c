@@ -597,8 +597,11 @@ int64_t or_merge(int32_t n, const int32_t* row_ptr, const int32_t* col, int64_t 
 /* ---- full solve ----------------------------------------------------------
  * round loop:
  *   GDP phase from the current lambda (F bits) until a fixed point or the cap;
- *   while pricing rounds remain: price with that lambda; if pairs were found,
- *     add them and start the next GDP phase (lambda kept);
+ *   while pricing rounds remain, after the first phase and after any phase
+ *     whose preceding scan found at least n/1024 pairs: price with that lambda;
+ *     if pairs were found, add them and start the next GDP phase (lambda kept)
+ *     -- after a scan that found few pairs the next phase goes straight on,
+ *     since the scan with the final lambda below finds what is still missing;
  *   otherwise extract x by rule (7); if a node's row does not sum to 2, run the
  *     exact finisher (lambda then has F+1 bits);
  *   price with the final lambda: no pair -> certified optimal over all pairs;
@@ -659,6 +662,7 @@ or_result* or_solve(int32_t n, const int32_t* xy, const int32_t* row_ptr,
   int32_t* pairs = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * pcap));
 
   const int32_t F = p->frac_bits;
+  int64_t last_pairs = 0; /* pairs found by the last scan */
   memset(info, 0, sizeof(*info));
   info->frac_bits = F;
   int status = OR_OK;
@@ -685,9 +689,11 @@ or_result* or_solve(int32_t n, const int32_t* xy, const int32_t* row_ptr,
     if (st == OR_OVERFLOW || st == OR_INVALID) { status = st; break; }
 
     int clean = 0; /* the GDP lambda was priced and no pair was found */
-    if (p->pricing && info->pricing_rounds < p->max_pricing_rounds) {
+    if (p->pricing && info->pricing_rounds < p->max_pricing_rounds &&
+        (info->phases == 1 || last_pairs * 1024 >= n)) {
       int64_t cnt = or_price_all(n, xy, r->row_ptr, r->col, lam, F, &pairs, &pcap);
       info->pricing_rounds += 1;
+      last_pairs = cnt;
       if (cnt > 0) {
         or_add_pairs(r, xy, &cost, cnt, pairs);
         info->edges_added += cnt;
@@ -717,6 +723,7 @@ or_result* or_solve(int32_t n, const int32_t* xy, const int32_t* row_ptr,
     if (info->pricing_rounds >= p->max_pricing_rounds) { status = OR_NOT_CONVERGED; break; }
     int64_t cnt = or_price_all(n, xy, r->row_ptr, r->col, r->lam, fb, &pairs, &pcap);
     info->pricing_rounds += 1;
+    last_pairs = cnt;
     if (cnt == 0) { info->certified = 2; break; }
     or_add_pairs(r, xy, &cost, cnt, pairs);
     info->edges_added += cnt;

@@ -45,6 +45,7 @@ static void free_finisher_buffers(f2m_ctx* c) {
   c->h_exl = nullptr; c->h_lam = nullptr; c->h_lam2 = nullptr;
   c->fin_cap = 0;
   c->fin_version = -1;
+  c->twin_version = -1;
 }
 
 // device and pinned host buffers for `cap` entries (node-sized ones once)
@@ -60,6 +61,7 @@ static cudaError_t alloc_finisher_buffers(f2m_ctx* c, int64_t cap) {
   c->h_iec = nullptr; c->h_twin = nullptr; c->h_y = nullptr;
   c->fin_cap = 0;
   c->fin_version = -1;
+  c->twin_version = -1;
   cudaError_t e = cudaMalloc((void**)&c->d_twin, sizeof(int32_t) * cap);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_fy, cap);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_iec, sizeof(int2) * cap);
@@ -733,49 +735,91 @@ f2m_status f2m::bound_internal(f2m_ctx* c, int64_t* b2) {
 // Exact finisher: device prep (twin arcs, initial flow, surpluses) on the
 // renumbered CSR, successive shortest paths on the host, results scattered back
 // to caller order on the device.
-f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug) {
+f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug, const uint8_t* h_include) {
   const int32_t n = c->n;
   const int32_t F = c->p.frac_bits;
   GdpPlan& P = c->plan;
+  const int32_t nseg = (int32_t)c->seg_off.size() - 1;
   if (c->fin_cap < c->nnz) CK(c, alloc_finisher_buffers(c, c->ec_cap));
   if (!c->fin_work) c->fin_work = finisher_work_new();
-  const bool mirror = c->fin_version != P.version;
-  if (mirror) {  // the graph changed: mirror it again
+  unsigned long long missing = 0;
+  const bool twin_new = c->twin_version != P.version;
+  if (twin_new) {  // the graph changed: reverse entries again
     CK(c, cudaMemsetAsync(c->d_bad, 0, sizeof(unsigned long long), c->st));
     CK(c, fin_build_twin(P, c->d_twin, c->d_bad, c->st));
-    CK(c, cudaMemcpyAsync(c->h_irp, P.irp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, c->st));
-    CK(c, cudaMemcpyAsync(c->h_iec, P.iec, sizeof(int2) * c->nnz, cudaMemcpyDeviceToHost, c->st));
-    CK(c, cudaMemcpyAsync(c->h_twin, c->d_twin, sizeof(int32_t) * c->nnz, cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaMemcpyAsync(&missing, c->d_bad, sizeof(missing), cudaMemcpyDeviceToHost, c->st));
   }
   int32_t* d_lam_int = P.ilam[0];   // free outside a GDP phase
   int32_t* d_lam2_int = P.ilam[1];
   int32_t* d_exl = P.tmp;
   CK(c, fin_prepare(P, c->d_lam[c->cur], c->d_b, F, d_lam_int, c->d_fy, d_exl, c->st));
   if (c->d_fin_include)
-    CK(c, launch_batch_mask_surplus(d_exl, c->d_seg_off, (int32_t)c->seg_off.size() - 1,
-                                    c->d_fin_include, n, c->st));
-  unsigned long long missing = 0;
-  CK(c, cudaMemcpyAsync(c->h_y, c->d_fy, c->nnz, cudaMemcpyDeviceToHost, c->st));
-  CK(c, cudaMemcpyAsync(c->h_exl, d_exl, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->st));
-  CK(c, cudaMemcpyAsync(c->h_lam, d_lam_int, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->st));
-  if (mirror) CK(c, cudaMemcpyAsync(&missing, c->d_bad, sizeof(missing), cudaMemcpyDeviceToHost, c->st));
+    CK(c, launch_batch_mask_surplus(d_exl, c->d_seg_off, nseg, c->d_fin_include, n, c->st));
+  // the host copy of the graph: whole (cached per graph version), or, when a
+  // batch names the instances the finisher works on, just theirs (node and
+  // entry ranges of segments are contiguous in the internal order); the others
+  // keep lambda, doubled to F+1 bits on the device
+  std::vector<int2> ranges;   // entry ranges [x, y) that the host reads and writes
+  std::vector<int2> nranges;  // their node ranges
+  if (h_include) {
+    CK(c, launch_double(d_lam_int, d_lam2_int, n, c->st));
+    CK(c, cudaMemcpyAsync(c->h_irp, P.irp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    c->fin_version = -1;  // the host copy is partial from here on
+    for (int32_t sg = 0; sg < nseg; ++sg) {
+      if (!h_include[sg]) continue;
+      const int32_t v0 = c->seg_off[sg], v1 = c->seg_off[sg + 1];
+      const int32_t e0 = c->h_irp[v0], e1 = c->h_irp[v1];
+      if (!nranges.empty() && nranges.back().y == v0) {
+        nranges.back().y = v1;
+        ranges.back().y = e1;
+      } else {
+        nranges.push_back(make_int2(v0, v1));
+        ranges.push_back(make_int2(e0, e1));
+      }
+    }
+    for (size_t k = 0; k < ranges.size(); ++k) {
+      const int2 q = ranges[k], v = nranges[k];
+      const size_t m = (size_t)(q.y - q.x), nv = (size_t)(v.y - v.x);
+      CK(c, cudaMemcpyAsync(c->h_iec + q.x, P.iec + q.x, sizeof(int2) * m, cudaMemcpyDeviceToHost, c->st));
+      CK(c, cudaMemcpyAsync(c->h_twin + q.x, c->d_twin + q.x, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, c->st));
+      CK(c, cudaMemcpyAsync(c->h_y + q.x, c->d_fy + q.x, m, cudaMemcpyDeviceToHost, c->st));
+      CK(c, cudaMemcpyAsync(c->h_exl + v.x, d_exl + v.x, sizeof(int32_t) * nv, cudaMemcpyDeviceToHost, c->st));
+      CK(c, cudaMemcpyAsync(c->h_lam + v.x, d_lam_int + v.x, sizeof(int32_t) * nv, cudaMemcpyDeviceToHost, c->st));
+    }
+  } else {
+    CK(c, cudaMemcpyAsync(c->h_exl, d_exl, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaMemcpyAsync(c->h_lam, d_lam_int, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->st));
+    if (c->fin_version != P.version) {
+      CK(c, cudaMemcpyAsync(c->h_irp, P.irp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, c->st));
+      CK(c, cudaMemcpyAsync(c->h_iec, P.iec, sizeof(int2) * c->nnz, cudaMemcpyDeviceToHost, c->st));
+      CK(c, cudaMemcpyAsync(c->h_twin, c->d_twin, sizeof(int32_t) * c->nnz, cudaMemcpyDeviceToHost, c->st));
+      c->fin_version = P.version;
+    }
+    CK(c, cudaMemcpyAsync(c->h_y, c->d_fy, c->nnz, cudaMemcpyDeviceToHost, c->st));
+    ranges.push_back(make_int2(0, (int32_t)c->nnz));
+    nranges.push_back(make_int2(0, n));
+  }
   CK(c, cudaStreamSynchronize(c->st));
-  if (mirror) {
+  if (twin_new) {
     if (missing) return fail(c, F2M_ERR_INVALID_ARG, "finisher: CSR not symmetric");
-    c->fin_version = P.version;
+    c->twin_version = P.version;
   }
   static const int32_t hw = (int32_t)std::thread::hardware_concurrency();
-  const int32_t nseg = (int32_t)c->seg_off.size() - 1;
   const int r = host_finisher(n, c->h_irp, c->h_iec, c->h_twin, c->h_y, c->h_exl, c->h_lam, F,
-                              c->h_lam2, c->seg_off.data(), nseg, hw > 1 ? hw : 1, aug,
+                              c->h_lam2, c->seg_off.data(), nseg, h_include, hw > 1 ? hw : 1, aug,
                               c->fin_work);
   if (r == 7)
     return fail(c, F2M_ERR_INFEASIBLE, c->d_b ? "no fractional b-matching exists on the candidate graph"
                                               : "no fractional 2-matching exists on the candidate graph");
   if (r == 5) return fail(c, F2M_ERR_OVERFLOW, "finisher lambda out of range");
   if (r != 0) return fail(c, F2M_ERR_INVALID_ARG, "finisher failed");
-  CK(c, cudaMemcpyAsync(c->d_fy, c->h_y, c->nnz, cudaMemcpyHostToDevice, c->st));
-  CK(c, cudaMemcpyAsync(d_lam2_int, c->h_lam2, sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->st));
+  for (size_t k = 0; k < ranges.size(); ++k) {
+    const int2 q = ranges[k], v = nranges[k];
+    CK(c, cudaMemcpyAsync(c->d_fy + q.x, c->h_y + q.x, (size_t)(q.y - q.x), cudaMemcpyHostToDevice, c->st));
+    CK(c, cudaMemcpyAsync(d_lam2_int + v.x, c->h_lam2 + v.x, sizeof(int32_t) * (size_t)(v.y - v.x),
+                          cudaMemcpyHostToDevice, c->st));
+  }
   CK(c, fin_scatter(P, c->d_rp, c->d_fy, c->d_twin, d_lam2_int, c->d_x2, c->d_lam2, c->d_seg_off,
                     (int32_t)c->seg_off.size() - 1, c->d_fin_include, c->st));
   CK(c, cudaStreamSynchronize(c->st));
@@ -797,6 +841,7 @@ extern "C" f2m_status f2m_solve(f2m_ctx* c, f2m_info* info_out) {
   info.frac_bits = F;
   info.batch_shape = -1;
   f2m_status status = F2M_OK;
+  int64_t last_pairs = 0;  // pairs found by the last scan
   for (;;) {
     int64_t sw = 0;
     f2m_status s = gdp_phase(c, c->p.max_iters, &sw, false, 0, &info.ms_gdp);
@@ -804,11 +849,16 @@ extern "C" f2m_status f2m_solve(f2m_ctx* c, f2m_info* info_out) {
     info.phases += 1;
     if (s != F2M_OK && s != F2M_ERR_NOT_CONVERGED) { status = s; break; }
 
+    // price the GDP lambda after the first phase and after a phase whose
+    // preceding scan found at least n/1024 pairs; otherwise go straight on
+    // (the scan with the final lambda finds what is still missing)
     bool clean = false;
-    if (c->p.pricing && info.pricing_rounds < c->p.max_pricing_rounds) {
+    if (c->p.pricing && info.pricing_rounds < c->p.max_pricing_rounds &&
+        (info.phases == 1 || last_pairs * 1024 >= c->n)) {
       s = price_internal(c, &info.ms_pricing);
       if (s != F2M_OK) { status = s; break; }
       info.pricing_rounds += 1;
+      last_pairs = c->npairs;
       if (c->npairs > 0) {
         s = merge_internal(c, c->d_pairs, c->npairs, &info.ms_merge);
         if (s != F2M_OK) { status = s; break; }
@@ -829,7 +879,7 @@ extern "C" f2m_status f2m_solve(f2m_ctx* c, f2m_info* info_out) {
       }
       const auto f0 = std::chrono::steady_clock::now();
       int64_t aug = 0;
-      s = finisher_internal(c, &aug);
+      s = finisher_internal(c, &aug, nullptr);
       info.ms_finish += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - f0).count();
       info.finisher_calls += 1;
       info.augmentations += aug;
@@ -847,6 +897,7 @@ extern "C" f2m_status f2m_solve(f2m_ctx* c, f2m_info* info_out) {
     s = price_internal(c, &info.ms_pricing);
     if (s != F2M_OK) { status = s; break; }
     info.pricing_rounds += 1;
+    last_pairs = c->npairs;
     if (c->npairs == 0) { info.certified = 2; break; }
     s = merge_internal(c, c->d_pairs, c->npairs, &info.ms_merge);
     if (s != F2M_OK) { status = s; break; }

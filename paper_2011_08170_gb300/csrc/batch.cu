@@ -713,6 +713,7 @@ extern "C" f2m_status f2m_solve_batch(f2m_batch* b, f2m_info* info_out, f2m_info
   std::vector<int> state(K, GDP);
   std::vector<uint8_t> clean(K, 0), active(K, 0), include(K, 0), done_now(K, 0);
   std::vector<int64_t> sweeps(K, 0), phases(K, 0), rounds(K, 0), added(K, 0), fin_calls(K, 0);
+  std::vector<int64_t> last_pairs(K, 0);  // pairs found by each instance's last scan
   std::vector<int32_t> certified(K, 0), inst_status(K, F2M_OK);
   b->res_eoff.assign(K, 0);
   b->res_nnz.assign(K, 0);
@@ -740,7 +741,10 @@ extern "C" f2m_status f2m_solve_batch(f2m_batch* b, f2m_info* info_out, f2m_info
         if (!active[s]) continue;
         phases[s] += 1;
         clean[s] = 0;
-        if (c->p.pricing && rounds[s] < c->p.max_pricing_rounds) {
+        // as f2m_solve: price after the first phase and after a phase whose
+        // preceding scan found at least n/1024 pairs
+        if (c->p.pricing && rounds[s] < c->p.max_pricing_rounds &&
+            (phases[s] == 1 || last_pairs[s] * 1024 >= b->n[s])) {
           c->seg_scan[s] = 1;
           any_scan = true;
         } else {
@@ -754,6 +758,7 @@ extern "C" f2m_status f2m_solve_batch(f2m_batch* b, f2m_info* info_out, f2m_info
         for (int32_t s = 0; s < K; ++s) {
           if (!c->seg_scan[s]) continue;
           rounds[s] += 1;
+          last_pairs[s] = c->seg_pairs[s];
           if (c->seg_pairs[s] > 0) {
             added[s] += c->seg_pairs[s];  // another GDP phase
           } else {
@@ -800,7 +805,7 @@ extern "C" f2m_status f2m_solve_batch(f2m_batch* b, f2m_info* info_out, f2m_info
       CK(c, cudaMemcpyAsync(c->d_fin_include, include.data(), K, cudaMemcpyHostToDevice, c->st));
       const auto f0 = std::chrono::steady_clock::now();
       int64_t aug = 0;
-      status = finisher_internal(c, &aug);
+      status = finisher_internal(c, &aug, include.data());
       tot.ms_finish += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - f0).count();
       if (status != F2M_OK) break;
       tot.finisher_calls += 1;
@@ -831,6 +836,7 @@ extern "C" f2m_status f2m_solve_batch(f2m_batch* b, f2m_info* info_out, f2m_info
       for (int32_t s = 0; s < K; ++s) {
         if (!c->seg_scan[s]) continue;
         rounds[s] += 1;
+        last_pairs[s] = c->seg_pairs[s];
         if (c->seg_pairs[s] == 0) {
           certified[s] = 2;
           done_now[s] = 1;

@@ -71,7 +71,8 @@ struct f2m_ctx {
   int32_t* d_twin = nullptr;
   uint8_t* d_fy = nullptr;
   int64_t fin_cap = 0;          // entries the finisher buffers hold
-  int64_t fin_version = -1;     // plan version mirrored on the host
+  int64_t fin_version = -1;     // plan version mirrored whole on the host
+  int64_t twin_version = -1;    // plan version of d_twin
   int32_t* h_irp = nullptr;
   int2* h_iec = nullptr;
   int32_t* h_twin = nullptr;
@@ -115,7 +116,8 @@ f2m_status price_internal(f2m_ctx* c, double* ms);
 f2m_status merge_internal(f2m_ctx* c, const int2* d_pairs, int64_t npairs, double* ms);
 f2m_status extract_internal(f2m_ctx* c, int64_t* bad, double* ms);
 f2m_status bound_internal(f2m_ctx* c, int64_t* b2);
-f2m_status finisher_internal(f2m_ctx* c, int64_t* aug);
+// h_include (host, per segment; NULL = all): the segments the finisher works on
+f2m_status finisher_internal(f2m_ctx* c, int64_t* aug, const uint8_t* h_include);
 // create a context for the graph, renumbering within segments when seg_off has
 // more than one segment (seg_off[0] = 0, seg_off.back() = n)
 f2m_status create_internal(const int32_t* xy, int32_t n, const int32_t* row_ptr, const int32_t* col,

@@ -316,12 +316,15 @@ void finisher_work_free(FinisherWork* w);
 // Min-cost flow on the bipartite double cover, internal node order; see
 // finisher.cpp.  y is the initial flow (updated to the optimal one), exl the
 // left surpluses, lam2 receives pi(L) - pi(R) (F+1 bits).  Blocks and segments
-// [seg_off[s], seg_off[s+1]) go to up to `threads` host threads.  Returns 0 ok,
-// 7 infeasible, 5 overflow.
+// [seg_off[s], seg_off[s+1]) go to up to `threads` host threads; with include
+// (per segment; NULL = all) the other segments are neither read nor written.
+// Returns 0 ok, 7 infeasible, 5 overflow.
 int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t* twin, uint8_t* y,
                   const int32_t* exl, const int32_t* lam, int32_t F, int32_t* lam2,
-                  const int32_t* seg_off, int32_t nseg, int32_t threads, int64_t* augmentations,
-                  FinisherWork* w);
+                  const int32_t* seg_off, int32_t nseg, const uint8_t* include, int32_t threads,
+                  int64_t* augmentations, FinisherWork* w);
+// lam_out = 2 * lam_in (F bits -> F+1 bits)
+cudaError_t launch_double(const int32_t* lam_in, int32_t* lam_out, int32_t n, cudaStream_t st);
 
 
 // ---- k nearest neighbours and warm-start features (knn.cu) -------------------------

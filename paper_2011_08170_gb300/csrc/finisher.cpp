@@ -245,8 +245,8 @@ int run_items(int32_t count, int32_t threads, FinisherWork* w, std::vector<int64
 
 int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t* twin, uint8_t* y,
                   const int32_t* exl, const int32_t* lam, int32_t F, int32_t* lam2,
-                  const int32_t* seg_off, int32_t nseg, int32_t threads, int64_t* augmentations,
-                  FinisherWork* w) {
+                  const int32_t* seg_off, int32_t nseg, const uint8_t* include, int32_t threads,
+                  int64_t* augmentations, FinisherWork* w) {
   finisher_work_reserve(w, n);
   if (w->stamp.load() > (1u << 31)) {  // far from wrapping: clear the stamps and restart
     std::fill(w->reached.begin(), w->reached.end(), 0u);
@@ -258,9 +258,13 @@ int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t*
   // phase 1: blocks of every segment, each first setting its own nodes'
   // potentials (lam, -lam) and surpluses; phase 2: whole segments
   std::vector<int2> blocks;
-  for (int32_t sg = 0; sg < nseg; ++sg)
+  std::vector<int32_t> segs;
+  for (int32_t sg = 0; sg < nseg; ++sg) {
+    if (include && !include[sg]) continue;  // left alone: not read, not written
+    segs.push_back(sg);
     for (int32_t b0 = seg_off[sg]; b0 < seg_off[sg + 1]; b0 += kFinBlock)
       blocks.push_back(make_int2(b0, std::min(b0 + kFinBlock, seg_off[sg + 1])));
+  }
   std::vector<int64_t> pushes;
   int r = run_items((int32_t)blocks.size(), threads, w, pushes,
                     [&](int32_t k, Searcher& sr, int64_t* p) {
@@ -273,11 +277,12 @@ int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t*
                       return solve_range(n, blocks[k].x, blocks[k].y, lam, irp, iec, twin, y, F, w, sr, p);
                     });
   if (r == 0)
-    r = run_items(nseg, threads, w, pushes, [&](int32_t k, Searcher& sr, int64_t* p) {
-      const int q = solve_range(n, seg_off[k], seg_off[k + 1], nullptr, irp, iec, twin, y, F, w, sr, p);
+    r = run_items((int32_t)segs.size(), threads, w, pushes, [&](int32_t k, Searcher& sr, int64_t* p) {
+      const int32_t sg = segs[k];
+      const int q = solve_range(n, seg_off[sg], seg_off[sg + 1], nullptr, irp, iec, twin, y, F, w, sr, p);
       if (q != 0) return q;
       int st = 0;
-      for (int32_t i = seg_off[k]; i < seg_off[k + 1]; ++i) {
+      for (int32_t i = seg_off[sg]; i < seg_off[sg + 1]; ++i) {
         const int64_t l2 = pi[i] - pi[n + i];
         if (l2 >= 2 * kLamLimit || l2 <= -2 * kLamLimit) st = 5;
         lam2[i] = (int32_t)l2;

@@ -243,6 +243,21 @@ __global__ void halve_kernel(const int32_t* __restrict__ in, int32_t* __restrict
     out[v] = in[v] >> 1;  // arithmetic shift: floor
 }
 
+__global__ void double_kernel(const int32_t* __restrict__ in, int32_t* __restrict__ out, int32_t n) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x)
+    out[v] = 2 * in[v];  // |lambda| < 2^29: no overflow
+}
+
+cudaError_t launch_double(const int32_t* lam_in, int32_t* lam_out, int32_t n, cudaStream_t st) {
+  const int threads = 256;
+  int blocks = (int)((n + threads - 1) / threads);
+  if (blocks > 4096) blocks = 4096;
+  double_kernel<<<blocks, threads, 0, st>>>(lam_in, lam_out, n);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_halve(const int32_t* lam_in, int32_t* lam_out, int32_t n, cudaStream_t st) {
   const int threads = 256;
   int blocks = (int)((n + threads - 1) / threads);
