@@ -599,9 +599,12 @@ int64_t or_merge(int32_t n, const int32_t* row_ptr, const int32_t* col, int64_t 
  *   GDP phase from the current lambda (F bits) until a fixed point or the cap;
  *   while pricing rounds remain, after the first phase and after any phase
  *     whose preceding scan found at least n/1024 pairs: price with that lambda;
- *     if pairs were found, add them and start the next GDP phase (lambda kept)
- *     -- after a scan that found few pairs the next phase goes straight on,
- *     since the scan with the final lambda below finds what is still missing;
+ *     if pairs were found, add them and start the next GDP phase (lambda kept),
+ *     except after the first phase's scan when it found fewer than n/1024
+ *     pairs: then go on to rule (7) and the finisher, which take the few new
+ *     edges from this lambda -- after a scan that found few pairs the next
+ *     phase goes straight on, since the scan with the final lambda below finds
+ *     what is still missing;
  *   otherwise extract x by rule (7); if a node's row does not sum to 2, run the
  *     exact finisher (lambda then has F+1 bits);
  *   price with the final lambda: no pair -> certified optimal over all pairs;
@@ -697,9 +700,12 @@ or_result* or_solve(int32_t n, const int32_t* xy, const int32_t* row_ptr,
       if (cnt > 0) {
         or_add_pairs(r, xy, &cost, cnt, pairs);
         info->edges_added += cnt;
-        continue;
+        /* another GDP phase, unless the first phase's scan found few pairs:
+         * the finisher then takes the few new edges from this lambda */
+        if (info->phases > 1 || cnt * 1024 >= n) continue;
+      } else {
+        clean = 1;
       }
-      clean = 1;
     }
 
     int32_t fb = F;

@@ -860,12 +860,16 @@ extern "C" f2m_status f2m_solve(f2m_ctx* c, f2m_info* info_out) {
       info.pricing_rounds += 1;
       last_pairs = c->npairs;
       if (c->npairs > 0) {
+        const int64_t found = c->npairs;
         s = merge_internal(c, c->d_pairs, c->npairs, &info.ms_merge);
         if (s != F2M_OK) { status = s; break; }
-        info.edges_added += c->npairs;
-        continue;
+        info.edges_added += found;
+        // another GDP phase, unless the first phase's scan found few pairs:
+        // the finisher then takes the few new edges from this lambda
+        if (info.phases > 1 || found * 1024 >= c->n) continue;
+      } else {
+        clean = true;
       }
-      clean = true;
     }
 
     int64_t bad = 0;

@@ -760,7 +760,10 @@ extern "C" f2m_status f2m_solve_batch(f2m_batch* b, f2m_info* info_out, f2m_info
           rounds[s] += 1;
           last_pairs[s] = c->seg_pairs[s];
           if (c->seg_pairs[s] > 0) {
-            added[s] += c->seg_pairs[s];  // another GDP phase
+            added[s] += c->seg_pairs[s];
+            // another GDP phase, unless the first phase's scan found few
+            // pairs (as f2m_solve): the finisher takes them from this lambda
+            if (phases[s] == 1 && c->seg_pairs[s] * 1024 < b->n[s]) state[s] = EXTRACT;
           } else {
             clean[s] = 1;
             state[s] = EXTRACT;
