@@ -309,6 +309,24 @@ void f2m_destroy_batch(f2m_batch* batch);
 
 /* ---- candidate graph and learned warm start ------------------------------------ */
 
+/* Reads a TSPLIB problem (the input of the GD program, Section 5.1) from text
+ * in memory: keyword lines, then NODE_COORD_SECTION with one "id x y" line
+ * per node (ids 1..DIMENSION, each once, any order), then optionally EOF.
+ * EDGE_WEIGHT_TYPE must be EUC_2D and TYPE, if present, TSP; coordinates must
+ * be integral (12, 12.0, 1.2e1) with a spread below 2^20 in x and in y.  Host
+ * code only (no GPU).
+ *   text, len    the file's bytes (not necessarily NUL-terminated).
+ *   xy           [cap][2] int32, host, written with the points translated so
+ *                that the smallest x and the smallest y are 0; NULL to query
+ *                the size only.
+ *   n_out        written: DIMENSION.
+ *   translation  [2] int64, host, or NULL: the (x, y) that was subtracted.
+ * Errors: INVALID_ARG, with the reason in f2m_tsplib_last_error(). */
+f2m_status f2m_tsplib_parse(const char* text, int64_t len, int32_t* xy, int32_t cap, int32_t* n_out,
+                            int64_t* translation);
+/* The reason of the last f2m_tsplib_parse failure on this thread ("" if none). */
+const char* f2m_tsplib_last_error(void);
+
 /* k nearest neighbours of every point (the top-N nearest-neighbour candidate
  * graph of Section 5.3): the k other points with the smallest exact squared
  * distance dx^2 + dy^2 (int64), ties broken by smaller index; a copy of the

@@ -43,7 +43,8 @@ EXPORTS = ["f2m_default_params", "f2m_create", "f2m_destroy", "f2m_set_lambda", 
            "f2m_batch_get_lambda", "f2m_batch_get_x", "f2m_batch_last_error", "f2m_destroy_batch",
            "f2m_knn", "f2m_knn_csr", "f2m_features", "f2m_mlp_create", "f2m_mlp_destroy",
            "f2m_mlp_get_params", "f2m_mlp_last_error", "f2m_mlp_forward", "f2m_mlp_grad",
-           "f2m_mlp_train", "f2m_warm_start", "f2m_set_degrees", "f2m_get_colors"]
+           "f2m_mlp_train", "f2m_warm_start", "f2m_set_degrees", "f2m_get_colors",
+           "f2m_tsplib_parse", "f2m_tsplib_last_error"]
 
 F2M_MLP_NPARAMS = 18817
 
@@ -104,6 +105,10 @@ def load(path: str = LIB_PATH):
     L.f2m_set_lambda.argtypes = [vp, vp, i32]
     L.f2m_set_degrees.argtypes = [vp, vp]
     L.f2m_get_colors.argtypes = [vp, vp, C.POINTER(i32)]
+    L.f2m_tsplib_parse.argtypes = [C.c_char_p, i64, vp, i32, C.POINTER(i32), vp]
+    L.f2m_tsplib_parse.restype = C.c_int
+    L.f2m_tsplib_last_error.argtypes = []
+    L.f2m_tsplib_last_error.restype = C.c_char_p
     L.f2m_solve.argtypes = [vp, C.POINTER(f2m_info)]
     L.f2m_gdp.argtypes = [vp, i64, C.POINTER(i64), vp, vp, i64]
     L.f2m_price.argtypes = [vp, C.POINTER(i64), vp, i64]
@@ -499,6 +504,33 @@ def _gcheck(st):
     if st != F2M_OK:
         L = load()
         raise F2MError(st, f"{L.f2m_status_string(st).decode()}: {L.f2m_last_error(None).decode()}")
+
+
+def f2m_tsplib_parse(text):
+    """TSPLIB EUC_2D problem text -> (xy int32 [n, 2] translated to start at 0,
+    (tx, ty) the translation).  Raises F2MError on anything else."""
+    data = text.encode() if isinstance(text, str) else bytes(text)
+    L = load()
+    n = C.c_int32()
+    st = L.f2m_tsplib_parse(data, len(data), None, 0, C.byref(n), None)
+    if st != F2M_OK:
+        raise F2MError(st, L.f2m_tsplib_last_error().decode())
+    xy = np.zeros((n.value, 2), np.int32)
+    tr = np.zeros(2, np.int64)
+    st = L.f2m_tsplib_parse(data, len(data), xy.ctypes.data, n.value, C.byref(n), tr.ctypes.data)
+    if st != F2M_OK:
+        raise F2MError(st, L.f2m_tsplib_last_error().decode())
+    return xy, (int(tr[0]), int(tr[1]))
+
+
+def f2m_tsplib_last_error() -> str:
+    return load().f2m_tsplib_last_error().decode()
+
+
+def read_tsplib(path):
+    """f2m_tsplib_parse of a file."""
+    with open(path, "rb") as fh:
+        return f2m_tsplib_parse(fh.read())
 
 
 def f2m_knn(xy, k: int, stream=None, with_d2: bool = True):
