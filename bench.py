@@ -128,6 +128,21 @@ def dist_env():
     return rank, world, local
 
 
+def replica_seed(w, rank):
+    """Replicas: rank r solves its own instance of the workload, seed + r."""
+    return w["seed"] + rank
+
+
+def max_over_ranks(dist, value, device="cuda"):
+    """The largest value over the ranks (the job's time is its slowest rank's)."""
+    if not dist:
+        return value
+    import torch
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_oracle_estimate(d, gpu_counts, budget_s=12.0):
     """Time the CPU oracle on bounded samples of the same instance and scale.
 
@@ -254,7 +269,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     # replicas: every rank solves its own instance of the same workload (seed + rank)
-    d = I.make_instance(w["kind"], w["n"], w["seed"] + rank, w["k"])
+    d = I.make_instance(w["kind"], w["n"], replica_seed(w, rank), w["k"])
     n, nnz0 = w["n"], int(d["row_ptr"][-1])
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
@@ -264,7 +279,7 @@ def main():
     b = None
     if args.degrees:
         lo, hi = (int(t) for t in args.degrees.split(":"))
-        key = I.stream_key(w["seed"] + rank, 91)
+        key = I.stream_key(replica_seed(w, rank), 91)
         draw = (I.draws(key, 0, n) % np.uint64(hi - lo + 1)).astype(np.int64) + lo
         b = np.minimum(draw, np.diff(d["row_ptr"]) - 1).astype(np.int32)
     variant = args.update != "jacobi" or b is not None or args.shift != 2
@@ -308,10 +323,7 @@ def main():
     for c in ctxs:
         f2m.f2m_destroy(c)
     ms = sum(step_ms) / len(step_ms)
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(dist, ms)
     for inf in infos:
         assert inf["status"] == 0 and inf["certified"] == 2, inf
 
@@ -336,10 +348,7 @@ def main():
         d2h = rp_o.nbytes + col_o.nbytes + x2_o.nbytes + cost_o.nbytes + lam_o.nbytes
         f2m.f2m_destroy(ctx)
     e2e = statistics.median(e2e_ms)
-    if dist:
-        t = torch.tensor([e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = float(t.item())
+    e2e = max_over_ranks(dist, e2e)
 
     peaks = load_peaks()
     inf0 = infos[0]
@@ -459,10 +468,7 @@ def run_batch(args, w, rank, world, local):
     for b in bs:
         f2m.f2m_destroy_batch(b)
     ms = sum(step_ms) / len(step_ms)
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(dist, ms)
     infos, tot = res[0]
     assert tot.status == 0 and tot.certified == 2, tot.as_dict()
     # end to end: create from host arrays, solve, read every instance back
@@ -483,7 +489,7 @@ def run_batch(args, w, rank, world, local):
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         f2m.f2m_destroy_batch(b)
-    e2e = statistics.median(e2e_ms)
+    e2e = max_over_ranks(dist, statistics.median(e2e_ms))
     peaks = load_peaks()
     sweeps = np.array([i.iterations for i in infos])
     gdp_bytes = float(np.sum(sweeps * (GDP_BYTES_PER_ENTRY * nnzs + GDP_BYTES_PER_NODE * ns)))
@@ -543,7 +549,7 @@ def run_warm(args, w, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    ds = [I.make_instance(kind, n, w["seed"] + rank, k) for kind, n, k in w["sizes"]]
+    ds = [I.make_instance(kind, n, replica_seed(w, rank), k) for kind, n, k in w["sizes"]]
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     m = f2m.f2m_mlp_create(W.load_weights(), stream=stream)
@@ -581,8 +587,8 @@ def run_warm(args, w, rank, world, local):
             infos[i] = (ic, iw)
     launches = f2m.f2m_kernel_launches() - launches0
     clk = clocks.stop()
-    warm_ms = sum(statistics.median(per[i]["warm"]) for i in per)
-    cold_ms = sum(statistics.median(per[i]["cold"]) for i in per)
+    warm_ms = max_over_ranks(dist, sum(statistics.median(per[i]["warm"]) for i in per))
+    cold_ms = max_over_ranks(dist, sum(statistics.median(per[i]["cold"]) for i in per))
     rows = []
     for i, (kind, n, k) in enumerate(w["sizes"]):
         ic, iw = infos[i]
@@ -607,6 +613,7 @@ def run_warm(args, w, rank, world, local):
         h2d += d["xy"].nbytes + d["row_ptr"].nbytes + d["col"].nbytes
         d2h += rp_o.nbytes + col_o.nbytes + x2_o.nbytes + cost_o.nbytes + lam_o.nbytes
         f2m.f2m_destroy(ctx)
+    e2e = max_over_ranks(dist, e2e)
     line = {"metric": METRIC + " (learned warm start, sum over the instances)", "value": warm_ms, "unit": "ms",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": warm_ms + cold_ms,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
