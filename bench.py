@@ -177,7 +177,8 @@ def cpu_oracle_estimate(d, gpu_counts, budget_s=12.0):
     sample = (f"{sweeps} oracle sweeps on the full instance ({t_sweep * 1e3:.1f} ms each) and "
               f"{pairs:.3g} oracle pricing pairs over rows 0..{rows} ({t_pair * 1e9:.2f} ns/pair), "
               f"scaled to {gpu_counts['iterations']} sweeps and {gpu_counts['pricing_rounds']} "
-              f"full scans; finisher host time added as measured")
+              + (f"full scans; finisher host time added as measured ({gpu_counts['ms_finish']:.1f} ms)"
+                 if gpu_counts["ms_finish"] > 0 else "full scans; finisher time not included"))
     return est_ms, sample
 
 
@@ -219,8 +220,8 @@ def run_reference(args, w, rank):
 # reference arm's bounded samples (a full oracle solve at n = 1e5 takes minutes).
 # c1 is small enough for the oracle to solve outright.
 REFERENCE_COUNTS: dict = {
-    "c2": {"iterations": 3717, "pricing_rounds": 3, "ms_finish": 0.0},
-    "c3": {"iterations": 3751, "pricing_rounds": 3, "ms_finish": 0.0},
+    "c2": {"iterations": 3064, "pricing_rounds": 2, "ms_finish": 0.0},
+    "c3": {"iterations": 3169, "pricing_rounds": 2, "ms_finish": 0.0},
 }
 
 
