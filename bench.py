@@ -364,8 +364,7 @@ def main():
     alu_peak = num_sms * 128 * sm_mhz * 1e6 / 1e12  # Tops/s at the sampled clock
     pr_tops = pr_pairs * PRICING_OPS_PER_PAIR / (ms_pr * 1e-3) / 1e12 if ms_pr > 0 else 0.0
     traffic = load_traffic(args.workload)
-    gdp_kernel = ("gdp_classes_kernel" if args.update == "classes" else
-                  "gdp_persistent_kernel" if b is not None else "gdp_tiled2_kernel")
+    gdp_kernel = "gdp_classes_kernel" if args.update == "classes" else "gdp_tiled2_kernel"
     if ms_gdp >= ms_pr:
         roofline = {"kernel": gdp_kernel, "bound": "hbm", "achieved": gdp_gbs,
                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gdp_gbs / peaks["hbm_gbs"],

@@ -185,7 +185,8 @@ f2m_status f2m_set_lambda(f2m_ctx* ctx, const int32_t* lambda, int32_t frac_bits
  *   b  [n] int32, host or device, copied; 1 <= b_v <= deg(v) - 1 for the
  *      graph held now (pricing only adds edges).  NULL restores b_v = 2.
  * Single-instance contexts only.  While b is set, GDP phases run on the
- * streaming kernel (the shared-memory kernels hold Eq. 10's top-3 only).
+ * two-sweep shared-memory kernel (a sorted top-8 per row when every b_v < 8,
+ * counting otherwise) or, where its tiles do not fit, the streaming kernel.
  * Errors: INVALID_ARG (range, with the first offending node in
  * f2m_last_error; the previous b stays), OOM, CUDA. */
 f2m_status f2m_set_degrees(f2m_ctx* ctx, const int32_t* b);

@@ -147,7 +147,7 @@ extern "C" void f2m_destroy(f2m_ctx* c) {
   dfree(c->d_ranges); dfree(c->d_boxes); dfree(c->d_smax);
   dfree(c->d_count); dfree(c->d_tile); dfree(c->d_deg); dfree(c->d_tmp_rp); dfree(c->d_new_rp);
   dfree(c->d_block_sums); dfree(c->d_tmp_col); dfree(c->d_out_a); dfree(c->d_out_b);
-  dfree(c->d_check); dfree(c->d_scalar); dfree(c->d_bad); dfree(c->d_b);
+  dfree(c->d_check); dfree(c->d_scalar); dfree(c->d_bad); dfree(c->d_b); dfree(c->d_b_int);
   free_finisher_buffers(c);
   if (c->fin_work) finisher_work_free(c->fin_work);
   plan2_free(c->plan);
@@ -328,6 +328,7 @@ extern "C" f2m_status f2m_set_degrees(f2m_ctx* c, const int32_t* b) {
   if (c->seg_off.size() != 2) return fail(c, F2M_ERR_INVALID_ARG, "degree requirements apply to a single-instance context");
   if (!b) {
     dfree(c->d_b);
+    dfree(c->d_b_int);
     c->b_max = 2;
     return F2M_OK;
   }
@@ -343,8 +344,15 @@ extern "C" f2m_status f2m_set_degrees(f2m_ctx* c, const int32_t* b) {
   if (e == cudaSuccess) e = read_check(c, &h);
   if (e != cudaSuccess) { dfree(d); return cuda_fail(c, e, "set_degrees"); }
   if (h.flags) { dfree(d); return fail(c, F2M_ERR_INVALID_ARG, check_message(h.flags, h.first_bad)); }
+  int32_t* di = nullptr;  // the same in the renumbered order of the tiled kernel
+  CK(c, dalloc(&di, c->n));
+  e = gather_perm(d, c->plan.perm, c->n, di, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) { dfree(d); dfree(di); return cuda_fail(c, e, "set_degrees"); }
   dfree(c->d_b);
+  dfree(c->d_b_int);
   c->d_b = d;
+  c->d_b_int = di;
   c->b_max = (int32_t)bmax;
   return F2M_OK;
 }
@@ -408,13 +416,13 @@ f2m_status f2m::gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, bool 
   }
   CK(c, cudaMemsetAsync(c->d_gdp, 0, sizeof(GdpCtl), c->st));
   CK(c, cudaEventRecord(c->ev0, c->st));
-  // the shared-memory kernels hold Eq. 10's top-3; degree requirements other
-  // than 2 run on the streaming kernel
-  bool two = c->plan.valid2 && !c->d_b;  // two sweeps per barrier
+  // degree requirements run on the two-sweep kernel or the streaming one (the
+  // one-sweep tiled kernel holds Eq. 10's top-3 only)
+  bool two = c->plan.valid2;  // two sweeps per barrier
   bool tiled = c->plan.valid && !c->d_b;
   if (two) {
     cudaError_t e = launch_gdp_tiled2(c->plan, c->d_lam[c->cur], c->p.damping_shift, max_sweeps, c->d_gdp, tb,
-                                      tc, tcap, c->p.barrier_budget_cycles, c->st);
+                                      tc, tcap, c->p.barrier_budget_cycles, c->d_b_int, c->b_max, c->st);
     if (e == cudaErrorCooperativeLaunchTooLarge) {
       cudaGetLastError();
       two = false;
@@ -449,15 +457,25 @@ f2m_status f2m::gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, bool 
       // the overflowing sweep
       const long long base = h.sweeps - 2;
       CK(c, cudaMemsetAsync(c->d_gdp, 0, sizeof(GdpCtl), c->st));
-      CK(c, launch_gdp_tiled(c->plan, c->d_lam[c->cur], c->p.damping_shift, 2, c->d_gdp,
-                             tb ? tb + base : nullptr, tc ? tc + base : nullptr,
-                             tcap > base ? tcap - base : 0, c->p.barrier_budget_cycles, c->st));
       GdpCtl h2{};
-      CK(c, cudaMemcpyAsync(&h2, c->d_gdp, sizeof(h2), cudaMemcpyDeviceToHost, c->st));
-      CK(c, cudaStreamSynchronize(c->st));
-      const bool ovf2 = (h2.status & kGdpOverflow) != 0;
-      if (!(h2.status & kGdpTimeout))
-        CK(c, plan_scatter_lambda(c->plan, (int)((ovf2 ? h2.sweeps - 1 : h2.sweeps) % 3), c->d_lam[c->cur], c->st));
+      if (c->d_b) {  // with degree requirements: the streaming kernel replays the round
+        CK(c, launch_gdp(c->d_rp, c->d_ec, c->d_b, c->b_max, c->d_lam[c->cur], c->d_lam[c->cur ^ 1], c->n, F,
+                         c->p.damping_shift, 2, c->d_gdp, tb ? tb + base : nullptr, tc ? tc + base : nullptr,
+                         tcap > base ? tcap - base : 0, c->p.barrier_budget_cycles, c->num_sms, c->st));
+        CK(c, cudaMemcpyAsync(&h2, c->d_gdp, sizeof(h2), cudaMemcpyDeviceToHost, c->st));
+        CK(c, cudaStreamSynchronize(c->st));
+        const bool ovf2 = (h2.status & kGdpOverflow) != 0;
+        if (!(h2.status & kGdpTimeout) && ((ovf2 ? h2.sweeps - 1 : h2.sweeps) & 1)) c->cur ^= 1;
+      } else {
+        CK(c, launch_gdp_tiled(c->plan, c->d_lam[c->cur], c->p.damping_shift, 2, c->d_gdp,
+                               tb ? tb + base : nullptr, tc ? tc + base : nullptr,
+                               tcap > base ? tcap - base : 0, c->p.barrier_budget_cycles, c->st));
+        CK(c, cudaMemcpyAsync(&h2, c->d_gdp, sizeof(h2), cudaMemcpyDeviceToHost, c->st));
+        CK(c, cudaStreamSynchronize(c->st));
+        const bool ovf2 = (h2.status & kGdpOverflow) != 0;
+        if (!(h2.status & kGdpTimeout))
+          CK(c, plan_scatter_lambda(c->plan, (int)((ovf2 ? h2.sweeps - 1 : h2.sweeps) % 3), c->d_lam[c->cur], c->st));
+      }
       h.status = (h.status & ~kGdpOddOverflow) | h2.status;
       h.sweeps = base + h2.sweeps;
       h.fixed_point = h2.fixed_point;

@@ -227,10 +227,11 @@ cudaError_t launch_gdp_tiled(GdpPlan& p, const int32_t* lam_in, int32_t shift, i
 // two-sweep form on top of a valid one-sweep plan of 1024-thread CTAs (valid2 false if it does not fit)
 cudaError_t plan_build2(GdpPlan& p, int32_t F, cudaStream_t st);
 void plan2_free(GdpPlan& p);
-// gathers lam_in into ilam[0], one cooperative launch; the result is in ilam[ctl->pad1]
+// gathers lam_in into ilam[0], one cooperative launch; the result is in ilam[ctl->pad1].
+// bint: degree requirements in internal order (NULL: b_v = 2), bmax their largest
 cudaError_t launch_gdp_tiled2(GdpPlan& p, const int32_t* lam_in, int32_t shift, int64_t max_sweeps, GdpCtl* ctl,
                               long long* trace_b2, unsigned long long* trace_ch, int64_t trace_cap,
-                              long long budget, cudaStream_t st);
+                              long long budget, const int32_t* bint, int32_t bmax, cudaStream_t st);
 // lam_out (caller order) = ilam[which]
 cudaError_t plan_scatter_lambda(const GdpPlan& p, int which, int32_t* lam_out, cudaStream_t st);
 

@@ -286,11 +286,68 @@ __device__ __forceinline__ void row_top3(const int2* ent, int depth, int lv, con
   top3_merge(a1, b1, c1, a, bb, cc);
 }
 
+// Degree requirements b_v (Section 3 with Eq. 8): z(b_v) and z(b_v + 1) of one
+// row, and, if BOUND, the row's sum of min(0, z).  MODE 1 (every b_v < 8):
+// the row's 8 smallest values kept sorted in registers; MODE 2: counting, the
+// entry value t being z(r) iff #{z < t} < r <= #{z <= t}.  Slice padding
+// entries have z above every real one and at least b_v + 1 entries are real.
+template <bool BOUND, int MODE>
+__device__ __forceinline__ void row_pair_deg(const int2* ent, int depth, int lv, const int* s_in, int bv,
+                                             int& z1, int& z2, long long& neg) {
+  neg = 0;
+  if constexpr (MODE == 1) {
+    int a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = INT_MAX;
+    for (int k = 0; k < depth; ++k) {
+      const int2 q = ent[k * 32];
+      const int z = q.y - lv - s_in[q.x];  // Eq. 9
+      if (BOUND) neg += min(z, 0);
+      if (z < a[7]) {
+        a[7] = z;
+#pragma unroll
+        for (int j = 7; j > 0; --j) {
+          const int lo2 = min(a[j - 1], a[j]), hi2 = max(a[j - 1], a[j]);
+          a[j - 1] = lo2;
+          a[j] = hi2;
+        }
+      }
+    }
+    z1 = INT_MAX;
+    z2 = INT_MAX;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (k == bv - 1) z1 = a[k];
+      if (k == bv) z2 = a[k];
+    }
+  } else {
+    int c1 = INT_MAX, c2 = INT_MAX;
+    for (int j = 0; j < depth; ++j) {
+      const int2 qj = ent[j * 32];
+      const int zj = qj.y - lv - s_in[qj.x];  // Eq. 9
+      if (BOUND) neg += min(zj, 0);
+      int lt = 0, le = 0;
+      for (int k = 0; k < depth; ++k) {
+        const int2 q = ent[k * 32];
+        const int z = q.y - lv - s_in[q.x];
+        lt += (z < zj);
+        le += (z <= zj);
+      }
+      if (lt < bv && bv <= le) c1 = min(c1, zj);
+      if (lt <= bv && bv + 1 <= le) c2 = min(c2, zj);
+    }
+    z1 = c1;
+    z2 = c2;
+  }
+}
+
 }  // namespace
 
-// BOUND: also sum the dual bound of every sweep (only traces need it)
-template <bool BOUND>
-__global__ void __launch_bounds__(1024, 1)
+// BOUND: also sum the dual bound of every sweep (only traces need it).
+// MODE 0: b_v = 2 (Eq. 10, top-3); 1 and 2: b_v per node from bint (internal
+// order), see row_pair_deg; these take 512 threads (more registers per row).
+template <bool BOUND, int MODE>
+__global__ void __launch_bounds__(MODE == 0 ? 1024 : 512, 1)
 gdp_tiled2_kernel(const int32_t* __restrict__ part, const int32_t* __restrict__ hcount,
                   const int32_t* __restrict__ hoff2, const int32_t* __restrict__ soff2,
                   const int32_t* __restrict__ sloff2, const int32_t* __restrict__ halo2,
@@ -298,7 +355,7 @@ gdp_tiled2_kernel(const int32_t* __restrict__ part, const int32_t* __restrict__ 
                   const int2* __restrict__ lec2, int32_t* lam0, int32_t* lam1, int32_t shift,
                   long long max_sweeps, GdpCtl* ctl, long long* trace_b2, unsigned long long* trace_ch,
                   long long trace_cap, long long budget, int32_t maxS, int32_t maxSl, int32_t maxL,
-                  int32_t maxHH) {
+                  int32_t maxHH, const int32_t* __restrict__ bint) {
   extern __shared__ __align__(16) unsigned char smem[];
   int2* s_lec = reinterpret_cast<int2*>(smem);         // sliced entries
   int2* s_slc = s_lec + maxS;                           // {offset, depth} per slice
@@ -422,16 +479,21 @@ gdp_tiled2_kernel(const int32_t* __restrict__ part, const int32_t* __restrict__ 
       const int2 sl = s_slc[s];
       const int vl = s_order[p];
       const int lv = s_A[vl];
-      int bb, cc;
+      int bb, cc, bv = 2;
       long long neg;
-      row_top3<BOUND>(s_lec + sl.x + (p & 31), sl.y, lv, s_A, bb, cc, neg);
-      const long long d = gdp_step(bb, cc, shift);  // Eq. 10, truncated toward 0
+      if constexpr (MODE == 0) {
+        row_top3<BOUND>(s_lec + sl.x + (p & 31), sl.y, lv, s_A, bb, cc, neg);
+      } else {
+        bv = __ldg(bint + (vl < own ? lo + vl : s_hid[vl - own]));
+        row_pair_deg<BOUND, MODE>(s_lec + sl.x + (p & 31), sl.y, lv, s_A, bv, bb, cc, neg);
+      }
+      const long long d = gdp_step(bb, cc, shift);  // Eq. 10 (Eq. 8), truncated toward 0
       const long long nl = (long long)lv + d;
       s_B[vl] = (int32_t)nl;
       if (is_own) {
         ovfa |= (nl >= kLamLimit || nl <= -kLamLimit);
         cha += (d != 0);
-        if (BOUND) b2a += neg + 4LL * lv;
+        if (BOUND) b2a += neg + 2LL * bv * lv;
       }
     }
     __syncthreads();
@@ -442,15 +504,20 @@ gdp_tiled2_kernel(const int32_t* __restrict__ part, const int32_t* __restrict__ 
         const int2 sl = s_slc[p >> 5];
         const int vl = s_order[p];
         const int lv = s_B[vl];
-        int bb, cc;
+        int bb, cc, bv = 2;
         long long neg;
-        row_top3<BOUND>(s_lec + sl.x + (p & 31), sl.y, lv, s_B, bb, cc, neg);
+        if constexpr (MODE == 0) {
+          row_top3<BOUND>(s_lec + sl.x + (p & 31), sl.y, lv, s_B, bb, cc, neg);
+        } else {
+          bv = __ldg(bint + lo + vl);
+          row_pair_deg<BOUND, MODE>(s_lec + sl.x + (p & 31), sl.y, lv, s_B, bv, bb, cc, neg);
+        }
         const long long d = gdp_step(bb, cc, shift);
         const long long nl = (long long)lv + d;
         s_A[vl] = (int32_t)nl;
         ovfb |= (nl >= kLamLimit || nl <= -kLamLimit);
         chb += (d != 0);
-        if (BOUND) b2b += neg + 4LL * lv;
+        if (BOUND) b2b += neg + 2LL * bv * lv;
       }
       __syncthreads();
     }
@@ -590,12 +657,20 @@ cudaError_t plan_build2(GdpPlan& p, int32_t F, cudaStream_t st) {
 
 cudaError_t launch_gdp_tiled2(GdpPlan& p, const int32_t* lam_in, int32_t shift, int64_t max_sweeps, GdpCtl* ctl,
                               long long* trace_b2, unsigned long long* trace_ch, int64_t trace_cap,
-                              long long budget, cudaStream_t st) {
+                              long long budget, const int32_t* bint, int32_t bmax, cudaStream_t st) {
   P2CK(gather_perm(lam_in, p.perm, p.n, p.ilam[0], st));
-  const void* kern = trace_cap > 0 ? (const void*)gdp_tiled2_kernel<true> : (const void*)gdp_tiled2_kernel<false>;
+  const int mode = !bint ? 0 : (bmax < 8 ? 1 : 2);
+  const bool tr = trace_cap > 0;
+  const void* kerns[2][3] = {
+      {(const void*)gdp_tiled2_kernel<false, 0>, (const void*)gdp_tiled2_kernel<false, 1>,
+       (const void*)gdp_tiled2_kernel<false, 2>},
+      {(const void*)gdp_tiled2_kernel<true, 0>, (const void*)gdp_tiled2_kernel<true, 1>,
+       (const void*)gdp_tiled2_kernel<true, 2>}};
+  const void* kern = kerns[tr ? 1 : 0][mode];
+  const int threads = mode == 0 ? 1024 : 512;
   P2CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem2));
   int per_sm = 0;
-  P2CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 1024, p.smem2));
+  P2CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, p.smem2));
   int dev = 0, sms = 0;
   P2CK(cudaGetDevice(&dev));
   P2CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -606,8 +681,9 @@ cudaError_t launch_gdp_tiled2(GdpPlan& p, const int32_t* lam_in, int32_t shift, 
   void* args[] = {(void*)&p.part, (void*)&p.hcount, (void*)&p.hoff2, (void*)&p.soff2, (void*)&p.sloff2,
                   (void*)&p.halo2, (void*)&p.order2, (void*)&p.slc2, (void*)&p.lec2, (void*)&l0, (void*)&l1,
                   (void*)&shift, (void*)&ms, (void*)&ctl, (void*)&trace_b2, (void*)&trace_ch, (void*)&tc,
-                  (void*)&budget, (void*)&p.maxS2, (void*)&p.maxSl2, (void*)&p.maxL2, (void*)&p.maxHH2};
-  cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(p.B), dim3(1024), args, p.smem2, st);
+                  (void*)&budget, (void*)&p.maxS2, (void*)&p.maxSl2, (void*)&p.maxL2, (void*)&p.maxHH2,
+                  (void*)&bint};
+  cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(p.B), dim3(threads), args, p.smem2, st);
   count_launch();
   return e;
 }

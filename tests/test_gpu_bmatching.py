@@ -46,14 +46,16 @@ CASES = [("uniform", 1000, 0, 10, (1, 4)), ("mixture", 2500, 3, 10, (1, 3)),
          ("uniform", 1500, 2, 16, (6, 14))]
 
 
+# flags 0: the two-sweep shared-memory kernel; 1: the streaming kernel
+@pytest.mark.parametrize("flags", [0, 1])
 @pytest.mark.parametrize("kind,n,seed,k,br", CASES)
-def test_gdp_phase_trace_with_b(lib, O, kind, n, seed, k, br):
+def test_gdp_phase_trace_with_b(lib, O, kind, n, seed, k, br, flags):
     d = I.make_instance(kind, n, seed, k)
     b = random_b(d["row_ptr"], *br, seed)
     cost = O.cost_table(d["xy"], d["row_ptr"], d["col"])
     st_o, lam_o, it_o, tb_o, tc_o = O.gdp(d["row_ptr"], d["col"], cost, np.zeros(n, np.int32),
                                           8, 2, 100000, trace=True, b=b)
-    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"])
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], f2m.f2m_default_params(flags=flags))
     f2m.f2m_set_degrees(ctx, b)
     st, sweeps, tb, tc = f2m.f2m_gdp(ctx, 100000, trace_cap=it_o)
     lam, fb = f2m.f2m_get_lambda(ctx)
@@ -111,14 +113,15 @@ def test_solve_with_b_bit_exact(lib, O, kind, n, seed, k, br):
 
 @pytest.mark.parametrize("kind,n,seed,k,br", [("uniform", 777, 5, 6, (1, 5)),
                                               ("mixture", 3000, 1, 12, (1, 11))])
-def test_infeasible_candidate_graph_overflows_alike(lib, O, kind, n, seed, k, br):
+@pytest.mark.parametrize("flags", [0, 1])
+def test_infeasible_candidate_graph_overflows_alike(lib, O, kind, n, seed, k, br, flags):
     # these b have no fractional b-matching on the k-NN graph: the dual is
     # unbounded and both sides stop at |lambda| = 2^29 after the same sweeps
     d = I.make_instance(kind, n, seed, k)
     b = random_b(d["row_ptr"], *br, seed + 1)
     r = O.solve(d["xy"], d["row_ptr"], d["col"], max_iters=1000000, b=b)
     assert r.status == O.OR_OVERFLOW
-    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], f2m.f2m_default_params(max_iters=1000000))
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], f2m.f2m_default_params(max_iters=1000000, flags=flags))
     f2m.f2m_set_degrees(ctx, b)
     info = f2m.f2m_solve(ctx, raise_on_error=False)
     assert info.status == f2m.F2M_ERR_OVERFLOW and info.iterations == r.iterations
