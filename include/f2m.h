@@ -137,7 +137,7 @@ typedef struct {
   int32_t status;               /* f2m_status of the solve */
   int32_t batch_shape;          /* batch totals: shape index of the batched GDP kernel; else -1 */
   int32_t batch_graph;          /* batch totals: 1 if the GDP phases ran from a captured graph */
-  int32_t reserved;
+  int32_t gdp_kernel;           /* GDP kernel of the last phase: F2M_GDP_KERNEL_* */
   double ms_gdp;                /* device time of the GDP phases */
   double ms_pricing;            /* device time of the pricing scans */
   double ms_merge;              /* device time of the CSR merges */
@@ -145,6 +145,15 @@ typedef struct {
   double ms_finish;             /* host time of the finisher incl. copies */
   double ms_total;              /* host wall time of f2m_solve */
 } f2m_info;
+
+/* f2m_info.gdp_kernel values */
+#define F2M_GDP_KERNEL_STREAMING 0     /* CSR read from global memory every sweep */
+#define F2M_GDP_KERNEL_TILED 1         /* shared-memory tiles, one sweep per barrier */
+#define F2M_GDP_KERNEL_TWO_SWEEP 2     /* shared-memory tiles, two sweeps per barrier */
+#define F2M_GDP_KERNEL_TWO_SWEEP_PACKED 3  /* the same with 4-byte entries (larger tiles) */
+#define F2M_GDP_KERNEL_CLASSES 4       /* class-by-class sweeps */
+#define F2M_GDP_KERNEL_BATCH 5         /* batched, union CSR streamed */
+#define F2M_GDP_KERNEL_BATCH_CLUSTERS 6  /* batched, one thread-block cluster per instance */
 
 /* Fills *p with the defaults above.  p must not be NULL. */
 void f2m_default_params(f2m_params* p);

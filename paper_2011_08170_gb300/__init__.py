@@ -34,6 +34,9 @@ F2M_FLAG_STREAMING_GDP = 1
 F2M_FLAG_ONE_SWEEP_GDP = 2
 F2M_FLAG_CLASS_SWEEPS = 4
 F2M_FLAG_BATCH_CLUSTERS = 8
+F2M_GDP_KERNEL_STREAMING, F2M_GDP_KERNEL_TILED, F2M_GDP_KERNEL_TWO_SWEEP = 0, 1, 2
+F2M_GDP_KERNEL_TWO_SWEEP_PACKED, F2M_GDP_KERNEL_CLASSES = 3, 4
+F2M_GDP_KERNEL_BATCH, F2M_GDP_KERNEL_BATCH_CLUSTERS = 5, 6
 
 # every symbol the header declares
 EXPORTS = ["f2m_default_params", "f2m_create", "f2m_destroy", "f2m_set_lambda", "f2m_solve",
@@ -70,12 +73,12 @@ class f2m_info(C.Structure):
                 ("finisher_calls", C.c_int64), ("augmentations", C.c_int64),
                 ("bound2", C.c_int64), ("nnz", C.c_int64), ("frac_bits", C.c_int32),
                 ("certified", C.c_int32), ("status", C.c_int32), ("batch_shape", C.c_int32),
-                ("batch_graph", C.c_int32), ("reserved", C.c_int32),
+                ("batch_graph", C.c_int32), ("gdp_kernel", C.c_int32),
                 ("ms_gdp", C.c_double), ("ms_pricing", C.c_double), ("ms_merge", C.c_double),
                 ("ms_extract", C.c_double), ("ms_finish", C.c_double), ("ms_total", C.c_double)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class F2MError(RuntimeError):

@@ -401,6 +401,7 @@ f2m_status f2m::gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, bool 
       c->classes.version = c->plan.version;
     }
     CK(c, cudaMemsetAsync(c->d_gdp, 0, sizeof(GdpCtl), c->st));
+    c->gdp_kernel = F2M_GDP_KERNEL_CLASSES;
     CK(c, launch_gdp_classes(c->d_rp, c->d_ec, c->d_b, c->b_max, c->d_lam[c->cur], c->classes, c->n,
                              F, c->p.damping_shift, max_sweeps, c->d_gdp, tb, tc, tcap,
                              c->p.barrier_budget_cycles, c->num_sms, c->st));
@@ -445,6 +446,8 @@ f2m_status f2m::gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, bool 
                      c->p.damping_shift, max_sweeps, c->d_gdp, tb, tc, tcap,
                      c->p.barrier_budget_cycles, c->num_sms, c->st));
   CK(c, cudaEventRecord(c->ev1, c->st));
+  c->gdp_kernel = two ? (c->plan.packed2 ? F2M_GDP_KERNEL_TWO_SWEEP_PACKED : F2M_GDP_KERNEL_TWO_SWEEP)
+                      : (tiled ? F2M_GDP_KERNEL_TILED : F2M_GDP_KERNEL_STREAMING);
   GdpCtl h{};
   CK(c, cudaMemcpyAsync(&h, c->d_gdp, sizeof(h), cudaMemcpyDeviceToHost, c->st));
   CK(c, cudaStreamSynchronize(c->st));
@@ -933,6 +936,7 @@ extern "C" f2m_status f2m_solve(f2m_ctx* c, f2m_info* info_out) {
     info.frac_bits = c->fb_cur;
   }
   info.nnz = c->nnz;
+  info.gdp_kernel = c->gdp_kernel;
   info.status = status;
   info.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (info_out) *info_out = info;

@@ -78,6 +78,7 @@ struct f2m_batch {
   struct ClusterClass {
     int32_t C = 0, threads = 0, emax = 0, nmax = 0;
   };
+  bool used_clusters = false;       // the last phase ran on clusters
   int64_t cl_version = -1;          // GdpPlan::version the cluster plan belongs to
   bool cl_ok = false;               // every instance fits a cluster that fits the device
   std::vector<int32_t> cl_class_of; // class (0..4: C = 1, 2, 4, 8, 16) per instance
@@ -543,12 +544,16 @@ static f2m_status batch_gdp_phase(f2m_batch* b, const std::vector<uint8_t>& acti
   }
   // clusters when asked for, unless a streaming-kernel shape is given or some
   // instance does not fit a cluster
+  b->used_clusters = false;
   if (c->p.batch_shape < 0 && (c->p.flags & F2M_FLAG_BATCH_CLUSTERS)) {
     if (b->cl_version != P.version) {
       f2m_status s = cluster_plan(b);
       if (s != F2M_OK) return s;
     }
-    if (b->cl_ok) return batch_cluster_phase(b, active, sweeps_out, ms);
+    if (b->cl_ok) {
+      b->used_clusters = true;
+      return batch_cluster_phase(b, active, sweeps_out, ms);
+    }
   }
   if (b->tiles_version != P.version) {
     f2m_status s = F2M_OK;
@@ -871,6 +876,7 @@ extern "C" f2m_status f2m_solve_batch(f2m_batch* b, f2m_info* info_out, f2m_info
   tot.nnz = b->res_used;
   tot.batch_shape = b->shape;
   tot.batch_graph = b->gexec != nullptr ? 1 : 0;
+  tot.gdp_kernel = b->used_clusters ? F2M_GDP_KERNEL_BATCH_CLUSTERS : F2M_GDP_KERNEL_BATCH;
   tot.certified = 2;
   for (int32_t s = 0; s < K; ++s) {
     tot.certified = std::min(tot.certified, certified[s]);

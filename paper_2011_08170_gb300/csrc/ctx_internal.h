@@ -41,6 +41,7 @@ struct f2m_ctx {
   int32_t* d_b = nullptr;  // degree requirements b_v, caller order (NULL: b_v = 2)
   int32_t* d_b_int = nullptr;  // the same in the renumbered (internal) order
   int32_t b_max = 2;       // the largest b_v
+  int32_t gdp_kernel = 0;  // F2M_GDP_KERNEL_* of the last GDP phase
   int cur = 0;          // d_lam[cur] holds lambda in units 2^-F
   int32_t fb_cur = 8;   // F, or F+1 while d_lam2 holds the current lambda
   f2m::GdpCtl* d_gdp = nullptr;

@@ -201,6 +201,10 @@ struct GdpPlan {
   int32_t* order2 = nullptr;     // local node of each slot
   int2* slc2 = nullptr;          // {offset, depth} per slice
   int2* lec2 = nullptr;          // sliced {local index, cost * 2^F}
+  uint32_t* lec2p = nullptr;     // the same packed as cost << 13 | local index (packed2)
+  int64_t lec2p_cap = 0;
+  bool packed2 = false;          // the kernel reads lec2p (the 8-byte tiles do not fit)
+  int32_t frac_bits2 = 8;        // F the entries were built with
   int32_t* tmp2 = nullptr;       // H2 lists during the build
   int32_t* stats2 = nullptr;
   int64_t cap2_small = 0, halo2_cap = 0, order2_cap = 0, slc2_cap = 0, lec2_cap = 0, tmp2_cap = 0;

@@ -20,6 +20,7 @@
 // that sweep) unmaterialised: the kernel reports it and the host replays the
 // round with the one-sweep kernel, which stops at the same place.
 #include <climits>
+#include <type_traits>
 #include <vector>
 
 #include "f2m_device.cuh"
@@ -261,8 +262,34 @@ __global__ void plan_map2_kernel(const int32_t* __restrict__ irp, const int2* __
 
 // one row of a slice: top-3 of z over the row (two chains) and, if BOUND, the
 // row's bound term sum min(0, z)
-template <bool BOUND>
-__device__ __forceinline__ void row_top3(const int2* ent, int depth, int lv, const int* s_in, int& bb, int& cc,
+// The sliced entries of one row (entry k of the row at index k * 32), as
+// {local index, cost * 2^F}: stored as such (8 bytes), or packed into 4 bytes
+// as cost << 13 | local index (cost below 2^19 - 1, local index below 2^13),
+// which plan_build2 chooses when the 8-byte tiles do not fit shared memory.
+struct EntWide {
+  const int2* p;
+  __device__ __forceinline__ int2 get(int k) const { return p[k * 32]; }
+};
+struct EntPacked {
+  const uint32_t* p;
+  int F;
+  __device__ __forceinline__ int2 get(int k) const {
+    const uint32_t e = p[k * 32];
+    return make_int2((int)(e & 0x1FFFu), (int)(e >> 13) << F);
+  }
+};
+template <bool PACKED>
+__device__ __forceinline__ auto make_ent(const typename std::conditional<PACKED, uint32_t, int2>::type* p, int F) {
+  if constexpr (PACKED) return EntPacked{p, F};
+  else return EntWide{p};
+}
+constexpr uint32_t kPackPadCost = (1u << 19) - 1;  // cost of a packed padding entry
+// lambda of the padding slot in the packed form: with cost kPackPadCost its z
+// is about 2^30 - lambda_v, above every real one (as the 8-byte padding's)
+constexpr int kPackPadLam = -(1 << 30) + (1 << 27);
+
+template <bool BOUND, typename E>
+__device__ __forceinline__ void row_top3(const E& ent, int depth, int lv, const int* s_in, int& bb, int& cc,
                                          long long& neg) {
   int a = INT_MAX, a1 = INT_MAX, b1 = INT_MAX, c1 = INT_MAX;
   bb = INT_MAX;
@@ -270,7 +297,7 @@ __device__ __forceinline__ void row_top3(const int2* ent, int depth, int lv, con
   neg = 0;
   int k = 0;
   for (; k + 1 < depth; k += 2) {
-    const int2 q = ent[k * 32], q1 = ent[(k + 1) * 32];
+    const int2 q = ent.get(k), q1 = ent.get(k + 1);
     const int z = q.y - lv - s_in[q.x];  // Eq. 9
     const int z1 = q1.y - lv - s_in[q1.x];
     if (BOUND) neg += min(z, 0) + min(z1, 0);
@@ -278,7 +305,7 @@ __device__ __forceinline__ void row_top3(const int2* ent, int depth, int lv, con
     top3_insert_minmax(z1, a1, b1, c1);
   }
   if (k < depth) {
-    const int2 q = ent[k * 32];
+    const int2 q = ent.get(k);
     const int z = q.y - lv - s_in[q.x];
     if (BOUND) neg += min(z, 0);
     top3_insert_minmax(z, a, bb, cc);
@@ -291,8 +318,8 @@ __device__ __forceinline__ void row_top3(const int2* ent, int depth, int lv, con
 // the row's 8 smallest values kept sorted in registers; MODE 2: counting, the
 // entry value t being z(r) iff #{z < t} < r <= #{z <= t}.  Slice padding
 // entries have z above every real one and at least b_v + 1 entries are real.
-template <bool BOUND, int MODE>
-__device__ __forceinline__ void row_pair_deg(const int2* ent, int depth, int lv, const int* s_in, int bv,
+template <bool BOUND, int MODE, typename E>
+__device__ __forceinline__ void row_pair_deg(const E& ent, int depth, int lv, const int* s_in, int bv,
                                              int& z1, int& z2, long long& neg) {
   neg = 0;
   if constexpr (MODE == 1) {
@@ -300,7 +327,7 @@ __device__ __forceinline__ void row_pair_deg(const int2* ent, int depth, int lv,
 #pragma unroll
     for (int k = 0; k < 8; ++k) a[k] = INT_MAX;
     for (int k = 0; k < depth; ++k) {
-      const int2 q = ent[k * 32];
+      const int2 q = ent.get(k);
       const int z = q.y - lv - s_in[q.x];  // Eq. 9
       if (BOUND) neg += min(z, 0);
       if (z < a[7]) {
@@ -323,12 +350,12 @@ __device__ __forceinline__ void row_pair_deg(const int2* ent, int depth, int lv,
   } else {
     int c1 = INT_MAX, c2 = INT_MAX;
     for (int j = 0; j < depth; ++j) {
-      const int2 qj = ent[j * 32];
+      const int2 qj = ent.get(j);
       const int zj = qj.y - lv - s_in[qj.x];  // Eq. 9
       if (BOUND) neg += min(zj, 0);
       int lt = 0, le = 0;
       for (int k = 0; k < depth; ++k) {
-        const int2 q = ent[k * 32];
+        const int2 q = ent.get(k);
         const int z = q.y - lv - s_in[q.x];
         lt += (z < zj);
         le += (z <= zj);
@@ -346,19 +373,21 @@ __device__ __forceinline__ void row_pair_deg(const int2* ent, int depth, int lv,
 // BOUND: also sum the dual bound of every sweep (only traces need it).
 // MODE 0: b_v = 2 (Eq. 10, top-3); 1 and 2: b_v per node from bint (internal
 // order), see row_pair_deg; these take 512 threads (more registers per row).
-template <bool BOUND, int MODE>
+template <bool BOUND, int MODE, bool PACKED>
 __global__ void __launch_bounds__(MODE == 0 ? 1024 : 512, 1)
 gdp_tiled2_kernel(const int32_t* __restrict__ part, const int32_t* __restrict__ hcount,
                   const int32_t* __restrict__ hoff2, const int32_t* __restrict__ soff2,
                   const int32_t* __restrict__ sloff2, const int32_t* __restrict__ halo2,
                   const int32_t* __restrict__ order2, const int2* __restrict__ slc2,
-                  const int2* __restrict__ lec2, int32_t* lam0, int32_t* lam1, int32_t shift,
+                  const void* __restrict__ lec2v, int32_t* lam0, int32_t* lam1, int32_t shift,
                   long long max_sweeps, GdpCtl* ctl, long long* trace_b2, unsigned long long* trace_ch,
                   long long trace_cap, long long budget, int32_t maxS, int32_t maxSl, int32_t maxL,
-                  int32_t maxHH, const int32_t* __restrict__ bint) {
+                  int32_t maxHH, const int32_t* __restrict__ bint, int32_t F) {
   extern __shared__ __align__(16) unsigned char smem[];
-  int2* s_lec = reinterpret_cast<int2*>(smem);         // sliced entries
-  int2* s_slc = s_lec + maxS;                           // {offset, depth} per slice
+  using EntT = typename std::conditional<PACKED, uint32_t, int2>::type;
+  EntT* s_lec = reinterpret_cast<EntT*>(smem);         // sliced entries
+  const int sS = PACKED ? ((maxS + 1) & ~1) : maxS;     // keeps what follows 8-byte aligned
+  int2* s_slc = reinterpret_cast<int2*>(s_lec + sS);    // {offset, depth} per slice
   int* s_order = reinterpret_cast<int*>(s_slc + maxSl); // local node of each slot
   int* s_A = s_order + 32 * maxSl;                      // lambda: own | H1 | H2 | zero
   int* s_B = s_A + maxL + 1;
@@ -377,14 +406,15 @@ gdp_tiled2_kernel(const int32_t* __restrict__ part, const int32_t* __restrict__ 
   const int sb = sloff2[b], nsl = sloff2[b + 1] - sb;
   const int nslo = (own + 31) / 32;
   const int zero_slot = own + HH;
+  const EntT* lec2 = reinterpret_cast<const EntT*>(lec2v);
   for (int e = tid; e < S; e += T) s_lec[e] = lec2[S0 + e];
   for (int s = tid; s < nsl; s += T) s_slc[s] = slc2[sb + s];
   for (int p = tid; p < 32 * nsl; p += T) s_order[p] = order2[(size_t)32 * sb + p];
   for (int h = tid; h < HH; h += T) s_hid[h] = halo2[hb + h];
   for (int i = tid; i < own; i += T) s_A[i] = lam0[lo + i];
   if (tid == 0) {
-    s_A[zero_slot] = 0;
-    s_B[zero_slot] = 0;
+    s_A[zero_slot] = PACKED ? kPackPadLam : 0;
+    s_B[zero_slot] = PACKED ? kPackPadLam : 0;
   }
   __syncthreads();
   volatile GdpCtl* vc = ctl;
@@ -481,11 +511,12 @@ gdp_tiled2_kernel(const int32_t* __restrict__ part, const int32_t* __restrict__ 
       const int lv = s_A[vl];
       int bb, cc, bv = 2;
       long long neg;
+      const auto ent = make_ent<PACKED>(s_lec + sl.x + (p & 31), F);
       if constexpr (MODE == 0) {
-        row_top3<BOUND>(s_lec + sl.x + (p & 31), sl.y, lv, s_A, bb, cc, neg);
+        row_top3<BOUND>(ent, sl.y, lv, s_A, bb, cc, neg);
       } else {
         bv = __ldg(bint + (vl < own ? lo + vl : s_hid[vl - own]));
-        row_pair_deg<BOUND, MODE>(s_lec + sl.x + (p & 31), sl.y, lv, s_A, bv, bb, cc, neg);
+        row_pair_deg<BOUND, MODE>(ent, sl.y, lv, s_A, bv, bb, cc, neg);
       }
       const long long d = gdp_step(bb, cc, shift);  // Eq. 10 (Eq. 8), truncated toward 0
       const long long nl = (long long)lv + d;
@@ -506,11 +537,12 @@ gdp_tiled2_kernel(const int32_t* __restrict__ part, const int32_t* __restrict__ 
         const int lv = s_B[vl];
         int bb, cc, bv = 2;
         long long neg;
+        const auto ent = make_ent<PACKED>(s_lec + sl.x + (p & 31), F);
         if constexpr (MODE == 0) {
-          row_top3<BOUND>(s_lec + sl.x + (p & 31), sl.y, lv, s_B, bb, cc, neg);
+          row_top3<BOUND>(ent, sl.y, lv, s_B, bb, cc, neg);
         } else {
           bv = __ldg(bint + lo + vl);
-          row_pair_deg<BOUND, MODE>(s_lec + sl.x + (p & 31), sl.y, lv, s_B, bv, bb, cc, neg);
+          row_pair_deg<BOUND, MODE>(ent, sl.y, lv, s_B, bv, bb, cc, neg);
         }
         const long long d = gdp_step(bb, cc, shift);
         const long long nl = (long long)lv + d;
@@ -574,13 +606,16 @@ gdp_tiled2_kernel(const int32_t* __restrict__ part, const int32_t* __restrict__ 
 
 void plan2_free(GdpPlan& p) {
   void* ptrs[] = {p.h2count, p.hhcount, p.s2count, p.nslc, p.hoff2, p.soff2, p.sloff2, p.halo2,
-                  p.order2, p.slc2, p.lec2, p.tmp2, p.stats2};
+                  p.order2, p.slc2, p.lec2, p.tmp2, p.stats2, p.lec2p};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   p.h2count = p.hhcount = p.s2count = p.nslc = p.hoff2 = p.soff2 = p.sloff2 = p.halo2 = p.order2 = nullptr;
   p.tmp2 = p.stats2 = nullptr;
   p.slc2 = nullptr;
   p.lec2 = nullptr;
+  p.lec2p = nullptr;
+  p.lec2p_cap = 0;
+  p.packed2 = false;
   p.cap2_small = p.halo2_cap = p.order2_cap = p.slc2_cap = p.lec2_cap = p.tmp2_cap = 0;
   p.valid2 = false;
 }
@@ -590,6 +625,19 @@ void plan2_free(GdpPlan& p) {
     cudaError_t e_ = (call);                    \
     if (e_ != cudaSuccess) return e_;           \
   } while (0)
+
+// 4-byte form of the sliced entries: cost << 13 | local index; the padding
+// entries (cost field 1 << 30) become kPackPadCost.  *bad counts entries that
+// do not pack (cost >= kPackPadCost or local index >= 2^13).
+__global__ void plan_pack2_kernel(const int2* __restrict__ lec, int32_t m, int32_t F, uint32_t* __restrict__ out,
+                                  int32_t* bad) {
+  F2M_GRID_STRIDE2(i, m) {
+    const int2 q = lec[i];
+    const uint32_t c = q.y == (1 << 30) ? kPackPadCost : (uint32_t)(q.y >> F);
+    if ((q.y != (1 << 30) && c >= kPackPadCost) || q.x < 0 || q.x >= (1 << 13)) atomicAdd(bad, 1);
+    out[i] = (c << 13) | (uint32_t)(q.x & 0x1FFF);
+  }
+}
 
 cudaError_t plan_build2(GdpPlan& p, int32_t F, cudaStream_t st) {
   p.valid2 = false;
@@ -621,13 +669,22 @@ cudaError_t plan_build2(GdpPlan& p, int32_t F, cudaStream_t st) {
   P2CK(cudaMemcpyAsync(stats, p.stats2, sizeof(stats), cudaMemcpyDeviceToHost, st));
   P2CK(cudaStreamSynchronize(st));
   if (stats[4]) return cudaSuccess;
-  const int64_t smem = 8LL * stats[0] + 8LL * stats[1] + 4LL * 32 * stats[1] + 8LL * (stats[2] + 1) +
-                       4LL * stats[3];
+  // shared memory per CTA: entries (8 bytes, or 4 packed), slices, slot
+  // order, two lambda buffers, halo ids
+  const int64_t rest = 8LL * stats[1] + 4LL * 32 * stats[1] + 8LL * (stats[2] + 1) + 4LL * stats[3];
+  const int64_t smem8 = 8LL * stats[0] + rest;
+  const int64_t smem4 = 4LL * ((stats[0] + 1) & ~1) + rest;
   int dev = 0, smem_optin = 0, smem_sm = 0;
   P2CK(cudaGetDevice(&dev));
   P2CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   P2CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-  if (smem > smem_optin || smem > smem_sm - 2048) return cudaSuccess;  // does not fit: one-sweep form
+  auto fits = [&](int64_t m) { return m <= smem_optin && m <= smem_sm - 2048; };
+  bool packed = false;
+  if (!fits(smem8)) {
+    if (!fits(smem4) || stats[2] + 1 >= (1 << 13)) return cudaSuccess;  // does not fit: one-sweep form
+    packed = true;
+  }
+  const int64_t smem = packed ? smem4 : smem8;
   P2CK(launch_scan(p.hhcount, p.hoff2, B, p.scan_tmp, st));
   P2CK(launch_scan(p.s2count, p.soff2, B, p.scan_tmp, st));
   P2CK(launch_scan(p.nslc, p.sloff2, B, p.scan_tmp, st));
@@ -646,11 +703,26 @@ cudaError_t plan_build2(GdpPlan& p, int32_t F, cudaStream_t st) {
                                              p.hoff2, p.soff2, p.sloff2, F, p.halo2, p.order2, p.slc2, p.lec2);
   count_launch();
   P2CK(cudaGetLastError());
+  p.packed2 = false;
+  if (packed) {  // 4-byte entries, if every cost is below the padding cost
+    P2CK(grow2(&p.lec2p, &p.lec2p_cap, tot[1] > 0 ? tot[1] : 1));
+    P2CK(cudaMemsetAsync(p.stats2, 0, sizeof(int32_t), st));
+    plan_pack2_kernel<<<(tot[1] + 255) / 256 > 0 ? (tot[1] + 255) / 256 : 1, 256, 0, st>>>(
+        p.lec2, tot[1], F, p.lec2p, p.stats2);
+    count_launch();
+    P2CK(cudaGetLastError());
+    int32_t bad = 0;
+    P2CK(cudaMemcpyAsync(&bad, p.stats2, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    P2CK(cudaStreamSynchronize(st));
+    if (bad) return cudaSuccess;  // some cost too large to pack: one-sweep form
+    p.packed2 = true;
+  }
   p.maxS2 = stats[0];
   p.maxSl2 = stats[1];
   p.maxL2 = stats[2];
   p.maxHH2 = stats[3];
   p.smem2 = (size_t)smem;
+  p.frac_bits2 = F;
   p.valid2 = true;
   return cudaSuccess;
 }
@@ -661,12 +733,18 @@ cudaError_t launch_gdp_tiled2(GdpPlan& p, const int32_t* lam_in, int32_t shift, 
   P2CK(gather_perm(lam_in, p.perm, p.n, p.ilam[0], st));
   const int mode = !bint ? 0 : (bmax < 8 ? 1 : 2);
   const bool tr = trace_cap > 0;
-  const void* kerns[2][3] = {
-      {(const void*)gdp_tiled2_kernel<false, 0>, (const void*)gdp_tiled2_kernel<false, 1>,
-       (const void*)gdp_tiled2_kernel<false, 2>},
-      {(const void*)gdp_tiled2_kernel<true, 0>, (const void*)gdp_tiled2_kernel<true, 1>,
-       (const void*)gdp_tiled2_kernel<true, 2>}};
-  const void* kern = kerns[tr ? 1 : 0][mode];
+  const void* kerns[2][2][3] = {
+      {{(const void*)gdp_tiled2_kernel<false, 0, false>, (const void*)gdp_tiled2_kernel<false, 1, false>,
+        (const void*)gdp_tiled2_kernel<false, 2, false>},
+       {(const void*)gdp_tiled2_kernel<true, 0, false>, (const void*)gdp_tiled2_kernel<true, 1, false>,
+        (const void*)gdp_tiled2_kernel<true, 2, false>}},
+      {{(const void*)gdp_tiled2_kernel<false, 0, true>, (const void*)gdp_tiled2_kernel<false, 1, true>,
+        (const void*)gdp_tiled2_kernel<false, 2, true>},
+       {(const void*)gdp_tiled2_kernel<true, 0, true>, (const void*)gdp_tiled2_kernel<true, 1, true>,
+        (const void*)gdp_tiled2_kernel<true, 2, true>}}};
+  const void* kern = kerns[p.packed2 ? 1 : 0][tr ? 1 : 0][mode];
+  const void* lec = p.packed2 ? (const void*)p.lec2p : (const void*)p.lec2;
+  int32_t F = p.frac_bits2;
   const int threads = mode == 0 ? 1024 : 512;
   P2CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem2));
   int per_sm = 0;
@@ -679,10 +757,10 @@ cudaError_t launch_gdp_tiled2(GdpPlan& p, const int32_t* lam_in, int32_t shift, 
   int32_t* l0 = p.ilam[0];
   int32_t* l1 = p.ilam[1];
   void* args[] = {(void*)&p.part, (void*)&p.hcount, (void*)&p.hoff2, (void*)&p.soff2, (void*)&p.sloff2,
-                  (void*)&p.halo2, (void*)&p.order2, (void*)&p.slc2, (void*)&p.lec2, (void*)&l0, (void*)&l1,
+                  (void*)&p.halo2, (void*)&p.order2, (void*)&p.slc2, (void*)&lec, (void*)&l0, (void*)&l1,
                   (void*)&shift, (void*)&ms, (void*)&ctl, (void*)&trace_b2, (void*)&trace_ch, (void*)&tc,
                   (void*)&budget, (void*)&p.maxS2, (void*)&p.maxSl2, (void*)&p.maxL2, (void*)&p.maxHH2,
-                  (void*)&bint};
+                  (void*)&bint, (void*)&F};
   cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(p.B), dim3(threads), args, p.smem2, st);
   count_launch();
   return e;

@@ -416,3 +416,30 @@ def test_gdp_full_size_sampled(lib, O):
     # one more oracle sweep from the GPU fixed point changes nothing
     st1, lam1, b2, ch = O.sweep(rp, col, cost, lam, 8, 2)
     assert ch == 0 and np.array_equal(lam1, lam)
+
+
+def test_two_sweep_packed_entries_at_full_size(lib, O):
+    # the 200,000-point clustered workload (k = 12): the 8-byte two-sweep tiles
+    # do not fit shared memory, the packed (4-byte) ones do.  The packed
+    # kernel's sweeps equal the one-sweep kernel's, and its last sweep equals
+    # the oracle's sweep from the GPU's previous lambda.
+    d = inst("mixture", 200000, 0, 12)
+    rp, col = d["row_ptr"], d["col"]
+    p0 = f2m.f2m_default_params(pricing=0, finisher=0, max_iters=60)
+    info = f2m.f2m_solve(f2m.f2m_create(d["xy"], rp, col, p0), raise_on_error=False)
+    assert info.gdp_kernel == f2m.F2M_GDP_KERNEL_TWO_SWEEP_PACKED and info.iterations == 60
+    runs = {}
+    for flags in (0, f2m.F2M_FLAG_ONE_SWEEP_GDP):
+        ctx = f2m.f2m_create(d["xy"], rp, col, f2m.f2m_default_params(flags=flags))
+        _, sw1, tb, tc = f2m.f2m_gdp(ctx, 59, trace_cap=59)
+        lam59, _ = f2m.f2m_get_lambda(ctx)
+        f2m.f2m_gdp(ctx, 1)
+        lam60, _ = f2m.f2m_get_lambda(ctx)
+        runs[flags] = (sw1, tb, tc, lam59, lam60)
+    a, b = runs[0], runs[f2m.F2M_FLAG_ONE_SWEEP_GDP]
+    assert a[0] == b[0] == 59
+    for x, y in zip(a[1:], b[1:]):
+        assert np.array_equal(x, y)
+    cost = O.cost_table(d["xy"], rp, col)
+    st, lam_o, _, _ = O.sweep(rp, col, cost, a[3], 8, 2)
+    assert st == O.OR_OK and np.array_equal(lam_o, a[4])
