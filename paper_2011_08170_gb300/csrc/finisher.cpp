@@ -42,7 +42,10 @@
 // ids here: L_i = i, R_i = n + i; key(L_i) = 2i, key(R_i) = 2i + 1.
 #include <algorithm>
 #include <atomic>
+#include <condition_variable>
 #include <cstdint>
+#include <functional>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -92,6 +95,64 @@ struct Searcher {
 
 constexpr int32_t kFinBlock = 2048;  // nodes per phase-1 block
 
+// Worker threads kept for the life of the process (one pool, shared by every
+// context; jobs from different host threads take turns): a job is a count of
+// items handed out by an atomic counter to the calling thread and the workers.
+struct WorkerPool {
+  std::vector<std::thread> threads;
+  std::mutex mu;
+  std::condition_variable cv_job, cv_done;
+  uint64_t generation = 0;  // bumped for every job
+  int32_t busy = 0;         // workers still on the current job
+  bool quit = false;
+  std::function<void(int32_t)> job;  // runs as worker k (k >= 1)
+  int32_t job_workers = 0;           // workers 1 .. job_workers - 1 take part
+
+  void start(int32_t nw) {  // nw - 1 threads (the caller is worker 0)
+    for (int32_t k = (int32_t)threads.size() + 1; k < nw; ++k)
+      threads.emplace_back([this, k] {
+        uint64_t seen = 0;
+        for (;;) {
+          std::function<void(int32_t)> fn;
+          {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_job.wait(lk, [&] { return quit || generation != seen; });
+            if (quit) return;
+            seen = generation;
+            if (k >= job_workers) continue;
+            fn = job;
+          }
+          fn(k);
+          std::lock_guard<std::mutex> lk(mu);
+          if (--busy == 0) cv_done.notify_all();
+        }
+      });
+  }
+  void run(int32_t nw, const std::function<void(int32_t)>& fn) {
+    start(nw);
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      job = fn;
+      job_workers = nw;
+      busy = nw - 1;
+      ++generation;
+    }
+    cv_job.notify_all();
+    fn(0);
+    std::unique_lock<std::mutex> lk(mu);
+    cv_done.wait(lk, [&] { return busy == 0; });
+    job = nullptr;
+  }
+  ~WorkerPool() {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      quit = true;
+    }
+    cv_job.notify_all();
+    for (std::thread& t : threads) t.join();
+  }
+};
+
 struct FinisherWork {
   std::vector<int64_t> pi, dist;
   std::vector<int32_t> excess, via, pred;
@@ -99,6 +160,12 @@ struct FinisherWork {
   std::atomic<uint32_t> stamp{0};
   std::vector<Searcher> workers;
 };
+
+WorkerPool& worker_pool() {
+  static WorkerPool pool;
+  return pool;
+}
+std::mutex g_pool_turn;  // one job at a time
 
 FinisherWork* finisher_work_new() { return new FinisherWork(); }
 void finisher_work_free(FinisherWork* w) { delete w; }
@@ -233,10 +300,8 @@ int run_items(int32_t count, int32_t threads, FinisherWork* w, std::vector<int64
   if (nw == 1) {
     run(0);
   } else {
-    std::vector<std::thread> pool;
-    for (int32_t k = 1; k < nw; ++k) pool.emplace_back(run, k);
-    run(0);
-    for (std::thread& th : pool) th.join();
+    std::lock_guard<std::mutex> turn(g_pool_turn);
+    worker_pool().run(nw, run);
   }
   return status.load();
 }
