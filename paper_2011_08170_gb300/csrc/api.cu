@@ -9,6 +9,8 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <map>
+#include <mutex>
 #include <climits>
 #include <cstdio>
 #include <cstring>
@@ -34,12 +36,57 @@ extern "C" int64_t f2m_kernel_launches(void) { return g_kernel_launches.load(); 
 
 
 
+// Pinned host blocks are costly to allocate (about a millisecond for the
+// finisher's mirrors of a 100k-node graph), so freed blocks are kept for the
+// next context, up to 2 GiB; a block is reused for a request of at least half
+// its size.
+namespace {
+std::mutex g_pin_mu;
+std::multimap<size_t, void*> g_pin_free;       // size -> cached block
+std::map<void*, size_t> g_pin_size;            // every block handed out or cached
+size_t g_pin_cached = 0;
+constexpr size_t kPinCacheMax = (size_t)1 << 31;
+
+cudaError_t pin_alloc(void** p, size_t bytes) {
+  if (bytes == 0) bytes = 1;
+  {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    auto it = g_pin_free.lower_bound(bytes);
+    if (it != g_pin_free.end() && it->first <= 2 * bytes) {
+      *p = it->second;
+      g_pin_cached -= it->first;
+      g_pin_free.erase(it);
+      return cudaSuccess;
+    }
+  }
+  cudaError_t e = cudaMallocHost(p, bytes);
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_size[*p] = bytes;
+  }
+  return e;
+}
+
+void pin_free(void* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  auto it = g_pin_size.find(p);
+  if (it == g_pin_size.end()) return;
+  if (g_pin_cached + it->second <= kPinCacheMax) {
+    g_pin_free.emplace(it->second, p);
+    g_pin_cached += it->second;
+  } else {
+    cudaFreeHost(p);
+    g_pin_size.erase(it);
+  }
+}
+}  // namespace
+
 static void free_finisher_buffers(f2m_ctx* c) {
   if (c->d_twin) cudaFree(c->d_twin);
   if (c->d_fy) cudaFree(c->d_fy);
   void* hp[] = {c->h_irp, c->h_iec, c->h_twin, c->h_y, c->h_exl, c->h_lam, c->h_lam2};
-  for (void* q : hp)
-    if (q) cudaFreeHost(q);
+  for (void* q : hp) pin_free(q);
   c->d_twin = nullptr; c->d_fy = nullptr;
   c->h_irp = nullptr; c->h_iec = nullptr; c->h_twin = nullptr; c->h_y = nullptr;
   c->h_exl = nullptr; c->h_lam = nullptr; c->h_lam2 = nullptr;
@@ -54,9 +101,9 @@ static cudaError_t alloc_finisher_buffers(f2m_ctx* c, int64_t cap) {
   const bool first = c->h_irp == nullptr;
   if (c->d_twin) cudaFree(c->d_twin);
   if (c->d_fy) cudaFree(c->d_fy);
-  if (c->h_iec) cudaFreeHost(c->h_iec);
-  if (c->h_twin) cudaFreeHost(c->h_twin);
-  if (c->h_y) cudaFreeHost(c->h_y);
+  pin_free(c->h_iec);
+  pin_free(c->h_twin);
+  pin_free(c->h_y);
   c->d_twin = nullptr; c->d_fy = nullptr;
   c->h_iec = nullptr; c->h_twin = nullptr; c->h_y = nullptr;
   c->fin_cap = 0;
@@ -64,14 +111,14 @@ static cudaError_t alloc_finisher_buffers(f2m_ctx* c, int64_t cap) {
   c->twin_version = -1;
   cudaError_t e = cudaMalloc((void**)&c->d_twin, sizeof(int32_t) * cap);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_fy, cap);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_iec, sizeof(int2) * cap);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_twin, sizeof(int32_t) * cap);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_y, cap);
+  if (e == cudaSuccess) e = pin_alloc((void**)&c->h_iec, sizeof(int2) * cap);
+  if (e == cudaSuccess) e = pin_alloc((void**)&c->h_twin, sizeof(int32_t) * cap);
+  if (e == cudaSuccess) e = pin_alloc((void**)&c->h_y, cap);
   if (e == cudaSuccess && first) {
-    e = cudaMallocHost((void**)&c->h_irp, sizeof(int32_t) * (n + 1));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_exl, sizeof(int32_t) * n);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_lam, sizeof(int32_t) * n);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_lam2, sizeof(int32_t) * n);
+    e = pin_alloc((void**)&c->h_irp, sizeof(int32_t) * (n + 1));
+    if (e == cudaSuccess) e = pin_alloc((void**)&c->h_exl, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = pin_alloc((void**)&c->h_lam, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = pin_alloc((void**)&c->h_lam2, sizeof(int32_t) * n);
   }
   if (e == cudaSuccess) c->fin_cap = cap;
   return e;
