@@ -193,9 +193,10 @@ def run_reference(args, w, rank):
     # the oracle's own counts are not affordable at this size; the sweep and
     # round counts of the method are those the oracle would take (the GPU path
     # is bit-exact with it), fixed here per workload from the solve record
-    counts = REFERENCE_COUNTS.get(args.workload)
+    mi = args.max_iters or 256  # the oracle's default, the library's too
+    counts = REFERENCE_COUNTS.get((args.workload, "fixed point" if mi >= 10 ** 5 else mi))
     if counts is None:
-        r = oracle.solve(d["xy"], d["row_ptr"], d["col"], max_iters=1000000)
+        r = oracle.solve(d["xy"], d["row_ptr"], d["col"], max_iters=mi)
         counts = {"iterations": r.iterations, "pricing_rounds": r.pricing_rounds, "ms_finish": 0.0}
     times = []
     sample = ""
@@ -207,21 +208,25 @@ def run_reference(args, w, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": v,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic", "config": {"workload": workload_name(w), "n": w["n"], "k": w["k"]},
+            "data": "synthetic", "config": {"workload": workload_name(w), "n": w["n"], "k": w["k"],
+                                            "max_iters": mi},
             "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-# Sweep and pricing-round counts of the certified solve of each workload.  The
-# method is deterministic and the CUDA path is bit-exact with the oracle, so
-# these are the counts the oracle itself would take; they only scale the CPU
-# reference arm's bounded samples (a full oracle solve at n = 1e5 takes minutes).
-# c1 is small enough for the oracle to solve outright.
+# Sweep and pricing-round counts of the certified solve of each workload, at
+# 256 sweeps per GDP phase (the oracle's own counts, recorded with its solve in
+# tests/golden/full_size_solves.json) and with every phase run to its fixed
+# point.  They only scale the CPU reference arm's bounded samples (a full
+# oracle solve at n = 1e5 takes a minute or more).  c1 is small enough for the
+# oracle to solve outright.
 REFERENCE_COUNTS: dict = {
-    "c2": {"iterations": 3064, "pricing_rounds": 2, "ms_finish": 0.0},
-    "c3": {"iterations": 3169, "pricing_rounds": 2, "ms_finish": 0.0},
+    ("c2", 256): {"iterations": 256, "pricing_rounds": 2, "ms_finish": 0.0},
+    ("c3", 256): {"iterations": 256, "pricing_rounds": 2, "ms_finish": 0.0},
+    ("c2", "fixed point"): {"iterations": 3064, "pricing_rounds": 2, "ms_finish": 0.0},
+    ("c3", "fixed point"): {"iterations": 3169, "pricing_rounds": 2, "ms_finish": 0.0},
 }
 
 
@@ -245,6 +250,9 @@ def main():
     ap.add_argument("--update", default="jacobi", choices=["jacobi", "classes"],
                     help="single instance: Jacobi sweeps (Section 5.1, the headline) or class-by-class sweeps")
     ap.add_argument("--shift", type=int, default=2, help="damping shift of the GDP step")
+    ap.add_argument("--max-iters", type=int, default=None,
+                    help="sweeps per GDP phase (default: the library's, 256); 1000000 runs every phase "
+                         "to its fixed point")
     ap.add_argument("--degrees", default=None,
                     help="single instance: degree requirements b_v drawn uniformly from LO:HI (capped at "
                          "deg(v) - 1), the fractional b-matching LP instead of F2M")
@@ -293,6 +301,8 @@ def main():
 
     # warm-up solves (also load the module, JIT nothing)
     params = f2m.f2m_default_params(pricing=args.pricing, flags=flags, damping_shift=args.shift)
+    if args.max_iters:
+        params.max_iters = args.max_iters
     for _ in range(args.warmup):
         ctx = make_ctx(d["xy"], d["row_ptr"], d["col"])
         f2m.f2m_solve(ctx)
@@ -388,7 +398,7 @@ def main():
             "config": {"workload": workload_name(w) + ("" if args.pricing == 1 else
                                                        "; pricing skips tile pairs too far apart to hold z < 0"),
                        "pricing": "full" if args.pricing == 1 else "culled", "n": n, "k": w["k"], "nnz": nnz0,
-                       "update": args.update, "damping_shift": args.shift,
+                       "update": args.update, "damping_shift": args.shift, "max_iters": int(params.max_iters),
                        "degrees": ("2 (F2M)" if b is None else
                                    f"b_v uniform in {args.degrees.replace(':', '..')}, capped at deg(v)-1"),
                        "l2": "flushed before every timed step (256 MB device write)",
@@ -436,6 +446,8 @@ def run_batch(args, w, rank, world, local):
     ds = [I.make_instance(*sp) for sp in specs]
     params = f2m.f2m_default_params(batch_shape=args.batch_shape, pricing=args.pricing,
                                     flags=f2m.F2M_FLAG_BATCH_CLUSTERS if args.batch_clusters else 0)
+    if args.max_iters:
+        params.max_iters = args.max_iters
     insts = [(d["xy"], d["row_ptr"], d["col"]) for d in ds]
     ns = np.array([d["xy"].shape[0] for d in ds])
     nnzs = np.array([int(d["row_ptr"][-1]) for d in ds])
@@ -515,6 +527,7 @@ def run_batch(args, w, rank, world, local):
                        workload_name(w) + f" (first {len(ns)} instances)", "instances": int(len(ns)),
                        "sum_n": int(ns.sum()), "kernel_shape": int(tot.batch_shape), "graph": bool(tot.batch_graph),
                        "gdp_path": "clusters" if args.batch_clusters else "streaming",
+                       "max_iters": int(params.max_iters),
                        "sum_nnz": int(nnzs.sum()), "l2": "working set larger than L2; flushed before every step",
                        "parallelism": f"replicas x{world}"},
             "breakdown_ms": {k: statistics.median(getattr(r[1], k) for r in res)
@@ -553,9 +566,12 @@ def run_warm(args, w, rank, world, local):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     m = f2m.f2m_mlp_create(W.load_weights(), stream=stream)
+    params = f2m.f2m_default_params()
+    if args.max_iters:
+        params.max_iters = args.max_iters
 
     def one(d, warm):
-        ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], stream=stream)
+        ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], params=params, stream=stream)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         flush.fill_(1)
@@ -603,7 +619,7 @@ def run_warm(args, w, rank, world, local):
     h2d = d2h = 0
     for d in ds:
         t0 = time.perf_counter()
-        ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], stream=stream)
+        ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], params=params, stream=stream)
         f2m.f2m_warm_start(ctx, m)
         f2m.f2m_solve(ctx)
         rp_o, col_o, x2_o, cost_o = f2m.f2m_get_x(ctx)
@@ -619,7 +635,7 @@ def run_warm(args, w, rank, world, local):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
             "config": {"workload": workload_name(w), "l2": "flushed before every solve (256 MB device write)",
-                       "parallelism": f"replicas x{world}"},
+                       "max_iters": int(params.max_iters), "parallelism": f"replicas x{world}"},
             "cold_start_ms": cold_ms, "instances": rows,
             "e2e": {"value": e2e, "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "clocks": clk, "gpu_launches": int(launches)}

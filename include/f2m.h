@@ -69,7 +69,10 @@ typedef struct f2m_ctx f2m_ctx;   /* opaque, library-owned */
 typedef struct {
   int32_t frac_bits;            /* F, fractional bits of lambda; 1..8; default 8 */
   int32_t damping_shift;        /* delta = trunc((z2+z3) / 2^shift); 1..8; default 2 */
-  int64_t max_iters;            /* sweeps per GDP phase; default 1,000,000 */
+  int64_t max_iters;            /* sweeps per GDP phase; default 256.  A phase ends at a
+                                   fixed point or after max_iters sweeps; f2m_solve then goes
+                                   on from the lambda reached (pricing, rule (7), finisher), so
+                                   the certified optimum does not depend on it */
   int32_t max_pricing_rounds;   /* pricing scans per solve; default 64 */
   int32_t pricing;              /* 0 = solve on the candidate graph only, 1 = full scan of all
                                    n(n-1)/2 pairs (default), 2 = the same scan skipping tile pairs

@@ -294,9 +294,11 @@ class OracleResult:
         return self.bound2 / (2.0 * (1 << self.frac_bits))
 
 
-def solve(xy, row_ptr, col, lam0=None, F=8, shift=2, max_iters=200000, max_pricing_rounds=64,
+def solve(xy, row_ptr, col, lam0=None, F=8, shift=2, max_iters=256, max_pricing_rounds=64,
           pricing=True, finisher=True, trace_cap=0, b=None, classes=False) -> OracleResult:
-    """classes: class-by-class (Gauss-Seidel) sweeps instead of Jacobi."""
+    """max_iters: sweeps per GDP phase (a phase also ends at a fixed point; the
+    solve goes on from the lambda reached either way).  classes: class-by-class
+    (Gauss-Seidel) sweeps instead of Jacobi."""
     xy, row_ptr, col = _i32(xy), _i32(row_ptr), _i32(col)
     n = row_ptr.size - 1
     bb = _degrees(b, n)

@@ -27,7 +27,8 @@
  *   - Precision: lambda in fixed point, F = 8 fractional bits, int32; the
  *     quotient is truncated toward zero (C division), which leaves a symmetric
  *     dead zone so an exact fixed point exists.
- *   - Stop: a sweep that changes no lambda, or max_iters sweeps.
+ *   - Stop: a sweep that changes no lambda, or max_iters sweeps; either way the
+ *     solve goes on from the lambda reached (pricing, rule (7), finisher).
  *   - Degenerate stops (Section 3, last paragraph: the constraint values are not
  *     controlled) are resolved by an exact min-cost-flow finisher.
  *   - Candidate graphs can miss optimal edges (Section 5.3); a pricing scan over

@@ -152,7 +152,7 @@ extern "C" void f2m_default_params(f2m_params* p) {
   if (!p) return;
   p->frac_bits = 8;
   p->damping_shift = 2;
-  p->max_iters = 1000000;
+  p->max_iters = 256;
   p->max_pricing_rounds = 64;
   p->pricing = 1;
   p->pricing_cap = 1 << 20;

@@ -1,0 +1,66 @@
+"""Writes full_size_solves.json: the CPU oracle's complete solve of the full-size
+single-instance workloads, at the default of 256 sweeps per GDP phase.
+
+Calls only the oracle (and the seeded instance generator).  The GPU test
+compares the library's solve of the same instance with these records: the
+counters of the solve, the optimum, and SHA-256 digests of the final candidate
+graph, x and lambda.  One oracle solve takes about 70 s (n = 100,000) and
+several minutes (n = 200,000) on one core.
+
+    python tests/golden/make_full_size_solves.py [name ...]
+"""
+import hashlib
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import instances as I  # noqa: E402
+import oracle  # noqa: E402
+
+CASES = {
+    "uniform_n100000_k10_seed0": ("uniform", 100_000, 0, 10),
+    "mixture_n200000_k12_seed0": ("mixture", 200_000, 0, 12),
+}
+MAX_ITERS = 256
+OUT = os.path.join(HERE, "full_size_solves.json")
+
+
+def digest(a, dtype):
+    return hashlib.sha256(np.ascontiguousarray(a, dtype=dtype).tobytes()).hexdigest()
+
+
+def record(kind, n, seed, k):
+    d = I.make_instance(kind, n, seed, k)
+    t = time.time()
+    r = oracle.solve(d["xy"], d["row_ptr"], d["col"], max_iters=MAX_ITERS)
+    rec = {"kind": kind, "n": n, "seed": seed, "k": k, "max_iters": MAX_ITERS,
+           "oracle_seconds": round(time.time() - t, 1)}
+    for f in ("status", "iterations", "phases", "pricing_rounds", "edges_added", "finisher_calls",
+              "augmentations", "bound2", "frac_bits", "certified"):
+        rec[f] = int(getattr(r, f))
+    rec["nnz"] = int(r.row_ptr[-1])
+    rec["sha256"] = {"row_ptr": digest(r.row_ptr, "<i4"), "col": digest(r.col, "<i4"),
+                     "x2": digest(r.x2, "u1"), "lam": digest(r.lam, "<i4")}
+    return rec
+
+
+def main(names):
+    oracle.build()
+    out = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    for name in names or list(CASES):
+        out[name] = record(*CASES[name])
+        print(name, out[name], flush=True)
+        with open(OUT, "w") as f:
+            json.dump(out, f, indent=1, sort_keys=True)
+            f.write("\n")
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])

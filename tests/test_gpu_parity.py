@@ -4,8 +4,13 @@ Steps covered: cost table (a1), GDP sweeps with their per-sweep bound and
 changed count (a2-a5), sign extraction (a6), pricing scan (a7), CSR merge
 (a8), and the whole solve (lambda, x, bound, iteration and round counts).
 Sizes span several tiles of every kernel with ragged tails; the full-size
-workload is checked on sampled outputs and by the certificate.
+workloads are checked on sampled outputs and, solved whole, against stored
+records of the oracle's solve of the same instances.
 """
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -103,7 +108,6 @@ def test_single_sweeps_from_random_lambda(lib, O, shift, flags):
 
 
 def test_golden_rectangle_on_gpu(lib, O):
-    import json, os
     g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "rectangle_3x4.json")))
     xy = np.array(g["xy"], dtype=np.int32)
     rp, col = complete_csr(4)
@@ -255,6 +259,56 @@ def test_solve_bit_exact(lib, O, kind, n, seed, k, flags):
 def test_solve_bit_exact_with_culled_pricing(lib, O, kind, n, seed, k):
     s, r = _compare_solve(O, inst(kind, n, seed, k), pricing=2)
     assert s.info["certified"] == 2
+
+
+# GDP phases cut at max_iters sweeps (tiny, odd, and the default 256): the solve
+# goes on from the lambda reached, bit-exact with the oracle all the way
+@pytest.mark.parametrize("flags", [0, 1, 2])
+@pytest.mark.parametrize("cap", [1, 7, 64, 256])
+@pytest.mark.parametrize("kind,n,seed,k", [("mixture", 3000, 2, 10), ("uniform", 2000, 1, 6)])
+def test_solve_bit_exact_with_capped_phases(lib, O, kind, n, seed, k, cap, flags):
+    s, r = _compare_solve(O, inst(kind, n, seed, k), max_iters=cap, flags=flags)
+    assert s.info["certified"] == 2 and s.info["iterations"] <= cap * s.info["phases"]
+
+
+def test_default_solve_equals_oracle_default(lib, O):
+    # both sides at their defaults (256 sweeps per phase); a sparse graph that
+    # takes several phases and pricing rounds
+    d = inst("mixture", 5000, 3, 4)
+    assert f2m.f2m_default_params().max_iters == 256
+    r = O.solve(d["xy"], d["row_ptr"], d["col"])
+    s = f2m.solve(d["xy"], d["row_ptr"], d["col"])
+    assert r.phases > 1 and s.info["certified"] == 2
+    for k in ("status", "iterations", "phases", "pricing_rounds", "edges_added", "finisher_calls",
+              "augmentations", "bound2", "frac_bits", "certified"):
+        assert s.info[k] == getattr(r, k), k
+    assert np.array_equal(s.lam, r.lam) and np.array_equal(s.x2, r.x2) and np.array_equal(s.col, r.col)
+
+
+def _full_size_records():
+    path = os.path.join(os.path.dirname(__file__), "golden", "full_size_solves.json")
+    return json.load(open(path)) if os.path.exists(path) else {}
+
+
+FULL = _full_size_records()
+
+
+@pytest.mark.parametrize("name", sorted(FULL))
+def test_full_size_solve_equals_oracle_record(lib, name):
+    # the 100,000- and 200,000-point workloads solved whole, against the
+    # oracle's record of the same solve (written by golden/make_full_size_solves.py)
+    g = FULL[name]
+    d = inst(g["kind"], g["n"], g["seed"], g["k"])
+    s = f2m.solve(d["xy"], d["row_ptr"], d["col"], params=f2m.f2m_default_params(max_iters=g["max_iters"]))
+    for k in ("status", "iterations", "phases", "pricing_rounds", "edges_added", "finisher_calls",
+              "augmentations", "bound2", "frac_bits", "certified", "nnz"):
+        assert s.info[k] == g[k], (k, s.info[k], g[k])
+
+    def digest(a, dt):
+        return hashlib.sha256(np.ascontiguousarray(a, dtype=dt).tobytes()).hexdigest()
+    got = {"row_ptr": digest(s.row_ptr, "<i4"), "col": digest(s.col, "<i4"), "x2": digest(s.x2, "u1"),
+           "lam": digest(s.lam, "<i4")}
+    assert got == g["sha256"]
 
 
 def test_solve_complete_graph_small(lib, O):

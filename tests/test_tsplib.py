@@ -84,7 +84,7 @@ def test_program_solves_a_tsplib_file(lib, oracle_lib, tmp_path):
     assert solve_tsp.main([str(path), "-k", "10", "-o", str(out)]) == 0
     xy, info, edges, x2 = solve_tsp.solve_file(str(path), 10)
     rp, col = oracle_lib.knn_csr(xy, 10)
-    r = oracle_lib.solve(xy, rp, col, max_iters=1000000)
+    r = oracle_lib.solve(xy, rp, col)
     assert info["certified"] == 2 and r.certified == 2
     assert info["bound2"] << (9 - info["frac_bits"]) == r.bound2 << (9 - r.frac_bits)
     # the written solution: every node's x sums to 2, and its cost is the optimum
