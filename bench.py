@@ -54,7 +54,7 @@ def batch_specs(w, rank=0):
 METRIC = "ms to certified F2M optimum"
 GDP_BYTES_PER_ENTRY = 8   # {col, cost} streamed per directed entry
 GDP_BYTES_PER_NODE = 12   # row_ptr + lambda read + lambda write
-PRICING_OPS_PER_PAIR = 7  # 2 FADD (dx, dy), FADD (t), FMUL (t^2), 2 FFMA, FSETP
+PRICING_OPS_PER_PAIR = 5  # FP32 lane operations of the filter: 3 adds (u, w, dy), 2 FMAs
 
 
 def workload_name(w):
@@ -99,6 +99,12 @@ class ClockSampler:
             self.thread.start()
         except Exception:
             self.proc = None
+            return
+        # nvidia-smi's start-up (NVML initialisation) takes CPU time and driver
+        # locks: let it finish before the timed region begins
+        t0 = time.perf_counter()
+        while not self.rows and self.proc.poll() is None and time.perf_counter() - t0 < 5.0:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -233,7 +239,7 @@ REFERENCE_COUNTS: dict = {
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="gdp", choices=["gdp", "reference"])
@@ -308,11 +314,11 @@ def main():
         f2m.f2m_solve(ctx)
         f2m.f2m_destroy(ctx)
     ctxs = [make_ctx(d["xy"], d["row_ptr"], d["col"]) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
     launches0 = f2m.f2m_kernel_launches()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
@@ -458,11 +464,11 @@ def run_batch(args, w, rank, world, local):
         f2m.f2m_solve_batch(b)
         f2m.f2m_destroy_batch(b)
     bs = [f2m.f2m_create_batch(insts, params=params, stream=stream) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
     launches0 = f2m.f2m_kernel_launches()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]

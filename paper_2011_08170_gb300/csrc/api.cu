@@ -189,7 +189,7 @@ extern "C" void f2m_destroy(f2m_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   dfree(c->d_xy); dfree(c->d_rp); dfree(c->d_ec); dfree(c->d_x2); dfree(c->d_tiles);
   dfree(c->d_seg_off); dfree(c->d_fin_include);
-  dfree(c->d_lam[0]); dfree(c->d_lam[1]); dfree(c->d_lam2); dfree(c->d_gdp);
+  dfree(c->d_lam[0]); dfree(c->d_lam[1]); dfree(c->d_lam2); dfree(c->d_exl); dfree(c->d_gdp);
   dfree(c->d_trace_b2); dfree(c->d_trace_ch); dfree(c->d_pts); dfree(c->d_pairs);
   dfree(c->d_ranges); dfree(c->d_boxes); dfree(c->d_smax);
   dfree(c->d_count); dfree(c->d_tile); dfree(c->d_deg); dfree(c->d_tmp_rp); dfree(c->d_new_rp);
@@ -461,6 +461,10 @@ f2m_status f2m::gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, bool 
     if (h.status & kGdpTimeout) return fail(c, F2M_ERR_TIMEOUT, "device-wide barrier wait exceeded its budget");
     if (h.status & kGdpOverflow) return fail(c, F2M_ERR_OVERFLOW, "|lambda| reached 2^29");
     return h.fixed_point ? F2M_OK : F2M_ERR_NOT_CONVERGED;
+  }
+  if (c->plan2_pending) {
+    CK(c, plan_build2(c->plan, c->p.frac_bits, c->st));
+    c->plan2_pending = false;
   }
   CK(c, cudaMemsetAsync(c->d_gdp, 0, sizeof(GdpCtl), c->st));
   CK(c, cudaEventRecord(c->ev0, c->st));
@@ -742,10 +746,10 @@ f2m_status f2m::merge_internal(f2m_ctx* c, const int2* d_pairs, int64_t npairs, 
   if (h.flags) return fail(c, F2M_ERR_INVALID_ARG, check_message(h.flags, h.first_bad));
   CK(c, plan_build(c->d_rp, c->d_ec, n, c->nnz, c->num_sms, !(c->p.flags & F2M_FLAG_STREAMING_GDP),
                    c->p.frac_bits, c->p.gdp_ctas_per_sm, c->plan, c->st));
-  if (c->seg_off.size() == 2 && !(c->p.flags & F2M_FLAG_ONE_SWEEP_GDP))
-    CK(c, plan_build2(c->plan, c->p.frac_bits, c->st));
-  else
-    c->plan.valid2 = false;
+  // the two-sweep tiles only serve GDP phases: built when the next one starts
+  // (a merge before the finisher and the last scan needs none)
+  c->plan.valid2 = false;
+  c->plan2_pending = c->seg_off.size() == 2 && !(c->p.flags & F2M_FLAG_ONE_SWEEP_GDP);
   CK(c, cudaEventRecord(c->ev1, c->st));
   if (ms) *ms += elapsed_ms(c);
   return F2M_OK;
@@ -819,7 +823,8 @@ f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug, const uint8_t* h_inc
   }
   int32_t* d_lam_int = P.ilam[0];   // free outside a GDP phase
   int32_t* d_lam2_int = P.ilam[1];
-  int32_t* d_exl = P.tmp;
+  if (!c->d_exl) CK(c, dalloc(&c->d_exl, n));
+  int32_t* d_exl = c->d_exl;
   CK(c, fin_prepare(P, c->d_lam[c->cur], c->d_b, F, d_lam_int, c->d_fy, d_exl, c->st));
   if (c->d_fin_include)
     CK(c, launch_batch_mask_surplus(d_exl, c->d_seg_off, nseg, c->d_fin_include, n, c->st));

@@ -38,6 +38,8 @@ struct f2m_ctx {
   uint8_t* d_x2 = nullptr;
   int32_t* d_lam[2] = {nullptr, nullptr};
   int32_t* d_lam2 = nullptr;
+  int32_t* d_exl = nullptr;   // [n] the finisher's surpluses (its own: the plan's scratch
+                              // still feeds a two-sweep plan built later)
   int32_t* d_b = nullptr;  // degree requirements b_v, caller order (NULL: b_v = 2)
   int32_t* d_b_int = nullptr;  // the same in the renumbered (internal) order
   int32_t b_max = 2;       // the largest b_v
@@ -68,6 +70,7 @@ struct f2m_ctx {
   unsigned long long* d_bad = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   f2m::GdpPlan plan;         // renumbering and tiles of the shared-memory GDP kernel
+  bool plan2_pending = false;  // the two-sweep tiles are built at the next GDP phase
   f2m::ClassPlan classes;    // colour classes of the class-by-class GDP
   // exact finisher: device scratch, pinned host mirrors, host work arrays
   int32_t* d_twin = nullptr;

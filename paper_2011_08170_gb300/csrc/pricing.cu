@@ -5,17 +5,24 @@
 // final duals are feasible for the complete graph.
 //
 // N-body tiling: the host lists tile pairs (TILE x TILE blocks of the pair
-// triangle of each segment, i.e. instance), handed out by an atomic counter; a CTA keeps TILE j-points in shared memory
-// and each thread P i-points in registers.  Per pair an fp32 filter runs:
-//   t = s_u + s_v,   e = dy^2 + (dx^2 - t^2)   (two FMAs),   pass if e < 1,
-// with s_v = max(lambda_v * 2^-fb + 1/4, 0) * (1 + 2^-19).
-// No false negatives: z < 0 implies c < T = (lambda_u + lambda_v) 2^-fb, hence
-// sqrt(d2) < c + 1/2 < T + 1/2 <= r_u + r_v with r = max(lambda 2^-fb + 1/4, 0).
-// The rounding of r, s and t is below 2^-22 relative, so t >= (r_u + r_v)
-// (1 + 2^-20) and t^2 exceeds d2 by more than 2^-20 t^2, while the two FMAs
-// err by at most 2^-23 t^2; d2 < 1 (duplicate points) passes trivially.  Pairs
-// that pass are decided exactly in integers (exact cost, int64 z), then
-// checked against the CSR row by binary search, then appended.
+// triangle of each segment, i.e. instance), handed out by an atomic counter;
+// a CTA keeps TILE j-points in shared memory and each thread P i-points in
+// registers, two at a time in packed fp32x2 registers (Blackwell's two-lane
+// FADD2 / FFMA2: one issue slot for two pairs).
+//
+// Filter.  r_v = max(lambda_v 2^-fb + 1/4, 0), s_v = (r_v + 2)(1 + 2^-17) in
+// fp32, a_v = x_v - s_v, c_v = x_v + s_v.  Per pair, with t = s_u + s_v:
+//   u = a_v - c_u = dx - t,  w = c_v - a_u = dx + t,  dy = y_v - y_u,
+//   e' = dy^2 + (u w - 1) = d^2 - t^2 - 1      (3 FADD2 + 2 FFMA2 per 2 pairs)
+// and the pair passes when e' < 0 (its sign bit, OR-ed over the thread's
+// pairs).  No false negatives: z < 0 implies c < T = (lambda_u + lambda_v)
+// 2^-fb, hence d < c + 1/2 < T + 1/2 <= R = r_u + r_v, and t >= (R + 4)(1 +
+// 2^-17.3) after the roundings of r (2^-23 relative) and s, so d^2 - t^2 <=
+// -(4 + 2^-17.3 t)(t + d).  The fp32 errors are at most 0.5 (t + d) (a, c and
+// u, w: 2^-24 of |x| + s < 2^20 + s each) plus 2^-20.9 t (t + d) (the products
+// and the sum), so e' stays negative.  Pairs that pass are decided exactly in
+// integers (exact cost, int64 z), then checked against the CSR row by binary
+// search, then appended.
 #include <climits>
 
 #include "f2m_device.cuh"
@@ -23,10 +30,10 @@
 
 namespace f2m {
 
-constexpr int kPriceThreads = 256;
-constexpr int kPriceP = 4;
-constexpr int kPriceTile = kPriceThreads * kPriceP;
-static_assert(kPriceTile == kPricingTile, "tile size shared with the tile-list builder");
+// A CTA takes kPricingTile i-points (P per thread, as P / 2 packed pairs) and
+// kPricingTile j-points.  P = 8 (128 threads) when there are many tile pairs,
+// P = 4 (256 threads: twice the threads on one tile pair) when there are few.
+constexpr int kPriceTile = kPricingTile;
 
 // pts[v] = {x, y, s, node} of node perm[v] (perm NULL: node v); the node id is
 // carried in the last component's bits
@@ -34,13 +41,13 @@ __global__ void pricing_prep_kernel(const int2* __restrict__ xy, const int32_t* 
                                     const int32_t* __restrict__ perm, int32_t n, int32_t fb,
                                     float4* __restrict__ pts) {
   const float scale = ldexpf(1.0f, -fb);
-  const float grow = 1.0f + ldexpf(1.0f, -19);
+  const float grow = 1.0f + ldexpf(1.0f, -17);
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
        v += (long long)gridDim.x * blockDim.x) {
     const int u = perm ? perm[v] : (int)v;
     const int2 p = xy[u];
-    float r = fmaxf((float)lam[u] * scale + 0.25f, 0.0f);
-    pts[v] = make_float4((float)p.x, (float)p.y, r * grow, __int_as_float(u));
+    const float r = fmaxf((float)lam[u] * scale + 0.25f, 0.0f);
+    pts[v] = make_float4((float)p.x, (float)p.y, (r + 2.0f) * grow, __int_as_float(u));
   }
 }
 
@@ -115,14 +122,19 @@ __device__ __noinline__ void pricing_confirm(int ii, int jj, int i, int j, int32
   if ((long long)k < cap) pairs[k] = make_int2(i, j);
 }
 
-__global__ void __launch_bounds__(kPriceThreads)
+template <int P>
+__global__ void __launch_bounds__(kPricingTile / P)
 pricing_kernel(const float4* __restrict__ pts, const int2* __restrict__ xy,
                const int32_t* __restrict__ lam, const int32_t* __restrict__ rp,
                const int2* __restrict__ ec, int32_t n, int32_t fb, const int4* __restrict__ tiles,
                int32_t ntiles, int2* pairs, long long cap, unsigned long long* count,
                unsigned int* tile_counter) {
-  __shared__ float4 sj[kPriceTile];
+  constexpr int kPriceThreads = kPriceTile / P;
+  constexpr int Q = P / 2;
+  __shared__ float4 s_ac[kPriceTile];  // {a, a, c, c} of the j-points
+  __shared__ float2 s_y[kPriceTile];   // {y, y}
   __shared__ int s_tp;
+  const float2 minus_one = make_float2(-1.0f, -1.0f);
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_tp = (int)atomicAdd(tile_counter, 1u);
@@ -131,42 +143,71 @@ pricing_kernel(const float4* __restrict__ pts, const int2* __restrict__ xy,
     if (tp >= ntiles) break;
     const int4 tl = tiles[tp];  // i in [x, y), j in [z, w)
 
-    float xi[kPriceP], yi[kPriceP], si[kPriceP];
-    int ni[kPriceP];
+    // i-points p = 2q + h at tl.x + p * kPriceThreads + tid, negated; a point
+    // past the range gets 1e18 (its e' stays above 1e36, finite)
+    float2 na[Q], nc[Q], ny[Q];
 #pragma unroll
-    for (int p = 0; p < kPriceP; ++p) {
-      const int i = tl.x + p * kPriceThreads + threadIdx.x;
-      if (i < tl.y) {
-        const float4 q = pts[i];
-        xi[p] = q.x; yi[p] = q.y; si[p] = q.z; ni[p] = __float_as_int(q.w);
-      } else {
-        xi[p] = 1e18f; yi[p] = 1e18f; si[p] = 0.0f; ni[p] = 0;
+    for (int q = 0; q < Q; ++q) {
+      float a[2], c[2], y[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = tl.x + (2 * q + h) * kPriceThreads + threadIdx.x;
+        if (i < tl.y) {
+          const float4 v = pts[i];
+          a[h] = v.x - v.z;
+          c[h] = v.x + v.z;
+          y[h] = v.y;
+        } else {
+          a[h] = 1e18f;
+          c[h] = 1e18f;
+          y[h] = 1e18f;
+        }
       }
+      na[q] = make_float2(-a[0], -a[1]);
+      nc[q] = make_float2(-c[0], -c[1]);
+      ny[q] = make_float2(-y[0], -y[1]);
     }
     for (int k = threadIdx.x; k < kPriceTile; k += kPriceThreads) {
       const int j = tl.z + k;
-      sj[k] = j < tl.w ? pts[j] : make_float4(-1e18f, -1e18f, 0.0f, __int_as_float(0));
+      if (j < tl.w) {
+        const float4 v = pts[j];
+        const float a = v.x - v.z, c = v.x + v.z;
+        s_ac[k] = make_float4(a, a, c, c);
+        s_y[k] = make_float2(v.y, v.y);
+      } else {
+        s_ac[k] = make_float4(-1e18f, -1e18f, -1e18f, -1e18f);
+        s_y[k] = make_float2(-1e18f, -1e18f);
+      }
     }
     __syncthreads();
-#pragma unroll 4
+#pragma unroll 2
     for (int k = 0; k < kPriceTile; ++k) {
-      const float4 q = sj[k];
-      float e[kPriceP];
+      const float4 ac = s_ac[k];
+      const float2 yj = s_y[k];
+      const float2 aj = make_float2(ac.x, ac.y), cj = make_float2(ac.z, ac.w);
+      float2 e[Q];
+      unsigned int sign = 0u;
 #pragma unroll
-      for (int p = 0; p < kPriceP; ++p) {
-        const float dx = q.x - xi[p], dy = q.y - yi[p], t = q.z + si[p];
-        e[p] = fmaf(dy, dy, fmaf(dx, dx, -t * t));
+      for (int q = 0; q < Q; ++q) {
+        const float2 u = __fadd2_rn(aj, nc[q]);
+        const float2 w = __fadd2_rn(cj, na[q]);
+        const float2 dy = __fadd2_rn(yj, ny[q]);
+        e[q] = __ffma2_rn(dy, dy, __ffma2_rn(u, w, minus_one));
+        sign |= __float_as_uint(e[q].x) | __float_as_uint(e[q].y);
       }
-      float m = e[0];
+      if ((int)sign < 0 && tl.z + k < tl.w) {  // rare: decide the passing pairs exactly
+        const int jj = tl.z + k;
+        const int node_j = __float_as_int(pts[jj].w);
 #pragma unroll
-      for (int p = 1; p < kPriceP; ++p) m = fminf(m, e[p]);
-      if (m < 1.0f) {
-        const int j = tl.z + k;
+        for (int q = 0; q < Q; ++q) {
 #pragma unroll
-        for (int p = 0; p < kPriceP; ++p)
-          if (e[p] < 1.0f)
-            pricing_confirm(tl.x + p * kPriceThreads + threadIdx.x, j, ni[p], __float_as_int(q.w),
-                            min(n, tl.w), xy, lam, rp, ec, fb, pairs, cap, count);
+          for (int h = 0; h < 2; ++h) {
+            const int ii = tl.x + (2 * q + h) * kPriceThreads + threadIdx.x;
+            if (__float_as_int(h ? e[q].y : e[q].x) < 0 && ii < tl.y)
+              pricing_confirm(ii, jj, __float_as_int(pts[ii].w), node_j, min(n, tl.w), xy, lam, rp, ec, fb,
+                              pairs, cap, count);
+          }
+        }
       }
     }
   }
@@ -198,14 +239,24 @@ cudaError_t launch_pricing_scan(const float4* pts, const int2* xy, const int32_t
   if (err == cudaSuccess) err = cudaMemsetAsync(tile_counter, 0, sizeof(unsigned int), st);
   if (err != cudaSuccess) return err;
   if (ntiles == 0) return cudaSuccess;
+  // P = 8 when the tile pairs fill the GPU several times over
   int per_sm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pricing_kernel, kPriceThreads, 0);
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pricing_kernel<8>, kPriceTile / 8, 0);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) per_sm = 1;
-  long long grid = (long long)num_sms * per_sm;
-  if (grid > ntiles) grid = ntiles;
-  pricing_kernel<<<(int)grid, kPriceThreads, 0, st>>>(pts, xy, lam, rp, ec, n, fb, tiles, ntiles,
-                                                      pairs, cap, count, tile_counter);
+  if ((long long)ntiles >= 4LL * num_sms * per_sm) {
+    const long long grid = (long long)num_sms * per_sm;
+    pricing_kernel<8><<<(int)grid, kPriceTile / 8, 0, st>>>(pts, xy, lam, rp, ec, n, fb, tiles, ntiles, pairs,
+                                                           cap, count, tile_counter);
+  } else {
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pricing_kernel<4>, kPriceTile / 4, 0);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) per_sm = 1;
+    long long grid = (long long)num_sms * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    pricing_kernel<4><<<(int)grid, kPriceTile / 4, 0, st>>>(pts, xy, lam, rp, ec, n, fb, tiles, ntiles, pairs,
+                                                           cap, count, tile_counter);
+  }
   count_launch();
   return cudaGetLastError();
 }

@@ -285,6 +285,23 @@ def test_default_solve_equals_oracle_default(lib, O):
     assert np.array_equal(s.lam, r.lam) and np.array_equal(s.x2, r.x2) and np.array_equal(s.col, r.col)
 
 
+@pytest.mark.parametrize("flags", [0, 2])
+def test_gdp_after_a_solve_that_merged(lib, O, flags):
+    # a solve whose scans added edges ends with the finisher's lambda (F + 1
+    # bits) on the merged graph; a GDP phase called afterwards starts from the
+    # floor to F bits on that graph, like the oracle's
+    d = inst("mixture", 5000, 3, 4)
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"], f2m.f2m_default_params(flags=flags))
+    info = f2m.f2m_solve(ctx)
+    assert info.edges_added > 0 and info.frac_bits == 9
+    lam9, _ = f2m.f2m_get_lambda(ctx)
+    rp, col, _, cost = f2m.f2m_get_x(ctx)
+    st_o, lam_o, it_o, tb_o, tc_o = O.gdp(rp, col, cost, lam9 >> 1, 8, 2, 50, trace=True)
+    st, sweeps, tb, tc = f2m.f2m_gdp(ctx, 50, trace_cap=50)
+    assert sweeps == it_o and np.array_equal(tb, tb_o) and np.array_equal(tc, tc_o)
+    assert np.array_equal(f2m.f2m_get_lambda(ctx)[0], lam_o)
+
+
 def _full_size_records():
     path = os.path.join(os.path.dirname(__file__), "golden", "full_size_solves.json")
     return json.load(open(path)) if os.path.exists(path) else {}
