@@ -14,8 +14,11 @@
 // fp32, a_v = x_v - s_v, c_v = x_v + s_v.  Per pair, with t = s_u + s_v:
 //   u = a_v - c_u = dx - t,  w = c_v - a_u = dx + t,  dy = y_v - y_u,
 //   e' = dy^2 + (u w - 1) = d^2 - t^2 - 1      (3 FADD2 + 2 FFMA2 per 2 pairs)
-// and the pair passes when e' < 0 (its sign bit, OR-ed over the thread's
-// pairs).  No false negatives: z < 0 implies c < T = (lambda_u + lambda_v)
+// and the pair passes when e' < 0.  The sign bits are OR-ed over a thread's
+// pairs with 4 j-points; a warp appends the groups with a set bit to its list
+// in shared memory (ballot, no atomics) and, after every 64 j-points, its
+// lanes re-evaluate the listed pairs and decide the passing ones exactly, so
+// the hot loop holds no call and no block-wide barrier.  No false negatives: z < 0 implies c < T = (lambda_u + lambda_v)
 // 2^-fb, hence d < c + 1/2 < T + 1/2 <= R = r_u + r_v, and t >= (R + 4)(1 +
 // 2^-17.3) after the roundings of r (2^-23 relative) and s, so d^2 - t^2 <=
 // -(4 + 2^-17.3 t)(t + d).  The fp32 errors are at most 0.5 (t + d) (a, c and
@@ -122,8 +125,51 @@ __device__ __noinline__ void pricing_confirm(int ii, int jj, int i, int j, int32
   if ((long long)k < cap) pairs[k] = make_int2(i, j);
 }
 
+// The filter of one pair, from a_v, c_v, y_v of the j-point and the negated
+// a_u, c_u, y_u of the i-point; the hot loop evaluates the same operations two
+// pairs at a time
+__device__ __forceinline__ float pricing_filter(float aj, float cj, float yj, float nai, float nci, float nyi) {
+  const float u = __fadd_rn(aj, nci), w = __fadd_rn(cj, nai), dy = __fadd_rn(yj, nyi);
+  return __fmaf_rn(dy, dy, __fmaf_rn(u, w, -1.0f));
+}
+
+// j-points per sign test, and per chunk after which a warp decides its hits;
+// a warp's list holds one chunk (one entry per lane and group at most)
+constexpr int kPriceGroup = 4;
+constexpr int kPriceChunk = 64;
+constexpr int kWarpHits = (kPriceChunk / kPriceGroup) * 32;
+static_assert(kPriceTile % kPriceChunk == 0 && kPriceChunk % kPriceGroup == 0, "chunking");
+
+// Decide exactly every passing pair of the groups in a warp's hit list (each
+// entry: first j of the group << 8 | thread); all lanes of the warp take part.
 template <int P>
-__global__ void __launch_bounds__(kPricingTile / P)
+__device__ __forceinline__ void pricing_hits(const int* hits, int nh, int lane, int4 tl, const float4* s_ac,
+                                          const float2* s_y, const float4* __restrict__ pts,
+                                          const int2* __restrict__ xy, const int32_t* __restrict__ lam,
+                                          const int32_t* __restrict__ rp, const int2* __restrict__ ec,
+                                          int32_t n, int32_t fb, int2* pairs, long long cap,
+                                          unsigned long long* count) {
+  constexpr int kPriceThreads = kPriceTile / P;
+  for (int h = lane; h < nh * P; h += 32) {
+    const int ent = hits[h / P], p = h % P;
+    const int t = ent & 0xFF, g = ent >> 8;
+    const int ii = tl.x + p * kPriceThreads + t;
+    if (ii >= tl.y) continue;
+    const float4 vi = pts[ii];
+    const float nai = -(vi.x - vi.z), nci = -(vi.x + vi.z), nyi = -vi.y;
+    for (int kk = 0; kk < kPriceGroup; ++kk) {
+      const int jj = tl.z + g + kk;
+      if (jj >= tl.w) break;
+      const float4 ac = s_ac[g + kk];
+      if (pricing_filter(ac.x, ac.z, s_y[g + kk].x, nai, nci, nyi) < 0.0f)
+        pricing_confirm(ii, jj, __float_as_int(vi.w), __float_as_int(pts[jj].w), min(n, tl.w), xy, lam, rp,
+                        ec, fb, pairs, cap, count);
+    }
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kPricingTile / P, P == 8 ? 6 : 4)
 pricing_kernel(const float4* __restrict__ pts, const int2* __restrict__ xy,
                const int32_t* __restrict__ lam, const int32_t* __restrict__ rp,
                const int2* __restrict__ ec, int32_t n, int32_t fb, const int4* __restrict__ tiles,
@@ -131,10 +177,14 @@ pricing_kernel(const float4* __restrict__ pts, const int2* __restrict__ xy,
                unsigned int* tile_counter) {
   constexpr int kPriceThreads = kPriceTile / P;
   constexpr int Q = P / 2;
-  __shared__ float4 s_ac[kPriceTile];  // {a, a, c, c} of the j-points
-  __shared__ float2 s_y[kPriceTile];   // {y, y}
+  static_assert(kPriceThreads <= 256 && kPriceTile <= (1 << 23), "hit entry packing");
+  __shared__ float4 s_ac[kPriceTile];                       // {a, a, c, c} of the j-points
+  __shared__ float2 s_y[kPriceTile];                        // {y, y}
+  __shared__ int s_hit[(kPriceThreads / 32) * kWarpHits];  // one list per warp
   __shared__ int s_tp;
   const float2 minus_one = make_float2(-1.0f, -1.0f);
+  const int lane = threadIdx.x & 31;
+  int* hits = s_hit + (threadIdx.x >> 5) * kWarpHits;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_tp = (int)atomicAdd(tile_counter, 1u);
@@ -180,34 +230,35 @@ pricing_kernel(const float4* __restrict__ pts, const int2* __restrict__ xy,
       }
     }
     __syncthreads();
+    for (int k0 = 0; k0 < kPriceTile; k0 += kPriceChunk) {
+      int nh = 0;  // entries in this warp's list (the same in every lane)
 #pragma unroll 2
-    for (int k = 0; k < kPriceTile; ++k) {
-      const float4 ac = s_ac[k];
-      const float2 yj = s_y[k];
-      const float2 aj = make_float2(ac.x, ac.y), cj = make_float2(ac.z, ac.w);
-      float2 e[Q];
-      unsigned int sign = 0u;
+      for (int g = k0; g < k0 + kPriceChunk; g += kPriceGroup) {
+        unsigned int sign = 0u;
 #pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const float2 u = __fadd2_rn(aj, nc[q]);
-        const float2 w = __fadd2_rn(cj, na[q]);
-        const float2 dy = __fadd2_rn(yj, ny[q]);
-        e[q] = __ffma2_rn(dy, dy, __ffma2_rn(u, w, minus_one));
-        sign |= __float_as_uint(e[q].x) | __float_as_uint(e[q].y);
-      }
-      if ((int)sign < 0 && tl.z + k < tl.w) {  // rare: decide the passing pairs exactly
-        const int jj = tl.z + k;
-        const int node_j = __float_as_int(pts[jj].w);
+        for (int kk = 0; kk < kPriceGroup; ++kk) {
+          const float4 ac = s_ac[g + kk];
+          const float2 yj = s_y[g + kk];
+          const float2 aj = make_float2(ac.x, ac.y), cj = make_float2(ac.z, ac.w);
 #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int ii = tl.x + (2 * q + h) * kPriceThreads + threadIdx.x;
-            if (__float_as_int(h ? e[q].y : e[q].x) < 0 && ii < tl.y)
-              pricing_confirm(ii, jj, __float_as_int(pts[ii].w), node_j, min(n, tl.w), xy, lam, rp, ec, fb,
-                              pairs, cap, count);
+          for (int q = 0; q < Q; ++q) {
+            const float2 u = __fadd2_rn(aj, nc[q]);
+            const float2 w = __fadd2_rn(cj, na[q]);
+            const float2 dy = __fadd2_rn(yj, ny[q]);
+            const float2 e = __ffma2_rn(dy, dy, __ffma2_rn(u, w, minus_one));
+            sign |= __float_as_uint(e.x) | __float_as_uint(e.y);
           }
         }
+        const unsigned int m = __ballot_sync(0xffffffffu, (int)sign < 0);
+        if (m) {  // rare: append the lanes' groups to the warp's list
+          if ((int)sign < 0) hits[nh + __popc(m & ((1u << lane) - 1u))] = (g << 8) | (int)threadIdx.x;
+          nh += __popc(m);
+        }
+      }
+      if (nh) {  // the same branch in every lane of the warp
+        __syncwarp();
+        pricing_hits<P>(hits, nh, lane, tl, s_ac, s_y, pts, xy, lam, rp, ec, n, fb, pairs, cap, count);
+        __syncwarp();  // the list is free for the next chunk
       }
     }
   }
