@@ -392,6 +392,11 @@ def main():
                     "unit": "Tops/s", "frac": pr_tops / alu_peak,
                     "traffic": traffic.get("pricing_kernel")}
     roofline["peak_source"] = "MEASURED_PEAKS.json" if not peaks.get("_fallback") else "fallback"
+    if args.pricing == 2 and roofline["kernel"] == "pricing_kernel":
+        roofline["effective"] = True
+        roofline["note"] = ("culled scan: the rate counts all n(n-1)/2 pairs per scan, but tile pairs that "
+                            "cannot hold z < 0 are not evaluated, so it is an effective rate and can exceed "
+                            "the lane peak")
     roofline["gdp_sweep_gbs"] = gdp_gbs
     roofline["gdp_sweep_frac_of_hbm"] = gdp_gbs / peaks["hbm_gbs"]
     roofline["gdp_working_set_mb"] = (GDP_BYTES_PER_ENTRY * nnz0 + GDP_BYTES_PER_NODE * n) / 1e6
