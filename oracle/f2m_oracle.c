@@ -295,20 +295,24 @@ int64_t or_extract(int32_t n, const int32_t* row_ptr, const int32_t* col,
  * searched in nearby parts of the plane.  (The paper gives no finisher; this
  * order is a stated choice.)
  *
- * Two phases, so that the first can run block by block in parallel with a
- * result that does not depend on the schedule.  Block k holds the nodes of rank
- * in [k*OR_FIN_BLOCK, (k+1)*OR_FIN_BLOCK), both copies.
- *   Phase 1, for each block in turn: its sources in key order, each searched as
- *   above except that (a) a node outside the block is never settled: if a heap
- *   item of an outside node comes to the top, or the heap empties, the search
- *   is dropped with nothing changed and the next source of the block is taken;
- *   (b) reduced costs of arcs into outside nodes use those nodes' potentials as
- *   they were when phase 1 began.  Potentials only grow, so every residual
- *   reduced cost stays >= 0; arcs and potentials a block reads are changed by
- *   that block alone, so the blocks do not depend on one another's progress.
- *   Phase 2: the plain search over all nodes in key order for what is left. */
+ * Three phases, so that the first two can run block by block in parallel with
+ * a result that does not depend on the schedule.  In a blocked phase with block
+ * size B, block k holds the nodes of rank in [k*B, (k+1)*B), both copies.
+ *   Blocked phase, for each block in turn: its sources in key order, each
+ *   searched as above except that (a) a node outside the block is never
+ *   settled: if a heap item of an outside node comes to the top, or the heap
+ *   empties, the search is dropped with nothing changed and the next source of
+ *   the block is taken; (b) reduced costs of arcs into outside nodes use those
+ *   nodes' potentials as they were when the phase began.  Potentials only
+ *   grow, so every residual reduced cost stays >= 0; arcs and potentials a
+ *   block reads are changed by that block alone, so the blocks do not depend
+ *   on one another's progress.
+ *   Phase 1: blocked, B = OR_FIN_BLOCK.  Phase 2: blocked, B = OR_FIN_BLOCK2,
+ *   for the searches phase 1 dropped.  Phase 3: the plain search over all
+ *   nodes in key order for what is left. */
 
 #define OR_FIN_BLOCK 2048
+#define OR_FIN_BLOCK2 16384
 
 typedef struct { int64_t d; int32_t key; int32_t v; } or_hitem;
 
@@ -421,18 +425,20 @@ int or_finisher(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int3
     ex[n + u] = in - bu;   /* R_u: inflow minus demand b_u */
   }
 
-  int64_t* pi0 = (int64_t*)malloc(sizeof(int64_t) * (size_t)N); /* potentials at phase 1's start */
-  memcpy(pi0, pi, sizeof(int64_t) * (size_t)N);
+  int64_t* pi0 = (int64_t*)malloc(sizeof(int64_t) * (size_t)N); /* potentials at the phase's start */
   int32_t* rank = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
   for (int32_t v = 0; v < n; ++v) rank[v] = key[v] / 2;
-  const int32_t nblocks = (n + OR_FIN_BLOCK - 1) / OR_FIN_BLOCK;
 
   int64_t stamp = 0;
-  for (int32_t phase = 1; phase <= 2 && status == OR_OK; ++phase) {
-    for (int32_t blk = 0; blk < (phase == 1 ? nblocks : 1) && status == OR_OK; ++blk) {
-      /* phase 1: keys of block blk; phase 2: every key */
-      const int32_t k0 = phase == 1 ? 2 * blk * OR_FIN_BLOCK : 0;
-      int32_t k1 = phase == 1 ? 2 * (blk + 1) * OR_FIN_BLOCK : N;
+  for (int32_t phase = 1; phase <= 3 && status == OR_OK; ++phase) {
+    const int32_t blocked = phase < 3;
+    const int32_t bsz = phase == 1 ? OR_FIN_BLOCK : OR_FIN_BLOCK2;
+    const int32_t nblocks = blocked ? (n + bsz - 1) / bsz : 1;
+    if (blocked) memcpy(pi0, pi, sizeof(int64_t) * (size_t)N);
+    for (int32_t blk = 0; blk < nblocks && status == OR_OK; ++blk) {
+      /* blocked phase: keys of block blk; phase 3: every key */
+      const int32_t k0 = blocked ? 2 * blk * bsz : 0;
+      int32_t k1 = blocked ? 2 * (blk + 1) * bsz : N;
       if (k1 > N) k1 = N;
       for (int32_t next = k0; next < k1 && status == OR_OK; ++next) {
         const int32_t src = by_key[next];
@@ -445,7 +451,7 @@ int or_finisher(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int3
           while (hs > 0) {
             or_hitem it = or_hpop(heap, &hs);
             int32_t i = it.v;
-            if (phase == 1 && rank[i < n ? i : i - n] / OR_FIN_BLOCK != blk) break; /* dropped */
+            if (blocked && rank[i < n ? i : i - n] / bsz != blk) break; /* dropped */
             if (done[i] == stamp || it.d != dist[i]) continue;
             done[i] = stamp;
             if (ex[i] < 0) { t = i; break; }
@@ -454,7 +460,7 @@ int or_finisher(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int3
               for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
                 if (y[e]) continue;
                 int32_t j = n + col[e];
-                int32_t out = phase == 1 && rank[col[e]] / OR_FIN_BLOCK != blk;
+                int32_t out = blocked && rank[col[e]] / bsz != blk;
                 int64_t rc = ((int64_t)cost[e] << F) - pi[i] + (out ? pi0[j] : pi[j]);
                 int64_t nd = dist[i] + rc;
                 if (out) { or_hpush(heap, &hs, (or_hitem){nd, key[j], j}); continue; }
@@ -469,7 +475,7 @@ int or_finisher(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int3
                 int32_t e = rev[f]; /* entry (col[f] -> v) */
                 if (!y[e]) continue;
                 int32_t j = col[f];
-                int32_t out = phase == 1 && rank[j] / OR_FIN_BLOCK != blk;
+                int32_t out = blocked && rank[j] / bsz != blk;
                 int64_t rc = -((int64_t)cost[e] << F) - pi[i] + (out ? pi0[j] : pi[j]);
                 int64_t nd = dist[i] + rc;
                 if (out) { or_hpush(heap, &hs, (or_hitem){nd, key[j], j}); continue; }
@@ -481,7 +487,7 @@ int or_finisher(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int3
             }
           }
           if (t < 0) {
-            if (phase == 1) break;  /* dropped or nothing reachable: left to phase 2 */
+            if (blocked) break;  /* dropped or nothing reachable: left to the next phase */
             status = OR_INFEASIBLE;
             break;
           }

@@ -25,16 +25,18 @@
 // copy, so successive searches stay in nearby memory.  The rules are fixed,
 // so the result is deterministic.
 //
-// Two phases.  Phase 1 splits every segment into blocks of kFinBlock nodes
+// Three phases.  A blocked phase splits every segment into blocks of B nodes
 // (consecutive internal ids, both copies) and runs the blocks on worker
 // threads: a block's sources in key order, each search restricted to the
 // block -- when a heap item of an outside node comes to the top, or the heap
 // runs dry, the search is dropped with nothing changed and the block moves to
 // its next source -- with arcs into outside nodes priced at the potentials of
-// phase 1's start.  Potentials only grow, so every residual reduced cost stays
-// non-negative; the arcs and potentials a block reads are written by that
-// block alone, so the result does not depend on the schedule.  Phase 2 runs
-// the plain search per segment for what phase 1 left.
+// the phase's start.  Potentials only grow, so every residual reduced cost
+// stays non-negative; the arcs and potentials a block reads are written by
+// that block alone, so the result does not depend on the schedule.  Phase 1 is
+// blocked with B = kFinBlock, phase 2 with B = kFinBlock2 for the searches
+// phase 1 dropped (they cross a small block's edge), and phase 3 runs the
+// plain search per segment for what is left.
 //
 // Layout: the graph arrives in the renumbered node order prepared on the
 // device (finisher_prep.cu): internal node i is the i-th point in (Morton
@@ -93,7 +95,8 @@ struct Searcher {
   }
 };
 
-constexpr int32_t kFinBlock = 2048;  // nodes per phase-1 block
+constexpr int32_t kFinBlock = 2048;    // nodes per phase-1 block
+constexpr int32_t kFinBlock2 = 16384;  // nodes per phase-2 block
 
 // Worker threads kept for the life of the process (one pool, shared by every
 // context; jobs from different host threads take turns): a job is a count of
@@ -155,6 +158,7 @@ struct WorkerPool {
 
 struct FinisherWork {
   std::vector<int64_t> pi, dist;
+  std::vector<int64_t> pi_start;  // potentials at phase 2's start (outside nodes are priced with them)
   std::vector<int32_t> excess, via, pred;
   std::vector<uint32_t> reached, closed;  // search stamps; every search takes a fresh one
   std::atomic<uint32_t> stamp{0};
@@ -174,6 +178,7 @@ void finisher_work_reserve(FinisherWork* w, int32_t n) {
   const size_t N = 2 * (size_t)n;
   if (w->pi.size() >= N) return;
   w->pi.assign(N, 0);
+  w->pi_start.assign(N, 0);
   w->dist.assign(N, 0);
   w->excess.assign(N, 0);
   w->via.assign(N, 0);
@@ -186,14 +191,15 @@ void finisher_work_reserve(FinisherWork* w, int32_t n) {
 namespace {
 
 // Successive shortest paths for the sources of nodes [lo, hi) (internal ids),
-// in key order.  lam0 == nullptr: [lo, hi) is a whole segment, which no arc
-// leaves (phase 2).  Otherwise [lo, hi) is a phase-1 block: outside nodes are
-// priced with their potentials at phase 1's start (lam0 for a left copy,
-// -lam0 for a right one) and never settled, and a search that would settle
-// one (or finds nothing) is dropped.
-int solve_range(int32_t n, int32_t lo, int32_t hi, const int32_t* lam0, const int32_t* irp,
-                const int2* iec, const int32_t* twin, uint8_t* y, int32_t F, FinisherWork* w,
-                Searcher& sr, int64_t* pushes_out) {
+// in key order.  lam0 == nullptr and pi0 == nullptr: [lo, hi) is a whole
+// segment, which no arc leaves (phase 3).  Otherwise [lo, hi) is a block of a
+// blocked phase: outside nodes are priced with their potentials at the
+// phase's start -- lam0 for a left copy and -lam0 for a right one in phase 1,
+// pi0 in phase 2 -- and never settled, and a search that would settle one (or
+// finds nothing) is dropped.
+int solve_range(int32_t n, int32_t lo, int32_t hi, const int32_t* lam0, const int64_t* pi0v,
+                const int32_t* irp, const int2* iec, const int32_t* twin, uint8_t* y, int32_t F,
+                FinisherWork* w, Searcher& sr, int64_t* pushes_out) {
   int64_t* pi = w->pi.data();
   int64_t* dist = w->dist.data();
   int32_t* excess = w->excess.data();
@@ -206,7 +212,11 @@ int solve_range(int32_t n, int32_t lo, int32_t hi, const int32_t* lam0, const in
     const int32_t i = node < n ? node : node - n;
     return i < lo || i >= hi;
   };
-  auto pi0 = [&](int32_t node) { return node < n ? (int64_t)lam0[node] : -(int64_t)lam0[node - n]; };
+  const bool blocked = lam0 || pi0v;
+  auto pi0 = [&](int32_t node) {
+    if (pi0v) return pi0v[node];
+    return node < n ? (int64_t)lam0[node] : -(int64_t)lam0[node - n];
+  };
   int64_t pushes = 0;
   for (int32_t i = lo; i < hi; ++i) {
     for (int side = 0; side < 2; ++side) {
@@ -223,7 +233,7 @@ int solve_range(int32_t n, int32_t lo, int32_t hi, const int32_t* lam0, const in
         while (!sr.heap.empty()) {
           const Searcher::Item top = sr.pop();
           const int32_t v = top.node;
-          if (lam0 && outside(v)) break;  // dropped
+          if (blocked && outside(v)) break;  // dropped
           if (closed[v] == round || top.d != dist[v]) continue;
           closed[v] = round;
           if (excess[v] < 0) { t = v; break; }
@@ -233,7 +243,7 @@ int solve_range(int32_t n, int32_t lo, int32_t hi, const int32_t* lam0, const in
             for (int32_t e = irp[v]; e < irp[v + 1]; ++e) {
               if (y[e]) continue;
               const int32_t j = n + iec[e].x;
-              if (lam0 && outside(j)) {
+              if (blocked && outside(j)) {
                 sr.push({dist[v] + ((int64_t)iec[e].y << F) - pi[v] + pi0(j), key_of(j), j});
                 continue;
               }
@@ -250,7 +260,7 @@ int solve_range(int32_t n, int32_t lo, int32_t hi, const int32_t* lam0, const in
               const int32_t a = twin[f];
               if (!y[a]) continue;
               const int32_t j = iec[f].x;  // L_x, the tail of arc a
-              if (lam0 && outside(j)) {
+              if (blocked && outside(j)) {
                 sr.push({dist[v] - ((int64_t)iec[f].y << F) - pi[v] + pi0(j), key_of(j), j});
                 continue;
               }
@@ -263,7 +273,7 @@ int solve_range(int32_t n, int32_t lo, int32_t hi, const int32_t* lam0, const in
           }
         }
         if (t < 0) {
-          if (lam0) break;  // dropped or nothing found: left to phase 2
+          if (blocked) break;  // dropped or nothing found: left to the next phase
           return 7;
         }
         for (int32_t j = t; j != s; j = pred[j]) y[via[j]] = (uint8_t)(j >= n);  // push one unit
@@ -321,14 +331,17 @@ int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t*
   int64_t* pi = w->pi.data();
   int32_t* excess = w->excess.data();
   // phase 1: blocks of every segment, each first setting its own nodes'
-  // potentials (lam, -lam) and surpluses; phase 2: whole segments
-  std::vector<int2> blocks;
+  // potentials (lam, -lam) and surpluses; phase 2: larger blocks, from a copy
+  // of the potentials phase 1 left; phase 3: whole segments
+  std::vector<int2> blocks, blocks2;
   std::vector<int32_t> segs;
   for (int32_t sg = 0; sg < nseg; ++sg) {
     if (include && !include[sg]) continue;  // left alone: not read, not written
     segs.push_back(sg);
     for (int32_t b0 = seg_off[sg]; b0 < seg_off[sg + 1]; b0 += kFinBlock)
       blocks.push_back(make_int2(b0, std::min(b0 + kFinBlock, seg_off[sg + 1])));
+    for (int32_t b0 = seg_off[sg]; b0 < seg_off[sg + 1]; b0 += kFinBlock2)
+      blocks2.push_back(make_int2(b0, std::min(b0 + kFinBlock2, seg_off[sg + 1])));
   }
   std::vector<int64_t> pushes;
   int r = run_items((int32_t)blocks.size(), threads, w, pushes,
@@ -339,12 +352,28 @@ int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t*
                         excess[i] = exl[i];       // L_i: supply b_i minus outflow
                         excess[n + i] = -exl[i];  // R_i: inflow minus demand b_i (z is symmetric)
                       }
-                      return solve_range(n, blocks[k].x, blocks[k].y, lam, irp, iec, twin, y, F, w, sr, p);
+                      return solve_range(n, blocks[k].x, blocks[k].y, lam, nullptr, irp, iec, twin, y, F, w,
+                                         sr, p);
                     });
+  int64_t* pi_start = w->pi_start.data();
+  if (r == 0)  // the potentials at phase 2's start, per block (every block copies its own nodes)
+    r = run_items((int32_t)blocks2.size(), threads, w, pushes, [&](int32_t k, Searcher&, int64_t*) {
+      const int32_t a = blocks2[k].x, b = blocks2[k].y;
+      std::copy(pi + a, pi + b, pi_start + a);
+      std::copy(pi + n + a, pi + n + b, pi_start + n + a);
+      return 0;
+    });
+  if (r == 0)
+    r = run_items((int32_t)blocks2.size(), threads, w, pushes,
+                  [&](int32_t k, Searcher& sr, int64_t* p) {
+                    return solve_range(n, blocks2[k].x, blocks2[k].y, nullptr, pi_start, irp, iec, twin, y, F,
+                                       w, sr, p);
+                  });
   if (r == 0)
     r = run_items((int32_t)segs.size(), threads, w, pushes, [&](int32_t k, Searcher& sr, int64_t* p) {
       const int32_t sg = segs[k];
-      const int q = solve_range(n, seg_off[sg], seg_off[sg + 1], nullptr, irp, iec, twin, y, F, w, sr, p);
+      const int q = solve_range(n, seg_off[sg], seg_off[sg + 1], nullptr, nullptr, irp, iec, twin, y, F, w,
+                                sr, p);
       if (q != 0) return q;
       int st = 0;
       for (int32_t i = seg_off[sg]; i < seg_off[sg + 1]; ++i) {

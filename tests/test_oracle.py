@@ -266,7 +266,7 @@ def test_finisher_reaches_candidate_optimum(oracle_lib):
 
 @pytest.mark.parametrize("kind,n,seed", [("uniform", 9000, 3), ("mixture", 7000, 4)])
 def test_blocked_finisher_reaches_candidate_optimum(oracle_lib, kind, n, seed):
-    # several finisher blocks (2048 nodes each): phase 1 per block, phase 2 for the rest
+    # several finisher blocks (2048 nodes each): phase 1 per block, phases 2 and 3 for the rest
     inst = I.make_instance(kind, n, seed, 10)
     xy, rp, col = inst["xy"], inst["row_ptr"], inst["col"]
     cost = oracle_lib.cost_table(xy, rp, col)
@@ -277,6 +277,24 @@ def test_blocked_finisher_reaches_candidate_optimum(oracle_lib, kind, n, seed):
     b2 = oracle_lib.bound2(rp, col, cost, lam2, 9)
     assert oracle_lib.certify(xy, rp, col, x2, lam2, 9, b2, full_scan=False) == 0
     assert abs(b2 / 1024.0 - highs_opt(xy, rp, col)) < 1e-6 * b2 / 1024.0
+
+
+def test_three_phase_finisher_certified_on_many_blocks(oracle_lib):
+    # 40,000 nodes: 20 phase-1 blocks and 3 phase-2 blocks; lambda after 64
+    # sweeps leaves many rows off.  The certificate (x feasible, complementary
+    # slackness, equal cost and bound) proves the result optimal on the graph,
+    # and the finisher from lambda = 0 reaches the same optimum.
+    inst = I.make_instance("uniform", 40000, 6, 6)
+    xy, rp, col = inst["xy"], inst["row_ptr"], inst["col"]
+    cost = oracle_lib.cost_table(xy, rp, col)
+    st, lam, it, _, _ = oracle_lib.gdp(rp, col, cost, np.zeros(40000, np.int32), 8, 2, 64)
+    bad, _ = oracle_lib.extract(rp, col, cost, lam, 8)
+    fst, x2, lam2, aug = oracle_lib.finisher(xy, rp, col, cost, lam, 8)
+    assert fst == 0 and aug >= bad // 2 > 1000
+    b2 = oracle_lib.bound2(rp, col, cost, lam2, 9)
+    assert oracle_lib.certify(xy, rp, col, x2, lam2, 9, b2, full_scan=False) == 0
+    fst0, x20, lam20, aug0 = oracle_lib.finisher(xy, rp, col, cost, np.zeros(40000, np.int32), 8)
+    assert fst0 == 0 and oracle_lib.bound2(rp, col, cost, lam20, 9) == b2
 
 
 def test_finisher_infeasible_graph(oracle_lib):
