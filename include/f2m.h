@@ -26,7 +26,8 @@
  * LB = 2 sum lambda + sum_e min(0, z_e), in units of 2^-frac_bits.  Every result
  * is bit-exact and independent of thread scheduling.
  *
- * A solve repeats: GDP to a fixed point; an all-pairs pricing scan that adds
+ * A solve repeats: a GDP phase (to a fixed point, or max_iters sweeps); an
+ * all-pairs pricing scan that adds
  * every non-candidate edge with z < 0 (the candidate graph may miss optimal
  * edges, Section 5.3); primal x from the signs of z (rule 7); where that x is
  * infeasible (the degenerate stops of Section 3, last paragraph) an exact
@@ -290,7 +291,8 @@ typedef struct f2m_batch f2m_batch;  /* opaque, library-owned */
 
 /* Creates a batch of `count` instances, solved together: every device step of
  * f2m_solve_batch (one persistent GDP launch per phase, with instances that
- * reached their fixed point frozen; one pricing scan over the pair tiles of the
+ * reached their fixed point frozen, for max_iters sweeps at most; one pricing
+ * scan over the pair tiles of the
  * instances that need one; one merge; one extraction; one finisher call) covers
  * all instances, and each instance's lambda, x and bound are those of its own
  * f2m_solve (the instances are kept apart as contiguous node ranges).

@@ -482,7 +482,8 @@ static f2m_status cluster_plan(f2m_batch* b) {
 }
 
 // A GDP phase with one cluster per active instance: the classes run side by
-// side on their own streams; every instance stops at its own fixed point.
+// side on their own streams; every instance stops at its own fixed point or
+// after max_iters sweeps.
 static f2m_status batch_cluster_phase(f2m_batch* b, const std::vector<uint8_t>& active,
                                       std::vector<int64_t>& sweeps_out, double* ms) {
   f2m_ctx* c = b->u;
