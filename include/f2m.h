@@ -27,12 +27,12 @@
  * is bit-exact and independent of thread scheduling.
  *
  * A solve repeats: a GDP phase (to a fixed point, or max_iters sweeps); an
- * all-pairs pricing scan that adds
- * every non-candidate edge with z < 0 (the candidate graph may miss optimal
- * edges, Section 5.3); primal x from the signs of z (rule 7); where that x is
- * infeasible (the degenerate stops of Section 3, last paragraph) an exact
- * min-cost-flow finisher on the host, after which lambda has frac_bits + 1
- * bits.  It ends when a scan with the final lambda finds nothing: x and lambda
+ * all-pairs pricing scan that adds every non-candidate edge with z < 0 (the
+ * candidate graph may miss optimal edges, Section 5.3); primal x from the
+ * signs of z (rule 7); where that x is infeasible (the degenerate stops of
+ * Section 3, last paragraph) an exact min-cost-flow finisher on the host,
+ * after which lambda has frac_bits + 1 bits.  It ends when a scan with the
+ * final lambda finds nothing: x and lambda
  * are then certified optimal for the COMPLETE graph on the points.
  *
  * Conventions.
