@@ -32,8 +32,8 @@
  * signs of z (rule 7); where that x is infeasible (the degenerate stops of
  * Section 3, last paragraph) an exact min-cost-flow finisher on the host,
  * after which lambda has frac_bits + 1 bits.  It ends when a scan with the
- * final lambda finds nothing: x and lambda
- * are then certified optimal for the COMPLETE graph on the points.
+ * final lambda finds nothing: x and lambda are then certified optimal for the
+ * COMPLETE graph on the points.
  *
  * Conventions.
  *  - Pointers marked "host or device" may point to either; the library asks
