@@ -578,9 +578,9 @@ static void build_tiles(const f2m_ctx* c, std::vector<int4>& tiles) {
     if (!c->seg_scan.empty() && !c->seg_scan[s]) continue;
     const int32_t a = c->seg_off[s], b = c->seg_off[s + 1];
     for (int32_t i0 = a; i0 < b; i0 += kPricingTile)
-      for (int32_t j0 = i0; j0 < b; j0 += kPricingTile)
+      for (int32_t j0 = i0; j0 < b; j0 += kPricingJ)  // half-height tiles: a shorter last wave
         tiles.push_back(make_int4(i0, i0 + kPricingTile < b ? i0 + kPricingTile : b, j0,
-                                  j0 + kPricingTile < b ? j0 + kPricingTile : b));
+                                  j0 + kPricingJ < b ? j0 + kPricingJ : b));
   }
 }
 

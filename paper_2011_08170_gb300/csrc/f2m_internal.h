@@ -94,7 +94,8 @@ cudaError_t launch_extract(const int32_t* rp, const int2* ec, const int32_t* bde
 cudaError_t launch_halve(const int32_t* lam_in, int32_t* lam_out, int32_t n, cudaStream_t st);
 // all-pairs pricing scan: pairs (u < v) outside the CSR with z < 0
 // Tile pairs {i0, i1, j0, j1}: test i in [i0, i1) against j in [j0, j1), j > i.
-constexpr int kPricingTile = 1024;
+constexpr int kPricingTile = 1024;  // i-points of a pricing tile pair (and the most j-points)
+constexpr int kPricingJ = 512;      // j-points of a tile pair in the lists built for a scan
 // pts[v] = {x, y, s, node perm[v]} (perm NULL: node v), s the filter radius of the node
 cudaError_t launch_pricing_prep(const int2* xy, const int32_t* lam, const int32_t* perm, int32_t n, int32_t fb,
                                 float4* pts, cudaStream_t st);

@@ -4,11 +4,13 @@
 // miss optimal edges (Section 5.3); this scan finds every such edge so the
 // final duals are feasible for the complete graph.
 //
-// N-body tiling: the host lists tile pairs (TILE x TILE blocks of the pair
-// triangle of each segment, i.e. instance), handed out by an atomic counter;
-// a CTA keeps TILE j-points in shared memory and each thread P i-points in
-// registers, two at a time in packed fp32x2 registers (Blackwell's two-lane
-// FADD2 / FFMA2: one issue slot for two pairs).
+// N-body tiling: the host lists tile pairs (blocks of the pair triangle of
+// each segment, i.e. instance: up to kPricingTile i-points by up to
+// kPricingTile j-points; the scan's lists use kPricingJ j-points, so the last
+// wave of tile pairs is short), handed out by an atomic counter; a CTA keeps
+// the j-points in shared memory and each thread P i-points in registers, two
+// at a time in packed fp32x2 registers (Blackwell's two-lane FADD2 / FFMA2:
+// one issue slot for two pairs).
 //
 // Filter.  r_v = max(lambda_v 2^-fb + 1/4, 0), s_v = (r_v + 2)(1 + 2^-17) in
 // fp32, a_v = x_v - s_v, c_v = x_v + s_v.  Per pair, with t = s_u + s_v:
@@ -217,7 +219,9 @@ pricing_kernel(const float4* __restrict__ pts, const int2* __restrict__ xy,
       nc[q] = make_float2(-c[0], -c[1]);
       ny[q] = make_float2(-y[0], -y[1]);
     }
-    for (int k = threadIdx.x; k < kPriceTile; k += kPriceThreads) {
+    // the tile's j-points, rounded up to whole chunks (at most kPriceTile)
+    const int kend = min(kPriceTile, (tl.w - tl.z + kPriceChunk - 1) / kPriceChunk * kPriceChunk);
+    for (int k = threadIdx.x; k < kend; k += kPriceThreads) {
       const int j = tl.z + k;
       if (j < tl.w) {
         const float4 v = pts[j];
@@ -230,7 +234,7 @@ pricing_kernel(const float4* __restrict__ pts, const int2* __restrict__ xy,
       }
     }
     __syncthreads();
-    for (int k0 = 0; k0 < kPriceTile; k0 += kPriceChunk) {
+    for (int k0 = 0; k0 < kend; k0 += kPriceChunk) {
       int nh = 0;  // entries in this warp's list (the same in every lane)
 #pragma unroll 2
       for (int g = k0; g < k0 + kPriceChunk; g += kPriceGroup) {
