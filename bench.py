@@ -153,9 +153,10 @@ def cpu_oracle_estimate(d, gpu_counts, budget_s=12.0):
     """Time the CPU oracle on bounded samples of the same instance and scale.
 
     Samples: oracle GDP sweeps on the full instance from lambda = 0 (as many as
-    fit in ~40% of the budget) and the oracle pricing scan over the first rows
-    (~40% of the budget).  Scaled by the sweep count and pricing-round count of
-    the solve; the finisher's host time is added as measured.  Single thread.
+    fit in ~40% of the budget, at most the solve's sweep count), the oracle
+    finisher from the lambda those sweeps reach, and the oracle pricing scan
+    over the first rows (~40% of the budget).  Sweeps and pairs are scaled by
+    the sweep count and pricing-round count of the solve.  Single thread.
     """
     import oracle
     xy, rp, col = d["xy"], d["row_ptr"], d["col"]
@@ -164,10 +165,13 @@ def cpu_oracle_estimate(d, gpu_counts, budget_s=12.0):
     lam = np.zeros(n, np.int32)
     t0 = time.perf_counter()
     sweeps = 0
-    while time.perf_counter() - t0 < 0.4 * budget_s or sweeps < 2:
+    while (time.perf_counter() - t0 < 0.4 * budget_s and sweeps < gpu_counts["iterations"]) or sweeps < 2:
         st, lam, _, _ = oracle.sweep(rp, col, cost, lam, 8, 2)
         sweeps += 1
     t_sweep = (time.perf_counter() - t0) / sweeps
+    t1 = time.perf_counter()
+    fst, _, _, fin_aug = oracle.finisher(xy, rp, col, cost, lam, 8)
+    t_fin = time.perf_counter() - t1
     rows, pairs, t_pr = 0, 0, 0.0
     step = max(1, n // 400)
     while t_pr < 0.4 * budget_s and rows < n:
@@ -179,12 +183,12 @@ def cpu_oracle_estimate(d, gpu_counts, budget_s=12.0):
     t_pair = t_pr / max(pairs, 1)
     total_pairs = n * (n - 1) / 2
     est_ms = 1e3 * (gpu_counts["iterations"] * t_sweep
-                    + gpu_counts["pricing_rounds"] * total_pairs * t_pair) + gpu_counts["ms_finish"]
-    sample = (f"{sweeps} oracle sweeps on the full instance ({t_sweep * 1e3:.1f} ms each) and "
-              f"{pairs:.3g} oracle pricing pairs over rows 0..{rows} ({t_pair * 1e9:.2f} ns/pair), "
-              f"scaled to {gpu_counts['iterations']} sweeps and {gpu_counts['pricing_rounds']} "
-              + (f"full scans; finisher host time added as measured ({gpu_counts['ms_finish']:.1f} ms)"
-                 if gpu_counts["ms_finish"] > 0 else "full scans; finisher time not included"))
+                    + gpu_counts["pricing_rounds"] * total_pairs * t_pair + t_fin)
+    sample = (f"{sweeps} oracle sweeps on the full instance ({t_sweep * 1e3:.1f} ms each), the oracle "
+              f"finisher from the lambda they reach ({t_fin * 1e3:.0f} ms, {fin_aug} augmentations, "
+              f"status {fst}) and {pairs:.3g} oracle pricing pairs over rows 0..{rows} "
+              f"({t_pair * 1e9:.2f} ns/pair), scaled to {gpu_counts['iterations']} sweeps and "
+              f"{gpu_counts['pricing_rounds']} full scans")
     return est_ms, sample
 
 
@@ -203,7 +207,7 @@ def run_reference(args, w, rank):
     counts = REFERENCE_COUNTS.get((args.workload, "fixed point" if mi >= 10 ** 5 else mi))
     if counts is None:
         r = oracle.solve(d["xy"], d["row_ptr"], d["col"], max_iters=mi)
-        counts = {"iterations": r.iterations, "pricing_rounds": r.pricing_rounds, "ms_finish": 0.0}
+        counts = {"iterations": r.iterations, "pricing_rounds": r.pricing_rounds}
     times = []
     sample = ""
     for i in range(args.warmup + args.steps):
@@ -229,10 +233,10 @@ def run_reference(args, w, rank):
 # oracle solve at n = 1e5 takes a minute or more).  c1 is small enough for the
 # oracle to solve outright.
 REFERENCE_COUNTS: dict = {
-    ("c2", 256): {"iterations": 256, "pricing_rounds": 2, "ms_finish": 0.0},
-    ("c3", 256): {"iterations": 256, "pricing_rounds": 2, "ms_finish": 0.0},
-    ("c2", "fixed point"): {"iterations": 3064, "pricing_rounds": 2, "ms_finish": 0.0},
-    ("c3", "fixed point"): {"iterations": 3169, "pricing_rounds": 2, "ms_finish": 0.0},
+    ("c2", 256): {"iterations": 256, "pricing_rounds": 2},
+    ("c3", 256): {"iterations": 256, "pricing_rounds": 2},
+    ("c2", "fixed point"): {"iterations": 3064, "pricing_rounds": 2},
+    ("c3", "fixed point"): {"iterations": 3169, "pricing_rounds": 2},
 }
 
 
@@ -427,8 +431,7 @@ def main():
             "roofline": roofline, "clocks": clk, "gpu_launches": int(launches)}
     if rank == 0 and not args.no_cpu_baseline and not variant:
         est, sample = cpu_oracle_estimate(d, {"iterations": inf0["iterations"],
-                                              "pricing_rounds": inf0["pricing_rounds"],
-                                              "ms_finish": line["breakdown_ms"]["ms_finish"]})
+                                              "pricing_rounds": inf0["pricing_rounds"]})
         line["cpu_baseline"] = {"value": est, "unit": "ms", "cores": 1, "kind": "oracle",
                                 "sample": sample}
     if rank == 0:
