@@ -1,14 +1,17 @@
-"""Benchmark: milliseconds to a certified F2M optimum, plus the GDP sweep's GB/s.
+"""Benchmark: milliseconds to a certified F2M optimum, with the roofline of the
+dominant kernel (the pricing scan's FP32 rate or the GDP sweep's GB/s).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c1|c2|c3|c4|c5]
     python bench.py --impl reference ...     # the CPU oracle on the same workload
+    python bench.py --max-iters 1000000      # every GDP phase to its fixed point
+    python bench.py --pricing 2              # scans skip tile pairs that cannot hold z < 0
     python bench.py --update classes --shift 1   # class-by-class GDP sweeps (variant)
     python bench.py --degrees 1:4                # fractional b-matching, b_v in 1..4 (variant)
 
-A step is one full f2m_solve from lambda = 0 on a fresh context: GDP phases,
-pricing scans over all n(n-1)/2 pairs, CSR merges, sign extraction and the
-exact finisher, until the solution is certified optimal for the complete
-graph.  Contexts are created before the timed region; L2 is flushed (a 256 MB
+A step is one full f2m_solve from lambda = 0 on a fresh context: GDP phases
+(256 sweeps at most each, by default), pricing scans over all n(n-1)/2 pairs,
+CSR merges, sign extraction and the exact finisher, until the solution is
+certified optimal for the complete graph.  Contexts are created before the timed region; L2 is flushed (a 256 MB
 device write) before every timed step.  Each step is bracketed by CUDA events
 on the stream the library runs on.
 
