@@ -18,7 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = ["f2m_oracle.c", "certify.c"]
+_SOURCES = ["f2m_oracle.c", "certify.c", "subtour.c"]
 
 OR_OK = 0
 OR_INVALID = 1
@@ -84,7 +84,7 @@ def lib():
         L.or_extract.restype = C.c_int64
         L.or_extract.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_void_p, _i32p, C.c_int32, _u8p]
         L.or_finisher.restype = C.c_int
-        L.or_finisher.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _i32p, C.c_void_p, _i32p, C.c_int32, _u8p,
+        L.or_finisher.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_void_p, _i32p, C.c_int32, _u8p,
                                   _i32p, C.POINTER(C.c_int64)]
         L.or_pricing_rows.restype = C.c_int64
         L.or_pricing_rows.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _i32p, C.c_int32,
@@ -115,6 +115,28 @@ def lib():
         L.or_gdp_gs.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_void_p, _i32p, C.c_int32,
                                 C.c_int32, C.c_int32, C.c_int64, _i32p, C.POINTER(C.c_int64),
                                 C.c_void_p, C.c_void_p, C.c_int64]
+        L.or_cut_z.restype = C.c_int64
+        L.or_cut_z.argtypes = [C.c_int32, _i32p, C.c_int32, C.c_void_p, C.c_void_p, _i32p, C.c_void_p,
+                               C.c_int32, C.c_int32, C.c_int32]
+        L.or_cut_bound2.restype = C.c_int64
+        L.or_cut_bound2.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_int32, C.c_void_p, C.c_void_p,
+                                    _i32p, C.c_void_p, C.c_int32]
+        L.or_cut_sweep.restype = C.c_int
+        L.or_cut_sweep.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_int32, C.c_void_p, C.c_void_p,
+                                   _i32p, C.c_void_p, C.c_int32, C.c_int32, _i32p, C.c_void_p,
+                                   C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.or_cut_gdp.restype = C.c_int
+        L.or_cut_gdp.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_int32, C.c_void_p, C.c_void_p,
+                                 C.c_int32, C.c_int32, C.c_int64, _i32p, C.c_void_p,
+                                 C.POINTER(C.c_int64), C.c_void_p, C.c_void_p, C.c_int64]
+        L.or_cut_extract.restype = C.c_int64
+        L.or_cut_extract.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_int32, C.c_void_p, C.c_void_p,
+                                     _i32p, C.c_void_p, C.c_int32, _u8p]
+        L.or_separate.restype = C.c_int32
+        L.or_separate.argtypes = [C.c_int32, _i32p, _i32p, _u8p, _i32p]
+        L.or_cut_pricing.restype = C.c_int64
+        L.or_cut_pricing.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_int32, C.c_void_p, C.c_void_p,
+                                     _i32p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int64]
         _lib = L
     return _lib
 
@@ -234,14 +256,15 @@ def extract(row_ptr, col, cost, lam, fb=8, b=None):
     return int(bad), x2
 
 
-def finisher(xy, row_ptr, col, cost, lam, F=8, b=None):
-    """Exact min-cost-flow finisher: returns (status, x2, lam2 at F+1 bits, augmentations)."""
+def finisher(row_ptr, col, cost, lam, F=8, b=None):
+    """Exact min-cost-flow finisher (plain successive shortest paths): returns
+    (status, x2, lam2 at F+1 bits, augmentations)."""
     x2 = np.zeros(np.asarray(col).size, dtype=np.uint8)
     lam = _i32(lam)
     bb = _degrees(b, lam.size)
     lam2 = np.zeros_like(lam)
     aug = C.c_int64()
-    st = lib().or_finisher(lam.size, _i32(xy).reshape(-1), _i32(row_ptr), _i32(col), _i32(cost),
+    st = lib().or_finisher(lam.size, _i32(row_ptr), _i32(col), _i32(cost),
                            _ptr(bb), lam, F, x2, lam2, C.byref(aug))
     return st, x2, lam2, aug.value
 
@@ -358,3 +381,109 @@ def knn_csr(xy, k):
     row_ptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(np.bincount(pairs // n, minlength=n), out=row_ptr[1:])
     return row_ptr.astype(np.int32), (pairs % n).astype(np.int32)
+
+
+# ---- subtour-elimination cuts (subtour.c) ------------------------------------
+
+class Cuts:
+    """A layered cut family: comp int32 [L, n] (-1: no cut of the layer, else the
+    cut's index in its layer) and ncuts [L]."""
+
+    def __init__(self, n, layers=()):
+        self.n = n
+        self.comp = np.zeros((0, n), dtype=np.int32)
+        self.ncuts = np.zeros(0, dtype=np.int32)
+        for comp, m in layers:
+            self.add(comp, m)
+
+    def add(self, comp, m):
+        comp = _i32(comp).reshape(1, self.n)
+        self.comp = np.ascontiguousarray(np.concatenate([self.comp, comp]), dtype=np.int32)
+        self.ncuts = np.ascontiguousarray(np.append(self.ncuts, int(m)), dtype=np.int32)
+
+    @property
+    def L(self):
+        return int(self.ncuts.size)
+
+    @property
+    def total(self):
+        return int(self.ncuts.sum())
+
+    def args(self):
+        return (self.L, self.comp.ctypes.data if self.L else None,
+                self.ncuts.ctypes.data if self.L else None)
+
+
+def _mu(mu, cuts):
+    mu = np.zeros(cuts.total, np.int32) if mu is None else _i32(mu).copy()
+    assert mu.size == cuts.total
+    return mu
+
+
+def _mu_ptr(mu):
+    return mu.ctypes.data if mu.size else None
+
+
+def cut_z(xy, cuts, lam, mu, fb, u, v) -> int:
+    mu = _mu(mu, cuts)
+    return int(lib().or_cut_z(cuts.n, _i32(xy).reshape(-1), *cuts.args(), _i32(lam), _mu_ptr(mu), fb, u, v))
+
+
+def cut_bound2(row_ptr, col, cost, cuts, lam, mu, fb=8) -> int:
+    mu = _mu(mu, cuts)
+    return int(lib().or_cut_bound2(cuts.n, _i32(row_ptr), _i32(col), _i32(cost), *cuts.args(), _i32(lam),
+                                   _mu_ptr(mu), fb))
+
+
+def cut_sweep(row_ptr, col, cost, cuts, lam, mu, F=8, shift=2):
+    """One Jacobi sweep of node and cut duals: (status, lam, mu, bound2, changed)."""
+    lam = _i32(lam)
+    mu = _mu(mu, cuts)
+    nl = np.zeros_like(lam)
+    nm = np.zeros_like(mu)
+    b2, ch = C.c_int64(), C.c_int64()
+    st = lib().or_cut_sweep(cuts.n, _i32(row_ptr), _i32(col), _i32(cost), *cuts.args(), lam, _mu_ptr(mu),
+                            F, shift, nl, _mu_ptr(nm), C.byref(b2), C.byref(ch))
+    return st, nl, nm, b2.value, ch.value
+
+
+def cut_gdp(row_ptr, col, cost, cuts, lam0, mu0=None, F=8, shift=2, max_iters=1000, trace=False):
+    """GDP phase with cuts: (status, lam, mu, iters, trace_bound2, trace_changed)."""
+    lam = _i32(lam0).copy()
+    mu = _mu(mu0, cuts)
+    it = C.c_int64()
+    tb = np.zeros(max_iters if trace else 1, dtype=np.int64)
+    tc = np.zeros_like(tb)
+    st = lib().or_cut_gdp(cuts.n, _i32(row_ptr), _i32(col), _i32(cost), *cuts.args(), F, shift, max_iters,
+                          lam, _mu_ptr(mu), C.byref(it), tb.ctypes.data if trace else None,
+                          tc.ctypes.data if trace else None, max_iters if trace else 0)
+    k = it.value
+    return st, lam, mu, k, (tb[:k] if trace else None), (tc[:k] if trace else None)
+
+
+def cut_extract(row_ptr, col, cost, cuts, lam, mu, fb=8):
+    mu = _mu(mu, cuts)
+    x2 = np.zeros(np.asarray(col).size, dtype=np.uint8)
+    bad = lib().or_cut_extract(cuts.n, _i32(row_ptr), _i32(col), _i32(cost), *cuts.args(), _i32(lam),
+                               _mu_ptr(mu), fb, x2)
+    return int(bad), x2
+
+
+def separate(row_ptr, col, x2):
+    """One cut layer from the components of the support of x2: (comp [n], ncuts)."""
+    n = np.asarray(row_ptr).size - 1
+    comp = np.zeros(n, dtype=np.int32)
+    m = lib().or_separate(n, _i32(row_ptr), _i32(col), np.ascontiguousarray(x2, dtype=np.uint8), comp)
+    return comp, int(m)
+
+
+def cut_pricing(xy, row_ptr, col, cuts, lam, mu, fb=8):
+    """Pairs (u < v) outside the CSR with z < 0, cut duals included; int32 [m, 2]."""
+    mu = _mu(mu, cuts)
+    xy, row_ptr, col, lam = _i32(xy), _i32(row_ptr), _i32(col), _i32(lam)
+    cnt = lib().or_cut_pricing(cuts.n, xy.reshape(-1), row_ptr, col, *cuts.args(), lam, _mu_ptr(mu), fb,
+                               None, 0)
+    out = np.zeros((max(cnt, 1), 2), dtype=np.int32)
+    lib().or_cut_pricing(cuts.n, xy.reshape(-1), row_ptr, col, *cuts.args(), lam, _mu_ptr(mu), fb,
+                         out.ctypes.data, cnt)
+    return int(cnt), out[:cnt]

@@ -277,6 +277,9 @@ int64_t or_extract(int32_t n, const int32_t* row_ptr, const int32_t* col,
 }
 
 /* ---- exact finisher: min-cost flow on the bipartite double cover ----------
+ * Section 3 (last paragraph) leaves the repair of degenerate stops to the
+ * problem at hand.  For F2M it is exact: the fractional 2-matching LP on a
+ * graph is half of the transportation problem on its bipartite double cover.
  * Node ids: left copy L_v = v, right copy R_v = n + v.  Entry e = (u -> v) is
  * the arc L_u -> R_v, capacity 1, cost C_e = c_e * 2^F.  Every L_v has supply b_v
  * (2 for the fractional 2-matching), every R_v demand b_v.
@@ -286,33 +289,14 @@ int64_t or_extract(int32_t n, const int32_t* row_ptr, const int32_t* col,
  * Reduced cost of a residual arc i -> j: C(i, j) - pi(i) + pi(j).
  * Warm start: pi(L_v) = lam_v, pi(R_v) = -lam_v (reduced cost of an arc = z_e),
  * arcs with z_e < 0 saturated, so every residual reduced cost is >= 0.
- * Successive shortest paths: repeatedly take the node with positive excess and
- * the smallest key, run Dijkstra (ties by key) to the first node with negative
- * excess, push one unit, raise pi(i) by d(t) - d(i) on nodes settled before t.
- * Key of a node: 2*rank(v) for L_v and 2*rank(v) + 1 for R_v, where rank(v) is
- * the position of v when points are ordered by Morton code (bit b of x at bit
- * 2b, bit b of y at bit 2b+1), ties by node id -- so that successive paths are
- * searched in nearby parts of the plane.  (The paper gives no finisher; this
- * order is a stated choice.)
- *
- * Three phases, so that the first two can run block by block in parallel with
- * a result that does not depend on the schedule.  In a blocked phase with block
- * size B, block k holds the nodes of rank in [k*B, (k+1)*B), both copies.
- *   Blocked phase, for each block in turn: its sources in key order, each
- *   searched as above except that (a) a node outside the block is never
- *   settled: if a heap item of an outside node comes to the top, or the heap
- *   empties, the search is dropped with nothing changed and the next source of
- *   the block is taken; (b) reduced costs of arcs into outside nodes use those
- *   nodes' potentials as they were when the phase began.  Potentials only
- *   grow, so every residual reduced cost stays >= 0; arcs and potentials a
- *   block reads are changed by that block alone, so the blocks do not depend
- *   on one another's progress.
- *   Phase 1: blocked, B = OR_FIN_BLOCK.  Phase 2: blocked, B = OR_FIN_BLOCK2,
- *   for the searches phase 1 dropped.  Phase 3: the plain search over all
- *   nodes in key order for what is left. */
-
-#define OR_FIN_BLOCK 2048
-#define OR_FIN_BLOCK2 16384
+ * Successive shortest paths (the textbook primal-dual method), one unit at a
+ * time: take the node with positive excess and the smallest key, run Dijkstra
+ * on the reduced costs from it (heap order: distance, then key) to the first
+ * settled node t with negative excess, push one unit along the path, and raise
+ * pi(i) by d(t) - d(i) on every node i settled before t.  Key of a node: 2v for
+ * L_v and 2v + 1 for R_v.  (The paper gives no finisher; the key order is a
+ * stated choice that makes the result deterministic.)  A source from which no
+ * deficit node is reachable means the graph has no fractional 2-matching. */
 
 typedef struct { int64_t d; int32_t key; int32_t v; } or_hitem;
 
@@ -342,32 +326,6 @@ static or_hitem or_hpop(or_hitem* h, int64_t* sz) {
   return top;
 }
 
-typedef struct { uint64_t code; int32_t v; } or_mkey;
-
-static int cmp_mkey(const void* a, const void* b) {
-  const or_mkey* x = (const or_mkey*)a;
-  const or_mkey* y = (const or_mkey*)b;
-  if (x->code != y->code) return (x->code > y->code) - (x->code < y->code);
-  return (x->v > y->v) - (x->v < y->v);
-}
-
-/* rank[v] = position of point v in (Morton code, id) order */
-static void or_morton_rank(int32_t n, const int32_t* xy, int32_t* rank) {
-  or_mkey* k = (or_mkey*)malloc(sizeof(or_mkey) * (size_t)(n > 0 ? n : 1));
-  for (int32_t v = 0; v < n; ++v) {
-    uint64_t code = 0;
-    for (int b = 0; b < 20; ++b) {
-      code |= (uint64_t)(((uint32_t)xy[2 * (int64_t)v] >> b) & 1u) << (2 * b);
-      code |= (uint64_t)(((uint32_t)xy[2 * (int64_t)v + 1] >> b) & 1u) << (2 * b + 1);
-    }
-    k[v].code = code;
-    k[v].v = v;
-  }
-  qsort(k, (size_t)n, sizeof(or_mkey), cmp_mkey);
-  for (int32_t r = 0; r < n; ++r) rank[k[r].v] = r;
-  free(k);
-}
-
 static int32_t or_find(const int32_t* row_ptr, const int32_t* col, int32_t u, int32_t v) {
   int32_t lo = row_ptr[u], hi = row_ptr[u + 1] - 1;
   while (lo <= hi) {
@@ -378,15 +336,18 @@ static int32_t or_find(const int32_t* row_ptr, const int32_t* col, int32_t u, in
   return -1;
 }
 
-int or_finisher(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int32_t* col,
+static int32_t or_key(int32_t n, int32_t i) { return i < n ? 2 * i : 2 * (i - n) + 1; }
+
+int or_finisher(int32_t n, const int32_t* row_ptr, const int32_t* col,
                 const int32_t* cost, const int32_t* b, const int32_t* lam, int32_t F, uint8_t* x2,
                 int32_t* lam2, int64_t* augmentations) {
   int64_t nnz = row_ptr[n];
   int32_t N = 2 * n;
-  int32_t* rev = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
-  int32_t* own = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1)); /* row of e */
-  uint8_t* y = (uint8_t*)calloc((size_t)(nnz > 0 ? nnz : 1), 1);
-  int64_t* pi = (int64_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(int64_t));
+  size_t ne = (size_t)(nnz > 0 ? nnz : 1);
+  int32_t* rev = (int32_t*)malloc(sizeof(int32_t) * ne);  /* entry (v -> u) of entry (u -> v) */
+  int32_t* own = (int32_t*)malloc(sizeof(int32_t) * ne);  /* row of each entry */
+  uint8_t* y = (uint8_t*)calloc(ne, 1);                   /* flow on arc L_u -> R_v */
+  int64_t* pi = (int64_t*)calloc((size_t)N, sizeof(int64_t));
   int64_t* ex = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
   int64_t* dist = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
   int32_t* par = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);   /* entry used to reach */
@@ -394,18 +355,9 @@ int or_finisher(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int3
   int64_t* done = (int64_t*)calloc((size_t)N, sizeof(int64_t));   /* stamp: settled */
   int32_t* settled = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
   or_hitem* heap = (or_hitem*)malloc(sizeof(or_hitem) * (size_t)(nnz + N + 1));
-  int32_t* key = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);   /* tie-break key per node */
-  int32_t* by_key = (int32_t*)malloc(sizeof(int32_t) * (size_t)N); /* node with each key */
   int status = OR_OK;
   int64_t aug = 0;
 
-  or_morton_rank(n, xy, key);
-  for (int32_t v = 0; v < n; ++v) {
-    int32_t r = key[v];
-    key[v] = 2 * r;
-    key[n + v] = 2 * r + 1;
-  }
-  for (int32_t i = 0; i < N; ++i) by_key[key[i]] = i;
   for (int32_t u = 0; u < n; ++u)
     for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
       rev[e] = or_find(row_ptr, col, col[e], u);
@@ -425,92 +377,65 @@ int or_finisher(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int3
     ex[n + u] = in - bu;   /* R_u: inflow minus demand b_u */
   }
 
-  int64_t* pi0 = (int64_t*)malloc(sizeof(int64_t) * (size_t)N); /* potentials at the phase's start */
-  int32_t* rank = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
-  for (int32_t v = 0; v < n; ++v) rank[v] = key[v] / 2;
-
+  /* Excess of a source only falls and a deficit node only fills, so taking the
+   * keys once in ascending order is taking the smallest key with excess. */
   int64_t stamp = 0;
-  for (int32_t phase = 1; phase <= 3 && status == OR_OK; ++phase) {
-    const int32_t blocked = phase < 3;
-    const int32_t bsz = phase == 1 ? OR_FIN_BLOCK : OR_FIN_BLOCK2;
-    const int32_t nblocks = blocked ? (n + bsz - 1) / bsz : 1;
-    if (blocked) memcpy(pi0, pi, sizeof(int64_t) * (size_t)N);
-    for (int32_t blk = 0; blk < nblocks && status == OR_OK; ++blk) {
-      /* blocked phase: keys of block blk; phase 3: every key */
-      const int32_t k0 = blocked ? 2 * blk * bsz : 0;
-      int32_t k1 = blocked ? 2 * (blk + 1) * bsz : N;
-      if (k1 > N) k1 = N;
-      for (int32_t next = k0; next < k1 && status == OR_OK; ++next) {
-        const int32_t src = by_key[next];
-        while (ex[src] > 0) {
-          ++stamp;
-          int64_t hs = 0, ns = 0;
-          int32_t t = -1;
-          dist[src] = 0; seen[src] = stamp; par[src] = -1;
-          or_hpush(heap, &hs, (or_hitem){0, key[src], src});
-          while (hs > 0) {
-            or_hitem it = or_hpop(heap, &hs);
-            int32_t i = it.v;
-            if (blocked && rank[i < n ? i : i - n] / bsz != blk) break; /* dropped */
-            if (done[i] == stamp || it.d != dist[i]) continue;
-            done[i] = stamp;
-            if (ex[i] < 0) { t = i; break; }
-            settled[ns++] = i;
-            if (i < n) { /* L_i: forward arcs with no flow */
-              for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-                if (y[e]) continue;
-                int32_t j = n + col[e];
-                int32_t out = blocked && rank[col[e]] / bsz != blk;
-                int64_t rc = ((int64_t)cost[e] << F) - pi[i] + (out ? pi0[j] : pi[j]);
-                int64_t nd = dist[i] + rc;
-                if (out) { or_hpush(heap, &hs, (or_hitem){nd, key[j], j}); continue; }
-                if (done[j] != stamp && (seen[j] != stamp || nd < dist[j])) {
-                  seen[j] = stamp; dist[j] = nd; par[j] = e;
-                  or_hpush(heap, &hs, (or_hitem){nd, key[j], j});
-                }
-              }
-            } else { /* R_v: reverse arcs of saturated entries (u -> v) */
-              int32_t v = i - n;
-              for (int32_t f = row_ptr[v]; f < row_ptr[v + 1]; ++f) {
-                int32_t e = rev[f]; /* entry (col[f] -> v) */
-                if (!y[e]) continue;
-                int32_t j = col[f];
-                int32_t out = blocked && rank[j] / bsz != blk;
-                int64_t rc = -((int64_t)cost[e] << F) - pi[i] + (out ? pi0[j] : pi[j]);
-                int64_t nd = dist[i] + rc;
-                if (out) { or_hpush(heap, &hs, (or_hitem){nd, key[j], j}); continue; }
-                if (done[j] != stamp && (seen[j] != stamp || nd < dist[j])) {
-                  seen[j] = stamp; dist[j] = nd; par[j] = e;
-                  or_hpush(heap, &hs, (or_hitem){nd, key[j], j});
-                }
-              }
+  for (int32_t k = 0; k < N && status == OR_OK; ++k) {
+    const int32_t src = (k & 1) ? n + k / 2 : k / 2; /* the node with key k */
+    while (ex[src] > 0) {
+      ++stamp;
+      int64_t hs = 0, ns = 0;
+      int32_t t = -1;
+      dist[src] = 0; seen[src] = stamp; par[src] = -1;
+      or_hpush(heap, &hs, (or_hitem){0, or_key(n, src), src});
+      while (hs > 0) {
+        or_hitem it = or_hpop(heap, &hs);
+        int32_t i = it.v;
+        if (done[i] == stamp || it.d != dist[i]) continue;
+        done[i] = stamp;
+        if (ex[i] < 0) { t = i; break; }
+        settled[ns++] = i;
+        if (i < n) { /* L_i: forward arcs with no flow */
+          for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            if (y[e]) continue;
+            int32_t j = n + col[e];
+            int64_t nd = dist[i] + ((int64_t)cost[e] << F) - pi[i] + pi[j];
+            if (done[j] != stamp && (seen[j] != stamp || nd < dist[j])) {
+              seen[j] = stamp; dist[j] = nd; par[j] = e;
+              or_hpush(heap, &hs, (or_hitem){nd, or_key(n, j), j});
             }
           }
-          if (t < 0) {
-            if (blocked) break;  /* dropped or nothing reachable: left to the next phase */
-            status = OR_INFEASIBLE;
-            break;
-          }
-          /* push one unit along the path, walking back from t to src */
-          for (int32_t j = t; j != src;) {
-            int32_t e = par[j];
-            if (j >= n) { y[e] = 1; j = own[e]; }      /* reached R_v by L_u -> R_v, e = (u -> v) */
-            else { y[e] = 0; j = n + col[e]; }         /* reached L_u by R_v -> L_u, e = (u -> v) */
-          }
-          ex[src] -= 1;
-          ex[t] += 1;
-          ++aug;
-          int64_t dt = dist[t];
-          for (int64_t k = 0; k < ns; ++k) {
-            int32_t i = settled[k];
-            pi[i] += dt - dist[i];
+        } else { /* R_v: reverse arcs of saturated entries (u -> v) */
+          int32_t v = i - n;
+          for (int32_t f = row_ptr[v]; f < row_ptr[v + 1]; ++f) {
+            int32_t e = rev[f]; /* entry (col[f] -> v) */
+            if (!y[e]) continue;
+            int32_t j = col[f];
+            int64_t nd = dist[i] - ((int64_t)cost[e] << F) - pi[i] + pi[j];
+            if (done[j] != stamp && (seen[j] != stamp || nd < dist[j])) {
+              seen[j] = stamp; dist[j] = nd; par[j] = e;
+              or_hpush(heap, &hs, (or_hitem){nd, or_key(n, j), j});
+            }
           }
         }
       }
+      if (t < 0) { status = OR_INFEASIBLE; break; }
+      /* push one unit along the path, walking back from t to src */
+      for (int32_t j = t; j != src;) {
+        int32_t e = par[j];
+        if (j >= n) { y[e] = 1; j = own[e]; }      /* reached R_v by L_u -> R_v, e = (u -> v) */
+        else { y[e] = 0; j = n + col[e]; }         /* reached L_u by R_v -> L_u, e = (u -> v) */
+      }
+      ex[src] -= 1;
+      ex[t] += 1;
+      ++aug;
+      int64_t dt = dist[t];
+      for (int64_t q = 0; q < ns; ++q) {
+        int32_t i = settled[q];
+        pi[i] += dt - dist[i];
+      }
     }
   }
-  free(pi0);
-  free(rank);
 
   if (status == OR_OK) {
     for (int32_t u = 0; u < n; ++u)
@@ -522,7 +447,6 @@ int or_finisher(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int3
     }
   }
   *augmentations = aug;
-  free(key); free(by_key);
   free(rev); free(own); free(y); free(pi); free(ex); free(dist); free(par);
   free(seen); free(done); free(settled); free(heap);
   return status;
@@ -721,7 +645,7 @@ or_result* or_solve(int32_t n, const int32_t* xy, const int32_t* row_ptr,
     if (bad > 0) {
       if (!p->finisher) { status = OR_NOT_CONVERGED; info->bound2 = or_bound2(n, r->row_ptr, r->col, cost, b, lam, F); break; }
       int64_t aug = 0;
-      st = or_finisher(n, xy, r->row_ptr, r->col, cost, b, lam, F, r->x2, lam2, &aug);
+      st = or_finisher(n, r->row_ptr, r->col, cost, b, lam, F, r->x2, lam2, &aug);
       info->finisher_calls += 1;
       info->augmentations += aug;
       if (st != OR_OK) { status = st; break; }

@@ -76,10 +76,11 @@ int64_t or_extract(int32_t n, const int32_t* row_ptr, const int32_t* col,
                    const int32_t* cost, const int32_t* b, const int32_t* lam, int32_t fb, uint8_t* x2);
 
 /* Exact finisher: min-cost flow on the bipartite double cover of the CSR graph,
- * warm-started from lam (F bits); successive shortest paths, sources and ties
- * in (Morton code of the point, id) order.  Writes x2 (half units) and lam2
- * (units 2^-(F+1)).  Returns OR_OK, OR_INFEASIBLE or OR_OVERFLOW. */
-int or_finisher(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int32_t* col,
+ * warm-started from lam (F bits); plain successive shortest paths over all
+ * nodes, sources and Dijkstra ties in key order (L_v: 2v, R_v: 2v + 1).
+ * Writes x2 (half units) and lam2 (units 2^-(F+1)).  Returns OR_OK,
+ * OR_INFEASIBLE or OR_OVERFLOW. */
+int or_finisher(int32_t n, const int32_t* row_ptr, const int32_t* col,
                 const int32_t* cost, const int32_t* b, const int32_t* lam, int32_t F, uint8_t* x2,
                 int32_t* lam2, int64_t* augmentations);
 
@@ -175,6 +176,35 @@ void or_knn(int32_t n, const int32_t* xy, int32_t k, int32_t* nbr, int64_t* d2);
 int or_certify(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int32_t* col,
                const int32_t* b, const uint8_t* x2, const int32_t* lam, int32_t fb, int64_t bound2,
                int32_t full_scan);
+
+
+/* ---- subtour-elimination cuts (subtour.c) ----------------------------------
+ * GDP on F2M plus cuts x(delta(S)) >= 2 of a layered family (see subtour.c):
+ * comp [L][n] labels (-1: no cut of the layer), ncuts [L], mu [sum ncuts]
+ * (units 2^-F, >= 0). */
+int64_t or_cut_z(int32_t n, const int32_t* xy, int32_t L, const int32_t* comp, const int32_t* ncuts,
+                 const int32_t* lam, const int32_t* mu, int32_t fb, int32_t u, int32_t v);
+int64_t or_cut_bound2(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* cost,
+                      int32_t L, const int32_t* comp, const int32_t* ncuts, const int32_t* lam,
+                      const int32_t* mu, int32_t fb);
+int or_cut_sweep(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* cost,
+                 int32_t L, const int32_t* comp, const int32_t* ncuts, const int32_t* lam_old,
+                 const int32_t* mu_old, int32_t F, int32_t shift, int32_t* lam_new, int32_t* mu_new,
+                 int64_t* bound2, int64_t* changed);
+int or_cut_gdp(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* cost, int32_t L,
+               const int32_t* comp, const int32_t* ncuts, int32_t F, int32_t shift, int64_t max_iters,
+               int32_t* lam, int32_t* mu, int64_t* iters, int64_t* trace_bound2, int64_t* trace_changed,
+               int64_t trace_cap);
+int64_t or_cut_extract(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* cost,
+                       int32_t L, const int32_t* comp, const int32_t* ncuts, const int32_t* lam,
+                       const int32_t* mu, int32_t fb, uint8_t* x2);
+/* components of the support of x2 as one cut layer: writes comp [n], returns
+ * the number of cuts */
+int32_t or_separate(int32_t n, const int32_t* row_ptr, const int32_t* col, const uint8_t* x2,
+                    int32_t* comp);
+int64_t or_cut_pricing(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int32_t* col,
+                       int32_t L, const int32_t* comp, const int32_t* ncuts, const int32_t* lam,
+                       const int32_t* mu, int32_t fb, int32_t* pairs, int64_t cap);
 
 #ifdef __cplusplus
 }

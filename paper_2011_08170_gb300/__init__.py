@@ -124,7 +124,7 @@ def load(path: str = LIB_PATH):
     L.f2m_status_string.restype = C.c_char_p
     L.f2m_last_error.argtypes = [vp]
     L.f2m_last_error.restype = C.c_char_p
-    L.f2m_gdp_noalloc.argtypes = [vp, vp, i32, i32, i32, i64, vp, C.POINTER(i64),
+    L.f2m_gdp_noalloc.argtypes = [vp, vp, i64, i32, i32, i32, i64, vp, C.POINTER(i64),
                                   C.POINTER(i64), vp, C.c_char_p, i64]
     L.f2m_gdp_noalloc.restype = C.c_int
     L.f2m_create_batch.argtypes = [i32, vp, vp, vp, vp, C.POINTER(f2m_params), vp, C.POINTER(vp)]
@@ -382,16 +382,17 @@ class Solution:
 
 
 def solve(xy, row_ptr, col, lam0=None, params: f2m_params | None = None, stream=None,
-          b=None) -> Solution:
+          b=None, raise_on_error: bool = True) -> Solution:
     """Create, optionally set degree requirements b (fractional b-matching) and
-    warm-start, solve, and read back everything."""
+    warm-start, solve, and read back everything (with raise_on_error False, also
+    the state a failed solve stopped in; info["status"] holds its status)."""
     ctx = f2m_create(xy, row_ptr, col, params, stream)
     try:
         if b is not None:
             f2m_set_degrees(ctx, b)
         if lam0 is not None:
             f2m_set_lambda(ctx, lam0, (params.frac_bits if params is not None else 8))
-        info = f2m_solve(ctx)
+        info = f2m_solve(ctx, raise_on_error)
         rp, c, x2, _ = f2m_get_x(ctx)
         lam, fb = f2m_get_lambda(ctx)
         return Solution(info.as_dict(), rp, c, x2, lam, fb)
@@ -417,9 +418,10 @@ def f2m_gdp_noalloc(row_ptr, ec, lam, max_sweeps: int, frac_bits: int = 8, dampi
     """GDP phase without allocation; row_ptr, ec ([nnz, 2] {col, cost}) and lam are
     CUDA tensors, lam is updated in place.  Returns (status, sweeps, bound2, message)."""
     n = int(row_ptr.shape[0]) - 1
+    nnz = int(ec.shape[0])
     sw, b2 = C.c_int64(), C.c_int64()
     buf = C.create_string_buffer(512)
-    st = load().f2m_gdp_noalloc(row_ptr.data_ptr(), ec.data_ptr(), n, frac_bits, damping_shift,
+    st = load().f2m_gdp_noalloc(row_ptr.data_ptr(), ec.data_ptr(), nnz, n, frac_bits, damping_shift,
                                 max_sweeps, lam.data_ptr(), C.byref(sw), C.byref(b2),
                                 _stream_handle(stream), buf, len(buf))
     return st, sw.value, b2.value, buf.value.decode()

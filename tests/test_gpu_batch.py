@@ -12,6 +12,7 @@ import pytest
 
 import instances as I
 import paper_2011_08170_gb300 as f2m
+from parity_helpers import compare_solves, same_optimum
 from paper_2011_08170_gb300 import build as B
 
 pytestmark = pytest.mark.gpu
@@ -72,16 +73,24 @@ def test_batch_with_culled_pricing(lib, oracle_lib):
 
 
 def test_batch_matches_oracle_optimum(lib, oracle_lib):
+    # each instance of the batch: the optimum of the oracle's solve, exactly; an
+    # instance that needed no finisher has the oracle's lambda and x bit for
+    # bit; and the single solve that the batch equals (compare above) is the
+    # oracle's, bit for bit up to the finisher and by its optimum after it
     ds = make_batch([("uniform", 800, 21, 8), ("mixture", 1100, 22, 10), ("uniform", 500, 23, 6)])
     b = f2m.f2m_create_batch([(d["xy"], d["row_ptr"], d["col"]) for d in ds])
     infos, tot = f2m.f2m_solve_batch(b)
     for i, d in enumerate(ds):
         r = oracle_lib.solve(d["xy"], d["row_ptr"], d["col"])  # both at 256 sweeps per phase
         fb = infos[i].frac_bits
-        assert infos[i].bound2 / (2.0 * (1 << fb)) == r.opt
+        assert same_optimum(infos[i].bound2, fb, r.bound2, r.frac_bits)
+        assert infos[i].certified == r.certified == 2
         lam, _ = f2m.f2m_batch_get_lambda(b, i)
-        if fb == r.frac_bits:
-            assert np.array_equal(lam, r.lam)
+        rp, col, x2 = f2m.f2m_batch_get_x(b, i)
+        if r.finisher_calls == 0:
+            assert infos[i].finisher_calls == 0 and fb == r.frac_bits
+            assert np.array_equal(lam, r.lam) and np.array_equal(x2, r.x2)
+        compare_solves(oracle_lib, f2m, d)
 
 
 def test_batch_log_uniform_sizes(lib, oracle_lib):
@@ -119,7 +128,8 @@ def test_every_kernel_shape_gives_the_same_result(lib, oracle_lib, shape):
     compare(oracle_lib, ds, f2m.f2m_default_params(batch_shape=shape))
 
 
-CLUSTERS = f2m.f2m_default_params(flags=f2m.F2M_FLAG_BATCH_CLUSTERS)
+def _clusters():
+    return f2m.f2m_default_params(flags=f2m.F2M_FLAG_BATCH_CLUSTERS)
 
 
 def test_cluster_sizes_match_single_solves(lib, oracle_lib):
@@ -127,13 +137,13 @@ def test_cluster_sizes_match_single_solves(lib, oracle_lib):
     # nodes and 24,000 entries per CTA)
     ds = make_batch([("uniform", 1500, 31, 10), ("mixture", 3000, 32, 10), ("uniform", 6000, 33, 10),
                      ("mixture", 12000, 34, 10), ("uniform", 20000, 35, 10), ("uniform", 37, 36, 6)])
-    compare(oracle_lib, ds, CLUSTERS)
+    compare(oracle_lib, ds, _clusters())
 
 
 def test_cluster_batch_with_pricing_rounds(lib, oracle_lib):
     ds = make_batch([("uniform", 600, 11, 4), ("mixture", 900, 12, 10), ("uniform", 1200, 13, 5),
                      ("mixture", 400, 14, 4), ("uniform", 1000, 0, 10)])
-    compare(oracle_lib, ds, CLUSTERS)
+    compare(oracle_lib, ds, _clusters())
 
 
 def test_cluster_and_streaming_batch_paths_agree(lib):
@@ -153,4 +163,4 @@ def test_instance_too_large_for_a_cluster(lib, oracle_lib):
     # 40,000 nodes need more than 16 CTAs of 2048 nodes: the batch runs on the
     # streaming kernels and still equals the single solves
     ds = make_batch([("uniform", 40000, 51, 10), ("mixture", 2000, 52, 10)])
-    compare(oracle_lib, ds, CLUSTERS)
+    compare(oracle_lib, ds, _clusters())

@@ -254,47 +254,59 @@ def test_finisher_reaches_candidate_optimum(oracle_lib):
     st, lam, it, _, _ = oracle_lib.gdp(rp, col, cost, np.zeros(2000, np.int32), 8, 2, 50000)
     bad, _ = oracle_lib.extract(rp, col, cost, lam, 8)
     assert bad > 0  # the sign rule alone is not enough here
-    fst, x2, lam2, aug = oracle_lib.finisher(xy, rp, col, cost, lam, 8)
+    fst, x2, lam2, aug = oracle_lib.finisher(rp, col, cost, lam, 8)
     assert fst == 0 and aug > 0
     b2 = oracle_lib.bound2(rp, col, cost, lam2, 9)
     assert oracle_lib.certify(xy, rp, col, x2, lam2, 9, b2, full_scan=False) == 0
     assert abs(b2 / 1024.0 - highs_opt(xy, rp, col)) < 1e-6 * b2 / 1024.0
     # started from lambda = 0 it reaches the same optimum
-    fst0, x20, lam20, aug0 = oracle_lib.finisher(xy, rp, col, cost, np.zeros(2000, np.int32), 8)
+    fst0, x20, lam20, aug0 = oracle_lib.finisher(rp, col, cost, np.zeros(2000, np.int32), 8)
     assert fst0 == 0 and oracle_lib.bound2(rp, col, cost, lam20, 9) == b2 and aug0 > aug
 
 
 @pytest.mark.parametrize("kind,n,seed", [("uniform", 9000, 3), ("mixture", 7000, 4)])
-def test_blocked_finisher_reaches_candidate_optimum(oracle_lib, kind, n, seed):
-    # several finisher blocks (2048 nodes each): phase 1 per block, phases 2 and 3 for the rest
+def test_finisher_reaches_candidate_optimum_larger(oracle_lib, kind, n, seed):
     inst = I.make_instance(kind, n, seed, 10)
     xy, rp, col = inst["xy"], inst["row_ptr"], inst["col"]
     cost = oracle_lib.cost_table(xy, rp, col)
     st, lam, it, _, _ = oracle_lib.gdp(rp, col, cost, np.zeros(n, np.int32), 8, 2, 100000)
     bad, _ = oracle_lib.extract(rp, col, cost, lam, 8)
-    fst, x2, lam2, aug = oracle_lib.finisher(xy, rp, col, cost, lam, 8)
+    fst, x2, lam2, aug = oracle_lib.finisher(rp, col, cost, lam, 8)
     assert fst == 0 and aug >= bad // 2 > 0
     b2 = oracle_lib.bound2(rp, col, cost, lam2, 9)
     assert oracle_lib.certify(xy, rp, col, x2, lam2, 9, b2, full_scan=False) == 0
     assert abs(b2 / 1024.0 - highs_opt(xy, rp, col)) < 1e-6 * b2 / 1024.0
 
 
-def test_three_phase_finisher_certified_on_many_blocks(oracle_lib):
-    # 40,000 nodes: 20 phase-1 blocks and 3 phase-2 blocks; lambda after 64
-    # sweeps leaves many rows off.  The certificate (x feasible, complementary
-    # slackness, equal cost and bound) proves the result optimal on the graph,
-    # and the finisher from lambda = 0 reaches the same optimum.
+def _initial_excess(rp, col, cost, lam, F, b=2):
+    """Units the finisher must move: with the arcs of z < 0 saturated, node v's
+    left copy holds b - #{z < 0 in row v} and its right copy the negative of
+    that (z is symmetric), so the total positive excess is sum |b - that count|."""
+    n = rp.size - 1
+    src = np.repeat(np.arange(n), np.diff(rp))
+    z = (cost.astype(np.int64) << F) - lam[src].astype(np.int64) - lam[col]
+    neg = np.bincount(src[z < 0], minlength=n)
+    return int(np.abs(b - neg).sum())
+
+
+def test_finisher_certified_from_a_short_gdp(oracle_lib):
+    # 40,000 nodes, lambda after 64 sweeps leaves many rows off.  The
+    # certificate (x feasible, complementary slackness, equal cost and bound)
+    # proves the result optimal on the graph; every augmentation moves one unit
+    # of the initial excess; the finisher from lambda = 0 reaches the same optimum.
     inst = I.make_instance("uniform", 40000, 6, 6)
     xy, rp, col = inst["xy"], inst["row_ptr"], inst["col"]
     cost = oracle_lib.cost_table(xy, rp, col)
     st, lam, it, _, _ = oracle_lib.gdp(rp, col, cost, np.zeros(40000, np.int32), 8, 2, 64)
     bad, _ = oracle_lib.extract(rp, col, cost, lam, 8)
-    fst, x2, lam2, aug = oracle_lib.finisher(xy, rp, col, cost, lam, 8)
+    fst, x2, lam2, aug = oracle_lib.finisher(rp, col, cost, lam, 8)
     assert fst == 0 and aug >= bad // 2 > 1000
+    assert aug == _initial_excess(rp, col, cost, lam, 8)
     b2 = oracle_lib.bound2(rp, col, cost, lam2, 9)
     assert oracle_lib.certify(xy, rp, col, x2, lam2, 9, b2, full_scan=False) == 0
-    fst0, x20, lam20, aug0 = oracle_lib.finisher(xy, rp, col, cost, np.zeros(40000, np.int32), 8)
+    fst0, x20, lam20, aug0 = oracle_lib.finisher(rp, col, cost, np.zeros(40000, np.int32), 8)
     assert fst0 == 0 and oracle_lib.bound2(rp, col, cost, lam20, 9) == b2
+    assert aug0 == _initial_excess(rp, col, cost, np.zeros(40000, np.int32), 8)
 
 
 def test_finisher_infeasible_graph(oracle_lib):
@@ -304,7 +316,7 @@ def test_finisher_infeasible_graph(oracle_lib):
     rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
     col = np.concatenate(rows).astype(np.int32)
     cost = oracle_lib.cost_table(xy, rp, col)
-    st, *_ = oracle_lib.finisher(xy, rp, col, cost, np.zeros(8, np.int32), 8)
+    st, *_ = oracle_lib.finisher(rp, col, cost, np.zeros(8, np.int32), 8)
     assert st == oracle_lib.OR_INFEASIBLE
 
 
