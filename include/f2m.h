@@ -259,13 +259,13 @@ f2m_status f2m_extract(f2m_ctx* ctx, uint8_t* x2, int64_t* bad);
  * loop may forbid allocation once started.  The paper has no counterpart of
  * this entry point; it exists for those callers.
  * It runs the same sweeps as f2m_gdp (same results, bit for bit), but its
- * scratch (the second lambda buffer and the kernel's control block) lives in a
- * fixed file-scope device array of about 1 MiB that every GPU loading this
- * library holds until the process exits.  It calls no cudaMalloc, cudaFree or
- * other allocating routine.
- *   row_ptr   [n+1] int32, device: the candidate CSR (rules of f2m_create; not
- *             re-checked here).
+ * scratch (the second lambda buffer, the kernel's control block and the flags
+ * of the input check) lives in a fixed file-scope device array of about 1 MiB
+ * that every GPU loading this library holds until the process exits.  It calls
+ * no cudaMalloc, cudaFree or other allocating routine.
+ *   row_ptr   [n+1] int32, device: the candidate CSR (rows as in f2m_create).
  *   ec        [nnz][2] int32, device: per CSR entry {column, cost c_e}.
+ *   nnz       entries of ec; 3 n <= nnz < 2^31.
  *   n         4 <= n <= 262,144 (the size of the scratch array); larger n
  *             returns INVALID_ARG with the limit in errbuf.
  *   frac_bits, damping_shift   as in f2m_params (1..8).
@@ -275,12 +275,19 @@ f2m_status f2m_extract(f2m_ctx* ctx, uint8_t* x2, int64_t* bad);
  *   bound2    NULL or host out: bound2 at the lambda the last sweep started from.
  *   stream    cudaStream_t as void*, NULL = legacy default stream.
  *   errbuf    NULL or a caller buffer of errlen bytes for a message.
- * The first call on each device looks up the array's device address (with that
- * device current) and caches it; make that first call before any stream
- * capture.  Every call reuses the same array and clears what must start at
- * zero; calls that overlap on the GPU (other streams or threads) race on it.
+ * Before the sweeps a check kernel reads the inputs (row_ptr over [0, n],
+ * ec over [0, nnz) only) and returns INVALID_ARG, with the first offending
+ * node in errbuf, unless row_ptr runs from 0 to nnz without decreasing, every
+ * column is in [0, n) and not its own row, every row has at least 3 entries,
+ * every cost is in [0, 2^(29 - frac_bits)) and every |lambda| < 2^29 (so that
+ * Eq. 9's z fits 32 bits).  Symmetry and the order of a row are not checked:
+ * they change the answer, not the memory touched.
+ * Every call looks up the array's device address on the current device, reuses
+ * the same array and clears what must start at zero; calls that overlap on the
+ * GPU (other streams or threads) race on it.  The call synchronizes `stream`
+ * before it returns.
  * Returns OK, NOT_CONVERGED, OVERFLOW, TIMEOUT, INVALID_ARG, CUDA. */
-f2m_status f2m_gdp_noalloc(const int32_t* row_ptr, const int32_t* ec, int32_t n,
+f2m_status f2m_gdp_noalloc(const int32_t* row_ptr, const int32_t* ec, int64_t nnz, int32_t n,
                            int32_t frac_bits, int32_t damping_shift, int64_t max_sweeps,
                            int32_t* lambda, int64_t* sweeps, int64_t* bound2, void* stream,
                            char* errbuf, int64_t errlen);
