@@ -57,7 +57,8 @@ def batch_specs(w, rank=0):
 METRIC = "ms to certified F2M optimum"
 GDP_BYTES_PER_ENTRY = 8   # {col, cost} streamed per directed entry
 GDP_BYTES_PER_NODE = 12   # row_ptr + lambda read + lambda write
-PRICING_OPS_PER_PAIR = 5  # FP32 lane operations of the filter: 3 adds (u, w, dy), 2 FMAs
+PRICING_OPS_PER_PAIR = 5  # FP32 lane operations of the kernel's packed filter: 3 adds (u, w, dy), 2 FMAs
+PRICING_SLOTS_PER_PAIR = 7  # algorithmic issue slots per pair: dx, dy, dx*dx, fma dy, r_u + r_v, square, compare
 
 
 def workload_name(w):
@@ -173,7 +174,7 @@ def cpu_oracle_estimate(d, gpu_counts, budget_s=12.0):
         sweeps += 1
     t_sweep = (time.perf_counter() - t0) / sweeps
     t1 = time.perf_counter()
-    fst, _, _, fin_aug = oracle.finisher(xy, rp, col, cost, lam, 8)
+    fst, _, _, fin_aug = oracle.finisher(rp, col, cost, lam, 8)
     t_fin = time.perf_counter() - t1
     rows, pairs, t_pr = 0, 0, 0.0
     step = max(1, n // 400)
@@ -227,6 +228,17 @@ def run_reference(args, w, rank):
                                             "max_iters": mi},
             "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    # one complete oracle solve of the same instance, timed here, outside the
+    # sampled steps (about a minute at n = 100,000; skipped for larger n)
+    if not args.no_ref_whole and w["n"] <= 100_000:
+        t0 = time.perf_counter()
+        r = oracle.solve(d["xy"], d["row_ptr"], d["col"], max_iters=mi)
+        t_whole = (time.perf_counter() - t0) * 1e3
+        line["cpu_baseline"]["whole_solve"] = {
+            "ms": t_whole, "status": int(r.status), "certified": int(r.certified),
+            "iterations": int(r.iterations), "pricing_rounds": int(r.pricing_rounds),
+            "note": "one complete oracle solve of the workload (all phases, scans, merges, finisher), "
+                    "single thread, timed once after the sampled steps"}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -302,7 +314,11 @@ def main():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="gdp", choices=["gdp", "reference"])
     ap.add_argument("--ref-budget", type=float, default=6.0)
+    ap.add_argument("--no-ref-whole", action="store_true",
+                    help="--impl reference: skip the one complete oracle solve after the sampled steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-c3", action="store_true",
+                    help="default workload: leave out the n = 200,000 object of the line")
     ap.add_argument("--instances", type=int, default=None,
                     help="batch workloads: solve only the first N instances (profiling)")
     ap.add_argument("--pricing", type=int, default=1, choices=[1, 2],
@@ -331,7 +347,6 @@ def main():
         return run_warm(args, w, rank, world, local)
 
     import torch
-    import instances as I
     import paper_2011_08170_gb300 as f2m
     from paper_2011_08170_gb300 import build as B
 
@@ -341,6 +356,39 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    line = single_line(args, args.workload, w, rank, world, local, dist, f2m, torch)
+    # the headline metric is quoted at n = 100k and 200k: the default line
+    # carries the 200k workload too, timed the same way
+    if args.workload == "c2" and line.get("_plain") and not args.no_c3:
+        line["c3"] = single_line(args, "c3", WORKLOADS["c3"], rank, world, local, dist, f2m, torch,
+                                 nested=True)
+    line.pop("_plain", None)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def recorded_whole_solve(w):
+    """The oracle's complete solve of this instance, as recorded with its
+    counters by tests/golden/make_full_size_solves.py (timed on the machine
+    that wrote the record, one core)."""
+    p = os.path.join(ROOT, "tests", "golden", "full_size_solves.json")
+    name = f"{w['kind']}_n{w['n']}_k{w['k']}_seed{w['seed']}"
+    try:
+        rec = json.load(open(p))[name]
+    except Exception:
+        return None
+    return {"ms": 1e3 * rec["oracle_seconds"], "record": f"tests/golden/full_size_solves.json[{name}]",
+            "note": "one complete oracle solve (all phases, scans, merges, finisher), timed once on the "
+                    "machine that wrote the record, single thread; not re-run here"}
+
+
+def single_line(args, wname, w, rank, world, local, dist, f2m, torch, nested=False):
+    """Times args.steps solves of one single-instance workload and returns its
+    JSON object (the bench line, or the nested object of a second size)."""
+    import instances as I
     # replicas: every rank solves its own instance of the same workload (seed + rank)
     d = I.make_instance(w["kind"], w["n"], replica_seed(w, rank), w["k"])
     n, nnz0 = w["n"], int(d["row_ptr"][-1])
@@ -381,13 +429,20 @@ def main():
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     infos = []
+    host = []  # per step: host ms of the flush enqueue, of f2m_solve, of the info read-out
     torch.cuda.synchronize()
     t_wall = time.perf_counter()
     for i in range(args.steps):
+        t0 = time.perf_counter()
         flush.fill_(i & 0xFF)
         evs[i][0].record(stream)
-        infos.append(f2m.f2m_solve(ctxs[i]).as_dict())
+        t1 = time.perf_counter()
+        inf = f2m.f2m_solve(ctxs[i])
+        t2 = time.perf_counter()
         evs[i][1].record(stream)
+        infos.append(inf.as_dict())
+        t3 = time.perf_counter()
+        host.append(((t1 - t0) * 1e3, (t2 - t1) * 1e3, (t3 - t2) * 1e3))
     torch.cuda.synchronize()
     wall_ms = (time.perf_counter() - t_wall) * 1e3
     launches = f2m.f2m_kernel_launches() - launches0
@@ -436,8 +491,9 @@ def main():
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     num_sms = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak = num_sms * 128 * sm_mhz * 1e6 / 1e12  # Tops/s at the sampled clock
-    pr_tops = pr_pairs * PRICING_OPS_PER_PAIR / (ms_pr * 1e-3) / 1e12 if ms_pr > 0 else 0.0
-    traffic = load_traffic(args.workload)
+    pr_tops = pr_pairs * PRICING_SLOTS_PER_PAIR / (ms_pr * 1e-3) / 1e12 if ms_pr > 0 else 0.0
+    pr_tops_pipe = pr_pairs * PRICING_OPS_PER_PAIR / (ms_pr * 1e-3) / 1e12 if ms_pr > 0 else 0.0
+    traffic = load_traffic(wname)
     gdp_kernel = "gdp_classes_kernel" if args.update == "classes" else "gdp_tiled2_kernel"
     if ms_gdp >= ms_pr:
         roofline = {"kernel": gdp_kernel, "bound": "hbm", "achieved": gdp_gbs,
@@ -448,8 +504,15 @@ def main():
     else:
         roofline = {"kernel": "pricing_kernel", "bound": "alu", "achieved": pr_tops, "peak": alu_peak,
                     "unit": "Tops/s", "frac": pr_tops / alu_peak,
-                    "traffic": traffic.get("pricing_kernel")}
+                    "traffic": traffic.get("pricing_kernel"),
+                    "work": f"{PRICING_SLOTS_PER_PAIR} issue slots per pair (2 FADD for dx, dy; FMUL, FFMA, "
+                            f"FADD r_u + r_v, FMUL square, FSETP) x n(n-1)/2 pairs per scan",
+                    "frac_pipe": pr_tops_pipe / alu_peak,
+                    "frac_pipe_work": f"{PRICING_OPS_PER_PAIR} FP32 lane operations per pair that the kernel's "
+                                      f"packed filter issues (3 adds, 2 FMAs)"}
     roofline["peak_source"] = "MEASURED_PEAKS.json" if not peaks.get("_fallback") else "fallback"
+    roofline["peak_note"] = f"{num_sms} SMs x 128 FP32 lanes x the SM clock sampled in the timed region" \
+        if roofline["kernel"] == "pricing_kernel" else "hbm_gbs of MEASURED_PEAKS.json"
     if args.pricing == 2 and roofline["kernel"] == "pricing_kernel":
         roofline["effective"] = True
         roofline["note"] = ("culled scan: the rate counts all n(n-1)/2 pairs per scan, but tile pairs that "
@@ -460,7 +523,13 @@ def main():
     roofline["gdp_working_set_mb"] = (GDP_BYTES_PER_ENTRY * nnz0 + GDP_BYTES_PER_NODE * n) / 1e6
     roofline["pricing_tops"] = pr_tops
     roofline["pricing_frac_of_alu"] = pr_tops / alu_peak
+    roofline["pricing_frac_pipe"] = pr_tops_pipe / alu_peak
 
+    host_ms = {"flush_enqueue": statistics.median(h[0] for h in host),
+               "f2m_solve": statistics.median(h[1] for h in host),
+               "info_readout": statistics.median(h[2] for h in host),
+               "per_step": [round(sum(h), 3) for h in host],
+               "event_ms_per_step": [round(x, 3) for x in step_ms]}
     line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
@@ -480,19 +549,26 @@ def main():
                                            "certified", "nnz")},
             "sweep_edges_per_s": iters * nnz0 / (ms_gdp * 1e-3),
             "wall_ms_timed_region": wall_ms,
+            "host_ms": host_ms,
             "e2e": {"value": e2e, "unit": "ms", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "roofline": roofline, "clocks": clk, "gpu_launches": int(launches)}
-    if rank == 0 and not args.no_cpu_baseline and not variant:
+    if nested:
+        for k in ("metric", "unit", "n_gpus", "warmup", "higher_is_better", "scaling", "vs_baseline",
+                  "dtype", "data"):
+            line.pop(k)
+    if rank == 0 and not args.no_cpu_baseline and not variant and not nested:
         est, sample = cpu_oracle_estimate(d, {"iterations": inf0["iterations"],
                                               "pricing_rounds": inf0["pricing_rounds"]})
         line["cpu_baseline"] = {"value": est, "unit": "ms", "cores": 1, "kind": "oracle",
                                 "sample": sample}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
-    return 0
+        whole = recorded_whole_solve(w)
+        if whole:
+            line["cpu_baseline"]["whole_solve_recorded"] = whole
+    line["_plain"] = not variant and args.pricing == 1 and not args.max_iters
+    if nested:
+        line.pop("_plain")
+    return line
 
 
 def run_batch(args, w, rank, world, local):
@@ -580,13 +656,15 @@ def run_batch(args, w, rank, world, local):
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     num_sms = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak = num_sms * 128 * sm_mhz * 1e6 / 1e12
-    pr_tops = pairs * PRICING_OPS_PER_PAIR / (ms_pr * 1e-3) / 1e12 if ms_pr > 0 else 0.0
+    pr_tops = pairs * PRICING_SLOTS_PER_PAIR / (ms_pr * 1e-3) / 1e12 if ms_pr > 0 else 0.0
+    pr_tops_pipe = pairs * PRICING_OPS_PER_PAIR / (ms_pr * 1e-3) / 1e12 if ms_pr > 0 else 0.0
     roofline = {"kernel": "gdp_batch_kernel", "bound": "hbm", "achieved": gdp_gbs,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gdp_gbs / peaks["hbm_gbs"],
                 "traffic": load_traffic(args.workload).get("gdp_batch_kernel"),
                 "peak_source": "MEASURED_PEAKS.json" if not peaks.get("_fallback") else "fallback",
                 "gdp_working_set_mb": float(np.sum(GDP_BYTES_PER_ENTRY * nnzs + GDP_BYTES_PER_NODE * ns)) / 1e6,
-                "pricing_tops": pr_tops, "pricing_frac_of_alu": pr_tops / alu_peak}
+                "pricing_tops": pr_tops, "pricing_frac_of_alu": pr_tops / alu_peak,
+                "pricing_frac_pipe": pr_tops_pipe / alu_peak}
     line = {"metric": METRIC + " (all instances of the batch)", "value": ms, "unit": "ms",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
