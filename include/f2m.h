@@ -158,6 +158,7 @@ typedef struct {
 #define F2M_GDP_KERNEL_CLASSES 4       /* class-by-class sweeps */
 #define F2M_GDP_KERNEL_BATCH 5         /* batched, union CSR streamed */
 #define F2M_GDP_KERNEL_BATCH_CLUSTERS 6  /* batched, one thread-block cluster per instance */
+#define F2M_GDP_KERNEL_CUTS 7          /* node and subtour-cut duals, streaming */
 
 /* Fills *p with the defaults above.  p must not be NULL. */
 void f2m_default_params(f2m_params* p);
@@ -291,6 +292,83 @@ f2m_status f2m_gdp_noalloc(const int32_t* row_ptr, const int32_t* ec, int64_t nn
                            int32_t frac_bits, int32_t damping_shift, int64_t max_sweeps,
                            int32_t* lambda, int64_t* sweeps, int64_t* bound2, void* stream,
                            char* errbuf, int64_t errlen);
+
+/* ---- subtour-elimination cuts ------------------------------------------------
+ * The paper's Discussion names F2M plus subtour elimination constraints as the
+ * next relaxation for the method.  With cuts the LP is
+ *   minimise c x  s.t.  x(delta(v)) = 2 for every node,  x(delta(S)) >= 2 for
+ *   every cut S of the context's family,  0 <= x <= 1,
+ * Section 2's LP3 with equalities (1) and inequalities (2), every constraint
+ * of Section 3's class (8).  A cut dual mu_S >= 0 (Eq. 5) joins the modified
+ * objective (Eq. 4): z_uv = c_uv 2^F - lambda_u - lambda_v - the mu_S of the
+ * cuts that hold exactly one of u, v.  One Jacobi sweep sets every lambda_v as
+ * before and every mu_S = max(0, mu_S + trunc((z(2) + z(3)) / 2^(shift + 2)))
+ * with z(2) <= z(3) the 2nd and 3rd smallest z over delta(S) (a quarter of the
+ * node step: many duals move a crossing edge at once); the bound becomes
+ * bound2 = 4 sum lambda + 4 sum mu + sum over directed entries of min(0, z), a
+ * lower bound on the LP with the cuts (on the complete graph once a pricing
+ * scan with the same duals finds no pair).
+ * The family is kept in up to 8 layers; layer l labels every node -1 or a cut
+ * index s in [0, ncuts); the nodes labelled s form one cut (cuts of a layer
+ * are disjoint).  While a context holds cuts, f2m_gdp, f2m_extract,
+ * f2m_get_bound and f2m_price include them (GDP on a streaming kernel with
+ * 64-bit z, f2m_info.gdp_kernel = F2M_GDP_KERNEL_CUTS); lambda stays in units
+ * 2^-frac_bits.  f2m_solve refuses (its finisher solves F2M only) and
+ * f2m_set_degrees refuses; single-instance contexts only. */
+
+/* One cut layer from the x held now (the last solve's or extraction's): the
+ * connected components of its support {e : x_e > 0}, numbered by their
+ * smallest node; with m >= 3 components each is a cut, with m = 2 the one
+ * without node 0 (delta(S) = delta(V \ S)), with m = 1 none; a component that
+ * fewer than 3 candidate edges leave is left out (Section 3's gradient takes a
+ * 3rd value).  The layer is not added (see f2m_add_cut_layer).
+ *   comp   NULL or [n] int32 (host or device): the labels.
+ *   ncuts  out: cuts in the layer (0: the support is connected).
+ * Errors: INVALID_ARG, OOM, CUDA. */
+f2m_status f2m_separate(f2m_ctx* ctx, int32_t* comp, int32_t* ncuts);
+
+/* Adds a cut layer; its duals start at 0.
+ *   comp   [n] int32 (host or device), copied: -1 or a cut index in [0, ncuts).
+ *   ncuts  >= 1.
+ * Every cut must have at least 3 candidate edges leaving it.  Errors:
+ * INVALID_ARG (labels, a short cut, a 9th layer, b_v set, a batch; the context
+ * is left as it was), OOM, CUDA. */
+f2m_status f2m_add_cut_layer(f2m_ctx* ctx, const int32_t* comp, int32_t ncuts);
+
+/* The cut duals, layer after layer (units 2^-frac_bits).
+ *   count   in: capacity of mu; out: number of cuts.
+ *   mu      NULL (query) or [count] int32, host or device.
+ *   layers  NULL or out: number of layers. */
+f2m_status f2m_get_cut_duals(f2m_ctx* ctx, int32_t* mu, int64_t* count, int32_t* layers);
+
+typedef struct {
+  int64_t iterations;           /* GDP sweeps, all stages */
+  int64_t phases;               /* GDP phases */
+  int64_t pricing_rounds;       /* pricing scans */
+  int64_t edges_added;          /* undirected edges added by pricing */
+  int64_t cuts;                 /* cuts added */
+  int64_t bound2_f2m;           /* 2*LB after the first stage (no cuts), units 2^-frac_bits */
+  int64_t bound2;               /* 2*LB at the end, units 2^-frac_bits */
+  int32_t rounds;               /* separation rounds that added a layer */
+  int32_t layers;               /* layers held at the end */
+  int32_t frac_bits;
+  int32_t certified;            /* 1: the last scan found no pair, so bound2 holds for the complete graph */
+  int32_t status;
+  int32_t pad;
+  double ms_gdp, ms_pricing, ms_merge, ms_separate, ms_total;
+} f2m_subtour_info;
+
+/* GDP on F2M with subtour cuts added round by round.  A stage is: a GDP phase
+ * (max_iters sweeps at most, or to a fixed point), then a pricing scan; while
+ * the scan finds pairs they are added and another phase runs; the stage ends
+ * with rule (7) x at the duals reached.  Stage 0 runs from the context's lambda
+ * on the cuts it holds; each of the next `rounds` stages (0..8) first adds one
+ * layer from f2m_separate on that x (it stops early when the support is
+ * connected or 8 layers are held).  No finisher runs: the result is the
+ * Lagrangian bound and the duals.  info may be NULL.
+ * Errors: INVALID_ARG, OVERFLOW, TIMEOUT, NOT_CONVERGED (pricing rounds), OOM,
+ * CUDA. */
+f2m_status f2m_solve_subtour(f2m_ctx* ctx, int32_t rounds, f2m_subtour_info* info);
 
 /* ---- batched solves: many independent instances in one context --------------- */
 

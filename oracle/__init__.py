@@ -65,6 +65,13 @@ class _Info(C.Structure):
                 ("certified", C.c_int32), ("status", C.c_int32)]
 
 
+class _SubtourInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int64), ("phases", C.c_int64), ("pricing_rounds", C.c_int64),
+                ("edges_added", C.c_int64), ("cuts", C.c_int64), ("bound2_f2m", C.c_int64),
+                ("bound2", C.c_int64), ("rounds", C.c_int32), ("layers", C.c_int32),
+                ("frac_bits", C.c_int32), ("certified", C.c_int32), ("status", C.c_int32)]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -137,6 +144,17 @@ def lib():
         L.or_cut_pricing.restype = C.c_int64
         L.or_cut_pricing.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_int32, C.c_void_p, C.c_void_p,
                                      _i32p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int64]
+        L.or_solve_subtour.restype = C.c_void_p
+        L.or_solve_subtour.argtypes = [C.c_int32, _i32p, _i32p, _i32p, C.c_void_p, C.c_int32, C.c_int32,
+                                       C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.POINTER(_SubtourInfo)]
+        L.or_subtour_nnz.restype = C.c_int64
+        L.or_subtour_nnz.argtypes = [C.c_void_p]
+        L.or_subtour_cuts.restype = C.c_int64
+        L.or_subtour_cuts.argtypes = [C.c_void_p]
+        L.or_subtour_layers.restype = C.c_int32
+        L.or_subtour_layers.argtypes = [C.c_void_p]
+        L.or_subtour_copy.argtypes = [C.c_void_p] + [C.c_void_p] * 7
+        L.or_subtour_free.argtypes = [C.c_void_p]
         _lib = L
     return _lib
 
@@ -487,3 +505,43 @@ def cut_pricing(xy, row_ptr, col, cuts, lam, mu, fb=8):
     lib().or_cut_pricing(cuts.n, xy.reshape(-1), row_ptr, col, *cuts.args(), lam, _mu_ptr(mu), fb,
                          out.ctypes.data, cnt)
     return int(cnt), out[:cnt]
+
+
+@dataclass
+class SubtourResult:
+    info: dict
+    row_ptr: np.ndarray
+    col: np.ndarray
+    x2: np.ndarray
+    lam: np.ndarray
+    mu: np.ndarray
+    cuts: "Cuts"
+
+
+def solve_subtour(xy, row_ptr, col, rounds=3, lam0=None, F=8, shift=2, max_iters=256, pricing=True,
+                  max_pricing_rounds=64) -> SubtourResult:
+    """Stages of GDP with pricing and subtour-cut layers between them (subtour.c)."""
+    xy, row_ptr, col = _i32(xy), _i32(row_ptr), _i32(col)
+    n = row_ptr.size - 1
+    info = _SubtourInfo()
+    lam0a = None if lam0 is None else _i32(lam0)
+    h = lib().or_solve_subtour(n, xy.reshape(-1), row_ptr, col, None if lam0a is None else lam0a.ctypes.data,
+                               F, shift, max_iters, int(pricing), max_pricing_rounds, rounds, C.byref(info))
+    try:
+        nnz = lib().or_subtour_nnz(h)
+        M = lib().or_subtour_cuts(h)
+        L = lib().or_subtour_layers(h)
+        rp = np.zeros(n + 1, np.int32)
+        cl = np.zeros(max(nnz, 1), np.int32)
+        x2 = np.zeros(max(nnz, 1), np.uint8)
+        lam = np.zeros(n, np.int32)
+        mu = np.zeros(max(M, 1), np.int32)
+        comp = np.zeros((max(L, 1), n), np.int32)
+        ncuts = np.zeros(max(L, 1), np.int32)
+        lib().or_subtour_copy(h, rp.ctypes.data, cl.ctypes.data, x2.ctypes.data, lam.ctypes.data,
+                              mu.ctypes.data, comp.ctypes.data, ncuts.ctypes.data)
+    finally:
+        lib().or_subtour_free(h)
+    cuts = Cuts(n, [(comp[l], int(ncuts[l])) for l in range(L)])
+    d = {k: getattr(info, k) for k, _ in _SubtourInfo._fields_}
+    return SubtourResult(d, rp, cl[:nnz], x2[:nnz], lam, mu[:M], cuts)

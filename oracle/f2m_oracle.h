@@ -206,6 +206,26 @@ int64_t or_cut_pricing(int32_t n, const int32_t* xy, const int32_t* row_ptr, con
                        int32_t L, const int32_t* comp, const int32_t* ncuts, const int32_t* lam,
                        const int32_t* mu, int32_t fb, int32_t* pairs, int64_t cap);
 
+typedef struct {
+  int64_t iterations, phases, pricing_rounds, edges_added, cuts;
+  int64_t bound2_f2m;   /* 2*LB after stage 0 (no cuts), units 2^-F */
+  int64_t bound2;       /* 2*LB at the end */
+  int32_t rounds, layers, frac_bits, certified, status;
+} or_subtour_info;
+typedef struct or_subtour or_subtour;
+/* stages of GDP with pricing and cut layers between them (see subtour.c);
+ * lam0 NULL: zero */
+or_subtour* or_solve_subtour(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int32_t* col,
+                             const int32_t* lam0, int32_t F, int32_t shift, int64_t max_iters,
+                             int32_t pricing, int32_t max_pricing_rounds, int32_t rounds,
+                             or_subtour_info* info);
+int64_t or_subtour_nnz(const or_subtour* r);
+int64_t or_subtour_cuts(const or_subtour* r);
+int32_t or_subtour_layers(const or_subtour* r);
+void or_subtour_copy(const or_subtour* r, int32_t* row_ptr, int32_t* col, uint8_t* x2, int32_t* lam,
+                     int32_t* mu, int32_t* comp, int32_t* ncuts);
+void or_subtour_free(or_subtour* r);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,10 @@
  *   - one Jacobi sweep updates every lambda and every mu from the same input
  *     (Section 5.1's parallel update extended to the cut duals):
  *       lambda_v += trunc((z(2) + z(3)) / 2^shift) over delta(v),
- *       mu_S = max(0, mu_S + trunc((z(2) + z(3)) / 2^shift)) over delta(S);
+ *       mu_S = max(0, mu_S + trunc((z(2) + z(3)) / 2^(shift + 2))) over delta(S);
+ *     the cut step is a quarter of the node step, because an edge's z moves
+ *     with both end duals and up to two cut duals per layer at once (with the
+ *     node-sized step the duals diverged after a few layers on the oracle);
  *   - bound2 = 4 sum lambda + 4 sum mu + sum over directed entries of
  *     min(0, z), twice the Lagrangian bound at the sweep's input;
  *   - a cut needs at least 3 crossing candidate edges (the 3rd value of
@@ -114,7 +117,7 @@ int or_cut_sweep(int32_t n, const int32_t* row_ptr, const int32_t* col, const in
   for (int32_t v = 0; v < n; ++v)
     if (row_ptr[v + 1] - row_ptr[v] > maxdeg) maxdeg = row_ptr[v + 1] - row_ptr[v];
   int64_t* buf = (int64_t*)malloc(sizeof(int64_t) * (size_t)(maxdeg > 0 ? maxdeg : 1));
-  for (int32_t v = 0; v < n && status == OR_OK; ++v) {
+  for (int32_t v = 0; v < n && status != OR_INVALID; ++v) {
     const int32_t deg = row_ptr[v + 1] - row_ptr[v];
     if (deg < 3) { status = OR_INVALID; break; }
     memcpy(buf, z + row_ptr[v], sizeof(int64_t) * (size_t)deg);
@@ -130,7 +133,7 @@ int or_cut_sweep(int32_t n, const int32_t* row_ptr, const int32_t* col, const in
   /* cut duals: 2nd and 3rd smallest z over delta(S); each crossing edge once,
    * from the entry whose row lies in S; projected onto mu >= 0 (Eq. 5) */
   int64_t off = 0;
-  for (int32_t l = 0; l < L && status == OR_OK; ++l) {
+  for (int32_t l = 0; l < L && status != OR_INVALID; ++l) {
     const int32_t* cl = comp + (int64_t)l * n;
     int64_t* cnt = (int64_t*)calloc((size_t)ncuts[l] + 1, sizeof(int64_t));
     for (int32_t u = 0; u < n; ++u) {
@@ -151,7 +154,7 @@ int or_cut_sweep(int32_t n, const int32_t* row_ptr, const int32_t* col, const in
       const int64_t k = cnt[s + 1] - cnt[s];
       if (k < 3) { status = OR_INVALID; break; }
       qsort(vals + cnt[s], (size_t)k, sizeof(int64_t), cmp_i64s);
-      const int64_t d = (vals[cnt[s] + 1] + vals[cnt[s] + 2]) / ((int64_t)1 << shift);
+      const int64_t d = (vals[cnt[s] + 1] + vals[cnt[s] + 2]) / ((int64_t)1 << (shift + 2));
       int64_t nm = (int64_t)mu_old[off + s] + d;
       if (nm < 0) nm = 0;
       if (nm >= OR_LAM_LIMIT) status = OR_OVERFLOW;
@@ -268,4 +271,128 @@ int64_t or_cut_pricing(int32_t n, const int32_t* xy, const int32_t* row_ptr, con
   }
   free(mark);
   return count;
+}
+
+/* ---- the driver: stages of GDP with pricing, cut layers between them -------
+ * A stage: a GDP phase (or_cut_gdp, at most max_iters sweeps); then a pricing
+ * scan with the cut terms; while it finds pairs they are merged (costs
+ * recomputed) and another phase runs; the stage ends with rule (7) x and the
+ * bound at the duals reached.  Stage 0 runs without cuts (the F2M GDP); each
+ * of the next `rounds` stages first adds the layer or_separate makes from the
+ * previous stage's x, and the rounds stop early when it makes no cut. */
+
+struct or_subtour {
+  int32_t n;
+  int64_t nnz;
+  int32_t* row_ptr;
+  int32_t* col;
+  uint8_t* x2;
+  int32_t* lam;
+  int32_t L;
+  int32_t ncuts[8];
+  int32_t* comp;  /* [8][n] */
+  int32_t* mu;
+  int64_t M;
+};
+
+int64_t or_subtour_nnz(const or_subtour* r) { return r->nnz; }
+int64_t or_subtour_cuts(const or_subtour* r) { return r->M; }
+int32_t or_subtour_layers(const or_subtour* r) { return r->L; }
+
+void or_subtour_copy(const or_subtour* r, int32_t* row_ptr, int32_t* col, uint8_t* x2, int32_t* lam,
+                     int32_t* mu, int32_t* comp, int32_t* ncuts) {
+  if (row_ptr) memcpy(row_ptr, r->row_ptr, sizeof(int32_t) * (size_t)(r->n + 1));
+  if (col) memcpy(col, r->col, sizeof(int32_t) * (size_t)r->nnz);
+  if (x2) memcpy(x2, r->x2, (size_t)r->nnz);
+  if (lam) memcpy(lam, r->lam, sizeof(int32_t) * (size_t)r->n);
+  if (mu && r->M) memcpy(mu, r->mu, sizeof(int32_t) * (size_t)r->M);
+  if (comp && r->L) memcpy(comp, r->comp, sizeof(int32_t) * (size_t)r->L * r->n);
+  if (ncuts && r->L) memcpy(ncuts, r->ncuts, sizeof(int32_t) * (size_t)r->L);
+}
+
+void or_subtour_free(or_subtour* r) {
+  if (!r) return;
+  free(r->row_ptr); free(r->col); free(r->x2); free(r->lam); free(r->comp); free(r->mu); free(r);
+}
+
+/* one stage; returns an OR_ status */
+static int or_stage(or_subtour* r, const int32_t* xy, int32_t** cost, int32_t F, int32_t shift,
+                    int64_t max_iters, int32_t pricing, int32_t max_pricing_rounds, or_subtour_info* info,
+                    int64_t* bound2) {
+  const int32_t n = r->n;
+  for (;;) {
+    int64_t it = 0;
+    int st = or_cut_gdp(n, r->row_ptr, r->col, *cost, r->L, r->comp, r->ncuts, F, shift, max_iters, r->lam,
+                        r->mu, &it, NULL, NULL, 0);
+    info->iterations += it;
+    info->phases += 1;
+    if (st != OR_OK && st != OR_NOT_CONVERGED) return st;
+    if (!pricing) break;
+    if (info->pricing_rounds >= max_pricing_rounds) return OR_NOT_CONVERGED;
+    int64_t cnt = or_cut_pricing(n, xy, r->row_ptr, r->col, r->L, r->comp, r->ncuts, r->lam, r->mu, F, NULL, 0);
+    int32_t* pairs = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * cnt + 2));
+    or_cut_pricing(n, xy, r->row_ptr, r->col, r->L, r->comp, r->ncuts, r->lam, r->mu, F, pairs, cnt);
+    info->pricing_rounds += 1;
+    if (cnt == 0) { free(pairs); break; }
+    int32_t* nrp = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1));
+    int32_t* ncl = (int32_t*)malloc(sizeof(int32_t) * (size_t)(r->nnz + 2 * cnt));
+    int64_t nnz = or_merge(n, r->row_ptr, r->col, cnt, pairs, nrp, ncl);
+    free(pairs);
+    free(r->row_ptr); free(r->col); free(*cost); free(r->x2);
+    r->row_ptr = nrp; r->col = ncl; r->nnz = nnz;
+    *cost = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+    r->x2 = (uint8_t*)calloc((size_t)(nnz > 0 ? nnz : 1), 1);
+    or_cost_table(n, xy, r->row_ptr, r->col, *cost);
+    info->edges_added += cnt;
+  }
+  or_cut_extract(n, r->row_ptr, r->col, *cost, r->L, r->comp, r->ncuts, r->lam, r->mu, F, r->x2);
+  *bound2 = or_cut_bound2(n, r->row_ptr, r->col, *cost, r->L, r->comp, r->ncuts, r->lam, r->mu, F);
+  return OR_OK;
+}
+
+or_subtour* or_solve_subtour(int32_t n, const int32_t* xy, const int32_t* row_ptr, const int32_t* col,
+                             const int32_t* lam0, int32_t F, int32_t shift, int64_t max_iters,
+                             int32_t pricing, int32_t max_pricing_rounds, int32_t rounds,
+                             or_subtour_info* info) {
+  or_subtour* r = (or_subtour*)calloc(1, sizeof(or_subtour));
+  r->n = n;
+  r->nnz = row_ptr[n];
+  r->row_ptr = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1));
+  r->col = (int32_t*)malloc(sizeof(int32_t) * (size_t)(r->nnz > 0 ? r->nnz : 1));
+  memcpy(r->row_ptr, row_ptr, sizeof(int32_t) * (size_t)(n + 1));
+  memcpy(r->col, col, sizeof(int32_t) * (size_t)r->nnz);
+  r->x2 = (uint8_t*)calloc((size_t)(r->nnz > 0 ? r->nnz : 1), 1);
+  r->lam = (int32_t*)calloc((size_t)n, sizeof(int32_t));
+  if (lam0) memcpy(r->lam, lam0, sizeof(int32_t) * (size_t)n);
+  r->comp = (int32_t*)malloc(sizeof(int32_t) * (size_t)8 * n);
+  r->mu = NULL;
+  int32_t* cost = (int32_t*)malloc(sizeof(int32_t) * (size_t)(r->nnz > 0 ? r->nnz : 1));
+  or_cost_table(n, xy, r->row_ptr, r->col, cost);
+  memset(info, 0, sizeof(*info));
+  info->frac_bits = F;
+  int64_t b2 = 0;
+  int st = or_stage(r, xy, &cost, F, shift, max_iters, pricing, max_pricing_rounds, info, &b2);
+  info->bound2_f2m = b2;
+  info->bound2 = b2;
+  int32_t* lab = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  for (int32_t k = 0; k < rounds && st == OR_OK && r->L < 8; ++k) {
+    int32_t m = or_separate(n, r->row_ptr, r->col, r->x2, lab);
+    if (m == 0) break;
+    memcpy(r->comp + (int64_t)r->L * n, lab, sizeof(int32_t) * (size_t)n);
+    r->ncuts[r->L] = m;
+    r->L += 1;
+    r->mu = (int32_t*)realloc(r->mu, sizeof(int32_t) * (size_t)(r->M + m));
+    memset(r->mu + r->M, 0, sizeof(int32_t) * (size_t)m);
+    r->M += m;
+    info->rounds += 1;
+    info->cuts += m;
+    st = or_stage(r, xy, &cost, F, shift, max_iters, pricing, max_pricing_rounds, info, &b2);
+    info->bound2 = b2;
+  }
+  free(lab);
+  free(cost);
+  info->layers = r->L;
+  info->certified = (st == OR_OK && pricing) ? 1 : 0;
+  info->status = st;
+  return r;
 }

@@ -47,7 +47,8 @@ EXPORTS = ["f2m_default_params", "f2m_create", "f2m_destroy", "f2m_set_lambda", 
            "f2m_knn", "f2m_knn_csr", "f2m_features", "f2m_mlp_create", "f2m_mlp_destroy",
            "f2m_mlp_get_params", "f2m_mlp_last_error", "f2m_mlp_forward", "f2m_mlp_grad",
            "f2m_mlp_train", "f2m_warm_start", "f2m_set_degrees", "f2m_get_colors",
-           "f2m_tsplib_parse", "f2m_tsplib_last_error"]
+           "f2m_tsplib_parse", "f2m_tsplib_last_error", "f2m_separate", "f2m_add_cut_layer",
+           "f2m_get_cut_duals", "f2m_solve_subtour"]
 
 F2M_MLP_NPARAMS = 18817
 
@@ -79,6 +80,18 @@ class f2m_info(C.Structure):
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class f2m_subtour_info(C.Structure):
+    _fields_ = [("iterations", C.c_int64), ("phases", C.c_int64), ("pricing_rounds", C.c_int64),
+                ("edges_added", C.c_int64), ("cuts", C.c_int64), ("bound2_f2m", C.c_int64),
+                ("bound2", C.c_int64), ("rounds", C.c_int32), ("layers", C.c_int32),
+                ("frac_bits", C.c_int32), ("certified", C.c_int32), ("status", C.c_int32),
+                ("pad", C.c_int32), ("ms_gdp", C.c_double), ("ms_pricing", C.c_double),
+                ("ms_merge", C.c_double), ("ms_separate", C.c_double), ("ms_total", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
 class F2MError(RuntimeError):
@@ -154,6 +167,12 @@ def load(path: str = LIB_PATH):
     L.f2m_warm_start.argtypes = [vp, vp, C.POINTER(C.c_double)]
     for name in ("f2m_knn", "f2m_knn_csr", "f2m_features", "f2m_mlp_create", "f2m_mlp_get_params",
                  "f2m_mlp_forward", "f2m_mlp_grad", "f2m_mlp_train", "f2m_warm_start"):
+        getattr(L, name).restype = C.c_int
+    L.f2m_separate.argtypes = [vp, vp, C.POINTER(i32)]
+    L.f2m_add_cut_layer.argtypes = [vp, vp, i32]
+    L.f2m_get_cut_duals.argtypes = [vp, vp, C.POINTER(i64), C.POINTER(i32)]
+    L.f2m_solve_subtour.argtypes = [vp, i32, C.POINTER(f2m_subtour_info)]
+    for name in ("f2m_separate", "f2m_add_cut_layer", "f2m_get_cut_duals", "f2m_solve_subtour"):
         getattr(L, name).restype = C.c_int
     L.f2m_kernel_launches.argtypes = []
     L.f2m_kernel_launches.restype = C.c_int64
@@ -398,6 +417,40 @@ def solve(xy, row_ptr, col, lam0=None, params: f2m_params | None = None, stream=
         return Solution(info.as_dict(), rp, c, x2, lam, fb)
     finally:
         f2m_destroy(ctx)
+
+
+# ---- subtour-elimination cuts --------------------------------------------------------
+
+def f2m_separate(ctx: Ctx, device=None):
+    """One cut layer from the x held now: (comp int32 [n], ncuts)."""
+    comp = _out((ctx.n,), np.int32, device)
+    m = C.c_int32()
+    p, _ = _ptr(comp)
+    _check(ctx, load().f2m_separate(ctx.handle, p, C.byref(m)))
+    return comp, m.value
+
+
+def f2m_add_cut_layer(ctx: Ctx, comp, ncuts: int) -> None:
+    p, keep = _ptr(_as(comp, np.int32))
+    _check(ctx, load().f2m_add_cut_layer(ctx.handle, p, int(ncuts)))
+
+
+def f2m_get_cut_duals(ctx: Ctx):
+    """(mu int32 [cuts], layers)."""
+    cnt, layers = C.c_int64(0), C.c_int32()
+    _check(ctx, load().f2m_get_cut_duals(ctx.handle, None, C.byref(cnt), C.byref(layers)))
+    mu = np.zeros(max(cnt.value, 1), np.int32)
+    if cnt.value:
+        _check(ctx, load().f2m_get_cut_duals(ctx.handle, mu.ctypes.data, C.byref(cnt), None))
+    return mu[:cnt.value], layers.value
+
+
+def f2m_solve_subtour(ctx: Ctx, rounds: int, raise_on_error: bool = True) -> dict:
+    info = f2m_subtour_info()
+    st = load().f2m_solve_subtour(ctx.handle, int(rounds), C.byref(info))
+    if raise_on_error:
+        _check(ctx, st)
+    return info.as_dict()
 
 
 def f2m_status_string(status: int) -> str:

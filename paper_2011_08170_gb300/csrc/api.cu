@@ -200,6 +200,7 @@ extern "C" void f2m_destroy(f2m_ctx* c) {
   plan2_free(c->plan);
   plan_free(c->plan);
   class_plan_free(c->classes);
+  cut_state_free(c->cuts);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   delete c;
@@ -373,6 +374,7 @@ extern "C" f2m_status f2m_set_lambda(f2m_ctx* c, const int32_t* lambda, int32_t 
 extern "C" f2m_status f2m_set_degrees(f2m_ctx* c, const int32_t* b) {
   if (!c) return fail(c, F2M_ERR_INVALID_ARG, "NULL context");
   if (c->seg_off.size() != 2) return fail(c, F2M_ERR_INVALID_ARG, "degree requirements apply to a single-instance context");
+  if (cut_count(c)) return fail(c, F2M_ERR_INVALID_ARG, "subtour cuts need b_v = 2");
   if (!b) {
     dfree(c->d_b);
     dfree(c->d_b_int);
@@ -441,6 +443,7 @@ f2m_status f2m::gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, bool 
   long long* tb = want_trace ? c->d_trace_b2 : nullptr;
   unsigned long long* tc = want_trace ? reinterpret_cast<unsigned long long*>(c->d_trace_ch) : nullptr;
   const int64_t tcap = want_trace ? trace_cap : 0;
+  if (cut_count(c) > 0) return cut_gdp_phase(c, max_sweeps, sweeps, tb, tc, tcap, ms);
   if (c->p.flags & F2M_FLAG_CLASS_SWEEPS) {
     CK(c, cudaEventRecord(c->ev0, c->st));
     if (c->classes.version != c->plan.version) {  // colour the graph held now
@@ -586,7 +589,7 @@ static void build_tiles(const f2m_ctx* c, std::vector<int4>& tiles) {
 
 // pricing scan into d_pairs (grown until every pair fits); count in c->npairs,
 // per-segment counts in c->seg_pairs
-f2m_status f2m::price_internal(f2m_ctx* c, double* ms) {
+f2m_status f2m::price_internal(f2m_ctx* c, double* ms, const int32_t* lam_override) {
   if (!c->d_pts) {
     CK(c, dalloc(&c->d_pts, c->n));
     CK(c, dalloc(&c->d_count, 1));
@@ -600,6 +603,7 @@ f2m_status f2m::price_internal(f2m_ctx* c, double* ms) {
   build_tiles(c, tiles);
   int32_t fb = 0;
   const int32_t* lam = cur_lambda(c, &fb);
+  if (lam_override) lam = lam_override;
   const int32_t nseg = (int32_t)c->seg_off.size() - 1;
   // full scan: points in caller order; culled scan: in the renumbered (Morton)
   // order, so that a tile is a compact patch with a small bounding box
@@ -697,7 +701,7 @@ f2m_status f2m::price_internal(f2m_ctx* c, double* ms) {
 
 extern "C" f2m_status f2m_price(f2m_ctx* c, int64_t* count, int32_t* pairs, int64_t cap) {
   if (!c || !count) return fail(c, F2M_ERR_INVALID_ARG, "NULL argument");
-  f2m_status s = price_internal(c, nullptr);
+  f2m_status s = cut_count(c) ? cut_price(c, nullptr) : price_internal(c, nullptr);
   if (s != F2M_OK) return s;
   *count = c->npairs;
   if (pairs && c->npairs > 0 && c->npairs <= cap) {
@@ -769,6 +773,7 @@ extern "C" f2m_status f2m_add_edges(f2m_ctx* c, const int32_t* pairs, int64_t np
 }
 
 f2m_status f2m::extract_internal(f2m_ctx* c, int64_t* bad, double* ms) {
+  if (cut_count(c)) return cut_bound_extract(c, true, nullptr, bad);
   int32_t fb = 0;
   const int32_t* lam = cur_lambda(c, &fb);
   CK(c, cudaEventRecord(c->ev0, c->st));
@@ -794,6 +799,7 @@ extern "C" f2m_status f2m_extract(f2m_ctx* c, uint8_t* x2, int64_t* bad) {
 }
 
 f2m_status f2m::bound_internal(f2m_ctx* c, int64_t* b2) {
+  if (cut_count(c)) return cut_bound_extract(c, false, b2, nullptr);
   int32_t fb = 0;
   const int32_t* lam = cur_lambda(c, &fb);
   CK(c, launch_bound(c->d_rp, c->d_ec, c->d_b, lam, c->n, fb, c->d_scalar, c->st));
@@ -907,6 +913,8 @@ f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug, const uint8_t* h_inc
 //   else merge and continue GDP from lambda (F bits).
 extern "C" f2m_status f2m_solve(f2m_ctx* c, f2m_info* info_out) {
   if (!c) return fail(c, F2M_ERR_INVALID_ARG, "NULL context");
+  if (cut_count(c))
+    return fail(c, F2M_ERR_INVALID_ARG, "the context holds subtour cuts: f2m_solve_subtour drives their solve");
   const auto t0 = std::chrono::steady_clock::now();
   f2m_info info;
   std::memset(&info, 0, sizeof(info));

@@ -10,6 +10,10 @@
 #include "../../include/f2m.h"
 #include "f2m_internal.h"
 
+namespace f2m {
+struct CutState;  // subtour-elimination cuts (cuts.cu)
+}
+
 struct f2m_ctx {
   // segments: contiguous node ranges that are separate instances (a batch);
   // one segment [0, n) for a single instance.  Pricing pairs stay inside a
@@ -86,6 +90,7 @@ struct f2m_ctx {
   int32_t* h_lam = nullptr;
   int32_t* h_lam2 = nullptr;
   f2m::FinisherWork* fin_work = nullptr;
+  f2m::CutState* cuts = nullptr;  // layers of subtour-elimination cuts and their duals
   std::string err;
 };
 
@@ -117,12 +122,20 @@ f2m_status check_params_internal(const f2m_params& p);
 const int32_t* cur_lambda(f2m_ctx* c, int32_t* fb);
 f2m_status gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, bool want_trace,
                      int64_t trace_cap, double* ms);
-f2m_status price_internal(f2m_ctx* c, double* ms);
+// lam_override (device, [n], units 2^-fb): scan with it in place of lambda
+f2m_status price_internal(f2m_ctx* c, double* ms, const int32_t* lam_override = nullptr);
 f2m_status merge_internal(f2m_ctx* c, const int2* d_pairs, int64_t npairs, double* ms);
 f2m_status extract_internal(f2m_ctx* c, int64_t* bad, double* ms);
 f2m_status bound_internal(f2m_ctx* c, int64_t* b2);
 // h_include (host, per segment; NULL = all): the segments the finisher works on
 f2m_status finisher_internal(f2m_ctx* c, int64_t* aug, const uint8_t* h_include);
+// subtour-elimination cuts (cuts.cu)
+void cut_state_free(CutState* s);
+int64_t cut_count(const f2m_ctx* c);
+f2m_status cut_gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, long long* tb,
+                         unsigned long long* tc, int64_t tcap, double* ms);
+f2m_status cut_bound_extract(f2m_ctx* c, bool want_x, int64_t* b2, int64_t* bad);
+f2m_status cut_price(f2m_ctx* c, double* ms);
 // create a context for the graph, renumbering within segments when seg_off has
 // more than one segment (seg_off[0] = 0, seg_off.back() = n)
 f2m_status create_internal(const int32_t* xy, int32_t n, const int32_t* row_ptr, const int32_t* col,

