@@ -35,8 +35,10 @@
 //   once per cut).
 // Kernel: one persistent cooperative launch per phase.  G = 4 lanes per node
 // stream its row (cut terms only on entries whose mask is set), then one warp
-// per cut streams its list; both from the same input, one device-wide barrier
-// per sweep.  z is computed in 64 bits (several duals per edge).
+// per cut streams its list (a whole block for a cut with 128 or more entries,
+// its warps' top-3s merged in shared memory); both from the same input, one
+// device-wide barrier per sweep.  z is computed in 64 bits (several duals per
+// edge).
 #include <algorithm>
 #include <chrono>
 #include <climits>
@@ -75,6 +77,10 @@ struct CutState {
   int2* d_items = nullptr;
   int64_t item_cap = 0;
   int64_t items = 0;
+  int32_t* d_lflag = nullptr;  // [ptr_cap] long-cut flags
+  int32_t* d_lpos = nullptr;   // [ptr_cap] their exclusive scan
+  int32_t* d_long = nullptr;   // [ptr_cap] the cuts a block takes
+  int32_t nlong = 0;
   int64_t built_version = -1;  // graph version the mask and lists were built for
   int32_t built_L = -1;
   // separation and pricing scratch
@@ -97,7 +103,8 @@ void cut_state_free(CutState* s) {
   dfree(s->d_comp); dfree(s->d_mu[0]); dfree(s->d_mu[1]); dfree(s->d_mask); dfree(s->d_cnt);
   dfree(s->d_ptr); dfree(s->d_scan); dfree(s->d_items); dfree(s->d_lab); dfree(s->d_cross);
   dfree(s->d_flag); dfree(s->d_rank); dfree(s->d_small); dfree(s->d_lamp); dfree(s->d_keep);
-  dfree(s->d_kpos); dfree(s->d_pairs2); dfree(s->d_pscan);
+  dfree(s->d_kpos); dfree(s->d_pairs2); dfree(s->d_pscan); dfree(s->d_lflag); dfree(s->d_lpos);
+  dfree(s->d_long);
   delete s;
 }
 
@@ -106,6 +113,7 @@ int64_t cut_count(const f2m_ctx* c) { return c->cuts ? c->cuts->M : 0; }
 namespace {
 
 constexpr long long kInfZ = LLONG_MAX / 4;
+constexpr int kLongCut = 128;  // crossing entries from which a block, not a warp, takes a cut
 
 __device__ __forceinline__ void top3_ins_ll(long long z, long long& a, long long& b, long long& c) {
   if (z < c) {
@@ -183,6 +191,20 @@ __global__ void cut_list_kernel(const int32_t* __restrict__ rp, const int2* __re
   }
 }
 
+// 1 for a cut whose list holds at least kLongCut entries
+__global__ void cut_long_flag_kernel(const int32_t* __restrict__ cnt, int32_t M, int32_t* flag) {
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < M;
+       s += (long long)gridDim.x * blockDim.x)
+    flag[s] = cnt[s] >= kLongCut;
+}
+
+__global__ void cut_long_list_kernel(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos,
+                                     int32_t M, int32_t* out) {
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < M;
+       s += (long long)gridDim.x * blockDim.x)
+    if (flag[s]) out[pos[s]] = (int32_t)s;
+}
+
 // labels of layer l in [-1, ncuts): else flag
 __global__ void cut_label_check_kernel(const int32_t* __restrict__ comp, int32_t n, int32_t ncuts,
                                        int32_t* flag) {
@@ -203,7 +225,8 @@ __global__ void cut_short_kernel(const int32_t* __restrict__ cnt, int32_t M, int
 template <int G>
 __global__ void __launch_bounds__(512)
 cut_gdp_kernel(const int32_t* __restrict__ rp, const int2* __restrict__ ec, const uint8_t* __restrict__ mask,
-               const __grid_constant__ CutArgs ca, const int32_t* __restrict__ cut_ptr, const int2* __restrict__ items, int32_t M,
+               const __grid_constant__ CutArgs ca, const int32_t* __restrict__ cut_ptr, const int2* __restrict__ items,
+               int32_t M, const int32_t* __restrict__ long_cuts, int32_t nlong,
                int32_t* lam0, int32_t* lam1, int32_t* mu0, int32_t* mu1, int32_t F, int32_t shift,
                long long max_sweeps, GdpCtl* ctl, long long* trace_b2, unsigned long long* trace_ch,
                long long trace_cap, long long budget) {
@@ -211,6 +234,7 @@ cut_gdp_kernel(const int32_t* __restrict__ rp, const int2* __restrict__ ec, cons
   __shared__ unsigned s_ch[32];
   __shared__ int s_ovf[32];
   __shared__ int s_stop;
+  __shared__ long long s_t3[32 * 3];
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int sub = lane & (G - 1);
@@ -257,9 +281,53 @@ cut_gdp_kernel(const int32_t* __restrict__ rp, const int2* __restrict__ ec, cons
         b2 += 4 * lv;
       }
     }
-    // cut duals: Section 3's gradient over delta(S), projected onto mu >= 0
+    // cut duals: Section 3's gradient over delta(S), projected onto mu >= 0.
+    // A cut with a long list is taken by a whole block (its warps' top-3s
+    // merged in shared memory), the others by one warp each.
+    auto cut_update = [&](long long s, long long a, long long b, long long c) {
+      const long long m = ld_cg_i(min_ + s);
+      long long nm = m + step_ll(b, c, shift + 2);
+      if (nm < 0) nm = 0;
+      ovf |= (nm >= kLamLimit);
+      mout[s] = (int32_t)nm;
+      ch += (nm != m);
+      b2 += 4 * m;
+    };
+    for (long long q = blockIdx.x; q < nlong; q += gridDim.x) {
+      const int s = __ldg(long_cuts + q);
+      const int p0 = __ldg(cut_ptr + s), p1 = __ldg(cut_ptr + s + 1);
+      long long a = kInfZ, b = kInfZ, c = kInfZ;
+      for (int k = p0 + tid; k < p1; k += blockDim.x) {
+        const int2 it = __ldg(items + k);
+        top3_ins_ll(entry_z(ca, lin, min_, __ldg(mask + it.y), it.x, __ldg(ec + it.y), F), a, b, c);
+      }
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long a1 = __shfl_xor_sync(0xffffffffu, a, o), b1 = __shfl_xor_sync(0xffffffffu, b, o),
+                        c1 = __shfl_xor_sync(0xffffffffu, c, o);
+        top3_ins_ll(a1, a, b, c);
+        top3_ins_ll(b1, a, b, c);
+        top3_ins_ll(c1, a, b, c);
+      }
+      if (lane == 0) { s_t3[3 * warp] = a; s_t3[3 * warp + 1] = b; s_t3[3 * warp + 2] = c; }
+      __syncthreads();
+      if (warp == 0) {
+        a = lane < nwarps ? s_t3[3 * lane] : kInfZ;
+        b = lane < nwarps ? s_t3[3 * lane + 1] : kInfZ;
+        c = lane < nwarps ? s_t3[3 * lane + 2] : kInfZ;
+        for (int o = 1; o < 32; o <<= 1) {
+          const long long a1 = __shfl_xor_sync(0xffffffffu, a, o), b1 = __shfl_xor_sync(0xffffffffu, b, o),
+                          c1 = __shfl_xor_sync(0xffffffffu, c, o);
+          top3_ins_ll(a1, a, b, c);
+          top3_ins_ll(b1, a, b, c);
+          top3_ins_ll(c1, a, b, c);
+        }
+        if (lane == 0) cut_update(s, a, b, c);
+      }
+      __syncthreads();
+    }
     for (long long s = gwarp; s < M; s += twarps) {
       const int p0 = __ldg(cut_ptr + s), p1 = __ldg(cut_ptr + s + 1);
+      if (p1 - p0 >= kLongCut) continue;  // a block's
       long long a = kInfZ, b = kInfZ, c = kInfZ;
       for (int k = p0 + lane; k < p1; k += 32) {
         const int2 it = __ldg(items + k);
@@ -272,15 +340,7 @@ cut_gdp_kernel(const int32_t* __restrict__ rp, const int2* __restrict__ ec, cons
         top3_ins_ll(b1, a, b, c);
         top3_ins_ll(c1, a, b, c);
       }
-      if (lane == 0) {
-        const long long m = ld_cg_i(min_ + s);
-        long long nm = m + step_ll(b, c, shift + 2);
-        if (nm < 0) nm = 0;
-        ovf |= (nm >= kLamLimit);
-        mout[s] = (int32_t)nm;
-        ch += (nm != m);
-        b2 += 4 * m;
-      }
+      if (lane == 0) cut_update(s, a, b, c);
     }
     b2 = warp_sum_ll(b2);
     ch = warp_sum_u(ch);
@@ -517,10 +577,16 @@ f2m_status cut_lists(f2m_ctx* c) {
     dfree(S->d_cnt);
     dfree(S->d_ptr);
     dfree(S->d_scan);
+    dfree(S->d_lflag);
+    dfree(S->d_lpos);
+    dfree(S->d_long);
     S->ptr_cap = S->M + 1 + 1024;
     CK(c, dalloc(&S->d_cnt, S->ptr_cap));
     CK(c, dalloc(&S->d_ptr, S->ptr_cap));
     CK(c, dalloc(&S->d_scan, (int64_t)scan_scratch_ints((int32_t)S->ptr_cap)));
+    CK(c, dalloc(&S->d_lflag, S->ptr_cap));
+    CK(c, dalloc(&S->d_lpos, S->ptr_cap));
+    CK(c, dalloc(&S->d_long, S->ptr_cap));
   }
   CK(c, cudaMemsetAsync(S->d_cnt, 0, sizeof(int32_t) * (S->M + 1), c->st));
   cut_list_kernel<false><<<grid_of(c->n, 256), 256, 0, c->st>>>(c->d_rp, c->d_ec, S->d_mask, a, S->d_cnt,
@@ -536,6 +602,16 @@ f2m_status cut_lists(f2m_ctx* c) {
                                                                  S->d_ptr, S->d_items);
   count_launch();
   CK(c, cudaGetLastError());
+  // the cuts with long lists, in index order
+  cut_long_flag_kernel<<<grid_of(S->M, 256), 256, 0, c->st>>>(S->d_cnt, (int32_t)S->M, S->d_lflag);
+  count_launch();
+  CK(c, launch_scan(S->d_lflag, S->d_lpos, (int32_t)S->M, S->d_scan, c->st));
+  cut_long_list_kernel<<<grid_of(S->M, 256), 256, 0, c->st>>>(S->d_lflag, S->d_lpos, (int32_t)S->M, S->d_long);
+  count_launch();
+  int32_t nlong = 0;
+  CK(c, cudaMemcpyAsync(&nlong, S->d_lpos + S->M, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  S->nlong = nlong;
   S->items = total;
   S->built_version = c->plan.version;
   S->built_L = S->L;
@@ -563,6 +639,8 @@ f2m_status cut_gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, long l
   const int32_t* ptr = S->d_ptr;
   const int2* items = S->d_items;
   int32_t M = (int32_t)S->M;
+  const int32_t* lcuts = S->d_long;
+  int32_t nlong = S->nlong;
   int32_t* l0 = c->d_lam[c->cur];
   int32_t* l1 = c->d_lam[c->cur ^ 1];
   int32_t* m0 = S->d_mu[S->cur];
@@ -571,7 +649,7 @@ f2m_status cut_gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, long l
   long long msw = max_sweeps, tcl = tcap, budget = c->p.barrier_budget_cycles;
   GdpCtl* ctl = c->d_gdp;
   void* args[] = {(void*)&rp, (void*)&ec, (void*)&mask, (void*)&a, (void*)&ptr, (void*)&items, (void*)&M,
-                  (void*)&l0, (void*)&l1, (void*)&m0, (void*)&m1, (void*)&F, (void*)&shift, (void*)&msw,
+                  (void*)&lcuts, (void*)&nlong, (void*)&l0, (void*)&l1, (void*)&m0, (void*)&m1, (void*)&F, (void*)&shift, (void*)&msw,
                   (void*)&ctl, (void*)&tb, (void*)&tc, (void*)&tcl, (void*)&budget};
   CK(c, cudaLaunchCooperativeKernel((const void*)cut_gdp_kernel<4>, dim3(grid), dim3(threads), args, 0, c->st));
   count_launch();
@@ -690,10 +768,16 @@ f2m_status cut_separate(f2m_ctx* c, int32_t* d_comp_out, int32_t* m_out) {
       dfree(S->d_cnt);
       dfree(S->d_ptr);
       dfree(S->d_scan);
+      dfree(S->d_lflag);
+      dfree(S->d_lpos);
+      dfree(S->d_long);
       S->ptr_cap = n + 1;
       CK(c, dalloc(&S->d_cnt, S->ptr_cap));
       CK(c, dalloc(&S->d_ptr, S->ptr_cap));
       CK(c, dalloc(&S->d_scan, (int64_t)scan_scratch_ints((int32_t)S->ptr_cap)));
+      CK(c, dalloc(&S->d_lflag, S->ptr_cap));
+      CK(c, dalloc(&S->d_lpos, S->ptr_cap));
+      CK(c, dalloc(&S->d_long, S->ptr_cap));
       S->built_version = -1;
     }
   }
