@@ -148,6 +148,16 @@ typedef struct {
   double ms_extract;            /* device time of the sign extraction */
   double ms_finish;             /* host time of the finisher incl. copies */
   double ms_total;              /* host wall time of f2m_solve */
+  /* the finisher's split (host clock): device preparation and copies to the
+   * host, the three phases of successive shortest paths (blocks of 2,048
+   * nodes on all host threads, blocks of 16,384, the rest per instance), and
+   * the copies back with the scatter; augmentations per phase */
+  double ms_finish_prep;
+  double ms_finish_phase[3];
+  double ms_finish_scatter;
+  int64_t finish_aug_phase[3];
+  int32_t finish_threads;       /* host threads the blocked phases used */
+  int32_t pad_info;
 } f2m_info;
 
 /* f2m_info.gdp_kernel values */

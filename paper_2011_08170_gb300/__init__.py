@@ -76,10 +76,18 @@ class f2m_info(C.Structure):
                 ("certified", C.c_int32), ("status", C.c_int32), ("batch_shape", C.c_int32),
                 ("batch_graph", C.c_int32), ("gdp_kernel", C.c_int32),
                 ("ms_gdp", C.c_double), ("ms_pricing", C.c_double), ("ms_merge", C.c_double),
-                ("ms_extract", C.c_double), ("ms_finish", C.c_double), ("ms_total", C.c_double)]
+                ("ms_extract", C.c_double), ("ms_finish", C.c_double), ("ms_total", C.c_double),
+                ("ms_finish_prep", C.c_double), ("ms_finish_phase", C.c_double * 3),
+                ("ms_finish_scatter", C.c_double), ("finish_aug_phase", C.c_int64 * 3),
+                ("finish_threads", C.c_int32), ("pad_info", C.c_int32)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            d[k] = list(v) if hasattr(v, "__len__") else v
+        d.pop("pad_info")
+        return d
 
 
 class f2m_subtour_info(C.Structure):

@@ -321,6 +321,21 @@ f2m_status f2m::create_internal(const int32_t* xy, int32_t n, const int32_t* row
       finisher_work_reserve(c->fin_work, n);
     }
     if (e == cudaSuccess) e = dalloc(&c->d_x2, c->ec_cap);
+    // the pricing scan's and the merge's buffers, so that a solve allocates
+    // nothing unless its graph outgrows them
+    if (e == cudaSuccess && p.pricing) {
+      c->pairs_cap = p.pricing_cap;
+      c->tmp_col_cap = c->ec_cap;
+      e = dalloc(&c->d_pts, n);
+      if (e == cudaSuccess) e = dalloc(&c->d_count, 1);
+      if (e == cudaSuccess) e = dalloc(&c->d_tile, 1);
+      if (e == cudaSuccess) e = dalloc(&c->d_pairs, c->pairs_cap);
+      if (e == cudaSuccess) e = dalloc(&c->d_deg, n + 1);
+      if (e == cudaSuccess) e = dalloc(&c->d_tmp_rp, n + 1);
+      if (e == cudaSuccess) e = dalloc(&c->d_new_rp, n + 1);
+      if (e == cudaSuccess) e = dalloc(&c->d_block_sums, (int64_t)scan_scratch_ints(n));
+      if (e == cudaSuccess) e = dalloc(&c->d_tmp_col, c->tmp_col_cap);
+    }
     if (e == cudaSuccess) e = dalloc(&c->d_lam[0], n);
     if (e == cudaSuccess) e = dalloc(&c->d_lam[1], n);
     if (e == cudaSuccess) e = dalloc(&c->d_lam2, n);
@@ -465,6 +480,10 @@ f2m_status f2m::gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, bool 
     if (h.status & kGdpOverflow) return fail(c, F2M_ERR_OVERFLOW, "|lambda| reached 2^29");
     return h.fixed_point ? F2M_OK : F2M_ERR_NOT_CONVERGED;
   }
+  if (c->plan1_pending) {
+    CK(c, plan_build_tiles(c->num_sms, c->p.frac_bits, c->p.gdp_ctas_per_sm, c->plan, c->st));
+    c->plan1_pending = false;
+  }
   if (c->plan2_pending) {
     CK(c, plan_build2(c->plan, c->p.frac_bits, c->st));
     c->plan2_pending = false;
@@ -599,8 +618,6 @@ f2m_status f2m::price_internal(f2m_ctx* c, double* ms, const int32_t* lam_overri
     c->pairs_cap = c->p.pricing_cap;
     CK(c, dalloc(&c->d_pairs, c->pairs_cap));
   }
-  std::vector<int4> tiles;
-  build_tiles(c, tiles);
   int32_t fb = 0;
   const int32_t* lam = cur_lambda(c, &fb);
   if (lam_override) lam = lam_override;
@@ -608,6 +625,12 @@ f2m_status f2m::price_internal(f2m_ctx* c, double* ms, const int32_t* lam_overri
   // full scan: points in caller order; culled scan: in the renumbered (Morton)
   // order, so that a tile is a compact patch with a small bounding box
   const bool culled = c->p.pricing == 2;
+  // the full scan's tile-pair list depends only on the segments scanned: it
+  // stays on the device from one scan to the next while they are the same
+  std::vector<int4> tiles;
+  const bool reuse = !culled && c->tiles_valid && c->tiles_seg_scan == c->seg_scan &&
+                     c->tiles_seg_off == c->seg_off;
+  if (!reuse) build_tiles(c, tiles);
   CK(c, cudaEventRecord(c->ev0, c->st));
   CK(c, launch_pricing_prep(c->d_xy, lam, culled ? c->plan.perm : nullptr, c->n, fb, c->d_pts, c->st));
   if (culled && !tiles.empty()) {
@@ -658,19 +681,26 @@ f2m_status f2m::price_internal(f2m_ctx* c, double* ms, const int32_t* lam_overri
     }
     tiles.swap(kept);
   }
-  if ((int64_t)tiles.size() > c->tiles_cap) {
-    dfree(c->d_tiles);
-    c->tiles_cap = (int64_t)tiles.size() + 64;
-    CK(c, dalloc(&c->d_tiles, c->tiles_cap));
+  if (!reuse) {
+    if ((int64_t)tiles.size() > c->tiles_cap) {
+      dfree(c->d_tiles);
+      c->tiles_cap = (int64_t)tiles.size() + 64;
+      CK(c, dalloc(&c->d_tiles, c->tiles_cap));
+    }
+    if (!tiles.empty())
+      CK(c, cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, c->st));
+    c->tiles_valid = !culled;
+    c->tiles_seg_scan = c->seg_scan;
+    c->tiles_seg_off = c->seg_off;
+    c->ntiles = (int64_t)tiles.size();
   }
-  if (!tiles.empty())
-    CK(c, cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, c->st));
+  const int64_t ntiles = c->ntiles;
   bool first = true;
   for (;;) {
     if (!first) CK(c, cudaEventRecord(c->ev0, c->st));
     first = false;
     CK(c, launch_pricing_scan(c->d_pts, c->d_xy, lam, c->d_rp, c->d_ec, c->n, fb, c->d_tiles,
-                              (int32_t)tiles.size(), c->d_pairs, c->pairs_cap, c->d_count, c->d_tile,
+                              (int32_t)ntiles, c->d_pairs, c->pairs_cap, c->d_count, c->d_tile,
                               c->num_sms, c->st));
     CK(c, cudaEventRecord(c->ev1, c->st));
     unsigned long long cnt = 0;
@@ -748,10 +778,12 @@ f2m_status f2m::merge_internal(f2m_ctx* c, const int2* d_pairs, int64_t npairs, 
   CK(c, read_check(c, &h));
   c->nnz = nnz_h;
   if (h.flags) return fail(c, F2M_ERR_INVALID_ARG, check_message(h.flags, h.first_bad));
-  CK(c, plan_build(c->d_rp, c->d_ec, n, c->nnz, c->num_sms, !(c->p.flags & F2M_FLAG_STREAMING_GDP),
-                   c->p.frac_bits, c->p.gdp_ctas_per_sm, c->plan, c->st));
-  // the two-sweep tiles only serve GDP phases: built when the next one starts
-  // (a merge before the finisher and the last scan needs none)
+  // the internal CSR now (the finisher reads it); the tiles of the
+  // shared-memory GDP kernels only serve GDP phases: built when the next one
+  // starts (a merge before the finisher and the last scan needs none)
+  CK(c, plan_build(c->d_rp, c->d_ec, n, c->nnz, c->num_sms, false, c->p.frac_bits, c->p.gdp_ctas_per_sm,
+                   c->plan, c->st));
+  c->plan1_pending = c->seg_off.size() == 2 && !(c->p.flags & F2M_FLAG_STREAMING_GDP);
   c->plan.valid2 = false;
   c->plan2_pending = c->seg_off.size() == 2 && !(c->p.flags & F2M_FLAG_ONE_SWEEP_GDP);
   CK(c, cudaEventRecord(c->ev1, c->st));
@@ -814,6 +846,8 @@ f2m_status f2m::bound_internal(f2m_ctx* c, int64_t* b2) {
 // renumbered CSR, successive shortest paths on the host, results scattered back
 // to caller order on the device.
 f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug, const uint8_t* h_include) {
+  using clk = std::chrono::steady_clock;
+  const auto t_prep = clk::now();
   const int32_t n = c->n;
   const int32_t F = c->p.frac_bits;
   GdpPlan& P = c->plan;
@@ -884,10 +918,12 @@ f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug, const uint8_t* h_inc
     if (missing) return fail(c, F2M_ERR_INVALID_ARG, "finisher: CSR not symmetric");
     c->twin_version = P.version;
   }
+  c->fin_stats.ms_prep += std::chrono::duration<double, std::milli>(clk::now() - t_prep).count();
   static const int32_t hw = (int32_t)std::thread::hardware_concurrency();
   const int r = host_finisher(n, c->h_irp, c->h_iec, c->h_twin, c->h_y, c->h_exl, c->h_lam, F,
                               c->h_lam2, c->seg_off.data(), nseg, h_include, hw > 1 ? hw : 1, aug,
-                              c->fin_work);
+                              c->fin_work, &c->fin_stats);
+  const auto t_scatter = clk::now();
   if (r == 7)
     return fail(c, F2M_ERR_INFEASIBLE, c->d_b ? "no fractional b-matching exists on the candidate graph"
                                               : "no fractional 2-matching exists on the candidate graph");
@@ -902,8 +938,20 @@ f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug, const uint8_t* h_inc
   CK(c, fin_scatter(P, c->d_rp, c->d_fy, c->d_twin, d_lam2_int, c->d_x2, c->d_lam2, c->d_seg_off,
                     (int32_t)c->seg_off.size() - 1, c->d_fin_include, c->st));
   CK(c, cudaStreamSynchronize(c->st));
+  c->fin_stats.ms_scatter += std::chrono::duration<double, std::milli>(clk::now() - t_scatter).count();
   c->fb_cur = F + 1;
   return F2M_OK;
+}
+
+void f2m::copy_finisher_stats(const f2m_ctx* c, f2m_info* info) {
+  const FinisherStats& f = c->fin_stats;
+  info->ms_finish_prep = f.ms_prep;
+  info->ms_finish_scatter = f.ms_scatter;
+  for (int k = 0; k < 3; ++k) {
+    info->ms_finish_phase[k] = f.ms_phase[k];
+    info->finish_aug_phase[k] = f.aug[k];
+  }
+  info->finish_threads = f.threads;
 }
 
 // The solve loop; its decisions match the CPU oracle's step for step:
@@ -921,6 +969,7 @@ extern "C" f2m_status f2m_solve(f2m_ctx* c, f2m_info* info_out) {
   const int32_t F = c->p.frac_bits;
   info.frac_bits = F;
   info.batch_shape = -1;
+  c->fin_stats = FinisherStats();
   f2m_status status = F2M_OK;
   int64_t last_pairs = 0;  // pairs found by the last scan
   for (;;) {
@@ -998,6 +1047,7 @@ extern "C" f2m_status f2m_solve(f2m_ctx* c, f2m_info* info_out) {
   info.nnz = c->nnz;
   info.gdp_kernel = c->gdp_kernel;
   info.status = status;
+  copy_finisher_stats(c, &info);
   info.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (info_out) *info_out = info;
   return status;

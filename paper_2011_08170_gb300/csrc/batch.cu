@@ -729,6 +729,7 @@ extern "C" f2m_status f2m_solve_batch(f2m_batch* b, f2m_info* info_out, f2m_info
   b->res_used = 0;
   f2m_info tot;
   std::memset(&tot, 0, sizeof(tot));
+  c->fin_stats = FinisherStats();
   f2m_status status = F2M_OK;
   auto any_in = [&](int st) {
     for (int s : state)
@@ -884,6 +885,7 @@ extern "C" f2m_status f2m_solve_batch(f2m_batch* b, f2m_info* info_out, f2m_info
     if (status == F2M_OK && inst_status[s] != F2M_OK) status = (f2m_status)inst_status[s];
   }
   tot.status = status;
+  copy_finisher_stats(c, &tot);
   tot.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (info_out) {
     for (int32_t s = 0; s < K; ++s) {

@@ -25,6 +25,10 @@ struct f2m_ctx {
   uint8_t* d_fin_include = nullptr;     // per segment: the finisher may change it (NULL = all)
   int4* d_tiles = nullptr;              // pricing tile-pair list
   int64_t tiles_cap = 0;
+  int64_t ntiles = 0;                   // tile pairs in d_tiles
+  bool tiles_valid = false;             // d_tiles holds the full scan's list for:
+  std::vector<uint8_t> tiles_seg_scan;  //   these scanned segments
+  std::vector<int32_t> tiles_seg_off;   //   of these segments
   int2* d_ranges = nullptr;             // culled pricing: point ranges of the tiles,
   float4* d_boxes = nullptr;            // their bounding boxes
   float* d_smax = nullptr;              // and largest filter radii
@@ -74,6 +78,7 @@ struct f2m_ctx {
   unsigned long long* d_bad = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   f2m::GdpPlan plan;         // renumbering and tiles of the shared-memory GDP kernel
+  bool plan1_pending = false;  // the one-sweep tiles are built at the next GDP phase
   bool plan2_pending = false;  // the two-sweep tiles are built at the next GDP phase
   f2m::ClassPlan classes;    // colour classes of the class-by-class GDP
   // exact finisher: device scratch, pinned host mirrors, host work arrays
@@ -90,6 +95,7 @@ struct f2m_ctx {
   int32_t* h_lam = nullptr;
   int32_t* h_lam2 = nullptr;
   f2m::FinisherWork* fin_work = nullptr;
+  f2m::FinisherStats fin_stats;  // the finisher's split, summed since the solve began
   f2m::CutState* cuts = nullptr;  // layers of subtour-elimination cuts and their duals
   std::string err;
 };
@@ -129,6 +135,7 @@ f2m_status extract_internal(f2m_ctx* c, int64_t* bad, double* ms);
 f2m_status bound_internal(f2m_ctx* c, int64_t* b2);
 // h_include (host, per segment; NULL = all): the segments the finisher works on
 f2m_status finisher_internal(f2m_ctx* c, int64_t* aug, const uint8_t* h_include);
+void copy_finisher_stats(const f2m_ctx* c, f2m_info* info);
 // subtour-elimination cuts (cuts.cu)
 void cut_state_free(CutState* s);
 int64_t cut_count(const f2m_ctx* c);

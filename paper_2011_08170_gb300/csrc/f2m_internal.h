@@ -158,6 +158,7 @@ cudaError_t launch_gdp_classes(const int32_t* rp, const int2* ec, const int32_t*
 // Spatial renumbering and per-CTA plan; see gdp_tiled.cu.
 struct GdpPlan {
   int32_t n = 0;
+  int64_t nnz = 0;               // entries of the internal CSR
   int64_t version = 0;           // bumped whenever the internal CSR is rebuilt
   bool valid = false;            // the tiled kernel can run this CSR
   int32_t B = 0, threads = 0;    // CTAs (one node range each) and threads per CTA
@@ -187,6 +188,7 @@ struct GdpPlan {
   int32_t* scan_tmp = nullptr;
   int64_t irp_cap = 0, iec_cap = 0, lec_cap = 0, tmp_cap = 0, halo_cap = 0, scan_cap = 0;
   int64_t order_cap = 0, slc_cap = 0;
+  int64_t cta_cap = 0;           // entries of part, hcount, scount, soff, hoff
   int64_t ilam_cap[3] = {0, 0, 0};
   // two-sweep form (gdp_tiled2.cu): H1 rows and the H2 ring per CTA
   bool valid2 = false;
@@ -220,6 +222,8 @@ cudaError_t plan_renumber(const int2* xy, int32_t n, const std::vector<int32_t>&
 // internal CSR (always) and, if `tiles`, the per-CTA tiles of the shared-memory kernel
 cudaError_t plan_build(const int32_t* rp, const int2* ec, int32_t n, int64_t nnz, int num_sms,
                        bool tiles, int32_t F, int32_t ctas_per_sm, GdpPlan& p, cudaStream_t st);
+// the per-CTA tiles alone, for the internal CSR plan_build made last
+cudaError_t plan_build_tiles(int num_sms, int32_t F, int32_t ctas_per_sm, GdpPlan& p, cudaStream_t st);
 // dst[i] = src[perm[i]]  /  dst[perm[i]] = src[i]
 cudaError_t gather_perm(const int32_t* src, const int32_t* perm, int32_t n, int32_t* dst,
                         cudaStream_t st);
@@ -326,10 +330,16 @@ void finisher_work_free(FinisherWork* w);
 // [seg_off[s], seg_off[s+1]) go to up to `threads` host threads; with include
 // (per segment; NULL = all) the other segments are neither read nor written.
 // Returns 0 ok, 7 infeasible, 5 overflow.
+// time and augmentations of the finisher, summed over its calls
+struct FinisherStats {
+  double ms_prep = 0, ms_phase[3] = {0, 0, 0}, ms_scatter = 0;
+  int64_t aug[3] = {0, 0, 0};
+  int32_t threads = 0;
+};
 int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t* twin, uint8_t* y,
                   const int32_t* exl, const int32_t* lam, int32_t F, int32_t* lam2,
                   const int32_t* seg_off, int32_t nseg, const uint8_t* include, int32_t threads,
-                  int64_t* augmentations, FinisherWork* w);
+                  int64_t* augmentations, FinisherWork* w, FinisherStats* stats);
 // lam_out = 2 * lam_in (F bits -> F+1 bits)
 cudaError_t launch_double(const int32_t* lam_in, int32_t* lam_out, int32_t n, cudaStream_t st);
 

@@ -44,6 +44,7 @@
 // ids here: L_i = i, R_i = n + i; key(L_i) = 2i, key(R_i) = 2i + 1.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <condition_variable>
 #include <cstdint>
 #include <functional>
@@ -321,7 +322,14 @@ int run_items(int32_t count, int32_t threads, FinisherWork* w, std::vector<int64
 int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t* twin, uint8_t* y,
                   const int32_t* exl, const int32_t* lam, int32_t F, int32_t* lam2,
                   const int32_t* seg_off, int32_t nseg, const uint8_t* include, int32_t threads,
-                  int64_t* augmentations, FinisherWork* w) {
+                  int64_t* augmentations, FinisherWork* w, FinisherStats* stats) {
+  using clk = std::chrono::steady_clock;
+  auto ms_since = [](clk::time_point t) { return std::chrono::duration<double, std::milli>(clk::now() - t).count(); };
+  auto pushes_total = [](const std::vector<int64_t>& v) {
+    int64_t t = 0;
+    for (int64_t p : v) t += p;
+    return t;
+  };
   finisher_work_reserve(w, n);
   if (w->stamp.load() > (1u << 31)) {  // far from wrapping: clear the stamps and restart
     std::fill(w->reached.begin(), w->reached.end(), 0u);
@@ -344,6 +352,7 @@ int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t*
       blocks2.push_back(make_int2(b0, std::min(b0 + kFinBlock2, seg_off[sg + 1])));
   }
   std::vector<int64_t> pushes;
+  auto t0 = clk::now();
   int r = run_items((int32_t)blocks.size(), threads, w, pushes,
                     [&](int32_t k, Searcher& sr, int64_t* p) {
                       for (int32_t i = blocks[k].x; i < blocks[k].y; ++i) {
@@ -355,6 +364,13 @@ int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t*
                       return solve_range(n, blocks[k].x, blocks[k].y, lam, nullptr, irp, iec, twin, y, F, w,
                                          sr, p);
                     });
+  int64_t done1 = pushes_total(pushes);
+  if (stats) {
+    stats->ms_phase[0] += ms_since(t0);
+    stats->aug[0] += done1;
+    stats->threads = std::max<int32_t>(stats->threads, std::min<int32_t>(threads, (int32_t)blocks.size()));
+  }
+  t0 = clk::now();
   int64_t* pi_start = w->pi_start.data();
   if (r == 0)  // the potentials at phase 2's start, per block (every block copies its own nodes)
     r = run_items((int32_t)blocks2.size(), threads, w, pushes, [&](int32_t k, Searcher&, int64_t*) {
@@ -369,6 +385,12 @@ int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t*
                     return solve_range(n, blocks2[k].x, blocks2[k].y, nullptr, pi_start, irp, iec, twin, y, F,
                                        w, sr, p);
                   });
+  const int64_t done2 = pushes_total(pushes);
+  if (stats) {
+    stats->ms_phase[1] += ms_since(t0);
+    stats->aug[1] += done2 - done1;
+  }
+  t0 = clk::now();
   if (r == 0)
     r = run_items((int32_t)segs.size(), threads, w, pushes, [&](int32_t k, Searcher& sr, int64_t* p) {
       const int32_t sg = segs[k];
@@ -383,8 +405,11 @@ int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t*
       }
       return st;
     });
-  int64_t total = 0;
-  for (int64_t p : pushes) total += p;
+  const int64_t total = pushes_total(pushes);
+  if (stats) {
+    stats->ms_phase[2] += ms_since(t0);
+    stats->aug[2] += total - done2;
+  }
   *augmentations = total;
   return r;
 }

@@ -587,8 +587,26 @@ cudaError_t plan_build(const int32_t* rp, const int2* ec, int32_t n, int64_t nnz
   internal_rows_kernel<<<grid_for(n, 128), 128, 0, st>>>(rp, ec, p.perm, p.inv, p.irp, n, p.iec);
   count_launch();
   PCK(cudaGetLastError());
+  p.n = n;
+  p.nnz = nnz;
   if (!tiles) return cudaSuccess;
+  return plan_build_tiles(num_sms, F, ctas_per_sm, p, st);
+}
 
+cudaError_t plan_build_tiles(int num_sms, int32_t F, int32_t ctas_per_sm, GdpPlan& p, cudaStream_t st) {
+  const int32_t n = p.n;
+  p.valid = false;
+  // per-CTA arrays, sized once for the largest grid (2 CTAs per SM)
+  if (p.cta_cap < 2LL * num_sms + 1) {
+    int32_t** arrs[] = {&p.part, &p.hcount, &p.scount, &p.soff, &p.hoff};
+    for (int32_t** a : arrs) {
+      if (*a) cudaFree(*a);
+      *a = nullptr;
+      int64_t cap = 0;
+      PCK(grow(a, &cap, 2LL * num_sms + 1));
+    }
+    p.cta_cap = 2LL * num_sms + 1;
+  }
   // CTAs: 2 per SM x 512 threads, or 1 per SM x 1024 threads when a CTA's
   // shared memory would not fit twice on an SM
   int dev = 0, smem_optin = 0, smem_sm = 0;
@@ -604,24 +622,8 @@ cudaError_t plan_build(const int32_t* rp, const int2* ec, int32_t n, int64_t nnz
     if (ctas_per_sm != 0 && ctas_per_sm != per_sm) continue;
     int B = num_sms * per_sm;
     if ((int64_t)B > (int64_t)n / 8) B = (int)((int64_t)n / 8 > 1 ? (int64_t)n / 8 : 1);
-    int64_t cap = 0;
-    if (p.part) cudaFree(p.part);
-    p.part = nullptr;
-    PCK(grow(&p.part, &cap, B + 1)); cap = 0;
-    if (p.hcount) cudaFree(p.hcount);
-    p.hcount = nullptr;
-    PCK(grow(&p.hcount, &cap, B + 1)); cap = 0;
-    if (p.scount) cudaFree(p.scount);
-    p.scount = nullptr;
-    PCK(grow(&p.scount, &cap, B + 1)); cap = 0;
-    if (p.soff) cudaFree(p.soff);
-    p.soff = nullptr;
-    PCK(grow(&p.soff, &cap, B + 1)); cap = 0;
-    if (p.hoff) cudaFree(p.hoff);
-    p.hoff = nullptr;
-    PCK(grow(&p.hoff, &cap, B + 1));
     if (!p.stats) {
-      cap = 0;
+      int64_t cap = 0;
       PCK(grow(&p.stats, &cap, 4));
     }
     PCK(cudaMemsetAsync(p.stats, 0, 4 * sizeof(int32_t), st));

@@ -39,6 +39,7 @@ namespace f2m {
 // kPricingTile j-points.  P = 8 (128 threads) when there are many tile pairs,
 // P = 4 (256 threads: twice the threads on one tile pair) when there are few.
 constexpr int kPriceTile = kPricingTile;
+constexpr int kPriceJMax = kPricingJ;  // j-points of a tile pair: the scan's lists never hold more
 
 // pts[v] = {x, y, s, node} of node perm[v] (perm NULL: node v); the node id is
 // carried in the last component's bits
@@ -140,7 +141,7 @@ __device__ __forceinline__ float pricing_filter(float aj, float cj, float yj, fl
 constexpr int kPriceGroup = 4;
 constexpr int kPriceChunk = 64;
 constexpr int kWarpHits = (kPriceChunk / kPriceGroup) * 32;
-static_assert(kPriceTile % kPriceChunk == 0 && kPriceChunk % kPriceGroup == 0, "chunking");
+static_assert(kPriceJMax % kPriceChunk == 0 && kPriceChunk % kPriceGroup == 0, "chunking");
 
 // Decide exactly every passing pair of the groups in a warp's hit list (each
 // entry: first j of the group << 8 | thread); all lanes of the warp take part.
@@ -171,7 +172,7 @@ __device__ __forceinline__ void pricing_hits(const int* hits, int nh, int lane, 
 }
 
 template <int P>
-__global__ void __launch_bounds__(kPricingTile / P, P == 8 ? 6 : 4)
+__global__ void __launch_bounds__(kPricingTile / P, P == 8 ? 7 : 4)
 pricing_kernel(const float4* __restrict__ pts, const int2* __restrict__ xy,
                const int32_t* __restrict__ lam, const int32_t* __restrict__ rp,
                const int2* __restrict__ ec, int32_t n, int32_t fb, const int4* __restrict__ tiles,
@@ -180,8 +181,8 @@ pricing_kernel(const float4* __restrict__ pts, const int2* __restrict__ xy,
   constexpr int kPriceThreads = kPriceTile / P;
   constexpr int Q = P / 2;
   static_assert(kPriceThreads <= 256 && kPriceTile <= (1 << 23), "hit entry packing");
-  __shared__ float4 s_ac[kPriceTile];                       // {a, a, c, c} of the j-points
-  __shared__ float2 s_y[kPriceTile];                        // {y, y}
+  __shared__ float4 s_ac[kPriceJMax];                       // {a, a, c, c} of the j-points
+  __shared__ float2 s_y[kPriceJMax];                        // {y, y}
   __shared__ int s_hit[(kPriceThreads / 32) * kWarpHits];  // one list per warp
   __shared__ int s_tp;
   const float2 minus_one = make_float2(-1.0f, -1.0f);
@@ -220,7 +221,7 @@ pricing_kernel(const float4* __restrict__ pts, const int2* __restrict__ xy,
       ny[q] = make_float2(-y[0], -y[1]);
     }
     // the tile's j-points, rounded up to whole chunks (at most kPriceTile)
-    const int kend = min(kPriceTile, (tl.w - tl.z + kPriceChunk - 1) / kPriceChunk * kPriceChunk);
+    const int kend = min(kPriceJMax, (tl.w - tl.z + kPriceChunk - 1) / kPriceChunk * kPriceChunk);
     for (int k = threadIdx.x; k < kend; k += kPriceThreads) {
       const int j = tl.z + k;
       if (j < tl.w) {
