@@ -551,7 +551,8 @@ def single_line(args, wname, w, rank, world, local, dist, f2m, torch, nested=Fal
                 "ms_prep": statistics.median(i["ms_finish_prep"] for i in infos),
                 "ms_phase": [statistics.median(i["ms_finish_phase"][k] for i in infos) for k in range(3)],
                 "ms_scatter": statistics.median(i["ms_finish_scatter"] for i in infos),
-                "aug_phase": inf0["finish_aug_phase"], "threads": inf0["finish_threads"]},
+                "aug_phase": inf0["finish_aug_phase"], "threads": inf0["finish_threads"],
+                "ms_prep_per_step": [round(i["ms_finish_prep"], 3) for i in infos]},
             "sweep_edges_per_s": iters * nnz0 / (ms_gdp * 1e-3),
             "wall_ms_timed_region": wall_ms,
             "host_ms": host_ms,

@@ -80,11 +80,105 @@ void pin_free(void* p) {
     g_pin_size.erase(it);
   }
 }
+
+// Device blocks: creating a context makes about sixty allocations, each
+// costing more than the kernel that fills it, so freed blocks are kept per
+// device (up to 4 GiB each) and reused for a request of at least half their
+// size.  A block enters the cache only after the device has finished all
+// work queued before its release (as cudaFree would wait), so no kernel still
+// in flight can see it handed out again.
+struct DevBlock {
+  size_t bytes;
+  int device;
+};
+std::mutex g_dev_mu;
+std::multimap<std::pair<int, size_t>, void*> g_dev_free;  // (device, size) -> cached block
+std::map<void*, DevBlock> g_dev_size;                      // every block handed out or cached
+std::map<int, size_t> g_dev_cached;
+constexpr size_t kDevCacheMax = (size_t)1 << 32;
+
+void dev_cache_flush(int dev) {  // caller holds g_dev_mu
+  for (auto it = g_dev_free.begin(); it != g_dev_free.end();) {
+    if (it->first.first == dev) {
+      cudaFree(it->second);
+      g_dev_size.erase(it->second);
+      it = g_dev_free.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  g_dev_cached[dev] = 0;
+}
+
+void dev_release_locked(void* p) {
+  auto it = g_dev_size.find(p);
+  if (it == g_dev_size.end()) {  // not ours: a plain block
+    cudaFree(p);
+    return;
+  }
+  const DevBlock b = it->second;
+  size_t& cached = g_dev_cached[b.device];
+  if (cached + b.bytes <= kDevCacheMax) {
+    g_dev_free.emplace(std::make_pair(b.device, b.bytes), p);
+    cached += b.bytes;
+  } else {
+    cudaFree(p);
+    g_dev_size.erase(it);
+  }
+}
 }  // namespace
 
+namespace f2m {
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  if (bytes == 0) bytes = 1;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  auto it = g_dev_free.lower_bound(std::make_pair(dev, bytes));
+  if (it != g_dev_free.end() && it->first.first == dev && it->first.second <= 2 * bytes) {
+    *p = it->second;
+    g_dev_cached[dev] -= it->first.second;
+    g_dev_free.erase(it);
+    return cudaSuccess;
+  }
+  e = cudaMalloc(p, bytes);
+  if (e == cudaErrorMemoryAllocation) {  // give the cached blocks back and try again
+    cudaGetLastError();
+    dev_cache_flush(dev);
+    e = cudaMalloc(p, bytes);
+  }
+  if (e == cudaSuccess) g_dev_size[*p] = DevBlock{bytes, dev};
+  return e;
+}
+
+static thread_local int t_dev_synced = 0;  // > 0 inside a DevSyncedScope
+
+DevSyncedScope::DevSyncedScope() {
+  cudaDeviceSynchronize();
+  ++t_dev_synced;
+}
+DevSyncedScope::~DevSyncedScope() { --t_dev_synced; }
+
+void dev_free(void* p) {
+  if (!p) return;
+  if (!t_dev_synced) cudaDeviceSynchronize();
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  dev_release_locked(p);
+}
+
+void dev_free_synced(void* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  dev_release_locked(p);
+}
+
+}  // namespace f2m
+
 static void free_finisher_buffers(f2m_ctx* c) {
-  if (c->d_twin) cudaFree(c->d_twin);
-  if (c->d_fy) cudaFree(c->d_fy);
+  dev_free(c->d_twin);
+  dev_free(c->d_fy);
   void* hp[] = {c->h_irp, c->h_iec, c->h_twin, c->h_y, c->h_exl, c->h_lam, c->h_lam2};
   for (void* q : hp) pin_free(q);
   c->d_twin = nullptr; c->d_fy = nullptr;
@@ -99,8 +193,8 @@ static void free_finisher_buffers(f2m_ctx* c) {
 static cudaError_t alloc_finisher_buffers(f2m_ctx* c, int64_t cap) {
   const int32_t n = c->n;
   const bool first = c->h_irp == nullptr;
-  if (c->d_twin) cudaFree(c->d_twin);
-  if (c->d_fy) cudaFree(c->d_fy);
+  dev_free(c->d_twin);
+  dev_free(c->d_fy);
   pin_free(c->h_iec);
   pin_free(c->h_twin);
   pin_free(c->h_y);
@@ -109,8 +203,8 @@ static cudaError_t alloc_finisher_buffers(f2m_ctx* c, int64_t cap) {
   c->fin_cap = 0;
   c->fin_version = -1;
   c->twin_version = -1;
-  cudaError_t e = cudaMalloc((void**)&c->d_twin, sizeof(int32_t) * cap);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_fy, cap);
+  cudaError_t e = dev_malloc((void**)&c->d_twin, sizeof(int32_t) * cap);
+  if (e == cudaSuccess) e = dev_malloc((void**)&c->d_fy, cap);
   if (e == cudaSuccess) e = pin_alloc((void**)&c->h_iec, sizeof(int2) * cap);
   if (e == cudaSuccess) e = pin_alloc((void**)&c->h_twin, sizeof(int32_t) * cap);
   if (e == cudaSuccess) e = pin_alloc((void**)&c->h_y, cap);
@@ -186,7 +280,7 @@ extern "C" const char* f2m_last_error(const f2m_ctx* ctx) {
 
 extern "C" void f2m_destroy(f2m_ctx* c) {
   if (!c) return;
-  if (c->st) cudaStreamSynchronize(c->st);
+  DevSyncedScope synced;  // one wait for the device, then every block goes to the cache
   dfree(c->d_xy); dfree(c->d_rp); dfree(c->d_ec); dfree(c->d_x2); dfree(c->d_tiles);
   dfree(c->d_seg_off); dfree(c->d_fin_include);
   dfree(c->d_lam[0]); dfree(c->d_lam[1]); dfree(c->d_lam2); dfree(c->d_exl); dfree(c->d_gdp);

@@ -105,10 +105,8 @@ f2m_status bfail(f2m_batch* b, f2m_status s, const std::string& msg) {
 
 extern "C" void f2m_destroy_batch(f2m_batch* b) {
   if (!b) return;
-  if (b->u) {
-    cudaStreamSynchronize(b->u->st);
-    f2m_destroy(b->u);
-  }
+  DevSyncedScope synced;  // one wait for the device, then every block goes to the cache
+  if (b->u) f2m_destroy(b->u);
   dfree(b->d_active); dfree(b->d_seg_ch); dfree(b->d_seg_sweeps); dfree(b->d_tiles); dfree(b->d_e1);
   dfree(b->d_chunk);
   if (b->h_tiles) cudaFreeHost(b->h_tiles);

@@ -115,12 +115,19 @@ template <typename T>
 cudaError_t dalloc(T** p, int64_t count) {
   *p = nullptr;
   size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
-  return cudaMalloc((void**)p, bytes);
+  return dev_malloc((void**)p, bytes);
 }
 
 template <typename T>
 void dfree(T*& p) {
-  if (p) cudaFree((void*)p);
+  if (p) dev_free((void*)p);
+  p = nullptr;
+}
+
+// for a caller that has already waited for every use of the block
+template <typename T>
+void dfree_synced(T*& p) {
+  if (p) dev_free_synced((void*)p);
   p = nullptr;
 }
 

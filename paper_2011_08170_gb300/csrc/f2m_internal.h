@@ -58,6 +58,19 @@ enum CheckBits {
   kBadDegreeReq = 256,
 };
 
+// Device memory of this library (api.cu): a process-wide cache of freed
+// blocks per device.  dev_free waits for the device (as cudaFree does) before
+// the block can be handed out again; dev_free_synced is for a caller that has
+// already waited for every use of the block.
+cudaError_t dev_malloc(void** p, size_t bytes);
+void dev_free(void* p);
+void dev_free_synced(void* p);
+// waits for the device once; while it lives, dev_free on this thread waits no more
+struct DevSyncedScope {
+  DevSyncedScope();
+  ~DevSyncedScope();
+};
+
 // process-wide count of kernel launches made by this library (api.cu)
 void count_launch();
 void count_launches(long long k);  // k launches replayed from a captured graph

@@ -118,15 +118,15 @@ cudaError_t color_classes(const int32_t* rp, const int2* ec, int32_t n, ClassPla
                           cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   if (cp.cap < n) {
-    if (cp.color) cudaFree(cp.color);
-    if (cp.order) cudaFree(cp.order);
-    if (cp.ctl) cudaFree(cp.ctl);
+    if (cp.color) dev_free(cp.color);
+    if (cp.order) dev_free(cp.order);
+    if (cp.ctl) dev_free(cp.ctl);
     cp.color = cp.order = nullptr;
     cp.ctl = nullptr;
     cp.cap = 0;
-    e = cudaMalloc((void**)&cp.color, sizeof(int32_t) * n);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&cp.order, sizeof(int32_t) * n);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&cp.ctl, sizeof(unsigned int) * 2);
+    e = dev_malloc((void**)&cp.color, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = dev_malloc((void**)&cp.order, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = dev_malloc((void**)&cp.ctl, sizeof(unsigned int) * 2);
     if (e != cudaSuccess) return e;
     cp.cap = n;
   }
@@ -150,11 +150,11 @@ cudaError_t color_classes(const int32_t* rp, const int2* ec, int32_t n, ClassPla
   }
   const int32_t C = (int32_t)h[1];
   // class offsets: counts on the device, prefix sums on the host (C is small)
-  if (cp.off) cudaFree(cp.off);
+  if (cp.off) dev_free(cp.off);
   cp.off = nullptr;
   int32_t* d_tmp = nullptr;
-  e = cudaMalloc((void**)&cp.off, sizeof(int32_t) * (C + 1));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&d_tmp, sizeof(int32_t) * (C + 1));
+  e = dev_malloc((void**)&cp.off, sizeof(int32_t) * (C + 1));
+  if (e == cudaSuccess) e = dev_malloc((void**)&d_tmp, sizeof(int32_t) * (C + 1));
   if (e == cudaSuccess) e = cudaMemsetAsync(d_tmp, 0, sizeof(int32_t) * (C + 1), st);
   if (e == cudaSuccess) {
     class_count_kernel<<<grid_for(n, 256), 256, 0, st>>>(cp.color, n, d_tmp);
@@ -176,17 +176,17 @@ cudaError_t color_classes(const int32_t* rp, const int2* ec, int32_t n, ClassPla
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (d_tmp) cudaFree(d_tmp);
+  if (d_tmp) dev_free(d_tmp);
   if (e != cudaSuccess) return e;
   cp.ncolors = C;
   return cudaSuccess;
 }
 
 void class_plan_free(ClassPlan& cp) {
-  if (cp.color) cudaFree(cp.color);
-  if (cp.order) cudaFree(cp.order);
-  if (cp.off) cudaFree(cp.off);
-  if (cp.ctl) cudaFree(cp.ctl);
+  if (cp.color) dev_free(cp.color);
+  if (cp.order) dev_free(cp.order);
+  if (cp.off) dev_free(cp.off);
+  if (cp.ctl) dev_free(cp.ctl);
   cp = ClassPlan{};
 }
 

@@ -495,11 +495,11 @@ constexpr int kPlanSortCap = 16384;
 template <typename T>
 static cudaError_t grow(T** p, int64_t* cap, int64_t need) {
   if (*p && *cap >= need) return cudaSuccess;
-  if (*p) cudaFree(*p);
+  if (*p) dev_free(*p);
   *p = nullptr;
   *cap = 0;
   const int64_t c = need + (need >> 3) + 64;
-  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (size_t)c);
+  cudaError_t e = dev_malloc((void**)p, sizeof(T) * (size_t)c);
   if (e == cudaSuccess) *cap = c;
   return e;
 }
@@ -509,7 +509,7 @@ void plan_free(GdpPlan& p) {
                   p.stats, p.ilam[0], p.ilam[1], p.ilam[2], p.keys, p.keys2, p.idx, p.sort_tmp,
                   p.scan_tmp, p.scount, p.soff, p.order, p.slc};
   for (void* q : ptrs)
-    if (q) cudaFree(q);
+    if (q) dev_free(q);
   p = GdpPlan();
 }
 
@@ -524,10 +524,10 @@ cudaError_t plan_renumber(const int2* xy, int32_t n, const std::vector<int32_t>&
   int64_t cap = 0;
   const int32_t nseg = (int32_t)seg_off.size() - 1;
   int32_t* d_seg = nullptr;
-  PCK(cudaMalloc((void**)&d_seg, sizeof(int32_t) * seg_off.size()));
+  PCK(dev_malloc((void**)&d_seg, sizeof(int32_t) * seg_off.size()));
   cudaError_t e0 = cudaMemcpyAsync(d_seg, seg_off.data(), sizeof(int32_t) * seg_off.size(),
                                    cudaMemcpyHostToDevice, st);
-  if (e0 != cudaSuccess) { cudaFree(d_seg); return e0; }
+  if (e0 != cudaSuccess) { dev_free(d_seg); return e0; }
   int end_bit = 40;
   while ((1LL << (end_bit - 40)) < nseg) ++end_bit;
   PCK(grow(&p.perm, &cap, n)); cap = 0;
@@ -539,11 +539,11 @@ cudaError_t plan_renumber(const int2* xy, int32_t n, const std::vector<int32_t>&
   count_launch();
   cudaError_t e1 = cudaGetLastError();
   if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(st);
-  cudaFree(d_seg);
+  dev_free(d_seg);
   PCK(e1);
   size_t bytes = 0;
   PCK(sort_pairs_u64(nullptr, bytes, p.keys, p.keys2, p.idx, p.perm, n, end_bit, st));
-  PCK(cudaMalloc(&p.sort_tmp, bytes > 0 ? bytes : 1));
+  PCK(dev_malloc(&p.sort_tmp, bytes > 0 ? bytes : 1));
   PCK(sort_pairs_u64(p.sort_tmp, bytes, p.keys, p.keys2, p.idx, p.perm, n, end_bit, st));
   count_launch();
   invert_perm_kernel<<<grid_for(n, 256), 256, 0, st>>>(p.perm, n, p.inv);
@@ -600,7 +600,7 @@ cudaError_t plan_build_tiles(int num_sms, int32_t F, int32_t ctas_per_sm, GdpPla
   if (p.cta_cap < 2LL * num_sms + 1) {
     int32_t** arrs[] = {&p.part, &p.hcount, &p.scount, &p.soff, &p.hoff};
     for (int32_t** a : arrs) {
-      if (*a) cudaFree(*a);
+      if (*a) dev_free(*a);
       *a = nullptr;
       int64_t cap = 0;
       PCK(grow(a, &cap, 2LL * num_sms + 1));

@@ -39,11 +39,11 @@ constexpr int kSortCap2 = 16384;  // shared-memory sort capacity of the plan ker
 template <typename T>
 cudaError_t grow2(T** p, int64_t* cap, int64_t need) {
   if (*p && *cap >= need) return cudaSuccess;
-  if (*p) cudaFree(*p);
+  if (*p) dev_free(*p);
   *p = nullptr;
   *cap = 0;
   const int64_t c = need + (need >> 3) + 64;
-  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (size_t)c);
+  cudaError_t e = dev_malloc((void**)p, sizeof(T) * (size_t)c);
   if (e == cudaSuccess) *cap = c;
   return e;
 }
@@ -608,7 +608,7 @@ void plan2_free(GdpPlan& p) {
   void* ptrs[] = {p.h2count, p.hhcount, p.s2count, p.nslc, p.hoff2, p.soff2, p.sloff2, p.halo2,
                   p.order2, p.slc2, p.lec2, p.tmp2, p.stats2, p.lec2p};
   for (void* q : ptrs)
-    if (q) cudaFree(q);
+    if (q) dev_free(q);
   p.h2count = p.hhcount = p.s2count = p.nslc = p.hoff2 = p.soff2 = p.sloff2 = p.halo2 = p.order2 = nullptr;
   p.tmp2 = p.stats2 = nullptr;
   p.slc2 = nullptr;
@@ -646,7 +646,7 @@ cudaError_t plan_build2(GdpPlan& p, int32_t F, cudaStream_t st) {
   if (p.cap2_small < B + 1) {
     int64_t c = 0;
     for (int32_t** q : {&p.h2count, &p.hhcount, &p.s2count, &p.nslc, &p.hoff2, &p.soff2, &p.sloff2}) {
-      if (*q) cudaFree(*q);
+      if (*q) dev_free(*q);
       *q = nullptr;
       c = 0;
       P2CK(grow2(q, &c, B + 1));

@@ -205,7 +205,7 @@ extern "C" f2m_status f2m_features(const int32_t* xy, int32_t n, float* feat, fl
 
 extern "C" void f2m_mlp_destroy(f2m_mlp* m) {
   if (!m) return;
-  cudaStreamSynchronize(m->st);
+  DevSyncedScope synced;  // one wait for the device, then every block goes to the cache
   dfree(m->master); dfree(m->m1); dfree(m->m2); dfree(m->img); dfree(m->partial);
   dfree(m->grad); dfree(m->step); dfree(m->status);
   if (m->ev0) cudaEventDestroy(m->ev0);
