@@ -17,6 +17,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/f2m.h"
@@ -71,6 +72,12 @@ struct f2m_batch {
   int2* d_res_ec = nullptr;         // arena of {col (union id), cost}
   uint8_t* d_res_x2 = nullptr;      // arena of x in half units
   int64_t res_cap = 0, res_used = 0;
+  int32_t* h_irp = nullptr;         // pinned copy of the internal row offsets (tile packing)
+  int32_t tiles_te = -1, tiles_tn = -1;  // tile limits tiles_all was packed with
+  long long* h_snap = nullptr;      // pinned staging of a snapshot
+  long long* d_snap_eoff = nullptr; // [count] arena offset of each instance being copied
+  uint8_t* d_snap_done = nullptr;   // [count] instances being copied
+  int32_t* d_snap_ent = nullptr;    // [count + 1] first entry of each instance
   std::vector<int64_t> res_eoff, res_nnz, res_b2;
   std::vector<int32_t> res_fb;
   std::vector<uint8_t> res_done;
@@ -108,6 +115,9 @@ extern "C" void f2m_destroy_batch(f2m_batch* b) {
   DevSyncedScope synced;  // one wait for the device, then every block goes to the cache
   if (b->u) f2m_destroy(b->u);
   dfree(b->d_active); dfree(b->d_seg_ch); dfree(b->d_seg_sweeps); dfree(b->d_tiles); dfree(b->d_e1);
+  dfree(b->d_snap_eoff); dfree(b->d_snap_done); dfree(b->d_snap_ent);
+  if (b->h_snap) cudaFreeHost(b->h_snap);
+  if (b->h_irp) cudaFreeHost(b->h_irp);
   dfree(b->d_chunk);
   if (b->h_tiles) cudaFreeHost(b->h_tiles);
   if (b->h_e1) cudaFreeHost(b->h_e1);
@@ -238,22 +248,49 @@ extern "C" f2m_status f2m_create_batch(int32_t count, const int32_t* n, const in
 static f2m_status batch_tiles(f2m_batch* b, int te, int tn, std::vector<int4>& tiles, std::vector<int32_t>& e1) {
   f2m_ctx* c = b->u;
   GdpPlan& P = c->plan;
-  std::vector<int32_t> irp(c->n + 1);
-  CK(c, cudaMemcpyAsync(irp.data(), P.irp, sizeof(int32_t) * (c->n + 1), cudaMemcpyDeviceToHost, c->st));
+  if (!b->h_irp) CK(c, cudaMallocHost((void**)&b->h_irp, sizeof(int32_t) * (c->n + 1)));
+  const int32_t* irp = b->h_irp;
+  CK(c, cudaMemcpyAsync(b->h_irp, P.irp, sizeof(int32_t) * (c->n + 1), cudaMemcpyDeviceToHost, c->st));
   CK(c, cudaStreamSynchronize(c->st));
-  tiles.clear();
-  e1.clear();
-  for (int32_t s = 0; s < b->count; ++s) {
-    int32_t v = c->seg_off[s];
-    const int32_t end = c->seg_off[s + 1];
+  // pack the node range [v, end) of segment s greedily: at most tn nodes and te entries a tile
+  auto pack = [&](int32_t s, int32_t v, int32_t end, std::vector<int4>& t_out, std::vector<int32_t>& e_out) {
     while (v < end) {
       const int32_t start = v, e0 = irp[v];
       while (v < end && v - start < tn && irp[v + 1] - e0 <= te) ++v;
-      if (v == start)
-        return fail(c, F2M_ERR_INVALID_ARG, "a node has more candidate edges than a batch tile holds");
-      tiles.push_back(make_int4(start, v, s, e0));
-      e1.push_back(irp[v]);
+      if (v == start) return false;
+      t_out.push_back(make_int4(start, v, s, e0));
+      e_out.push_back(irp[v]);
     }
+    return true;
+  };
+  const bool own = &tiles == &b->tiles_all;  // the phase's list (the autotuner packs its own)
+  const bool update = own && b->tiles_te == te && b->tiles_tn == tn && !tiles.empty();
+  std::vector<int4> nt;
+  std::vector<int32_t> ne;
+  nt.reserve(tiles.size() + 64);
+  ne.reserve(tiles.size() + 64);
+  if (update) {
+    // a merge only adds entries: keep every tile's node range with its new
+    // entry range, and pack again only a range that now holds too many entries
+    for (const int4& t : tiles) {
+      const int32_t e0 = irp[t.x], e1v = irp[t.y];
+      if (e1v - e0 <= te) {
+        nt.push_back(make_int4(t.x, t.y, t.z, e0));
+        ne.push_back(e1v);
+      } else if (!pack(t.z, t.x, t.y, nt, ne)) {
+        return fail(c, F2M_ERR_INVALID_ARG, "a node has more candidate edges than a batch tile holds");
+      }
+    }
+  } else {
+    for (int32_t s = 0; s < b->count; ++s)
+      if (!pack(s, c->seg_off[s], c->seg_off[s + 1], nt, ne))
+        return fail(c, F2M_ERR_INVALID_ARG, "a node has more candidate edges than a batch tile holds");
+  }
+  tiles.swap(nt);
+  e1.swap(ne);
+  if (own) {
+    b->tiles_te = te;
+    b->tiles_tn = tn;
   }
   return F2M_OK;
 }
@@ -658,16 +695,26 @@ static f2m_status snapshot(f2m_batch* b, const std::vector<uint8_t>& done) {
   const int32_t K = b->count;
   int32_t fb = 0;
   const int32_t* lam = cur_lambda(c, &fb);
+  if (!b->h_snap) {  // pinned staging: bounds and entry offsets down, mask and arena offsets up
+    CK(c, cudaMallocHost((void**)&b->h_snap, sizeof(long long) * K + sizeof(int32_t) * (K + 1) +
+                                              sizeof(long long) * K + K));
+    CK(c, dalloc(&b->d_snap_eoff, K));
+    CK(c, dalloc(&b->d_snap_done, K));
+    CK(c, dalloc(&b->d_snap_ent, K + 1));
+  }
+  long long* h_b2 = b->h_snap;
+  int32_t* h_ent = reinterpret_cast<int32_t*>(h_b2 + K);
+  long long* h_eoff = reinterpret_cast<long long*>(h_ent + K + 1);
+  uint8_t* h_done = reinterpret_cast<uint8_t*>(h_eoff + K);
   CK(c, launch_batch_extract_bound(c->d_rp, c->d_ec, lam, c->n, fb, c->d_seg_off, K, c->d_x2,
                                    b->d_seg_b2, b->d_seg_bad, nullptr, c->st));
-  std::vector<long long> b2(K);
-  std::vector<int32_t> rp(c->n + 1);
-  CK(c, cudaMemcpyAsync(b2.data(), b->d_seg_b2, sizeof(long long) * K, cudaMemcpyDeviceToHost, c->st));
-  CK(c, cudaMemcpyAsync(rp.data(), c->d_rp, sizeof(int32_t) * (c->n + 1), cudaMemcpyDeviceToHost, c->st));
+  CK(c, launch_batch_seg_entry(c->d_rp, c->d_seg_off, K, b->d_snap_ent, c->st));
+  CK(c, cudaMemcpyAsync(h_b2, b->d_seg_b2, sizeof(long long) * K, cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaMemcpyAsync(h_ent, b->d_snap_ent, sizeof(int32_t) * (K + 1), cudaMemcpyDeviceToHost, c->st));
   CK(c, cudaStreamSynchronize(c->st));
   int64_t need = b->res_used;
   for (int32_t s = 0; s < K; ++s)
-    if (done[s]) need += rp[c->seg_off[s + 1]] - rp[c->seg_off[s]];
+    if (done[s]) need += h_ent[s + 1] - h_ent[s];
   if (need > b->res_cap) {  // grow the arenas, keeping what they hold
     const int64_t cap = need + (need >> 2) + 1024;
     int2* ec = nullptr;
@@ -685,23 +732,26 @@ static f2m_status snapshot(f2m_batch* b, const std::vector<uint8_t>& done) {
     b->d_res_x2 = x2;
     b->res_cap = cap;
   }
+  bool any = false;
   for (int32_t s = 0; s < K; ++s) {
+    h_done[s] = done[s];
+    h_eoff[s] = 0;
     if (!done[s]) continue;
-    const int32_t v0 = c->seg_off[s], ns = c->seg_off[s + 1] - v0;
-    const int64_t e0 = rp[v0], nz = rp[v0 + ns] - e0;
-    CK(c, cudaMemcpyAsync(b->d_res_lam + v0, lam + v0, sizeof(int32_t) * ns, cudaMemcpyDeviceToDevice, c->st));
-    CK(c, cudaMemcpyAsync(b->d_res_rp + v0 + s, c->d_rp + v0, sizeof(int32_t) * (ns + 1), cudaMemcpyDeviceToDevice, c->st));
-    if (nz) {
-      CK(c, cudaMemcpyAsync(b->d_res_ec + b->res_used, c->d_ec + e0, sizeof(int2) * nz, cudaMemcpyDeviceToDevice, c->st));
-      CK(c, cudaMemcpyAsync(b->d_res_x2 + b->res_used, c->d_x2 + e0, nz, cudaMemcpyDeviceToDevice, c->st));
-    }
+    any = true;
+    const int64_t nz = h_ent[s + 1] - h_ent[s];
+    h_eoff[s] = b->res_used;
     b->res_eoff[s] = b->res_used;
     b->res_nnz[s] = nz;
-    b->res_b2[s] = b2[s];
+    b->res_b2[s] = h_b2[s];
     b->res_fb[s] = fb;
     b->res_done[s] = 1;
     b->res_used += nz;
   }
+  if (!any) return F2M_OK;
+  CK(c, cudaMemcpyAsync(b->d_snap_done, h_done, K, cudaMemcpyHostToDevice, c->st));
+  CK(c, cudaMemcpyAsync(b->d_snap_eoff, h_eoff, sizeof(long long) * K, cudaMemcpyHostToDevice, c->st));
+  CK(c, launch_batch_snapshot(b->d_snap_done, c->d_seg_off, K, c->d_rp, lam, c->d_ec, c->d_x2, b->d_snap_eoff,
+                              b->d_res_lam, b->d_res_rp, b->d_res_ec, b->d_res_x2, c->st));
   CK(c, cudaStreamSynchronize(c->st));
   return F2M_OK;
 }

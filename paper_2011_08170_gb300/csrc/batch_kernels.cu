@@ -838,4 +838,52 @@ cudaError_t launch_batch_mask_surplus(int32_t* exl, const int32_t* seg_off, int3
   return cudaGetLastError();
 }
 
+
+// Copies the state of the instances flagged in done into the result arenas:
+// one block per instance; lambda, its row offsets (kept absolute, as the
+// caller reads them back relative to the first), and its {col, cost} and x
+// entries to the arena offset eoff[s].
+__global__ void batch_snapshot_kernel(const uint8_t* __restrict__ done, const int32_t* __restrict__ seg_off,
+                                      const int32_t* __restrict__ rp, const int32_t* __restrict__ lam,
+                                      const int2* __restrict__ ec, const uint8_t* __restrict__ x2,
+                                      const long long* __restrict__ eoff, int32_t* res_lam, int32_t* res_rp,
+                                      int2* res_ec, uint8_t* res_x2) {
+  const int s = blockIdx.x;
+  if (!done[s]) return;
+  const int v0 = seg_off[s], ns = seg_off[s + 1] - v0;
+  const int e0 = rp[v0], nz = rp[v0 + ns] - e0;
+  const long long o = eoff[s];
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) res_lam[v0 + i] = lam[v0 + i];
+  for (int i = threadIdx.x; i <= ns; i += blockDim.x) res_rp[v0 + s + i] = rp[v0 + i];
+  for (int i = threadIdx.x; i < nz; i += blockDim.x) {
+    res_ec[o + i] = ec[e0 + i];
+    res_x2[o + i] = x2[e0 + i];
+  }
+}
+
+cudaError_t launch_batch_snapshot(const uint8_t* done, const int32_t* seg_off, int32_t nseg, const int32_t* rp,
+                                  const int32_t* lam, const int2* ec, const uint8_t* x2, const long long* eoff,
+                                  int32_t* res_lam, int32_t* res_rp, int2* res_ec, uint8_t* res_x2,
+                                  cudaStream_t st) {
+  if (nseg <= 0) return cudaSuccess;
+  batch_snapshot_kernel<<<nseg, 256, 0, st>>>(done, seg_off, rp, lam, ec, x2, eoff, res_lam, res_rp, res_ec,
+                                              res_x2);
+  count_launch();
+  return cudaGetLastError();
+}
+
+
+// out[s] = rp[seg_off[s]] for s = 0..nseg: the first entry of every instance
+__global__ void batch_seg_entry_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ seg_off,
+                                       int32_t nseg, int32_t* out) {
+  F2M_GRID_STRIDE(s, nseg + 1) out[s] = rp[seg_off[s]];
+}
+
+cudaError_t launch_batch_seg_entry(const int32_t* rp, const int32_t* seg_off, int32_t nseg, int32_t* out,
+                                   cudaStream_t st) {
+  batch_seg_entry_kernel<<<grid_for(nseg + 1, 256), 256, 0, st>>>(rp, seg_off, nseg, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace f2m

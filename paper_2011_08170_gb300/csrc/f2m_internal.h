@@ -332,6 +332,14 @@ cudaError_t launch_batch_union(const int32_t* rp_local, const int32_t* col_local
                                cudaStream_t st);
 cudaError_t launch_batch_mask_surplus(int32_t* exl, const int32_t* seg_off, int32_t nseg,
                                       const uint8_t* include, int32_t n, cudaStream_t st);
+// out[s] = rp[seg_off[s]], s = 0..nseg
+cudaError_t launch_batch_seg_entry(const int32_t* rp, const int32_t* seg_off, int32_t nseg, int32_t* out,
+                                   cudaStream_t st);
+// results of the instances flagged in done (device mask) into the arenas, entries at eoff[s]
+cudaError_t launch_batch_snapshot(const uint8_t* done, const int32_t* seg_off, int32_t nseg, const int32_t* rp,
+                                  const int32_t* lam, const int2* ec, const uint8_t* x2, const long long* eoff,
+                                  int32_t* res_lam, int32_t* res_rp, int2* res_ec, uint8_t* res_x2,
+                                  cudaStream_t st);
 
 struct FinisherWork;
 FinisherWork* finisher_work_new();
