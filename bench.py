@@ -325,6 +325,9 @@ def main():
                     help="1: full scan of all pairs (the headline); 2: the scan with far tile pairs skipped")
     ap.add_argument("--batch-shape", type=int, default=-1,
                     help="batch workloads: fixed kernel shape instead of the autotuner's")
+    ap.add_argument("--finisher", default="host", choices=["host", "gpu"],
+                    help="where the finisher's first phase runs (the host threads by default, one warp "
+                         "per block of 2,048 nodes on the GPU)")
     ap.add_argument("--batch-clusters", action="store_true",
                     help="batch workloads: one thread-block cluster per instance instead of the streaming kernels")
     ap.add_argument("--update", default="jacobi", choices=["jacobi", "classes"],
@@ -412,7 +415,8 @@ def single_line(args, wname, w, rank, world, local, dist, f2m, torch, nested=Fal
         return c
 
     # warm-up solves (also load the module, JIT nothing)
-    params = f2m.f2m_default_params(pricing=args.pricing, flags=flags, damping_shift=args.shift)
+    params = f2m.f2m_default_params(pricing=args.pricing, flags=flags | finisher_flag(f2m, args),
+                                    damping_shift=args.shift)
     if args.max_iters:
         params.max_iters = args.max_iters
     for _ in range(args.warmup):
@@ -552,6 +556,7 @@ def single_line(args, wname, w, rank, world, local, dist, f2m, torch, nested=Fal
                 "ms_phase": [statistics.median(i["ms_finish_phase"][k] for i in infos) for k in range(3)],
                 "ms_scatter": statistics.median(i["ms_finish_scatter"] for i in infos),
                 "aug_phase": inf0["finish_aug_phase"], "threads": inf0["finish_threads"],
+                "phase1_gpu": inf0["finish_phase1_gpu"],
                 "ms_prep_per_step": [round(i["ms_finish_prep"], 3) for i in infos]},
             "sweep_edges_per_s": iters * nnz0 / (ms_gdp * 1e-3),
             "wall_ms_timed_region": wall_ms,
@@ -595,7 +600,8 @@ def run_batch(args, w, rank, world, local):
         specs = specs[:args.instances]
     ds = [I.make_instance(*sp) for sp in specs]
     params = f2m.f2m_default_params(batch_shape=args.batch_shape, pricing=args.pricing,
-                                    flags=f2m.F2M_FLAG_BATCH_CLUSTERS if args.batch_clusters else 0)
+                                    flags=(f2m.F2M_FLAG_BATCH_CLUSTERS if args.batch_clusters else 0) |
+                                    finisher_flag(f2m, args))
     if args.max_iters:
         params.max_iters = args.max_iters
     insts = [(d["xy"], d["row_ptr"], d["col"]) for d in ds]
@@ -684,6 +690,11 @@ def run_batch(args, w, rank, world, local):
                        "parallelism": f"replicas x{world}"},
             "breakdown_ms": {k: statistics.median(getattr(r[1], k) for r in res)
                              for k in ("ms_gdp", "ms_pricing", "ms_merge", "ms_extract", "ms_finish", "ms_total")},
+            "finisher_split": {
+                "ms_prep": statistics.median(r[1].ms_finish_prep for r in res),
+                "ms_phase": [statistics.median(r[1].ms_finish_phase[k] for r in res) for k in range(3)],
+                "ms_scatter": statistics.median(r[1].ms_finish_scatter for r in res),
+                "aug_phase": list(tot.finish_aug_phase), "phase1_gpu": int(tot.finish_phase1_gpu)},
             "solve": {"sweeps_total": int(sweeps.sum()), "sweeps_max": int(sweeps.max()),
                       "phases": int(tot.phases), "pricing_scans": int(tot.pricing_rounds),
                       "edges_added": int(tot.edges_added), "finisher_calls": int(tot.finisher_calls),
@@ -796,6 +807,10 @@ def run_warm(args, w, rank, world, local):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def finisher_flag(f2m, args):
+    return {"host": 0, "gpu": f2m.F2M_FLAG_FINISHER_GPU}[args.finisher]
 
 
 def load_traffic(workload):

@@ -127,6 +127,16 @@ typedef struct {
  * kernels.  Same results either way. */
 #define F2M_FLAG_BATCH_CLUSTERS 8u
 
+/* f2m_params.flags: where the finisher's first phase (successive shortest
+ * paths block by block, 2,048 nodes a block) runs.  By default (or with
+ * F2M_FLAG_FINISHER_HOST) it runs on the host threads; F2M_FLAG_FINISHER_GPU
+ * runs it on the GPU, one warp per block.  The same searches run in the same
+ * order either way, so the results are identical; the searches are sequential
+ * within a block, and one warp per block is slower than a host thread per
+ * block at the sizes measured, so the host is the default. */
+#define F2M_FLAG_FINISHER_HOST 16u
+#define F2M_FLAG_FINISHER_GPU 32u
+
 typedef struct {
   int64_t iterations;           /* GDP sweeps, all phases */
   int64_t phases;               /* GDP phases */
@@ -157,7 +167,7 @@ typedef struct {
   double ms_finish_scatter;
   int64_t finish_aug_phase[3];
   int32_t finish_threads;       /* host threads the blocked phases used */
-  int32_t pad_info;
+  int32_t finish_phase1_gpu;    /* 1 if the finisher's phase 1 ran on the GPU */
 } f2m_info;
 
 /* f2m_info.gdp_kernel values */

@@ -34,6 +34,8 @@ F2M_FLAG_STREAMING_GDP = 1
 F2M_FLAG_ONE_SWEEP_GDP = 2
 F2M_FLAG_CLASS_SWEEPS = 4
 F2M_FLAG_BATCH_CLUSTERS = 8
+F2M_FLAG_FINISHER_HOST = 16
+F2M_FLAG_FINISHER_GPU = 32
 F2M_GDP_KERNEL_STREAMING, F2M_GDP_KERNEL_TILED, F2M_GDP_KERNEL_TWO_SWEEP = 0, 1, 2
 F2M_GDP_KERNEL_TWO_SWEEP_PACKED, F2M_GDP_KERNEL_CLASSES = 3, 4
 F2M_GDP_KERNEL_BATCH, F2M_GDP_KERNEL_BATCH_CLUSTERS = 5, 6
@@ -79,14 +81,13 @@ class f2m_info(C.Structure):
                 ("ms_extract", C.c_double), ("ms_finish", C.c_double), ("ms_total", C.c_double),
                 ("ms_finish_prep", C.c_double), ("ms_finish_phase", C.c_double * 3),
                 ("ms_finish_scatter", C.c_double), ("finish_aug_phase", C.c_int64 * 3),
-                ("finish_threads", C.c_int32), ("pad_info", C.c_int32)]
+                ("finish_threads", C.c_int32), ("finish_phase1_gpu", C.c_int32)]
 
     def as_dict(self) -> dict:
         d = {}
         for k, _ in self._fields_:
             v = getattr(self, k)
             d[k] = list(v) if hasattr(v, "__len__") else v
-        d.pop("pad_info")
         return d
 
 

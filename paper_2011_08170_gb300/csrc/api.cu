@@ -179,6 +179,15 @@ void dev_free_synced(void* p) {
 static void free_finisher_buffers(f2m_ctx* c) {
   dev_free(c->d_twin);
   dev_free(c->d_fy);
+  dfree(c->d_fpi); dfree(c->d_fdist); dfree(c->d_fex); dfree(c->d_fvia); dfree(c->d_fpred);
+  dfree(c->d_freach); dfree(c->d_fclos); dfree(c->d_forder); dfree(c->d_fstat); dfree(c->d_fblk);
+  dfree(c->d_fcaps); dfree(c->d_fheap_off); dfree(c->d_fpush); dfree(c->d_fheap);
+  pin_free(c->h_fpi);
+  pin_free(c->h_fex);
+  c->h_fpi = nullptr;
+  c->h_fex = nullptr;
+  c->fblk_cap = 0;
+  c->fheap_cap = 0;
   void* hp[] = {c->h_irp, c->h_iec, c->h_twin, c->h_y, c->h_exl, c->h_lam, c->h_lam2};
   for (void* q : hp) pin_free(q);
   c->d_twin = nullptr; c->d_fy = nullptr;
@@ -936,9 +945,76 @@ f2m_status f2m::bound_internal(f2m_ctx* c, int64_t* b2) {
   return F2M_OK;
 }
 
+// Phase 1 of the finisher on the GPU for the given blocks (internal node
+// ranges): the state it leaves is in d_fy (flow), d_fpi and d_fex.
+static f2m_status fin_gpu_phase1(f2m_ctx* c, const std::vector<int2>& fblocks, const int32_t* d_exl,
+                                 const int32_t* d_lam_int, const unsigned long long* missing,
+                                 int64_t* pushes_out) {
+  const int32_t n = c->n;
+  const int32_t nb = (int32_t)fblocks.size();
+  GdpPlan& P = c->plan;
+  if (!c->d_fpi) {  // node-sized state, both copies of every node
+    CK(c, dalloc(&c->d_fpi, 2LL * n));
+    CK(c, dalloc(&c->d_fdist, 2LL * n));
+    CK(c, dalloc(&c->d_fex, 2LL * n));
+    CK(c, dalloc(&c->d_fvia, 2LL * n));
+    CK(c, dalloc(&c->d_fpred, 2LL * n));
+    CK(c, dalloc(&c->d_freach, 2LL * n));
+    CK(c, dalloc(&c->d_fclos, 2LL * n));
+    CK(c, dalloc(&c->d_forder, 2LL * n));
+    CK(c, dalloc(&c->d_fstat, 1));
+    CK(c, pin_alloc((void**)&c->h_fpi, sizeof(int64_t) * 2 * (size_t)n));
+    CK(c, pin_alloc((void**)&c->h_fex, sizeof(int32_t) * 2 * (size_t)n));
+  }
+  if (nb > c->fblk_cap) {
+    dfree(c->d_fblk);
+    dfree(c->d_fcaps);
+    dfree(c->d_fheap_off);
+    dfree(c->d_fpush);
+    c->fblk_cap = nb + nb / 4 + 16;
+    CK(c, dalloc(&c->d_fblk, c->fblk_cap));
+    CK(c, dalloc(&c->d_fcaps, c->fblk_cap));
+    CK(c, dalloc(&c->d_fheap_off, c->fblk_cap + 1));
+    CK(c, dalloc(&c->d_fpush, c->fblk_cap));
+  }
+  CK(c, cudaMemcpyAsync(c->d_fblk, fblocks.data(), sizeof(int2) * nb, cudaMemcpyHostToDevice, c->st));
+  CK(c, launch_fin_block_caps(c->d_fblk, nb, P.irp, c->d_fcaps, c->st));
+  std::vector<long long> caps(nb), off(nb + 1, 0);
+  CK(c, cudaMemcpyAsync(caps.data(), c->d_fcaps, sizeof(long long) * nb, cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  // every twin entry must exist before the kernel follows them
+  if (*missing) return fail(c, F2M_ERR_INVALID_ARG, "finisher: CSR not symmetric");
+  for (int32_t k = 0; k < nb; ++k) off[k + 1] = off[k] + caps[k];
+  const size_t item = fin_heap_item_bytes();
+  if ((int64_t)off[nb] > c->fheap_cap) {
+    dfree(c->d_fheap);
+    c->fheap_cap = off[nb] + off[nb] / 4 + 1024;
+    CK(c, dalloc(&c->d_fheap, (int64_t)(c->fheap_cap * item)));
+  }
+  CK(c, cudaMemcpyAsync(c->d_fheap_off, off.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice, c->st));
+  CK(c, cudaMemsetAsync(c->d_fstat, 0, sizeof(int32_t), c->st));
+  CK(c, launch_fin_blocks(n, c->d_fblk, nb, P.irp, P.iec, c->d_twin, c->d_fy, d_exl, d_lam_int, c->p.frac_bits,
+                          c->d_fpi, c->d_fdist, c->d_fex, c->d_fvia, c->d_fpred, c->d_freach, c->d_fclos,
+                          c->d_fheap, c->d_fheap_off, c->d_forder, c->d_fpush, c->d_fstat,
+                          4 * c->p.barrier_budget_cycles, c->st));
+  std::vector<long long> pushes(nb);
+  int32_t stat = 0;
+  CK(c, cudaMemcpyAsync(pushes.data(), c->d_fpush, sizeof(long long) * nb, cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaMemcpyAsync(&stat, c->d_fstat, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  if (stat) return fail(c, F2M_ERR_TIMEOUT, "finisher phase 1 on the GPU ran past its budget or its heap");
+  int64_t tot = 0;
+  for (long long q : pushes) tot += q;
+  *pushes_out = tot;
+  c->fin_stats.aug[0] += tot;
+  c->fin_stats.phase1_gpu = 1;
+  return F2M_OK;
+}
+
 // Exact finisher: device prep (twin arcs, initial flow, surpluses) on the
-// renumbered CSR, successive shortest paths on the host, results scattered back
-// to caller order on the device.
+// renumbered CSR, successive shortest paths on the host (phase 1 on the GPU
+// with F2M_FLAG_FINISHER_GPU), results scattered back to caller order on the
+// device.
 f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug, const uint8_t* h_include) {
   using clk = std::chrono::steady_clock;
   const auto t_prep = clk::now();
@@ -962,6 +1038,26 @@ f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug, const uint8_t* h_inc
   CK(c, fin_prepare(P, c->d_lam[c->cur], c->d_b, F, d_lam_int, c->d_fy, d_exl, c->st));
   if (c->d_fin_include)
     CK(c, launch_batch_mask_surplus(d_exl, c->d_seg_off, nseg, c->d_fin_include, n, c->st));
+  // phase 1 of the successive shortest paths on the GPU, one warp per block,
+  // when the flags ask for it: it leaves the flow, potentials and surpluses of
+  // the host's phase 1, and the host goes on with phases 2 and 3
+  std::vector<int2> fblocks;
+  for (int32_t sg = 0; sg < nseg; ++sg) {
+    if (h_include && !h_include[sg]) continue;
+    for (int32_t b0 = c->seg_off[sg]; b0 < c->seg_off[sg + 1]; b0 += kFinBlockNodes)
+      fblocks.push_back(make_int2(b0, std::min(b0 + kFinBlockNodes, c->seg_off[sg + 1])));
+  }
+  const uint32_t fl = c->p.flags;
+  const bool gpu1 = !fblocks.empty() && !(fl & F2M_FLAG_FINISHER_HOST) && (fl & F2M_FLAG_FINISHER_GPU);
+  int64_t gpu_pushes = 0;
+  double ms_gpu1 = 0;  // wall time of phase 1 on the GPU: phase 1's, not prep's
+  if (gpu1) {
+    const auto t1 = clk::now();
+    const f2m_status s1 = fin_gpu_phase1(c, fblocks, d_exl, d_lam_int, &missing, &gpu_pushes);
+    if (s1 != F2M_OK) return s1;
+    ms_gpu1 = std::chrono::duration<double, std::milli>(clk::now() - t1).count();
+    c->fin_stats.ms_phase[0] += ms_gpu1;
+  }
   // the host copy of the graph: whole (cached per graph version), or, when a
   // batch names the instances the finisher works on, just theirs (node and
   // entry ranges of segments are contiguous in the internal order); the others
@@ -1007,16 +1103,28 @@ f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug, const uint8_t* h_inc
     ranges.push_back(make_int2(0, (int32_t)c->nnz));
     nranges.push_back(make_int2(0, n));
   }
+  if (gpu1) {  // phase 1's potentials and surpluses, both copies of the nodes worked on
+    for (const int2& v : nranges) {
+      const size_t nv = (size_t)(v.y - v.x);
+      CK(c, cudaMemcpyAsync(c->h_fpi + v.x, c->d_fpi + v.x, sizeof(int64_t) * nv, cudaMemcpyDeviceToHost, c->st));
+      CK(c, cudaMemcpyAsync(c->h_fpi + n + v.x, c->d_fpi + n + v.x, sizeof(int64_t) * nv, cudaMemcpyDeviceToHost,
+                            c->st));
+      CK(c, cudaMemcpyAsync(c->h_fex + v.x, c->d_fex + v.x, sizeof(int32_t) * nv, cudaMemcpyDeviceToHost, c->st));
+      CK(c, cudaMemcpyAsync(c->h_fex + n + v.x, c->d_fex + n + v.x, sizeof(int32_t) * nv, cudaMemcpyDeviceToHost,
+                            c->st));
+    }
+  }
   CK(c, cudaStreamSynchronize(c->st));
   if (twin_new) {
     if (missing) return fail(c, F2M_ERR_INVALID_ARG, "finisher: CSR not symmetric");
     c->twin_version = P.version;
   }
-  c->fin_stats.ms_prep += std::chrono::duration<double, std::milli>(clk::now() - t_prep).count();
+  c->fin_stats.ms_prep += std::chrono::duration<double, std::milli>(clk::now() - t_prep).count() - ms_gpu1;
   static const int32_t hw = (int32_t)std::thread::hardware_concurrency();
   const int r = host_finisher(n, c->h_irp, c->h_iec, c->h_twin, c->h_y, c->h_exl, c->h_lam, F,
                               c->h_lam2, c->seg_off.data(), nseg, h_include, hw > 1 ? hw : 1, aug,
-                              c->fin_work, &c->fin_stats);
+                              c->fin_work, &c->fin_stats, gpu1 ? c->h_fpi : nullptr, gpu1 ? c->h_fex : nullptr);
+  *aug += gpu_pushes;
   const auto t_scatter = clk::now();
   if (r == 7)
     return fail(c, F2M_ERR_INFEASIBLE, c->d_b ? "no fractional b-matching exists on the candidate graph"
@@ -1039,6 +1147,7 @@ f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug, const uint8_t* h_inc
 
 void f2m::copy_finisher_stats(const f2m_ctx* c, f2m_info* info) {
   const FinisherStats& f = c->fin_stats;
+  info->finish_phase1_gpu = f.phase1_gpu;
   info->ms_finish_prep = f.ms_prep;
   info->ms_finish_scatter = f.ms_scatter;
   for (int k = 0; k < 3; ++k) {

@@ -95,6 +95,24 @@ struct f2m_ctx {
   int32_t* h_lam = nullptr;
   int32_t* h_lam2 = nullptr;
   f2m::FinisherWork* fin_work = nullptr;
+  // the finisher's phase 1 on the GPU: node state of both copies, blocks, heaps
+  long long* d_fpi = nullptr;
+  long long* d_fdist = nullptr;
+  int32_t* d_fex = nullptr;
+  int32_t* d_fvia = nullptr;
+  int32_t* d_fpred = nullptr;
+  uint32_t* d_freach = nullptr;
+  uint32_t* d_fclos = nullptr;
+  int32_t* d_forder = nullptr;
+  int32_t* d_fstat = nullptr;
+  int2* d_fblk = nullptr;
+  long long* d_fcaps = nullptr;
+  long long* d_fheap_off = nullptr;
+  long long* d_fpush = nullptr;
+  uint8_t* d_fheap = nullptr;
+  int64_t fblk_cap = 0, fheap_cap = 0;  // blocks, heap items
+  int64_t* h_fpi = nullptr;             // pinned copies of the phase-1 state for the host
+  int32_t* h_fex = nullptr;
   f2m::FinisherStats fin_stats;  // the finisher's split, summed since the solve began
   f2m::CutState* cuts = nullptr;  // layers of subtour-elimination cuts and their duals
   std::string err;

@@ -356,11 +356,27 @@ struct FinisherStats {
   double ms_prep = 0, ms_phase[3] = {0, 0, 0}, ms_scatter = 0;
   int64_t aug[3] = {0, 0, 0};
   int32_t threads = 0;
+  int32_t phase1_gpu = 0;  // 1 if phase 1 ran on the GPU
 };
+// ext_pi / ext_ex (NULL: none): potentials [2n] and surpluses [2n] that phase
+// 1 left when it ran on the GPU; the host then runs phases 2 and 3 only (the
+// augmentations it reports are its own)
 int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t* twin, uint8_t* y,
                   const int32_t* exl, const int32_t* lam, int32_t F, int32_t* lam2,
                   const int32_t* seg_off, int32_t nseg, const uint8_t* include, int32_t threads,
-                  int64_t* augmentations, FinisherWork* w, FinisherStats* stats);
+                  int64_t* augmentations, FinisherWork* w, FinisherStats* stats, int64_t* ext_pi = nullptr,
+                  int32_t* ext_ex = nullptr);
+// the finisher's phase 1 on the GPU (finisher_gpu.cu): one warp per block
+size_t fin_heap_item_bytes();
+cudaError_t launch_fin_block_caps(const int2* blocks, int32_t nblocks, const int32_t* irp, long long* caps,
+                                  cudaStream_t st);
+cudaError_t launch_fin_blocks(int32_t n, const int2* blocks, int32_t nblocks, const int32_t* irp, const int2* iec,
+                              const int32_t* twin, uint8_t* y, const int32_t* exl, const int32_t* lam, int32_t F,
+                              long long* pi, long long* dist, int32_t* excess, int32_t* via, int32_t* pred,
+                              uint32_t* reached, uint32_t* closed, void* heaps, const long long* heap_off,
+                              int32_t* orders, long long* pushes, int32_t* status, long long budget,
+                              cudaStream_t st);
+constexpr int32_t kFinBlockNodes = 2048;  // nodes per block of the finisher's phase 1 (host and GPU)
 // lam_out = 2 * lam_in (F bits -> F+1 bits)
 cudaError_t launch_double(const int32_t* lam_in, int32_t* lam_out, int32_t n, cudaStream_t st);
 

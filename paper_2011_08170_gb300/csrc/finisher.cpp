@@ -96,7 +96,7 @@ struct Searcher {
   }
 };
 
-constexpr int32_t kFinBlock = 2048;    // nodes per phase-1 block
+constexpr int32_t kFinBlock = kFinBlockNodes;  // nodes per phase-1 block
 constexpr int32_t kFinBlock2 = 16384;  // nodes per phase-2 block
 
 // Worker threads kept for the life of the process (one pool, shared by every
@@ -158,6 +158,8 @@ struct WorkerPool {
 };
 
 struct FinisherWork {
+  int64_t* pi_p = nullptr;    // the potentials in use: pi.data(), or the caller's
+  int32_t* ex_p = nullptr;    // the surpluses in use: excess.data(), or the caller's
   std::vector<int64_t> pi, dist;
   std::vector<int64_t> pi_start;  // potentials at phase 2's start (outside nodes are priced with them)
   std::vector<int32_t> excess, via, pred;
@@ -201,9 +203,9 @@ namespace {
 int solve_range(int32_t n, int32_t lo, int32_t hi, const int32_t* lam0, const int64_t* pi0v,
                 const int32_t* irp, const int2* iec, const int32_t* twin, uint8_t* y, int32_t F,
                 FinisherWork* w, Searcher& sr, int64_t* pushes_out) {
-  int64_t* pi = w->pi.data();
+  int64_t* pi = w->pi_p;
   int64_t* dist = w->dist.data();
-  int32_t* excess = w->excess.data();
+  int32_t* excess = w->ex_p;
   int32_t* via = w->via.data();
   int32_t* pred = w->pred.data();
   uint32_t* reached = w->reached.data();
@@ -322,7 +324,8 @@ int run_items(int32_t count, int32_t threads, FinisherWork* w, std::vector<int64
 int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t* twin, uint8_t* y,
                   const int32_t* exl, const int32_t* lam, int32_t F, int32_t* lam2,
                   const int32_t* seg_off, int32_t nseg, const uint8_t* include, int32_t threads,
-                  int64_t* augmentations, FinisherWork* w, FinisherStats* stats) {
+                  int64_t* augmentations, FinisherWork* w, FinisherStats* stats, int64_t* ext_pi,
+                  int32_t* ext_ex) {
   using clk = std::chrono::steady_clock;
   auto ms_since = [](clk::time_point t) { return std::chrono::duration<double, std::milli>(clk::now() - t).count(); };
   auto pushes_total = [](const std::vector<int64_t>& v) {
@@ -336,8 +339,13 @@ int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t*
     std::fill(w->closed.begin(), w->closed.end(), 0u);
     w->stamp.store(0);
   }
-  int64_t* pi = w->pi.data();
-  int32_t* excess = w->excess.data();
+  // ext_pi / ext_ex: potentials and surpluses left by phase 1 run elsewhere
+  // (the GPU); the host then starts at phase 2
+  w->pi_p = ext_pi ? ext_pi : w->pi.data();
+  w->ex_p = ext_ex ? ext_ex : w->excess.data();
+  const bool skip1 = ext_pi && ext_ex;
+  int64_t* pi = w->pi_p;
+  int32_t* excess = w->ex_p;
   // phase 1: blocks of every segment, each first setting its own nodes'
   // potentials (lam, -lam) and surpluses; phase 2: larger blocks, from a copy
   // of the potentials phase 1 left; phase 3: whole segments
@@ -353,7 +361,7 @@ int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t*
   }
   std::vector<int64_t> pushes;
   auto t0 = clk::now();
-  int r = run_items((int32_t)blocks.size(), threads, w, pushes,
+  int r = skip1 ? 0 : run_items((int32_t)blocks.size(), threads, w, pushes,
                     [&](int32_t k, Searcher& sr, int64_t* p) {
                       for (int32_t i = blocks[k].x; i < blocks[k].y; ++i) {
                         pi[i] = lam[i];
@@ -365,7 +373,7 @@ int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t*
                                          sr, p);
                     });
   int64_t done1 = pushes_total(pushes);
-  if (stats) {
+  if (stats && !skip1) {
     stats->ms_phase[0] += ms_since(t0);
     stats->aug[0] += done1;
     stats->threads = std::max<int32_t>(stats->threads, std::min<int32_t>(threads, (int32_t)blocks.size()));
