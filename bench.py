@@ -9,7 +9,7 @@ dominant kernel (the pricing scan's FP32 rate or the GDP sweep's GB/s).
     python bench.py --degrees 1:4                # fractional b-matching, b_v in 1..4 (variant)
 
 A step is one full f2m_solve from lambda = 0 on a fresh context: GDP phases
-(256 sweeps at most each, by default), pricing scans over all n(n-1)/2 pairs,
+(128 sweeps at most each, by default), pricing scans over all n(n-1)/2 pairs,
 CSR merges, sign extraction and the exact finisher, until the solution is
 certified optimal for the complete graph.  Contexts are created before the timed region; L2 is flushed (a 256 MB
 device write) before every timed step.  Each step is bracketed by CUDA events
@@ -203,7 +203,7 @@ def run_reference(args, w, rank):
     import instances as I
     import oracle
     oracle.build()
-    mi = args.max_iters or 256  # the oracle's default, the library's too
+    mi = args.max_iters or 128  # the oracle's default, the library's too
     if w["kind"] in ("batch", "warm"):
         return run_reference_multi(args, w, mi)
     d = I.make_instance(w["kind"], w["n"], w["seed"], w["k"])
@@ -293,14 +293,14 @@ def run_reference_multi(args, w, mi):
 
 
 # Sweep and pricing-round counts of the certified solve of each workload, at
-# 256 sweeps per GDP phase (the oracle's own counts, recorded with its solve in
+# 128 sweeps per GDP phase (the oracle's own counts, recorded with its solve in
 # tests/golden/full_size_solves.json) and with every phase run to its fixed
 # point.  They only scale the CPU reference arm's bounded samples (a full
 # oracle solve at n = 1e5 takes a minute or more).  c1 is small enough for the
 # oracle to solve outright.
 REFERENCE_COUNTS: dict = {
-    ("c2", 256): {"iterations": 256, "pricing_rounds": 2},
-    ("c3", 256): {"iterations": 256, "pricing_rounds": 2},
+    ("c2", 128): {"iterations": 128, "pricing_rounds": 2},
+    ("c3", 128): {"iterations": 128, "pricing_rounds": 2},
     ("c2", "fixed point"): {"iterations": 3064, "pricing_rounds": 2},
     ("c3", "fixed point"): {"iterations": 3169, "pricing_rounds": 2},
 }
@@ -323,6 +323,8 @@ def main():
                     help="batch workloads: solve only the first N instances (profiling)")
     ap.add_argument("--pricing", type=int, default=1, choices=[1, 2],
                     help="1: full scan of all pairs (the headline); 2: the scan with far tile pairs skipped")
+    ap.add_argument("--pricing-tensor", action="store_true",
+                    help="full scan with the tensor-core filter instead of the fp32 filter on the CUDA cores")
     ap.add_argument("--batch-shape", type=int, default=-1,
                     help="batch workloads: fixed kernel shape instead of the autotuner's")
     ap.add_argument("--finisher", default="host", choices=["host", "gpu"],
@@ -334,7 +336,7 @@ def main():
                     help="single instance: Jacobi sweeps (Section 5.1, the headline) or class-by-class sweeps")
     ap.add_argument("--shift", type=int, default=2, help="damping shift of the GDP step")
     ap.add_argument("--max-iters", type=int, default=None,
-                    help="sweeps per GDP phase (default: the library's, 256); 1000000 runs every phase "
+                    help="sweeps per GDP phase (default: the library's, 128); 1000000 runs every phase "
                          "to its fixed point")
     ap.add_argument("--degrees", default=None,
                     help="single instance: degree requirements b_v drawn uniformly from LO:HI (capped at "
@@ -810,7 +812,8 @@ def run_warm(args, w, rank, world, local):
 
 
 def finisher_flag(f2m, args):
-    return {"host": 0, "gpu": f2m.F2M_FLAG_FINISHER_GPU}[args.finisher]
+    fl = {"host": 0, "gpu": f2m.F2M_FLAG_FINISHER_GPU}[args.finisher]
+    return fl | (f2m.F2M_FLAG_PRICING_TENSOR if args.pricing_tensor else 0)
 
 
 def load_traffic(workload):

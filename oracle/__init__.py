@@ -335,7 +335,7 @@ class OracleResult:
         return self.bound2 / (2.0 * (1 << self.frac_bits))
 
 
-def solve(xy, row_ptr, col, lam0=None, F=8, shift=2, max_iters=256, max_pricing_rounds=64,
+def solve(xy, row_ptr, col, lam0=None, F=8, shift=2, max_iters=128, max_pricing_rounds=64,
           pricing=True, finisher=True, trace_cap=0, b=None, classes=False) -> OracleResult:
     """max_iters: sweeps per GDP phase (a phase also ends at a fixed point; the
     solve goes on from the lambda reached either way).  classes: class-by-class
@@ -518,7 +518,7 @@ class SubtourResult:
     cuts: "Cuts"
 
 
-def solve_subtour(xy, row_ptr, col, rounds=3, lam0=None, F=8, shift=2, max_iters=256, pricing=True,
+def solve_subtour(xy, row_ptr, col, rounds=3, lam0=None, F=8, shift=2, max_iters=128, pricing=True,
                   max_pricing_rounds=64) -> SubtourResult:
     """Stages of GDP with pricing and subtour-cut layers between them (subtour.c)."""
     xy, row_ptr, col = _i32(xy), _i32(row_ptr), _i32(col)

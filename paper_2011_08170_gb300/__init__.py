@@ -36,6 +36,7 @@ F2M_FLAG_CLASS_SWEEPS = 4
 F2M_FLAG_BATCH_CLUSTERS = 8
 F2M_FLAG_FINISHER_HOST = 16
 F2M_FLAG_FINISHER_GPU = 32
+F2M_FLAG_PRICING_TENSOR = 64
 F2M_GDP_KERNEL_STREAMING, F2M_GDP_KERNEL_TILED, F2M_GDP_KERNEL_TWO_SWEEP = 0, 1, 2
 F2M_GDP_KERNEL_TWO_SWEEP_PACKED, F2M_GDP_KERNEL_CLASSES = 3, 4
 F2M_GDP_KERNEL_BATCH, F2M_GDP_KERNEL_BATCH_CLUSTERS = 5, 6
@@ -50,7 +51,7 @@ EXPORTS = ["f2m_default_params", "f2m_create", "f2m_destroy", "f2m_set_lambda", 
            "f2m_mlp_get_params", "f2m_mlp_last_error", "f2m_mlp_forward", "f2m_mlp_grad",
            "f2m_mlp_train", "f2m_warm_start", "f2m_set_degrees", "f2m_get_colors",
            "f2m_tsplib_parse", "f2m_tsplib_last_error", "f2m_separate", "f2m_add_cut_layer",
-           "f2m_get_cut_duals", "f2m_solve_subtour"]
+           "f2m_get_cut_duals", "f2m_solve_subtour", "f2m_pricing_mma_check"]
 
 F2M_MLP_NPARAMS = 18817
 
@@ -183,6 +184,7 @@ def load(path: str = LIB_PATH):
     L.f2m_solve_subtour.argtypes = [vp, i32, C.POINTER(f2m_subtour_info)]
     for name in ("f2m_separate", "f2m_add_cut_layer", "f2m_get_cut_duals", "f2m_solve_subtour"):
         getattr(L, name).restype = C.c_int
+    L.f2m_pricing_mma_check.argtypes = [i64, C.c_uint64, C.POINTER(i64), C.POINTER(i64)]
     L.f2m_kernel_launches.argtypes = []
     L.f2m_kernel_launches.restype = C.c_int64
     for name in ("f2m_create", "f2m_set_lambda", "f2m_set_degrees", "f2m_get_colors", "f2m_solve", "f2m_gdp", "f2m_price",
@@ -468,6 +470,14 @@ def f2m_status_string(status: int) -> str:
 
 def f2m_last_error(ctx: Ctx | None = None) -> str:
     return load().f2m_last_error(ctx.handle if ctx is not None else None).decode()
+
+
+def f2m_pricing_mma_check(rounds: int, seed: int = 0):
+    """Tensor-core arithmetic check of the pricing filter: (values checked, mismatches)."""
+    L = load()
+    chk, bad = C.c_int64(), C.c_int64()
+    _check(None, L.f2m_pricing_mma_check(int(rounds), int(seed), C.byref(chk), C.byref(bad)))
+    return chk.value, bad.value
 
 
 def f2m_kernel_launches() -> int:

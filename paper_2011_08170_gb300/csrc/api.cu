@@ -255,7 +255,7 @@ extern "C" void f2m_default_params(f2m_params* p) {
   if (!p) return;
   p->frac_bits = 8;
   p->damping_shift = 2;
-  p->max_iters = 256;
+  p->max_iters = 128;
   p->max_pricing_rounds = 64;
   p->pricing = 1;
   p->pricing_cap = 1 << 20;
@@ -294,6 +294,8 @@ extern "C" void f2m_destroy(f2m_ctx* c) {
   dfree(c->d_seg_off); dfree(c->d_fin_include);
   dfree(c->d_lam[0]); dfree(c->d_lam[1]); dfree(c->d_lam2); dfree(c->d_exl); dfree(c->d_gdp);
   dfree(c->d_trace_b2); dfree(c->d_trace_ch); dfree(c->d_pts); dfree(c->d_pairs);
+  dfree(c->d_pts4); dfree(c->d_pstat); dfree(c->d_mranges); dfree(c->d_mtblk); dfree(c->d_mbox);
+  dfree(c->d_mlmax); dfree(c->d_mframes); dfree(c->d_mcand); dfree(c->d_mncand);
   dfree(c->d_ranges); dfree(c->d_boxes); dfree(c->d_smax);
   dfree(c->d_count); dfree(c->d_tile); dfree(c->d_deg); dfree(c->d_tmp_rp); dfree(c->d_new_rp);
   dfree(c->d_block_sums); dfree(c->d_tmp_col); dfree(c->d_out_a); dfree(c->d_out_b);
@@ -709,6 +711,32 @@ static void build_tiles(const f2m_ctx* c, std::vector<int4>& tiles) {
   }
 }
 
+// the tensor-core scan's tile pairs: per scanned segment, i-blocks of
+// kMmaTileI positions from its start, each against j-blocks of kMmaTileJ from
+// the i-block's start (every pair u < v of the segment in exactly one)
+// (tiles {i0, i1, j0, j1}; tblk {i-block, j-block, second j-block or -1};
+// ranges: the blocks of kMmaTileI positions; a j-block pair starts on a block)
+static void build_mma_tiles(const f2m_ctx* c, std::vector<int4>& tiles, std::vector<int4>& tblk,
+                            std::vector<int2>& ranges) {
+  static_assert(kMmaTileJ == kMmaTileI, "a j-block is a block");
+  tiles.clear();
+  tblk.clear();
+  ranges.clear();
+  const int32_t nseg = (int32_t)c->seg_off.size() - 1;
+  for (int32_t s = 0; s < nseg; ++s) {
+    if (!c->seg_scan.empty() && !c->seg_scan[s]) continue;
+    const int32_t a = c->seg_off[s], b = c->seg_off[s + 1];
+    const int32_t base = (int32_t)ranges.size();
+    for (int32_t i0 = a; i0 < b; i0 += kMmaTileI) ranges.push_back(make_int2(i0, std::min(i0 + kMmaTileI, b)));
+    for (int32_t i0 = a; i0 < b; i0 += kMmaTileI)
+      for (int32_t j0 = i0; j0 < b; j0 += kMmaTileJ) {
+        const int32_t jb = base + (j0 - a) / kMmaTileI;
+        tiles.push_back(make_int4(i0, std::min(i0 + kMmaTileI, b), j0, std::min(j0 + kMmaTileJ, b)));
+        tblk.push_back(make_int4(base + (i0 - a) / kMmaTileI, jb, -1, 0));
+      }
+  }
+}
+
 // pricing scan into d_pairs (grown until every pair fits); count in c->npairs,
 // per-segment counts in c->seg_pairs
 f2m_status f2m::price_internal(f2m_ctx* c, double* ms, const int32_t* lam_override) {
@@ -725,17 +753,60 @@ f2m_status f2m::price_internal(f2m_ctx* c, double* ms, const int32_t* lam_overri
   const int32_t* lam = cur_lambda(c, &fb);
   if (lam_override) lam = lam_override;
   const int32_t nseg = (int32_t)c->seg_off.size() - 1;
-  // full scan: points in caller order; culled scan: in the renumbered (Morton)
+  // full scan: with the fp32 filter (caller order), or on the tensor cores
+  // (renumbered order); culled scan: fp32 filter in the renumbered (Morton)
   // order, so that a tile is a compact patch with a small bounding box
   const bool culled = c->p.pricing == 2;
+  const bool mma = !culled && (c->p.flags & F2M_FLAG_PRICING_TENSOR);
+  const int kind = mma ? 1 : 0;
   // the full scan's tile-pair list depends only on the segments scanned: it
   // stays on the device from one scan to the next while they are the same
   std::vector<int4> tiles;
-  const bool reuse = !culled && c->tiles_valid && c->tiles_seg_scan == c->seg_scan &&
+  const bool reuse = !culled && c->tiles_valid && c->tiles_kind == kind && c->tiles_seg_scan == c->seg_scan &&
                      c->tiles_seg_off == c->seg_off;
-  if (!reuse) build_tiles(c, tiles);
+  if (mma && !c->d_pts4) {
+    CK(c, dalloc(&c->d_pts4, c->n));
+    CK(c, dalloc(&c->d_pstat, 1));
+    CK(c, dalloc(&c->d_mncand, 1));
+    c->mcand_cap = std::max<int64_t>(4LL * c->n, 1 << 20);
+    CK(c, dalloc(&c->d_mcand, c->mcand_cap));
+  }
+  if (!reuse) {
+    if (mma) {
+      std::vector<int4> tblk;
+      std::vector<int2> ranges;
+      build_mma_tiles(c, tiles, tblk, ranges);
+      if ((int64_t)ranges.size() > c->mblocks_cap) {
+        dfree(c->d_mranges);
+        dfree(c->d_mbox);
+        dfree(c->d_mlmax);
+        c->mblocks_cap = (int64_t)ranges.size() + 64;
+        CK(c, dalloc(&c->d_mranges, c->mblocks_cap));
+        CK(c, dalloc(&c->d_mbox, c->mblocks_cap));
+        CK(c, dalloc(&c->d_mlmax, c->mblocks_cap));
+      }
+      if ((int64_t)tblk.size() > c->mtiles_cap) {
+        dfree(c->d_mtblk);
+        dfree(c->d_mframes);
+        c->mtiles_cap = (int64_t)tblk.size() + 64;
+        CK(c, dalloc(&c->d_mtblk, c->mtiles_cap));
+        CK(c, dalloc(&c->d_mframes, c->mtiles_cap));
+      }
+      if (!ranges.empty())
+        CK(c, cudaMemcpyAsync(c->d_mranges, ranges.data(), sizeof(int2) * ranges.size(), cudaMemcpyHostToDevice,
+                              c->st));
+      if (!tblk.empty())
+        CK(c, cudaMemcpyAsync(c->d_mtblk, tblk.data(), sizeof(int4) * tblk.size(), cudaMemcpyHostToDevice, c->st));
+      c->mblocks = (int64_t)ranges.size();
+    } else {
+      build_tiles(c, tiles);
+    }
+  }
   CK(c, cudaEventRecord(c->ev0, c->st));
-  CK(c, launch_pricing_prep(c->d_xy, lam, culled ? c->plan.perm : nullptr, c->n, fb, c->d_pts, c->st));
+  if (mma)
+    CK(c, launch_pricing_mma_prep(c->d_xy, lam, c->plan.perm, c->n, c->d_pts4, c->st));
+  else
+    CK(c, launch_pricing_prep(c->d_xy, lam, culled ? c->plan.perm : nullptr, c->n, fb, c->d_pts, c->st));
   if (culled && !tiles.empty()) {
     // A pair (u, v) can have z < 0 only if its distance is below s_u + s_v
     // (the filter's radii, see pricing.cu), so a tile pair whose bounding
@@ -793,6 +864,7 @@ f2m_status f2m::price_internal(f2m_ctx* c, double* ms, const int32_t* lam_overri
     if (!tiles.empty())
       CK(c, cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, c->st));
     c->tiles_valid = !culled;
+    c->tiles_kind = kind;
     c->tiles_seg_scan = c->seg_scan;
     c->tiles_seg_off = c->seg_off;
     c->ntiles = (int64_t)tiles.size();
@@ -802,14 +874,33 @@ f2m_status f2m::price_internal(f2m_ctx* c, double* ms, const int32_t* lam_overri
   for (;;) {
     if (!first) CK(c, cudaEventRecord(c->ev0, c->st));
     first = false;
-    CK(c, launch_pricing_scan(c->d_pts, c->d_xy, lam, c->d_rp, c->d_ec, c->n, fb, c->d_tiles,
-                              (int32_t)ntiles, c->d_pairs, c->pairs_cap, c->d_count, c->d_tile,
-                              c->num_sms, c->st));
+    if (mma)
+      CK(c, launch_pricing_mma_scan(c->d_pts4, c->d_xy, lam, c->d_rp, c->d_ec, fb, c->d_tiles, c->d_mtblk,
+                                    (int32_t)ntiles, c->d_mranges, (int32_t)c->mblocks, c->d_mbox, c->d_mlmax,
+                                    c->d_mframes, c->d_mcand, c->mcand_cap, c->d_mncand, c->d_pairs,
+                                    c->pairs_cap, c->d_count, c->d_tile, c->d_pstat, c->num_sms, c->st));
+    else
+      CK(c, launch_pricing_scan(c->d_pts, c->d_xy, lam, c->d_rp, c->d_ec, c->n, fb, c->d_tiles,
+                                (int32_t)ntiles, c->d_pairs, c->pairs_cap, c->d_count, c->d_tile,
+                                c->num_sms, c->st));
     CK(c, cudaEventRecord(c->ev1, c->st));
     unsigned long long cnt = 0;
+    int32_t pstat = 0;
+    unsigned long long ncand = 0;
     CK(c, cudaMemcpyAsync(&cnt, c->d_count, sizeof(cnt), cudaMemcpyDeviceToHost, c->st));
+    if (mma) {
+      CK(c, cudaMemcpyAsync(&pstat, c->d_pstat, sizeof(pstat), cudaMemcpyDeviceToHost, c->st));
+      CK(c, cudaMemcpyAsync(&ncand, c->d_mncand, sizeof(ncand), cudaMemcpyDeviceToHost, c->st));
+    }
     CK(c, cudaStreamSynchronize(c->st));
     if (ms) *ms += elapsed_ms(c);
+    if (pstat) return fail(c, F2M_ERR_TIMEOUT, "pricing scan: a tensor-core wait ran past its budget");
+    if (mma && (int64_t)ncand > c->mcand_cap) {  // the candidate list overflowed: grow it, scan again
+      dfree(c->d_mcand);
+      c->mcand_cap = (int64_t)ncand + ((int64_t)ncand >> 2) + 1024;
+      CK(c, dalloc(&c->d_mcand, c->mcand_cap));
+      continue;
+    }
     c->npairs = (int64_t)cnt;
     if ((int64_t)cnt <= c->pairs_cap) break;
     dfree(c->d_pairs);
@@ -829,6 +920,24 @@ f2m_status f2m::price_internal(f2m_ctx* c, double* ms, const int32_t* lam_overri
       c->seg_pairs[s] += 1;
     }
   }
+  return F2M_OK;
+}
+
+extern "C" f2m_status f2m_pricing_mma_check(int64_t rounds, uint64_t seed, int64_t* checked,
+                                            int64_t* mismatches) {
+  if (!checked || !mismatches || rounds < 0) return fail(nullptr, F2M_ERR_INVALID_ARG, "bad argument");
+  unsigned long long* d = nullptr;
+  cudaError_t e = dalloc(&d, 3);
+  if (e == cudaSuccess) e = cudaMemset(d, 0, 3 * sizeof(unsigned long long));
+  if (e == cudaSuccess)
+    e = launch_pricing_mma_check(rounds, seed, d, d + 1, reinterpret_cast<int32_t*>(d + 2), nullptr);
+  unsigned long long h[3] = {0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  if (d) dev_free_synced(d);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "f2m_pricing_mma_check");
+  *checked = (int64_t)h[0];
+  *mismatches = (int64_t)h[1];
+  if ((int32_t)h[2]) return fail(nullptr, F2M_ERR_TIMEOUT, "f2m_pricing_mma_check: an mbarrier wait gave up");
   return F2M_OK;
 }
 

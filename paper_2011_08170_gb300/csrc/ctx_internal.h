@@ -26,6 +26,7 @@ struct f2m_ctx {
   int4* d_tiles = nullptr;              // pricing tile-pair list
   int64_t tiles_cap = 0;
   int64_t ntiles = 0;                   // tile pairs in d_tiles
+  int tiles_kind = 0;                   // the list's form: 0 fp32 scan, 1 tensor-core scan
   bool tiles_valid = false;             // d_tiles holds the full scan's list for:
   std::vector<uint8_t> tiles_seg_scan;  //   these scanned segments
   std::vector<int32_t> tiles_seg_off;   //   of these segments
@@ -59,6 +60,17 @@ struct f2m_ctx {
   unsigned long long* d_trace_ch = nullptr;
   int64_t trace_cap = 0;
   float4* d_pts = nullptr;
+  int4* d_pts4 = nullptr;       // tensor-core scan: {x, y, lambda, node} per renumbered position
+  int32_t* d_pstat = nullptr;   // its status word
+  int2* d_mranges = nullptr;    // its 128-point blocks (with the tile list: same segments)
+  int4* d_mtblk = nullptr;      // blocks of each tile pair
+  int4* d_mbox = nullptr;       // per block: bounding box, largest lambda (per scan)
+  int32_t* d_mlmax = nullptr;
+  int4* d_mframes = nullptr;    // per tile pair: the frame (per scan)
+  int64_t mblocks = 0, mblocks_cap = 0, mtiles_cap = 0;
+  int2* d_mcand = nullptr;      // the filter's candidates
+  unsigned long long* d_mncand = nullptr;
+  int64_t mcand_cap = 0;
   int2* d_pairs = nullptr;
   int64_t pairs_cap = 0;
   int64_t npairs = 0;   // pairs held in d_pairs after the last scan

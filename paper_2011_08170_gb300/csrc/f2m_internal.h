@@ -121,6 +121,24 @@ cudaError_t launch_pricing_scan(const float4* pts, const int2* xy, const int32_t
                                 const int2* ec, int32_t n, int32_t fb, const int4* tiles, int32_t ntiles,
                                 int2* pairs, int64_t cap, unsigned long long* count, unsigned int* tile_counter,
                                 int num_sms, cudaStream_t st);
+// the same scan on the tensor cores (pricing.cu): pts4[v] = {x, y, lambda, node
+// perm[v]}; tiles {i0, i1, j0, j1} of at most kMmaTileI x kMmaTileJ positions
+cudaError_t launch_pricing_mma_check(long long rounds, unsigned long long seed, unsigned long long* checked,
+                                     unsigned long long* mismatches, int32_t* status, cudaStream_t st);
+constexpr int kMmaTileI = 128;
+constexpr int kMmaTileJ = 128;
+cudaError_t launch_pricing_mma_prep(const int2* xy, const int32_t* lam, const int32_t* perm, int32_t n,
+                                    int4* pts4, cudaStream_t st);
+// ranges [nblocks]: the 128-point blocks; tblk [ntiles]: each tile pair's
+// blocks {i-block, j-block, second j-block or -1}; box, lmax, frames: scratch;
+// cand [cand_cap]: the filter's candidates (*ncand of them, more than
+// cand_cap when the list overflowed: the scan is then incomplete)
+cudaError_t launch_pricing_mma_scan(const int4* pts4, const int2* xy, const int32_t* lam, const int32_t* rp,
+                                    const int2* ec, int32_t fb, const int4* tiles, const int4* tblk,
+                                    int32_t ntiles, const int2* ranges, int32_t nblocks, int4* box, int32_t* lmax,
+                                    int4* frames, int2* cand, int64_t cand_cap, unsigned long long* ncand,
+                                    int2* pairs, int64_t cap, unsigned long long* count,
+                                    unsigned int* tile_counter, int32_t* status, int num_sms, cudaStream_t st);
 // CSR union with pairs; sizes: see graph.cu.  Returns the new nnz through *new_nnz_dev.
 struct MergeBuffers {
   int32_t* deg;        // [n+1]

@@ -1,5 +1,5 @@
 """Writes full_size_solves.json: the CPU oracle's solves of the full-size
-single-instance workloads, at the default of 256 sweeps per GDP phase.
+single-instance workloads, at the default of 128 sweeps per GDP phase.
 
 Calls only the oracle (and the seeded instance generator).  Two solves per
 instance:
@@ -35,7 +35,7 @@ CASES = {
     "uniform_n100000_k10_seed0": ("uniform", 100_000, 0, 10),
     "mixture_n200000_k12_seed0": ("mixture", 200_000, 0, 12),
 }
-MAX_ITERS = 256
+MAX_ITERS = 128
 OUT = os.path.join(HERE, "full_size_solves.json")
 
 

@@ -47,7 +47,7 @@ def test_binding_names_match_header(lib):
 def test_default_params(lib):
     p = f2m.f2m_default_params()
     assert (p.frac_bits, p.damping_shift, p.pricing, p.finisher) == (8, 2, 1, 1)
-    assert p.max_iters == 256 and p.pricing_cap > 0 and p.barrier_budget_cycles > 0
+    assert p.max_iters == 128 and p.pricing_cap > 0 and p.barrier_budget_cycles > 0
 
 
 def test_status_strings(lib):

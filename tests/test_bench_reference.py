@@ -26,7 +26,7 @@ def test_reference_line(workload):
     assert d["impl"] == "reference" and d["unit"] == "ms" and d["higher_is_better"] is False
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
-    assert d["config"]["max_iters"] == 256
+    assert d["config"]["max_iters"] == 128
     if workload == "c1":  # small enough for the one complete oracle solve
         whole = d["cpu_baseline"]["whole_solve"]
         assert whole["ms"] > 0 and whole["status"] == 0 and whole["certified"] == 2

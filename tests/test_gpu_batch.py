@@ -81,7 +81,7 @@ def test_batch_matches_oracle_optimum(lib, oracle_lib):
     b = f2m.f2m_create_batch([(d["xy"], d["row_ptr"], d["col"]) for d in ds])
     infos, tot = f2m.f2m_solve_batch(b)
     for i, d in enumerate(ds):
-        r = oracle_lib.solve(d["xy"], d["row_ptr"], d["col"])  # both at 256 sweeps per phase
+        r = oracle_lib.solve(d["xy"], d["row_ptr"], d["col"])  # both at 128 sweeps per phase
         fb = infos[i].frac_bits
         assert same_optimum(infos[i].bound2, fb, r.bound2, r.frac_bits)
         assert infos[i].certified == r.certified == 2

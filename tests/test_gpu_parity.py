@@ -255,10 +255,10 @@ def test_solve_bit_exact_with_culled_pricing(lib, O, kind, n, seed, k):
     assert s.info["certified"] == 2
 
 
-# GDP phases cut at max_iters sweeps (tiny, odd, and the default 256): the solve
+# GDP phases cut at max_iters sweeps (tiny, odd, the default 128 and 256): the solve
 # goes on from the lambda reached, bit-exact with the oracle all the way
 @pytest.mark.parametrize("flags", [0, 1, 2])
-@pytest.mark.parametrize("cap", [1, 7, 64, 256])
+@pytest.mark.parametrize("cap", [1, 7, 64, 128, 256])
 @pytest.mark.parametrize("kind,n,seed,k", [("mixture", 3000, 2, 10), ("uniform", 2000, 1, 6)])
 def test_solve_bit_exact_with_capped_phases(lib, O, kind, n, seed, k, cap, flags):
     s, r = _compare_solve(O, inst(kind, n, seed, k), max_iters=cap, flags=flags)
@@ -266,10 +266,10 @@ def test_solve_bit_exact_with_capped_phases(lib, O, kind, n, seed, k, cap, flags
 
 
 def test_default_solve_equals_oracle_default(lib, O):
-    # both sides at their defaults (256 sweeps per phase); a sparse graph that
+    # both sides at their defaults (128 sweeps per phase); a sparse graph that
     # takes several phases and pricing rounds
     d = inst("mixture", 5000, 3, 4)
-    assert f2m.f2m_default_params().max_iters == 256
+    assert f2m.f2m_default_params().max_iters == 128
     s, r = compare_solves(O, f2m, d)
     assert r.phases > 1 and s.info["certified"] == 2
 
