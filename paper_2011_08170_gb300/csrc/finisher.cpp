@@ -46,6 +46,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <climits>
 #include <cstdint>
 #include <functional>
 #include <mutex>
@@ -65,6 +66,7 @@ struct Searcher {
   };
   std::vector<Item> heap;
   std::vector<int32_t> order;
+  uint32_t stamp_next = 0, stamp_end = 0;  // this worker's unused visit stamps [next, end)
 
   static bool less(const Item& a, const Item& b) { return a.d < b.d || (a.d == b.d && a.key < b.key); }
   void push(const Item& it) {
@@ -98,6 +100,7 @@ struct Searcher {
 
 constexpr int32_t kFinBlock = kFinBlockNodes;  // nodes per phase-1 block
 constexpr int32_t kFinBlock2 = 16384;  // nodes per phase-2 block
+constexpr uint32_t kStampChunk = 1024;  // visit stamps a worker takes at a time
 
 // Worker threads kept for the life of the process (one pool, shared by every
 // context; jobs from different host threads take turns): a job is a count of
@@ -200,9 +203,12 @@ namespace {
 // phase's start -- lam0 for a left copy and -lam0 for a right one in phase 1,
 // pi0 in phase 2 -- and never settled, and a search that would settle one (or
 // finds nothing) is dropped.
+// srcs (NULL: every node of [lo, hi)): the nodes that may hold a surplus, in
+// key order -- the others are skipped without a look.
 int solve_range(int32_t n, int32_t lo, int32_t hi, const int32_t* lam0, const int64_t* pi0v,
                 const int32_t* irp, const int2* iec, const int32_t* twin, uint8_t* y, int32_t F,
-                FinisherWork* w, Searcher& sr, int64_t* pushes_out) {
+                FinisherWork* w, Searcher& sr, int64_t* pushes_out, const int32_t* srcs = nullptr,
+                int64_t nsrc = 0) {
   int64_t* pi = w->pi_p;
   int64_t* dist = w->dist.data();
   int32_t* excess = w->ex_p;
@@ -221,11 +227,17 @@ int solve_range(int32_t n, int32_t lo, int32_t hi, const int32_t* lam0, const in
     return node < n ? (int64_t)lam0[node] : -(int64_t)lam0[node - n];
   };
   int64_t pushes = 0;
-  for (int32_t i = lo; i < hi; ++i) {
-    for (int side = 0; side < 2; ++side) {
-      const int32_t s = side == 0 ? i : n + i;  // key order: L_i (2i) before R_i (2i+1)
+  const int64_t nitems = srcs ? nsrc : 2LL * (hi - lo);
+  for (int64_t item = 0; item < nitems; ++item) {
+    {
+      // key order: L_i (2i) before R_i (2i+1)
+      const int32_t s = srcs ? srcs[item] : ((item & 1) ? n + lo + (int32_t)(item >> 1) : lo + (int32_t)(item >> 1));
       while (excess[s] > 0) {
-        const uint32_t round = w->stamp.fetch_add(1) + 1;
+        if (sr.stamp_next == sr.stamp_end) {  // a fresh chunk of stamps, unique across workers
+          sr.stamp_next = w->stamp.fetch_add(kStampChunk) + 1;
+          sr.stamp_end = sr.stamp_next + kStampChunk;
+        }
+        const uint32_t round = sr.stamp_next++;
         sr.order.clear();
         sr.heap.clear();
         dist[s] = 0;
@@ -233,6 +245,13 @@ int solve_range(int32_t n, int32_t lo, int32_t hi, const int32_t* lam0, const in
         pred[s] = -1;
         sr.push({0, key_of(s), s});
         int32_t t = -1;
+        // the smallest distance at which a node with deficit has been reached:
+        // an item farther than that can never come to the top before the
+        // search ends, so it is not pushed (the search is unchanged)
+        int64_t bound = INT64_MAX;
+        auto note = [&](int32_t j, int64_t d) {
+          if (excess[j] < 0 && d < bound) bound = d;
+        };
         while (!sr.heap.empty()) {
           const Searcher::Item top = sr.pop();
           const int32_t v = top.node;
@@ -247,13 +266,15 @@ int solve_range(int32_t n, int32_t lo, int32_t hi, const int32_t* lam0, const in
               if (y[e]) continue;
               const int32_t j = n + iec[e].x;
               if (blocked && outside(j)) {
-                sr.push({dist[v] + ((int64_t)iec[e].y << F) - pi[v] + pi0(j), key_of(j), j});
+                const int64_t d = dist[v] + ((int64_t)iec[e].y << F) - pi[v] + pi0(j);
+                if (d <= bound) sr.push({d, key_of(j), j});
                 continue;
               }
               const int64_t d = dist[v] + ((int64_t)iec[e].y << F) - pi[v] + pi[j];
-              if (closed[j] != round && (reached[j] != round || d < dist[j])) {
+              if (d <= bound && closed[j] != round && (reached[j] != round || d < dist[j])) {
                 reached[j] = round; dist[j] = d; via[j] = e; pred[j] = v;
                 sr.push({d, key_of(j), j});
+                note(j, d);
               }
             }
           } else {
@@ -264,13 +285,15 @@ int solve_range(int32_t n, int32_t lo, int32_t hi, const int32_t* lam0, const in
               if (!y[a]) continue;
               const int32_t j = iec[f].x;  // L_x, the tail of arc a
               if (blocked && outside(j)) {
-                sr.push({dist[v] - ((int64_t)iec[f].y << F) - pi[v] + pi0(j), key_of(j), j});
+                const int64_t d = dist[v] - ((int64_t)iec[f].y << F) - pi[v] + pi0(j);
+                if (d <= bound) sr.push({d, key_of(j), j});
                 continue;
               }
               const int64_t d = dist[v] - ((int64_t)iec[f].y << F) - pi[v] + pi[j];
-              if (closed[j] != round && (reached[j] != round || d < dist[j])) {
+              if (d <= bound && closed[j] != round && (reached[j] != round || d < dist[j])) {
                 reached[j] = round; dist[j] = d; via[j] = a; pred[j] = v;
                 sr.push({d, key_of(j), j});
+                note(j, d);
               }
             }
           }
@@ -338,6 +361,7 @@ int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t*
     std::fill(w->reached.begin(), w->reached.end(), 0u);
     std::fill(w->closed.begin(), w->closed.end(), 0u);
     w->stamp.store(0);
+    for (Searcher& sr : w->workers) sr.stamp_next = sr.stamp_end = 0;
   }
   // ext_pi / ext_ex: potentials and surpluses left by phase 1 run elsewhere
   // (the GPU); the host then starts at phase 2
@@ -399,21 +423,43 @@ int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t*
     stats->aug[1] += done2 - done1;
   }
   t0 = clk::now();
+  // phase 3: per segment, the plain search from each node still holding a
+  // surplus (collected per phase-2 block, in key order)
+  std::vector<std::vector<int32_t>> left(blocks2.size());
+  if (r == 0)
+    r = run_items((int32_t)blocks2.size(), threads, w, pushes, [&](int32_t k, Searcher&, int64_t*) {
+      std::vector<int32_t>& out = left[k];
+      out.clear();
+      for (int32_t i = blocks2[k].x; i < blocks2[k].y; ++i) {
+        if (excess[i] > 0) out.push_back(i);
+        if (excess[n + i] > 0) out.push_back(n + i);
+      }
+      return 0;
+    });
+  std::vector<std::vector<int32_t>> seg_src(segs.size());
+  for (size_t k = 0, q = 0; k < segs.size(); ++k) {
+    const int32_t sg = segs[k];
+    for (; q < blocks2.size() && blocks2[q].x < seg_off[sg + 1]; ++q)
+      seg_src[k].insert(seg_src[k].end(), left[q].begin(), left[q].end());
+  }
   if (r == 0)
     r = run_items((int32_t)segs.size(), threads, w, pushes, [&](int32_t k, Searcher& sr, int64_t* p) {
       const int32_t sg = segs[k];
-      const int q = solve_range(n, seg_off[sg], seg_off[sg + 1], nullptr, nullptr, irp, iec, twin, y, F, w,
-                                sr, p);
-      if (q != 0) return q;
+      return solve_range(n, seg_off[sg], seg_off[sg + 1], nullptr, nullptr, irp, iec, twin, y, F, w, sr, p,
+                         seg_src[k].data(), (int64_t)seg_src[k].size());
+    });
+  const int64_t total3 = pushes_total(pushes);
+  if (r == 0)  // lambda at F + 1 bits: pi(L_i) - pi(R_i), block by block
+    r = run_items((int32_t)blocks2.size(), threads, w, pushes, [&](int32_t k, Searcher&, int64_t*) {
       int st = 0;
-      for (int32_t i = seg_off[sg]; i < seg_off[sg + 1]; ++i) {
+      for (int32_t i = blocks2[k].x; i < blocks2[k].y; ++i) {
         const int64_t l2 = pi[i] - pi[n + i];
         if (l2 >= 2 * kLamLimit || l2 <= -2 * kLamLimit) st = 5;
         lam2[i] = (int32_t)l2;
       }
       return st;
     });
-  const int64_t total = pushes_total(pushes);
+  const int64_t total = total3;
   if (stats) {
     stats->ms_phase[2] += ms_since(t0);
     stats->aug[2] += total - done2;
