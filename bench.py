@@ -493,7 +493,9 @@ def single_line(args, wname, w, rank, world, local, dist, f2m, torch, nested=Fal
     ms_pr = statistics.median(i["ms_pricing"] for i in infos)
     gdp_bytes = iters * (GDP_BYTES_PER_ENTRY * nnz0 + GDP_BYTES_PER_NODE * n)
     gdp_gbs = gdp_bytes / (ms_gdp * 1e-3) / 1e9
-    pr_pairs = inf0["pricing_rounds"] * n * (n - 1) / 2
+    # pairs the scans evaluated: n(n-1)/2 a full scan, rows x n the scan that
+    # certifies the finisher's lambda (only rows whose lambda rose)
+    pr_pairs = inf0.get("pricing_pairs") or inf0["pricing_rounds"] * n * (n - 1) / 2
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     num_sms = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak = num_sms * 128 * sm_mhz * 1e6 / 1e12  # Tops/s at the sampled clock

@@ -177,6 +177,12 @@ typedef struct {
   int64_t finish_aug_phase[3];
   int32_t finish_threads;       /* host threads the blocked phases used */
   int32_t finish_phase1_gpu;    /* 1 if the finisher's phase 1 ran on the GPU */
+  int64_t pricing_pairs;        /* pairs the pricing scans evaluated: n(n-1)/2 a full scan (also
+                                   the culled one, which skips pairs it proves positive), rows x n
+                                   a certifying scan of the finisher's lambda (only the nodes
+                                   whose lambda rose can make a pair negative) */
+  int32_t certifying_scans;     /* scans of that second kind */
+  int32_t pad_;
 } f2m_info;
 
 /* f2m_info.gdp_kernel values */

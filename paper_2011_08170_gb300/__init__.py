@@ -82,7 +82,8 @@ class f2m_info(C.Structure):
                 ("ms_extract", C.c_double), ("ms_finish", C.c_double), ("ms_total", C.c_double),
                 ("ms_finish_prep", C.c_double), ("ms_finish_phase", C.c_double * 3),
                 ("ms_finish_scatter", C.c_double), ("finish_aug_phase", C.c_int64 * 3),
-                ("finish_threads", C.c_int32), ("finish_phase1_gpu", C.c_int32)]
+                ("finish_threads", C.c_int32), ("finish_phase1_gpu", C.c_int32),
+                ("pricing_pairs", C.c_int64), ("certifying_scans", C.c_int32), ("pad_", C.c_int32)]
 
     def as_dict(self) -> dict:
         d = {}

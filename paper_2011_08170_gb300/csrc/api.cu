@@ -296,6 +296,7 @@ extern "C" void f2m_destroy(f2m_ctx* c) {
   dfree(c->d_trace_b2); dfree(c->d_trace_ch); dfree(c->d_pts); dfree(c->d_pairs);
   dfree(c->d_pts4); dfree(c->d_pstat); dfree(c->d_mranges); dfree(c->d_mtblk); dfree(c->d_mbox);
   dfree(c->d_mlmax); dfree(c->d_mframes); dfree(c->d_mcand); dfree(c->d_mncand);
+  dfree(c->d_lam_ref); dfree(c->d_raised); dfree(c->d_pts_raised); dfree(c->d_nraised);
   dfree(c->d_ranges); dfree(c->d_boxes); dfree(c->d_smax);
   dfree(c->d_count); dfree(c->d_tile); dfree(c->d_deg); dfree(c->d_tmp_rp); dfree(c->d_new_rp);
   dfree(c->d_block_sums); dfree(c->d_tmp_col); dfree(c->d_out_a); dfree(c->d_out_b);
@@ -440,6 +441,12 @@ f2m_status f2m::create_internal(const int32_t* xy, int32_t n, const int32_t* row
       if (e == cudaSuccess) e = dalloc(&c->d_new_rp, n + 1);
       if (e == cudaSuccess) e = dalloc(&c->d_block_sums, (int64_t)scan_scratch_ints(n));
       if (e == cudaSuccess) e = dalloc(&c->d_tmp_col, c->tmp_col_cap);
+      if (e == cudaSuccess && seg_off.size() == 2) {  // the certifying scan's rows (one instance)
+        e = dalloc(&c->d_lam_ref, n);
+        if (e == cudaSuccess) e = dalloc(&c->d_raised, n);
+        if (e == cudaSuccess) e = dalloc(&c->d_pts_raised, n);
+        if (e == cudaSuccess) e = dalloc(&c->d_nraised, 1);
+      }
     }
     if (e == cudaSuccess) e = dalloc(&c->d_lam[0], n);
     if (e == cudaSuccess) e = dalloc(&c->d_lam[1], n);
@@ -488,6 +495,7 @@ extern "C" f2m_status f2m_set_lambda(f2m_ctx* c, const int32_t* lambda, int32_t 
   CK(c, read_check(c, &h));
   if (h.flags) return fail(c, F2M_ERR_INVALID_ARG, "lambda out of range at node " + std::to_string(h.first_bad));
   c->fb_cur = frac_bits;
+  c->lam_version += 1;
   return F2M_OK;
 }
 
@@ -549,6 +557,7 @@ const int32_t* f2m::cur_lambda(f2m_ctx* c, int32_t* fb) {
 f2m_status f2m::gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, bool want_trace,
                             int64_t trace_cap, double* ms) {
   const int32_t F = c->p.frac_bits;
+  c->lam_version += 1;
   if (c->fb_cur != F) {  // continue from the finisher's lambda: floor to F bits
     CK(c, launch_halve(c->d_lam2, c->d_lam[c->cur], c->n, c->st));
     c->fb_cur = F;
@@ -753,6 +762,56 @@ f2m_status f2m::price_internal(f2m_ctx* c, double* ms, const int32_t* lam_overri
   const int32_t* lam = cur_lambda(c, &fb);
   if (lam_override) lam = lam_override;
   const int32_t nseg = (int32_t)c->seg_off.size() - 1;
+  const bool plain = !lam_override && !cut_count(c);  // a scan of lambda itself, F2M terms only
+  // The scan that certifies the finisher's lambda.  A complete scan at lambda
+  // lam_ref left z >= 0 on every pair outside the CSR (the pairs it found were
+  // merged); the finisher is the only change of lambda since, and returns
+  // lambda' = lam_ref * 2^(fb - ref_fb) + delta.  Then z'_uv = z_uv 2^(fb -
+  // ref_fb) - delta_u - delta_v can be negative only if delta_u > 0 or
+  // delta_v > 0: only the rows of the nodes whose lambda rose are scanned,
+  // against all points, for the same pairs as a full scan.
+  if (plain && nseg == 1 && c->p.pricing == 1 && !(c->p.flags & F2M_FLAG_PRICING_TENSOR) && c->d_lam_ref &&
+      c->ref_version == c->fin_src_version && c->lam_version == c->fin_dst_version && fb > c->ref_fb) {
+    CK(c, cudaEventRecord(c->ev0, c->st));
+    CK(c, launch_pricing_prep(c->d_xy, lam, nullptr, c->n, fb, c->d_pts, c->st));
+    CK(c, launch_pricing_raised(lam, c->d_lam_ref, c->n, fb - c->ref_fb, c->d_pts, c->d_raised, c->d_pts_raised,
+                                c->d_nraised, c->st));
+    unsigned int nu = 0;
+    CK(c, cudaMemcpyAsync(&nu, c->d_nraised, sizeof(nu), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    const int64_t ntiles_r = (int64_t)((nu + kPricingTile - 1) / kPricingTile) * ((c->n + kPricingJ - 1) / kPricingJ);
+    for (bool first = true;; first = false) {
+      if (!first) CK(c, cudaEventRecord(c->ev0, c->st));
+      CK(c, launch_pricing_scan(c->d_pts, c->d_xy, lam, c->d_rp, c->d_ec, c->n, fb, nullptr, (int32_t)ntiles_r,
+                                c->d_pairs, c->pairs_cap, c->d_count, c->d_tile, c->num_sms, c->st,
+                                c->d_pts_raised, c->d_raised, (int32_t)nu));
+      CK(c, cudaEventRecord(c->ev1, c->st));
+      unsigned long long cnt = 0;
+      CK(c, cudaMemcpyAsync(&cnt, c->d_count, sizeof(cnt), cudaMemcpyDeviceToHost, c->st));
+      CK(c, cudaStreamSynchronize(c->st));
+      if (ms) *ms += elapsed_ms(c);
+      c->npairs = (int64_t)cnt;
+      if ((int64_t)cnt <= c->pairs_cap) break;
+      dfree(c->d_pairs);
+      c->pairs_cap = (int64_t)cnt + ((int64_t)cnt >> 2) + 1024;
+      CK(c, dalloc(&c->d_pairs, c->pairs_cap));
+    }
+    c->seg_pairs.assign(1, c->npairs);
+    c->last_scan_rows = (int64_t)nu;
+    c->last_scan_pairs = (int64_t)nu * c->n;
+    // a complete result for this lambda: it is the next reference
+    CK(c, cudaMemcpyAsync(c->d_lam_ref, lam, sizeof(int32_t) * c->n, cudaMemcpyDeviceToDevice, c->st));
+    c->ref_fb = fb;
+    c->ref_version = c->lam_version;
+    return F2M_OK;
+  }
+  c->last_scan_rows = -1;
+  c->last_scan_pairs = 0;
+  for (int32_t sg = 0; sg < nseg; ++sg)
+    if (c->seg_scan.empty() || c->seg_scan[sg]) {
+      const int64_t m = c->seg_off[sg + 1] - c->seg_off[sg];
+      c->last_scan_pairs += m * (m - 1) / 2;
+    }
   // full scan: with the fp32 filter (caller order), or on the tensor cores
   // (renumbered order); culled scan: fp32 filter in the renumbered (Morton)
   // order, so that a tile is a compact patch with a small bounding box
@@ -906,6 +965,11 @@ f2m_status f2m::price_internal(f2m_ctx* c, double* ms, const int32_t* lam_overri
     dfree(c->d_pairs);
     c->pairs_cap = (int64_t)cnt + ((int64_t)cnt >> 2) + 1024;
     CK(c, dalloc(&c->d_pairs, c->pairs_cap));
+  }
+  if (plain && c->d_lam_ref) {  // the reference of a later certifying scan
+    CK(c, cudaMemcpyAsync(c->d_lam_ref, lam, sizeof(int32_t) * c->n, cudaMemcpyDeviceToDevice, c->st));
+    c->ref_fb = fb;
+    c->ref_version = c->lam_version;
   }
   c->seg_pairs.assign(nseg, 0);
   if (nseg == 1) {
@@ -1127,6 +1191,9 @@ static f2m_status fin_gpu_phase1(f2m_ctx* c, const std::vector<int2>& fblocks, c
 f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug, const uint8_t* h_include) {
   using clk = std::chrono::steady_clock;
   const auto t_prep = clk::now();
+  c->fin_src_version = c->lam_version;
+  c->lam_version += 1;  // lambda changes below (or the call fails)
+  c->fin_dst_version = h_include ? -3 : c->lam_version;  // a partial call does not qualify
   const int32_t n = c->n;
   const int32_t F = c->p.frac_bits;
   GdpPlan& P = c->plan;
@@ -1300,6 +1367,8 @@ extern "C" f2m_status f2m_solve(f2m_ctx* c, f2m_info* info_out) {
       s = price_internal(c, &info.ms_pricing);
       if (s != F2M_OK) { status = s; break; }
       info.pricing_rounds += 1;
+      info.pricing_pairs += c->last_scan_pairs;
+      info.certifying_scans += c->last_scan_rows >= 0;
       last_pairs = c->npairs;
       if (c->npairs > 0) {
         const int64_t found = c->npairs;
@@ -1343,6 +1412,8 @@ extern "C" f2m_status f2m_solve(f2m_ctx* c, f2m_info* info_out) {
     s = price_internal(c, &info.ms_pricing);
     if (s != F2M_OK) { status = s; break; }
     info.pricing_rounds += 1;
+    info.pricing_pairs += c->last_scan_pairs;
+    info.certifying_scans += c->last_scan_rows >= 0;
     last_pairs = c->npairs;
     if (c->npairs == 0) { info.certified = 2; break; }
     s = merge_internal(c, c->d_pairs, c->npairs, &info.ms_merge);

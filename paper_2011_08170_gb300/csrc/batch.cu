@@ -522,6 +522,7 @@ static f2m_status cluster_plan(f2m_batch* b) {
 static f2m_status batch_cluster_phase(f2m_batch* b, const std::vector<uint8_t>& active,
                                       std::vector<int64_t>& sweeps_out, double* ms) {
   f2m_ctx* c = b->u;
+  c->lam_version += 1;
   GdpPlan& P = c->plan;
   const int32_t K = b->count;
   CK(c, enqueue_phase_start(b, c->st, nullptr));
@@ -572,6 +573,7 @@ static f2m_status batch_cluster_phase(f2m_batch* b, const std::vector<uint8_t>& 
 static f2m_status batch_gdp_phase(f2m_batch* b, const std::vector<uint8_t>& active,
                                   std::vector<int64_t>& sweeps_out, double* ms) {
   f2m_ctx* c = b->u;
+  c->lam_version += 1;
   GdpPlan& P = c->plan;
   const int32_t F = c->p.frac_bits;
   if (c->fb_cur != F) {  // continue from the finisher's lambda: floor to F bits
@@ -808,6 +810,7 @@ extern "C" f2m_status f2m_solve_batch(f2m_batch* b, f2m_info* info_out, f2m_info
       }
       if (any_scan) {  // pricing with the GDP lambda
         status = price_internal(c, &tot.ms_pricing);
+        tot.pricing_pairs += c->last_scan_pairs;
         if (status != F2M_OK) break;
         tot.pricing_rounds += 1;
         for (int32_t s = 0; s < K; ++s) {
@@ -889,6 +892,7 @@ extern "C" f2m_status f2m_solve_batch(f2m_batch* b, f2m_info* info_out, f2m_info
     }
     if (any_scan) {
       status = price_internal(c, &tot.ms_pricing);
+      tot.pricing_pairs += c->last_scan_pairs;
       if (status != F2M_OK) break;
       tot.pricing_rounds += 1;
       for (int32_t s = 0; s < K; ++s) {

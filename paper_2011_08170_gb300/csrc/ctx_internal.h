@@ -71,6 +71,22 @@ struct f2m_ctx {
   int2* d_mcand = nullptr;      // the filter's candidates
   unsigned long long* d_mncand = nullptr;
   int64_t mcand_cap = 0;
+  // the scan that certifies the finisher's lambda: a complete scan at lambda
+  // lam_ref (units 2^-ref_fb) left every pair outside the CSR with z >= 0; if
+  // the finisher is the only change of lambda since (lam_version counts every
+  // change), a pair can turn negative only where lambda rose, so only those
+  // nodes' rows are scanned
+  int64_t lam_version = 0;      // bumped by every change of lambda
+  int64_t ref_version = -1;     // lam_version of the scan that wrote d_lam_ref
+  int64_t fin_src_version = -2; // lam_version before / after the last finisher call
+  int64_t fin_dst_version = -3;
+  int32_t ref_fb = 0;
+  int32_t* d_lam_ref = nullptr; // [n] caller order
+  uint8_t* d_raised = nullptr;  // [n] nodes whose lambda rose
+  float4* d_pts_raised = nullptr;  // [n] their points
+  unsigned int* d_nraised = nullptr;
+  int64_t last_scan_rows = -1;  // rows of the last scan if it was a certifying one, else -1
+  int64_t last_scan_pairs = 0;  // pairs the last scan evaluated
   int2* d_pairs = nullptr;
   int64_t pairs_cap = 0;
   int64_t npairs = 0;   // pairs held in d_pairs after the last scan

@@ -621,6 +621,7 @@ f2m_status cut_lists(f2m_ctx* c) {
 f2m_status cut_gdp_phase(f2m_ctx* c, int64_t max_sweeps, int64_t* sweeps, long long* tb,
                          unsigned long long* tc, int64_t tcap, double* ms) {
   CutState* S = c->cuts;
+  c->lam_version += 1;
   f2m_status s = cut_lists(c);
   if (s != F2M_OK) return s;
   const CutArgs a = cut_args(c);

@@ -117,10 +117,18 @@ cudaError_t launch_pricing_prep(const int2* xy, const int32_t* lam, const int32_
 cudaError_t launch_pricing_boxes(const float4* pts, const int2* ranges, int32_t nranges, float4* box, float* smax,
                                  cudaStream_t st);
 // the scan over the tile pairs (positions in pts); count and pairs (nodes, u < v)
+// tiles NULL: i-tiles of the ni points pts_i against j-tiles of all n points
+// (inU flags the nodes of pts_i; ntiles = its tile count), else the list's
+// tile pairs over pts (pts_i NULL)
 cudaError_t launch_pricing_scan(const float4* pts, const int2* xy, const int32_t* lam, const int32_t* rp,
                                 const int2* ec, int32_t n, int32_t fb, const int4* tiles, int32_t ntiles,
                                 int2* pairs, int64_t cap, unsigned long long* count, unsigned int* tile_counter,
-                                int num_sms, cudaStream_t st);
+                                int num_sms, cudaStream_t st, const float4* pts_i = nullptr,
+                                const uint8_t* inU = nullptr, int32_t ni = 0);
+// nodes whose lambda rose above lam_ref << shift: flags, their points, their count
+cudaError_t launch_pricing_raised(const int32_t* lam, const int32_t* lam_ref, int32_t n, int32_t shift,
+                                  const float4* pts, uint8_t* inU, float4* pts_u, unsigned int* count,
+                                  cudaStream_t st);
 // the same scan on the tensor cores (pricing.cu): pts4[v] = {x, y, lambda, node
 // perm[v]}; tiles {i0, i1, j0, j1} of at most kMmaTileI x kMmaTileJ positions
 cudaError_t launch_pricing_mma_check(long long rounds, unsigned long long seed, unsigned long long* checked,

@@ -385,6 +385,7 @@ extern "C" f2m_status f2m_warm_start(f2m_ctx* c, f2m_mlp* m, double* ms) {
   float* feat = nullptr;
   float* scale = nullptr;
   CK(c, cudaEventRecord(c->ev0, c->st));
+  c->lam_version += 1;
   CK(c, cudaMallocAsync((void**)&feat, sizeof(float) * (size_t)c->n * kFeatures, c->st));
   CK(c, cudaMallocAsync((void**)&scale, sizeof(float) * (size_t)c->n, c->st));
   cudaError_t e = features_device(c->d_xy, c->n, feat, scale, c->st);

@@ -106,12 +106,19 @@ __global__ void pricing_boxes_kernel(const float4* __restrict__ pts, const int2*
 
 // exact decision for a pair that passed the filter: positions ii < jj in the
 // point array (each unordered pair once), nodes i and j
+// (inU non-NULL: the i-points are the nodes flagged in inU, the j-points all
+// nodes; a pair of two flagged nodes is taken from the row of the smaller)
 __device__ __noinline__ void pricing_confirm(int ii, int jj, int i, int j, int32_t n, const int2* __restrict__ xy,
                                              const int32_t* __restrict__ lam,
                                              const int32_t* __restrict__ rp,
                                              const int2* __restrict__ ec, int32_t fb, int2* pairs,
-                                             long long cap, unsigned long long* count) {
-  if (jj <= ii || jj >= n) return;  // each unordered pair once; tail of the last tile
+                                             long long cap, unsigned long long* count,
+                                             const uint8_t* __restrict__ inU = nullptr) {
+  if (inU) {
+    if (jj >= n || j == i || (inU[j] && j < i)) return;
+  } else if (jj <= ii || jj >= n) {
+    return;  // each unordered pair once; tail of the last tile
+  }
   if (j < i) {
     const int t = i;
     i = j;
@@ -152,6 +159,7 @@ static_assert(kPriceJMax % kPriceChunk == 0 && kPriceChunk % kPriceGroup == 0, "
 template <int P>
 __device__ __forceinline__ void pricing_hits(const int* hits, int nh, int lane, int4 tl, const float4* s_ac,
                                           const float2* s_y, const float4* __restrict__ pts,
+                                          const float4* __restrict__ pts_i, const uint8_t* __restrict__ inU,
                                           const int2* __restrict__ xy, const int32_t* __restrict__ lam,
                                           const int32_t* __restrict__ rp, const int2* __restrict__ ec,
                                           int32_t n, int32_t fb, int2* pairs, long long cap,
@@ -162,7 +170,7 @@ __device__ __forceinline__ void pricing_hits(const int* hits, int nh, int lane, 
     const int t = ent & 0xFF, g = ent >> 8;
     const int ii = tl.x + p * kPriceThreads + t;
     if (ii >= tl.y) continue;
-    const float4 vi = pts[ii];
+    const float4 vi = pts_i[ii];
     const float nai = -(vi.x - vi.z), nci = -(vi.x + vi.z), nyi = -vi.y;
     for (int kk = 0; kk < kPriceGroup; ++kk) {
       const int jj = tl.z + g + kk;
@@ -170,7 +178,7 @@ __device__ __forceinline__ void pricing_hits(const int* hits, int nh, int lane, 
       const float4 ac = s_ac[g + kk];
       if (pricing_filter(ac.x, ac.z, s_y[g + kk].x, nai, nci, nyi) < 0.0f)
         pricing_confirm(ii, jj, __float_as_int(vi.w), __float_as_int(pts[jj].w), min(n, tl.w), xy, lam, rp,
-                        ec, fb, pairs, cap, count);
+                        ec, fb, pairs, cap, count, inU);
     }
   }
 }
@@ -181,7 +189,8 @@ pricing_kernel(const float4* __restrict__ pts, const int2* __restrict__ xy,
                const int32_t* __restrict__ lam, const int32_t* __restrict__ rp,
                const int2* __restrict__ ec, int32_t n, int32_t fb, const int4* __restrict__ tiles,
                int32_t ntiles, int2* pairs, long long cap, unsigned long long* count,
-               unsigned int* tile_counter) {
+               unsigned int* tile_counter, const float4* __restrict__ pts_i, const uint8_t* __restrict__ inU,
+               int32_t ni, int32_t nj_tiles) {
   constexpr int kPriceThreads = kPriceTile / P;
   constexpr int Q = P / 2;
   static_assert(kPriceThreads <= 256 && kPriceTile <= (1 << 23), "hit entry packing");
@@ -198,7 +207,14 @@ pricing_kernel(const float4* __restrict__ pts, const int2* __restrict__ xy,
     __syncthreads();
     const int tp = s_tp;
     if (tp >= ntiles) break;
-    const int4 tl = tiles[tp];  // i in [x, y), j in [z, w)
+    // i in [x, y), j in [z, w); no list: i-tiles of the ni i-points by j-tiles of all points
+    int4 tl;
+    if (tiles) {
+      tl = tiles[tp];
+    } else {
+      const int it = tp / nj_tiles, jt = tp % nj_tiles;
+      tl = make_int4(it * kPriceTile, min((it + 1) * kPriceTile, ni), jt * kPriceJMax, min((jt + 1) * kPriceJMax, n));
+    }
 
     // i-points p = 2q + h at tl.x + p * kPriceThreads + tid, negated; a point
     // past the range gets 1e18 (its e' stays above 1e36, finite)
@@ -210,7 +226,7 @@ pricing_kernel(const float4* __restrict__ pts, const int2* __restrict__ xy,
       for (int h = 0; h < 2; ++h) {
         const int i = tl.x + (2 * q + h) * kPriceThreads + threadIdx.x;
         if (i < tl.y) {
-          const float4 v = pts[i];
+          const float4 v = pts_i[i];
           a[h] = v.x - v.z;
           c[h] = v.x + v.z;
           y[h] = v.y;
@@ -266,11 +282,39 @@ pricing_kernel(const float4* __restrict__ pts, const int2* __restrict__ xy,
       }
       if (nh) {  // the same branch in every lane of the warp
         __syncwarp();
-        pricing_hits<P>(hits, nh, lane, tl, s_ac, s_y, pts, xy, lam, rp, ec, n, fb, pairs, cap, count);
+        pricing_hits<P>(hits, nh, lane, tl, s_ac, s_y, pts, pts_i, inU, xy, lam, rp, ec, n, fb, pairs, cap, count);
         __syncwarp();  // the list is free for the next chunk
       }
     }
   }
+}
+
+// the nodes whose lambda (units 2^-fb) exceeds the reference (units 2^-fb_ref,
+// fb >= fb_ref) scaled to fb: flagged in inU, their points appended to pts_u
+// (order unspecified), their number in *count
+__global__ void pricing_raised_kernel(const int32_t* __restrict__ lam, const int32_t* __restrict__ lam_ref,
+                                      int32_t n, int32_t shift, const float4* __restrict__ pts,
+                                      uint8_t* __restrict__ inU, float4* __restrict__ pts_u,
+                                      unsigned int* count) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    const bool up = (long long)lam[v] > ((long long)lam_ref[v] << shift);
+    inU[v] = up ? 1 : 0;
+    if (up) pts_u[atomicAdd(count, 1u)] = pts[v];
+  }
+}
+
+cudaError_t launch_pricing_raised(const int32_t* lam, const int32_t* lam_ref, int32_t n, int32_t shift,
+                                  const float4* pts, uint8_t* inU, float4* pts_u, unsigned int* count,
+                                  cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  pricing_raised_kernel<<<blocks, 256, 0, st>>>(lam, lam_ref, n, shift, pts, inU, pts_u, count);
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pricing_prep(const int2* xy, const int32_t* lam, const int32_t* perm, int32_t n, int32_t fb,
@@ -294,7 +338,9 @@ cudaError_t launch_pricing_boxes(const float4* pts, const int2* ranges, int32_t 
 cudaError_t launch_pricing_scan(const float4* pts, const int2* xy, const int32_t* lam, const int32_t* rp,
                                 const int2* ec, int32_t n, int32_t fb, const int4* tiles, int32_t ntiles,
                                 int2* pairs, int64_t cap, unsigned long long* count, unsigned int* tile_counter,
-                                int num_sms, cudaStream_t st) {
+                                int num_sms, cudaStream_t st, const float4* pts_i, const uint8_t* inU, int32_t ni) {
+  if (!pts_i) pts_i = pts;
+  const int32_t nj_tiles = (n + kPriceJMax - 1) / kPriceJMax;
   cudaError_t err = cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
   if (err == cudaSuccess) err = cudaMemsetAsync(tile_counter, 0, sizeof(unsigned int), st);
   if (err != cudaSuccess) return err;
@@ -307,7 +353,7 @@ cudaError_t launch_pricing_scan(const float4* pts, const int2* xy, const int32_t
   if ((long long)ntiles >= 4LL * num_sms * per_sm) {
     const long long grid = (long long)num_sms * per_sm;
     pricing_kernel<8><<<(int)grid, kPriceTile / 8, 0, st>>>(pts, xy, lam, rp, ec, n, fb, tiles, ntiles, pairs,
-                                                           cap, count, tile_counter);
+                                                           cap, count, tile_counter, pts_i, inU, ni, nj_tiles);
   } else {
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pricing_kernel<4>, kPriceTile / 4, 0);
     if (err != cudaSuccess) return err;
@@ -315,7 +361,7 @@ cudaError_t launch_pricing_scan(const float4* pts, const int2* xy, const int32_t
     long long grid = (long long)num_sms * per_sm;
     if (grid > ntiles) grid = ntiles;
     pricing_kernel<4><<<(int)grid, kPriceTile / 4, 0, st>>>(pts, xy, lam, rp, ec, n, fb, tiles, ntiles, pairs,
-                                                           cap, count, tile_counter);
+                                                           cap, count, tile_counter, pts_i, inU, ni, nj_tiles);
   }
   count_launch();
   return cudaGetLastError();

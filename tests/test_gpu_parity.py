@@ -274,6 +274,33 @@ def test_default_solve_equals_oracle_default(lib, O):
     assert r.phases > 1 and s.info["certified"] == 2
 
 
+@pytest.mark.parametrize("kind,n,seed,k,rows", [("uniform", 20000, 0, 10, True), ("mixture", 20000, 1, 12, True),
+                                                ("mixture", 9000, 3, 4, False)])
+def test_certifying_scan_of_the_finisher_lambda(lib, O, kind, n, seed, k, rows):
+    # after a finisher call the scan of its lambda covers only the rows whose
+    # lambda rose (a pair elsewhere stays z >= 0): fewer pairs than a full
+    # scan; the solve matches the oracle's (which scans in full) up to the
+    # finisher bit for bit and after it by its optimum, and the oracle's
+    # certificate -- its own scan of all n(n-1)/2 pairs -- accepts the result
+    # (rows False: a sparse graph whose last GDP phase follows the last
+    # complete scan, so the finisher's lambda is scanned in full)
+    d = inst(kind, n, seed, k)
+    s, r = compare_solves(O, f2m, d)
+    assert s.info["certified"] == 2 and s.info["finisher_calls"] >= 1
+    full = n * (n - 1) // 2
+    if rows:
+        assert s.info["certifying_scans"] >= 1
+        assert s.info["pricing_pairs"] < s.info["pricing_rounds"] * full
+    else:
+        assert s.info["certifying_scans"] == 0
+        assert s.info["pricing_pairs"] == s.info["pricing_rounds"] * full
+    # a context whose lambda is then set by hand scans in full again
+    ctx = f2m.f2m_create(d["xy"], s.row_ptr, s.col)
+    f2m.f2m_set_lambda(ctx, s.lam, s.frac_bits)
+    cnt, _ = f2m.f2m_price(ctx)
+    assert cnt == 0
+
+
 @pytest.mark.parametrize("flags", [0, 2])
 def test_gdp_after_a_solve_that_merged(lib, O, flags):
     # a solve whose scans added edges ends with the finisher's lambda (F + 1
