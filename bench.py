@@ -399,6 +399,8 @@ def single_line(args, wname, w, rank, world, local, dist, f2m, torch, nested=Fal
     n, nnz0 = w["n"], int(d["row_ptr"][-1])
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    flush.fill_(0)  # the fill kernel is loaded here, not in the first timed step
+    torch.cuda.synchronize()
 
     # variants: class-by-class sweeps, degree requirements
     flags = f2m.F2M_FLAG_CLASS_SWEEPS if args.update == "classes" else 0
@@ -613,6 +615,8 @@ def run_batch(args, w, rank, world, local):
     nnzs = np.array([int(d["row_ptr"][-1]) for d in ds])
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    flush.fill_(0)  # the fill kernel is loaded here, not in the first timed step
+    torch.cuda.synchronize()
     for _ in range(args.warmup):
         b = f2m.f2m_create_batch(insts, params=params, stream=stream)
         f2m.f2m_solve_batch(b)
@@ -732,6 +736,8 @@ def run_warm(args, w, rank, world, local):
     ds = [I.make_instance(kind, n, replica_seed(w, rank), k) for kind, n, k in w["sizes"]]
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    flush.fill_(0)  # the fill kernel is loaded here, not in the first timed step
+    torch.cuda.synchronize()
     m = f2m.f2m_mlp_create(W.load_weights(), stream=stream)
     params = f2m.f2m_default_params()
     if args.max_iters:

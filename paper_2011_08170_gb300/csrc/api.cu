@@ -1240,6 +1240,7 @@ f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug, const uint8_t* h_inc
   // keep lambda, doubled to F+1 bits on the device
   std::vector<int2> ranges;   // entry ranges [x, y) that the host reads and writes
   std::vector<int2> nranges;  // their node ranges
+  bool wide = false;          // one span that also covers instances the finisher leaves alone
   if (h_include) {
     CK(c, launch_double(d_lam_int, d_lam2_int, n, c->st));
     CK(c, cudaMemcpyAsync(c->h_irp, P.irp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, c->st));
@@ -1256,6 +1257,14 @@ f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug, const uint8_t* h_inc
         nranges.push_back(make_int2(v0, v1));
         ranges.push_back(make_int2(e0, e1));
       }
+    }
+    // many ranges: one span from the first to the last instead (the copies'
+    // fixed cost dominates); the instances between are copied and written
+    // back unchanged, their lambda at F+1 bits set on the host below
+    if (ranges.size() > 8) {
+      ranges.assign(1, make_int2(ranges.front().x, ranges.back().y));
+      nranges.assign(1, make_int2(nranges.front().x, nranges.back().y));
+      wide = true;
     }
     for (size_t k = 0; k < ranges.size(); ++k) {
       const int2 q = ranges[k], v = nranges[k];
@@ -1307,6 +1316,12 @@ f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug, const uint8_t* h_inc
                                               : "no fractional 2-matching exists on the candidate graph");
   if (r == 5) return fail(c, F2M_ERR_OVERFLOW, "finisher lambda out of range");
   if (r != 0) return fail(c, F2M_ERR_INVALID_ARG, "finisher failed");
+  if (wide) {  // the instances left alone inside the span keep lambda, doubled
+    for (int32_t sg = 0; sg < nseg; ++sg) {
+      if (h_include[sg] || c->seg_off[sg] < nranges[0].x || c->seg_off[sg + 1] > nranges[0].y) continue;
+      for (int32_t v = c->seg_off[sg]; v < c->seg_off[sg + 1]; ++v) c->h_lam2[v] = 2 * c->h_lam[v];
+    }
+  }
   for (size_t k = 0; k < ranges.size(); ++k) {
     const int2 q = ranges[k], v = nranges[k];
     CK(c, cudaMemcpyAsync(c->d_fy + q.x, c->h_y + q.x, (size_t)(q.y - q.x), cudaMemcpyHostToDevice, c->st));
