@@ -1200,6 +1200,7 @@ f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug, const uint8_t* h_inc
   const int32_t nseg = (int32_t)c->seg_off.size() - 1;
   if (c->fin_cap < c->nnz) CK(c, alloc_finisher_buffers(c, c->ec_cap));
   if (!c->fin_work) c->fin_work = finisher_work_new();
+  static const int32_t hw = (int32_t)std::thread::hardware_concurrency();
   unsigned long long missing = 0;
   const bool twin_new = c->twin_version != P.version;
   if (twin_new) {  // the graph changed: reverse entries again
@@ -1299,13 +1300,14 @@ f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug, const uint8_t* h_inc
                             c->st));
     }
   }
+  // the host's worker threads wake while the device prepares and copies
+  finisher_pool_wake(std::min<int32_t>(hw, (int32_t)fblocks.size()));
   CK(c, cudaStreamSynchronize(c->st));
   if (twin_new) {
     if (missing) return fail(c, F2M_ERR_INVALID_ARG, "finisher: CSR not symmetric");
     c->twin_version = P.version;
   }
   c->fin_stats.ms_prep += std::chrono::duration<double, std::milli>(clk::now() - t_prep).count() - ms_gpu1;
-  static const int32_t hw = (int32_t)std::thread::hardware_concurrency();
   const int r = host_finisher(n, c->h_irp, c->h_iec, c->h_twin, c->h_y, c->h_exl, c->h_lam, F,
                               c->h_lam2, c->seg_off.data(), nseg, h_include, hw > 1 ? hw : 1, aug,
                               c->fin_work, &c->fin_stats, gpu1 ? c->h_fpi : nullptr, gpu1 ? c->h_fex : nullptr);

@@ -369,6 +369,10 @@ cudaError_t launch_batch_snapshot(const uint8_t* done, const int32_t* seg_off, i
 
 struct FinisherWork;
 FinisherWork* finisher_work_new();
+// lets up to `threads` - 1 worker threads of the host finisher poll for a job
+// that is about to come (a finisher call after some device work), so that the
+// call does not wait for them to wake
+void finisher_pool_wake(int32_t threads);
 void finisher_work_reserve(FinisherWork* w, int32_t n);  // host work arrays for n nodes
 void finisher_work_free(FinisherWork* w);
 // Min-cost flow on the bipartite double cover, internal node order; see

@@ -57,8 +57,10 @@
 
 namespace f2m {
 
-// Search state of one worker: heap, settled list and visit stamps.
-struct Searcher {
+// Search state of one worker: heap, settled list and visit stamps.  Every
+// push and pop writes the vectors' bounds, so each worker's state has cache
+// lines of its own (128 bytes: adjacent-line prefetch pairs 64-byte lines).
+struct alignas(128) Searcher {
   struct Item {
     int64_t d;
     int32_t key;   // the tie-break
@@ -105,35 +107,68 @@ constexpr uint32_t kStampChunk = 1024;  // visit stamps a worker takes at a time
 // Worker threads kept for the life of the process (one pool, shared by every
 // context; jobs from different host threads take turns): a job is a count of
 // items handed out by an atomic counter to the calling thread and the workers.
+// The phases of one finisher call follow each other closely, so a worker that
+// finished a job, and the caller waiting for the workers, first poll for up to
+// kSpinMicros before they sleep on the condition variable: a sleeping thread
+// takes tens of microseconds to wake, which is the length of a whole phase.
+constexpr int64_t kSpinMicros = 200;
+
 struct WorkerPool {
   std::vector<std::thread> threads;
   std::mutex mu;
   std::condition_variable cv_job, cv_done;
-  uint64_t generation = 0;  // bumped for every job
-  int32_t busy = 0;         // workers still on the current job
-  bool quit = false;
+  uint64_t generation = 0;               // bumped for every job (under mu)
+  std::atomic<uint64_t> published{0};    // the same, for polling
+  std::atomic<int32_t> busy{0};          // workers still on the current job
+  std::atomic<bool> quit{false};
+  uint64_t wake_seq = 0;             // bumped by wake() (under mu)
   std::function<void(int32_t)> job;  // runs as worker k (k >= 1)
   int32_t job_workers = 0;           // workers 1 .. job_workers - 1 take part
+
+  // polls `done` for up to kSpinMicros; true if it became true
+  template <typename Pred>
+  static bool spin(Pred done) {
+    const auto until = std::chrono::steady_clock::now() + std::chrono::microseconds(kSpinMicros);
+    for (uint32_t it = 0;; ++it) {
+      if (done()) return true;
+      if ((it & 255u) == 255u && std::chrono::steady_clock::now() > until) return false;
+    }
+  }
 
   void start(int32_t nw) {  // nw - 1 threads (the caller is worker 0)
     for (int32_t k = (int32_t)threads.size() + 1; k < nw; ++k)
       threads.emplace_back([this, k] {
-        uint64_t seen = 0;
+        uint64_t seen = 0, seen_wake = 0;
         for (;;) {
+          spin([&] { return published.load(std::memory_order_acquire) != seen || quit.load(); });
           std::function<void(int32_t)> fn;
           {
             std::unique_lock<std::mutex> lk(mu);
-            cv_job.wait(lk, [&] { return quit || generation != seen; });
-            if (quit) return;
+            cv_job.wait(lk, [&] { return quit.load() || generation != seen || wake_seq != seen_wake; });
+            if (quit.load()) return;
+            seen_wake = wake_seq;
+            if (generation == seen) continue;  // woken ahead of a job: poll for it
             seen = generation;
             if (k >= job_workers) continue;
             fn = job;
           }
           fn(k);
-          std::lock_guard<std::mutex> lk(mu);
-          if (--busy == 0) cv_done.notify_all();
+          if (busy.fetch_sub(1, std::memory_order_acq_rel) == 1) {
+            std::lock_guard<std::mutex> lk(mu);
+            cv_done.notify_all();
+          }
         }
       });
+  }
+  // wakes the workers 1 .. nw - 1 (creating them if needed) to poll for a
+  // job that is about to come
+  void wake(int32_t nw) {
+    start(nw);
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      ++wake_seq;
+    }
+    cv_job.notify_all();
   }
   void run(int32_t nw, const std::function<void(int32_t)>& fn) {
     start(nw);
@@ -141,19 +176,23 @@ struct WorkerPool {
       std::lock_guard<std::mutex> lk(mu);
       job = fn;
       job_workers = nw;
-      busy = nw - 1;
+      busy.store(nw - 1);
       ++generation;
+      published.store(generation, std::memory_order_release);
     }
     cv_job.notify_all();
     fn(0);
-    std::unique_lock<std::mutex> lk(mu);
-    cv_done.wait(lk, [&] { return busy == 0; });
+    if (!spin([&] { return busy.load(std::memory_order_acquire) == 0; })) {
+      std::unique_lock<std::mutex> lk(mu);
+      cv_done.wait(lk, [&] { return busy.load(std::memory_order_acquire) == 0; });
+    }
+    std::lock_guard<std::mutex> lk(mu);
     job = nullptr;
   }
   ~WorkerPool() {
     {
       std::lock_guard<std::mutex> lk(mu);
-      quit = true;
+      quit.store(true);
     }
     cv_job.notify_all();
     for (std::thread& t : threads) t.join();
@@ -176,6 +215,12 @@ WorkerPool& worker_pool() {
   return pool;
 }
 std::mutex g_pool_turn;  // one job at a time
+
+void finisher_pool_wake(int32_t threads) {
+  if (threads < 2) return;
+  std::unique_lock<std::mutex> turn(g_pool_turn, std::try_to_lock);
+  if (turn.owns_lock()) worker_pool().wake(threads);  // (busy with another job: nothing to do)
+}
 
 FinisherWork* finisher_work_new() { return new FinisherWork(); }
 void finisher_work_free(FinisherWork* w) { delete w; }
@@ -204,11 +249,12 @@ namespace {
 // pi0 in phase 2 -- and never settled, and a search that would settle one (or
 // finds nothing) is dropped.
 // srcs (NULL: every node of [lo, hi)): the nodes that may hold a surplus, in
-// key order -- the others are skipped without a look.
+// key order -- the others are skipped without a look.  settled (optional)
+// collects the nodes whose potential an augmentation raised.
 int solve_range(int32_t n, int32_t lo, int32_t hi, const int32_t* lam0, const int64_t* pi0v,
                 const int32_t* irp, const int2* iec, const int32_t* twin, uint8_t* y, int32_t F,
                 FinisherWork* w, Searcher& sr, int64_t* pushes_out, const int32_t* srcs = nullptr,
-                int64_t nsrc = 0) {
+                int64_t nsrc = 0, std::vector<int32_t>* settled = nullptr) {
   int64_t* pi = w->pi_p;
   int64_t* dist = w->dist.data();
   int32_t* excess = w->ex_p;
@@ -308,6 +354,7 @@ int solve_range(int32_t n, int32_t lo, int32_t hi, const int32_t* lam0, const in
         ++pushes;
         const int64_t dt = dist[t];
         for (int32_t v : sr.order) pi[v] += dt - dist[v];
+        if (settled) settled->insert(settled->end(), sr.order.begin(), sr.order.end());
       }
     }
   }
@@ -384,17 +431,61 @@ int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t*
       blocks2.push_back(make_int2(b0, std::min(b0 + kFinBlock2, seg_off[sg + 1])));
   }
   std::vector<int64_t> pushes;
+  int64_t* pi_start = w->pi_start.data();
+  // lambda at F + 1 bits, pi(L_i) - pi(R_i): every block writes it for its
+  // nodes when it is done, and the later phases again for the nodes they
+  // settle (no other potential changes); a value out of range is noted, and
+  // the range is then checked on the final values
+  std::atomic<bool> any_wide{false};
+  auto write_lam2 = [&](int32_t i) {
+    const int64_t l2 = pi[i] - pi[n + i];
+    lam2[i] = (int32_t)l2;
+    return l2 >= 2 * kLamLimit || l2 <= -2 * kLamLimit;
+  };
+  auto write_lam2_nodes = [&](const std::vector<int32_t>& nodes) {  // L or R copies
+    bool wd = false;
+    for (int32_t v : nodes) wd |= write_lam2(v < n ? v : v - n);
+    if (wd) any_wide.store(true);
+  };
+  // a block's nodes still holding a surplus, in key order
+  auto sources_left = [&](int32_t a, int32_t b, std::vector<int32_t>& out) {
+    out.clear();
+    for (int32_t i = a; i < b; ++i) {
+      if (excess[i] > 0) out.push_back(i);
+      if (excess[n + i] > 0) out.push_back(n + i);
+    }
+  };
+  // phase 1 from each block's sources; every block then copies its nodes'
+  // potentials into pi_start (phase 1 writes no other node's, so that is the
+  // state phase 2 starts from), writes their lambda and keeps the sources it
+  // left for phase 2
+  std::vector<std::vector<int32_t>> left1(skip1 ? 0 : blocks.size());
   auto t0 = clk::now();
   int r = skip1 ? 0 : run_items((int32_t)blocks.size(), threads, w, pushes,
                     [&](int32_t k, Searcher& sr, int64_t* p) {
-                      for (int32_t i = blocks[k].x; i < blocks[k].y; ++i) {
+                      const int32_t a = blocks[k].x, b = blocks[k].y;
+                      std::vector<int32_t>& src = left1[k];  // the block's sources, in key order
+                      src.clear();
+                      for (int32_t i = a; i < b; ++i) {
                         pi[i] = lam[i];
                         pi[n + i] = -(int64_t)lam[i];
                         excess[i] = exl[i];       // L_i: supply b_i minus outflow
                         excess[n + i] = -exl[i];  // R_i: inflow minus demand b_i (z is symmetric)
+                        if (exl[i] > 0) src.push_back(i);
+                        if (exl[i] < 0) src.push_back(n + i);
                       }
-                      return solve_range(n, blocks[k].x, blocks[k].y, lam, nullptr, irp, iec, twin, y, F, w,
-                                         sr, p);
+                      const int rc = solve_range(n, a, b, lam, nullptr, irp, iec, twin, y, F, w, sr, p,
+                                                 src.data(), (int64_t)src.size());
+                      std::copy(pi + a, pi + b, pi_start + a);
+                      std::copy(pi + n + a, pi + n + b, pi_start + n + a);
+                      bool wd = false;
+                      for (int32_t i = a; i < b; ++i) wd |= write_lam2(i);
+                      if (wd) any_wide.store(true);
+                      size_t kept = 0;  // a surplus never grows: the sources left are among these
+                      for (int32_t v : src)
+                        if (excess[v] > 0) src[kept++] = v;
+                      src.resize(kept);
+                      return rc;
                     });
   int64_t done1 = pushes_total(pushes);
   if (stats && !skip1) {
@@ -403,19 +494,52 @@ int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t*
     stats->threads = std::max<int32_t>(stats->threads, std::min<int32_t>(threads, (int32_t)blocks.size()));
   }
   t0 = clk::now();
-  int64_t* pi_start = w->pi_start.data();
-  if (r == 0)  // the potentials at phase 2's start, per block (every block copies its own nodes)
+  if (r == 0 && skip1)  // phase 1 ran elsewhere: the copy is taken here
     r = run_items((int32_t)blocks2.size(), threads, w, pushes, [&](int32_t k, Searcher&, int64_t*) {
       const int32_t a = blocks2[k].x, b = blocks2[k].y;
       std::copy(pi + a, pi + b, pi_start + a);
       std::copy(pi + n + a, pi + n + b, pi_start + n + a);
       return 0;
     });
+  // phase 2, from the sources phase 1 left (a phase-2 block is a run of
+  // whole phase-1 blocks: both start at the segment's first node, and
+  // kFinBlock2 is a multiple of kFinBlock); each block then lists its sources
+  // left for phase 3 and writes lambda for the nodes it settled
+  static_assert(kFinBlock2 % kFinBlock == 0, "phase-2 blocks are runs of phase-1 blocks");
+  std::vector<int32_t> first1(blocks2.size() + 1, 0);  // phase-1 blocks of phase-2 block k
+  if (!skip1) {
+    size_t q = 0;
+    for (size_t k = 0; k < blocks2.size(); ++k) {
+      while (q < blocks.size() && blocks[q].x < blocks2[k].x) ++q;
+      first1[k] = (int32_t)q;
+    }
+    first1[blocks2.size()] = (int32_t)blocks.size();
+  }
+  std::vector<std::vector<int32_t>> left(blocks2.size()), src2(blocks2.size()), settled2(blocks2.size());
   if (r == 0)
     r = run_items((int32_t)blocks2.size(), threads, w, pushes,
                   [&](int32_t k, Searcher& sr, int64_t* p) {
-                    return solve_range(n, blocks2[k].x, blocks2[k].y, nullptr, pi_start, irp, iec, twin, y, F,
-                                       w, sr, p);
+                    const int32_t a = blocks2[k].x, b = blocks2[k].y;
+                    if (skip1) {  // no lists from phase 1: every node is a candidate
+                      const int rc = solve_range(n, a, b, nullptr, pi_start, irp, iec, twin, y, F, w, sr, p);
+                      sources_left(a, b, left[k]);
+                      bool wd = false;
+                      for (int32_t i = a; i < b; ++i) wd |= write_lam2(i);
+                      if (wd) any_wide.store(true);
+                      return rc;
+                    }
+                    std::vector<int32_t>& src = src2[k];
+                    src.clear();
+                    for (int32_t q = first1[k]; q < first1[k + 1]; ++q)
+                      src.insert(src.end(), left1[q].begin(), left1[q].end());
+                    settled2[k].clear();
+                    const int rc = solve_range(n, a, b, nullptr, pi_start, irp, iec, twin, y, F, w, sr, p,
+                                               src.data(), (int64_t)src.size(), &settled2[k]);
+                    left[k].clear();  // a surplus never grows: the sources left are among these
+                    for (int32_t v : src)
+                      if (excess[v] > 0) left[k].push_back(v);
+                    write_lam2_nodes(settled2[k]);
+                    return rc;
                   });
   const int64_t done2 = pushes_total(pushes);
   if (stats) {
@@ -424,19 +548,8 @@ int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t*
   }
   t0 = clk::now();
   // phase 3: per segment, the plain search from each node still holding a
-  // surplus (collected per phase-2 block, in key order)
-  std::vector<std::vector<int32_t>> left(blocks2.size());
-  if (r == 0)
-    r = run_items((int32_t)blocks2.size(), threads, w, pushes, [&](int32_t k, Searcher&, int64_t*) {
-      std::vector<int32_t>& out = left[k];
-      out.clear();
-      for (int32_t i = blocks2[k].x; i < blocks2[k].y; ++i) {
-        if (excess[i] > 0) out.push_back(i);
-        if (excess[n + i] > 0) out.push_back(n + i);
-      }
-      return 0;
-    });
-  std::vector<std::vector<int32_t>> seg_src(segs.size());
+  // surplus
+  std::vector<std::vector<int32_t>> seg_src(segs.size()), settled(segs.size());
   for (size_t k = 0, q = 0; k < segs.size(); ++k) {
     const int32_t sg = segs[k];
     for (; q < blocks2.size() && blocks2[q].x < seg_off[sg + 1]; ++q)
@@ -445,20 +558,19 @@ int host_finisher(int32_t n, const int32_t* irp, const int2* iec, const int32_t*
   if (r == 0)
     r = run_items((int32_t)segs.size(), threads, w, pushes, [&](int32_t k, Searcher& sr, int64_t* p) {
       const int32_t sg = segs[k];
-      return solve_range(n, seg_off[sg], seg_off[sg + 1], nullptr, nullptr, irp, iec, twin, y, F, w, sr, p,
-                         seg_src[k].data(), (int64_t)seg_src[k].size());
+      settled[k].clear();
+      const int rc = solve_range(n, seg_off[sg], seg_off[sg + 1], nullptr, nullptr, irp, iec, twin, y, F, w, sr,
+                                 p, seg_src[k].data(), (int64_t)seg_src[k].size(), &settled[k]);
+      write_lam2_nodes(settled[k]);
+      return rc;
     });
   const int64_t total3 = pushes_total(pushes);
-  if (r == 0)  // lambda at F + 1 bits: pi(L_i) - pi(R_i), block by block
-    r = run_items((int32_t)blocks2.size(), threads, w, pushes, [&](int32_t k, Searcher&, int64_t*) {
-      int st = 0;
-      for (int32_t i = blocks2[k].x; i < blocks2[k].y; ++i) {
-        const int64_t l2 = pi[i] - pi[n + i];
-        if (l2 >= 2 * kLamLimit || l2 <= -2 * kLamLimit) st = 5;
-        lam2[i] = (int32_t)l2;
-      }
-      return st;
-    });
+  if (r == 0 && any_wide.load()) {  // some lambda was out of range on the way: check the final values
+    bool wd = false;
+    for (const int2& bl : blocks2)
+      for (int32_t i = bl.x; i < bl.y; ++i) wd |= write_lam2(i);
+    if (wd) r = 5;
+  }
   const int64_t total = total3;
   if (stats) {
     stats->ms_phase[2] += ms_since(t0);
