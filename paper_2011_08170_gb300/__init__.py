@@ -366,9 +366,25 @@ def f2m_extract(ctx: Ctx, device=None):
     return bad.value, x2
 
 
-def f2m_get_lambda(ctx: Ctx, device=None):
-    """Returns (lambda int32 [n], frac_bits)."""
-    lam = _out((ctx.n,), np.int32, device)
+def _room(a, count, what):
+    """Checks that the caller's output array `a` holds at least `count` entries."""
+    size = a.numel() if hasattr(a, "numel") else np.asarray(a).size
+    if size < count:
+        raise ValueError(f"{what}: the output array holds {size} entries, {count} are needed")
+    if not hasattr(a, "data_ptr") and not np.asarray(a).flags["C_CONTIGUOUS"]:
+        raise ValueError(f"{what}: the output array must be contiguous")
+    return size
+
+
+def f2m_get_lambda(ctx: Ctx, device=None, out=None):
+    """Returns (lambda int32 [n], frac_bits).  out: an int32 array (numpy or a
+    torch tensor: host, pinned host or device) of at least n entries to write
+    into instead of a new one; the result is its first n entries."""
+    if out is not None:
+        _room(out, ctx.n, "f2m_get_lambda")
+        lam = out[:ctx.n]
+    else:
+        lam = _out((ctx.n,), np.int32, device)
     p, keep = _ptr(lam)
     fb = C.c_int32()
     _check(ctx, load().f2m_get_lambda(ctx.handle, p, C.byref(fb)))
@@ -383,10 +399,23 @@ def f2m_get_bound(ctx: Ctx):
     return b.value, fb.value
 
 
-def f2m_get_x(ctx: Ctx, device=None):
-    """Returns (row_ptr, col, x2, cost) of the current candidate graph."""
+def f2m_get_x(ctx: Ctx, device=None, out=None):
+    """Returns (row_ptr, col, x2, cost) of the current candidate graph.  out:
+    (row_ptr, col, x2, cost) arrays (int32, int32, uint8, int32; numpy or torch
+    tensors: host, pinned host or device) to write into instead of new ones,
+    row_ptr with n + 1 entries and the others with room for the graph's
+    entries; the result is their leading parts."""
     L = load()
     nnz = C.c_int64(0)
+    if out is not None:
+        rp, col, x2, cost = out
+        _room(rp, ctx.n + 1, "f2m_get_x row_ptr")
+        nnz.value = min(_room(a, 0, "f2m_get_x") for a in (col, x2, cost))
+        rp = rp[:ctx.n + 1]
+        ptrs = [_ptr(a) for a in (rp, col, x2, cost)]
+        _check(ctx, L.f2m_get_x(ctx.handle, C.byref(nnz), *[p for p, _ in ptrs]))
+        m = nnz.value
+        return rp, col[:m], x2[:m], cost[:m]
     _check(ctx, L.f2m_get_x(ctx.handle, C.byref(nnz), None, None, None, None))
     rp = _out((ctx.n + 1,), np.int32, device)
     col = _out((nnz.value,), np.int32, device)
@@ -547,16 +576,33 @@ def f2m_solve_batch(b: Batch, raise_on_error: bool = True):
     return list(infos), tot
 
 
-def f2m_batch_get_lambda(b: Batch, i: int):
-    lam = np.zeros(b.ns[i], np.int32)
+def f2m_batch_get_lambda(b: Batch, i: int, out=None):
+    """(lambda of instance i, frac_bits); out as in f2m_get_lambda."""
+    if out is not None:
+        _room(out, b.ns[i], "f2m_batch_get_lambda")
+        lam = out[:b.ns[i]]
+    else:
+        lam = np.zeros(b.ns[i], np.int32)
+    p, keep = _ptr(lam)
     fb = C.c_int32()
-    _bcheck(b, load().f2m_batch_get_lambda(b.handle, i, lam.ctypes.data, C.byref(fb)))
+    _bcheck(b, load().f2m_batch_get_lambda(b.handle, i, p, C.byref(fb)))
     return lam, fb.value
 
 
-def f2m_batch_get_x(b: Batch, i: int):
+def f2m_batch_get_x(b: Batch, i: int, out=None):
+    """(row_ptr, col, x2) of instance i; out: (row_ptr, col, x2) arrays to write
+    into, as in f2m_get_x."""
     L = load()
     nnz = C.c_int64(0)
+    if out is not None:
+        rp, col, x2 = out
+        _room(rp, b.ns[i] + 1, "f2m_batch_get_x row_ptr")
+        nnz.value = min(_room(a, 0, "f2m_batch_get_x") for a in (col, x2))
+        rp = rp[:b.ns[i] + 1]
+        ptrs = [_ptr(a) for a in (rp, col, x2)]
+        _bcheck(b, L.f2m_batch_get_x(b.handle, i, C.byref(nnz), *[p for p, _ in ptrs]))
+        m = nnz.value
+        return rp, col[:m], x2[:m]
     _bcheck(b, L.f2m_batch_get_x(b.handle, i, C.byref(nnz), None, None, None))
     rp = np.zeros(b.ns[i] + 1, np.int32)
     col = np.zeros(max(nnz.value, 1), np.int32)

@@ -290,7 +290,7 @@ extern "C" const char* f2m_last_error(const f2m_ctx* ctx) {
 extern "C" void f2m_destroy(f2m_ctx* c) {
   if (!c) return;
   DevSyncedScope synced;  // one wait for the device, then every block goes to the cache
-  dfree(c->d_xy); dfree(c->d_rp); dfree(c->d_ec); dfree(c->d_x2); dfree(c->d_tiles);
+  dfree(c->d_xy); dfree(c->d_rp); dfree(c->d_ec); dfree(c->d_ec_alt); dfree(c->d_x2); dfree(c->d_tiles);
   dfree(c->d_seg_off); dfree(c->d_fin_include);
   dfree(c->d_lam[0]); dfree(c->d_lam[1]); dfree(c->d_lam2); dfree(c->d_exl); dfree(c->d_gdp);
   dfree(c->d_trace_b2); dfree(c->d_trace_ch); dfree(c->d_pts); dfree(c->d_pairs);
@@ -427,12 +427,15 @@ f2m_status f2m::create_internal(const int32_t* xy, int32_t n, const int32_t* row
       finisher_work_reserve(c->fin_work, n);
     }
     if (e == cudaSuccess) e = dalloc(&c->d_x2, c->ec_cap);
+    c->x2_cap = c->ec_cap;
     // the pricing scan's and the merge's buffers, so that a solve allocates
     // nothing unless its graph outgrows them
     if (e == cudaSuccess && p.pricing) {
       c->pairs_cap = p.pricing_cap;
       c->tmp_col_cap = c->ec_cap;
-      e = dalloc(&c->d_pts, n);
+      c->ec_alt_cap = c->ec_cap;
+      e = dalloc(&c->d_ec_alt, c->ec_alt_cap);
+      if (e == cudaSuccess) e = dalloc(&c->d_pts, n);
       if (e == cudaSuccess) e = dalloc(&c->d_count, 1);
       if (e == cudaSuccess) e = dalloc(&c->d_tile, 1);
       if (e == cudaSuccess) e = dalloc(&c->d_pairs, c->pairs_cap);
@@ -1038,15 +1041,19 @@ f2m_status f2m::merge_internal(f2m_ctx* c, const int2* d_pairs, int64_t npairs, 
   CK(c, cudaEventRecord(c->ev0, c->st));
   CK(c, launch_merge_count(c->d_rp, d_pairs, npairs, n, mb, c->st));
   CK(c, launch_merge_fill(c->d_rp, c->d_ec, d_pairs, npairs, n, mb, c->st));
-  if (need > c->ec_cap) {  // old entries now live in tmp_col: the edge array can be replaced
-    CK(c, cudaStreamSynchronize(c->st));
-    dfree(c->d_ec);
-    dfree(c->d_x2);
-    c->ec_cap = need + (need >> 3);
-    CK(c, dalloc(&c->d_ec, c->ec_cap));
-    CK(c, dalloc(&c->d_x2, c->ec_cap));
+  if (need > c->ec_alt_cap) {  // the array the merged rows go to
+    dfree(c->d_ec_alt);
+    c->ec_alt_cap = need + (need >> 3);
+    CK(c, dalloc(&c->d_ec_alt, c->ec_alt_cap));
   }
-  CK(c, launch_merge_finish(c->d_xy, n, mb, c->d_ec, c->st));
+  if (need > c->x2_cap) {
+    dfree(c->d_x2);
+    c->x2_cap = need + (need >> 3);
+    CK(c, dalloc(&c->d_x2, c->x2_cap));
+  }
+  CK(c, launch_merge_finish(c->d_xy, c->d_rp, c->d_ec, n, mb, c->d_ec_alt, c->st));
+  std::swap(c->d_ec, c->d_ec_alt);
+  std::swap(c->ec_cap, c->ec_alt_cap);
   CK(c, cudaMemcpyAsync(c->d_rp, c->d_new_rp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToDevice, c->st));
   int32_t nnz_h = 0;
   CK(c, cudaMemcpyAsync(&nnz_h, c->d_new_rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st));

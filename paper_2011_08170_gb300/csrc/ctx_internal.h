@@ -44,7 +44,10 @@ struct f2m_ctx {
   int2* d_xy = nullptr;
   int32_t* d_rp = nullptr;
   int2* d_ec = nullptr;
+  int2* d_ec_alt = nullptr;  // [ec_alt_cap] the merge writes here, then the two swap
+  int64_t ec_alt_cap = 0;
   uint8_t* d_x2 = nullptr;
+  int64_t x2_cap = 0;
   int32_t* d_lam[2] = {nullptr, nullptr};
   int32_t* d_lam2 = nullptr;
   int32_t* d_exl = nullptr;   // [n] the finisher's surpluses (its own: the plan's scratch

@@ -160,8 +160,9 @@ cudaError_t launch_merge_count(const int32_t* rp, const int2* pairs, int64_t npa
                                MergeBuffers& mb, cudaStream_t st);
 cudaError_t launch_merge_fill(const int32_t* rp, const int2* ec, const int2* pairs, int64_t npairs,
                               int32_t n, MergeBuffers& mb, cudaStream_t st);
-cudaError_t launch_merge_finish(const int2* xy, int32_t n, MergeBuffers& mb, int2* ec_out,
-                                cudaStream_t st);
+// ec_out: another array than ec_in (untouched rows are copied from ec_in)
+cudaError_t launch_merge_finish(const int2* xy, const int32_t* rp, const int2* ec_in, int32_t n,
+                                MergeBuffers& mb, int2* ec_out, cudaStream_t st);
 // exclusive scan of in[0..m) into out[0..m], out[m] = total (m+1 outputs)
 cudaError_t launch_scan(const int32_t* in, int32_t* out, int32_t m, int32_t* block_sums,
                         cudaStream_t st);

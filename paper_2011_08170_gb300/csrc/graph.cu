@@ -235,11 +235,21 @@ cudaError_t launch_merge_count(const int32_t* rp, const int2* pairs, int64_t npa
   return launch_scan(mb.deg, mb.tmp_rp, n, mb.block_sums, st);
 }
 
-// copy old rows to the front of each new row; deg becomes the append cursor
+// Rows are strictly increasing (checked when the graph is created, and kept
+// so by every merge), so a row that no pair touches comes out of the merge as
+// it went in: only the touched rows (those that gained room in tmp_rp) are
+// copied, sorted and deduplicated in tmp_col; the others keep their entries.
+__device__ __forceinline__ bool merge_touched(const int32_t* rp, const int32_t* tmp_rp, int v) {
+  return tmp_rp[v + 1] - tmp_rp[v] != rp[v + 1] - rp[v];
+}
+
+// copy a touched row's old entries to the front of its new row; deg becomes
+// the append cursor
 __global__ void merge_copy_kernel(const int32_t* __restrict__ rp, const int2* __restrict__ ec,
                                   int32_t n, const int32_t* __restrict__ tmp_rp, int32_t* tmp_col,
                                   int32_t* cursor) {
   F2M_GRID_STRIDE(v, n) {
+    if (!merge_touched(rp, tmp_rp, (int)v)) continue;
     const int a = rp[v], b = rp[v + 1], o = tmp_rp[v];
     for (int e = a; e < b; ++e) tmp_col[o + (e - a)] = ec[e].x;
     cursor[v] = o + (b - a);
@@ -268,11 +278,16 @@ cudaError_t launch_merge_fill(const int32_t* rp, const int2* ec, const int2* pai
   return cudaGetLastError();
 }
 
-// sort each row (insertion sort: rows are short) and count distinct columns
-__global__ void merge_sort_rows_kernel(const int32_t* __restrict__ tmp_rp, int32_t* tmp_col,
-                                       int32_t n, int32_t* uniq) {
+// sort each touched row (insertion sort: rows are short) and count distinct
+// columns; an untouched row keeps its length
+__global__ void merge_sort_rows_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ tmp_rp,
+                                       int32_t* tmp_col, int32_t n, int32_t* uniq) {
   F2M_GRID_STRIDE(v, n) {
     const int a = tmp_rp[v], b = tmp_rp[v + 1];
+    if (!merge_touched(rp, tmp_rp, (int)v)) {
+      uniq[v] = b - a;
+      continue;
+    }
     for (int i = a + 1; i < b; ++i) {
       const int x = tmp_col[i];
       int j = i - 1;
@@ -285,12 +300,20 @@ __global__ void merge_sort_rows_kernel(const int32_t* __restrict__ tmp_rp, int32
   }
 }
 
-__global__ void merge_compact_kernel(const int2* __restrict__ xy, const int32_t* __restrict__ tmp_rp,
+// the merged rows into ec_out (another array than ec_in): an untouched row's
+// entries as they were (its costs are the exact costs of its points), a
+// touched row's distinct columns with their exact costs
+__global__ void merge_compact_kernel(const int2* __restrict__ xy, const int32_t* __restrict__ rp,
+                                     const int2* __restrict__ ec_in, const int32_t* __restrict__ tmp_rp,
                                      const int32_t* __restrict__ tmp_col, int32_t n,
                                      const int32_t* __restrict__ new_rp, int2* __restrict__ ec_out) {
   F2M_GRID_STRIDE(v, n) {
-    const int a = tmp_rp[v], b = tmp_rp[v + 1];
     int o = new_rp[v];
+    if (!merge_touched(rp, tmp_rp, (int)v)) {
+      for (int e = rp[v]; e < rp[v + 1]; ++e) ec_out[o++] = ec_in[e];
+      continue;
+    }
+    const int a = tmp_rp[v], b = tmp_rp[v + 1];
     const int2 pv = xy[v];
     for (int i = a; i < b; ++i) {
       if (i > a && tmp_col[i] == tmp_col[i - 1]) continue;
@@ -300,15 +323,15 @@ __global__ void merge_compact_kernel(const int2* __restrict__ xy, const int32_t*
   }
 }
 
-cudaError_t launch_merge_finish(const int2* xy, int32_t n, MergeBuffers& mb, int2* ec_out,
-                                cudaStream_t st) {
-  merge_sort_rows_kernel<<<grid_for(n, 128), 128, 0, st>>>(mb.tmp_rp, mb.tmp_col, n, mb.deg);
+cudaError_t launch_merge_finish(const int2* xy, const int32_t* rp, const int2* ec_in, int32_t n,
+                                MergeBuffers& mb, int2* ec_out, cudaStream_t st) {
+  merge_sort_rows_kernel<<<grid_for(n, 128), 128, 0, st>>>(rp, mb.tmp_rp, mb.tmp_col, n, mb.deg);
   count_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   err = launch_scan(mb.deg, mb.new_rp, n, mb.block_sums, st);
   if (err != cudaSuccess) return err;
-  merge_compact_kernel<<<grid_for(n, 128), 128, 0, st>>>(xy, mb.tmp_rp, mb.tmp_col, n, mb.new_rp,
+  merge_compact_kernel<<<grid_for(n, 128), 128, 0, st>>>(xy, rp, ec_in, mb.tmp_rp, mb.tmp_col, n, mb.new_rp,
                                                          ec_out);
   count_launch();
   return cudaGetLastError();

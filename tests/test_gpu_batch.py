@@ -91,6 +91,13 @@ def test_batch_matches_oracle_optimum(lib, oracle_lib):
             assert infos[i].finisher_calls == 0 and fb == r.frac_bits
             assert np.array_equal(lam, r.lam) and np.array_equal(x2, r.x2)
         compare_solves(oracle_lib, f2m, d)
+        # the same read into the caller's buffers (with spare room)
+        n, m = len(d["xy"]), len(col)
+        out = (np.zeros(n + 3, np.int32), np.zeros(m + 5, np.int32), np.zeros(m + 5, np.uint8))
+        got = f2m.f2m_batch_get_x(b, i, out=out)
+        assert all(np.array_equal(a, c) for a, c in zip(got, (rp, col, x2)))
+        got_lam, _ = f2m.f2m_batch_get_lambda(b, i, out=np.zeros(n + 1, np.int32))
+        assert np.array_equal(got_lam, lam)
 
 
 def test_batch_log_uniform_sizes(lib, oracle_lib):

@@ -232,6 +232,58 @@ def test_merge(lib, O):
     assert np.array_equal(rp2, rp_o) and np.array_equal(col2, col_o)
 
 
+def test_read_back_into_caller_buffers(lib):
+    # the out= forms write the same values into the caller's arrays (pinned
+    # host tensors, numpy arrays with spare room) and return their leading parts
+    import torch
+    d = inst("uniform", 5000, 4, 10)
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"])
+    f2m.f2m_solve(ctx)
+    rp, col, x2, cost = f2m.f2m_get_x(ctx)
+    lam, fb = f2m.f2m_get_lambda(ctx)
+    m = len(col)
+    pinned = (torch.empty(5001, dtype=torch.int32).pin_memory(), torch.empty(m + 7, dtype=torch.int32).pin_memory(),
+              torch.empty(m + 7, dtype=torch.uint8).pin_memory(), torch.empty(m + 7, dtype=torch.int32).pin_memory())
+    plain = (np.full(5003, -1, np.int32), np.full(m, -1, np.int32), np.full(m + 1, 9, np.uint8),
+             np.full(m + 2, -1, np.int32))
+    for out in (pinned, plain):
+        got = f2m.f2m_get_x(ctx, out=out)
+        for a, b in zip(got, (rp, col, x2, cost)):
+            assert np.array_equal(np.asarray(a), b)
+    lam_out = torch.empty(5000, dtype=torch.int32).pin_memory()
+    got, fb2 = f2m.f2m_get_lambda(ctx, out=lam_out)
+    assert fb2 == fb and np.array_equal(got.numpy(), lam)
+    with pytest.raises(f2m.F2MError):  # room for fewer entries than the graph has: INVALID_ARG
+        f2m.f2m_get_x(ctx, out=(plain[0], plain[1][:m - 1], plain[2], plain[3]))
+    with pytest.raises(ValueError):  # a row_ptr array too short is caught before the call
+        f2m.f2m_get_x(ctx, out=(plain[0][:5000], plain[1], plain[2], plain[3]))
+
+
+def test_merge_sequence_touching_few_rows(lib, O):
+    # rows no pair touches are carried over as they are: merges of a few
+    # pairs, one of pairs already present, then one that outgrows the edge
+    # arrays, each equal to the oracle's union of everything added so far
+    n = 20000
+    d = inst("uniform", n, 3, 10)
+    rng = np.random.default_rng(7)
+    ctx = f2m.f2m_create(d["xy"], d["row_ptr"], d["col"])
+    rp_o, col_o = d["row_ptr"], d["col"]
+    present = np.stack([np.repeat(np.arange(n), np.diff(rp_o))[:5], col_o[:5]], 1).astype(np.int32)
+    for size in (3, 40, 0, 2 * len(col_o)):
+        if size == 0:
+            pairs = present
+        else:
+            u = rng.integers(0, n, size=size)
+            v = rng.integers(0, n, size=size)
+            keep = u != v
+            pairs = np.stack([u, v], 1)[keep].astype(np.int32)
+        rp_o, col_o = O.merge(rp_o, col_o, np.unique(np.sort(pairs, 1), axis=0))
+        f2m.f2m_add_edges(ctx, pairs)
+        rp, col, _, cost = f2m.f2m_get_x(ctx)
+        assert np.array_equal(rp, rp_o) and np.array_equal(col, col_o)
+        assert np.array_equal(cost, O.cost_table(d["xy"], rp_o, col_o))
+
+
 # ---- the whole solve ------------------------------------------------------------------------
 
 def _compare_solve(O, d, **kw):
