@@ -176,6 +176,62 @@ void dev_free_synced(void* p) {
 
 }  // namespace f2m
 
+// The host's pinned copies of the finisher's input and output (row offsets,
+// entries, twins, flow, surpluses, lambda): one set for the process, taken by
+// one finisher call at a time.  Contexts that each kept their own set touched
+// tens of MB of pinned pages apiece, and the device's copies into pages it had
+// not touched lately ran several times slower than into recently used ones;
+// one set stays in use.  `owner` is the context whose graph the entry arrays
+// hold (its fin_version says at which version); any other context copies its
+// graph again.
+struct HostMirror {
+  std::mutex mu;
+  int32_t* irp = nullptr;
+  int2* iec = nullptr;
+  int32_t* twin = nullptr;
+  uint8_t* y = nullptr;
+  int32_t* exl = nullptr;
+  int32_t* lam = nullptr;
+  int32_t* lam2 = nullptr;
+  int64_t cap = 0;    // entries
+  int64_t ncap = 0;   // nodes
+  const f2m_ctx* owner = nullptr;
+};
+static HostMirror g_mirror;
+
+// takes the mirror for context c (lock held by the caller) with room for its
+// graph; points c's host arrays at it
+static cudaError_t take_mirror(f2m_ctx* c) {
+  HostMirror& M = g_mirror;
+  const int64_t cap = std::max<int64_t>(c->fin_cap, c->nnz);
+  if (M.cap < cap || M.ncap < (int64_t)c->n + 1) {
+    const int64_t ec = std::max<int64_t>(cap, M.cap), nc = std::max<int64_t>((int64_t)c->n + 1, M.ncap);
+    void* old[] = {M.irp, M.iec, M.twin, M.y, M.exl, M.lam, M.lam2};
+    for (void* q : old) pin_free(q);
+    M.irp = nullptr; M.iec = nullptr; M.twin = nullptr; M.y = nullptr;
+    M.exl = nullptr; M.lam = nullptr; M.lam2 = nullptr;
+    M.cap = M.ncap = 0;
+    M.owner = nullptr;
+    cudaError_t e = pin_alloc((void**)&M.iec, sizeof(int2) * ec);
+    if (e == cudaSuccess) e = pin_alloc((void**)&M.twin, sizeof(int32_t) * ec);
+    if (e == cudaSuccess) e = pin_alloc((void**)&M.y, ec);
+    if (e == cudaSuccess) e = pin_alloc((void**)&M.irp, sizeof(int32_t) * nc);
+    if (e == cudaSuccess) e = pin_alloc((void**)&M.exl, sizeof(int32_t) * nc);
+    if (e == cudaSuccess) e = pin_alloc((void**)&M.lam, sizeof(int32_t) * nc);
+    if (e == cudaSuccess) e = pin_alloc((void**)&M.lam2, sizeof(int32_t) * nc);
+    if (e != cudaSuccess) return e;
+    M.cap = ec;
+    M.ncap = nc;
+  }
+  if (M.owner != c) {
+    c->fin_version = -1;  // the entry arrays hold another graph
+    M.owner = c;
+  }
+  c->h_irp = M.irp; c->h_iec = M.iec; c->h_twin = M.twin; c->h_y = M.y;
+  c->h_exl = M.exl; c->h_lam = M.lam; c->h_lam2 = M.lam2;
+  return cudaSuccess;
+}
+
 static void free_finisher_buffers(f2m_ctx* c) {
   dev_free(c->d_twin);
   dev_free(c->d_fy);
@@ -188,8 +244,10 @@ static void free_finisher_buffers(f2m_ctx* c) {
   c->h_fex = nullptr;
   c->fblk_cap = 0;
   c->fheap_cap = 0;
-  void* hp[] = {c->h_irp, c->h_iec, c->h_twin, c->h_y, c->h_exl, c->h_lam, c->h_lam2};
-  for (void* q : hp) pin_free(q);
+  {
+    std::lock_guard<std::mutex> lk(g_mirror.mu);
+    if (g_mirror.owner == c) g_mirror.owner = nullptr;  // a later context may sit at this address
+  }
   c->d_twin = nullptr; c->d_fy = nullptr;
   c->h_irp = nullptr; c->h_iec = nullptr; c->h_twin = nullptr; c->h_y = nullptr;
   c->h_exl = nullptr; c->h_lam = nullptr; c->h_lam2 = nullptr;
@@ -198,31 +256,17 @@ static void free_finisher_buffers(f2m_ctx* c) {
   c->twin_version = -1;
 }
 
-// device and pinned host buffers for `cap` entries (node-sized ones once)
+// device buffers for `cap` entries (the host side is the process's mirror,
+// taken per finisher call)
 static cudaError_t alloc_finisher_buffers(f2m_ctx* c, int64_t cap) {
-  const int32_t n = c->n;
-  const bool first = c->h_irp == nullptr;
   dev_free(c->d_twin);
   dev_free(c->d_fy);
-  pin_free(c->h_iec);
-  pin_free(c->h_twin);
-  pin_free(c->h_y);
   c->d_twin = nullptr; c->d_fy = nullptr;
-  c->h_iec = nullptr; c->h_twin = nullptr; c->h_y = nullptr;
   c->fin_cap = 0;
   c->fin_version = -1;
   c->twin_version = -1;
   cudaError_t e = dev_malloc((void**)&c->d_twin, sizeof(int32_t) * cap);
   if (e == cudaSuccess) e = dev_malloc((void**)&c->d_fy, cap);
-  if (e == cudaSuccess) e = pin_alloc((void**)&c->h_iec, sizeof(int2) * cap);
-  if (e == cudaSuccess) e = pin_alloc((void**)&c->h_twin, sizeof(int32_t) * cap);
-  if (e == cudaSuccess) e = pin_alloc((void**)&c->h_y, cap);
-  if (e == cudaSuccess && first) {
-    e = pin_alloc((void**)&c->h_irp, sizeof(int32_t) * (n + 1));
-    if (e == cudaSuccess) e = pin_alloc((void**)&c->h_exl, sizeof(int32_t) * n);
-    if (e == cudaSuccess) e = pin_alloc((void**)&c->h_lam, sizeof(int32_t) * n);
-    if (e == cudaSuccess) e = pin_alloc((void**)&c->h_lam2, sizeof(int32_t) * n);
-  }
   if (e == cudaSuccess) c->fin_cap = cap;
   return e;
 }
@@ -1207,6 +1251,14 @@ f2m_status f2m::finisher_internal(f2m_ctx* c, int64_t* aug, const uint8_t* h_inc
   const int32_t nseg = (int32_t)c->seg_off.size() - 1;
   if (c->fin_cap < c->nnz) CK(c, alloc_finisher_buffers(c, c->ec_cap));
   if (!c->fin_work) c->fin_work = finisher_work_new();
+  // the host mirror for this call; on any return the stream is drained
+  // before the next call may take the mirror (no copy still reads or writes it)
+  std::unique_lock<std::mutex> mirror_lock(g_mirror.mu);
+  struct Drain {
+    cudaStream_t st;
+    ~Drain() { cudaStreamSynchronize(st); }
+  } drain{c->st};
+  CK(c, take_mirror(c));
   static const int32_t hw = (int32_t)std::thread::hardware_concurrency();
   unsigned long long missing = 0;
   const bool twin_new = c->twin_version != P.version;
