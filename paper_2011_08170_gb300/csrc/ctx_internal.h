@@ -112,11 +112,12 @@ struct f2m_ctx {
   bool plan1_pending = false;  // the one-sweep tiles are built at the next GDP phase
   bool plan2_pending = false;  // the two-sweep tiles are built at the next GDP phase
   f2m::ClassPlan classes;    // colour classes of the class-by-class GDP
-  // exact finisher: device scratch, pinned host mirrors, host work arrays
+  // exact finisher: device scratch, host work arrays; the h_ arrays point into
+  // the process's one pinned host mirror while a finisher call holds it
   int32_t* d_twin = nullptr;
   uint8_t* d_fy = nullptr;
-  int64_t fin_cap = 0;          // entries the finisher buffers hold
-  int64_t fin_version = -1;     // plan version mirrored whole on the host
+  int64_t fin_cap = 0;          // entries the device finisher buffers hold
+  int64_t fin_version = -1;     // plan version the host mirror holds whole (while this context owns it)
   int64_t twin_version = -1;    // plan version of d_twin
   int32_t* h_irp = nullptr;
   int2* h_iec = nullptr;
